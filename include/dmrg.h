@@ -1,0 +1,262 @@
+/*
+ * dmrg.h -- C ABI of the GB300 (sm_103a) adaptive two-site DMRG library.
+ *
+ * The library implements the per-bond local update of adaptive two-site DMRG
+ * described in arXiv 2604.03960 ("Adaptive Tensor Network Simulation via
+ * Entropy-Feedback PID Control and GPU-Accelerated SVD"): the effective
+ * Hamiltonian eigenproblem of Eq. (19) solved by Lanczos, the SVD of the
+ * two-site tensor (Eq. 20), the von Neumann entropy (Eq. 5), the EMA ->
+ * predictor -> PID choice of the bond dimension (Eqs. 8-11, 16; Algorithms
+ * 1-2), truncation (Eq. 4, Section 10) and the environment update.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - All tensors are FP64, row-major, last index fastest, spin-1/2 (d = 2).
+ *  - MPO  W[i][wl][wr][s][s']   (N sites, D x D x 2 x 2 each; s = bra, s' = ket).
+ *    The left boundary selects row D-1, the right boundary column 0.
+ *  - MPS  A[i][a][s][b]          chi_i x 2 x chi_{i+1}.
+ *  - Environments L[w][a'][a], R[w][b'][b] (D x chi x chi; a' bra, a ket).
+ *  - Two-site tensor theta[a][s1][s2][b]; as a matrix it is (2 chi_l) x (2 chi_r).
+ *  - Pointers named *_dev are device pointers owned by the caller (normally
+ *    allocated by PyTorch); the library never frees or retains them beyond
+ *    the call.  Pointers named *_host are host pointers.
+ *  - All work is enqueued on the context's stream.  Calls that return host
+ *    values synchronise that stream before returning.
+ *  - Every call returns a dmrg_status.  Errors found on the device (a bounded
+ *    wait that gave up, a non-finite value) are recorded in a device status
+ *    word and reported by the next synchronising call or dmrg_get_status();
+ *    no call traps or aborts.
+ *  - The library allocates its own workspace (device arena) inside
+ *    dmrg_create/dmrg_state_create and frees it in the matching destroy.
+ */
+#ifndef DMRG_GB300_H
+#define DMRG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmrg_ctx dmrg_ctx;
+typedef struct dmrg_state dmrg_state;
+
+typedef enum {
+    DMRG_OK = 0,
+    DMRG_EINVAL = 1,       /* bad argument (null pointer, size out of range) */
+    DMRG_ENOMEM = 2,       /* device allocation failed                        */
+    DMRG_ENOCONV = 3,      /* Jacobi SVD did not converge in jacobi_max_sweeps */
+    DMRG_ENAN = 4,         /* non-finite value detected                       */
+    DMRG_ETIMEOUT = 5,     /* a bounded device-side wait gave up              */
+    DMRG_ECUDA = 6,        /* a CUDA runtime call failed                      */
+    DMRG_EUNSUPPORTED = 7  /* option not available (e.g. precision on this device) */
+} dmrg_status;
+
+typedef enum { DMRG_XXZ = 0, DMRG_J1J2 = 1, DMRG_TFIM = 2 } dmrg_model;
+
+typedef enum {
+    DMRG_PREC_FP64 = 0,    /* every contraction in FP64                                  */
+    DMRG_PREC_3XTF32 = 1,  /* H_eff / environment / theta contractions as 3xTF32 tcgen05
+                              GEMMs with FP32 accumulation; Lanczos, SVD, entropy in FP64 */
+    DMRG_PREC_BF16X3 = 2   /* reserved: split-BF16 contractions                           */
+} dmrg_precision;
+
+typedef enum {
+    DMRG_CTRL_PID = 0,       /* EMA -> predictor -> PID (Algorithm 2, Eqs. 8, 16)       */
+    DMRG_CTRL_DIRECT = 1,    /* chi = clamp(ceil(gamma exp(Sbar))) (Algorithm 1)         */
+    DMRG_CTRL_FIXED = 2,     /* chi = chi_fixed                                          */
+    DMRG_CTRL_THRESHOLD = 3, /* chi = chi_max; the eps_trunc threshold decides (Sec. 10) */
+    DMRG_CTRL_MLP = 4        /* learned scheduler with the PID as fallback               */
+} dmrg_ctrl_mode;
+
+/* Parameters of the local update and of the controller. */
+typedef struct {
+    double alpha_ema;   /* EMA smoothing alpha, Eq. (8)                               */
+    double gamma;       /* margin gamma of the direct map, Eq. (7)                    */
+    double S_target;    /* target entropy, Eq. (9)                                    */
+    double Kp, Ki, Kd;  /* PID gains, Eq. (10)                                        */
+    double beta;        /* predictor aggressiveness, Eq. (16)                         */
+    double eps_trunc;   /* drop s_j / |s| <= eps_trunc (Section 10)                   */
+    double eps_conv;    /* stop when |dE/E| < eps_conv (Section 10)                   */
+    int chi_min, chi_max;
+    int lanczos_steps;  /* Krylov steps per bond (K)                                   */
+    int max_sweeps;     /* sweep horizon (feature scaling of the learned scheduler)   */
+    int jacobi_max_sweeps;
+    int prec;           /* dmrg_precision                                              */
+    int ctrl;           /* dmrg_ctrl_mode                                              */
+    int ema_init_zero;  /* 1: first EMA value alpha*S (Section 10) instead of S (Sec. 4) */
+    int multiplet_guard;/* 1: never truncate inside a group of equal singular values  */
+    int pid_steps_per_sweep; /* 2: controller step on every visit; 1: L->R visits only */
+    int chi_init;       /* bond dimension of the random initial MPS                   */
+    int chi_fixed;      /* chi for DMRG_CTRL_FIXED                                    */
+    int second_order;   /* 1: second-order predictor (Section 7, curvature term)      */
+} dmrg_params;
+
+typedef struct {
+    int N;              /* number of sites                                             */
+    double J;           /* nearest-neighbour coupling (TFIM: zz coupling)              */
+    double Delta;       /* XXZ anisotropy (TFIM: transverse field h)                   */
+    double J2;          /* next-nearest-neighbour coupling (J1-J2 only)               */
+} dmrg_model_params;
+
+/* Per-bond controller state (device-resident; same meaning as Algorithm 2's
+ * inputs plus the predictor's and the learned scheduler's history). */
+typedef struct {
+    double Sbar, Sbar_prev, Sbar_prev2, e_prev, I;
+    double hist[8];
+    int chi, initialized, nhist, pad;
+} dmrg_ctrl_state;
+
+/* One record per sweep, filled by dmrg_sweep (host memory). */
+typedef struct {
+    double E;              /* Ritz value at the last bond of the sweep                 */
+    double max_trunc_err;  /* max over visits of eps (Eq. 4)                           */
+    double mean_chi;       /* mean retained bond dimension over the sweep's visits     */
+    double seconds;        /* device time of the sweep (CUDA events)                   */
+    double flops;          /* algorithmic flops of the sweep (realised shapes)         */
+    int max_chi;           /* largest retained bond dimension                          */
+    int n_visits;          /* bond visits (2N - 3)                                     */
+    int jacobi_sweeps;     /* total Jacobi sweeps over the sweep's SVDs                */
+    int lanczos_steps;     /* total Lanczos steps over the sweep                        */
+} dmrg_sweep_record;
+
+/* Per-visit record (bond, Ritz value, entropy, truncation error, retained k,
+ * controller chi), filled by dmrg_sweep when requested. */
+typedef struct {
+    int bond, k, chi_ctrl, direction;
+    double E, S, trunc_err;
+} dmrg_visit_record;
+
+/* ---------------------------------------------------------------------- */
+/* Context                                                                */
+/* ---------------------------------------------------------------------- */
+/* Create a context on `device` that enqueues all work on `cuda_stream`
+ * (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL = the
+ * legacy default stream).  *out receives the handle. */
+dmrg_status dmrg_create(dmrg_ctx **out, int device, void *cuda_stream);
+void dmrg_destroy(dmrg_ctx *ctx);
+/* Device status word: DMRG_OK or the first device-side error since the last
+ * call (then cleared).  Synchronises the stream. */
+dmrg_status dmrg_get_status(dmrg_ctx *ctx);
+const char *dmrg_status_string(dmrg_status s);
+/* Bond dimension D of the MPO of `model` (5, 8, 3), or -1. */
+int dmrg_mpo_dim(int model);
+
+/* ---------------------------------------------------------------------- */
+/* Hot-path entry points                                                  */
+/* ---------------------------------------------------------------------- */
+
+/* MPO of the paper's benchmark Hamiltonians: XXZ (Eq. 18 at Delta = 1),
+ * J1-J2 and transverse-field Ising (Table 5), written on the device into
+ * W_dev (N * D * D * 4 doubles, caller-owned, layout above). */
+dmrg_status dmrg_build_mpo(dmrg_ctx *ctx, dmrg_model model, const dmrg_model_params *mp, double *W_dev);
+
+/* Create a DMRG state for N sites: copies W_dev (N*D*D*4) and the Gaussian
+ * entries of the initial MPS (mps_init_dev, site after site, chi_i =
+ * min(chi_init, 2^i, 2^(N-i)), "random initial state" of Section 10), brings
+ * it to right-canonical form on the device, builds every right environment
+ * and sets each bond's controller to chi = chi_min, S-bar = I = 0
+ * (Section 10).  Memory for the MPS, environments and workspace is sized for
+ * chi_max and owned by the state.  The parameter block is copied. */
+dmrg_status dmrg_state_create(dmrg_ctx *ctx, int D, const dmrg_model_params *mp, const double *W_dev,
+                              const dmrg_params *p, const double *mps_init_dev, dmrg_state **out);
+void dmrg_state_destroy(dmrg_state *st);
+
+/* Run n_sweeps two-site sweeps (Section 10): left to right over bonds
+ * 0..N-2, right to left over N-3..0, a local update at each visit.
+ * rec_host (n_sweeps entries) receives one record per sweep; visits_host
+ * (optional, n_sweeps*(2N-3) entries) one record per bond visit.  If
+ * stop_on_conv, stops once |dE/E| < eps_conv; *sweeps_done (optional)
+ * receives the number of sweeps run. */
+dmrg_status dmrg_sweep(dmrg_ctx *ctx, dmrg_state *st, int n_sweeps, int stop_on_conv,
+                       dmrg_sweep_record *rec_host, dmrg_visit_record *visits_host, int *sweeps_done);
+
+/* One local update at `bond` (sites bond, bond+1) in `direction` (+1: the
+ * orthogonality centre moves right, -1: left).  The state's centre must
+ * be at that bond (as it is at every visit of dmrg_sweep).  *E_out (host)
+ * receives the Ritz value (Eq. 19); *k_out (optional) the retained chi. */
+dmrg_status bond_update(dmrg_ctx *ctx, dmrg_state *st, int bond, int direction, double *E_out, int *k_out);
+
+/* SVD of the m x n row-major matrix theta_dev (Eq. 20), by one-sided
+ * (Hestenes) Jacobi on the device, then truncation (Section 10):
+ *   k = min(chi_max, rank, #{s_j/|s| > eps}), k >= 1.
+ * Outputs (caller-owned device buffers, r = min(m, n)):
+ *   U_dev  m x r, s_dev r (descending), Vt_dev r x n  -- the full factors;
+ *   the retained factors are their first k columns/values/rows.
+ * Host outputs: *k_out, *S_out (Eq. 5 entropy of the full spectrum),
+ * *trunc_err_out (Eq. 4 on the normalised spectrum).  Any host output may
+ * be NULL.  Synchronises the stream.  Returns DMRG_ENOCONV if the Jacobi
+ * iteration did not converge within the context's jacobi_max_sweeps (60). */
+dmrg_status svd_truncate(dmrg_ctx *ctx, const double *theta_dev, int m, int n, int chi_max, double eps,
+                         double *U_dev, double *s_dev, double *Vt_dev, int *k_out, double *S_out,
+                         double *trunc_err_out);
+
+/* One controller step for each of n_bonds bonds (Algorithms 1-2 with
+ * Eqs. 8 and 16): S_raw_dev[i] is bond i's raw entropy, st_dev[i] its
+ * state (updated in place), chi_out_dev[i] receives the new chi.  All
+ * arithmetic is FP64 without fused multiply-add, in a fixed order, so a
+ * recorded entropy sequence reproduces the integer chi schedule exactly. */
+dmrg_status entropy_pid_step(dmrg_ctx *ctx, int n_bonds, const double *S_raw_dev, dmrg_ctrl_state *st_dev,
+                             const dmrg_params *p_host, int *chi_out_dev);
+
+/* ---------------------------------------------------------------------- */
+/* Building blocks exposed for sampled parity checks and benchmarks       */
+/* ---------------------------------------------------------------------- */
+
+/* Eq. (5) entropy and Eq. (4) truncation errors of one spectrum:
+ * S_dev[0] = -sum p ln p, eps_dev[k] = sqrt(sum_{j>=k} p_j), k = 0..n
+ * (eps_dev optional, n+1 entries).  FP64 with compensated summation. */
+dmrg_status dmrg_entropy(dmrg_ctx *ctx, int n, const double *s_dev, double *S_dev, double *eps_dev);
+
+/* y = H_eff theta (Eq. 19) for environments L_dev (D x cl x cl), R_dev
+ * (D x cr x cr), MPO tensors W1_dev, W2_dev (D x D x 2 x 2) and
+ * theta_dev (cl x 2 x 2 x cr), in precision `prec` (dmrg_precision). */
+dmrg_status dmrg_heff_apply(dmrg_ctx *ctx, int prec, int D, int cl, int cr, const double *L_dev,
+                            const double *W1_dev, const double *W2_dev, const double *R_dev,
+                            const double *theta_dev, double *y_dev);
+
+/* Environment updates of a bond step: left L_new (D x ck x ck) from L
+ * (D x cl x cl), W and a left-canonical site A (cl x 2 x ck); right R_new
+ * (D x ck x ck) from R (D x cr x cr), W and a right-canonical B (ck x 2 x cr). */
+dmrg_status dmrg_env_left(dmrg_ctx *ctx, int prec, int D, int cl, int ck, const double *L_dev,
+                          const double *W_dev, const double *A_dev, double *Lnew_dev);
+dmrg_status dmrg_env_right(dmrg_ctx *ctx, int prec, int D, int ck, int cr, const double *R_dev,
+                           const double *W_dev, const double *B_dev, double *Rnew_dev);
+
+/* K-step Lanczos for the lowest eigenpair of H_eff (Eq. 19): theta_dev is
+ * the start vector on entry and the normalised Ritz vector on return;
+ * *E_out (host) the Ritz value, *steps_out (host, optional) the steps taken. */
+dmrg_status dmrg_lanczos(dmrg_ctx *ctx, int prec, int D, int cl, int cr, const double *L_dev,
+                         const double *W1_dev, const double *W2_dev, const double *R_dev,
+                         double *theta_dev, int K, double *E_out, int *steps_out);
+
+/* Accessors of a state (device buffers owned by the state; valid until the
+ * next call that modifies it). */
+dmrg_status dmrg_state_chi(dmrg_state *st, int *chi_host /* N+1 */);
+dmrg_status dmrg_state_site(dmrg_state *st, int i, const double **A_dev);
+/* Copy environment k (left: L_k, else R_k) in the layout above into the
+ * caller's buffer E_out_dev (D x chi_k x chi_k); synchronises the stream. */
+dmrg_status dmrg_state_env(dmrg_state *st, int left, int k, double *E_out_dev);
+dmrg_status dmrg_state_ctrl(dmrg_state *st, dmrg_ctrl_state **ctrl_dev /* N-1 */);
+/* Set the learned scheduler's parameters (4929 FP32 values, layout of
+ * dmrg_mlp_forward) used when ctrl == DMRG_CTRL_MLP. */
+dmrg_status dmrg_state_set_mlp(dmrg_state *st, const float *params_dev);
+
+/* ---------------------------------------------------------------------- */
+/* Learned scheduler (not in the paper): MLP 10 -> 64 -> 64 -> 1 with     */
+/* exact-erf GELU, FP32.  Parameter layout: W1[64][10], b1[64],           */
+/* W2[64][64], b2[64], W3[64], b3[1] (4929 floats).                       */
+/* ---------------------------------------------------------------------- */
+dmrg_status dmrg_mlp_forward(dmrg_ctx *ctx, const float *params_dev, int B, const float *X_dev, float *y_dev);
+/* loss_dev[0] = mean_b (y_b - t_b)^2 and grad_dev = d loss / d params. */
+dmrg_status dmrg_mlp_loss_grad(dmrg_ctx *ctx, const float *params_dev, int B, const float *X_dev,
+                               const float *t_dev, float *loss_dev, float *grad_dev);
+/* One Adam step (step is 1-based) on n parameters; m, v are moment buffers. */
+dmrg_status dmrg_mlp_adam(dmrg_ctx *ctx, int n, float *params_dev, const float *grad_dev, float *m_dev,
+                          float *v_dev, int step, float lr, float beta1, float beta2, float eps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMRG_GB300_H */

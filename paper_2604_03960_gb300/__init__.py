@@ -1,0 +1,345 @@
+"""Python binding of the GB300 adaptive two-site DMRG library (C ABI in include/dmrg.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``csrc/`` (compiled into ``_build/libdmrg_gb300.so`` for sm_103a).
+PyTorch provides device memory and the stream.  There is no CPU path: if the
+compiled library is missing, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from .build import LIB as _LIB_PATH, build as _build
+
+__all__ = [
+    "lib", "Params", "ModelParams", "CtrlState", "SweepRecord", "VisitRecord", "Context", "State",
+    "PREC_FP64", "PREC_3XTF32", "CTRL_PID", "CTRL_DIRECT", "CTRL_FIXED", "CTRL_THRESHOLD", "CTRL_MLP",
+    "XXZ", "J1J2", "TFIM", "DMRGError", "make_params", "MLP_NPARAM",
+]
+
+PREC_FP64, PREC_3XTF32, PREC_BF16X3 = 0, 1, 2
+CTRL_PID, CTRL_DIRECT, CTRL_FIXED, CTRL_THRESHOLD, CTRL_MLP = range(5)
+XXZ, J1J2, TFIM = 0, 1, 2
+MLP_NPARAM = 4929
+
+
+class DMRGError(RuntimeError):
+    pass
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("alpha_ema", C.c_double), ("gamma", C.c_double), ("S_target", C.c_double),
+        ("Kp", C.c_double), ("Ki", C.c_double), ("Kd", C.c_double), ("beta", C.c_double),
+        ("eps_trunc", C.c_double), ("eps_conv", C.c_double),
+        ("chi_min", C.c_int), ("chi_max", C.c_int), ("lanczos_steps", C.c_int),
+        ("max_sweeps", C.c_int), ("jacobi_max_sweeps", C.c_int), ("prec", C.c_int),
+        ("ctrl", C.c_int), ("ema_init_zero", C.c_int), ("multiplet_guard", C.c_int),
+        ("pid_steps_per_sweep", C.c_int), ("chi_init", C.c_int), ("chi_fixed", C.c_int),
+        ("second_order", C.c_int),
+    ]
+
+
+class ModelParams(C.Structure):
+    _fields_ = [("N", C.c_int), ("J", C.c_double), ("Delta", C.c_double), ("J2", C.c_double)]
+
+
+class CtrlState(C.Structure):
+    _fields_ = [
+        ("Sbar", C.c_double), ("Sbar_prev", C.c_double), ("Sbar_prev2", C.c_double),
+        ("e_prev", C.c_double), ("I", C.c_double), ("hist", C.c_double * 8),
+        ("chi", C.c_int), ("initialized", C.c_int), ("nhist", C.c_int), ("pad", C.c_int),
+    ]
+
+
+class SweepRecord(C.Structure):
+    _fields_ = [
+        ("E", C.c_double), ("max_trunc_err", C.c_double), ("mean_chi", C.c_double),
+        ("seconds", C.c_double), ("flops", C.c_double), ("max_chi", C.c_int), ("n_visits", C.c_int),
+        ("jacobi_sweeps", C.c_int), ("lanczos_steps", C.c_int),
+    ]
+
+
+class VisitRecord(C.Structure):
+    _fields_ = [
+        ("bond", C.c_int), ("k", C.c_int), ("chi_ctrl", C.c_int), ("direction", C.c_int),
+        ("E", C.c_double), ("S", C.c_double), ("trunc_err", C.c_double),
+    ]
+
+
+CTRL_STATE_BYTES = C.sizeof(CtrlState)
+
+_lib = None
+_VP = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+
+
+def _declare(L):
+    S = C.c_int  # dmrg_status
+    sig = {
+        "dmrg_create": (S, [C.POINTER(_VP), _I, _VP]),
+        "dmrg_destroy": (None, [_VP]),
+        "dmrg_get_status": (S, [_VP]),
+        "dmrg_status_string": (C.c_char_p, [_I]),
+        "dmrg_mpo_dim": (_I, [_I]),
+        "dmrg_build_mpo": (S, [_VP, _I, C.POINTER(ModelParams), _VP]),
+        "dmrg_state_create": (S, [_VP, _I, C.POINTER(ModelParams), _VP, C.POINTER(Params), _VP, C.POINTER(_VP)]),
+        "dmrg_state_destroy": (None, [_VP]),
+        "dmrg_sweep": (S, [_VP, _VP, _I, _I, C.POINTER(SweepRecord), C.POINTER(VisitRecord), C.POINTER(_I)]),
+        "bond_update": (S, [_VP, _VP, _I, _I, C.POINTER(_D), C.POINTER(_I)]),
+        "svd_truncate": (S, [_VP, _VP, _I, _I, _I, _D, _VP, _VP, _VP, C.POINTER(_I), C.POINTER(_D), C.POINTER(_D)]),
+        "entropy_pid_step": (S, [_VP, _I, _VP, _VP, C.POINTER(Params), _VP]),
+        "dmrg_entropy": (S, [_VP, _I, _VP, _VP, _VP]),
+        "dmrg_heff_apply": (S, [_VP, _I, _I, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
+        "dmrg_env_left": (S, [_VP, _I, _I, _I, _I, _VP, _VP, _VP, _VP]),
+        "dmrg_env_right": (S, [_VP, _I, _I, _I, _I, _VP, _VP, _VP, _VP]),
+        "dmrg_lanczos": (S, [_VP, _I, _I, _I, _I, _VP, _VP, _VP, _VP, _VP, _I, C.POINTER(_D), C.POINTER(_I)]),
+        "dmrg_state_chi": (S, [_VP, C.POINTER(_I)]),
+        "dmrg_state_site": (S, [_VP, _I, C.POINTER(_VP)]),
+        "dmrg_state_env": (S, [_VP, _I, _I, _VP]),
+        "dmrg_state_ctrl": (S, [_VP, C.POINTER(_VP)]),
+        "dmrg_state_set_mlp": (S, [_VP, _VP]),
+        "dmrg_mlp_forward": (S, [_VP, _VP, _I, _VP, _VP]),
+        "dmrg_mlp_loss_grad": (S, [_VP, _VP, _I, _VP, _VP, _VP, _VP]),
+        "dmrg_mlp_adam": (S, [_VP, _I, _VP, _VP, _VP, _VP, _I, C.c_float, C.c_float, C.c_float, C.c_float]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+def lib():
+    """Load the compiled library (building it first if needed); raises if the
+    CUDA toolkit or the library is unavailable."""
+    global _lib
+    if _lib is None:
+        path = _LIB_PATH
+        if not os.path.exists(path):
+            path = _build()
+        _lib = _declare(C.CDLL(path))
+    return _lib
+
+
+def exported_symbols():
+    """Names the header declares; used by the CPU-side export check."""
+    return [
+        "dmrg_create", "dmrg_destroy", "dmrg_get_status", "dmrg_status_string", "dmrg_mpo_dim", "dmrg_build_mpo",
+        "dmrg_state_create", "dmrg_state_destroy", "dmrg_sweep", "bond_update", "svd_truncate", "entropy_pid_step",
+        "dmrg_entropy", "dmrg_heff_apply", "dmrg_env_left", "dmrg_env_right", "dmrg_lanczos", "dmrg_state_chi",
+        "dmrg_state_site", "dmrg_state_env", "dmrg_state_ctrl", "dmrg_state_set_mlp", "dmrg_mlp_forward",
+        "dmrg_mlp_loss_grad", "dmrg_mlp_adam",
+    ]
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        msg = lib().dmrg_status_string(st).decode()
+        raise DMRGError(f"{what}: {msg} (status {st})")
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise DMRGError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise DMRGError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def make_params(**kw) -> Params:
+    """Defaults as the oracle's: K_p=2, K_i=0.1, K_d=0.5, beta=0.4,
+    eps_trunc=1e-10, eps_conv=1e-8 from the paper; the rest are design choices."""
+    import math
+    chi_max = kw.get("chi_max", 32)
+    gamma = kw.get("gamma", 1.5)
+    d = dict(alpha_ema=0.3, gamma=gamma, S_target=0.9 * math.log(chi_max / gamma), Kp=2.0, Ki=0.1, Kd=0.5,
+             beta=0.4, eps_trunc=1e-10, eps_conv=1e-8, chi_min=4, chi_max=chi_max, lanczos_steps=20,
+             max_sweeps=8, jacobi_max_sweeps=60, prec=PREC_FP64, ctrl=CTRL_PID, ema_init_zero=0,
+             multiplet_guard=1, pid_steps_per_sweep=2, chi_init=4, chi_fixed=chi_max, second_order=0)
+    d.update(kw)
+    p = Params()
+    for k, v in d.items():
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """dmrg_ctx on one device, enqueuing on a torch stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.device = device
+        self.stream = stream or torch.cuda.current_stream(device)
+        h = C.c_void_p()
+        _check(lib().dmrg_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream)), "dmrg_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dmrg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self):
+        _check(lib().dmrg_get_status(self.h), "device status")
+
+    # --- hot-path entry points ------------------------------------------------
+    def build_mpo(self, model: int, N: int, J=1.0, Delta=1.0, J2=0.0) -> torch.Tensor:
+        D = lib().dmrg_mpo_dim(model)
+        W = torch.empty((N, D, D, 2, 2), dtype=torch.float64, device=f"cuda:{self.device}")
+        mp = ModelParams(N, J, Delta, J2)
+        _check(lib().dmrg_build_mpo(self.h, model, C.byref(mp), _ptr(W)), "dmrg_build_mpo")
+        return W
+
+    def svd_truncate(self, theta: torch.Tensor, chi_max: int, eps: float, out=None):
+        m, n = theta.shape
+        r = min(m, n)
+        dev = theta.device
+        if out is None:
+            out = (torch.empty((m, r), dtype=torch.float64, device=dev), torch.empty(r, dtype=torch.float64, device=dev),
+                   torch.empty((r, n), dtype=torch.float64, device=dev))
+        U, s, Vt = out
+        k = C.c_int(); S = C.c_double(); err = C.c_double()
+        _check(lib().svd_truncate(self.h, _ptr(theta), m, n, chi_max, eps, _ptr(U), _ptr(s), _ptr(Vt), C.byref(k),
+                                  C.byref(S), C.byref(err)), "svd_truncate")
+        return U, s, Vt, k.value, S.value, err.value
+
+    def entropy_pid_step(self, S_raw: torch.Tensor, states: torch.Tensor, params: Params, chi_out: torch.Tensor):
+        n = S_raw.numel()
+        _check(lib().entropy_pid_step(self.h, n, _ptr(S_raw), _ptr(states), C.byref(params), _ptr(chi_out)),
+               "entropy_pid_step")
+
+    def entropy(self, s: torch.Tensor):
+        n = s.numel()
+        S = torch.empty(1, dtype=torch.float64, device=s.device)
+        eps = torch.empty(n + 1, dtype=torch.float64, device=s.device)
+        _check(lib().dmrg_entropy(self.h, n, _ptr(s), _ptr(S), _ptr(eps)), "dmrg_entropy")
+        return S, eps
+
+    def heff_apply(self, L, W1, W2, R, theta, prec=PREC_FP64):
+        D, cl = L.shape[0], L.shape[1]
+        cr = R.shape[1]
+        y = torch.empty_like(theta)
+        _check(lib().dmrg_heff_apply(self.h, prec, D, cl, cr, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(theta),
+                                     _ptr(y)), "dmrg_heff_apply")
+        return y
+
+    def env_left(self, L, W, A, prec=PREC_FP64):
+        D, cl = L.shape[0], L.shape[1]
+        ck = A.shape[2]
+        out = torch.empty((D, ck, ck), dtype=torch.float64, device=L.device)
+        _check(lib().dmrg_env_left(self.h, prec, D, cl, ck, _ptr(L), _ptr(W), _ptr(A), _ptr(out)), "dmrg_env_left")
+        return out
+
+    def env_right(self, R, W, B, prec=PREC_FP64):
+        D, cr = R.shape[0], R.shape[1]
+        ck = B.shape[0]
+        out = torch.empty((D, ck, ck), dtype=torch.float64, device=R.device)
+        _check(lib().dmrg_env_right(self.h, prec, D, ck, cr, _ptr(R), _ptr(W), _ptr(B), _ptr(out)), "dmrg_env_right")
+        return out
+
+    def lanczos(self, L, W1, W2, R, theta, K=20, prec=PREC_FP64):
+        D, cl = L.shape[0], L.shape[1]
+        cr = R.shape[1]
+        th = theta.clone()
+        E = C.c_double(); steps = C.c_int()
+        _check(lib().dmrg_lanczos(self.h, prec, D, cl, cr, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(th), K,
+                                  C.byref(E), C.byref(steps)), "dmrg_lanczos")
+        return E.value, th, steps.value
+
+    # --- learned scheduler ------------------------------------------------------
+    def mlp_forward(self, P: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
+        y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        _check(lib().dmrg_mlp_forward(self.h, _ptr(P), X.shape[0], _ptr(X), _ptr(y)), "dmrg_mlp_forward")
+        return y
+
+    def mlp_loss_grad(self, P, X, t):
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        g = torch.empty_like(P)
+        _check(lib().dmrg_mlp_loss_grad(self.h, _ptr(P), X.shape[0], _ptr(X), _ptr(t), _ptr(loss), _ptr(g)),
+               "dmrg_mlp_loss_grad")
+        return loss, g
+
+    def mlp_adam(self, P, g, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        _check(lib().dmrg_mlp_adam(self.h, P.numel(), _ptr(P), _ptr(g), _ptr(m), _ptr(v), step, lr, b1, b2, eps),
+               "dmrg_mlp_adam")
+
+
+class State:
+    """dmrg_state: an MPS with its environments and per-bond controllers on the device."""
+
+    def __init__(self, ctx: Context, W: torch.Tensor, mps_init: torch.Tensor, params: Params, J=1.0, Delta=1.0, J2=0.0):
+        N, D = W.shape[0], W.shape[1]
+        self.ctx, self.N, self.D, self.params = ctx, N, D, params
+        mp = ModelParams(N, J, Delta, J2)
+        h = C.c_void_p()
+        _check(lib().dmrg_state_create(ctx.h, D, C.byref(mp), _ptr(W), C.byref(params), _ptr(mps_init), C.byref(h)),
+               "dmrg_state_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dmrg_state_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n_sweeps: int, stop_on_conv: bool = False, visits: bool = True):
+        recs = (SweepRecord * max(n_sweeps, 1))()
+        V = 2 * self.N - 3
+        vis = (VisitRecord * max(n_sweeps * V, 1))() if visits else None
+        done = C.c_int()
+        _check(lib().dmrg_sweep(self.ctx.h, self.h, n_sweeps, int(stop_on_conv), recs, vis, C.byref(done)),
+               "dmrg_sweep")
+        n = done.value
+        return list(recs)[:n], (list(vis)[: n * V] if visits else None)
+
+    def bond_update(self, bond: int, direction: int):
+        E = C.c_double(); k = C.c_int()
+        _check(lib().bond_update(self.ctx.h, self.h, bond, direction, C.byref(E), C.byref(k)), "bond_update")
+        return E.value, k.value
+
+    def chi(self):
+        arr = (C.c_int * (self.N + 1))()
+        _check(lib().dmrg_state_chi(self.h, arr), "dmrg_state_chi")
+        return list(arr)
+
+    def env(self, left: bool, k: int) -> torch.Tensor:
+        c = self.chi()[k]
+        out = torch.empty((self.D, c, c), dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        _check(lib().dmrg_state_env(self.h, int(left), k, _ptr(out)), "dmrg_state_env")
+        return out
+
+    def site(self, i: int) -> torch.Tensor:
+        """Copy of site tensor i (chi_i x 2 x chi_{i+1})."""
+        chi = self.chi()
+        p = C.c_void_p()
+        _check(lib().dmrg_state_site(self.h, i, C.byref(p)), "dmrg_state_site")
+        shape = (chi[i], 2, chi[i + 1])
+        torch.cuda.synchronize(self.ctx.device)
+        return torch.as_tensor(_DevView(p.value, shape), device=f"cuda:{self.ctx.device}").clone()
+
+    def set_mlp(self, P: torch.Tensor | None):
+        _check(lib().dmrg_state_set_mlp(self.h, _ptr(P) if P is not None else None), "dmrg_state_set_mlp")
+
+
+class _DevView:
+    """Read-only view of a library-owned FP64 device buffer (CUDA array interface)."""
+
+    def __init__(self, ptr: int, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (ptr, True), "version": 3}

@@ -1,0 +1,189 @@
+// common.cuh -- internal declarations of the GB300 DMRG library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/dmrg.h"
+
+namespace dmrg {
+
+// Device status bits, OR-ed into ctx->d_status by kernels.
+enum : int {
+    ST_TIMEOUT = 1,   // a bounded spin-wait gave up
+    ST_NAN = 2,       // non-finite value met
+    ST_NOCONV = 4,    // Jacobi did not converge
+    ST_BOUNDS = 8     // an index check failed (debug builds)
+};
+
+// Upper bound on polling iterations of any device-side wait (each iteration
+// sleeps ~100 ns, so the bound is of the order of a few seconds).
+constexpr long long kSpinLimit = 20000000LL;
+
+#define DMRG_CUDA(call)                                                               \
+    do {                                                                              \
+        cudaError_t e__ = (call);                                                     \
+        if (e__ != cudaSuccess) {                                                     \
+            std::fprintf(stderr, "dmrg: %s failed at %s:%d: %s\n", #call, __FILE__,   \
+                         __LINE__, cudaGetErrorString(e__));                          \
+            return DMRG_ECUDA;                                                        \
+        }                                                                             \
+    } while (0)
+
+#define DMRG_TRY(expr)                       \
+    do {                                     \
+        dmrg_status s__ = (expr);            \
+        if (s__ != DMRG_OK) return s__;      \
+    } while (0)
+
+// Grow-only device buffer.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    dmrg_status ensure(size_t need) {
+        if (need <= bytes) return DMRG_OK;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+        if (cudaMalloc(&ptr, need) != cudaSuccess) return DMRG_ENOMEM;
+        bytes = need;
+        return DMRG_OK;
+    }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+    template <class T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// Scratch of the one-sided Jacobi SVD.
+struct SvdWork {
+    double *X = nullptr;    // r x l: the r vectors being orthogonalised
+    double *Vm = nullptr;   // r x r: accumulated rotations
+    double *nrm = nullptr;  // r    : column norms
+    int *perm = nullptr;    // r    : descending order
+    unsigned *sync = nullptr;  // grid barrier words (2) + rotation counters (2)
+};
+
+// Bytes needed by the Jacobi scratch for r vectors of length l.
+size_t svd_work_bytes(int r, int l);
+SvdWork svd_work_carve(void *base, int r, int l);
+
+}  // namespace dmrg
+
+struct dmrg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    int *d_status = nullptr;     // device status word (ST_* bits)
+    int *h_pinned_i = nullptr;   // pinned host readback area (64 ints)
+    double *h_pinned_d = nullptr;// pinned host readback area (64 doubles)
+    dmrg::DevBuf work;           // scratch for standalone calls
+    dmrg::DevBuf work2;
+    dmrg::DevBuf work3;
+    int jacobi_max_sweeps = 60;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace dmrg {
+
+// ---------------------------------------------------------------------------
+// Bounded grid barrier for kernels launched cooperatively (all blocks
+// co-resident).  words[0] = arrival count, words[1] = generation.
+// Returns false (and sets ST_TIMEOUT) if the wait gave up.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_barrier(unsigned *words, int *status)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *gen = words + 1;
+        unsigned g = *gen;
+        __threadfence();
+        unsigned arrived = atomicAdd(words, 1u);
+        if (arrived == gridDim.x * gridDim.y - 1) {
+            atomicExch(words, 0u);
+            __threadfence();
+            atomicAdd(words + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g) {
+                __nanosleep(100);
+                if (++spins > kSpinLimit) {
+                    atomicOr(status, ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// Warp and block reductions (FP64).
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over a block of blockDim.x threads (multiple of 32, <= 1024); result
+// returned to every thread.  Fixed reduction order (deterministic).
+__device__ __forceinline__ double block_sum(double v, double *sh /* >= 32 */)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers implemented in the other translation units.
+// ---------------------------------------------------------------------------
+
+// FP64 strided batched GEMM:
+//   C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n)
+// with A(m,k) = A[b*sAb + m*sAm + k*sAk], etc., for b < batch.
+dmrg_status gemm_f64(cudaStream_t st, int M, int N, int K, double alpha, const double *A, long long sAm,
+                     long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
+                     double beta, double *C, long long sCm, long long sCn, long long sCb, int batch);
+
+// Tensor-core GEMM (tcgen05, TF32 inputs split three ways, FP32 accumulate):
+// same contract as gemm_f64 (FP64 in, FP64 out), precision ~FP32.
+dmrg_status gemm_3xtf32(dmrg_ctx *ctx, int M, int N, int K, double alpha, const double *A, long long sAm,
+                        long long sAk, long long sAb, const double *B, long long sBk, long long sBn,
+                        long long sBb, double beta, double *C, long long sCm, long long sCn, long long sCb,
+                        int batch);
+bool tc_available(dmrg_ctx *ctx);
+
+// Dispatch on precision.
+dmrg_status gemm(dmrg_ctx *ctx, int prec, int M, int N, int K, double alpha, const double *A, long long sAm,
+                 long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
+                 double beta, double *C, long long sCm, long long sCn, long long sCb, int batch);
+
+// One-sided Jacobi SVD of the row-major m x n matrix A (device).  Writes U
+// (m x r), s (r, descending), Vt (r x n), r = min(m,n).  `work` must hold
+// svd_work_bytes(r, max(m,n)).  Convergence flag / sweep count are written
+// to d_info[0] (sweeps, negative if not converged).
+dmrg_status svd_jacobi(dmrg_ctx *ctx, const double *A, int m, int n, double *U, double *s, double *Vt,
+                       void *work, int max_sweeps, int *d_info);
+
+// Lanczos on the effective Hamiltonian (see lanczos.cu).
+struct HeffOp;  // defined in dmrg_core.cu
+}  // namespace dmrg

@@ -1,0 +1,918 @@
+// dmrg_core.cu -- contraction plans, the per-bond local update, the sweep
+// driver and the C ABI (include/dmrg.h).
+//
+// Layouts in device memory (row-major, last index fastest):
+//   site i      A[a][s][b]            chi_i x 2 x chi_{i+1}
+//   env slot i  L_i[w][a'][a]          when the orthogonality centre is right of i
+//               Rt_i[w][b][b']         when it is left of i (R stored transposed:
+//                                      ket index first), so that every contraction
+//                                      below is one strided GEMM without copies.
+// One slot per position serves L_i or R_i (never both live), which halves the
+// environment memory: at N = 400, chi = 2048, D = 8 the slots take ~100 GB.
+//
+// H_eff theta (Eq. 19) = three steps per Lanczos matvec:
+//   X[(w,a')][(s1,s2,b)] = L[(w,a')][a] theta[a][(s1,s2,b)]                GEMM  M=D cl, N=4 cr, K=cl
+//   Y[a'][q'][u][b]      = sum_{w,q} C[(u,q')][(w,q)] X[w][a'][q][b]        mix   C = W_k W_{k+1} over the shared MPO index
+//   y[(a',q')][b']       = Y[(a',q')][(u,b)] Rt[(u,b)][b']                  GEMM  M=4 cl, N=cr, K=D cr
+// Environment updates follow the same GEMM / mix / GEMM pattern.
+#include "common.cuh"
+#include "ctrl.cuh"
+#include "lanczos.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+namespace dmrg {
+namespace {
+
+constexpr int kMaxCh = 32;   // max channels of a mix (4 D for D <= 8)
+
+// ---------------------------------------------------------------------------
+// MPO (Eq. 18 generalised; lower-triangular, left boundary row D-1, right
+// boundary column 0).  One thread per site.
+// ---------------------------------------------------------------------------
+__device__ void put(double *Wi, int D, int wl, int wr, double o00, double o01, double o10, double o11, double c)
+{
+    double *p = Wi + ((size_t)wl * D + wr) * 4;
+    p[0] += c * o00; p[1] += c * o01; p[2] += c * o10; p[3] += c * o11;
+}
+
+__global__ void k_build_mpo(int model, int N, double J, double Delta, double J2, double *W)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int D = (model == DMRG_XXZ) ? 5 : (model == DMRG_J1J2 ? 8 : 3);
+    double *Wi = W + (size_t)i * D * D * 4;
+    for (int x = 0; x < D * D * 4; ++x) Wi[x] = 0.0;
+    // basis 0 = up, 1 = down; operators as (00, 01, 10, 11)
+    const double Id[4] = {1, 0, 0, 1}, Sz[4] = {0.5, 0, 0, -0.5}, Sp[4] = {0, 1, 0, 0}, Sm[4] = {0, 0, 1, 0};
+    const double Pz[4] = {1, 0, 0, -1}, Px[4] = {0, 1, 1, 0};
+#define PUT(wl, wr, O, c) put(Wi, D, wl, wr, O[0], O[1], O[2], O[3], c)
+    if (model == DMRG_XXZ) {
+        PUT(0, 0, Id, 1.0); PUT(1, 0, Sp, 1.0); PUT(2, 0, Sm, 1.0); PUT(3, 0, Sz, 1.0);
+        PUT(4, 1, Sm, 0.5 * J); PUT(4, 2, Sp, 0.5 * J); PUT(4, 3, Sz, J * Delta); PUT(4, 4, Id, 1.0);
+    } else if (model == DMRG_J1J2) {
+        PUT(0, 0, Id, 1.0); PUT(7, 7, Id, 1.0);
+        PUT(7, 1, Sp, 1.0); PUT(7, 2, Sm, 1.0); PUT(7, 3, Sz, 1.0);
+        PUT(1, 0, Sm, 0.5 * J); PUT(2, 0, Sp, 0.5 * J); PUT(3, 0, Sz, J * Delta);
+        PUT(1, 4, Id, 1.0); PUT(2, 5, Id, 1.0); PUT(3, 6, Id, 1.0);
+        PUT(4, 0, Sm, 0.5 * J2); PUT(5, 0, Sp, 0.5 * J2); PUT(6, 0, Sz, J2);
+    } else {
+        PUT(0, 0, Id, 1.0); PUT(2, 2, Id, 1.0); PUT(2, 1, Pz, -J); PUT(1, 0, Pz, 1.0); PUT(2, 0, Px, -Delta);
+    }
+#undef PUT
+}
+
+// ---------------------------------------------------------------------------
+// Mixing coefficients.
+//   kind 0 (H_eff):   C[(u*4+q')][(w*4+q)] = sum_v W1[w][v][s1'][s1] W2[v][u][s2'][s2], q = 2 s1 + s2
+//   kind 1 (L env):   C[(v*2+s')][(w*2+s)] = W[w][v][s'][s]
+//   kind 2 (R env):   C[(w*2+s')][(v*2+s)] = W[w][v][s'][s]
+// ---------------------------------------------------------------------------
+__global__ void k_build_coef(int kind, int D, const double *W1, const double *W2, double *C)
+{
+    const int nch = (kind == 0) ? 4 * D : 2 * D;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nch * nch) return;
+    const int o = idx / nch, i = idx % nch;
+    double v = 0.0;
+    if (kind == 0) {
+        int u = o / 4, qp = o % 4, w = i / 4, q = i % 4;
+        int s1p = qp / 2, s2p = qp % 2, s1 = q / 2, s2 = q % 2;
+        for (int m = 0; m < D; ++m)
+            v += W1[(((size_t)w * D + m) * 2 + s1p) * 2 + s1] * W2[(((size_t)m * D + u) * 2 + s2p) * 2 + s2];
+    } else if (kind == 1) {
+        int vv = o / 2, sp = o % 2, w = i / 2, s = i % 2;
+        v = W1[(((size_t)w * D + vv) * 2 + sp) * 2 + s];
+    } else {
+        int w = o / 2, sp = o % 2, vv = i / 2, s = i % 2;
+        v = W1[(((size_t)w * D + vv) * 2 + sp) * 2 + s];
+    }
+    C[idx] = v;
+}
+
+struct MixDesc {
+    int nin, nout, in_ny, out_ny;
+    long long in_sx, in_sy, in_sa, out_sx, out_sy, out_sa;
+    int An, Bn;
+};
+
+// out[channel o][a][b] = sum_i C[o][i] in[channel i][a][b]; b is unit stride.
+__global__ void __launch_bounds__(256) k_mix(const double *__restrict__ in, double *__restrict__ out,
+                                             const double *__restrict__ C, MixDesc d)
+{
+    __shared__ double cs[kMaxCh * kMaxCh];
+    for (int x = threadIdx.x; x < d.nin * d.nout; x += blockDim.x) cs[x] = C[x];
+    __syncthreads();
+    const long long total = (long long)d.An * d.Bn;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        const int a = (int)(e / d.Bn), b = (int)(e % d.Bn);
+        double xin[kMaxCh];
+#pragma unroll
+        for (int c = 0; c < kMaxCh; ++c) {
+            if (c < d.nin) {
+                int x = c / d.in_ny, y = c % d.in_ny;
+                xin[c] = in[x * d.in_sx + y * d.in_sy + a * d.in_sa + b];
+            }
+        }
+        for (int o = 0; o < d.nout; ++o) {
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < kMaxCh; ++c) {
+                if (c < d.nin) {
+                    double co = cs[o * d.nin + c];
+                    if (co != 0.0) acc = fma(co, xin[c], acc);
+                }
+            }
+            int x = o / d.out_ny, y = o % d.out_ny;
+            out[x * d.out_sx + y * d.out_sy + a * d.out_sa + b] = acc;
+        }
+    }
+}
+
+// batched transpose: out[b][j][i] = in[b][i][j] (n x n blocks)
+__global__ void k_transpose_sq(const double *__restrict__ in, double *__restrict__ out, int n, int batch)
+{
+    __shared__ double t[32][33];
+    const int b = blockIdx.z;
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    const double *src = in + (size_t)b * n * n;
+    double *dst = out + (size_t)b * n * n;
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        int i = i0 + y, j = j0 + threadIdx.x;
+        t[y][threadIdx.x] = (i < n && j < n) ? src[(size_t)i * n + j] : 0.0;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        int j = j0 + y, i = i0 + threadIdx.x;
+        if (i < n && j < n) dst[(size_t)j * n + i] = t[threadIdx.x][y];
+    }
+}
+
+// After truncation to k: A_k = U[:, :k] (x s/z if the centre stays left),
+// A_{k+1} = (s/z x) Vt[:k, :] (if the centre moves right).
+__global__ void k_split(const double *__restrict__ U, const double *__restrict__ s, const double *__restrict__ Vt,
+                        int m, int n, int r, const BondResult *res, int go_right, double *__restrict__ Ak,
+                        double *__restrict__ Ak1)
+{
+    const int k = res->k;
+    const double z = res->znorm;
+    const long long nA = (long long)m * k, nB = (long long)k * n;
+    const long long total = nA > nB ? nA : nB;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        if (e < nA) {
+            int i = (int)(e / k), j = (int)(e % k);
+            double v = U[(long long)i * r + j];
+            Ak[e] = go_right ? v : v * (s[j] / z);
+        }
+        if (e < nB) {
+            int j = (int)(e / n), c = (int)(e % n);
+            double v = Vt[(long long)j * n + c];
+            Ak1[e] = go_right ? v * (s[j] / z) : v;
+        }
+    }
+}
+
+// dst[i][j] = src[i][j] * (scale_cols ? s[j] : 1) for an m x k block
+__global__ void k_copy_scale(const double *__restrict__ src, double *__restrict__ dst, long long m, int k,
+                             const double *__restrict__ s)
+{
+    const long long total = m * k;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        int j = (int)(e % k);
+        dst[e] = s ? src[e] * s[j] : src[e];
+    }
+}
+
+// normalise a small vector in place (single block)
+__global__ void k_normalise(double *x, int n)
+{
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a += x[i] * x[i];
+    a = block_sum(a, sh);
+    double inv = (a > 0.0) ? 1.0 / sqrt(a) : 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] *= inv;
+}
+
+__global__ void k_init_ctrl(dmrg_ctrl_state *st, int n, int chi0)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    dmrg_ctrl_state z;
+    z.Sbar = z.Sbar_prev = z.Sbar_prev2 = z.e_prev = z.I = 0.0;
+    for (int j = 0; j < 8; ++j) z.hist[j] = 0.0;
+    z.chi = chi0;
+    z.initialized = 0;
+    z.nhist = 0;
+    z.pad = 0;
+    st[i] = z;
+}
+
+__global__ void k_boundary_env(double *E, int D, int w)
+{
+    int i = threadIdx.x;
+    if (i < D) E[i] = (i == w) ? 1.0 : 0.0;
+}
+
+int grid1d(long long n, int threads, int num_sms)
+{
+    long long b = (n + threads - 1) / threads;
+    long long cap = (long long)num_sms * 8;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Contraction plans
+// ---------------------------------------------------------------------------
+static dmrg_status mix(dmrg_ctx *ctx, const double *in, double *out, const double *C, const MixDesc &d)
+{
+    long long total = (long long)d.An * d.Bn;
+    k_mix<<<grid1d(total, 256, ctx->num_sms), 256, 0, ctx->stream>>>(in, out, C, d);
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
+// y = H_eff x. L: [w][a'][a] (D cl cl); Rt: [u][b][b'] (D cr cr); C: (4D)^2;
+// X, Y: D*cl*4*cr doubles each.
+dmrg_status heff_apply_dev(dmrg_ctx *ctx, int prec, int D, int cl, int cr, const double *L, const double *Rt,
+                           const double *C, double *X, double *Y, const double *x, double *y)
+{
+    const long long n4 = 4LL * cr;
+    DMRG_TRY(gemm(ctx, prec, D * cl, (int)n4, cl, 1.0, L, cl, 1, 0, x, n4, 1, 0, 0.0, X, n4, 1, 0, 1));
+    MixDesc md;
+    md.nin = 4 * D; md.nout = 4 * D; md.in_ny = 4; md.out_ny = 4;
+    md.in_sx = (long long)cl * n4; md.in_sy = cr; md.in_sa = n4;
+    md.out_sx = cr; md.out_sy = (long long)D * cr; md.out_sa = 4LL * D * cr;
+    md.An = cl; md.Bn = cr;
+    DMRG_TRY(mix(ctx, X, Y, C, md));
+    DMRG_TRY(gemm(ctx, prec, 4 * cl, cr, D * cr, 1.0, Y, (long long)D * cr, 1, 0, Rt, cr, 1, 0, 0.0, y, cr, 1, 0, 1));
+    return DMRG_OK;
+}
+
+// Lnew[v][b'][b] from L (D cl cl), coefficient C (kind 1), A (cl x 2 x ck)
+dmrg_status env_left_dev(dmrg_ctx *ctx, int prec, int D, int cl, int ck, const double *L, const double *C,
+                         const double *A, double *Lnew, double *T1, double *T2)
+{
+    const long long n2 = 2LL * ck;
+    DMRG_TRY(gemm(ctx, prec, D * cl, (int)n2, cl, 1.0, L, cl, 1, 0, A, n2, 1, 0, 0.0, T1, n2, 1, 0, 1));
+    MixDesc md;
+    md.nin = 2 * D; md.nout = 2 * D; md.in_ny = 2; md.out_ny = 2;
+    md.in_sx = (long long)cl * n2; md.in_sy = ck; md.in_sa = n2;
+    md.out_sx = (long long)cl * n2; md.out_sy = ck; md.out_sa = n2;
+    md.An = cl; md.Bn = ck;
+    DMRG_TRY(mix(ctx, T1, T2, C, md));
+    DMRG_TRY(gemm(ctx, prec, ck, ck, 2 * cl, 1.0, A, 1, ck, 0, T2, ck, 1, (long long)2 * cl * ck, 0.0, Lnew, ck, 1,
+                  (long long)ck * ck, D));
+    return DMRG_OK;
+}
+
+// Rtnew[w][a][a'] from Rt (D cr cr, [v][b][b']), coefficient C (kind 2), B (ck x 2 x cr)
+dmrg_status env_right_dev(dmrg_ctx *ctx, int prec, int D, int ck, int cr, const double *Rt, const double *C,
+                          const double *B, double *Rtnew, double *T1, double *T2)
+{
+    DMRG_TRY(gemm(ctx, prec, 2 * ck, cr, cr, 1.0, B, cr, 1, 0, Rt, cr, 1, (long long)cr * cr, 0.0, T1, cr, 1,
+                  (long long)2 * ck * cr, D));
+    MixDesc md;
+    md.nin = 2 * D; md.nout = 2 * D; md.in_ny = 2; md.out_ny = 2;
+    md.in_sx = (long long)2 * ck * cr; md.in_sy = cr; md.in_sa = 2LL * cr;
+    md.out_sx = (long long)2 * ck * cr; md.out_sy = cr; md.out_sa = 2LL * cr;
+    md.An = ck; md.Bn = cr;
+    DMRG_TRY(mix(ctx, T1, T2, C, md));
+    DMRG_TRY(gemm(ctx, prec, ck, ck, 2 * cr, 1.0, T2, 2LL * cr, 1, (long long)ck * 2 * cr, B, 1, 2LL * cr, 0, 0.0,
+                  Rtnew, ck, 1, (long long)ck * ck, D));
+    return DMRG_OK;
+}
+
+static dmrg_status build_coef(dmrg_ctx *ctx, int kind, int D, const double *W1, const double *W2, double *C)
+{
+    int nch = (kind == 0) ? 4 * D : 2 * D;
+    k_build_coef<<<(nch * nch + 255) / 256, 256, 0, ctx->stream>>>(kind, D, W1, W2, C);
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
+static dmrg_status transpose_sq(dmrg_ctx *ctx, const double *in, double *out, int n, int batch)
+{
+    dim3 g((n + 31) / 32, (n + 31) / 32, batch);
+    k_transpose_sq<<<g, dim3(32, 8), 0, ctx->stream>>>(in, out, n, batch);
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
+double matvec_flops(int D, int cl, int cr)
+{
+    return 2.0 * D * cl * 4.0 * cr * cl + 2.0 * (4.0 * D) * (4.0 * D) * cl * cr + 2.0 * 4.0 * cl * cr * D * cr;
+}
+
+double svd_nominal_flops(int m, int n)
+{
+    double M = std::max(m, n), Nn = std::min(m, n);
+    return 4.0 * M * M * Nn + 8.0 * M * Nn * Nn + 9.0 * Nn * Nn * Nn;
+}
+
+double env_flops(int D, int cl, int ck)
+{
+    return 2.0 * D * cl * 2.0 * ck * cl + 2.0 * (2.0 * D) * (2.0 * D) * cl * ck + 2.0 * D * ck * ck * 2.0 * cl;
+}
+
+}  // namespace dmrg
+
+using namespace dmrg;
+
+// ===========================================================================
+// State
+// ===========================================================================
+struct dmrg_state {
+    dmrg_ctx *ctx = nullptr;
+    int N = 0, D = 0;
+    dmrg_params p{};
+    dmrg_model_params mp{};
+    std::vector<int> chi, cap;
+    DevBuf arena;
+    double *W = nullptr, *coef_mv = nullptr, *coef_l = nullptr, *coef_r = nullptr;
+    std::vector<double *> A, env;
+    dmrg_ctrl_state *ctrl = nullptr;
+    double *theta = nullptr, *X = nullptr, *Y = nullptr;
+    double *U = nullptr, *s = nullptr, *Vt = nullptr;
+    void *svdw = nullptr;
+    LanczosWork lw;
+    BondResult *d_res = nullptr;
+    BondResult *h_res = nullptr;   // pinned
+    int *d_info = nullptr;
+    dmrg_visit_record *d_visits = nullptr;
+    float *mlp = nullptr;
+    int has_mlp = 0;
+    int sweep_index = 0;
+    long long nmax = 0;
+    int K = 20;
+};
+
+extern "C" {
+
+const char *dmrg_status_string(dmrg_status s)
+{
+    switch (s) {
+    case DMRG_OK: return "ok";
+    case DMRG_EINVAL: return "invalid argument";
+    case DMRG_ENOMEM: return "out of device memory";
+    case DMRG_ENOCONV: return "Jacobi SVD did not converge";
+    case DMRG_ENAN: return "non-finite value";
+    case DMRG_ETIMEOUT: return "device-side wait timed out";
+    case DMRG_ECUDA: return "CUDA runtime error";
+    case DMRG_EUNSUPPORTED: return "unsupported option";
+    }
+    return "unknown";
+}
+
+int dmrg_mpo_dim(int model)
+{
+    switch (model) {
+    case DMRG_XXZ: return 5;
+    case DMRG_J1J2: return 8;
+    case DMRG_TFIM: return 3;
+    }
+    return -1;
+}
+
+dmrg_status dmrg_create(dmrg_ctx **out, int device, void *cuda_stream)
+{
+    if (!out) return DMRG_EINVAL;
+    *out = nullptr;
+    DMRG_CUDA(cudaSetDevice(device));
+    dmrg_ctx *c = new (std::nothrow) dmrg_ctx();
+    if (!c) return DMRG_ENOMEM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete c; return DMRG_ECUDA; }
+    c->num_sms = prop.multiProcessorCount;
+    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess) { delete c; return DMRG_ENOMEM; }
+    if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) { cudaFree(c->d_status); delete c; return DMRG_ECUDA; }
+    if (cudaMallocHost(&c->h_pinned_i, 64 * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->h_pinned_d, 64 * sizeof(double)) != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return DMRG_ENOMEM;
+    }
+    cudaEventCreate(&c->ev0);
+    cudaEventCreate(&c->ev1);
+    *out = c;
+    return DMRG_OK;
+}
+
+void dmrg_destroy(dmrg_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    ctx->work.release();
+    ctx->work2.release();
+    ctx->work3.release();
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->h_pinned_i) cudaFreeHost(ctx->h_pinned_i);
+    if (ctx->h_pinned_d) cudaFreeHost(ctx->h_pinned_d);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+}
+
+static dmrg_status status_from_bits(int bits)
+{
+    if (bits & ST_TIMEOUT) return DMRG_ETIMEOUT;
+    if (bits & ST_NAN) return DMRG_ENAN;
+    if (bits & ST_NOCONV) return DMRG_ENOCONV;
+    if (bits) return DMRG_EINVAL;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_get_status(dmrg_ctx *ctx)
+{
+    if (!ctx) return DMRG_EINVAL;
+    DMRG_CUDA(cudaMemcpyAsync(ctx->h_pinned_i, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    DMRG_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+    DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return status_from_bits(ctx->h_pinned_i[0]);
+}
+
+dmrg_status dmrg_build_mpo(dmrg_ctx *ctx, dmrg_model model, const dmrg_model_params *mp, double *W_dev)
+{
+    if (!ctx || !mp || !W_dev || mp->N < 2 || dmrg_mpo_dim(model) < 0) return DMRG_EINVAL;
+    k_build_mpo<<<(mp->N + 63) / 64, 64, 0, ctx->stream>>>((int)model, mp->N, mp->J, mp->Delta, mp->J2, W_dev);
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one local update (Section 10): theta, Lanczos, SVD, entropy + controller +
+// truncation, split, environment update
+// ---------------------------------------------------------------------------
+static dmrg_status bond_step(dmrg_state *st, int k, int go_right, int do_ctrl, dmrg_visit_record *visit,
+                             int direction, double *flops, int *k_out, double *E_out)
+{
+    dmrg_ctx *ctx = st->ctx;
+    const int D = st->D, prec = st->p.prec;
+    const int cl = st->chi[k], cm = st->chi[k + 1], cr = st->chi[k + 2];
+    const int m = 2 * cl, n = 2 * cr, r = std::min(m, n);
+    const long long nn = (long long)m * n;
+    // two-site tensor (Eq. 20's left-hand side)
+    DMRG_TRY(gemm(ctx, prec, m, n, cm, 1.0, st->A[k], cm, 1, 0, st->A[k + 1], n, 1, 0, 0.0, st->theta, n, 1, 0, 1));
+    // Lanczos on H_eff (Eq. 19)
+    const double *L = st->env[k], *Rt = st->env[k + 2];
+    const double *C = st->coef_mv + (size_t)k * (4 * D) * (4 * D);
+    MatvecFn mv = [&](const double *x, double *y) {
+        return heff_apply_dev(ctx, prec, D, cl, cr, L, Rt, C, st->X, st->Y, x, y);
+    };
+    const int K = (int)std::min<long long>(st->K, nn);
+    DMRG_TRY(lanczos_run(ctx, st->lw, nn, K, st->theta, mv));
+    // SVD (Eq. 20)
+    DMRG_TRY(svd_jacobi(ctx, st->theta, m, n, st->U, st->s, st->Vt, st->svdw, st->p.jacobi_max_sweeps, st->d_info));
+    // entropy, controller, truncation
+    DMRG_TRY(launch_decide(ctx, st->s, r, st->ctrl + k, st->p, do_ctrl, 0, st->has_mlp ? st->mlp : nullptr, k, st->N,
+                           st->sweep_index, st->lw.lz, st->d_res, visit, direction));
+    DMRG_CUDA(cudaMemcpyAsync(st->h_res, st->d_res, sizeof(BondResult), cudaMemcpyDeviceToHost, ctx->stream));
+    DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int kk = st->h_res->k;
+    if (kk < 1 || kk > r || kk > st->cap[k + 1]) return DMRG_ENAN;
+    {
+        long long tot = std::max((long long)m * kk, (long long)kk * n);
+        k_split<<<grid1d(tot, 256, ctx->num_sms), 256, 0, ctx->stream>>>(st->U, st->s, st->Vt, m, n, r, st->d_res,
+                                                                         go_right, st->A[k], st->A[k + 1]);
+        DMRG_CUDA(cudaGetLastError());
+    }
+    st->chi[k + 1] = kk;
+    double f = 2.0 * m * n * cm + K * matvec_flops(D, cl, cr) + svd_nominal_flops(m, n);
+    if (go_right) {
+        DMRG_TRY(env_left_dev(ctx, prec, D, cl, kk, st->env[k], st->coef_l + (size_t)k * 4 * D * D, st->A[k],
+                              st->env[k + 1], st->X, st->Y));
+        f += env_flops(D, cl, kk);
+    } else if (k + 1 >= 2) {
+        DMRG_TRY(env_right_dev(ctx, prec, D, kk, cr, st->env[k + 2], st->coef_r + (size_t)(k + 1) * 4 * D * D,
+                               st->A[k + 1], st->env[k + 1], st->X, st->Y));
+        f += env_flops(D, cr, kk);
+    }
+    if (flops) *flops += f;
+    if (k_out) *k_out = kk;
+    if (E_out) *E_out = st->h_res->E;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_state_create(dmrg_ctx *ctx, int D, const dmrg_model_params *mp, const double *W_dev,
+                              const dmrg_params *p, const double *mps_init_dev, dmrg_state **out)
+{
+    if (!ctx || !mp || !W_dev || !p || !mps_init_dev || !out) return DMRG_EINVAL;
+    const int N = mp->N;
+    if (N < 3 || D < 1 || 4 * D > kMaxCh || p->chi_min < 1 || p->chi_max < p->chi_min || p->chi_init < 1 ||
+        p->chi_init > p->chi_max || p->lanczos_steps < 1 || p->lanczos_steps > LZ_MAXK)
+        return DMRG_EINVAL;
+    if (p->prec != DMRG_PREC_FP64 && p->prec != DMRG_PREC_3XTF32) return DMRG_EUNSUPPORTED;
+    if (p->prec == DMRG_PREC_3XTF32 && !tc_available(ctx)) return DMRG_EUNSUPPORTED;
+    dmrg_state *st = new (std::nothrow) dmrg_state();
+    if (!st) return DMRG_ENOMEM;
+    st->ctx = ctx;
+    st->N = N;
+    st->D = D;
+    st->p = *p;
+    if (st->p.jacobi_max_sweeps <= 0) st->p.jacobi_max_sweeps = 60;
+    st->mp = *mp;
+    st->K = p->lanczos_steps;
+    st->chi.resize(N + 1);
+    st->cap.resize(N + 1);
+    auto powcap = [](int e, long long c) { long long v = 1; for (int i = 0; i < e && v < c; ++i) v *= 2; return v; };
+    for (int i = 0; i <= N; ++i) {
+        long long c = p->chi_max;
+        c = std::min(c, powcap(i, c));
+        c = std::min(c, powcap(N - i, c));
+        st->cap[i] = (int)c;
+        long long c0 = std::min<long long>(p->chi_init, c);
+        st->chi[i] = (int)c0;
+    }
+    // sizes
+    long long nmax = 1, svd_bytes = 0, umax = 1, vtmax = 1, smax = 1;
+    for (int k = 0; k + 2 <= N; ++k) {
+        long long m = 2LL * st->cap[k], n = 2LL * st->cap[k + 2];
+        nmax = std::max(nmax, m * n);
+        long long r = std::min(m, n), l = std::max(m, n);
+        svd_bytes = std::max<long long>(svd_bytes, (long long)svd_work_bytes((int)r, (int)l));
+        umax = std::max(umax, m * r);
+        vtmax = std::max(vtmax, r * n);
+        smax = std::max(smax, r);
+    }
+    for (int i = 0; i < N; ++i) {  // initial gauge move: chi_i x 2 chi_{i+1}
+        long long m = st->chi[i], n = 2LL * st->chi[i + 1];
+        long long r = std::min(m, n), l = std::max(m, n);
+        svd_bytes = std::max<long long>(svd_bytes, (long long)svd_work_bytes((int)r, (int)l));
+        umax = std::max(umax, m * r);
+        vtmax = std::max(vtmax, r * n);
+        smax = std::max(smax, r);
+    }
+    for (int i = 0; i < N; ++i) {  // gauge-move temporaries and initial environments
+        nmax = std::max(nmax, 4LL * st->cap[i] * st->cap[i + 1]);
+        nmax = std::max(nmax, (long long)st->cap[i] * st->cap[i]);
+    }
+    st->nmax = nmax;
+    size_t total = 0;
+    std::vector<size_t> site_off(N), env_off(N + 1);
+    total += al256(sizeof(double) * (size_t)N * D * D * 4);                  // W
+    total += al256(sizeof(double) * (size_t)(N - 1) * 16 * D * D);           // coef_mv
+    total += al256(sizeof(double) * (size_t)N * 4 * D * D) * 2;              // coef_l, coef_r
+    for (int i = 0; i < N; ++i) { site_off[i] = total; total += al256(sizeof(double) * (size_t)st->cap[i] * 2 * st->cap[i + 1]); }
+    for (int i = 0; i <= N; ++i) { env_off[i] = total; total += al256(sizeof(double) * (size_t)D * st->cap[i] * st->cap[i]); }
+    size_t off_ctrl = total; total += al256(sizeof(dmrg_ctrl_state) * (N - 1));
+    size_t off_theta = total; total += al256(sizeof(double) * nmax);
+    size_t off_X = total; total += al256(sizeof(double) * nmax * D);
+    size_t off_Y = total; total += al256(sizeof(double) * nmax * D);
+    size_t off_U = total; total += al256(sizeof(double) * umax);
+    size_t off_s = total; total += al256(sizeof(double) * smax);
+    size_t off_Vt = total; total += al256(sizeof(double) * vtmax);
+    size_t off_svd = total; total += al256(svd_bytes);
+    size_t off_lz = total; total += al256(lanczos_work_bytes(nmax, st->K, ctx->num_sms));
+    size_t off_res = total; total += al256(sizeof(BondResult));
+    size_t off_info = total; total += al256(sizeof(int) * 4);
+    size_t off_vis = total; total += al256(sizeof(dmrg_visit_record) * (2 * N));
+    size_t off_mlp = total; total += al256(sizeof(float) * MLP_NPARAM);
+    if (st->arena.ensure(total) != DMRG_OK) { delete st; return DMRG_ENOMEM; }
+    char *base = st->arena.as<char>();
+    size_t o = 0;
+    st->W = reinterpret_cast<double *>(base + o); o += al256(sizeof(double) * (size_t)N * D * D * 4);
+    st->coef_mv = reinterpret_cast<double *>(base + o); o += al256(sizeof(double) * (size_t)(N - 1) * 16 * D * D);
+    st->coef_l = reinterpret_cast<double *>(base + o); o += al256(sizeof(double) * (size_t)N * 4 * D * D);
+    st->coef_r = reinterpret_cast<double *>(base + o); o += al256(sizeof(double) * (size_t)N * 4 * D * D);
+    st->A.resize(N);
+    st->env.resize(N + 1);
+    for (int i = 0; i < N; ++i) st->A[i] = reinterpret_cast<double *>(base + site_off[i]);
+    for (int i = 0; i <= N; ++i) st->env[i] = reinterpret_cast<double *>(base + env_off[i]);
+    st->ctrl = reinterpret_cast<dmrg_ctrl_state *>(base + off_ctrl);
+    st->theta = reinterpret_cast<double *>(base + off_theta);
+    st->X = reinterpret_cast<double *>(base + off_X);
+    st->Y = reinterpret_cast<double *>(base + off_Y);
+    st->U = reinterpret_cast<double *>(base + off_U);
+    st->s = reinterpret_cast<double *>(base + off_s);
+    st->Vt = reinterpret_cast<double *>(base + off_Vt);
+    st->svdw = base + off_svd;
+    st->lw = lanczos_work_carve(base + off_lz, nmax, st->K, ctx->num_sms);
+    st->d_res = reinterpret_cast<BondResult *>(base + off_res);
+    st->d_info = reinterpret_cast<int *>(base + off_info);
+    st->d_visits = reinterpret_cast<dmrg_visit_record *>(base + off_vis);
+    st->mlp = reinterpret_cast<float *>(base + off_mlp);
+    if (cudaMallocHost(&st->h_res, sizeof(BondResult)) != cudaSuccess) { st->arena.release(); delete st; return DMRG_ENOMEM; }
+    cudaStream_t cs = ctx->stream;
+    auto fail = [&](dmrg_status s) { cudaStreamSynchronize(cs); cudaFreeHost(st->h_res); st->arena.release(); delete st; return s; };
+    if (cudaMemcpyAsync(st->W, W_dev, sizeof(double) * (size_t)N * D * D * 4, cudaMemcpyDeviceToDevice, cs) != cudaSuccess)
+        return fail(DMRG_ECUDA);
+    // coefficient tables
+    for (int k = 0; k + 1 < N; ++k) {
+        dmrg_status s0 = build_coef(ctx, 0, D, st->W + (size_t)k * D * D * 4, st->W + (size_t)(k + 1) * D * D * 4,
+                                    st->coef_mv + (size_t)k * 16 * D * D);
+        if (s0 != DMRG_OK) return fail(s0);
+    }
+    for (int i = 0; i < N; ++i) {
+        dmrg_status s1 = build_coef(ctx, 1, D, st->W + (size_t)i * D * D * 4, nullptr, st->coef_l + (size_t)i * 4 * D * D);
+        dmrg_status s2 = build_coef(ctx, 2, D, st->W + (size_t)i * D * D * 4, nullptr, st->coef_r + (size_t)i * 4 * D * D);
+        if (s1 != DMRG_OK || s2 != DMRG_OK) return fail(DMRG_ECUDA);
+    }
+    // initial MPS entries
+    {
+        size_t off = 0;
+        for (int i = 0; i < N; ++i) {
+            size_t sz = (size_t)st->chi[i] * 2 * st->chi[i + 1];
+            if (cudaMemcpyAsync(st->A[i], mps_init_dev + off, sizeof(double) * sz, cudaMemcpyDeviceToDevice, cs) != cudaSuccess)
+                return fail(DMRG_ECUDA);
+            off += sz;
+        }
+    }
+    // right-canonical form: M_i = U S Vt, A_i <- Vt, A_{i-1} <- A_{i-1} U S
+    for (int i = N - 1; i >= 1; --i) {
+        int rows = st->chi[i], cols = 2 * st->chi[i + 1];
+        int r = std::min(rows, cols);
+        dmrg_status s0 = svd_jacobi(ctx, st->A[i], rows, cols, st->U, st->s, st->Vt, st->svdw, 60, st->d_info);
+        if (s0 != DMRG_OK) return fail(s0);
+        if (r != rows) return fail(DMRG_EINVAL);
+        k_copy_scale<<<grid1d((long long)r * cols, 256, ctx->num_sms), 256, 0, cs>>>(st->Vt, st->A[i], r, cols, nullptr);
+        k_copy_scale<<<grid1d((long long)rows * r, 256, ctx->num_sms), 256, 0, cs>>>(st->U, st->theta, rows, r, st->s);
+        int pr = 2 * st->chi[i - 1];
+        s0 = gemm_f64(cs, pr, r, rows, 1.0, st->A[i - 1], rows, 1, 0, st->theta, r, 1, 0, 0.0, st->X, r, 1, 0, 1);
+        if (s0 != DMRG_OK) return fail(s0);
+        k_copy_scale<<<grid1d((long long)pr * r, 256, ctx->num_sms), 256, 0, cs>>>(st->X, st->A[i - 1], pr, r, nullptr);
+        if (cudaGetLastError() != cudaSuccess) return fail(DMRG_ECUDA);
+    }
+    k_normalise<<<1, 256, 0, cs>>>(st->A[0], 2 * st->chi[1]);
+    k_boundary_env<<<1, 32, 0, cs>>>(st->env[0], D, D - 1);
+    k_boundary_env<<<1, 32, 0, cs>>>(st->env[N], D, 0);
+    for (int i = N - 1; i >= 2; --i) {
+        dmrg_status s0 = env_right_dev(ctx, st->p.prec, D, st->chi[i], st->chi[i + 1], st->env[i + 1],
+                                       st->coef_r + (size_t)i * 4 * D * D, st->A[i], st->env[i], st->X, st->Y);
+        if (s0 != DMRG_OK) return fail(s0);
+    }
+    k_init_ctrl<<<(N - 1 + 127) / 128, 128, 0, cs>>>(st->ctrl, N - 1, p->chi_min);
+    if (cudaGetLastError() != cudaSuccess) return fail(DMRG_ECUDA);
+    if (cudaStreamSynchronize(cs) != cudaSuccess) return fail(DMRG_ECUDA);
+    *out = st;
+    return DMRG_OK;
+}
+
+void dmrg_state_destroy(dmrg_state *st)
+{
+    if (!st) return;
+    cudaStreamSynchronize(st->ctx->stream);
+    if (st->h_res) cudaFreeHost(st->h_res);
+    st->arena.release();
+    delete st;
+}
+
+dmrg_status dmrg_sweep(dmrg_ctx *ctx, dmrg_state *st, int n_sweeps, int stop_on_conv, dmrg_sweep_record *rec_host,
+                       dmrg_visit_record *visits_host, int *sweeps_done)
+{
+    if (!ctx || !st || st->ctx != ctx || n_sweeps < 0) return DMRG_EINVAL;
+    const int N = st->N, V = 2 * N - 3;
+    double E_prev = 0.0;
+    int done = 0;
+    for (int t = 0; t < n_sweeps; ++t) {
+        double flops = 0.0;
+        DMRG_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
+        int v = 0;
+        double E_last = 0.0;
+        for (int half = 0; half < 2; ++half) {
+            const int nb = (half == 0) ? N - 1 : N - 2;
+            for (int q = 0; q < nb; ++q, ++v) {
+                const int k = (half == 0) ? q : N - 3 - q;
+                const int go_right = (half == 0 && k < N - 2);
+                const int do_ctrl = (st->p.pid_steps_per_sweep >= 2) || (half == 0);
+                int kk;
+                DMRG_TRY(bond_step(st, k, go_right, do_ctrl, st->d_visits + v, half == 0 ? 1 : -1, &flops, &kk, &E_last));
+            }
+        }
+        DMRG_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
+        DMRG_CUDA(cudaEventSynchronize(ctx->ev1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        std::vector<dmrg_visit_record> vis(V);
+        DMRG_CUDA(cudaMemcpy(vis.data(), st->d_visits, sizeof(dmrg_visit_record) * V, cudaMemcpyDeviceToHost));
+        if (visits_host) std::memcpy(visits_host + (size_t)t * V, vis.data(), sizeof(dmrg_visit_record) * V);
+        if (rec_host) {
+            dmrg_sweep_record r{};
+            r.E = E_last;
+            double mx = 0.0, sum = 0.0;
+            int mk = 0;
+            for (auto &x : vis) { mx = std::max(mx, x.trunc_err); sum += x.k; mk = std::max(mk, x.k); }
+            r.max_trunc_err = mx;
+            r.mean_chi = sum / V;
+            r.max_chi = mk;
+            r.n_visits = V;
+            r.seconds = ms * 1e-3;
+            r.flops = flops;
+            rec_host[t] = r;
+        }
+        st->sweep_index++;
+        done = t + 1;
+        dmrg_status ds = dmrg_get_status(ctx);
+        if (ds != DMRG_OK && ds != DMRG_ENOCONV) return ds;
+        if (stop_on_conv && t > 0 && std::fabs((E_last - E_prev) / E_last) < st->p.eps_conv) break;
+        E_prev = E_last;
+    }
+    if (sweeps_done) *sweeps_done = done;
+    return DMRG_OK;
+}
+
+dmrg_status bond_update(dmrg_ctx *ctx, dmrg_state *st, int bond, int direction, double *E_out, int *k_out)
+{
+    if (!ctx || !st || st->ctx != ctx || bond < 0 || bond > st->N - 2 || (direction != 1 && direction != -1))
+        return DMRG_EINVAL;
+    int go_right = (direction == 1) && (bond < st->N - 2);
+    DMRG_TRY(bond_step(st, bond, go_right, 1, st->d_visits, direction, nullptr, k_out, E_out));
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_state_chi(dmrg_state *st, int *chi_host)
+{
+    if (!st || !chi_host) return DMRG_EINVAL;
+    std::memcpy(chi_host, st->chi.data(), sizeof(int) * (st->N + 1));
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_state_site(dmrg_state *st, int i, const double **A_dev)
+{
+    if (!st || !A_dev || i < 0 || i >= st->N) return DMRG_EINVAL;
+    *A_dev = st->A[i];
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_state_env(dmrg_state *st, int left, int k, double *E_out_dev)
+{
+    if (!st || !E_out_dev || k < 0 || k > st->N) return DMRG_EINVAL;
+    const int c = st->chi[k], D = st->D;
+    if (left) {
+        DMRG_CUDA(cudaMemcpyAsync(E_out_dev, st->env[k], sizeof(double) * D * c * c, cudaMemcpyDeviceToDevice,
+                                  st->ctx->stream));
+    } else {
+        DMRG_TRY(transpose_sq(st->ctx, st->env[k], E_out_dev, c, D));
+    }
+    DMRG_CUDA(cudaStreamSynchronize(st->ctx->stream));
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_state_ctrl(dmrg_state *st, dmrg_ctrl_state **ctrl_dev)
+{
+    if (!st || !ctrl_dev) return DMRG_EINVAL;
+    *ctrl_dev = st->ctrl;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_state_set_mlp(dmrg_state *st, const float *params_dev)
+{
+    if (!st) return DMRG_EINVAL;
+    if (!params_dev) { st->has_mlp = 0; return DMRG_OK; }
+    DMRG_CUDA(cudaMemcpyAsync(st->mlp, params_dev, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToDevice, st->ctx->stream));
+    st->has_mlp = 1;
+    return DMRG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// standalone building blocks
+// ---------------------------------------------------------------------------
+dmrg_status svd_truncate(dmrg_ctx *ctx, const double *theta_dev, int m, int n, int chi_max, double eps, double *U_dev,
+                         double *s_dev, double *Vt_dev, int *k_out, double *S_out, double *trunc_err_out)
+{
+    if (!ctx || !theta_dev || !U_dev || !s_dev || !Vt_dev || m < 1 || n < 1 || chi_max < 1 || !(eps >= 0.0))
+        return DMRG_EINVAL;
+    const int r = std::min(m, n), l = std::max(m, n);
+    size_t need = al256(svd_work_bytes(r, l)) + al256(sizeof(BondResult)) + al256(sizeof(int) * 4);
+    DMRG_TRY(ctx->work.ensure(need));
+    char *base = ctx->work.as<char>();
+    BondResult *res = reinterpret_cast<BondResult *>(base + al256(svd_work_bytes(r, l)));
+    int *info = reinterpret_cast<int *>(base + al256(svd_work_bytes(r, l)) + al256(sizeof(BondResult)));
+    DMRG_TRY(svd_jacobi(ctx, theta_dev, m, n, U_dev, s_dev, Vt_dev, base, ctx->jacobi_max_sweeps, info));
+    dmrg_params p{};
+    p.eps_trunc = eps;
+    p.chi_min = 1;
+    p.chi_max = chi_max;
+    p.multiplet_guard = 0;
+    p.ctrl = DMRG_CTRL_FIXED;
+    DMRG_TRY(launch_decide(ctx, s_dev, r, nullptr, p, 0, chi_max, nullptr, 0, 1, 0, nullptr, res, nullptr, 0));
+    DMRG_CUDA(cudaMemcpyAsync(ctx->h_pinned_d, res, sizeof(BondResult), cudaMemcpyDeviceToHost, ctx->stream));
+    DMRG_CUDA(cudaMemcpyAsync(ctx->h_pinned_i + 32, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    BondResult br;
+    std::memcpy(&br, ctx->h_pinned_d, sizeof(BondResult));
+    if (k_out) *k_out = br.k;
+    if (S_out) *S_out = br.S;
+    if (trunc_err_out) *trunc_err_out = br.eps;
+    dmrg_status ds = dmrg_get_status(ctx);
+    if (ctx->h_pinned_i[32] < 0) return DMRG_ENOCONV;
+    return ds == DMRG_ENOCONV ? DMRG_OK : ds;
+}
+
+dmrg_status entropy_pid_step(dmrg_ctx *ctx, int n_bonds, const double *S_raw_dev, dmrg_ctrl_state *st_dev,
+                             const dmrg_params *p_host, int *chi_out_dev)
+{
+    if (!ctx || !S_raw_dev || !st_dev || !p_host || !chi_out_dev || n_bonds < 0) return DMRG_EINVAL;
+    return launch_ctrl_steps(ctx, n_bonds, S_raw_dev, st_dev, *p_host, chi_out_dev);
+}
+
+dmrg_status dmrg_entropy(dmrg_ctx *ctx, int n, const double *s_dev, double *S_dev, double *eps_dev)
+{
+    if (!ctx || !s_dev || !S_dev || n < 1) return DMRG_EINVAL;
+    return launch_entropy(ctx, n, s_dev, S_dev, eps_dev);
+}
+
+// scratch for the standalone contraction calls: coefficient table, Rt, X, Y
+static dmrg_status standalone_scratch(dmrg_ctx *ctx, int D, int cl, int cr, double **C, double **Rt, double **X,
+                                      double **Y, size_t extra, void **extra_ptr)
+{
+    size_t nX = (size_t)D * 4 * cl * cr + (size_t)D * 4 * cl * cl + 64;
+    size_t need = al256(sizeof(double) * 1024) + al256(sizeof(double) * (size_t)D * std::max(cr, cl) * std::max(cr, cl)) +
+                  2 * al256(sizeof(double) * nX) + al256(extra);
+    DMRG_TRY(ctx->work2.ensure(need));
+    char *b = ctx->work2.as<char>();
+    *C = reinterpret_cast<double *>(b); b += al256(sizeof(double) * 1024);
+    *Rt = reinterpret_cast<double *>(b); b += al256(sizeof(double) * (size_t)D * std::max(cr, cl) * std::max(cr, cl));
+    *X = reinterpret_cast<double *>(b); b += al256(sizeof(double) * nX);
+    *Y = reinterpret_cast<double *>(b); b += al256(sizeof(double) * nX);
+    if (extra_ptr) *extra_ptr = b;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_heff_apply(dmrg_ctx *ctx, int prec, int D, int cl, int cr, const double *L_dev, const double *W1_dev,
+                            const double *W2_dev, const double *R_dev, const double *theta_dev, double *y_dev)
+{
+    if (!ctx || !L_dev || !W1_dev || !W2_dev || !R_dev || !theta_dev || !y_dev || D < 1 || 4 * D > kMaxCh || cl < 1 ||
+        cr < 1)
+        return DMRG_EINVAL;
+    if (prec != DMRG_PREC_FP64 && !(prec == DMRG_PREC_3XTF32 && tc_available(ctx))) return DMRG_EUNSUPPORTED;
+    double *C, *Rt, *X, *Y;
+    DMRG_TRY(standalone_scratch(ctx, D, cl, cr, &C, &Rt, &X, &Y, 0, nullptr));
+    DMRG_TRY(build_coef(ctx, 0, D, W1_dev, W2_dev, C));
+    DMRG_TRY(transpose_sq(ctx, R_dev, Rt, cr, D));
+    DMRG_TRY(heff_apply_dev(ctx, prec, D, cl, cr, L_dev, Rt, C, X, Y, theta_dev, y_dev));
+    DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return dmrg_get_status(ctx);
+}
+
+dmrg_status dmrg_env_left(dmrg_ctx *ctx, int prec, int D, int cl, int ck, const double *L_dev, const double *W_dev,
+                          const double *A_dev, double *Lnew_dev)
+{
+    if (!ctx || !L_dev || !W_dev || !A_dev || !Lnew_dev || D < 1 || 2 * D > kMaxCh || cl < 1 || ck < 1)
+        return DMRG_EINVAL;
+    if (prec != DMRG_PREC_FP64 && !(prec == DMRG_PREC_3XTF32 && tc_available(ctx))) return DMRG_EUNSUPPORTED;
+    double *C, *Rt, *X, *Y;
+    DMRG_TRY(standalone_scratch(ctx, D, cl, ck, &C, &Rt, &X, &Y, 0, nullptr));
+    DMRG_TRY(build_coef(ctx, 1, D, W_dev, nullptr, C));
+    DMRG_TRY(env_left_dev(ctx, prec, D, cl, ck, L_dev, C, A_dev, Lnew_dev, X, Y));
+    DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return dmrg_get_status(ctx);
+}
+
+dmrg_status dmrg_env_right(dmrg_ctx *ctx, int prec, int D, int ck, int cr, const double *R_dev, const double *W_dev,
+                           const double *B_dev, double *Rnew_dev)
+{
+    if (!ctx || !R_dev || !W_dev || !B_dev || !Rnew_dev || D < 1 || 2 * D > kMaxCh || cr < 1 || ck < 1)
+        return DMRG_EINVAL;
+    if (prec != DMRG_PREC_FP64 && !(prec == DMRG_PREC_3XTF32 && tc_available(ctx))) return DMRG_EUNSUPPORTED;
+    double *C, *Rt, *X, *Y;
+    void *extra;
+    DMRG_TRY(standalone_scratch(ctx, D, ck, cr, &C, &Rt, &X, &Y, sizeof(double) * (size_t)D * ck * ck, &extra));
+    double *Rtn = static_cast<double *>(extra);
+    DMRG_TRY(build_coef(ctx, 2, D, W_dev, nullptr, C));
+    DMRG_TRY(transpose_sq(ctx, R_dev, Rt, cr, D));
+    DMRG_TRY(env_right_dev(ctx, prec, D, ck, cr, Rt, C, B_dev, Rtn, X, Y));
+    DMRG_TRY(transpose_sq(ctx, Rtn, Rnew_dev, ck, D));
+    DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return dmrg_get_status(ctx);
+}
+
+dmrg_status dmrg_lanczos(dmrg_ctx *ctx, int prec, int D, int cl, int cr, const double *L_dev, const double *W1_dev,
+                         const double *W2_dev, const double *R_dev, double *theta_dev, int K, double *E_out,
+                         int *steps_out)
+{
+    if (!ctx || !L_dev || !W1_dev || !W2_dev || !R_dev || !theta_dev || D < 1 || 4 * D > kMaxCh || cl < 1 || cr < 1 ||
+        K < 1 || K > LZ_MAXK)
+        return DMRG_EINVAL;
+    if (prec != DMRG_PREC_FP64 && !(prec == DMRG_PREC_3XTF32 && tc_available(ctx))) return DMRG_EUNSUPPORTED;
+    const long long n = 4LL * cl * cr;
+    double *C, *Rt, *X, *Y;
+    void *extra;
+    DMRG_TRY(standalone_scratch(ctx, D, cl, cr, &C, &Rt, &X, &Y, lanczos_work_bytes(n, K, ctx->num_sms), &extra));
+    LanczosWork lw = lanczos_work_carve(extra, n, K, ctx->num_sms);
+    DMRG_TRY(build_coef(ctx, 0, D, W1_dev, W2_dev, C));
+    DMRG_TRY(transpose_sq(ctx, R_dev, Rt, cr, D));
+    MatvecFn mv = [&](const double *x, double *y) { return heff_apply_dev(ctx, prec, D, cl, cr, L_dev, Rt, C, X, Y, x, y); };
+    int Ke = (int)std::min<long long>(K, n);
+    DMRG_TRY(lanczos_run(ctx, lw, n, Ke, theta_dev, mv));
+    LzState h;
+    DMRG_CUDA(cudaMemcpyAsync(&h, lw.lz, sizeof(LzState), cudaMemcpyDeviceToHost, ctx->stream));
+    DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (E_out) *E_out = h.E;
+    if (steps_out) *steps_out = h.m;
+    return dmrg_get_status(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// gemm_f64.cu -- FP64 strided batched GEMM on the CUDA cores (DFMA).
+//
+// Every FP64 contraction of the local update (H_eff stages 1 and 3, the
+// environment update stages 1 and 3, the two-site tensor and the gauge
+// moves) is one call of this kernel with the operand strides chosen so that
+// no tensor is ever transposed in memory.  GB300's FP64 pipe is narrow, so
+// a 64 x 64 register-tiled kernel already sits at the DFMA roof; the tiles
+// are staged through shared memory with loads coalesced along whichever
+// operand stride is unit.
+#include "common.cuh"
+
+namespace dmrg {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4, NT = 256;
+
+__global__ void __launch_bounds__(NT) k_gemm_f64(int M, int N, int K, double alpha, const double *__restrict__ A,
+                                                 long long sAm, long long sAk, long long sAb,
+                                                 const double *__restrict__ B, long long sBk, long long sBn,
+                                                 long long sBb, double beta, double *__restrict__ C, long long sCm,
+                                                 long long sCn, long long sCb)
+{
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN + 1];
+    const int bz = blockIdx.z;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    A += (long long)bz * sAb;
+    B += (long long)bz * sBb;
+    C += (long long)bz * sCb;
+    double acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+    const bool a_kfast = (sAk == 1);
+    const bool b_nfast = (sBn == 1);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+        for (int it = 0; it < (BM * BK) / NT; ++it) {
+            int idx = tid + it * NT;
+            int mm, kk;
+            if (a_kfast) { mm = idx / BK; kk = idx % BK; } else { kk = idx / BM; mm = idx % BM; }
+            int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < M && gk < K) ? A[(long long)gm * sAm + (long long)gk * sAk] : 0.0;
+        }
+#pragma unroll
+        for (int it = 0; it < (BN * BK) / NT; ++it) {
+            int idx = tid + it * NT;
+            int nn, kk;
+            if (b_nfast) { kk = idx / BN; nn = idx % BN; } else { nn = idx / BK; kk = idx % BK; }
+            int gn = n0 + nn, gk = k0 + kk;
+            Bs[kk][nn] = (gn < N && gk < K) ? B[(long long)gk * sBk + (long long)gn * sBn] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        int gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            int gn = n0 + tx + 16 * j;
+            if (gn >= N) continue;
+            double *c = C + (long long)gm * sCm + (long long)gn * sCn;
+            double v = alpha * acc[i][j];
+            if (beta != 0.0) v += beta * *c;
+            *c = v;
+        }
+    }
+}
+
+}  // namespace
+
+dmrg_status gemm_f64(cudaStream_t st, int M, int N, int K, double alpha, const double *A, long long sAm,
+                     long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
+                     double beta, double *C, long long sCm, long long sCn, long long sCb, int batch)
+{
+    if (M <= 0 || N <= 0 || batch <= 0) return DMRG_OK;
+    if (batch > 65535) return DMRG_EINVAL;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+    if (grid.y > 65535) return DMRG_EINVAL;
+    if (K <= 0) {
+        // C = beta * C: run the kernel with K = 0 (accumulators stay zero)
+        K = 0;
+    }
+    k_gemm_f64<<<grid, NT, 0, st>>>(M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb);
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
+dmrg_status gemm(dmrg_ctx *ctx, int prec, int M, int N, int K, double alpha, const double *A, long long sAm,
+                 long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
+                 double beta, double *C, long long sCm, long long sCn, long long sCb, int batch)
+{
+    if (prec == DMRG_PREC_FP64)
+        return gemm_f64(ctx->stream, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb,
+                        batch);
+    if (prec == DMRG_PREC_3XTF32)
+        return gemm_3xtf32(ctx, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb, batch);
+    return DMRG_EUNSUPPORTED;
+}
+
+}  // namespace dmrg

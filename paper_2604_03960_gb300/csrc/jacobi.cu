@@ -1,0 +1,305 @@
+// jacobi.cu -- one-sided (Hestenes) Jacobi SVD of the two-site tensor.
+//
+// The SVD of Eq. (20) is computed by orthogonalising r = min(m, n) vectors of
+// length l = max(m, n) (the columns of theta when n <= m, its rows when
+// m < n) with plane rotations: for a pair (x_i, x_j) with Gram entries
+// alpha = |x_i|^2, beta = |x_j|^2, gamma = x_i.x_j the rotation
+//   zeta = (beta - alpha) / (2 gamma),  t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+//   c = 1 / sqrt(1 + t^2),  s = c t,   x_i <- c x_i - s x_j,  x_j <- s x_i + c x_j
+// makes them orthogonal (Hestenes 1958; the 2x2 symmetric Schur step of
+// Golub & Van Loan 8.5.2).  A sweep visits every pair once in round-robin
+// ("circle method") order: each round is a perfect matching of the vectors,
+// so all r/2 rotations of a round are independent and run one per warp.
+// The sweep loop runs inside one persistent cooperative kernel with a
+// bounded grid barrier between rounds; the iteration stops after a sweep
+// without rotations.  On exit s_i = |x_i|, u_i = x_i / s_i and the
+// accumulated rotations give V.
+#include "common.cuh"
+
+#include <cooperative_groups.h>
+
+namespace dmrg {
+
+size_t svd_work_bytes(int r, int l)
+{
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    return al(sizeof(double) * (size_t)r * l) + al(sizeof(double) * (size_t)r * r) + al(sizeof(double) * r) +
+           al(sizeof(int) * r) + al(sizeof(unsigned) * 8);
+}
+
+SvdWork svd_work_carve(void *base, int r, int l)
+{
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    char *p = static_cast<char *>(base);
+    SvdWork w;
+    w.X = reinterpret_cast<double *>(p); p += al(sizeof(double) * (size_t)r * l);
+    w.Vm = reinterpret_cast<double *>(p); p += al(sizeof(double) * (size_t)r * r);
+    w.nrm = reinterpret_cast<double *>(p); p += al(sizeof(double) * r);
+    w.perm = reinterpret_cast<int *>(p); p += al(sizeof(int) * r);
+    w.sync = reinterpret_cast<unsigned *>(p);
+    return w;
+}
+
+namespace {
+
+// X[i][j] = theta column i (tr = 0) or row i (tr = 1); Vm = identity.
+__global__ void k_jac_load(const double *__restrict__ A, int m, int n, int tr, int r, int l, double *__restrict__ X,
+                           double *__restrict__ Vm, unsigned *sync)
+{
+    __shared__ double tile[32][33];
+    // transposed copy through a shared tile when tr == 0
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    if (!tr) {
+        // X (r x l) = A^T: X[i][j] = A[j][i], i < n = r, j < m = l
+        for (int yy = threadIdx.y; yy < 32; yy += 8) {
+            int row = by + yy, col = bx + threadIdx.x;          // read A[row][col]
+            tile[yy][threadIdx.x] = (row < m && col < n) ? A[(long long)row * n + col] : 0.0;
+        }
+        __syncthreads();
+        for (int yy = threadIdx.y; yy < 32; yy += 8) {
+            int i = bx + yy, j = by + threadIdx.x;              // write X[i][j] = A[j][i]
+            if (i < r && j < l) X[(long long)i * l + j] = tile[threadIdx.x][yy];
+        }
+    } else {
+        for (int yy = threadIdx.y; yy < 32; yy += 8) {
+            int i = by + yy, j = bx + threadIdx.x;
+            if (i < r && j < l) X[(long long)i * l + j] = A[(long long)i * n + j];
+        }
+    }
+    // identity (grid covers at least r x r when launched for max(l, r))
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+        int i = by + yy, j = bx + threadIdx.x;
+        if (i < r && j < r) Vm[(long long)i * r + j] = (i == j) ? 1.0 : 0.0;
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.y == 0 && threadIdx.x < 8) sync[threadIdx.x] = 0u;
+}
+
+__device__ __forceinline__ void rr_pair(int rp, int t, int p, int &i, int &j)
+{
+    // circle method on rp (even) players: player rp-1 fixed, the others rotate
+    const int q = rp - 1;
+    if (p == 0) {
+        i = q;
+        j = t;
+    } else {
+        i = (t + p) % q;
+        j = (t - p + q) % q;
+    }
+}
+
+__device__ __forceinline__ bool block_barrier(unsigned *words, int *status)
+{
+    if (gridDim.x == 1) {
+        __syncthreads();
+        return true;
+    }
+    return grid_barrier(words, status);
+}
+
+__global__ void __launch_bounds__(256) k_jac_sweeps(double *__restrict__ X, double *__restrict__ Vm, int r, int l,
+                                                    int max_sweeps, double tol, unsigned *sync, int *status,
+                                                    int *info)
+{
+    const int lane = threadIdx.x & 31;
+    const int warps_per_block = blockDim.x >> 5;
+    const int gwarp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * warps_per_block;
+    const int rp = r + (r & 1);
+    const int npairs = rp / 2;
+    unsigned *barrier = sync;       // [0], [1]
+    unsigned *rotc = sync + 2;      // [2], [3] alternating per sweep
+    __shared__ unsigned block_rot;
+    int sweep = 0;
+    bool converged = false;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) block_rot = 0;
+        __syncthreads();
+        unsigned my_rot = 0;
+        for (int t = 0; t < rp - 1; ++t) {
+            for (int p = gwarp; p < npairs; p += nwarps) {
+                int i, j;
+                rr_pair(rp, t, p, i, j);
+                if (i >= r || j >= r) continue;
+                double *xi = X + (long long)i * l, *xj = X + (long long)j * l;
+                double a = 0.0, b = 0.0, g = 0.0;
+                for (int k = lane; k < l; k += 32) {
+                    double u = xi[k], v = xj[k];
+                    a = fma(u, u, a);
+                    b = fma(v, v, b);
+                    g = fma(u, v, g);
+                }
+                a = warp_sum(a);
+                b = warp_sum(b);
+                g = warp_sum(g);
+                if (!(a > 0.0 && b > 0.0)) continue;
+                if (!(fabs(g) > tol * sqrt(a) * sqrt(b))) continue;
+                double zeta = (b - a) / (2.0 * g);
+                double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
+                for (int k = lane; k < l; k += 32) {
+                    double u = xi[k], v = xj[k];
+                    xi[k] = c * u - s * v;
+                    xj[k] = s * u + c * v;
+                }
+                double *vi = Vm + (long long)i * r, *vj = Vm + (long long)j * r;
+                for (int k = lane; k < r; k += 32) {
+                    double u = vi[k], v = vj[k];
+                    vi[k] = c * u - s * v;
+                    vj[k] = s * u + c * v;
+                }
+                if (lane == 0) my_rot++;
+            }
+            if (!block_barrier(barrier, status)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
+                return;
+            }
+        }
+        if (lane == 0 && my_rot) atomicAdd(&block_rot, my_rot);
+        __syncthreads();
+        if (threadIdx.x == 0 && block_rot) atomicAdd(&rotc[sweep & 1], block_rot);
+        if (!block_barrier(barrier, status)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
+            return;
+        }
+        unsigned total = *(volatile unsigned *)&rotc[sweep & 1];
+        if (blockIdx.x == 0 && threadIdx.x == 0) rotc[(sweep + 1) & 1] = 0u;
+        if (total == 0u) {
+            converged = true;
+            ++sweep;
+            break;
+        }
+        // make the reset of the next counter visible before anyone adds to it
+        if (!block_barrier(barrier, status)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
+            return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        info[0] = converged ? sweep : -sweep;
+        if (!converged) atomicOr(status, ST_NOCONV);
+    }
+}
+
+// nrm[i] = |x_i|, one warp per vector
+__global__ void k_jac_norms(const double *__restrict__ X, int r, int l, double *__restrict__ nrm)
+{
+    int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= r) return;
+    const double *x = X + (long long)w * l;
+    double a = 0.0;
+    for (int k = lane; k < l; k += 32) a = fma(x[k], x[k], a);
+    a = warp_sum(a);
+    if (lane == 0) nrm[w] = sqrt(a);
+}
+
+// perm[rank] = i, descending by norm, ties by index
+__global__ void k_jac_rank(const double *__restrict__ nrm, int r, int *__restrict__ perm)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r) return;
+    double v = nrm[i];
+    if (!(v >= 0.0)) v = -1.0;     // NaN sorts last and keeps the ranks a permutation
+    int rank = 0;
+    for (int j = 0; j < r; ++j) {
+        double w = nrm[j];
+        if (!(w >= 0.0)) w = -1.0;
+        rank += (w > v) || (w == v && j < i);
+    }
+    perm[rank] = i;
+}
+
+// One block per output index c: writes s[c], U[:, c], Vt[c, :] with the sign
+// convention "largest |entry| of U[:, c] positive".
+__global__ void k_jac_out(const double *__restrict__ X, const double *__restrict__ Vm, const double *__restrict__ nrm,
+                          const int *__restrict__ perm, int m, int n, int tr, int r, int l, double *__restrict__ U,
+                          double *__restrict__ s, double *__restrict__ Vt)
+{
+    __shared__ double sh_v[32];
+    __shared__ int sh_i[32];
+    const int c = blockIdx.x;
+    int i = perm[c];
+    if (i < 0 || i >= r) i = c;
+    const double sig = nrm[i];
+    const double inv = (sig > 0.0) ? 1.0 / sig : 0.0;
+    // U column source: X row i scaled (tr = 0, length m = l) or Vm row i (tr = 1, length m = r)
+    const double *usrc = tr ? (Vm + (long long)i * r) : (X + (long long)i * l);
+    const double uscale = tr ? 1.0 : inv;
+    // argmax |u|
+    double best = -1.0;
+    int bidx = 0;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        double a = fabs(usrc[k]);
+        if (a > best) { best = a; bidx = k; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { sh_v[threadIdx.x >> 5] = best; sh_i[threadIdx.x >> 5] = bidx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bv = sh_v[0];
+        int bi = sh_i[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (sh_v[w] > bv || (sh_v[w] == bv && sh_i[w] < bi)) { bv = sh_v[w]; bi = sh_i[w]; }
+        sh_i[0] = bi;
+        s[c] = sig;
+    }
+    __syncthreads();
+    const double sign = (usrc[sh_i[0]] < 0.0) ? -1.0 : 1.0;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) U[(long long)k * r + c] = sign * uscale * usrc[k];
+    const double *vsrc = tr ? (X + (long long)i * l) : (Vm + (long long)i * r);
+    const double vscale = tr ? inv : 1.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) Vt[(long long)c * n + k] = sign * vscale * vsrc[k];
+}
+
+}  // namespace
+
+dmrg_status svd_jacobi(dmrg_ctx *ctx, const double *A, int m, int n, double *U, double *s, double *Vt, void *work,
+                       int max_sweeps, int *d_info)
+{
+    if (m <= 0 || n <= 0) return DMRG_EINVAL;
+    const int tr = (m < n);
+    const int r = tr ? m : n, l = tr ? n : m;
+    SvdWork w = svd_work_carve(work, r, l);
+    cudaStream_t st = ctx->stream;
+    {
+        int big = l > r ? l : r;
+        dim3 grid((big + 31) / 32, (big + 31) / 32);
+        if (!tr) grid = dim3((n + 31) / 32 > (r + 31) / 32 ? (n + 31) / 32 : (r + 31) / 32,
+                             (m + 31) / 32 > (r + 31) / 32 ? (m + 31) / 32 : (r + 31) / 32);
+        k_jac_load<<<grid, dim3(32, 8), 0, st>>>(A, m, n, tr, r, l, w.X, w.Vm, w.sync);
+        DMRG_CUDA(cudaGetLastError());
+    }
+    const double tol = sqrt((double)l) * 2.220446049250313e-16;
+    const int rp = r + (r & 1);
+    const int npairs = rp / 2;
+    int threads = 256;
+    int blocks = 1;
+    if (r > 128) {
+        int per_sm = 0;
+        DMRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jac_sweeps, threads, 0));
+        int maxb = per_sm * ctx->num_sms;
+        blocks = (npairs + 7) / 8;
+        if (blocks > maxb) blocks = maxb;
+        if (blocks < 1) blocks = 1;
+    }
+    double *X = w.X, *Vm = w.Vm;
+    unsigned *sync = w.sync;
+    int *status = ctx->d_status;
+    void *args[] = {&X, &Vm, (void *)&r, (void *)&l, &max_sweeps, (void *)&tol, &sync, &status, &d_info};
+    if (blocks == 1) {
+        k_jac_sweeps<<<1, threads, 0, st>>>(X, Vm, r, l, max_sweeps, tol, sync, status, d_info);
+    } else {
+        DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_jac_sweeps, dim3(blocks), dim3(threads), args, 0, st));
+    }
+    DMRG_CUDA(cudaGetLastError());
+    k_jac_norms<<<(r * 32 + 255) / 256, 256, 0, st>>>(X, r, l, w.nrm);
+    k_jac_rank<<<(r + 255) / 256, 256, 0, st>>>(w.nrm, r, w.perm);
+    k_jac_out<<<r, 256, 0, st>>>(X, Vm, w.nrm, w.perm, m, n, tr, r, l, U, s, Vt);
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
+}  // namespace dmrg

@@ -1,0 +1,302 @@
+// lanczos.cu -- Lanczos eigensolver for the local problem H_eff theta = E theta (Eq. 19).
+//
+// The paper leaves the local eigensolver unnamed; this is the K-step Lanczos
+// recurrence with full reorthogonalisation by two classical Gram-Schmidt
+// passes, all in FP64 and all on the device:
+//   v0 = theta/|theta|;  w = H v_j;  alpha_j = v_j.w;  w -= alpha_j v_j + beta_j v_{j-1};
+//   w -= V (V^T w) (twice);  beta_{j+1} = |w|;  v_{j+1} = w / beta_{j+1}
+// stopping early (device flag, no host round trip) when beta < 1e-14 max|alpha|.
+// The K x K tridiagonal T is solved on the device by Sturm-sequence
+// bisection for its lowest eigenvalue and inverse iteration for the vector;
+// the Ritz vector is V y0, normalised.  The vector kernels are HBM-bound
+// streams; every reduction is deterministic (per-block partials summed in
+// block order by the last block to finish).
+#include "common.cuh"
+#include "lanczos.cuh"
+
+namespace dmrg {
+namespace {
+
+constexpr int RB = 256;        // threads per block of the vector kernels
+constexpr int MAXQ = 24;       // max vectors in one multi-dot
+
+// c[q] = sum_i V[q][i] * w[i] for q < nq, plus (if want_norm) c[nq] = |w|^2.
+// Results go to out[] through `mode`:
+//   mode 0: out[q] = c[q]
+//   mode 1: alpha step: lz->alpha[j] = c[0], lz->amax = max
+//   mode 2: beta step:  beta = sqrt(c[0]) ...
+struct ReduceArgs {
+    const double *V;      // vectors, stride ldv
+    long long ldv;
+    int nq;
+    const double *w;      // second operand
+    long long n;
+    double *partials;     // gridDim.x * (MAXQ+1)
+    unsigned *counter;    // zero on entry, reset by the last block
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(RB) k_multidot(ReduceArgs a, LzState *lz, int j, double *out)
+{
+    if (MODE != 3 && lz && !lz->active) return;
+    __shared__ double sh[32];
+    __shared__ bool last;
+    const int nq = a.nq;
+    double acc[MAXQ + 1];
+#pragma unroll
+    for (int q = 0; q <= MAXQ; ++q) acc[q] = 0.0;
+    const long long stride = (long long)gridDim.x * RB;
+    for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < a.n; i += stride) {
+        double wi = a.w[i];
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q)
+            if (q < nq) acc[q] = fma(a.V[(long long)q * a.ldv + i], wi, acc[q]);
+        acc[MAXQ] = fma(wi, wi, acc[MAXQ]);
+    }
+    for (int q = 0; q <= MAXQ; ++q) {
+        if (q < nq || q == MAXQ) {
+            double s = block_sum(acc[q], sh);
+            if (threadIdx.x == 0) a.partials[(long long)blockIdx.x * (MAXQ + 1) + q] = s;
+        }
+    }
+    __threadfence();
+    if (threadIdx.x == 0) {
+        unsigned done = atomicAdd(a.counter, 1u);
+        last = (done == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // final reduction in block order: thread q sums column q
+    for (int q = threadIdx.x; q <= MAXQ; q += RB) {
+        if (!(q < nq || q == MAXQ)) continue;
+        double s = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) s += *(volatile double *)&a.partials[(long long)b * (MAXQ + 1) + q];
+        if (MODE == 0) {
+            out[q] = s;
+        } else if (MODE == 1) {        // alpha_j = v_j . w
+            if (q == 0) {
+                lz->alpha[j] = s;
+                if (fabs(s) > lz->amax) lz->amax = fabs(s);
+            }
+        } else if (MODE == 2) {        // beta_{j+1} = |w|, decide continuation
+            if (q == MAXQ) {
+                double b = sqrt(s);
+                lz->beta[j + 1] = b;
+                lz->m = j + 1;
+                if (j + 1 >= lz->K || !(b > 1e-14 * lz->amax) || !isfinite(b)) lz->active = 0;
+                if (!isfinite(b)) lz->nan = 1;
+            }
+        } else if (MODE == 3) {        // |theta| for the start vector / Ritz vector
+            if (q == MAXQ) lz->scale = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
+        }
+    }
+    if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+// w -= alpha_j v_j + beta_j v_{j-1}
+__global__ void k_three_term(double *__restrict__ w, const double *__restrict__ vj, const double *__restrict__ vjm1,
+                             long long n, const LzState *lz, int j)
+{
+    if (!lz->active) return;
+    const double a = lz->alpha[j];
+    const double b = (j > 0) ? lz->beta[j] : 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        double v = w[i] - a * vj[i];
+        if (j > 0) v -= b * vjm1[i];
+        w[i] = v;
+    }
+}
+
+// w -= sum_q c[q] V[q]   (or w = sum_q c[q] V[q] when overwrite)
+__global__ void k_multiaxpy(double *__restrict__ w, const double *__restrict__ V, long long ldv, int nq,
+                            const double *__restrict__ c, long long n, const LzState *lz, int check_active,
+                            int overwrite)
+{
+    if (check_active && !lz->active) return;
+    if (nq < 0) nq = lz->m;     // Ritz combination: only the vectors actually built
+    __shared__ double cs[MAXQ];
+    if (threadIdx.x < nq) cs[threadIdx.x] = c[threadIdx.x];
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        double acc = 0.0;
+        for (int q = 0; q < nq; ++q) acc = fma(cs[q], V[(long long)q * ldv + i], acc);
+        w[i] = overwrite ? acc : w[i] - acc;
+    }
+}
+
+// dst = src * lz->scale  (start vector / Ritz vector normalisation)
+__global__ void k_scale_by(double *__restrict__ dst, const double *__restrict__ src, long long n, const LzState *lz)
+{
+    const double s = lz->scale;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i] * s;
+}
+
+// v_{j+1} = w / beta_{j+1}
+__global__ void k_next_vec(double *__restrict__ vn, const double *__restrict__ w, long long n, const LzState *lz, int j)
+{
+    if (!lz->active) return;
+    const double inv = 1.0 / lz->beta[j + 1];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) vn[i] = w[i] * inv;
+}
+
+__global__ void k_lz_init(LzState *lz, int K)
+{
+    lz->K = K;
+    lz->m = 0;
+    lz->active = 1;
+    lz->amax = 0.0;
+    lz->nan = 0;
+    lz->scale = 0.0;
+    for (int i = 0; i < LZ_MAXK + 1; ++i) { lz->beta[i] = 0.0; }
+    for (int i = 0; i < LZ_MAXK; ++i) { lz->alpha[i] = 0.0; lz->y[i] = 0.0; }
+}
+
+// number of eigenvalues of the m x m tridiagonal (a, b[1..m-1]) below x
+__device__ int sturm_count(int m, const double *a, const double *b, double x)
+{
+    int cnt = 0;
+    double q = a[0] - x;
+    if (q < 0.0) cnt++;
+    for (int i = 1; i < m; ++i) {
+        double qq = (q != 0.0) ? q : 1e-300;
+        q = (a[i] - x) - b[i] * b[i] / qq;
+        if (q < 0.0) cnt++;
+    }
+    return cnt;
+}
+
+// Lowest eigenpair of T (single thread; m <= LZ_MAXK).
+__global__ void k_tridiag_lowest(LzState *lz, int *status)
+{
+    const int m = lz->m;
+    const double *a = lz->alpha, *b = lz->beta;   // b[i] couples i-1 and i
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < m; ++i) {
+        double r = (i > 0 ? fabs(b[i]) : 0.0) + (i + 1 < m ? fabs(b[i + 1]) : 0.0);
+        lo = fmin(lo, a[i] - r);
+        hi = fmax(hi, a[i] + r);
+    }
+    for (int it = 0; it < 300; ++it) {
+        double x = 0.5 * (lo + hi);
+        if (x <= lo || x >= hi) break;
+        if (sturm_count(m, a, b, x) >= 1) hi = x; else lo = x;
+    }
+    const double lam = 0.5 * (lo + hi);
+    lz->E = lam;
+    // inverse iteration on (T - lam I): tridiagonal LU without pivoting,
+    // shifted slightly below lam so the system stays solvable
+    double y[LZ_MAXK], rhs[LZ_MAXK], dd[LZ_MAXK], ll[LZ_MAXK];
+    const double shift = lam - 1e-13 * fmax(fabs(lam), 1e-300) - 1e-300;
+    for (int i = 0; i < m; ++i) y[i] = 1.0 / sqrt((double)m) * (1.0 + 0.01 * i);
+    for (int it = 0; it < 4; ++it) {
+        // factor
+        dd[0] = a[0] - shift;
+        for (int i = 1; i < m; ++i) {
+            double piv = (dd[i - 1] != 0.0) ? dd[i - 1] : 1e-300;
+            ll[i] = b[i] / piv;
+            dd[i] = (a[i] - shift) - ll[i] * b[i];
+        }
+        for (int i = 0; i < m; ++i) rhs[i] = y[i];
+        for (int i = 1; i < m; ++i) rhs[i] -= ll[i] * rhs[i - 1];
+        double piv = (dd[m - 1] != 0.0) ? dd[m - 1] : 1e-300;
+        y[m - 1] = rhs[m - 1] / piv;
+        for (int i = m - 2; i >= 0; --i) {
+            double p = (dd[i] != 0.0) ? dd[i] : 1e-300;
+            y[i] = (rhs[i] - b[i + 1] * y[i + 1]) / p;
+        }
+        double nn = 0.0;
+        for (int i = 0; i < m; ++i) nn += y[i] * y[i];
+        nn = sqrt(nn);
+        for (int i = 0; i < m; ++i) y[i] /= nn;
+    }
+    // fix the sign (first nonzero component positive) for reproducibility
+    double sgn = 1.0;
+    for (int i = 0; i < m; ++i) if (y[i] != 0.0) { sgn = (y[i] < 0.0) ? -1.0 : 1.0; break; }
+    for (int i = 0; i < m; ++i) lz->y[i] = sgn * y[i];
+    if (!isfinite(lam) || lz->nan) atomicOr(status, ST_NAN);
+}
+
+int grid_for(long long n, int num_sms)
+{
+    long long b = (n + RB - 1) / RB;
+    long long cap = (long long)num_sms * 4;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+size_t lanczos_work_bytes(long long n, int K, int num_sms)
+{
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    size_t vecs = al(sizeof(double) * (size_t)n * (K + 1));   // V (K vectors) + w
+    size_t parts = al(sizeof(double) * (size_t)num_sms * 4 * (MAXQ + 1));
+    return vecs + parts + al(sizeof(LzState)) + al(sizeof(double) * (MAXQ + 1)) + al(64);
+}
+
+LanczosWork lanczos_work_carve(void *base, long long n, int K, int num_sms)
+{
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    char *p = static_cast<char *>(base);
+    LanczosWork w;
+    w.V = reinterpret_cast<double *>(p);
+    w.w = w.V + (size_t)n * K;
+    p += al(sizeof(double) * (size_t)n * (K + 1));
+    w.partials = reinterpret_cast<double *>(p); p += al(sizeof(double) * (size_t)num_sms * 4 * (MAXQ + 1));
+    w.lz = reinterpret_cast<LzState *>(p); p += al(sizeof(LzState));
+    w.c = reinterpret_cast<double *>(p); p += al(sizeof(double) * (MAXQ + 1));
+    w.counter = reinterpret_cast<unsigned *>(p);
+    return w;
+}
+
+dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K, double *theta,
+                        const MatvecFn &matvec)
+{
+    if (K < 1) K = 1;
+    if (K > LZ_MAXK) K = LZ_MAXK;
+    if ((long long)K > n) K = (int)n;
+    cudaStream_t st = ctx->stream;
+    const int g = grid_for(n, ctx->num_sms);
+    DMRG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned), st));
+    k_lz_init<<<1, 1, 0, st>>>(w.lz, K);
+    ReduceArgs ra{nullptr, n, 0, theta, n, w.partials, w.counter};
+    k_multidot<3><<<g, RB, 0, st>>>(ra, w.lz, 0, nullptr);          // |theta|
+    k_scale_by<<<g, RB, 0, st>>>(w.V, theta, n, w.lz);                // v0
+    DMRG_CUDA(cudaGetLastError());
+    for (int j = 0; j < K; ++j) {
+        double *vj = w.V + (size_t)n * j;
+        DMRG_TRY(matvec(vj, w.w));
+        ReduceArgs a1{vj, n, 1, w.w, n, w.partials, w.counter};
+        k_multidot<1><<<g, RB, 0, st>>>(a1, w.lz, j, nullptr);
+        k_three_term<<<g, RB, 0, st>>>(w.w, vj, j > 0 ? vj - n : vj, n, w.lz, j);
+        for (int pass = 0; pass < 2; ++pass) {
+            ReduceArgs a2{w.V, n, j + 1, w.w, n, w.partials, w.counter};
+            k_multidot<0><<<g, RB, 0, st>>>(a2, w.lz, j, w.c);
+            k_multiaxpy<<<g, RB, 0, st>>>(w.w, w.V, n, j + 1, w.c, n, w.lz, 1, 0);
+        }
+        ReduceArgs a3{nullptr, n, 0, w.w, n, w.partials, w.counter};
+        k_multidot<2><<<g, RB, 0, st>>>(a3, w.lz, j, nullptr);
+        if (j + 1 < K) k_next_vec<<<g, RB, 0, st>>>(w.V + (size_t)n * (j + 1), w.w, n, w.lz, j);
+        DMRG_CUDA(cudaGetLastError());
+    }
+    k_tridiag_lowest<<<1, 1, 0, st>>>(w.lz, ctx->d_status);
+    // theta = V y0 (only the first m vectors carry weight: y is zero beyond m)
+    {
+        // copy y to the coefficient buffer (device to device)
+        DMRG_CUDA(cudaMemcpyAsync(w.c, w.lz->y, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
+        k_multiaxpy<<<g, RB, 0, st>>>(theta, w.V, n, -1, w.c, n, w.lz, 0, 1);
+        ReduceArgs a4{nullptr, n, 0, theta, n, w.partials, w.counter};
+        k_multidot<3><<<g, RB, 0, st>>>(a4, w.lz, 0, nullptr);
+        k_scale_by<<<g, RB, 0, st>>>(theta, theta, n, w.lz);
+    }
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
+}  // namespace dmrg

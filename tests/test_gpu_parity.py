@@ -1,0 +1,277 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64
+oracle on the same seeded inputs.
+
+Tolerances (FP64 path):
+  * singular values: |s - s_ref| <= 1e-10 s_ref + 8 n eps s_1 (Weyl bound for
+    the rounding of the input, see the design notes); reconstruction and
+    orthogonality at 1e-13 relative;
+  * contractions: elementwise 1e-12 relative to max |y_ref|;
+  * energies: 1e-10 per site; integer controller output: bit-exact on replay.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+EPS = np.finfo(float).eps
+
+
+@pytest.fixture(scope="module")
+def G():
+    import paper_2604_03960_gb300 as G
+    G.lib()
+    return G
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    c = G.Context(0)
+    yield c
+    c.close()
+
+
+def dev(x, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0", dtype)
+
+
+# ---------------------------------------------------------------------------
+# SVD + entropy + truncation
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["exp", "pow"])
+@pytest.mark.parametrize("chi", [4, 17, 32, 64, 128])
+def test_svd_exact_spectrum(ctx, kind, chi):
+    n = 2 * chi
+    s_ref = synth.spectrum(kind, n, chi)
+    A = synth.svd_test_matrix(synth.workload_seed(1, chi), n, n, s_ref)
+    U, s, Vt, k, S, err = ctx.svd_truncate(dev(A), chi, 1e-10)
+    U, s, Vt = (x.cpu().numpy() for x in (U, s, Vt))
+    assert np.all(np.abs(s - s_ref) <= 1e-10 * s_ref + 8 * n * EPS * s_ref[0])
+    assert np.linalg.norm(U * s @ Vt - A) <= 1e-13 * np.linalg.norm(A)
+    assert np.abs(U.T @ U - np.eye(n)).max() <= 1e-13
+    assert np.abs(Vt @ Vt.T - np.eye(n)).max() <= 1e-13
+    S_ref, eps_ref = O.entropy(s_ref)
+    assert abs(S - S_ref) <= 1e-12
+    k_ref = O.trunc_k(s_ref, chi, 1e-10, multiplet_guard=0)
+    assert k == k_ref
+    assert abs(err - eps_ref[k]) <= 1e-12
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (1, 7), (7, 1), (3, 5), (40, 24), (24, 40), (130, 66), (66, 258)])
+def test_svd_rectangular_vs_oracle(ctx, m, n):
+    rng = np.random.default_rng(m * 1000 + n)
+    A = rng.standard_normal((m, n))
+    U, s, Vt, k, S, err = ctx.svd_truncate(dev(A), min(m, n), 0.0)
+    U, s, Vt = (x.cpu().numpy() for x in (U, s, Vt))
+    _, s_ref, _ = O.svd(A)
+    assert np.allclose(s, s_ref, rtol=1e-12, atol=1e-13 * s_ref[0])
+    assert np.linalg.norm(U * s @ Vt - A) <= 1e-13 * np.linalg.norm(A)
+    r = min(m, n)
+    assert np.abs(U.T @ U - np.eye(r)).max() <= 1e-13
+    assert np.abs(Vt @ Vt.T - np.eye(r)).max() <= 1e-13
+    # same sign convention as the oracle: projectors agree column by column
+    Ur, sr, Vtr = O.svd(A)
+    for j in range(r):
+        if j + 1 < r and abs(sr[j] - sr[j + 1]) < 1e-8 * sr[0]:
+            continue
+        if j > 0 and abs(sr[j] - sr[j - 1]) < 1e-8 * sr[0]:
+            continue
+        assert np.allclose(U[:, j], Ur[:, j], atol=1e-10)
+
+
+def test_svd_rank_deficient_and_zero(ctx):
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((30, 3)) @ rng.standard_normal((3, 20))
+    U, s, Vt, k, S, err = ctx.svd_truncate(dev(A), 20, 1e-10)
+    s = s.cpu().numpy()
+    assert k == 3
+    assert np.allclose(s[:3], np.linalg.svd(A, compute_uv=False)[:3], rtol=1e-12)
+    assert np.all(s[3:] <= 1e-12 * s[0])
+    # truncation to chi_max = 1 and the eps rule
+    U, s, Vt, k, S, err = ctx.svd_truncate(dev(A), 1, 1e-10)
+    assert k == 1
+    sv = np.linalg.svd(A, compute_uv=False)
+    assert abs(err - np.sqrt(np.sum(sv[1:] ** 2) / np.sum(sv ** 2))) < 1e-12
+
+
+def test_entropy_kernel(ctx):
+    rng = np.random.default_rng(2)
+    for s in [np.array([1.0, 0.0, 0.0]), np.full(7, 0.3), np.sort(rng.random(300))[::-1]]:
+        S, eps = ctx.entropy(dev(s))
+        S_ref, eps_ref = O.entropy(s)
+        assert abs(S.item() - S_ref) <= 1e-13
+        assert np.allclose(eps.cpu().numpy(), eps_ref, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# controller: bit-exact replay
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", ["plain", "second_order", "init_zero"])
+def test_controller_replay_bit_exact(G, ctx, mode, variant):
+    rng = np.random.default_rng(100 + mode)
+    T, B = 40, 63
+    S_seq = np.cumsum(rng.normal(0.05, 0.3, (T, B)), axis=0) + 1.0
+    S_seq = np.abs(S_seq)
+    kw = dict(chi_max=512, chi_min=4, ctrl=mode, S_target=1.2, alpha_ema=0.3, beta=0.4)
+    if variant == "second_order":
+        kw["second_order"] = 1
+    if variant == "init_zero":
+        kw["ema_init_zero"] = 1
+    p_ref = O.make_params(**kw)
+    chi_ref, st_ref = O.ctrl_replay(S_seq, p_ref)
+    p = G.make_params(**kw)
+    states = torch.zeros(B * G.CTRL_STATE_BYTES, dtype=torch.uint8, device="cuda:0")
+    # chi = chi_min initially (Section 10), everything else zero
+    host = (G.CtrlState * B)()
+    for i in range(B):
+        host[i].chi = p.chi_min
+    states.copy_(torch.frombuffer(bytearray(host), dtype=torch.uint8))
+    chi = torch.empty(B, dtype=torch.int32, device="cuda:0")
+    out = np.zeros((T, B), dtype=np.int32)
+    for t in range(T):
+        ctx.entropy_pid_step(dev(S_seq[t]), states, p, chi)
+        out[t] = chi.cpu().numpy()
+    assert np.array_equal(out, chi_ref)
+    # the floating-point state matches bit for bit too
+    back = (G.CtrlState * B).from_buffer_copy(states.cpu().numpy().tobytes())
+    for i in range(B):
+        assert back[i].I == st_ref[i].I and back[i].Sbar == st_ref[i].Sbar and back[i].e_prev == st_ref[i].e_prev
+
+
+# ---------------------------------------------------------------------------
+# contractions
+# ---------------------------------------------------------------------------
+def random_env(rng, D, c):
+    E = rng.standard_normal((D, c, c))
+    return E
+
+
+@pytest.mark.parametrize("model,D", [(O.MODEL_XXZ, 5), (O.MODEL_J1J2, 8), (O.MODEL_TFIM, 3)])
+@pytest.mark.parametrize("cl,cr", [(1, 2), (7, 13), (37, 70), (96, 64), (130, 129)])
+def test_heff_apply_fp64(ctx, model, D, cl, cr):
+    rng = np.random.default_rng(cl * 31 + cr + D)
+    W = O.mpo(model, 4, 1.0, 0.8, 0.3)
+    L, R = random_env(rng, D, cl), random_env(rng, D, cr)
+    th = rng.standard_normal((cl, 2, 2, cr))
+    y_ref = O.heff_apply(L, W[1], W[2], R, th)
+    y = ctx.heff_apply(dev(L), dev(W[1]), dev(W[2]), dev(R), dev(th)).cpu().numpy()
+    assert np.max(np.abs(y - y_ref)) <= 1e-12 * np.max(np.abs(y_ref))
+
+
+@pytest.mark.parametrize("cl,ck", [(1, 2), (9, 15), (64, 100), (129, 70)])
+def test_env_updates_fp64(ctx, cl, ck):
+    rng = np.random.default_rng(cl + 7 * ck)
+    D = 5
+    W = O.mpo(O.MODEL_XXZ, 3, 1.0, 1.3)
+    L = random_env(rng, D, cl)
+    A = rng.standard_normal((cl, 2, ck))
+    ref = O.env_left(L, W[1], A)
+    got = ctx.env_left(dev(L), dev(W[1]), dev(A)).cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    R = random_env(rng, D, cl)
+    B = rng.standard_normal((ck, 2, cl))
+    ref = O.env_right(R, W[1], B)
+    got = ctx.env_right(dev(R), dev(W[1]), dev(B)).cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def canonical_envs(rng, N, k, chi, model=O.MODEL_XXZ):
+    """Environments of a random canonical MPS around bond k (built by the oracle)."""
+    W = O.mpo(model, N, 1.0, 1.0, 0.24)
+    D = W.shape[1]
+    dims = [min(chi, 2 ** i, 2 ** (N - i)) for i in range(N + 1)]
+    L = np.zeros((D, 1, 1)); L[-1] = 1.0
+    for i in range(k):
+        Q, _ = np.linalg.qr(rng.standard_normal((dims[i] * 2, dims[i + 1])))
+        L = O.env_left(L, W[i], Q.reshape(dims[i], 2, dims[i + 1]))
+    R = np.zeros((D, 1, 1)); R[0] = 1.0
+    for i in range(N - 1, k + 1, -1):
+        Q, _ = np.linalg.qr(rng.standard_normal((2 * dims[i + 1], dims[i])))
+        R = O.env_right(R, W[i], Q.T.reshape(dims[i], 2, dims[i + 1]))
+    return W, L, R
+
+
+@pytest.mark.parametrize("N,k,chi", [(8, 3, 8), (12, 5, 24), (14, 6, 48)])
+def test_lanczos_fp64(ctx, N, k, chi):
+    rng = np.random.default_rng(N * 100 + chi)
+    W, L, R = canonical_envs(rng, N, k, chi)
+    cl, cr = L.shape[1], R.shape[1]
+    th = rng.standard_normal((cl, 2, 2, cr))
+    E_ref, th_ref, steps_ref, _, _ = O.lanczos(L, W[k], W[k + 1], R, th, K=20)
+    E, th_g, steps = ctx.lanczos(dev(L), dev(W[k]), dev(W[k + 1]), dev(R), dev(th), K=20)
+    assert steps == steps_ref
+    assert abs(E - E_ref) <= 1e-11 * max(1.0, abs(E_ref))
+    ov = abs(np.dot(th_g.cpu().numpy().ravel(), th_ref.ravel()))
+    assert abs(ov - 1.0) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# full sweeps against the oracle and exact diagonalisation (N = 16, d = 2, D = 5)
+# ---------------------------------------------------------------------------
+def run_pair(G, ctx, N, sweeps, model=O.MODEL_XXZ, J=1.0, Delta=1.0, J2=0.0, **kw):
+    p_ref = O.make_params(**kw)
+    W_ref = O.mpo(model, N, J, Delta, J2)
+    m0 = synth.initial_mps_entries(synth.workload_seed(0, 0), N, p_ref.chi_init)
+    ref = O.dmrg_run(W_ref, m0, p_ref, sweeps)
+    p = G.make_params(**kw)
+    W = ctx.build_mpo(model, N, J, Delta, J2)
+    assert np.array_equal(W.cpu().numpy(), W_ref)
+    st = G.State(ctx, W, dev(m0), p, J, Delta, J2)
+    recs, vis = st.sweep(sweeps)
+    st.close()
+    return ref, recs, vis
+
+
+def near_tie_mask(ref, vis_k):
+    return np.zeros(len(vis_k), dtype=bool)
+
+
+@pytest.mark.parametrize("ctrl,chi_max", [(3, 256), (0, 32), (2, 32)])
+def test_dmrg_sweeps_match_oracle_N16(G, ctx, ctrl, chi_max):
+    N = 16
+    ref, recs, vis = run_pair(G, ctx, N, 4, ctrl=ctrl, chi_max=chi_max)
+    E = np.array([r.E for r in recs])
+    assert np.all(np.abs(E - ref["E"]) / N <= 1e-10)
+    k = np.array([v.k for v in vis])
+    chi = np.array([v.chi_ctrl for v in vis])
+    S = np.array([v.S for v in vis])
+    assert np.array_equal(k, ref["k"])
+    assert np.array_equal(chi, ref["chi"])
+    assert np.max(np.abs(S - ref["S"])) <= 1e-9
+    if ctrl == 3 and chi_max == 256:
+        E0 = O.ed_ground(O.MODEL_XXZ, N)
+        assert abs(E[-1] - E0) / N <= 1e-10
+
+
+def test_dmrg_j1j2_majumdar_ghosh(G, ctx):
+    N = 12
+    ref, recs, vis = run_pair(G, ctx, N, 3, model=O.MODEL_J1J2, J2=0.5, ctrl=3, chi_max=16)
+    assert abs(recs[-1].E + 3 * N / 8) <= 1e-10
+    assert abs(recs[-1].E - ref["E"][-1]) <= 1e-10
+
+
+# ---------------------------------------------------------------------------
+# learned scheduler kernels
+# ---------------------------------------------------------------------------
+def test_mlp_forward_grad_adam(G, ctx):
+    rng = np.random.default_rng(12)
+    P = (rng.standard_normal(G.MLP_NPARAM) * 0.2).astype(np.float32)
+    X = rng.standard_normal((37, 10)).astype(np.float32)
+    t = rng.standard_normal(37).astype(np.float32)
+    y = ctx.mlp_forward(dev(P, torch.float32), dev(X, torch.float32)).cpu().numpy()
+    y_ref = O.mlp_forward(P.astype(np.float64), X.astype(np.float64))
+    assert np.allclose(y, y_ref, rtol=1e-4, atol=1e-5)
+    loss, g = ctx.mlp_loss_grad(dev(P, torch.float32), dev(X, torch.float32), dev(t, torch.float32))
+    L_ref, g_ref = O.mlp_loss_grad(P.astype(np.float64), X.astype(np.float64), t.astype(np.float64))
+    assert abs(loss.item() - L_ref) <= 1e-4 * max(1.0, L_ref)
+    g = g.cpu().numpy()
+    assert np.max(np.abs(g - g_ref)) <= 1e-4 * max(1.0, np.max(np.abs(g_ref)))
+    m = torch.zeros(G.MLP_NPARAM, device="cuda:0"); v = torch.zeros(G.MLP_NPARAM, device="cuda:0")
+    Pd = dev(P, torch.float32)
+    ctx.mlp_adam(Pd, dev(g_ref, torch.float32), m, v, 1, lr=1e-3)
+    Pr = P.astype(np.float64).copy(); mr = np.zeros_like(Pr); vr = np.zeros_like(Pr)
+    O.adam_step(Pr, g_ref.copy(), mr, vr, 1, lr=1e-3)
+    assert np.allclose(Pd.cpu().numpy(), Pr, atol=1e-6)
