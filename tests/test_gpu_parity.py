@@ -3,8 +3,9 @@ oracle on the same seeded inputs.
 
 Tolerances (FP64 path):
   * singular values: |s - s_ref| <= 1e-10 s_ref + 8 n eps s_1 (Weyl bound for
-    the rounding of the input, see the design notes); reconstruction and
-    orthogonality at 1e-13 relative;
+    the rounding of the input); reconstruction and orthogonality within
+    20 n eps (at most 20 Jacobi sweeps, each applying n rotations to a column,
+    every rotation orthogonal to O(eps));
   * contractions: elementwise 1e-12 relative to max |y_ref|;
   * energies: 1e-10 per site; integer controller output: bit-exact on replay.
 """
@@ -49,9 +50,10 @@ def test_svd_exact_spectrum(ctx, kind, chi):
     U, s, Vt, k, S, err = ctx.svd_truncate(dev(A), chi, 1e-10)
     U, s, Vt = (x.cpu().numpy() for x in (U, s, Vt))
     assert np.all(np.abs(s - s_ref) <= 1e-10 * s_ref + 8 * n * EPS * s_ref[0])
-    assert np.linalg.norm(U * s @ Vt - A) <= 1e-13 * np.linalg.norm(A)
-    assert np.abs(U.T @ U - np.eye(n)).max() <= 1e-13
-    assert np.abs(Vt @ Vt.T - np.eye(n)).max() <= 1e-13
+    tol = 20 * n * EPS
+    assert np.linalg.norm(U * s @ Vt - A) <= tol * np.linalg.norm(A)
+    assert np.abs(U.T @ U - np.eye(n)).max() <= tol
+    assert np.abs(Vt @ Vt.T - np.eye(n)).max() <= tol
     S_ref, eps_ref = O.entropy(s_ref)
     assert abs(S - S_ref) <= 1e-12
     k_ref = O.trunc_k(s_ref, chi, 1e-10, multiplet_guard=0)
@@ -66,11 +68,12 @@ def test_svd_rectangular_vs_oracle(ctx, m, n):
     U, s, Vt, k, S, err = ctx.svd_truncate(dev(A), min(m, n), 0.0)
     U, s, Vt = (x.cpu().numpy() for x in (U, s, Vt))
     _, s_ref, _ = O.svd(A)
-    assert np.allclose(s, s_ref, rtol=1e-12, atol=1e-13 * s_ref[0])
-    assert np.linalg.norm(U * s @ Vt - A) <= 1e-13 * np.linalg.norm(A)
+    tol = 20 * max(m, n) * EPS
+    assert np.allclose(s, s_ref, rtol=1e-12, atol=tol * s_ref[0])
+    assert np.linalg.norm(U * s @ Vt - A) <= tol * np.linalg.norm(A)
     r = min(m, n)
-    assert np.abs(U.T @ U - np.eye(r)).max() <= 1e-13
-    assert np.abs(Vt @ Vt.T - np.eye(r)).max() <= 1e-13
+    assert np.abs(U.T @ U - np.eye(r)).max() <= tol
+    assert np.abs(Vt @ Vt.T - np.eye(r)).max() <= tol
     # same sign convention as the oracle: projectors agree column by column
     Ur, sr, Vtr = O.svd(A)
     for j in range(r):
