@@ -140,6 +140,13 @@ void dmrg_destroy(dmrg_ctx *ctx);
  * call (then cleared).  Synchronises the stream. */
 dmrg_status dmrg_get_status(dmrg_ctx *ctx);
 const char *dmrg_status_string(dmrg_status s);
+/* Tuning knobs of a context (no counterpart in the paper): "tc_force" (1: use
+ * the tensor cores even for tiny products), "tc_min_work" (multiply-adds
+ * below which 3xTF32 requests run on the FP64 kernel), "tc_bn" (0, 128 or
+ * 256: tile width of the tensor-core GEMM, 0 = heuristic),
+ * "jacobi_max_sweeps" (standalone svd_truncate).  DMRG_EINVAL for an
+ * unknown name or value. */
+dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value);
 /* Bond dimension D of the MPO of `model` (5, 8, 3), or -1. */
 int dmrg_mpo_dim(int model);
 
@@ -231,6 +238,14 @@ dmrg_status dmrg_lanczos(dmrg_ctx *ctx, int prec, int D, int cl, int cr, const d
                          const double *W1_dev, const double *W2_dev, const double *R_dev,
                          double *theta_dev, int K, double *E_out, int *steps_out);
 
+/* C (M x N) = A (M x K) B (K x N), all row-major FP64 device buffers, in
+ * precision `prec`; the contraction engine behind every step above.  With
+ * prec = DMRG_PREC_3XTF32 each operand is split into two TF32 parts and the
+ * product runs on the tcgen05 tensor cores with FP32 accumulation; products
+ * smaller than 2^22 multiply-adds use the FP64 kernel unless force_tc != 0. */
+dmrg_status dmrg_gemm(dmrg_ctx *ctx, int prec, int force_tc, int M, int N, int K, const double *A_dev,
+                      const double *B_dev, double *C_dev);
+
 /* Accessors of a state (device buffers owned by the state; valid until the
  * next call that modifies it). */
 dmrg_status dmrg_state_chi(dmrg_state *st, int *chi_host /* N+1 */);
@@ -239,6 +254,25 @@ dmrg_status dmrg_state_site(dmrg_state *st, int i, const double **A_dev);
  * caller's buffer E_out_dev (D x chi_k x chi_k); synchronises the stream. */
 dmrg_status dmrg_state_env(dmrg_state *st, int left, int k, double *E_out_dev);
 dmrg_status dmrg_state_ctrl(dmrg_state *st, dmrg_ctrl_state **ctrl_dev /* N-1 */);
+/* Checkpoint / restore of the MPS (no counterpart in the paper): the site
+ * tensors at the current bond dimensions, concatenated site after site
+ * (sum_i chi_i * 2 * chi_{i+1} doubles, see dmrg_state_mps_size).  `out` /
+ * `in` may be host (pageable or pinned) or device memory.  put_mps requires
+ * the same bond dimensions and gauge as the matching get_mps (environments
+ * are kept); both synchronise the stream. */
+long long dmrg_state_mps_size(dmrg_state *st);
+dmrg_status dmrg_state_get_mps(dmrg_state *st, double *out);
+dmrg_status dmrg_state_put_mps(dmrg_state *st, const double *in);
+/* Kernels launched by this library since it was loaded (all contexts). */
+long long dmrg_launch_count(void);
+/* Live timing of the heavy kernels (no counterpart in the paper): with
+ * profiling on, CUDA events on the context stream bracket every launch of
+ * kind 0 (tensor-core GEMM), 1 (FP32 Jacobi sweeps), 2 (FP64 Jacobi sweeps),
+ * 3 (FP64 GEMM).  dmrg_profile(ctx, on) resets the counters;
+ * dmrg_profile_read returns the summed device time (ms), the launches and
+ * their algorithmic flops and bytes. */
+dmrg_status dmrg_profile(dmrg_ctx *ctx, int on);
+dmrg_status dmrg_profile_read(dmrg_ctx *ctx, int kind, double *ms, long long *launches, double *flops, double *bytes);
 /* Set the learned scheduler's parameters (4929 FP32 values, layout of
  * dmrg_mlp_forward) used when ctrl == DMRG_CTRL_MLP. */
 dmrg_status dmrg_state_set_mlp(dmrg_state *st, const float *params_dev);

@@ -106,6 +106,14 @@ def _declare(L):
         "dmrg_mlp_forward": (S, [_VP, _VP, _I, _VP, _VP]),
         "dmrg_mlp_loss_grad": (S, [_VP, _VP, _I, _VP, _VP, _VP, _VP]),
         "dmrg_mlp_adam": (S, [_VP, _I, _VP, _VP, _VP, _VP, _I, C.c_float, C.c_float, C.c_float, C.c_float]),
+        "dmrg_gemm": (S, [_VP, _I, _I, _I, _I, _I, _VP, _VP, _VP]),
+        "dmrg_set_option": (S, [_VP, C.c_char_p, _D]),
+        "dmrg_state_mps_size": (C.c_longlong, [_VP]),
+        "dmrg_state_get_mps": (S, [_VP, _VP]),
+        "dmrg_state_put_mps": (S, [_VP, _VP]),
+        "dmrg_launch_count": (C.c_longlong, []),
+        "dmrg_profile": (S, [_VP, _I]),
+        "dmrg_profile_read": (S, [_VP, _I, C.POINTER(_D), C.POINTER(C.c_longlong), C.POINTER(_D), C.POINTER(_D)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -133,7 +141,9 @@ def exported_symbols():
         "dmrg_state_create", "dmrg_state_destroy", "dmrg_sweep", "bond_update", "svd_truncate", "entropy_pid_step",
         "dmrg_entropy", "dmrg_heff_apply", "dmrg_env_left", "dmrg_env_right", "dmrg_lanczos", "dmrg_state_chi",
         "dmrg_state_site", "dmrg_state_env", "dmrg_state_ctrl", "dmrg_state_set_mlp", "dmrg_mlp_forward",
-        "dmrg_mlp_loss_grad", "dmrg_mlp_adam",
+        "dmrg_mlp_loss_grad", "dmrg_mlp_adam", "dmrg_gemm", "dmrg_set_option",
+        "dmrg_state_mps_size", "dmrg_state_get_mps", "dmrg_state_put_mps", "dmrg_launch_count",
+        "dmrg_profile", "dmrg_profile_read",
     ]
 
 
@@ -193,6 +203,18 @@ class Context:
 
     def status(self):
         _check(lib().dmrg_get_status(self.h), "device status")
+
+    def profile(self, on: bool):
+        _check(lib().dmrg_profile(self.h, int(on)), "dmrg_profile")
+
+    def profile_read(self, kind: int):
+        ms = C.c_double(); n = C.c_longlong(); fl = C.c_double(); by = C.c_double()
+        _check(lib().dmrg_profile_read(self.h, kind, C.byref(ms), C.byref(n), C.byref(fl), C.byref(by)),
+               "dmrg_profile_read")
+        return dict(ms=ms.value, launches=n.value, flops=fl.value, bytes=by.value)
+
+    def set_option(self, name: str, value: float):
+        _check(lib().dmrg_set_option(self.h, name.encode(), float(value)), f"dmrg_set_option({name})")
 
     # --- hot-path entry points ------------------------------------------------
     def build_mpo(self, model: int, N: int, J=1.0, Delta=1.0, J2=0.0) -> torch.Tensor:
@@ -257,6 +279,13 @@ class Context:
         _check(lib().dmrg_lanczos(self.h, prec, D, cl, cr, _ptr(L), _ptr(W1), _ptr(W2), _ptr(R), _ptr(th), K,
                                   C.byref(E), C.byref(steps)), "dmrg_lanczos")
         return E.value, th, steps.value
+
+    def gemm(self, A: torch.Tensor, B: torch.Tensor, prec=PREC_FP64, force_tc=False) -> torch.Tensor:
+        M, K = A.shape
+        N = B.shape[1]
+        Cm = torch.empty((M, N), dtype=torch.float64, device=A.device)
+        _check(lib().dmrg_gemm(self.h, prec, int(force_tc), M, N, K, _ptr(A), _ptr(B), _ptr(Cm)), "dmrg_gemm")
+        return Cm
 
     # --- learned scheduler ------------------------------------------------------
     def mlp_forward(self, P: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
@@ -334,8 +363,23 @@ class State:
         torch.cuda.synchronize(self.ctx.device)
         return torch.as_tensor(_DevView(p.value, shape), device=f"cuda:{self.ctx.device}").clone()
 
+    def mps_size(self) -> int:
+        return int(lib().dmrg_state_mps_size(self.h))
+
+    def get_mps(self, out: torch.Tensor):
+        """Copy all site tensors into `out` (host or device, float64, mps_size() values)."""
+        _check(lib().dmrg_state_get_mps(self.h, C.c_void_p(out.data_ptr())), "dmrg_state_get_mps")
+
+    def put_mps(self, src: torch.Tensor):
+        _check(lib().dmrg_state_put_mps(self.h, C.c_void_p(src.data_ptr())), "dmrg_state_put_mps")
+
     def set_mlp(self, P: torch.Tensor | None):
         _check(lib().dmrg_state_set_mlp(self.h, _ptr(P) if P is not None else None), "dmrg_state_set_mlp")
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far (all contexts)."""
+    return int(lib().dmrg_launch_count())
 
 
 class _DevView:

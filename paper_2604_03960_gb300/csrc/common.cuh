@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -10,6 +11,10 @@
 #include "../../include/dmrg.h"
 
 namespace dmrg {
+
+// Number of kernels this library has launched (reported by dmrg_launch_count).
+extern std::atomic<long long> g_launch_count;
+#define DMRG_COUNT_LAUNCH() (::dmrg::g_launch_count.fetch_add(1, std::memory_order_relaxed))
 
 // Device status bits, OR-ed into ctx->d_status by kernels.
 enum : int {
@@ -75,6 +80,18 @@ SvdWork svd_work_carve(void *base, int r, int l);
 
 }  // namespace dmrg
 
+namespace dmrg {
+// Live per-kernel timing (CUDA events on the context stream), enabled by
+// dmrg_profile; used for the roofline of the dominant kernel.
+enum ProfKind { PROF_TC_GEMM = 0, PROF_JACOBI32 = 1, PROF_JACOBI64 = 2, PROF_F64_GEMM = 3, PROF_KINDS = 4 };
+struct ProfSlot {
+    std::vector<cudaEvent_t> ev;
+    size_t used = 0;
+    long long n = 0;
+    double flops = 0.0, bytes = 0.0;
+};
+}  // namespace dmrg
+
 struct dmrg_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -87,7 +104,37 @@ struct dmrg_ctx {
     dmrg::DevBuf work3;
     int jacobi_max_sweeps = 60;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // tensor-core GEMM path
+    dmrg::DevBuf tcbuf;          // split TF32 operands
+    int tc_ok = -1;              // -1 unknown, 0 no, 1 yes
+    int tc_bn_override = 0;      // force a tile width (autotuner / tests)
+    int tc_force = 0;            // use the tensor cores even for tiny products
+    double tc_min_work = 4194304.0;   // M*N*K below which the FP64 kernel is used
+    int prof = 0;
+    dmrg::ProfSlot prof_slot[dmrg::PROF_KINDS];
 };
+
+namespace dmrg {
+inline void prof_mark(dmrg_ctx *ctx, int kind)
+{
+    if (!ctx || !ctx->prof) return;
+    ProfSlot &p = ctx->prof_slot[kind];
+    if (p.used == p.ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        p.ev.push_back(e);
+    }
+    cudaEventRecord(p.ev[p.used++], ctx->stream);
+}
+inline void prof_count(dmrg_ctx *ctx, int kind, double flops, double bytes)
+{
+    if (!ctx || !ctx->prof) return;
+    ProfSlot &p = ctx->prof_slot[kind];
+    p.n++;
+    p.flops += flops;
+    p.bytes += bytes;
+}
+}  // namespace dmrg
 
 namespace dmrg {
 
@@ -183,6 +230,14 @@ dmrg_status gemm(dmrg_ctx *ctx, int prec, int M, int N, int K, double alpha, con
 // to d_info[0] (sweeps, negative if not converged).
 dmrg_status svd_jacobi(dmrg_ctx *ctx, const double *A, int m, int n, double *U, double *s, double *Vt,
                        void *work, int max_sweeps, int *d_info);
+
+// FP32 one-sided Jacobi (mixed-precision form), vectors = columns (dir 0) or
+// rows (dir 1) of A; see jacobi.cu.
+size_t jac32_work_bytes(int r, int l);
+dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, void *work, int max_sweeps,
+                         int *d_info, double *s_sorted, float **X_out, double **nrm_out, int **perm_out);
+dmrg_status gather_unit_vectors(dmrg_ctx *ctx, const float *X, const double *nrm, const int *perm, const int *kdev,
+                                int kmax, int l, double *Q);
 
 // Lanczos on the effective Hamiltonian (see lanczos.cu).
 struct HeffOp;  // defined in dmrg_core.cu

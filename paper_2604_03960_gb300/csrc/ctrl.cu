@@ -77,7 +77,8 @@ __device__ int trunc_k_dev(const double *s, int r, int chi, int rank, int above,
 __global__ void __launch_bounds__(DB) k_decide(const double *__restrict__ s, int r, dmrg_ctrl_state *st,
                                                dmrg_params p, int do_ctrl, int chi_override, const float *mlp,
                                                int bond, int N, int sweep, const LzState *lz, BondResult *res,
-                                               dmrg_visit_record *visit, int direction, int *status)
+                                               dmrg_visit_record *visit, int direction, double rank_floor,
+                                               int *status)
 {
     __shared__ double sh[32];
     __shared__ float h1[MLP_H], h2[MLP_H], xin[MLP_IN], red[2];
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(DB) k_decide(const double *__restrict__ s, int
     const double S = block_sum_neum(en, sh);
     // 3. numerical rank and the count above the threshold on the normalised spectrum
     const double nz = sqrt(Z);
-    const double rank_tol = (double)r * 2.220446049250313e-16 * (r > 0 ? s[0] : 0.0);
+    const double rank_tol = rank_floor * (r > 0 ? s[0] : 0.0);
     double cr = 0.0, ca = 0.0;
     for (int j = t; j < r; j += DB) {
         if (s[j] > rank_tol) cr += 1.0;
@@ -202,7 +203,6 @@ __global__ void k_ctrl_steps(int n, const double *__restrict__ S, dmrg_ctrl_stat
 __global__ void k_entropy(int n, const double *__restrict__ s, double *S_out, double *eps)
 {
     __shared__ double sh[32];
-    __shared__ double Zs;
     Neum z;
     for (int j = threadIdx.x; j < n; j += blockDim.x) z.add(s[j] * s[j]);
     const double Z = block_sum_neum(z, sh);
@@ -215,7 +215,6 @@ __global__ void k_entropy(int n, const double *__restrict__ s, double *S_out, do
     const double S = block_sum_neum(en, sh);
     if (threadIdx.x == 0) {
         S_out[0] = S;
-        Zs = Z;
         if (eps) {
             Neum tail;
             eps[n] = 0.0;
@@ -231,11 +230,12 @@ __global__ void k_entropy(int n, const double *__restrict__ s, double *S_out, do
 
 dmrg_status launch_decide(dmrg_ctx *ctx, const double *s, int r, dmrg_ctrl_state *st_bond, const dmrg_params &p,
                           int do_ctrl, int chi_override, const float *mlp, int bond, int N, int sweep,
-                          const void *lz_state, BondResult *res, dmrg_visit_record *visit, int direction)
+                          const void *lz_state, BondResult *res, dmrg_visit_record *visit, int direction,
+                          double rank_floor)
 {
     k_decide<<<1, DB, 0, ctx->stream>>>(s, r, st_bond, p, do_ctrl, chi_override, mlp, bond, N, sweep,
-                                        static_cast<const LzState *>(lz_state), res, visit, direction,
-                                        ctx->d_status);
+                                        static_cast<const LzState *>(lz_state), res, visit, direction, rank_floor,
+                                        ctx->d_status); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }
@@ -244,7 +244,7 @@ dmrg_status launch_ctrl_steps(dmrg_ctx *ctx, int n, const double *S, dmrg_ctrl_s
                               int *chi_out)
 {
     if (n <= 0) return DMRG_OK;
-    k_ctrl_steps<<<(n + 127) / 128, 128, 0, ctx->stream>>>(n, S, st, p, chi_out);
+    k_ctrl_steps<<<(n + 127) / 128, 128, 0, ctx->stream>>>(n, S, st, p, chi_out); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }
@@ -252,7 +252,7 @@ dmrg_status launch_ctrl_steps(dmrg_ctx *ctx, int n, const double *S, dmrg_ctrl_s
 dmrg_status launch_entropy(dmrg_ctx *ctx, int n, const double *s, double *S, double *eps)
 {
     if (n <= 0) return DMRG_EINVAL;
-    k_entropy<<<1, 256, 0, ctx->stream>>>(n, s, S, eps);
+    k_entropy<<<1, 256, 0, ctx->stream>>>(n, s, S, eps); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }

@@ -27,6 +27,9 @@ namespace dmrg {
 namespace {
 
 constexpr int kMaxCh = 32;   // max channels of a mix (4 D for D <= 8)
+// singular values below 2^-17 s_0 are not resolved by the FP32 Jacobi of the
+// mixed form and count as zero there
+constexpr double kMixedRankFloor = 7.62939453125e-06;
 
 // ---------------------------------------------------------------------------
 // MPO (Eq. 18 generalised; lower-triangular, left boundary row D-1, right
@@ -219,6 +222,47 @@ __global__ void k_boundary_env(double *E, int D, int w)
     if (i < D) E[i] = (i == w) ? 1.0 : 0.0;
 }
 
+// out (C x R) = in (R x C)^T
+__global__ void k_transpose_rect(const double *__restrict__ in, double *__restrict__ out, int R, int C)
+{
+    __shared__ double t[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        int r = r0 + y, c = c0 + threadIdx.x;
+        t[y][threadIdx.x] = (r < R && c < C) ? in[(size_t)r * C + c] : 0.0;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        int c = c0 + y, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[(size_t)c * R + r] = t[threadIdx.x][y];
+    }
+}
+
+// two-pass deterministic normalisation of a vector to unit 2-norm
+constexpr int kNormBlocks = 256;
+__global__ void k_sumsq_partial(const double *__restrict__ x, long long n, double *__restrict__ part)
+{
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a = fma(x[i], x[i], a);
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
+__global__ void k_scale_partials(double *__restrict__ x, long long n, const double *__restrict__ part, int nparts)
+{
+    __shared__ double inv;
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int b = 0; b < nparts; ++b) a += part[b];
+        inv = (a > 0.0) ? 1.0 / sqrt(a) : 0.0;
+    }
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] *= inv;
+}
+
 int grid1d(long long n, int threads, int num_sms)
 {
     long long b = (n + threads - 1) / threads;
@@ -238,7 +282,7 @@ size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 static dmrg_status mix(dmrg_ctx *ctx, const double *in, double *out, const double *C, const MixDesc &d)
 {
     long long total = (long long)d.An * d.Bn;
-    k_mix<<<grid1d(total, 256, ctx->num_sms), 256, 0, ctx->stream>>>(in, out, C, d);
+    k_mix<<<grid1d(total, 256, ctx->num_sms), 256, 0, ctx->stream>>>(in, out, C, d); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }
@@ -294,10 +338,18 @@ dmrg_status env_right_dev(dmrg_ctx *ctx, int prec, int D, int ck, int cr, const 
     return DMRG_OK;
 }
 
+static dmrg_status normalise(dmrg_ctx *ctx, double *x, long long n, double *part)
+{
+    k_sumsq_partial<<<kNormBlocks, 256, 0, ctx->stream>>>(x, n, part); DMRG_COUNT_LAUNCH();
+    k_scale_partials<<<grid1d(n, 256, ctx->num_sms), 256, 0, ctx->stream>>>(x, n, part, kNormBlocks); DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
 static dmrg_status build_coef(dmrg_ctx *ctx, int kind, int D, const double *W1, const double *W2, double *C)
 {
     int nch = (kind == 0) ? 4 * D : 2 * D;
-    k_build_coef<<<(nch * nch + 255) / 256, 256, 0, ctx->stream>>>(kind, D, W1, W2, C);
+    k_build_coef<<<(nch * nch + 255) / 256, 256, 0, ctx->stream>>>(kind, D, W1, W2, C); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }
@@ -305,7 +357,7 @@ static dmrg_status build_coef(dmrg_ctx *ctx, int kind, int D, const double *W1, 
 static dmrg_status transpose_sq(dmrg_ctx *ctx, const double *in, double *out, int n, int batch)
 {
     dim3 g((n + 31) / 32, (n + 31) / 32, batch);
-    k_transpose_sq<<<g, dim3(32, 8), 0, ctx->stream>>>(in, out, n, batch);
+    k_transpose_sq<<<g, dim3(32, 8), 0, ctx->stream>>>(in, out, n, batch); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }
@@ -375,6 +427,29 @@ const char *dmrg_status_string(dmrg_status s)
     return "unknown";
 }
 
+dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
+{
+    if (!ctx || !name) return DMRG_EINVAL;
+    if (!std::strcmp(name, "tc_force")) { ctx->tc_force = value != 0.0; return DMRG_OK; }
+    if (!std::strcmp(name, "tc_min_work")) {
+        if (!(value >= 0.0)) return DMRG_EINVAL;
+        ctx->tc_min_work = value;
+        return DMRG_OK;
+    }
+    if (!std::strcmp(name, "tc_bn")) {
+        int v = (int)value;
+        if (v != 0 && v != 128 && v != 256) return DMRG_EINVAL;
+        ctx->tc_bn_override = v;
+        return DMRG_OK;
+    }
+    if (!std::strcmp(name, "jacobi_max_sweeps")) {
+        if (!(value >= 1.0 && value <= 1000.0)) return DMRG_EINVAL;
+        ctx->jacobi_max_sweeps = (int)value;
+        return DMRG_OK;
+    }
+    return DMRG_EINVAL;
+}
+
 int dmrg_mpo_dim(int model)
 {
     switch (model) {
@@ -418,11 +493,14 @@ void dmrg_destroy(dmrg_ctx *ctx)
     ctx->work.release();
     ctx->work2.release();
     ctx->work3.release();
+    ctx->tcbuf.release();
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_pinned_i) cudaFreeHost(ctx->h_pinned_i);
     if (ctx->h_pinned_d) cudaFreeHost(ctx->h_pinned_d);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (auto &p : ctx->prof_slot)
+        for (auto e : p.ev) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -447,7 +525,7 @@ dmrg_status dmrg_get_status(dmrg_ctx *ctx)
 dmrg_status dmrg_build_mpo(dmrg_ctx *ctx, dmrg_model model, const dmrg_model_params *mp, double *W_dev)
 {
     if (!ctx || !mp || !W_dev || mp->N < 2 || dmrg_mpo_dim(model) < 0) return DMRG_EINVAL;
-    k_build_mpo<<<(mp->N + 63) / 64, 64, 0, ctx->stream>>>((int)model, mp->N, mp->J, mp->Delta, mp->J2, W_dev);
+    k_build_mpo<<<(mp->N + 63) / 64, 64, 0, ctx->stream>>>((int)model, mp->N, mp->J, mp->Delta, mp->J2, W_dev); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }
@@ -474,20 +552,60 @@ static dmrg_status bond_step(dmrg_state *st, int k, int go_right, int do_ctrl, d
     };
     const int K = (int)std::min<long long>(st->K, nn);
     DMRG_TRY(lanczos_run(ctx, st->lw, nn, K, st->theta, mv));
-    // SVD (Eq. 20)
-    DMRG_TRY(svd_jacobi(ctx, st->theta, m, n, st->U, st->s, st->Vt, st->svdw, st->p.jacobi_max_sweeps, st->d_info));
-    // entropy, controller, truncation
-    DMRG_TRY(launch_decide(ctx, st->s, r, st->ctrl + k, st->p, do_ctrl, 0, st->has_mlp ? st->mlp : nullptr, k, st->N,
-                           st->sweep_index, st->lw.lz, st->d_res, visit, direction));
-    DMRG_CUDA(cudaMemcpyAsync(st->h_res, st->d_res, sizeof(BondResult), cudaMemcpyDeviceToHost, ctx->stream));
-    DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
-    const int kk = st->h_res->k;
-    if (kk < 1 || kk > r || kk > st->cap[k + 1]) return DMRG_ENAN;
-    {
+    const float *mlp = st->has_mlp ? st->mlp : nullptr;
+    int kk;
+    if (prec == DMRG_PREC_FP64) {
+        // SVD (Eq. 20) in FP64, then entropy, controller and truncation
+        DMRG_TRY(svd_jacobi(ctx, st->theta, m, n, st->U, st->s, st->Vt, st->svdw, st->p.jacobi_max_sweeps,
+                            st->d_info));
+        DMRG_TRY(launch_decide(ctx, st->s, r, st->ctrl + k, st->p, do_ctrl, 0, mlp, k, st->N, st->sweep_index,
+                               st->lw.lz, st->d_res, visit, direction, (double)r * 2.220446049250313e-16));
+        DMRG_CUDA(cudaMemcpyAsync(st->h_res, st->d_res, sizeof(BondResult), cudaMemcpyDeviceToHost, ctx->stream));
+        DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
+        kk = st->h_res->k;
+        if (kk < 1 || kk > r || kk > st->cap[k + 1]) return DMRG_ENAN;
         long long tot = std::max((long long)m * kk, (long long)kk * n);
         k_split<<<grid1d(tot, 256, ctx->num_sms), 256, 0, ctx->stream>>>(st->U, st->s, st->Vt, m, n, r, st->d_res,
-                                                                         go_right, st->A[k], st->A[k + 1]);
+                                                                         go_right, st->A[k], st->A[k + 1]); DMRG_COUNT_LAUNCH();
         DMRG_CUDA(cudaGetLastError());
+    } else {
+        // Mixed form: FP32 Jacobi on the vectors that become the isometry
+        // (columns of theta if the centre moves right, rows if it moves left),
+        // one FP64 Newton-Schulz step Q <- Q - (Q Q^T - I) Q / 2 on the k
+        // retained unit vectors, and the centre tensor as the projection of
+        // theta on them (3xTF32), renormalised.
+        const int dir = go_right ? 0 : 1;
+        const int len = dir == 0 ? m : n;
+        float *X32;
+        double *nrm;
+        int *perm;
+        DMRG_TRY(svd_jacobi32(ctx, st->theta, m, n, dir, st->svdw, st->p.jacobi_max_sweeps, st->d_info, st->s, &X32,
+                              &nrm, &perm));
+        DMRG_TRY(launch_decide(ctx, st->s, r, st->ctrl + k, st->p, do_ctrl, 0, mlp, k, st->N, st->sweep_index,
+                               st->lw.lz, st->d_res, visit, direction, kMixedRankFloor));
+        DMRG_CUDA(cudaMemcpyAsync(st->h_res, st->d_res, sizeof(BondResult), cudaMemcpyDeviceToHost, ctx->stream));
+        DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
+        kk = st->h_res->k;
+        if (kk < 1 || kk > r || kk > st->cap[k + 1]) return DMRG_ENAN;
+        double *Q = st->X, *T = st->Y, *E = st->Vt;
+        DMRG_TRY(gather_unit_vectors(ctx, X32, nrm, perm, &st->d_res->k, kk, len, Q));
+        DMRG_TRY(gemm_f64(ctx->stream, kk, kk, len, 1.0, Q, len, 1, 0, Q, 1, len, 0, 0.0, E, kk, 1, 0, 1));
+        DMRG_CUDA(cudaMemcpyAsync(T, Q, sizeof(double) * (size_t)kk * len, cudaMemcpyDeviceToDevice, ctx->stream));
+        DMRG_TRY(gemm_f64(ctx->stream, kk, len, kk, -0.5, E, kk, 1, 0, Q, len, 1, 0, 1.5, T, len, 1, 0, 1));
+        if (dir == 0) {
+            dim3 g((kk + 31) / 32, (m + 31) / 32);
+            // A_k = T^T (m x kk): k_transpose_rect(in = T (kk x m), out = A_k (m x kk))
+            k_transpose_rect<<<dim3((m + 31) / 32, (kk + 31) / 32), dim3(32, 8), 0, ctx->stream>>>(T, st->A[k], kk, m); DMRG_COUNT_LAUNCH();
+            DMRG_CUDA(cudaGetLastError());
+            (void)g;
+            DMRG_TRY(gemm(ctx, prec, kk, n, m, 1.0, T, m, 1, 0, st->theta, n, 1, 0, 0.0, st->A[k + 1], n, 1, 0, 1));
+            DMRG_TRY(normalise(ctx, st->A[k + 1], (long long)kk * n, st->s + r));
+        } else {
+            DMRG_CUDA(cudaMemcpyAsync(st->A[k + 1], T, sizeof(double) * (size_t)kk * n, cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+            DMRG_TRY(gemm(ctx, prec, m, kk, n, 1.0, st->theta, n, 1, 0, T, 1, n, 0, 0.0, st->A[k], kk, 1, 0, 1));
+            DMRG_TRY(normalise(ctx, st->A[k], (long long)m * kk, st->s + r));
+        }
     }
     st->chi[k + 1] = kk;
     double f = 2.0 * m * n * cm + K * matvec_flops(D, cl, cr) + svd_nominal_flops(m, n);
@@ -572,7 +690,7 @@ dmrg_status dmrg_state_create(dmrg_ctx *ctx, int D, const dmrg_model_params *mp,
     size_t off_X = total; total += al256(sizeof(double) * nmax * D);
     size_t off_Y = total; total += al256(sizeof(double) * nmax * D);
     size_t off_U = total; total += al256(sizeof(double) * umax);
-    size_t off_s = total; total += al256(sizeof(double) * smax);
+    size_t off_s = total; total += al256(sizeof(double) * (smax + 2 * kNormBlocks));
     size_t off_Vt = total; total += al256(sizeof(double) * vtmax);
     size_t off_svd = total; total += al256(svd_bytes);
     size_t off_lz = total; total += al256(lanczos_work_bytes(nmax, st->K, ctx->num_sms));
@@ -637,23 +755,23 @@ dmrg_status dmrg_state_create(dmrg_ctx *ctx, int D, const dmrg_model_params *mp,
         dmrg_status s0 = svd_jacobi(ctx, st->A[i], rows, cols, st->U, st->s, st->Vt, st->svdw, 60, st->d_info);
         if (s0 != DMRG_OK) return fail(s0);
         if (r != rows) return fail(DMRG_EINVAL);
-        k_copy_scale<<<grid1d((long long)r * cols, 256, ctx->num_sms), 256, 0, cs>>>(st->Vt, st->A[i], r, cols, nullptr);
-        k_copy_scale<<<grid1d((long long)rows * r, 256, ctx->num_sms), 256, 0, cs>>>(st->U, st->theta, rows, r, st->s);
+        k_copy_scale<<<grid1d((long long)r * cols, 256, ctx->num_sms), 256, 0, cs>>>(st->Vt, st->A[i], r, cols, nullptr); DMRG_COUNT_LAUNCH();
+        k_copy_scale<<<grid1d((long long)rows * r, 256, ctx->num_sms), 256, 0, cs>>>(st->U, st->theta, rows, r, st->s); DMRG_COUNT_LAUNCH();
         int pr = 2 * st->chi[i - 1];
         s0 = gemm_f64(cs, pr, r, rows, 1.0, st->A[i - 1], rows, 1, 0, st->theta, r, 1, 0, 0.0, st->X, r, 1, 0, 1);
         if (s0 != DMRG_OK) return fail(s0);
-        k_copy_scale<<<grid1d((long long)pr * r, 256, ctx->num_sms), 256, 0, cs>>>(st->X, st->A[i - 1], pr, r, nullptr);
+        k_copy_scale<<<grid1d((long long)pr * r, 256, ctx->num_sms), 256, 0, cs>>>(st->X, st->A[i - 1], pr, r, nullptr); DMRG_COUNT_LAUNCH();
         if (cudaGetLastError() != cudaSuccess) return fail(DMRG_ECUDA);
     }
-    k_normalise<<<1, 256, 0, cs>>>(st->A[0], 2 * st->chi[1]);
-    k_boundary_env<<<1, 32, 0, cs>>>(st->env[0], D, D - 1);
-    k_boundary_env<<<1, 32, 0, cs>>>(st->env[N], D, 0);
+    k_normalise<<<1, 256, 0, cs>>>(st->A[0], 2 * st->chi[1]); DMRG_COUNT_LAUNCH();
+    k_boundary_env<<<1, 32, 0, cs>>>(st->env[0], D, D - 1); DMRG_COUNT_LAUNCH();
+    k_boundary_env<<<1, 32, 0, cs>>>(st->env[N], D, 0); DMRG_COUNT_LAUNCH();
     for (int i = N - 1; i >= 2; --i) {
         dmrg_status s0 = env_right_dev(ctx, st->p.prec, D, st->chi[i], st->chi[i + 1], st->env[i + 1],
                                        st->coef_r + (size_t)i * 4 * D * D, st->A[i], st->env[i], st->X, st->Y);
         if (s0 != DMRG_OK) return fail(s0);
     }
-    k_init_ctrl<<<(N - 1 + 127) / 128, 128, 0, cs>>>(st->ctrl, N - 1, p->chi_min);
+    k_init_ctrl<<<(N - 1 + 127) / 128, 128, 0, cs>>>(st->ctrl, N - 1, p->chi_min); DMRG_COUNT_LAUNCH();
     if (cudaGetLastError() != cudaSuccess) return fail(DMRG_ECUDA);
     if (cudaStreamSynchronize(cs) != cudaSuccess) return fail(DMRG_ECUDA);
     *out = st;
@@ -767,6 +885,68 @@ dmrg_status dmrg_state_ctrl(dmrg_state *st, dmrg_ctrl_state **ctrl_dev)
     return DMRG_OK;
 }
 
+long long dmrg_state_mps_size(dmrg_state *st)
+{
+    if (!st) return -1;
+    long long n = 0;
+    for (int i = 0; i < st->N; ++i) n += (long long)st->chi[i] * 2 * st->chi[i + 1];
+    return n;
+}
+
+dmrg_status dmrg_state_get_mps(dmrg_state *st, double *out)
+{
+    if (!st || !out) return DMRG_EINVAL;
+    long long off = 0;
+    for (int i = 0; i < st->N; ++i) {
+        size_t n = (size_t)st->chi[i] * 2 * st->chi[i + 1];
+        DMRG_CUDA(cudaMemcpyAsync(out + off, st->A[i], sizeof(double) * n, cudaMemcpyDefault, st->ctx->stream));
+        off += (long long)n;
+    }
+    DMRG_CUDA(cudaStreamSynchronize(st->ctx->stream));
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_state_put_mps(dmrg_state *st, const double *in)
+{
+    if (!st || !in) return DMRG_EINVAL;
+    long long off = 0;
+    for (int i = 0; i < st->N; ++i) {
+        size_t n = (size_t)st->chi[i] * 2 * st->chi[i + 1];
+        DMRG_CUDA(cudaMemcpyAsync(st->A[i], in + off, sizeof(double) * n, cudaMemcpyDefault, st->ctx->stream));
+        off += (long long)n;
+    }
+    DMRG_CUDA(cudaStreamSynchronize(st->ctx->stream));
+    return DMRG_OK;
+}
+
+long long dmrg_launch_count(void) { return g_launch_count.load(); }
+
+dmrg_status dmrg_profile(dmrg_ctx *ctx, int on)
+{
+    if (!ctx) return DMRG_EINVAL;
+    DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (auto &p : ctx->prof_slot) { p.used = 0; p.n = 0; p.flops = 0.0; p.bytes = 0.0; }
+    ctx->prof = on ? 1 : 0;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_profile_read(dmrg_ctx *ctx, int kind, double *ms, long long *launches, double *flops, double *bytes)
+{
+    if (!ctx || kind < 0 || kind >= PROF_KINDS) return DMRG_EINVAL;
+    DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    ProfSlot &p = ctx->prof_slot[kind];
+    double t = 0.0;
+    for (size_t i = 0; i + 1 < p.used; i += 2) {
+        float x = 0.f;
+        if (cudaEventElapsedTime(&x, p.ev[i], p.ev[i + 1]) == cudaSuccess) t += x;
+    }
+    if (ms) *ms = t;
+    if (launches) *launches = p.n;
+    if (flops) *flops = p.flops;
+    if (bytes) *bytes = p.bytes;
+    return DMRG_OK;
+}
+
 dmrg_status dmrg_state_set_mlp(dmrg_state *st, const float *params_dev)
 {
     if (!st) return DMRG_EINVAL;
@@ -797,7 +977,8 @@ dmrg_status svd_truncate(dmrg_ctx *ctx, const double *theta_dev, int m, int n, i
     p.chi_max = chi_max;
     p.multiplet_guard = 0;
     p.ctrl = DMRG_CTRL_FIXED;
-    DMRG_TRY(launch_decide(ctx, s_dev, r, nullptr, p, 0, chi_max, nullptr, 0, 1, 0, nullptr, res, nullptr, 0));
+    DMRG_TRY(launch_decide(ctx, s_dev, r, nullptr, p, 0, chi_max, nullptr, 0, 1, 0, nullptr, res, nullptr, 0,
+                           (double)r * 2.220446049250313e-16));
     DMRG_CUDA(cudaMemcpyAsync(ctx->h_pinned_d, res, sizeof(BondResult), cudaMemcpyDeviceToHost, ctx->stream));
     DMRG_CUDA(cudaMemcpyAsync(ctx->h_pinned_i + 32, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     DMRG_CUDA(cudaStreamSynchronize(ctx->stream));

@@ -10,6 +10,9 @@
 #include "common.cuh"
 
 namespace dmrg {
+
+std::atomic<long long> g_launch_count{0};
+
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4, NT = 256;
@@ -97,7 +100,7 @@ dmrg_status gemm_f64(cudaStream_t st, int M, int N, int K, double alpha, const d
         // C = beta * C: run the kernel with K = 0 (accumulators stay zero)
         K = 0;
     }
-    k_gemm_f64<<<grid, NT, 0, st>>>(M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb);
+    k_gemm_f64<<<grid, NT, 0, st>>>(M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }
@@ -106,9 +109,15 @@ dmrg_status gemm(dmrg_ctx *ctx, int prec, int M, int N, int K, double alpha, con
                  long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
                  double beta, double *C, long long sCm, long long sCn, long long sCb, int batch)
 {
-    if (prec == DMRG_PREC_FP64)
-        return gemm_f64(ctx->stream, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb,
-                        batch);
+    if (prec == DMRG_PREC_FP64) {
+        prof_mark(ctx, PROF_F64_GEMM);
+        dmrg_status s = gemm_f64(ctx->stream, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn,
+                                 sCb, batch);
+        prof_mark(ctx, PROF_F64_GEMM);
+        prof_count(ctx, PROF_F64_GEMM, 2.0 * M * (double)N * K * batch,
+                   8.0 * ((double)M * K + (double)K * N + (double)M * N) * batch);
+        return s;
+    }
     if (prec == DMRG_PREC_3XTF32)
         return gemm_3xtf32(ctx, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb, batch);
     return DMRG_EUNSUPPORTED;

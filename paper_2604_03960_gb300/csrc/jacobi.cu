@@ -254,6 +254,149 @@ __global__ void k_jac_out(const double *__restrict__ X, const double *__restrict
     for (int k = threadIdx.x; k < n; k += blockDim.x) Vt[(long long)c * n + k] = sign * vscale * vsrc[k];
 }
 
+// ---------------------------------------------------------------------------
+// FP32 variant for the mixed-precision form: vectors only (no V), dot
+// products accumulated per lane in FP32 (two chains) and across lanes in FP64.
+// ---------------------------------------------------------------------------
+__global__ void k_jac32_load(const double *__restrict__ A, int m, int n, int dir, int r, int l, float *__restrict__ X,
+                             unsigned *sync)
+{
+    __shared__ float tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    if (dir == 0) {
+        // vectors are the columns of A: X[i][t] = A[t][i], i < n = r, t < m = l
+        for (int yy = threadIdx.y; yy < 32; yy += 8) {
+            int row = by + yy, col = bx + threadIdx.x;
+            tile[yy][threadIdx.x] = (row < m && col < n) ? (float)A[(long long)row * n + col] : 0.0f;
+        }
+        __syncthreads();
+        for (int yy = threadIdx.y; yy < 32; yy += 8) {
+            int i = bx + yy, t = by + threadIdx.x;
+            if (i < r && t < l) X[(long long)i * l + t] = tile[threadIdx.x][yy];
+        }
+    } else {
+        for (int yy = threadIdx.y; yy < 32; yy += 8) {
+            int i = by + yy, t = bx + threadIdx.x;
+            if (i < r && t < l) X[(long long)i * l + t] = (float)A[(long long)i * n + t];
+        }
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.y == 0 && threadIdx.x < 8) sync[threadIdx.x] = 0u;
+}
+
+__global__ void __launch_bounds__(256) k_jac32_sweeps(float *__restrict__ X, int r, int l, int max_sweeps, double tol,
+                                                      unsigned *sync, int *status, int *info)
+{
+    const int lane = threadIdx.x & 31;
+    const int warps_per_block = blockDim.x >> 5;
+    const int gwarp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * warps_per_block;
+    const int rp = r + (r & 1);
+    const int npairs = rp / 2;
+    unsigned *barrier = sync;
+    unsigned *rotc = sync + 2;
+    __shared__ unsigned block_rot;
+    int sweep = 0;
+    bool converged = false;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) block_rot = 0;
+        __syncthreads();
+        unsigned my_rot = 0;
+        for (int t = 0; t < rp - 1; ++t) {
+            for (int p = gwarp; p < npairs; p += nwarps) {
+                int i, j;
+                rr_pair(rp, t, p, i, j);
+                if (i >= r || j >= r) continue;
+                float *xi = X + (long long)i * l, *xj = X + (long long)j * l;
+                float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f, g0 = 0.f, g1 = 0.f;
+                int k = lane;
+                for (; k + 32 < l; k += 64) {
+                    float u = xi[k], v = xj[k], u2 = xi[k + 32], v2 = xj[k + 32];
+                    a0 = fmaf(u, u, a0); b0 = fmaf(v, v, b0); g0 = fmaf(u, v, g0);
+                    a1 = fmaf(u2, u2, a1); b1 = fmaf(v2, v2, b1); g1 = fmaf(u2, v2, g1);
+                }
+                if (k < l) {
+                    float u = xi[k], v = xj[k];
+                    a0 = fmaf(u, u, a0); b0 = fmaf(v, v, b0); g0 = fmaf(u, v, g0);
+                }
+                double a = warp_sum((double)a0 + (double)a1);
+                double b = warp_sum((double)b0 + (double)b1);
+                double g = warp_sum((double)g0 + (double)g1);
+                if (!(a > 0.0 && b > 0.0)) continue;
+                if (!(fabs(g) > tol * sqrt(a) * sqrt(b))) continue;
+                double zeta = (b - a) / (2.0 * g);
+                double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double cd = 1.0 / sqrt(1.0 + tt * tt);
+                float c = (float)cd, s = (float)(cd * tt);
+                for (int q = lane; q < l; q += 32) {
+                    float u = xi[q], v = xj[q];
+                    xi[q] = fmaf(c, u, -s * v);
+                    xj[q] = fmaf(s, u, c * v);
+                }
+                if (lane == 0) my_rot++;
+            }
+            if (!block_barrier(barrier, status)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
+                return;
+            }
+        }
+        if (lane == 0 && my_rot) atomicAdd(&block_rot, my_rot);
+        __syncthreads();
+        if (threadIdx.x == 0 && block_rot) atomicAdd(&rotc[sweep & 1], block_rot);
+        if (!block_barrier(barrier, status)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
+            return;
+        }
+        unsigned total = *(volatile unsigned *)&rotc[sweep & 1];
+        if (blockIdx.x == 0 && threadIdx.x == 0) rotc[(sweep + 1) & 1] = 0u;
+        if (total == 0u) {
+            converged = true;
+            ++sweep;
+            break;
+        }
+        if (!block_barrier(barrier, status)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
+            return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        info[0] = converged ? sweep : -sweep;
+        if (!converged) atomicOr(status, ST_NOCONV);
+    }
+}
+
+__global__ void k_jac32_norms(const float *__restrict__ X, int r, int l, double *__restrict__ nrm)
+{
+    int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= r) return;
+    const float *x = X + (long long)w * l;
+    double a = 0.0;
+    for (int k = lane; k < l; k += 32) a = fma((double)x[k], (double)x[k], a);
+    a = warp_sum(a);
+    if (lane == 0) nrm[w] = sqrt(a);
+}
+
+__global__ void k_sorted_values(const double *__restrict__ nrm, const int *__restrict__ perm, int r_out,
+                                double *__restrict__ s)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < r_out) s[c] = nrm[perm[c]];
+}
+
+// Q[j][t] = X[perm[j]][t] / nrm[perm[j]]  (FP64), j < k
+__global__ void k_gather_unit(const float *__restrict__ X, const double *__restrict__ nrm, const int *__restrict__ perm,
+                              const int *__restrict__ kdev, int l, double *__restrict__ Q)
+{
+    const int k = *kdev;
+    const long long total = (long long)k * l;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        const int j = (int)(e / l), t = (int)(e % l);
+        const int i = perm[j];
+        const double nv = nrm[i];
+        Q[e] = nv > 0.0 ? (double)X[(long long)i * l + t] / nv : 0.0;
+    }
+}
+
 }  // namespace
 
 dmrg_status svd_jacobi(dmrg_ctx *ctx, const double *A, int m, int n, double *U, double *s, double *Vt, void *work,
@@ -269,10 +412,13 @@ dmrg_status svd_jacobi(dmrg_ctx *ctx, const double *A, int m, int n, double *U, 
         dim3 grid((big + 31) / 32, (big + 31) / 32);
         if (!tr) grid = dim3((n + 31) / 32 > (r + 31) / 32 ? (n + 31) / 32 : (r + 31) / 32,
                              (m + 31) / 32 > (r + 31) / 32 ? (m + 31) / 32 : (r + 31) / 32);
-        k_jac_load<<<grid, dim3(32, 8), 0, st>>>(A, m, n, tr, r, l, w.X, w.Vm, w.sync);
+        k_jac_load<<<grid, dim3(32, 8), 0, st>>>(A, m, n, tr, r, l, w.X, w.Vm, w.sync); DMRG_COUNT_LAUNCH();
         DMRG_CUDA(cudaGetLastError());
     }
-    const double tol = sqrt((double)l) * 2.220446049250313e-16;
+    // rotate only while |x_i.x_j| > l eps |x_i||x_j|: the rounding noise of the
+    // computed dot product is ~ sqrt(l) eps, so this margin of sqrt(l) lets the
+    // sweep loop terminate instead of rotating on noise
+    const double tol = (double)(l > 16 ? l : 16) * 2.220446049250313e-16;
     const int rp = r + (r & 1);
     const int npairs = rp / 2;
     int threads = 256;
@@ -289,15 +435,104 @@ dmrg_status svd_jacobi(dmrg_ctx *ctx, const double *A, int m, int n, double *U, 
     unsigned *sync = w.sync;
     int *status = ctx->d_status;
     void *args[] = {&X, &Vm, (void *)&r, (void *)&l, &max_sweeps, (void *)&tol, &sync, &status, &d_info};
+    prof_mark(ctx, PROF_JACOBI64);
     if (blocks == 1) {
-        k_jac_sweeps<<<1, threads, 0, st>>>(X, Vm, r, l, max_sweeps, tol, sync, status, d_info);
+        k_jac_sweeps<<<1, threads, 0, st>>>(X, Vm, r, l, max_sweeps, tol, sync, status, d_info); DMRG_COUNT_LAUNCH();
     } else {
-        DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_jac_sweeps, dim3(blocks), dim3(threads), args, 0, st));
+        DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_jac_sweeps, dim3(blocks), dim3(threads), args, 0, st)); DMRG_COUNT_LAUNCH();
+    }
+    prof_mark(ctx, PROF_JACOBI64);
+    // nominal full-SVD flop count (4 m^2 n + 8 m n^2 + 9 n^3, m >= n) and the
+    // minimum bytes of one pass over the vectors and V
+    prof_count(ctx, PROF_JACOBI64, 4.0 * l * (double)l * r + 8.0 * l * (double)r * r + 9.0 * (double)r * r * r,
+               8.0 * ((double)r * l + (double)r * r) * 2.0);
+    DMRG_CUDA(cudaGetLastError());
+    k_jac_norms<<<(r * 32 + 255) / 256, 256, 0, st>>>(X, r, l, w.nrm); DMRG_COUNT_LAUNCH();
+    k_jac_rank<<<(r + 255) / 256, 256, 0, st>>>(w.nrm, r, w.perm); DMRG_COUNT_LAUNCH();
+    k_jac_out<<<r, 256, 0, st>>>(X, Vm, w.nrm, w.perm, m, n, tr, r, l, U, s, Vt); DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
+}  // namespace dmrg
+
+namespace dmrg {
+
+size_t jac32_work_bytes(int r, int l)
+{
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    return al(sizeof(float) * (size_t)r * l) + al(sizeof(double) * r) + al(sizeof(int) * r) + al(sizeof(unsigned) * 8);
+}
+
+// FP32 one-sided Jacobi on the columns (dir 0) or rows (dir 1) of theta; on
+// return s_sorted[0..min(m,n)) holds the vector norms in descending order and
+// perm the vector of each.  Scratch layout: X32 | nrm | perm | sync.
+dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, void *work, int max_sweeps,
+                         int *d_info, double *s_sorted, float **X_out, double **nrm_out, int **perm_out)
+{
+    if (m <= 0 || n <= 0) return DMRG_EINVAL;
+    const int r = dir == 0 ? n : m, l = dir == 0 ? m : n;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    char *p = static_cast<char *>(work);
+    float *X = reinterpret_cast<float *>(p); p += al(sizeof(float) * (size_t)r * l);
+    double *nrm = reinterpret_cast<double *>(p); p += al(sizeof(double) * r);
+    int *perm = reinterpret_cast<int *>(p); p += al(sizeof(int) * r);
+    unsigned *sync = reinterpret_cast<unsigned *>(p);
+    cudaStream_t st = ctx->stream;
+    {
+        dim3 grid = dir == 0 ? dim3((n + 31) / 32, (m + 31) / 32) : dim3((n + 31) / 32, (m + 31) / 32);
+        k_jac32_load<<<grid, dim3(32, 8), 0, st>>>(A, m, n, dir, r, l, X, sync); DMRG_COUNT_LAUNCH();
+        DMRG_CUDA(cudaGetLastError());
+    }
+    // FP32 storage resolves orthogonality to a few units of 2^-24; rotate while
+    // the cosine exceeds 2^-18 (the cross-lane FP64 sums keep the test clean)
+    const double tol = 3.814697265625e-06;
+    const int rp = r + (r & 1);
+    const int npairs = rp / 2;
+    int threads = 256, blocks = 1;
+    if (r > 128) {
+        int per_sm = 0;
+        DMRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jac32_sweeps, threads, 0));
+        int maxb = per_sm * ctx->num_sms;
+        blocks = (npairs + 7) / 8;
+        if (blocks > maxb) blocks = maxb;
+        if (blocks < 1) blocks = 1;
+    }
+    int *status = ctx->d_status;
+    void *args[] = {&X, (void *)&r, (void *)&l, &max_sweeps, (void *)&tol, &sync, &status, &d_info};
+    prof_mark(ctx, PROF_JACOBI32);
+    if (blocks == 1) {
+        k_jac32_sweeps<<<1, threads, 0, st>>>(X, r, l, max_sweeps, tol, sync, status, d_info);
+    } else {
+        DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_jac32_sweeps, dim3(blocks), dim3(threads), args, 0, st));
+    }
+    DMRG_COUNT_LAUNCH();
+    prof_mark(ctx, PROF_JACOBI32);
+    {
+        const double M_ = l > r ? l : r, N_ = l > r ? r : l;
+        prof_count(ctx, PROF_JACOBI32, 4.0 * M_ * M_ * N_ + 8.0 * M_ * N_ * N_ + 9.0 * N_ * N_ * N_,
+                   4.0 * (double)r * l * 2.0);
     }
     DMRG_CUDA(cudaGetLastError());
-    k_jac_norms<<<(r * 32 + 255) / 256, 256, 0, st>>>(X, r, l, w.nrm);
-    k_jac_rank<<<(r + 255) / 256, 256, 0, st>>>(w.nrm, r, w.perm);
-    k_jac_out<<<r, 256, 0, st>>>(X, Vm, w.nrm, w.perm, m, n, tr, r, l, U, s, Vt);
+    k_jac32_norms<<<(r * 32 + 255) / 256, 256, 0, st>>>(X, r, l, nrm); DMRG_COUNT_LAUNCH();
+    k_jac_rank<<<(r + 255) / 256, 256, 0, st>>>(nrm, r, perm); DMRG_COUNT_LAUNCH();
+    const int r_out = m < n ? m : n;
+    k_sorted_values<<<(r_out + 255) / 256, 256, 0, st>>>(nrm, perm, r_out, s_sorted); DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    *X_out = X;
+    *nrm_out = nrm;
+    *perm_out = perm;
+    return DMRG_OK;
+}
+
+dmrg_status gather_unit_vectors(dmrg_ctx *ctx, const float *X, const double *nrm, const int *perm, const int *kdev,
+                                int kmax, int l, double *Q)
+{
+    long long total = (long long)kmax * l;
+    long long b = (total + 255) / 256;
+    if (b > ctx->num_sms * 8LL) b = ctx->num_sms * 8LL;
+    if (b < 1) b = 1;
+    k_gather_unit<<<(int)b, 256, 0, ctx->stream>>>(X, nrm, perm, kdev, l, Q); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }

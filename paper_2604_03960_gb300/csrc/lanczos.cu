@@ -264,36 +264,36 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
     cudaStream_t st = ctx->stream;
     const int g = grid_for(n, ctx->num_sms);
     DMRG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned), st));
-    k_lz_init<<<1, 1, 0, st>>>(w.lz, K);
+    k_lz_init<<<1, 1, 0, st>>>(w.lz, K); DMRG_COUNT_LAUNCH();
     ReduceArgs ra{nullptr, n, 0, theta, n, w.partials, w.counter};
-    k_multidot<3><<<g, RB, 0, st>>>(ra, w.lz, 0, nullptr);          // |theta|
-    k_scale_by<<<g, RB, 0, st>>>(w.V, theta, n, w.lz);                // v0
+    k_multidot<3><<<g, RB, 0, st>>>(ra, w.lz, 0, nullptr); DMRG_COUNT_LAUNCH();          // |theta|
+    k_scale_by<<<g, RB, 0, st>>>(w.V, theta, n, w.lz); DMRG_COUNT_LAUNCH();                // v0
     DMRG_CUDA(cudaGetLastError());
     for (int j = 0; j < K; ++j) {
         double *vj = w.V + (size_t)n * j;
         DMRG_TRY(matvec(vj, w.w));
         ReduceArgs a1{vj, n, 1, w.w, n, w.partials, w.counter};
-        k_multidot<1><<<g, RB, 0, st>>>(a1, w.lz, j, nullptr);
-        k_three_term<<<g, RB, 0, st>>>(w.w, vj, j > 0 ? vj - n : vj, n, w.lz, j);
+        k_multidot<1><<<g, RB, 0, st>>>(a1, w.lz, j, nullptr); DMRG_COUNT_LAUNCH();
+        k_three_term<<<g, RB, 0, st>>>(w.w, vj, j > 0 ? vj - n : vj, n, w.lz, j); DMRG_COUNT_LAUNCH();
         for (int pass = 0; pass < 2; ++pass) {
             ReduceArgs a2{w.V, n, j + 1, w.w, n, w.partials, w.counter};
-            k_multidot<0><<<g, RB, 0, st>>>(a2, w.lz, j, w.c);
-            k_multiaxpy<<<g, RB, 0, st>>>(w.w, w.V, n, j + 1, w.c, n, w.lz, 1, 0);
+            k_multidot<0><<<g, RB, 0, st>>>(a2, w.lz, j, w.c); DMRG_COUNT_LAUNCH();
+            k_multiaxpy<<<g, RB, 0, st>>>(w.w, w.V, n, j + 1, w.c, n, w.lz, 1, 0); DMRG_COUNT_LAUNCH();
         }
         ReduceArgs a3{nullptr, n, 0, w.w, n, w.partials, w.counter};
-        k_multidot<2><<<g, RB, 0, st>>>(a3, w.lz, j, nullptr);
-        if (j + 1 < K) k_next_vec<<<g, RB, 0, st>>>(w.V + (size_t)n * (j + 1), w.w, n, w.lz, j);
+        k_multidot<2><<<g, RB, 0, st>>>(a3, w.lz, j, nullptr); DMRG_COUNT_LAUNCH();
+        if (j + 1 < K) k_next_vec<<<g, RB, 0, st>>>(w.V + (size_t)n * (j + 1), w.w, n, w.lz, j); DMRG_COUNT_LAUNCH();
         DMRG_CUDA(cudaGetLastError());
     }
-    k_tridiag_lowest<<<1, 1, 0, st>>>(w.lz, ctx->d_status);
+    k_tridiag_lowest<<<1, 1, 0, st>>>(w.lz, ctx->d_status); DMRG_COUNT_LAUNCH();
     // theta = V y0 (only the first m vectors carry weight: y is zero beyond m)
     {
         // copy y to the coefficient buffer (device to device)
         DMRG_CUDA(cudaMemcpyAsync(w.c, w.lz->y, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
-        k_multiaxpy<<<g, RB, 0, st>>>(theta, w.V, n, -1, w.c, n, w.lz, 0, 1);
+        k_multiaxpy<<<g, RB, 0, st>>>(theta, w.V, n, -1, w.c, n, w.lz, 0, 1); DMRG_COUNT_LAUNCH();
         ReduceArgs a4{nullptr, n, 0, theta, n, w.partials, w.counter};
-        k_multidot<3><<<g, RB, 0, st>>>(a4, w.lz, 0, nullptr);
-        k_scale_by<<<g, RB, 0, st>>>(theta, theta, n, w.lz);
+        k_multidot<3><<<g, RB, 0, st>>>(a4, w.lz, 0, nullptr); DMRG_COUNT_LAUNCH();
+        k_scale_by<<<g, RB, 0, st>>>(theta, theta, n, w.lz); DMRG_COUNT_LAUNCH();
     }
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;

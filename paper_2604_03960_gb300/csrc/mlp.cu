@@ -143,7 +143,7 @@ dmrg_status dmrg_mlp_forward(dmrg_ctx *ctx, const float *params_dev, int B, cons
 {
     if (!ctx || !params_dev || !X_dev || !y_dev || B < 1) return DMRG_EINVAL;
     k_mlp_fwd<<<(B + 127) / 128, 128, 0, ctx->stream>>>(params_dev, B, X_dev, y_dev, nullptr, nullptr, nullptr,
-                                                         nullptr);
+                                                         nullptr); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }
@@ -158,10 +158,10 @@ dmrg_status dmrg_mlp_loss_grad(dmrg_ctx *ctx, const float *params_dev, int B, co
     float *z1 = ctx->work3.as<float>(), *h1 = z1 + per, *z2 = h1 + per, *h2 = z2 + per, *dz1 = h2 + per,
           *dz2 = dz1 + per, *y = dz2 + per, *dy = y + B;
     cudaStream_t st = ctx->stream;
-    k_mlp_fwd<<<(B + 127) / 128, 128, 0, st>>>(params_dev, B, X_dev, y, z1, h1, z2, h2);
-    k_mlp_bwd_act<<<(B + 127) / 128, 128, 0, st>>>(params_dev, B, y, t_dev, z1, z2, dy, dz1, dz2);
-    k_mlp_grad<<<(MLP_NPARAM + 127) / 128, 128, 0, st>>>(B, X_dev, h1, h2, dy, dz1, dz2, grad_dev);
-    k_mlp_loss<<<1, 256, 0, st>>>(B, y, t_dev, loss_dev);
+    k_mlp_fwd<<<(B + 127) / 128, 128, 0, st>>>(params_dev, B, X_dev, y, z1, h1, z2, h2); DMRG_COUNT_LAUNCH();
+    k_mlp_bwd_act<<<(B + 127) / 128, 128, 0, st>>>(params_dev, B, y, t_dev, z1, z2, dy, dz1, dz2); DMRG_COUNT_LAUNCH();
+    k_mlp_grad<<<(MLP_NPARAM + 127) / 128, 128, 0, st>>>(B, X_dev, h1, h2, dy, dz1, dz2, grad_dev); DMRG_COUNT_LAUNCH();
+    k_mlp_loss<<<1, 256, 0, st>>>(B, y, t_dev, loss_dev); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }
@@ -172,7 +172,7 @@ dmrg_status dmrg_mlp_adam(dmrg_ctx *ctx, int n, float *params_dev, const float *
     if (!ctx || !params_dev || !grad_dev || !m_dev || !v_dev || n < 1 || step < 1) return DMRG_EINVAL;
     float bc1 = 1.0f - powf(beta1, (float)step), bc2 = 1.0f - powf(beta2, (float)step);
     k_adam<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, params_dev, grad_dev, m_dev, v_dev, lr, beta1, beta2, eps, bc1,
-                                                     bc2);
+                                                     bc2); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }

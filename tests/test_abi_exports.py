@@ -14,7 +14,7 @@ HEADER = os.path.join(ROOT, "include", "dmrg.h")
 def header_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:dmrg_status|void|int|const char \*)\s*\**\s*(\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:dmrg_status|void|int|long long|const char \*)\s*\**\s*(\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
