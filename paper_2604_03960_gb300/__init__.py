@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import torch
 
@@ -189,9 +190,12 @@ class Context:
         h = C.c_void_p()
         _check(lib().dmrg_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream)), "dmrg_create")
         self.h = h
+        self._states = weakref.WeakSet()
 
     def close(self):
         if getattr(self, "h", None):
+            for st in list(getattr(self, "_states", ())):
+                st.close()
             lib().dmrg_destroy(self.h)
             self.h = None
 
@@ -316,6 +320,7 @@ class State:
         _check(lib().dmrg_state_create(ctx.h, D, C.byref(mp), _ptr(W), C.byref(params), _ptr(mps_init), C.byref(h)),
                "dmrg_state_create")
         self.h = h
+        ctx._states.add(self)
 
     def close(self):
         if getattr(self, "h", None):

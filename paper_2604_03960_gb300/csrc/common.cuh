@@ -160,7 +160,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *words, int *status)
         } else {
             long long spins = 0;
             while (*gen == g) {
-                __nanosleep(100);
+                if (spins > 4096) __nanosleep(64);
                 if (++spins > kSpinLimit) {
                     atomicOr(status, ST_TIMEOUT);
                     ok = 0;

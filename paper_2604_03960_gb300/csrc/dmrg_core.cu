@@ -27,9 +27,10 @@ namespace dmrg {
 namespace {
 
 constexpr int kMaxCh = 32;   // max channels of a mix (4 D for D <= 8)
-// singular values below 2^-17 s_0 are not resolved by the FP32 Jacobi of the
-// mixed form and count as zero there
-constexpr double kMixedRankFloor = 7.62939453125e-06;
+// singular values below 2^-22 s_0 are not resolved by the FP32 Jacobi of the
+// mixed form (rounding theta to FP32 moves every singular value by up to
+// 2^-24 |theta|, Weyl) and count as zero there
+constexpr double kMixedRankFloor = 2.384185791015625e-07;   // 2^-22
 
 // ---------------------------------------------------------------------------
 // MPO (Eq. 18 generalised; lower-triangular, left boundary row D-1, right
@@ -387,6 +388,7 @@ using namespace dmrg;
 // ===========================================================================
 struct dmrg_state {
     dmrg_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;   // copy of ctx->stream (destroy does not touch ctx)
     int N = 0, D = 0;
     dmrg_params p{};
     dmrg_model_params mp{};
@@ -637,6 +639,7 @@ dmrg_status dmrg_state_create(dmrg_ctx *ctx, int D, const dmrg_model_params *mp,
     dmrg_state *st = new (std::nothrow) dmrg_state();
     if (!st) return DMRG_ENOMEM;
     st->ctx = ctx;
+    st->stream = ctx->stream;
     st->N = N;
     st->D = D;
     st->p = *p;
@@ -781,7 +784,7 @@ dmrg_status dmrg_state_create(dmrg_ctx *ctx, int D, const dmrg_model_params *mp,
 void dmrg_state_destroy(dmrg_state *st)
 {
     if (!st) return;
-    cudaStreamSynchronize(st->ctx->stream);
+    cudaStreamSynchronize(st->stream);
     if (st->h_res) cudaFreeHost(st->h_res);
     st->arena.release();
     delete st;

@@ -96,10 +96,23 @@ __device__ __forceinline__ bool block_barrier(unsigned *words, int *status)
     return grid_barrier(words, status);
 }
 
+// F2[0] = sum of squares of all entries (|A|_F^2), for the negligible-vector test
+__global__ void k_frob2(const double *__restrict__ A, long long n, double *F2)
+{
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) a = fma(A[i], A[i], a);
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) F2[0] = a;
+}
+
 __global__ void __launch_bounds__(256) k_jac_sweeps(double *__restrict__ X, double *__restrict__ Vm, int r, int l,
                                                     int max_sweeps, double tol, unsigned *sync, int *status,
-                                                    int *info)
+                                                    int *info, const double *F2, double small)
 {
+    // vectors with |x|^2 below small^2 |A|_F^2 are numerically zero: their
+    // mutual angles are rounding noise and they are never retained
+    const double floor2 = small * small * F2[0];
     const int lane = threadIdx.x & 31;
     const int warps_per_block = blockDim.x >> 5;
     const int gwarp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
@@ -131,7 +144,7 @@ __global__ void __launch_bounds__(256) k_jac_sweeps(double *__restrict__ X, doub
                 a = warp_sum(a);
                 b = warp_sum(b);
                 g = warp_sum(g);
-                if (!(a > 0.0 && b > 0.0)) continue;
+                if (!(a > floor2 && b > floor2)) continue;
                 if (!(fabs(g) > tol * sqrt(a) * sqrt(b))) continue;
                 double zeta = (b - a) / (2.0 * g);
                 double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
@@ -284,8 +297,10 @@ __global__ void k_jac32_load(const double *__restrict__ A, int m, int n, int dir
 }
 
 __global__ void __launch_bounds__(256) k_jac32_sweeps(float *__restrict__ X, int r, int l, int max_sweeps, double tol,
-                                                      unsigned *sync, int *status, int *info)
+                                                      unsigned *sync, int *status, int *info, const double *F2,
+                                                      double small)
 {
+    const double floor2 = small * small * F2[0];
     const int lane = threadIdx.x & 31;
     const int warps_per_block = blockDim.x >> 5;
     const int gwarp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
@@ -321,7 +336,7 @@ __global__ void __launch_bounds__(256) k_jac32_sweeps(float *__restrict__ X, int
                 double a = warp_sum((double)a0 + (double)a1);
                 double b = warp_sum((double)b0 + (double)b1);
                 double g = warp_sum((double)g0 + (double)g1);
-                if (!(a > 0.0 && b > 0.0)) continue;
+                if (!(a > floor2 && b > floor2)) continue;
                 if (!(fabs(g) > tol * sqrt(a) * sqrt(b))) continue;
                 double zeta = (b - a) / (2.0 * g);
                 double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
@@ -362,6 +377,88 @@ __global__ void __launch_bounds__(256) k_jac32_sweeps(float *__restrict__ X, int
         info[0] = converged ? sweep : -sweep;
         if (!converged) atomicOr(status, ST_NOCONV);
     }
+}
+
+// Single-CTA FP32 Jacobi with the vectors resident in shared memory (r*l
+// floats <= kSmemJacFloats): the rounds synchronise with __syncthreads only.
+constexpr int kSmemJacFloats = 50 * 1024;
+
+__global__ void __launch_bounds__(1024) k_jac32_smem(float *__restrict__ Xg, int r, int l, int max_sweeps, double tol,
+                                                     int *status, int *info, const double *F2, double small)
+{
+    extern __shared__ float xs[];
+    __shared__ unsigned rot_count;
+    const long long n = (long long)r * l;
+    for (long long e = threadIdx.x; e < n; e += blockDim.x) xs[e] = Xg[e];
+    const double floor2 = small * small * F2[0];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int rp = r + (r & 1), npairs = rp / 2;
+    int sweep = 0;
+    bool converged = false;
+    __syncthreads();
+    for (; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) rot_count = 0;
+        __syncthreads();
+        unsigned my_rot = 0;
+        for (int t = 0; t < rp - 1; ++t) {
+            for (int p = warp; p < npairs; p += nw) {
+                int i, j;
+                rr_pair(rp, t, p, i, j);
+                if (i >= r || j >= r) continue;
+                float *xi = xs + (long long)i * l, *xj = xs + (long long)j * l;
+                float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f, g0 = 0.f, g1 = 0.f;
+                int k = lane;
+                for (; k + 32 < l; k += 64) {
+                    float u = xi[k], v = xj[k], u2 = xi[k + 32], v2 = xj[k + 32];
+                    a0 = fmaf(u, u, a0); b0 = fmaf(v, v, b0); g0 = fmaf(u, v, g0);
+                    a1 = fmaf(u2, u2, a1); b1 = fmaf(v2, v2, b1); g1 = fmaf(u2, v2, g1);
+                }
+                if (k < l) {
+                    float u = xi[k], v = xj[k];
+                    a0 = fmaf(u, u, a0); b0 = fmaf(v, v, b0); g0 = fmaf(u, v, g0);
+                }
+                double a = warp_sum((double)a0 + (double)a1);
+                double b = warp_sum((double)b0 + (double)b1);
+                double g = warp_sum((double)g0 + (double)g1);
+                if (!(a > floor2 && b > floor2)) continue;
+                if (!(fabs(g) > tol * sqrt(a) * sqrt(b))) continue;
+                double zeta = (b - a) / (2.0 * g);
+                double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double cd = 1.0 / sqrt(1.0 + tt * tt);
+                float c = (float)cd, sn = (float)(cd * tt);
+                for (int q = lane; q < l; q += 32) {
+                    float u = xi[q], v = xj[q];
+                    xi[q] = fmaf(c, u, -sn * v);
+                    xj[q] = fmaf(sn, u, c * v);
+                }
+                if (lane == 0) my_rot++;
+            }
+            __syncthreads();
+        }
+        if (lane == 0 && my_rot) atomicAdd(&rot_count, my_rot);
+        __syncthreads();
+        const unsigned total = rot_count;
+        __syncthreads();
+        if (total == 0u) {
+            converged = true;
+            ++sweep;
+            break;
+        }
+    }
+    for (long long e = threadIdx.x; e < n; e += blockDim.x) Xg[e] = xs[e];
+    if (threadIdx.x == 0) {
+        info[0] = converged ? sweep : -sweep;
+        if (!converged) atomicOr(status, ST_NOCONV);
+    }
+}
+
+__global__ void k_frob2_f(const float *__restrict__ A, long long n, double *F2)
+{
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) a = fma((double)A[i], (double)A[i], a);
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) F2[0] = a;
 }
 
 __global__ void k_jac32_norms(const float *__restrict__ X, int r, int l, double *__restrict__ nrm)
@@ -421,23 +518,29 @@ dmrg_status svd_jacobi(dmrg_ctx *ctx, const double *A, int m, int n, double *U, 
     const double tol = (double)(l > 16 ? l : 16) * 2.220446049250313e-16;
     const int rp = r + (r & 1);
     const int npairs = rp / 2;
+    // GB300's per-SM FP64 rate is low, so even small problems are spread over
+    // several CTAs (one warp per pair) as soon as there are enough pairs
     int threads = 256;
     int blocks = 1;
-    if (r > 128) {
+    if (r > 48) {
         int per_sm = 0;
         DMRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jac_sweeps, threads, 0));
         int maxb = per_sm * ctx->num_sms;
-        blocks = (npairs + 7) / 8;
+        blocks = (npairs + 3) / 4;      // two pairs per warp per round at most
         if (blocks > maxb) blocks = maxb;
         if (blocks < 1) blocks = 1;
     }
     double *X = w.X, *Vm = w.Vm;
     unsigned *sync = w.sync;
     int *status = ctx->d_status;
-    void *args[] = {&X, &Vm, (void *)&r, (void *)&l, &max_sweeps, (void *)&tol, &sync, &status, &d_info};
+    const double *F2 = reinterpret_cast<const double *>(w.sync + 4);
+    const double small = (double)(l > 16 ? l : 16) * 2.220446049250313e-16;
+    k_frob2<<<1, 256, 0, st>>>(X, (long long)r * l, reinterpret_cast<double *>(w.sync + 4)); DMRG_COUNT_LAUNCH();
+    void *args[] = {&X, &Vm, (void *)&r, (void *)&l, &max_sweeps, (void *)&tol, &sync, &status, &d_info, &F2,
+                    (void *)&small};
     prof_mark(ctx, PROF_JACOBI64);
     if (blocks == 1) {
-        k_jac_sweeps<<<1, threads, 0, st>>>(X, Vm, r, l, max_sweeps, tol, sync, status, d_info); DMRG_COUNT_LAUNCH();
+        k_jac_sweeps<<<1, threads, 0, st>>>(X, Vm, r, l, max_sweeps, tol, sync, status, d_info, F2, small); DMRG_COUNT_LAUNCH();
     } else {
         DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_jac_sweeps, dim3(blocks), dim3(threads), args, 0, st)); DMRG_COUNT_LAUNCH();
     }
@@ -499,10 +602,25 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
         if (blocks < 1) blocks = 1;
     }
     int *status = ctx->d_status;
-    void *args[] = {&X, (void *)&r, (void *)&l, &max_sweeps, (void *)&tol, &sync, &status, &d_info};
+    // F2 = |A|_F^2 from the FP32 copy; vectors below 2^-23 |A|_F are dropped anyway
+    const double *F2 = reinterpret_cast<const double *>(sync + 4);
+    const double small = 1.1920928955078125e-07;
+    k_frob2_f<<<1, 256, 0, st>>>(X, (long long)r * l, reinterpret_cast<double *>(sync + 4)); DMRG_COUNT_LAUNCH();
+    void *args[] = {&X, (void *)&r, (void *)&l, &max_sweeps, (void *)&tol, &sync, &status, &d_info, &F2,
+                    (void *)&small};
     prof_mark(ctx, PROF_JACOBI32);
-    if (blocks == 1) {
-        k_jac32_sweeps<<<1, threads, 0, st>>>(X, r, l, max_sweeps, tol, sync, status, d_info);
+    if ((long long)r * l <= kSmemJacFloats) {
+        const int smem = (int)(sizeof(float) * (size_t)r * l);
+        static bool attr = false;
+        if (!attr) {
+            DMRG_CUDA(cudaFuncSetAttribute(k_jac32_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(float) * kSmemJacFloats)));
+            attr = true;
+        }
+        int thr = r >= 64 ? 1024 : (r >= 16 ? 256 : 64);
+        k_jac32_smem<<<1, thr, smem, st>>>(X, r, l, max_sweeps, tol, status, d_info, F2, small);
+    } else if (blocks == 1) {
+        k_jac32_sweeps<<<1, threads, 0, st>>>(X, r, l, max_sweeps, tol, sync, status, d_info, F2, small);
     } else {
         DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_jac32_sweeps, dim3(blocks), dim3(threads), args, 0, st));
     }
