@@ -126,6 +126,8 @@ typedef struct {
 typedef struct {
     int bond, k, chi_ctrl, direction;
     double E, S, trunc_err;
+    int jacobi_sweeps;     /* Jacobi sweeps of the visit's SVD (negative: not converged) */
+    int lanczos_steps;     /* Krylov steps taken                                          */
 } dmrg_visit_record;
 
 /* ---------------------------------------------------------------------- */
@@ -144,6 +146,10 @@ const char *dmrg_status_string(dmrg_status s);
  * the tensor cores even for tiny products), "tc_min_work" (multiply-adds
  * below which 3xTF32 requests run on the FP64 kernel), "tc_bn" (0, 128 or
  * 256: tile width of the tensor-core GEMM, 0 = heuristic),
+ * "mixed_env_tc" (1: environment updates of the 3xTF32 form on the tensor
+ * cores instead of FP64), "svd_prec" (standalone svd_truncate: 0 FP64 Jacobi,
+ * 1 mixed: FP32 Jacobi, FP64-re-orthonormalised isometry, tensor-core
+ * projection for the other factor; values below 2^-22 s_0 are not resolved),
  * "jacobi_max_sweeps" (standalone svd_truncate).  DMRG_EINVAL for an
  * unknown name or value. */
 dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value);

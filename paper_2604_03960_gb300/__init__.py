@@ -68,6 +68,7 @@ class VisitRecord(C.Structure):
     _fields_ = [
         ("bond", C.c_int), ("k", C.c_int), ("chi_ctrl", C.c_int), ("direction", C.c_int),
         ("E", C.c_double), ("S", C.c_double), ("trunc_err", C.c_double),
+        ("jacobi_sweeps", C.c_int), ("lanczos_steps", C.c_int),
     ]
 
 

@@ -112,6 +112,8 @@ struct dmrg_ctx {
     double tc_min_work = 4194304.0;   // M*N*K below which the FP64 kernel is used
     int prof = 0;
     dmrg::ProfSlot prof_slot[dmrg::PROF_KINDS];
+    int mixed_env_tc = 0;        // 1: environment updates of the mixed form on the tensor cores too
+    int svd_prec = 0;            // standalone svd_truncate: 0 FP64 Jacobi, 1 mixed
 };
 
 namespace dmrg {

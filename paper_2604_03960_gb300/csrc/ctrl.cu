@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(DB) k_decide(const double *__restrict__ s, int
                                                dmrg_params p, int do_ctrl, int chi_override, const float *mlp,
                                                int bond, int N, int sweep, const LzState *lz, BondResult *res,
                                                dmrg_visit_record *visit, int direction, double rank_floor,
-                                               int *status)
+                                               const int *jac_info, int *status)
 {
     __shared__ double sh[32];
     __shared__ float h1[MLP_H], h2[MLP_H], xin[MLP_IN], red[2];
@@ -188,6 +188,8 @@ __global__ void __launch_bounds__(DB) k_decide(const double *__restrict__ s, int
             visit->E = br.E;
             visit->S = S;
             visit->trunc_err = br.eps;
+            visit->jacobi_sweeps = jac_info ? jac_info[0] : 0;
+            visit->lanczos_steps = lz ? lz->m : 0;
         }
         if (!isfinite(S) || !isfinite(br.znorm) || br.znorm == 0.0) atomicOr(status, ST_NAN);
     }
@@ -231,11 +233,11 @@ __global__ void k_entropy(int n, const double *__restrict__ s, double *S_out, do
 dmrg_status launch_decide(dmrg_ctx *ctx, const double *s, int r, dmrg_ctrl_state *st_bond, const dmrg_params &p,
                           int do_ctrl, int chi_override, const float *mlp, int bond, int N, int sweep,
                           const void *lz_state, BondResult *res, dmrg_visit_record *visit, int direction,
-                          double rank_floor)
+                          double rank_floor, const int *jac_info)
 {
     k_decide<<<1, DB, 0, ctx->stream>>>(s, r, st_bond, p, do_ctrl, chi_override, mlp, bond, N, sweep,
                                         static_cast<const LzState *>(lz_state), res, visit, direction, rank_floor,
-                                        ctx->d_status); DMRG_COUNT_LAUNCH();
+                                        jac_info, ctx->d_status); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }

@@ -86,7 +86,7 @@ __device__ __forceinline__ int ctrl_step_dev(dmrg_ctrl_state *st, double S, cons
 dmrg_status launch_decide(dmrg_ctx *ctx, const double *s, int r, dmrg_ctrl_state *st_bond, const dmrg_params &p,
                           int do_ctrl, int chi_override, const float *mlp, int bond, int N, int sweep,
                           const void *lz_state, BondResult *res, dmrg_visit_record *visit, int direction,
-                          double rank_floor);
+                          double rank_floor, const int *jac_info = nullptr);
 dmrg_status launch_ctrl_steps(dmrg_ctx *ctx, int n, const double *S, dmrg_ctrl_state *st, const dmrg_params &p,
                               int *chi_out);
 dmrg_status launch_entropy(dmrg_ctx *ctx, int n, const double *s, double *S, double *eps);

@@ -264,6 +264,30 @@ __global__ void k_scale_partials(double *__restrict__ x, long long n, const doub
         x[i] *= inv;
 }
 
+__global__ void k_fill_int(int *p, int v) { *p = v; }
+
+// out[i][j] = in[i][j] / s[i]  (r x n), zero where s[i] == 0
+__global__ void k_scale_rows_inv(const double *__restrict__ in, double *__restrict__ out, int r, int n,
+                                 const double *__restrict__ s)
+{
+    const long long total = (long long)r * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const double v = s[e / n];
+        out[e] = v > 0.0 ? in[e] / v : 0.0;
+    }
+}
+
+// out[i][j] = in[i][j] / s[j]  (m x r)
+__global__ void k_scale_cols_inv(const double *__restrict__ in, double *__restrict__ out, int m, int r,
+                                 const double *__restrict__ s)
+{
+    const long long total = (long long)m * r;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const double v = s[e % r];
+        out[e] = v > 0.0 ? in[e] / v : 0.0;
+    }
+}
+
 int grid1d(long long n, int threads, int num_sms)
 {
     long long b = (n + threads - 1) / threads;
@@ -444,6 +468,12 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         ctx->tc_bn_override = v;
         return DMRG_OK;
     }
+    if (!std::strcmp(name, "mixed_env_tc")) { ctx->mixed_env_tc = value != 0.0; return DMRG_OK; }
+    if (!std::strcmp(name, "svd_prec")) {
+        if (value != 0.0 && value != 1.0) return DMRG_EINVAL;
+        ctx->svd_prec = (int)value;
+        return DMRG_OK;
+    }
     if (!std::strcmp(name, "jacobi_max_sweeps")) {
         if (!(value >= 1.0 && value <= 1000.0)) return DMRG_EINVAL;
         ctx->jacobi_max_sweeps = (int)value;
@@ -561,7 +591,8 @@ static dmrg_status bond_step(dmrg_state *st, int k, int go_right, int do_ctrl, d
         DMRG_TRY(svd_jacobi(ctx, st->theta, m, n, st->U, st->s, st->Vt, st->svdw, st->p.jacobi_max_sweeps,
                             st->d_info));
         DMRG_TRY(launch_decide(ctx, st->s, r, st->ctrl + k, st->p, do_ctrl, 0, mlp, k, st->N, st->sweep_index,
-                               st->lw.lz, st->d_res, visit, direction, (double)r * 2.220446049250313e-16));
+                               st->lw.lz, st->d_res, visit, direction, (double)r * 2.220446049250313e-16,
+                               st->d_info));
         DMRG_CUDA(cudaMemcpyAsync(st->h_res, st->d_res, sizeof(BondResult), cudaMemcpyDeviceToHost, ctx->stream));
         DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
         kk = st->h_res->k;
@@ -584,7 +615,7 @@ static dmrg_status bond_step(dmrg_state *st, int k, int go_right, int do_ctrl, d
         DMRG_TRY(svd_jacobi32(ctx, st->theta, m, n, dir, st->svdw, st->p.jacobi_max_sweeps, st->d_info, st->s, &X32,
                               &nrm, &perm));
         DMRG_TRY(launch_decide(ctx, st->s, r, st->ctrl + k, st->p, do_ctrl, 0, mlp, k, st->N, st->sweep_index,
-                               st->lw.lz, st->d_res, visit, direction, kMixedRankFloor));
+                               st->lw.lz, st->d_res, visit, direction, kMixedRankFloor, st->d_info));
         DMRG_CUDA(cudaMemcpyAsync(st->h_res, st->d_res, sizeof(BondResult), cudaMemcpyDeviceToHost, ctx->stream));
         DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
         kk = st->h_res->k;
@@ -611,12 +642,16 @@ static dmrg_status bond_step(dmrg_state *st, int k, int go_right, int do_ctrl, d
     }
     st->chi[k + 1] = kk;
     double f = 2.0 * m * n * cm + K * matvec_flops(D, cl, cr) + svd_nominal_flops(m, n);
+    // Environments carry the energy of whole blocks and each is built from the
+    // previous one, so FP32-accumulated errors would add up along the chain:
+    // the mixed form keeps them in FP64 unless the context asks otherwise.
+    const int eprec = (prec == DMRG_PREC_3XTF32 && !ctx->mixed_env_tc) ? DMRG_PREC_FP64 : prec;
     if (go_right) {
-        DMRG_TRY(env_left_dev(ctx, prec, D, cl, kk, st->env[k], st->coef_l + (size_t)k * 4 * D * D, st->A[k],
+        DMRG_TRY(env_left_dev(ctx, eprec, D, cl, kk, st->env[k], st->coef_l + (size_t)k * 4 * D * D, st->A[k],
                               st->env[k + 1], st->X, st->Y));
         f += env_flops(D, cl, kk);
     } else if (k + 1 >= 2) {
-        DMRG_TRY(env_right_dev(ctx, prec, D, kk, cr, st->env[k + 2], st->coef_r + (size_t)(k + 1) * 4 * D * D,
+        DMRG_TRY(env_right_dev(ctx, eprec, D, kk, cr, st->env[k + 2], st->coef_r + (size_t)(k + 1) * 4 * D * D,
                                st->A[k + 1], st->env[k + 1], st->X, st->Y));
         f += env_flops(D, cr, kk);
     }
@@ -962,12 +997,83 @@ dmrg_status dmrg_state_set_mlp(dmrg_state *st, const float *params_dev)
 // ---------------------------------------------------------------------------
 // standalone building blocks
 // ---------------------------------------------------------------------------
+// Mixed-precision SVD (context option svd_prec = 1): FP32 Jacobi on the
+// min(m,n) vectors of the longer side, one FP64 Newton-Schulz step on the
+// unit vectors, the other factor as diag(1/s) (isometry^T theta) on the
+// tensor cores.  Singular values below 2^-22 s_0 are not resolved.
+static dmrg_status svd_mixed_full(dmrg_ctx *ctx, const double *A, int m, int n, double *U, double *s, double *Vt,
+                                  BondResult *res, int *info)
+{
+    const int dir = (n <= m) ? 0 : 1;          // vectors = columns (length m) or rows (length n)
+    const int r = std::min(m, n), len = dir == 0 ? m : n;
+    const size_t w1 = al256(jac32_work_bytes(dir == 0 ? n : m, len));
+    const size_t need = w1 + 3 * al256(sizeof(double) * (size_t)r * len) + al256(sizeof(double) * (size_t)r * r) +
+                        al256(sizeof(double) * 512) + al256(sizeof(int) * 4);
+    DMRG_TRY(ctx->work3.ensure(need));
+    char *b = ctx->work3.as<char>();
+    void *jw = b; b += w1;
+    double *Q = reinterpret_cast<double *>(b); b += al256(sizeof(double) * (size_t)r * len);
+    double *T = reinterpret_cast<double *>(b); b += al256(sizeof(double) * (size_t)r * len);
+    double *P = reinterpret_cast<double *>(b); b += al256(sizeof(double) * (size_t)r * len);
+    double *E = reinterpret_cast<double *>(b); b += al256(sizeof(double) * (size_t)r * r);
+    int *rdev = reinterpret_cast<int *>(b);
+    float *X32;
+    double *nrm;
+    int *perm;
+    DMRG_TRY(svd_jacobi32(ctx, A, m, n, dir, jw, ctx->jacobi_max_sweeps, info, s, &X32, &nrm, &perm));
+    // all r vectors
+    (void)res;
+    k_fill_int<<<1, 1, 0, ctx->stream>>>(rdev, r); DMRG_COUNT_LAUNCH();
+    DMRG_TRY(gather_unit_vectors(ctx, X32, nrm, perm, rdev, r, len, Q));
+    DMRG_TRY(gemm_f64(ctx->stream, r, r, len, 1.0, Q, len, 1, 0, Q, 1, len, 0, 0.0, E, r, 1, 0, 1));
+    DMRG_CUDA(cudaMemcpyAsync(T, Q, sizeof(double) * (size_t)r * len, cudaMemcpyDeviceToDevice, ctx->stream));
+    DMRG_TRY(gemm_f64(ctx->stream, r, len, r, -0.5, E, r, 1, 0, Q, len, 1, 0, 1.5, T, len, 1, 0, 1));
+    if (dir == 0) {
+        // U = T^T (m x r); Vt = diag(1/s) T A  (r x n)
+        k_transpose_rect<<<dim3((m + 31) / 32, (r + 31) / 32), dim3(32, 8), 0, ctx->stream>>>(T, U, r, m); DMRG_COUNT_LAUNCH();
+        DMRG_TRY(gemm(ctx, DMRG_PREC_3XTF32, r, n, m, 1.0, T, m, 1, 0, A, n, 1, 0, 0.0, P, n, 1, 0, 1));
+        k_scale_rows_inv<<<grid1d((long long)r * n, 256, ctx->num_sms), 256, 0, ctx->stream>>>(P, Vt, r, n, s); DMRG_COUNT_LAUNCH();
+    } else {
+        // Vt = T (r x n); U = A T^T diag(1/s)  (m x r)
+        DMRG_CUDA(cudaMemcpyAsync(Vt, T, sizeof(double) * (size_t)r * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        DMRG_TRY(gemm(ctx, DMRG_PREC_3XTF32, m, r, n, 1.0, A, n, 1, 0, T, 1, n, 0, 0.0, P, r, 1, 0, 1));
+        k_scale_cols_inv<<<grid1d((long long)m * r, 256, ctx->num_sms), 256, 0, ctx->stream>>>(P, U, m, r, s); DMRG_COUNT_LAUNCH();
+    }
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
 dmrg_status svd_truncate(dmrg_ctx *ctx, const double *theta_dev, int m, int n, int chi_max, double eps, double *U_dev,
                          double *s_dev, double *Vt_dev, int *k_out, double *S_out, double *trunc_err_out)
 {
     if (!ctx || !theta_dev || !U_dev || !s_dev || !Vt_dev || m < 1 || n < 1 || chi_max < 1 || !(eps >= 0.0))
         return DMRG_EINVAL;
     const int r = std::min(m, n), l = std::max(m, n);
+    if (ctx->svd_prec == 1) {
+        if (!tc_available(ctx)) return DMRG_EUNSUPPORTED;
+        DMRG_TRY(ctx->work.ensure(al256(sizeof(BondResult)) + al256(sizeof(int) * 4)));
+        BondResult *res = reinterpret_cast<BondResult *>(ctx->work.as<char>());
+        int *info = reinterpret_cast<int *>(ctx->work.as<char>() + al256(sizeof(BondResult)));
+        DMRG_TRY(svd_mixed_full(ctx, theta_dev, m, n, U_dev, s_dev, Vt_dev, res, info));
+        dmrg_params p{};
+        p.eps_trunc = eps;
+        p.chi_min = 1;
+        p.chi_max = chi_max;
+        p.ctrl = DMRG_CTRL_FIXED;
+        DMRG_TRY(launch_decide(ctx, s_dev, r, nullptr, p, 0, chi_max, nullptr, 0, 1, 0, nullptr, res, nullptr, 0,
+                               kMixedRankFloor));
+        DMRG_CUDA(cudaMemcpyAsync(ctx->h_pinned_d, res, sizeof(BondResult), cudaMemcpyDeviceToHost, ctx->stream));
+        DMRG_CUDA(cudaMemcpyAsync(ctx->h_pinned_i + 32, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
+        BondResult br;
+        std::memcpy(&br, ctx->h_pinned_d, sizeof(BondResult));
+        if (k_out) *k_out = br.k;
+        if (S_out) *S_out = br.S;
+        if (trunc_err_out) *trunc_err_out = br.eps;
+        dmrg_status ds = dmrg_get_status(ctx);
+        if (ctx->h_pinned_i[32] < 0) return DMRG_ENOCONV;
+        return ds == DMRG_ENOCONV ? DMRG_OK : ds;
+    }
     size_t need = al256(svd_work_bytes(r, l)) + al256(sizeof(BondResult)) + al256(sizeof(int) * 4);
     DMRG_TRY(ctx->work.ensure(need));
     char *base = ctx->work.as<char>();
