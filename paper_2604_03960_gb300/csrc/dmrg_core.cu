@@ -239,6 +239,20 @@ __global__ void k_transpose_rect(const double *__restrict__ in, double *__restri
     }
 }
 
+// E = x.y / x.x into a Lanczos state (FP64 Rayleigh quotient), single block
+__global__ void k_rayleigh(const double *__restrict__ x, const double *__restrict__ y, long long n, LzState *lz)
+{
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        a = fma(x[i], y[i], a);
+        b = fma(x[i], x[i], b);
+    }
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    if (threadIdx.x == 0 && b > 0.0) lz->E = a / b;
+}
+
 // two-pass deterministic normalisation of a vector to unit 2-norm
 constexpr int kNormBlocks = 256;
 __global__ void k_sumsq_partial(const double *__restrict__ x, long long n, double *__restrict__ part)
@@ -584,6 +598,14 @@ static dmrg_status bond_step(dmrg_state *st, int k, int go_right, int do_ctrl, d
     };
     const int K = (int)std::min<long long>(st->K, nn);
     DMRG_TRY(lanczos_run(ctx, st->lw, nn, K, st->theta, mv));
+    if (prec != DMRG_PREC_FP64 && k == 0 && direction == -1) {
+        // last visit of a sweep: the sweep energy is the FP64 Rayleigh
+        // quotient of the Ritz vector (second order in its error), so the
+        // FP32 accumulation of the tensor-core matvecs does not reach it
+        DMRG_TRY(heff_apply_dev(ctx, DMRG_PREC_FP64, D, cl, cr, L, Rt, C, st->X, st->Y, st->theta, st->lw.w));
+        k_rayleigh<<<1, 256, 0, ctx->stream>>>(st->theta, st->lw.w, nn, st->lw.lz); DMRG_COUNT_LAUNCH();
+        DMRG_CUDA(cudaGetLastError());
+    }
     const float *mlp = st->has_mlp ? st->mlp : nullptr;
     int kk;
     if (prec == DMRG_PREC_FP64) {

@@ -17,6 +17,7 @@
 #include "common.cuh"
 
 #include <cooperative_groups.h>
+#include <algorithm>
 
 namespace dmrg {
 
@@ -452,6 +453,155 @@ __global__ void __launch_bounds__(1024) k_jac32_smem(float *__restrict__ Xg, int
     }
 }
 
+// Blocked FP32 Jacobi: the vectors are grouped in blocks of BW; a sweep
+// pairs the blocks in round-robin order, and the CTA that owns a block pair
+// loads its 2 BW vectors into shared memory and applies one inner sweep of
+// plane rotations over every pair among them before writing them back.  The
+// grid barrier is paid once per block round, and each vector crosses L2 once
+// per block round instead of once per vector round.
+template <int BW>
+__global__ void __launch_bounds__(256) k_bjac32(float *__restrict__ X, int r, int l, int max_sweeps, double tol,
+                                                unsigned *sync, int *status, int *info, const double *F2, double small)
+{
+    extern __shared__ float xs[];            // [2 BW][l]
+    __shared__ int vid[2 * BW];
+    __shared__ unsigned block_rot;
+    const double floor2 = small * small * F2[0];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nb = (r + BW - 1) / BW;
+    const int nbp = nb + (nb & 1);
+    const int npairs = nbp / 2;
+    unsigned *barrier = sync;
+    unsigned *rotc = sync + 2;
+    int sweep = 0;
+    bool converged = false;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) block_rot = 0;
+        __syncthreads();
+        unsigned my_rot = 0;
+        for (int t = 0; t < nbp - 1; ++t) {
+            for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
+                int I, J;
+                rr_pair(nbp, t, p, I, J);
+                if (threadIdx.x < 2 * BW) {
+                    const int blk = threadIdx.x < BW ? I : J;
+                    const int v = blk * BW + (threadIdx.x % BW);
+                    vid[threadIdx.x] = (blk < nb && v < r) ? v : -1;
+                }
+                __syncthreads();
+                // load
+                for (int q = warp; q < 2 * BW; q += nw) {
+                    const int v = vid[q];
+                    float *dst = xs + (long long)q * l;
+                    if (v >= 0) {
+                        const float *src = X + (long long)v * l;
+                        for (int e = lane; e < l; e += 32) dst[e] = src[e];
+                    }
+                }
+                __syncthreads();
+                // one inner sweep: round-robin over the 2 BW local vectors
+                constexpr int nv = 2 * BW;
+                for (int u = 0; u < nv - 1; ++u) {
+                    for (int pp = warp; pp < BW; pp += nw) {
+                        int a_, b_;
+                        rr_pair(nv, u, pp, a_, b_);
+                        if (vid[a_] < 0 || vid[b_] < 0) continue;
+                        float *xi = xs + (long long)a_ * l, *xj = xs + (long long)b_ * l;
+                        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f, g0 = 0.f, g1 = 0.f;
+                        int k = lane;
+                        for (; k + 32 < l; k += 64) {
+                            float x0 = xi[k], y0 = xj[k], x1 = xi[k + 32], y1 = xj[k + 32];
+                            a0 = fmaf(x0, x0, a0); b0 = fmaf(y0, y0, b0); g0 = fmaf(x0, y0, g0);
+                            a1 = fmaf(x1, x1, a1); b1 = fmaf(y1, y1, b1); g1 = fmaf(x1, y1, g1);
+                        }
+                        if (k < l) {
+                            float x0 = xi[k], y0 = xj[k];
+                            a0 = fmaf(x0, x0, a0); b0 = fmaf(y0, y0, b0); g0 = fmaf(x0, y0, g0);
+                        }
+                        const double a = warp_sum((double)a0 + (double)a1);
+                        const double b = warp_sum((double)b0 + (double)b1);
+                        const double g = warp_sum((double)g0 + (double)g1);
+                        if (!(a > floor2 && b > floor2)) continue;
+                        if (!(fabs(g) > tol * sqrt(a) * sqrt(b))) continue;
+                        const double zeta = (b - a) / (2.0 * g);
+                        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                        const double cd = 1.0 / sqrt(1.0 + tt * tt);
+                        const float c = (float)cd, sn = (float)(cd * tt);
+                        for (int q = lane; q < l; q += 32) {
+                            const float x0 = xi[q], y0 = xj[q];
+                            xi[q] = fmaf(c, x0, -sn * y0);
+                            xj[q] = fmaf(sn, x0, c * y0);
+                        }
+                        if (lane == 0) my_rot++;
+                    }
+                    __syncthreads();
+                }
+                // store
+                for (int q = warp; q < 2 * BW; q += nw) {
+                    const int v = vid[q];
+                    if (v >= 0) {
+                        const float *src = xs + (long long)q * l;
+                        float *dst = X + (long long)v * l;
+                        for (int e = lane; e < l; e += 32) dst[e] = src[e];
+                    }
+                }
+                __syncthreads();
+            }
+            if (!block_barrier(barrier, status)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
+                return;
+            }
+        }
+        if (lane == 0 && my_rot) atomicAdd(&block_rot, my_rot);
+        __syncthreads();
+        if (threadIdx.x == 0 && block_rot) atomicAdd(&rotc[sweep & 1], block_rot);
+        if (!block_barrier(barrier, status)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
+            return;
+        }
+        const unsigned total = *(volatile unsigned *)&rotc[sweep & 1];
+        if (blockIdx.x == 0 && threadIdx.x == 0) rotc[(sweep + 1) & 1] = 0u;
+        if (total == 0u) {
+            converged = true;
+            ++sweep;
+            break;
+        }
+        if (!block_barrier(barrier, status)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
+            return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        info[0] = converged ? sweep : -sweep;
+        if (!converged) atomicOr(status, ST_NOCONV);
+    }
+}
+
+template <int BW>
+dmrg_status launch_bjac32(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps, double tol, unsigned *sync,
+                          int *d_info, const double *F2, double small)
+{
+    const size_t smem = sizeof(float) * 2 * BW * (size_t)l;
+    static size_t attr = 0;
+    if (attr < smem) {
+        DMRG_CUDA(cudaFuncSetAttribute(k_bjac32<BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = smem;
+    }
+    int per_sm = 0;
+    DMRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjac32<BW>, 256, smem));
+    if (per_sm < 1) return DMRG_EUNSUPPORTED;
+    const int nb = (r + BW - 1) / BW;
+    const int npairs = (nb + (nb & 1)) / 2;
+    int blocks = std::min(npairs, per_sm * ctx->num_sms);
+    if (blocks < 1) blocks = 1;
+    int *status = ctx->d_status;
+    void *args[] = {&X, (void *)&r, (void *)&l, &max_sweeps, (void *)&tol, &sync, &status, &d_info, (void *)&F2,
+                    (void *)&small};
+    DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_bjac32<BW>, dim3(blocks), dim3(256), args, smem,
+                                          ctx->stream)); DMRG_COUNT_LAUNCH();
+    return DMRG_OK;
+}
+
 __global__ void k_frob2_f(const float *__restrict__ A, long long n, double *F2)
 {
     __shared__ double sh[32];
@@ -481,16 +631,17 @@ __global__ void k_sorted_values(const double *__restrict__ nrm, const int *__res
 
 // Q[j][t] = X[perm[j]][t] / nrm[perm[j]]  (FP64), j < k
 __global__ void k_gather_unit(const float *__restrict__ X, const double *__restrict__ nrm, const int *__restrict__ perm,
-                              const int *__restrict__ kdev, int l, double *__restrict__ Q)
+                              const int *__restrict__ kdev, int l, double *__restrict__ Q, double rel_floor)
 {
     const int k = *kdev;
+    const double cut = rel_floor * nrm[perm[0]];   // unresolved vectors are returned as zero
     const long long total = (long long)k * l;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
         const int j = (int)(e / l), t = (int)(e % l);
         const int i = perm[j];
         const double nv = nrm[i];
-        Q[e] = nv > 0.0 ? (double)X[(long long)i * l + t] / nv : 0.0;
+        Q[e] = nv > cut ? (double)X[(long long)i * l + t] / nv : 0.0;
     }
 }
 
@@ -619,12 +770,26 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
         }
         int thr = r >= 64 ? 1024 : (r >= 16 ? 256 : 64);
         k_jac32_smem<<<1, thr, smem, st>>>(X, r, l, max_sweeps, tol, status, d_info, F2, small);
-    } else if (blocks == 1) {
-        k_jac32_sweeps<<<1, threads, 0, st>>>(X, r, l, max_sweeps, tol, sync, status, d_info, F2, small);
+        DMRG_COUNT_LAUNCH();
     } else {
-        DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_jac32_sweeps, dim3(blocks), dim3(threads), args, 0, st));
+        // blocked form: block width so that about one block pair per SM is
+        // available each round and 2 BW vectors fit in shared memory
+        const long long cap = (200LL * 1024) / (8LL * l);      // max BW for shared memory
+        int bw = 1;
+        while (bw < 16 && 2LL * bw <= cap && (r / (2 * bw)) > ctx->num_sms) bw *= 2;
+        while (bw > 1 && (long long)bw > cap) bw /= 2;
+        (void)args;
+        (void)blocks;
+        dmrg_status e;
+        switch (bw) {
+        case 16: e = launch_bjac32<16>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small); break;
+        case 8: e = launch_bjac32<8>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small); break;
+        case 4: e = launch_bjac32<4>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small); break;
+        case 2: e = launch_bjac32<2>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small); break;
+        default: e = launch_bjac32<1>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small); break;
+        }
+        if (e != DMRG_OK) return e;
     }
-    DMRG_COUNT_LAUNCH();
     prof_mark(ctx, PROF_JACOBI32);
     {
         const double M_ = l > r ? l : r, N_ = l > r ? r : l;
@@ -650,7 +815,7 @@ dmrg_status gather_unit_vectors(dmrg_ctx *ctx, const float *X, const double *nrm
     long long b = (total + 255) / 256;
     if (b > ctx->num_sms * 8LL) b = ctx->num_sms * 8LL;
     if (b < 1) b = 1;
-    k_gather_unit<<<(int)b, 256, 0, ctx->stream>>>(X, nrm, perm, kdev, l, Q); DMRG_COUNT_LAUNCH();
+    k_gather_unit<<<(int)b, 256, 0, ctx->stream>>>(X, nrm, perm, kdev, l, Q, 2.384185791015625e-07); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }
