@@ -363,11 +363,10 @@ class State:
     def site(self, i: int) -> torch.Tensor:
         """Copy of site tensor i (chi_i x 2 x chi_{i+1})."""
         chi = self.chi()
-        p = C.c_void_p()
-        _check(lib().dmrg_state_site(self.h, i, C.byref(p)), "dmrg_state_site")
-        shape = (chi[i], 2, chi[i + 1])
-        torch.cuda.synchronize(self.ctx.device)
-        return torch.as_tensor(_DevView(p.value, shape), device=f"cuda:{self.ctx.device}").clone()
+        flat = torch.empty(self.mps_size(), dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        self.get_mps(flat)
+        off = sum(chi[j] * 2 * chi[j + 1] for j in range(i))
+        return flat[off: off + chi[i] * 2 * chi[i + 1]].view(chi[i], 2, chi[i + 1]).clone()
 
     def mps_size(self) -> int:
         return int(lib().dmrg_state_mps_size(self.h))
@@ -388,8 +387,3 @@ def launch_count() -> int:
     return int(lib().dmrg_launch_count())
 
 
-class _DevView:
-    """Read-only view of a library-owned FP64 device buffer (CUDA array interface)."""
-
-    def __init__(self, ptr: int, shape):
-        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (ptr, True), "version": 3}

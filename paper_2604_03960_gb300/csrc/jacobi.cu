@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(256) k_bjac32(float *__restrict__ X, int r, in
 {
     extern __shared__ float xs[];            // [2 BW][l]
     __shared__ int vid[2 * BW];
-    __shared__ unsigned block_rot;
+    __shared__ unsigned block_rot, inner_rot;
     const double floor2 = small * small * F2[0];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nb = (r + BW - 1) / BW;
@@ -499,8 +499,12 @@ __global__ void __launch_bounds__(256) k_bjac32(float *__restrict__ X, int r, in
                     }
                 }
                 __syncthreads();
-                // one inner sweep: round-robin over the 2 BW local vectors
+                // inner sweeps (up to 3, stopping when one does not rotate):
+                // round-robin over the 2 BW local vectors
                 constexpr int nv = 2 * BW;
+                for (int inner = 0; inner < 3; ++inner) {
+                if (threadIdx.x == 0) inner_rot = 0;
+                __syncthreads();
                 for (int u = 0; u < nv - 1; ++u) {
                     for (int pp = warp; pp < BW; pp += nw) {
                         int a_, b_;
@@ -532,9 +536,13 @@ __global__ void __launch_bounds__(256) k_bjac32(float *__restrict__ X, int r, in
                             xi[q] = fmaf(c, x0, -sn * y0);
                             xj[q] = fmaf(sn, x0, c * y0);
                         }
-                        if (lane == 0) my_rot++;
+                        if (lane == 0) { my_rot++; atomicAdd(&inner_rot, 1u); }
                     }
                     __syncthreads();
+                }
+                const unsigned ir = inner_rot;
+                __syncthreads();
+                if (ir == 0u || BW == 1) break;
                 }
                 // store
                 for (int q = warp; q < 2 * BW; q += nw) {
@@ -611,7 +619,10 @@ __global__ void k_frob2_f(const float *__restrict__ A, long long n, double *F2)
     if (threadIdx.x == 0) F2[0] = a;
 }
 
-__global__ void k_jac32_norms(const float *__restrict__ X, int r, int l, double *__restrict__ nrm)
+// vectors shorter than 2^-22 |A|_F are unresolved after the FP32 rounding of
+// A (Weyl) and were not orthogonalised (pairs below 2^-23 |A|_F are skipped):
+// their norm is reported as zero so they sort last and are never retained
+__global__ void k_jac32_norms(const float *__restrict__ X, int r, int l, double *__restrict__ nrm, const double *F2)
 {
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (w >= r) return;
@@ -619,7 +630,8 @@ __global__ void k_jac32_norms(const float *__restrict__ X, int r, int l, double 
     double a = 0.0;
     for (int k = lane; k < l; k += 32) a = fma((double)x[k], (double)x[k], a);
     a = warp_sum(a);
-    if (lane == 0) nrm[w] = sqrt(a);
+    const double cut = 2.384185791015625e-07 * sqrt(F2[0]);
+    if (lane == 0) nrm[w] = sqrt(a) > cut ? sqrt(a) : 0.0;
 }
 
 __global__ void k_sorted_values(const double *__restrict__ nrm, const int *__restrict__ perm, int r_out,
@@ -738,9 +750,10 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
         k_jac32_load<<<grid, dim3(32, 8), 0, st>>>(A, m, n, dir, r, l, X, sync); DMRG_COUNT_LAUNCH();
         DMRG_CUDA(cudaGetLastError());
     }
-    // FP32 storage resolves orthogonality to a few units of 2^-24; rotate while
-    // the cosine exceeds 2^-18 (the cross-lane FP64 sums keep the test clean)
-    const double tol = 3.814697265625e-06;
+    // rotate while the cosine exceeds 1e-5: FP32 dot products over a few
+    // thousand terms are good to ~1e-6, and the FP64 Newton-Schulz step that
+    // follows takes the retained vectors from 1e-5 to ~1e-10
+    const double tol = 1.0e-5;
     const int rp = r + (r & 1);
     const int npairs = rp / 2;
     int threads = 256, blocks = 1;
@@ -774,9 +787,11 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
     } else {
         // blocked form: block width so that about one block pair per SM is
         // available each round and 2 BW vectors fit in shared memory
+        // each grid barrier costs a few microseconds with ~100 CTAs arriving,
+        // so aim for ~48 block pairs per round: fewer, heavier rounds
         const long long cap = (200LL * 1024) / (8LL * l);      // max BW for shared memory
         int bw = 1;
-        while (bw < 16 && 2LL * bw <= cap && (r / (2 * bw)) > ctx->num_sms) bw *= 2;
+        while (bw < 16 && 2LL * bw <= cap && (r / (2 * bw)) > 48) bw *= 2;
         while (bw > 1 && (long long)bw > cap) bw /= 2;
         (void)args;
         (void)blocks;
@@ -797,7 +812,7 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
                    4.0 * (double)r * l * 2.0);
     }
     DMRG_CUDA(cudaGetLastError());
-    k_jac32_norms<<<(r * 32 + 255) / 256, 256, 0, st>>>(X, r, l, nrm); DMRG_COUNT_LAUNCH();
+    k_jac32_norms<<<(r * 32 + 255) / 256, 256, 0, st>>>(X, r, l, nrm, F2); DMRG_COUNT_LAUNCH();
     k_jac_rank<<<(r + 255) / 256, 256, 0, st>>>(nrm, r, perm); DMRG_COUNT_LAUNCH();
     const int r_out = m < n ? m : n;
     k_sorted_values<<<(r_out + 255) / 256, 256, 0, st>>>(nrm, perm, r_out, s_sorted); DMRG_COUNT_LAUNCH();
