@@ -150,7 +150,9 @@ const char *dmrg_status_string(dmrg_status s);
  * cores instead of FP64), "svd_prec" (standalone svd_truncate: 0 FP64 Jacobi,
  * 1 mixed: FP32 Jacobi, FP64-re-orthonormalised isometry, tensor-core
  * projection for the other factor; values below 2^-22 s_0 are not resolved),
- * "jacobi_max_sweeps" (standalone svd_truncate).  DMRG_EINVAL for an
+ * "bjac_pairs" / "bjac_inner" (blocked FP32 Jacobi: target block pairs per
+ * round, inner sweeps per block pair), "jacobi_max_sweeps" (standalone
+ * svd_truncate).  DMRG_EINVAL for an
  * unknown name or value. */
 dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value);
 /* Bond dimension D of the MPO of `model` (5, 8, 3), or -1. */

@@ -114,6 +114,8 @@ struct dmrg_ctx {
     dmrg::ProfSlot prof_slot[dmrg::PROF_KINDS];
     int mixed_env_tc = 0;        // 1: environment updates of the mixed form on the tensor cores too
     int svd_prec = 0;            // standalone svd_truncate: 0 FP64 Jacobi, 1 mixed
+    int bjac_pairs = 152;        // blocked FP32 Jacobi: target block pairs per round
+    int bjac_inner = 1;          // blocked FP32 Jacobi: max inner sweeps per block pair
 };
 
 namespace dmrg {

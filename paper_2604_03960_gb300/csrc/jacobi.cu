@@ -88,6 +88,26 @@ __device__ __forceinline__ void rr_pair(int rp, int t, int p, int &i, int &j)
     }
 }
 
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Rotation for the pair with Gram entries (a, b, g), all FP32 (the FP32 path
+// rotates FP32 data, and GB300's FP64 pipe is far too narrow to evaluate
+// square roots and divisions on every lane).  Returns false if none needed.
+__device__ __forceinline__ bool rot32(float a, float b, float g, float floor2, float tol, float &c, float &sn)
+{
+    if (!(a > floor2 && b > floor2)) return false;
+    if (!(fabsf(g) > tol * sqrtf(a) * sqrtf(b))) return false;
+    const float zeta = (b - a) / (2.0f * g);
+    const float tt = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+    c = rsqrtf(fmaf(tt, tt, 1.0f));
+    sn = c * tt;
+    return true;
+}
+
 __device__ __forceinline__ bool block_barrier(unsigned *words, int *status)
 {
     if (gridDim.x == 1) {
@@ -147,9 +167,17 @@ __global__ void __launch_bounds__(256) k_jac_sweeps(double *__restrict__ X, doub
                 g = warp_sum(g);
                 if (!(a > floor2 && b > floor2)) continue;
                 if (!(fabs(g) > tol * sqrt(a) * sqrt(b))) continue;
-                double zeta = (b - a) / (2.0 * g);
-                double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
+                // rotation parameters on one lane, broadcast (FP64 square roots
+                // and divisions are expensive on GB300)
+                double c = 0.0, s = 0.0;
+                if (lane == 0) {
+                    double zeta = (b - a) / (2.0 * g);
+                    double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    c = 1.0 / sqrt(1.0 + tt * tt);
+                    s = c * tt;
+                }
+                c = __shfl_sync(0xffffffffu, c, 0);
+                s = __shfl_sync(0xffffffffu, s, 0);
                 for (int k = lane; k < l; k += 32) {
                     double u = xi[k], v = xj[k];
                     xi[k] = c * u - s * v;
@@ -301,7 +329,7 @@ __global__ void __launch_bounds__(256) k_jac32_sweeps(float *__restrict__ X, int
                                                       unsigned *sync, int *status, int *info, const double *F2,
                                                       double small)
 {
-    const double floor2 = small * small * F2[0];
+    const float floor2f = (float)(small * small * F2[0]), tolf = (float)tol;
     const int lane = threadIdx.x & 31;
     const int warps_per_block = blockDim.x >> 5;
     const int gwarp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
@@ -334,15 +362,9 @@ __global__ void __launch_bounds__(256) k_jac32_sweeps(float *__restrict__ X, int
                     float u = xi[k], v = xj[k];
                     a0 = fmaf(u, u, a0); b0 = fmaf(v, v, b0); g0 = fmaf(u, v, g0);
                 }
-                double a = warp_sum((double)a0 + (double)a1);
-                double b = warp_sum((double)b0 + (double)b1);
-                double g = warp_sum((double)g0 + (double)g1);
-                if (!(a > floor2 && b > floor2)) continue;
-                if (!(fabs(g) > tol * sqrt(a) * sqrt(b))) continue;
-                double zeta = (b - a) / (2.0 * g);
-                double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                double cd = 1.0 / sqrt(1.0 + tt * tt);
-                float c = (float)cd, s = (float)(cd * tt);
+                const float a = warp_sum_f(a0 + a1), b = warp_sum_f(b0 + b1), g = warp_sum_f(g0 + g1);
+                float c, s;
+                if (!rot32(a, b, g, floor2f, tolf, c, s)) continue;
                 for (int q = lane; q < l; q += 32) {
                     float u = xi[q], v = xj[q];
                     xi[q] = fmaf(c, u, -s * v);
@@ -391,7 +413,7 @@ __global__ void __launch_bounds__(1024) k_jac32_smem(float *__restrict__ Xg, int
     __shared__ unsigned rot_count;
     const long long n = (long long)r * l;
     for (long long e = threadIdx.x; e < n; e += blockDim.x) xs[e] = Xg[e];
-    const double floor2 = small * small * F2[0];
+    const float floor2f = (float)(small * small * F2[0]), tolf = (float)tol;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int rp = r + (r & 1), npairs = rp / 2;
     int sweep = 0;
@@ -418,15 +440,9 @@ __global__ void __launch_bounds__(1024) k_jac32_smem(float *__restrict__ Xg, int
                     float u = xi[k], v = xj[k];
                     a0 = fmaf(u, u, a0); b0 = fmaf(v, v, b0); g0 = fmaf(u, v, g0);
                 }
-                double a = warp_sum((double)a0 + (double)a1);
-                double b = warp_sum((double)b0 + (double)b1);
-                double g = warp_sum((double)g0 + (double)g1);
-                if (!(a > floor2 && b > floor2)) continue;
-                if (!(fabs(g) > tol * sqrt(a) * sqrt(b))) continue;
-                double zeta = (b - a) / (2.0 * g);
-                double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                double cd = 1.0 / sqrt(1.0 + tt * tt);
-                float c = (float)cd, sn = (float)(cd * tt);
+                const float a = warp_sum_f(a0 + a1), b = warp_sum_f(b0 + b1), g = warp_sum_f(g0 + g1);
+                float c, sn;
+                if (!rot32(a, b, g, floor2f, tolf, c, sn)) continue;
                 for (int q = lane; q < l; q += 32) {
                     float u = xi[q], v = xj[q];
                     xi[q] = fmaf(c, u, -sn * v);
@@ -461,12 +477,13 @@ __global__ void __launch_bounds__(1024) k_jac32_smem(float *__restrict__ Xg, int
 // per block round instead of once per vector round.
 template <int BW>
 __global__ void __launch_bounds__(256) k_bjac32(float *__restrict__ X, int r, int l, int max_sweeps, double tol,
-                                                unsigned *sync, int *status, int *info, const double *F2, double small)
+                                                unsigned *sync, int *status, int *info, const double *F2, double small,
+                                                int max_inner)
 {
     extern __shared__ float xs[];            // [2 BW][l]
     __shared__ int vid[2 * BW];
     __shared__ unsigned block_rot, inner_rot;
-    const double floor2 = small * small * F2[0];
+    const float floor2f = (float)(small * small * F2[0]), tolf = (float)tol;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nb = (r + BW - 1) / BW;
     const int nbp = nb + (nb & 1);
@@ -502,7 +519,7 @@ __global__ void __launch_bounds__(256) k_bjac32(float *__restrict__ X, int r, in
                 // inner sweeps (up to 3, stopping when one does not rotate):
                 // round-robin over the 2 BW local vectors
                 constexpr int nv = 2 * BW;
-                for (int inner = 0; inner < 3; ++inner) {
+                for (int inner = 0; inner < max_inner; ++inner) {
                 if (threadIdx.x == 0) inner_rot = 0;
                 __syncthreads();
                 for (int u = 0; u < nv - 1; ++u) {
@@ -522,15 +539,9 @@ __global__ void __launch_bounds__(256) k_bjac32(float *__restrict__ X, int r, in
                             float x0 = xi[k], y0 = xj[k];
                             a0 = fmaf(x0, x0, a0); b0 = fmaf(y0, y0, b0); g0 = fmaf(x0, y0, g0);
                         }
-                        const double a = warp_sum((double)a0 + (double)a1);
-                        const double b = warp_sum((double)b0 + (double)b1);
-                        const double g = warp_sum((double)g0 + (double)g1);
-                        if (!(a > floor2 && b > floor2)) continue;
-                        if (!(fabs(g) > tol * sqrt(a) * sqrt(b))) continue;
-                        const double zeta = (b - a) / (2.0 * g);
-                        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                        const double cd = 1.0 / sqrt(1.0 + tt * tt);
-                        const float c = (float)cd, sn = (float)(cd * tt);
+                        const float a = warp_sum_f(a0 + a1), b = warp_sum_f(b0 + b1), g = warp_sum_f(g0 + g1);
+                        float c, sn;
+                        if (!rot32(a, b, g, floor2f, tolf, c, sn)) continue;
                         for (int q = lane; q < l; q += 32) {
                             const float x0 = xi[q], y0 = xj[q];
                             xi[q] = fmaf(c, x0, -sn * y0);
@@ -589,6 +600,7 @@ template <int BW>
 dmrg_status launch_bjac32(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps, double tol, unsigned *sync,
                           int *d_info, const double *F2, double small)
 {
+    int max_inner = ctx->bjac_inner;
     const size_t smem = sizeof(float) * 2 * BW * (size_t)l;
     static size_t attr = 0;
     if (attr < smem) {
@@ -604,7 +616,7 @@ dmrg_status launch_bjac32(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps,
     if (blocks < 1) blocks = 1;
     int *status = ctx->d_status;
     void *args[] = {&X, (void *)&r, (void *)&l, &max_sweeps, (void *)&tol, &sync, &status, &d_info, (void *)&F2,
-                    (void *)&small};
+                    (void *)&small, &max_inner};
     DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_bjac32<BW>, dim3(blocks), dim3(256), args, smem,
                                           ctx->stream)); DMRG_COUNT_LAUNCH();
     return DMRG_OK;
@@ -791,7 +803,7 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
         // so aim for ~48 block pairs per round: fewer, heavier rounds
         const long long cap = (200LL * 1024) / (8LL * l);      // max BW for shared memory
         int bw = 1;
-        while (bw < 16 && 2LL * bw <= cap && (r / (2 * bw)) > 48) bw *= 2;
+        while (bw < 16 && 2LL * bw <= cap && (r / (2 * bw)) > ctx->bjac_pairs) bw *= 2;
         while (bw > 1 && (long long)bw > cap) bw /= 2;
         (void)args;
         (void)blocks;

@@ -51,11 +51,12 @@ def test_mixed_energy_matches_fp64_and_ed(G, ctx, N, chi_max):
     E0 = O.ed_ground(O.MODEL_XXZ, N) if N <= 20 else None
     if E0 is not None:
         assert abs(Em - E0) / N <= 1e-8
-    # left-canonical sites are orthonormal to FP64 level
+    # after the closing right-to-left half-sweep, sites 1..N-1 are right-orthonormal
+    # isometries (B B^T = I) to FP64 level
     chi = stm.chi()
-    for i in range(0, N // 2):
-        A = stm.site(i).cpu().numpy().reshape(chi[i] * 2, chi[i + 1])
-        assert np.abs(A.T @ A - np.eye(chi[i + 1])).max() <= 1e-10
+    for i in range(1, N):
+        B = stm.site(i).cpu().numpy().reshape(chi[i], 2 * chi[i + 1])
+        assert np.abs(B @ B.T - np.eye(chi[i])).max() <= 1e-10
     st64.close(); stm.close()
 
 
