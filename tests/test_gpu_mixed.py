@@ -52,11 +52,12 @@ def test_mixed_energy_matches_fp64_and_ed(G, ctx, N, chi_max):
     if E0 is not None:
         assert abs(Em - E0) / N <= 1e-8
     # after the closing right-to-left half-sweep, sites 1..N-1 are right-orthonormal
-    # isometries (B B^T = I) to FP64 level
+    # isometries (B B^T = I): the FP32 Jacobi leaves cosines below tol = 1e-5 and
+    # one Newton-Schulz step maps them to about (3/4) chi tol^2
     chi = stm.chi()
     for i in range(1, N):
         B = stm.site(i).cpu().numpy().reshape(chi[i], 2 * chi[i + 1])
-        assert np.abs(B @ B.T - np.eye(chi[i])).max() <= 1e-10
+        assert np.abs(B @ B.T - np.eye(chi[i])).max() <= 2 * chi[i] * 1e-10
     st64.close(); stm.close()
 
 
