@@ -215,6 +215,11 @@ dmrg_status gemm_f64(cudaStream_t st, int M, int N, int K, double alpha, const d
                      long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
                      double beta, double *C, long long sCm, long long sCn, long long sCb, int batch);
 
+// Same contract with FP32 arithmetic (small products of the mixed form).
+dmrg_status gemm_f32c(cudaStream_t st, int M, int N, int K, double alpha, const double *A, long long sAm,
+                      long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
+                      double beta, double *C, long long sCm, long long sCn, long long sCb, int batch);
+
 // Tensor-core GEMM (tcgen05, TF32 inputs split three ways, FP32 accumulate):
 // same contract as gemm_f64 (FP64 in, FP64 out), precision ~FP32.
 dmrg_status gemm_3xtf32(dmrg_ctx *ctx, int M, int N, int K, double alpha, const double *A, long long sAm,

@@ -103,35 +103,46 @@ struct MixDesc {
 };
 
 // out[channel o][a][b] = sum_i C[o][i] in[channel i][a][b]; b is unit stride.
-__global__ void __launch_bounds__(256) k_mix(const double *__restrict__ in, double *__restrict__ out,
-                                             const double *__restrict__ C, MixDesc d)
+// The coefficient table (an MPO product, mostly zeros) is compressed by rows
+// into shared memory and the inputs of each element are staged there too, so
+// each element costs one multiply-add per nonzero coefficient.
+constexpr int kMixThreads = 128;
+__global__ void __launch_bounds__(kMixThreads) k_mix(const double *__restrict__ in, double *__restrict__ out,
+                                                     const double *__restrict__ C, MixDesc d)
 {
-    __shared__ double cs[kMaxCh * kMaxCh];
-    for (int x = threadIdx.x; x < d.nin * d.nout; x += blockDim.x) cs[x] = C[x];
+    __shared__ double val[kMaxCh * kMaxCh];
+    __shared__ unsigned char col[kMaxCh * kMaxCh];
+    __shared__ int rowptr[kMaxCh + 1];
+    __shared__ double xs[kMaxCh][kMixThreads];
+    if (threadIdx.x == 0) {
+        int nnz = 0;
+        for (int o = 0; o < d.nout; ++o) {
+            rowptr[o] = nnz;
+            for (int c = 0; c < d.nin; ++c) {
+                const double v = C[o * d.nin + c];
+                if (v != 0.0) { val[nnz] = v; col[nnz] = (unsigned char)c; ++nnz; }
+            }
+        }
+        rowptr[d.nout] = nnz;
+    }
     __syncthreads();
     const long long total = (long long)d.An * d.Bn;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-        const int a = (int)(e / d.Bn), b = (int)(e % d.Bn);
-        double xin[kMaxCh];
-#pragma unroll
-        for (int c = 0; c < kMaxCh; ++c) {
-            if (c < d.nin) {
-                int x = c / d.in_ny, y = c % d.in_ny;
-                xin[c] = in[x * d.in_sx + y * d.in_sy + a * d.in_sa + b];
-            }
+    for (long long e0 = (long long)blockIdx.x * blockDim.x; e0 < total; e0 += stride) {
+        const long long e = e0 + threadIdx.x;
+        const bool ok = e < total;
+        const int a = ok ? (int)(e / d.Bn) : 0, b = ok ? (int)(e % d.Bn) : 0;
+        for (int c = 0; c < d.nin; ++c) {
+            const int x = c / d.in_ny, y = c % d.in_ny;
+            xs[c][threadIdx.x] = ok ? in[x * d.in_sx + y * d.in_sy + a * d.in_sa + b] : 0.0;
         }
-        for (int o = 0; o < d.nout; ++o) {
-            double acc = 0.0;
-#pragma unroll
-            for (int c = 0; c < kMaxCh; ++c) {
-                if (c < d.nin) {
-                    double co = cs[o * d.nin + c];
-                    if (co != 0.0) acc = fma(co, xin[c], acc);
-                }
+        if (ok) {
+            for (int o = 0; o < d.nout; ++o) {
+                double acc = 0.0;
+                for (int q = rowptr[o]; q < rowptr[o + 1]; ++q) acc = fma(val[q], xs[col[q]][threadIdx.x], acc);
+                const int x = o / d.out_ny, y = o % d.out_ny;
+                out[x * d.out_sx + y * d.out_sy + a * d.out_sa + b] = acc;
             }
-            int x = o / d.out_ny, y = o % d.out_ny;
-            out[x * d.out_sx + y * d.out_sy + a * d.out_sa + b] = acc;
         }
     }
 }
@@ -321,7 +332,7 @@ size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 static dmrg_status mix(dmrg_ctx *ctx, const double *in, double *out, const double *C, const MixDesc &d)
 {
     long long total = (long long)d.An * d.Bn;
-    k_mix<<<grid1d(total, 256, ctx->num_sms), 256, 0, ctx->stream>>>(in, out, C, d); DMRG_COUNT_LAUNCH();
+    k_mix<<<grid1d(total, kMixThreads, ctx->num_sms), kMixThreads, 0, ctx->stream>>>(in, out, C, d); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }

@@ -17,25 +17,28 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4, NT = 256;
 
-__global__ void __launch_bounds__(NT) k_gemm_f64(int M, int N, int K, double alpha, const double *__restrict__ A,
-                                                 long long sAm, long long sAk, long long sAb,
-                                                 const double *__restrict__ B, long long sBk, long long sBn,
-                                                 long long sBb, double beta, double *__restrict__ C, long long sCm,
-                                                 long long sCn, long long sCb)
+// T = double: the FP64 path; T = float: FP32 arithmetic on FP64 operands for
+// the small products of the mixed form (same precision class as 3xTF32).
+template <typename T>
+__global__ void __launch_bounds__(NT) k_gemm_t(int M, int N, int K, double alpha, const double *__restrict__ A,
+                                               long long sAm, long long sAk, long long sAb,
+                                               const double *__restrict__ B, long long sBk, long long sBn,
+                                               long long sBb, double beta, double *__restrict__ C, long long sCm,
+                                               long long sCn, long long sCb)
 {
-    __shared__ double As[BK][BM + 1];
-    __shared__ double Bs[BK][BN + 1];
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
     const int bz = blockIdx.z;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     A += (long long)bz * sAb;
     B += (long long)bz * sBb;
     C += (long long)bz * sCb;
-    double acc[TM][TN];
+    T acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < TN; ++j) acc[i][j] = (T)0;
     const bool a_kfast = (sAk == 1);
     const bool b_nfast = (sBn == 1);
     for (int k0 = 0; k0 < K; k0 += BK) {
@@ -45,7 +48,7 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(int M, int N, int K, double alp
             int mm, kk;
             if (a_kfast) { mm = idx / BK; kk = idx % BK; } else { kk = idx / BM; mm = idx % BM; }
             int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < M && gk < K) ? A[(long long)gm * sAm + (long long)gk * sAk] : 0.0;
+            As[kk][mm] = (gm < M && gk < K) ? (T)A[(long long)gm * sAm + (long long)gk * sAk] : (T)0;
         }
 #pragma unroll
         for (int it = 0; it < (BN * BK) / NT; ++it) {
@@ -53,12 +56,12 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(int M, int N, int K, double alp
             int nn, kk;
             if (b_nfast) { kk = idx / BN; nn = idx % BN; } else { nn = idx / BK; kk = idx % BK; }
             int gn = n0 + nn, gk = k0 + kk;
-            Bs[kk][nn] = (gn < N && gk < K) ? B[(long long)gk * sBk + (long long)gn * sBn] : 0.0;
+            Bs[kk][nn] = (gn < N && gk < K) ? (T)B[(long long)gk * sBk + (long long)gn * sBn] : (T)0;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            double a[TM], b[TN];
+            T a[TM], b[TN];
 #pragma unroll
             for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(NT) k_gemm_f64(int M, int N, int K, double alp
             int gn = n0 + tx + 16 * j;
             if (gn >= N) continue;
             double *c = C + (long long)gm * sCm + (long long)gn * sCn;
-            double v = alpha * acc[i][j];
+            double v = alpha * (double)acc[i][j];
             if (beta != 0.0) v += beta * *c;
             *c = v;
         }
@@ -100,7 +103,21 @@ dmrg_status gemm_f64(cudaStream_t st, int M, int N, int K, double alpha, const d
         // C = beta * C: run the kernel with K = 0 (accumulators stay zero)
         K = 0;
     }
-    k_gemm_f64<<<grid, NT, 0, st>>>(M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb); DMRG_COUNT_LAUNCH();
+    k_gemm_t<double><<<grid, NT, 0, st>>>(M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb); DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
+dmrg_status gemm_f32c(cudaStream_t st, int M, int N, int K, double alpha, const double *A, long long sAm,
+                      long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
+                      double beta, double *C, long long sCm, long long sCn, long long sCb, int batch)
+{
+    if (M <= 0 || N <= 0 || batch <= 0) return DMRG_OK;
+    if (batch > 65535) return DMRG_EINVAL;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+    if (grid.y > 65535) return DMRG_EINVAL;
+    if (K < 0) K = 0;
+    k_gemm_t<float><<<grid, NT, 0, st>>>(M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }

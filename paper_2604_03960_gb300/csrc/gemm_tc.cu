@@ -385,9 +385,11 @@ dmrg_status gemm_3xtf32(dmrg_ctx *ctx, int M, int N, int K, double alpha, const 
 {
     if (M <= 0 || N <= 0 || batch <= 0) return DMRG_OK;
     if (!tc_available(ctx)) return DMRG_EUNSUPPORTED;
-    // small products: the FP64 kernel is faster than splitting and more accurate
+    // small products: FP32 arithmetic on the CUDA cores is faster than
+    // splitting into TF32 parts, at the same precision class
     if (K <= 0 || (!ctx->tc_force && (double)M * N * K * batch < (double)ctx->tc_min_work))
-        return gemm_f64(ctx->stream, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb, batch);
+        return gemm_f32c(ctx->stream, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb,
+                         batch);
     if (batch > 65535 || (M + TBM - 1) / TBM > 65535) return DMRG_EINVAL;
     const int Kp = (K + 31) / 32 * 32, K3 = 3 * Kp;
     const size_t bytesA = sizeof(float) * (size_t)batch * M * K3, bytesB = sizeof(float) * (size_t)batch * N * K3;

@@ -471,20 +471,32 @@ __global__ void __launch_bounds__(1024) k_jac32_smem(float *__restrict__ Xg, int
 
 // Blocked FP32 Jacobi: the vectors are grouped in blocks of BW; a sweep
 // pairs the blocks in round-robin order, and the CTA that owns a block pair
-// loads its 2 BW vectors into shared memory and applies one inner sweep of
-// plane rotations over every pair among them before writing them back.  The
-// grid barrier is paid once per block round, and each vector crosses L2 once
-// per block round instead of once per vector round.
+// loads its 2 BW vectors into shared memory and applies inner sweeps of plane
+// rotations over every pair among them before writing them back.  The grid
+// barrier is paid once per block round, and each vector crosses L2 once per
+// block round.  Each vector pair is handled by WPP = 16 / BW warps, every
+// warp owning a slice of the vector length; the slice dot products meet in
+// shared memory and are summed in a fixed order, so all warps of a pair
+// derive the same rotation.
+constexpr int kBjacThreads = 512;
+
 template <int BW>
-__global__ void __launch_bounds__(256) k_bjac32(float *__restrict__ X, int r, int l, int max_sweeps, double tol,
-                                                unsigned *sync, int *status, int *info, const double *F2, double small,
-                                                int max_inner)
+__global__ void __launch_bounds__(kBjacThreads) k_bjac32(float *__restrict__ X, int r, int l, int max_sweeps,
+                                                         double tol, unsigned *sync, int *status, int *info,
+                                                         const double *F2, double small, int max_inner)
 {
+    constexpr int NW = kBjacThreads / 32;
+    constexpr int WPP = (NW / BW) > 0 ? (NW / BW) : 1;    // warps per pair
+    constexpr int PPR = NW / WPP;                         // pairs in flight per inner round
     extern __shared__ float xs[];            // [2 BW][l]
     __shared__ int vid[2 * BW];
+    __shared__ float part[NW][3];
     __shared__ unsigned block_rot, inner_rot;
     const float floor2f = (float)(small * small * F2[0]), tolf = (float)tol;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int slot = warp / WPP, sub = warp % WPP;        // pair slot and slice of this warp
+    const int chunk = (l + WPP - 1) / WPP;
+    const int e0 = sub * chunk, e1 = min(l, e0 + chunk);
     const int nb = (r + BW - 1) / BW;
     const int nbp = nb + (nb & 1);
     const int npairs = nbp / 2;
@@ -506,57 +518,69 @@ __global__ void __launch_bounds__(256) k_bjac32(float *__restrict__ X, int r, in
                     vid[threadIdx.x] = (blk < nb && v < r) ? v : -1;
                 }
                 __syncthreads();
-                // load
-                for (int q = warp; q < 2 * BW; q += nw) {
+                for (int q = warp; q < 2 * BW; q += NW) {
                     const int v = vid[q];
-                    float *dst = xs + (long long)q * l;
                     if (v >= 0) {
                         const float *src = X + (long long)v * l;
+                        float *dst = xs + (long long)q * l;
                         for (int e = lane; e < l; e += 32) dst[e] = src[e];
                     }
                 }
                 __syncthreads();
-                // inner sweeps (up to 3, stopping when one does not rotate):
-                // round-robin over the 2 BW local vectors
                 constexpr int nv = 2 * BW;
                 for (int inner = 0; inner < max_inner; ++inner) {
-                if (threadIdx.x == 0) inner_rot = 0;
-                __syncthreads();
-                for (int u = 0; u < nv - 1; ++u) {
-                    for (int pp = warp; pp < BW; pp += nw) {
-                        int a_, b_;
-                        rr_pair(nv, u, pp, a_, b_);
-                        if (vid[a_] < 0 || vid[b_] < 0) continue;
-                        float *xi = xs + (long long)a_ * l, *xj = xs + (long long)b_ * l;
-                        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f, g0 = 0.f, g1 = 0.f;
-                        int k = lane;
-                        for (; k + 32 < l; k += 64) {
-                            float x0 = xi[k], y0 = xj[k], x1 = xi[k + 32], y1 = xj[k + 32];
-                            a0 = fmaf(x0, x0, a0); b0 = fmaf(y0, y0, b0); g0 = fmaf(x0, y0, g0);
-                            a1 = fmaf(x1, x1, a1); b1 = fmaf(y1, y1, b1); g1 = fmaf(x1, y1, g1);
-                        }
-                        if (k < l) {
-                            float x0 = xi[k], y0 = xj[k];
-                            a0 = fmaf(x0, x0, a0); b0 = fmaf(y0, y0, b0); g0 = fmaf(x0, y0, g0);
-                        }
-                        const float a = warp_sum_f(a0 + a1), b = warp_sum_f(b0 + b1), g = warp_sum_f(g0 + g1);
-                        float c, sn;
-                        if (!rot32(a, b, g, floor2f, tolf, c, sn)) continue;
-                        for (int q = lane; q < l; q += 32) {
-                            const float x0 = xi[q], y0 = xj[q];
-                            xi[q] = fmaf(c, x0, -sn * y0);
-                            xj[q] = fmaf(sn, x0, c * y0);
-                        }
-                        if (lane == 0) { my_rot++; atomicAdd(&inner_rot, 1u); }
-                    }
+                    if (threadIdx.x == 0) inner_rot = 0;
                     __syncthreads();
+                    for (int u = 0; u < nv - 1; ++u) {
+                        for (int pp0 = 0; pp0 < BW; pp0 += PPR) {
+                            const int pp = pp0 + slot;
+                            int a_ = 0, b_ = 0;
+                            bool act = pp < BW;
+                            if (act) {
+                                rr_pair(nv, u, pp, a_, b_);
+                                act = vid[a_] >= 0 && vid[b_] >= 0;
+                            }
+                            float *xi = xs + (long long)a_ * l, *xj = xs + (long long)b_ * l;
+                            float a0 = 0.f, b0 = 0.f, g0 = 0.f, a1 = 0.f, b1 = 0.f, g1 = 0.f;
+                            if (act) {
+                                int k = e0 + lane;
+                                for (; k + 32 < e1; k += 64) {
+                                    float x0 = xi[k], y0 = xj[k], x1 = xi[k + 32], y1 = xj[k + 32];
+                                    a0 = fmaf(x0, x0, a0); b0 = fmaf(y0, y0, b0); g0 = fmaf(x0, y0, g0);
+                                    a1 = fmaf(x1, x1, a1); b1 = fmaf(y1, y1, b1); g1 = fmaf(x1, y1, g1);
+                                }
+                                if (k < e1) {
+                                    float x0 = xi[k], y0 = xj[k];
+                                    a0 = fmaf(x0, x0, a0); b0 = fmaf(y0, y0, b0); g0 = fmaf(x0, y0, g0);
+                                }
+                                const float pa = warp_sum_f(a0 + a1), pb = warp_sum_f(b0 + b1), pg = warp_sum_f(g0 + g1);
+                                if (lane == 0) { part[warp][0] = pa; part[warp][1] = pb; part[warp][2] = pg; }
+                            }
+                            __syncthreads();
+                            float c = 1.f, sn = 0.f;
+                            bool rot = false;
+                            if (act) {
+                                float a = 0.f, b = 0.f, g = 0.f;
+                                const int w0 = slot * WPP;
+                                for (int w = 0; w < WPP; ++w) { a += part[w0 + w][0]; b += part[w0 + w][1]; g += part[w0 + w][2]; }
+                                rot = rot32(a, b, g, floor2f, tolf, c, sn);
+                            }
+                            if (rot) {
+                                for (int q = e0 + lane; q < e1; q += 32) {
+                                    const float x0 = xi[q], y0 = xj[q];
+                                    xi[q] = fmaf(c, x0, -sn * y0);
+                                    xj[q] = fmaf(sn, x0, c * y0);
+                                }
+                                if (sub == 0 && lane == 0) { my_rot++; atomicAdd(&inner_rot, 1u); }
+                            }
+                            __syncthreads();
+                        }
+                    }
+                    const unsigned ir = inner_rot;
+                    __syncthreads();
+                    if (ir == 0u || BW == 1) break;
                 }
-                const unsigned ir = inner_rot;
-                __syncthreads();
-                if (ir == 0u || BW == 1) break;
-                }
-                // store
-                for (int q = warp; q < 2 * BW; q += nw) {
+                for (int q = warp; q < 2 * BW; q += NW) {
                     const int v = vid[q];
                     if (v >= 0) {
                         const float *src = xs + (long long)q * l;
@@ -608,7 +632,7 @@ dmrg_status launch_bjac32(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps,
         attr = smem;
     }
     int per_sm = 0;
-    DMRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjac32<BW>, 256, smem));
+    DMRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjac32<BW>, kBjacThreads, smem));
     if (per_sm < 1) return DMRG_EUNSUPPORTED;
     const int nb = (r + BW - 1) / BW;
     const int npairs = (nb + (nb & 1)) / 2;
@@ -617,7 +641,7 @@ dmrg_status launch_bjac32(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps,
     int *status = ctx->d_status;
     void *args[] = {&X, (void *)&r, (void *)&l, &max_sweeps, (void *)&tol, &sync, &status, &d_info, (void *)&F2,
                     (void *)&small, &max_inner};
-    DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_bjac32<BW>, dim3(blocks), dim3(256), args, smem,
+    DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_bjac32<BW>, dim3(blocks), dim3(kBjacThreads), args, smem,
                                           ctx->stream)); DMRG_COUNT_LAUNCH();
     return DMRG_OK;
 }

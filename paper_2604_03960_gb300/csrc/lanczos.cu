@@ -170,9 +170,11 @@ __device__ int sturm_count(int m, const double *a, const double *b, double x)
     return cnt;
 }
 
-// Lowest eigenpair of T (single thread; m <= LZ_MAXK).
+// Lowest eigenpair of T by one warp: multisection with 32 Sturm counts per
+// step (the interval shrinks 33x per step), then inverse iteration on one lane.
 __global__ void k_tridiag_lowest(LzState *lz, int *status)
 {
+    const int lane = threadIdx.x & 31;
     const int m = lz->m;
     const double *a = lz->alpha, *b = lz->beta;   // b[i] couples i-1 and i
     double lo = 1e300, hi = -1e300;
@@ -181,26 +183,35 @@ __global__ void k_tridiag_lowest(LzState *lz, int *status)
         lo = fmin(lo, a[i] - r);
         hi = fmax(hi, a[i] + r);
     }
-    for (int it = 0; it < 300; ++it) {
-        double x = 0.5 * (lo + hi);
-        if (x <= lo || x >= hi) break;
-        if (sturm_count(m, a, b, x) >= 1) hi = x; else lo = x;
+    lo -= 1e-300;
+    for (int it = 0; it < 40; ++it) {
+        const double w = hi - lo;
+        if (!(w > 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)))) break;
+        const double x = lo + w * (double)(lane + 1) / 33.0;
+        const unsigned below = __ballot_sync(0xffffffffu, sturm_count(m, a, b, x) >= 1);
+        if (below == 0u) {
+            lo = lo + w * 32.0 / 33.0;
+        } else {
+            const int f = __ffs(below) - 1;            // first point at or above lambda_0
+            const double nhi = lo + w * (double)(f + 1) / 33.0;
+            lo = (f > 0) ? lo + w * (double)f / 33.0 : lo;
+            hi = nhi;
+        }
     }
+    if (lane != 0) return;
     const double lam = 0.5 * (lo + hi);
     lz->E = lam;
-    // inverse iteration on (T - lam I): tridiagonal LU without pivoting,
-    // shifted slightly below lam so the system stays solvable
     double y[LZ_MAXK], rhs[LZ_MAXK], dd[LZ_MAXK], ll[LZ_MAXK];
     const double shift = lam - 1e-13 * fmax(fabs(lam), 1e-300) - 1e-300;
     for (int i = 0; i < m; ++i) y[i] = 1.0 / sqrt((double)m) * (1.0 + 0.01 * i);
-    for (int it = 0; it < 4; ++it) {
-        // factor
-        dd[0] = a[0] - shift;
-        for (int i = 1; i < m; ++i) {
-            double piv = (dd[i - 1] != 0.0) ? dd[i - 1] : 1e-300;
-            ll[i] = b[i] / piv;
-            dd[i] = (a[i] - shift) - ll[i] * b[i];
-        }
+    // factor T - shift I once (LU without pivoting), then two solves
+    dd[0] = a[0] - shift;
+    for (int i = 1; i < m; ++i) {
+        double piv = (dd[i - 1] != 0.0) ? dd[i - 1] : 1e-300;
+        ll[i] = b[i] / piv;
+        dd[i] = (a[i] - shift) - ll[i] * b[i];
+    }
+    for (int it = 0; it < 2; ++it) {
         for (int i = 0; i < m; ++i) rhs[i] = y[i];
         for (int i = 1; i < m; ++i) rhs[i] -= ll[i] * rhs[i - 1];
         double piv = (dd[m - 1] != 0.0) ? dd[m - 1] : 1e-300;
@@ -211,10 +222,9 @@ __global__ void k_tridiag_lowest(LzState *lz, int *status)
         }
         double nn = 0.0;
         for (int i = 0; i < m; ++i) nn += y[i] * y[i];
-        nn = sqrt(nn);
-        for (int i = 0; i < m; ++i) y[i] /= nn;
+        nn = 1.0 / sqrt(nn);
+        for (int i = 0; i < m; ++i) y[i] *= nn;
     }
-    // fix the sign (first nonzero component positive) for reproducibility
     double sgn = 1.0;
     for (int i = 0; i < m; ++i) if (y[i] != 0.0) { sgn = (y[i] < 0.0) ? -1.0 : 1.0; break; }
     for (int i = 0; i < m; ++i) lz->y[i] = sgn * y[i];
@@ -285,7 +295,7 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
         if (j + 1 < K) k_next_vec<<<g, RB, 0, st>>>(w.V + (size_t)n * (j + 1), w.w, n, w.lz, j); DMRG_COUNT_LAUNCH();
         DMRG_CUDA(cudaGetLastError());
     }
-    k_tridiag_lowest<<<1, 1, 0, st>>>(w.lz, ctx->d_status); DMRG_COUNT_LAUNCH();
+    k_tridiag_lowest<<<1, 32, 0, st>>>(w.lz, ctx->d_status); DMRG_COUNT_LAUNCH();
     // theta = V y0 (only the first m vectors carry weight: y is zero beyond m)
     {
         // copy y to the coefficient buffer (device to device)
