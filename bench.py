@@ -50,7 +50,57 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--micro", choices=["gemm", "svd"], default=None,
+                    help="one kernel-level invocation (for profiling): gemm M,N,K or svd chi")
+    ap.add_argument("--shape", default="5120,4096,1024", help="--micro gemm: M,N,K")
+    ap.add_argument("--chi", type=int, default=512, help="--micro svd: matrix 2chi x 2chi")
+    ap.add_argument("--reps", type=int, default=3)
     return ap.parse_args()
+
+
+def run_micro(args):
+    """Kernel-level timing of the contraction engine or the SVD (CUDA events)."""
+    import torch
+
+    import synth
+    import paper_2604_03960_gb300 as G
+
+    ctx = G.Context(0)
+    prec = G.PREC_3XTF32 if args.prec == "mixed" else G.PREC_FP64
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.micro == "gemm":
+        M, N, K = (int(x) for x in args.shape.split(","))
+        g = torch.Generator(device="cuda").manual_seed(0)
+        A = torch.randn(M, K, dtype=torch.float64, device="cuda", generator=g)
+        B = torch.randn(K, N, dtype=torch.float64, device="cuda", generator=g)
+        ctx.gemm(A, B, prec=prec)
+        ctx.profile(True)
+        ev0.record(ctx.stream)
+        for _ in range(args.reps):
+            ctx.gemm(A, B, prec=prec)
+        ev1.record(ctx.stream)
+        torch.cuda.synchronize()
+        pr = ctx.profile_read(0 if prec == G.PREC_3XTF32 else 3)
+        out = {"micro": "gemm", "shape": [M, N, K], "prec": args.prec, "ms_per_call": ev0.elapsed_time(ev1) / args.reps,
+               "kernel_ms": pr["ms"] / max(1, pr["launches"]),
+               "kernel_tflops": pr["flops"] / (pr["ms"] / 1e3) / 1e12 if pr["ms"] > 0 else None}
+    else:
+        chi = args.chi
+        n = 2 * chi
+        ctx.set_option("svd_prec", 1 if prec == G.PREC_3XTF32 else 0)
+        A = torch.from_numpy(synth.svd_test_matrix(synth.workload_seed(1, chi), n, n,
+                                                   synth.spectrum("exp", n, chi))).cuda()
+        ctx.svd_truncate(A, chi, 1e-10)
+        ev0.record(ctx.stream)
+        for _ in range(args.reps):
+            ctx.svd_truncate(A, chi, 1e-10)
+        ev1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.reps
+        out = {"micro": "svd", "n": n, "prec": args.prec, "ms_per_call": ms,
+               "gflops_nominal": 21.0 * n ** 3 / (ms / 1e3) / 1e9}
+    print(json.dumps(out))
+    ctx.close()
 
 
 # ---------------------------------------------------------------------------
@@ -338,7 +388,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.micro:
+        run_micro(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
