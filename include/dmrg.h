@@ -207,6 +207,27 @@ dmrg_status svd_truncate(dmrg_ctx *ctx, const double *theta_dev, int m, int n, i
                          double *U_dev, double *s_dev, double *Vt_dev, int *k_out, double *S_out,
                          double *trunc_err_out);
 
+/* svd_truncate for callers that cannot allocate device memory (no
+ * counterpart in the paper).  Same inputs, outputs and results as
+ * svd_truncate in its default FP64 form, limited to m, n <= 256.  Some
+ * callers cannot call cudaMalloc: code whose device memory is owned by
+ * another component (a framework's caching pool that must see every
+ * allocation, or a budget fixed ahead of time), and time-critical loops in
+ * which an allocation, which can synchronise the whole device, is not
+ * acceptable.  This call allocates nothing: its scratch is a file-scope
+ * device array of about 1.06 MiB (1088 KiB reserved) that every GPU which
+ * loads the library holds until the process exits.
+ *  - The first call on a device looks up that array's device address with
+ *    that device current; make this first call before any stream capture.
+ *  - Every call on a device shares the one array, and it keeps the last
+ *    call's contents (the call clears what must start at zero).  Calls that
+ *    overlap on the GPU (other streams, other threads, other contexts on the
+ *    same device) race on it: serialise them.
+ *  - Sizes above 256 return DMRG_EINVAL with a message on stderr. */
+dmrg_status svd_truncate_noalloc(dmrg_ctx *ctx, const double *theta_dev, int m, int n, int chi_max, double eps,
+                                 double *U_dev, double *s_dev, double *Vt_dev, int *k_out, double *S_out,
+                                 double *trunc_err_out);
+
 /* One controller step for each of n_bonds bonds (Algorithms 1-2 with
  * Eqs. 8 and 16): S_raw_dev[i] is bond i's raw entropy, st_dev[i] its
  * state (updated in place), chi_out_dev[i] receives the new chi.  All

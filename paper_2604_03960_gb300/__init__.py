@@ -115,6 +115,8 @@ def _declare(L):
         "dmrg_state_put_mps": (S, [_VP, _VP]),
         "dmrg_launch_count": (C.c_longlong, []),
         "dmrg_profile": (S, [_VP, _I]),
+        "svd_truncate_noalloc": (S, [_VP, _VP, _I, _I, _I, _D, _VP, _VP, _VP, C.POINTER(_I), C.POINTER(_D),
+                                     C.POINTER(_D)]),
         "dmrg_profile_read": (S, [_VP, _I, C.POINTER(_D), C.POINTER(C.c_longlong), C.POINTER(_D), C.POINTER(_D)]),
     }
     for name, (res, args) in sig.items():
@@ -145,7 +147,7 @@ def exported_symbols():
         "dmrg_state_site", "dmrg_state_env", "dmrg_state_ctrl", "dmrg_state_set_mlp", "dmrg_mlp_forward",
         "dmrg_mlp_loss_grad", "dmrg_mlp_adam", "dmrg_gemm", "dmrg_set_option",
         "dmrg_state_mps_size", "dmrg_state_get_mps", "dmrg_state_put_mps", "dmrg_launch_count",
-        "dmrg_profile", "dmrg_profile_read",
+        "dmrg_profile", "dmrg_profile_read", "svd_truncate_noalloc",
     ]
 
 
@@ -240,6 +242,16 @@ class Context:
         k = C.c_int(); S = C.c_double(); err = C.c_double()
         _check(lib().svd_truncate(self.h, _ptr(theta), m, n, chi_max, eps, _ptr(U), _ptr(s), _ptr(Vt), C.byref(k),
                                   C.byref(S), C.byref(err)), "svd_truncate")
+        return U, s, Vt, k.value, S.value, err.value
+
+    def svd_truncate_noalloc(self, theta: torch.Tensor, chi_max: int, eps: float, out):
+        """svd_truncate without any device allocation by the library (m, n <= 256);
+        `out` = (U, s, Vt) caller-owned device tensors."""
+        m, n = theta.shape
+        U, s, Vt = out
+        k = C.c_int(); S = C.c_double(); err = C.c_double()
+        _check(lib().svd_truncate_noalloc(self.h, _ptr(theta), m, n, chi_max, eps, _ptr(U), _ptr(s), _ptr(Vt),
+                                          C.byref(k), C.byref(S), C.byref(err)), "svd_truncate_noalloc")
         return U, s, Vt, k.value, S.value, err.value
 
     def entropy_pid_step(self, S_raw: torch.Tensor, states: torch.Tensor, params: Params, chi_out: torch.Tensor):
