@@ -128,6 +128,11 @@ typedef struct {
     double E, S, trunc_err;
     int jacobi_sweeps;     /* Jacobi sweeps of the visit's SVD (negative: not converged) */
     int lanczos_steps;     /* Krylov steps taken                                          */
+    float feat[10];        /* learned-scheduler features after this visit's controller
+                              step: last 8 EMA entropies, (bond+1)/N, sweep/max_sweeps   */
+    int k_star;            /* smallest k with sum_{j>=k} p_j <= eps_target^2 (context
+                              option "mlp_eps_target"): the training label source       */
+    int mlp_used;          /* 1 if the learned scheduler's chi was taken this visit       */
 } dmrg_visit_record;
 
 /* ---------------------------------------------------------------------- */
@@ -146,6 +151,7 @@ const char *dmrg_status_string(dmrg_status s);
  * the tensor cores even for tiny products), "tc_min_work" (multiply-adds
  * below which 3xTF32 requests run on the FP64 kernel), "tc_bn" (0, 128 or
  * 256: tile width of the tensor-core GEMM, 0 = heuristic),
+ * "mlp_eps_target" (truncation-error target of the k_star label, 1e-5),
  * "mixed_env_tc" (1: environment updates of the 3xTF32 form on the tensor
  * cores instead of FP64), "svd_prec" (standalone svd_truncate: 0 FP64 Jacobi,
  * 1 mixed: FP32 Jacobi, FP64-re-orthonormalised isometry, tensor-core
@@ -315,6 +321,14 @@ dmrg_status dmrg_mlp_forward(dmrg_ctx *ctx, const float *params_dev, int B, cons
 /* loss_dev[0] = mean_b (y_b - t_b)^2 and grad_dev = d loss / d params. */
 dmrg_status dmrg_mlp_loss_grad(dmrg_ctx *ctx, const float *params_dev, int B, const float *X_dev,
                                const float *t_dev, float *loss_dev, float *grad_dev);
+/* Train the network on (X_dev [B][10], t_dev [B]) for `steps` full-batch
+ * Adam steps (lr, betas 0.9/0.999, eps 1e-8) starting at Adam step
+ * first_step; m_dev, v_dev are the moment buffers (4929 floats each, zero
+ * for a fresh start).  Every step runs dmrg_mlp_loss_grad's kernels and the
+ * Adam kernel on the device; *loss_host (optional) receives the loss before
+ * the last step. */
+dmrg_status dmrg_mlp_train(dmrg_ctx *ctx, float *params_dev, int B, const float *X_dev, const float *t_dev,
+                           float *m_dev, float *v_dev, int first_step, int steps, float lr, float *loss_host);
 /* One Adam step (step is 1-based) on n parameters; m, v are moment buffers. */
 dmrg_status dmrg_mlp_adam(dmrg_ctx *ctx, int n, float *params_dev, const float *grad_dev, float *m_dev,
                           float *v_dev, int step, float lr, float beta1, float beta2, float eps);

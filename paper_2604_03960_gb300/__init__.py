@@ -60,7 +60,8 @@ class SweepRecord(C.Structure):
     _fields_ = [
         ("E", C.c_double), ("max_trunc_err", C.c_double), ("mean_chi", C.c_double),
         ("seconds", C.c_double), ("flops", C.c_double), ("max_chi", C.c_int), ("n_visits", C.c_int),
-        ("jacobi_sweeps", C.c_int), ("lanczos_steps", C.c_int),
+        ("jacobi_sweeps", C.c_int), ("lanczos_steps", C.c_int), ("feat", C.c_float * 10),
+        ("k_star", C.c_int), ("mlp_used", C.c_int),
     ]
 
 
@@ -68,7 +69,8 @@ class VisitRecord(C.Structure):
     _fields_ = [
         ("bond", C.c_int), ("k", C.c_int), ("chi_ctrl", C.c_int), ("direction", C.c_int),
         ("E", C.c_double), ("S", C.c_double), ("trunc_err", C.c_double),
-        ("jacobi_sweeps", C.c_int), ("lanczos_steps", C.c_int),
+        ("jacobi_sweeps", C.c_int), ("lanczos_steps", C.c_int), ("feat", C.c_float * 10),
+        ("k_star", C.c_int), ("mlp_used", C.c_int),
     ]
 
 
@@ -115,6 +117,7 @@ def _declare(L):
         "dmrg_state_put_mps": (S, [_VP, _VP]),
         "dmrg_launch_count": (C.c_longlong, []),
         "dmrg_profile": (S, [_VP, _I]),
+        "dmrg_mlp_train": (S, [_VP, _VP, _I, _VP, _VP, _VP, _VP, _I, _I, C.c_float, C.POINTER(C.c_float)]),
         "svd_truncate_noalloc": (S, [_VP, _VP, _I, _I, _I, _D, _VP, _VP, _VP, C.POINTER(_I), C.POINTER(_D),
                                      C.POINTER(_D)]),
         "dmrg_profile_read": (S, [_VP, _I, C.POINTER(_D), C.POINTER(C.c_longlong), C.POINTER(_D), C.POINTER(_D)]),
@@ -147,7 +150,7 @@ def exported_symbols():
         "dmrg_state_site", "dmrg_state_env", "dmrg_state_ctrl", "dmrg_state_set_mlp", "dmrg_mlp_forward",
         "dmrg_mlp_loss_grad", "dmrg_mlp_adam", "dmrg_gemm", "dmrg_set_option",
         "dmrg_state_mps_size", "dmrg_state_get_mps", "dmrg_state_put_mps", "dmrg_launch_count",
-        "dmrg_profile", "dmrg_profile_read", "svd_truncate_noalloc",
+        "dmrg_profile", "dmrg_profile_read", "svd_truncate_noalloc", "dmrg_mlp_train",
     ]
 
 
@@ -316,6 +319,12 @@ class Context:
         _check(lib().dmrg_mlp_loss_grad(self.h, _ptr(P), X.shape[0], _ptr(X), _ptr(t), _ptr(loss), _ptr(g)),
                "dmrg_mlp_loss_grad")
         return loss, g
+
+    def mlp_train(self, P, X, t, m, v, first_step, steps, lr=1e-3):
+        loss = C.c_float()
+        _check(lib().dmrg_mlp_train(self.h, _ptr(P), X.shape[0], _ptr(X), _ptr(t), _ptr(m), _ptr(v), first_step,
+                                    steps, lr, C.byref(loss)), "dmrg_mlp_train")
+        return loss.value
 
     def mlp_adam(self, P, g, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         _check(lib().dmrg_mlp_adam(self.h, P.numel(), _ptr(P), _ptr(g), _ptr(m), _ptr(v), step, lr, b1, b2, eps),

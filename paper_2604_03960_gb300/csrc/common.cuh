@@ -116,6 +116,7 @@ struct dmrg_ctx {
     int svd_prec = 0;            // standalone svd_truncate: 0 FP64 Jacobi, 1 mixed
     int bjac_pairs = 152;        // blocked FP32 Jacobi: target block pairs per round
     int bjac_inner = 1;          // blocked FP32 Jacobi: max inner sweeps per block pair
+    double mlp_eps_target = 1e-5;// truncation-error target of the learned scheduler's label
 };
 
 namespace dmrg {

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(DB) k_decide(const double *__restrict__ s, int
                                                dmrg_params p, int do_ctrl, int chi_override, const float *mlp,
                                                int bond, int N, int sweep, const LzState *lz, BondResult *res,
                                                dmrg_visit_record *visit, int direction, double rank_floor,
-                                               const int *jac_info, int *status)
+                                               const int *jac_info, double eps_target, int *status)
 {
     __shared__ double sh[32];
     __shared__ float h1[MLP_H], h2[MLP_H], xin[MLP_IN], red[2];
@@ -190,6 +190,32 @@ __global__ void __launch_bounds__(DB) k_decide(const double *__restrict__ s, int
             visit->trunc_err = br.eps;
             visit->jacobi_sweeps = jac_info ? jac_info[0] : 0;
             visit->lanczos_steps = lz ? lz->m : 0;
+            visit->mlp_used = sh_mlp_ok && !sh_fb;
+            // learned-scheduler features after this step (same recipe as its inference)
+            if (st) {
+                const int h = st->nhist;
+                for (int j = 0; j < 8; ++j) {
+                    int idx = h - 8 + j;
+                    if (idx < 0) idx = 0;
+                    visit->feat[j] = (h > 0) ? (float)st->hist[idx] : 0.0f;
+                }
+            } else {
+                for (int j = 0; j < 8; ++j) visit->feat[j] = 0.0f;
+            }
+            visit->feat[8] = (float)(bond + 1) / (float)N;
+            visit->feat[9] = (float)sweep / (float)(p.max_sweeps > 0 ? p.max_sweeps : 1);
+            // label source: smallest k whose discarded weight is <= eps_target^2
+            int ks = r;
+            if (Z > 0.0) {
+                double tail = 0.0;
+                const double lim = eps_target * eps_target, iz = 1.0 / Z;
+                for (int j = r - 1; j >= 1; --j) {
+                    tail += s[j] * s[j] * iz;
+                    if (tail > lim) break;
+                    ks = j;
+                }
+            }
+            visit->k_star = ks;
         }
         if (!isfinite(S) || !isfinite(br.znorm) || br.znorm == 0.0) atomicOr(status, ST_NAN);
     }
@@ -237,7 +263,7 @@ dmrg_status launch_decide(dmrg_ctx *ctx, const double *s, int r, dmrg_ctrl_state
 {
     k_decide<<<1, DB, 0, ctx->stream>>>(s, r, st_bond, p, do_ctrl, chi_override, mlp, bond, N, sweep,
                                         static_cast<const LzState *>(lz_state), res, visit, direction, rank_floor,
-                                        jac_info, ctx->d_status); DMRG_COUNT_LAUNCH();
+                                        jac_info, ctx->mlp_eps_target, ctx->d_status); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }

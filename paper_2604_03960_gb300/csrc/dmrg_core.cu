@@ -494,6 +494,11 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         return DMRG_OK;
     }
     if (!std::strcmp(name, "mixed_env_tc")) { ctx->mixed_env_tc = value != 0.0; return DMRG_OK; }
+    if (!std::strcmp(name, "mlp_eps_target")) {
+        if (!(value > 0.0 && value < 1.0)) return DMRG_EINVAL;
+        ctx->mlp_eps_target = value;
+        return DMRG_OK;
+    }
     if (!std::strcmp(name, "bjac_pairs")) {
         if (!(value >= 1.0 && value <= 100000.0)) return DMRG_EINVAL;
         ctx->bjac_pairs = (int)value;

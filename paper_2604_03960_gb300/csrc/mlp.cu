@@ -166,6 +166,26 @@ dmrg_status dmrg_mlp_loss_grad(dmrg_ctx *ctx, const float *params_dev, int B, co
     return DMRG_OK;
 }
 
+dmrg_status dmrg_mlp_train(dmrg_ctx *ctx, float *params_dev, int B, const float *X_dev, const float *t_dev,
+                           float *m_dev, float *v_dev, int first_step, int steps, float lr, float *loss_host)
+{
+    if (!ctx || !params_dev || !X_dev || !t_dev || !m_dev || !v_dev || B < 1 || first_step < 1 || steps < 0)
+        return DMRG_EINVAL;
+    DMRG_TRY(ctx->work2.ensure(sizeof(float) * (MLP_NPARAM + 64)));
+    float *grad = ctx->work2.as<float>();
+    float *loss = grad + MLP_NPARAM;
+    for (int i = 0; i < steps; ++i) {
+        DMRG_TRY(dmrg_mlp_loss_grad(ctx, params_dev, B, X_dev, t_dev, loss, grad));
+        DMRG_TRY(dmrg_mlp_adam(ctx, MLP_NPARAM, params_dev, grad, m_dev, v_dev, first_step + i, lr, 0.9f, 0.999f,
+                               1e-8f));
+    }
+    if (loss_host) {
+        DMRG_CUDA(cudaMemcpyAsync(loss_host, loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return DMRG_OK;
+}
+
 dmrg_status dmrg_mlp_adam(dmrg_ctx *ctx, int n, float *params_dev, const float *grad_dev, float *m_dev, float *v_dev,
                           int step, float lr, float beta1, float beta2, float eps)
 {
