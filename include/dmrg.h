@@ -234,6 +234,30 @@ dmrg_status svd_truncate_noalloc(dmrg_ctx *ctx, const double *theta_dev, int m, 
                                  double *U_dev, double *s_dev, double *Vt_dev, int *k_out, double *S_out,
                                  double *trunc_err_out);
 
+/* Batched SVD + entropy + truncation of `batch` independent matrices (the
+ * uneven isolated-SVD workload; Eqs. 4-5, 20).  Matrix b is m[b] x n[b]
+ * (host arrays), row-major at theta_dev + off_in[b]; U_b (m x r), s_b (r,
+ * descending) and Vt_b (r x n), r = min(m, n), go to U_dev + off_U[b],
+ * s_dev + off_s[b], Vt_dev + off_Vt[b] (host offset arrays, counted in
+ * doubles).  k_dev[b], S_dev[b], err_dev[b] (device) receive k = min(chi_max,
+ * rank, #{s_j/|s| > eps}), the entropy and the truncation error.  prec:
+ * DMRG_PREC_FP64, or DMRG_PREC_3XTF32 for FP32 Jacobi (factors orthogonal to
+ * ~1e-5; values below 2^-22 s_0 unresolved).  One CTA per matrix.  No host
+ * synchronisation; the descriptors are staged in the context's pinned
+ * memory, so after a first call of the same shapes the call can be captured
+ * with dmrg_graph_begin/end and replayed with dmrg_graph_launch. */
+dmrg_status svd_truncate_batched(dmrg_ctx *ctx, int prec, int batch, const int *m, const int *n,
+                                 const double *theta_dev, const long long *off_in, double *U_dev,
+                                 const long long *off_U, double *s_dev, const long long *off_s, double *Vt_dev,
+                                 const long long *off_Vt, int chi_max, double eps, int *k_dev, double *S_dev,
+                                 double *err_dev);
+/* CUDA-graph capture of a context's stream (which must not be the legacy
+ * default stream): begin, end (instantiates into *graph_exec), launch, destroy. */
+dmrg_status dmrg_graph_begin(dmrg_ctx *ctx);
+dmrg_status dmrg_graph_end(dmrg_ctx *ctx, void **graph_exec);
+dmrg_status dmrg_graph_launch(dmrg_ctx *ctx, void *graph_exec);
+dmrg_status dmrg_graph_destroy(void *graph_exec);
+
 /* One controller step for each of n_bonds bonds (Algorithms 1-2 with
  * Eqs. 8 and 16): S_raw_dev[i] is bond i's raw entropy, st_dev[i] its
  * state (updated in place), chi_out_dev[i] receives the new chi.  All

@@ -60,8 +60,7 @@ class SweepRecord(C.Structure):
     _fields_ = [
         ("E", C.c_double), ("max_trunc_err", C.c_double), ("mean_chi", C.c_double),
         ("seconds", C.c_double), ("flops", C.c_double), ("max_chi", C.c_int), ("n_visits", C.c_int),
-        ("jacobi_sweeps", C.c_int), ("lanczos_steps", C.c_int), ("feat", C.c_float * 10),
-        ("k_star", C.c_int), ("mlp_used", C.c_int),
+        ("jacobi_sweeps", C.c_int), ("lanczos_steps", C.c_int),
     ]
 
 
@@ -117,6 +116,12 @@ def _declare(L):
         "dmrg_state_put_mps": (S, [_VP, _VP]),
         "dmrg_launch_count": (C.c_longlong, []),
         "dmrg_profile": (S, [_VP, _I]),
+        "svd_truncate_batched": (S, [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _D, _VP,
+                                     _VP, _VP]),
+        "dmrg_graph_begin": (S, [_VP]),
+        "dmrg_graph_end": (S, [_VP, C.POINTER(_VP)]),
+        "dmrg_graph_launch": (S, [_VP, _VP]),
+        "dmrg_graph_destroy": (S, [_VP]),
         "dmrg_mlp_train": (S, [_VP, _VP, _I, _VP, _VP, _VP, _VP, _I, _I, C.c_float, C.POINTER(C.c_float)]),
         "svd_truncate_noalloc": (S, [_VP, _VP, _I, _I, _I, _D, _VP, _VP, _VP, C.POINTER(_I), C.POINTER(_D),
                                      C.POINTER(_D)]),
@@ -151,6 +156,7 @@ def exported_symbols():
         "dmrg_mlp_loss_grad", "dmrg_mlp_adam", "dmrg_gemm", "dmrg_set_option",
         "dmrg_state_mps_size", "dmrg_state_get_mps", "dmrg_state_put_mps", "dmrg_launch_count",
         "dmrg_profile", "dmrg_profile_read", "svd_truncate_noalloc", "dmrg_mlp_train",
+        "svd_truncate_batched", "dmrg_graph_begin", "dmrg_graph_end", "dmrg_graph_launch", "dmrg_graph_destroy",
     ]
 
 
@@ -256,6 +262,54 @@ class Context:
         _check(lib().svd_truncate_noalloc(self.h, _ptr(theta), m, n, chi_max, eps, _ptr(U), _ptr(s), _ptr(Vt),
                                           C.byref(k), C.byref(S), C.byref(err)), "svd_truncate_noalloc")
         return U, s, Vt, k.value, S.value, err.value
+
+    def svd_batched(self, mats, chi_max: int, eps: float, prec=PREC_FP64, packed=None):
+        """Batched SVD + truncation of a list of 2-D CUDA float64 tensors.  Returns
+        the packed buffers (theta, U, s, Vt, k, S, err and the host offset
+        arrays).  `packed` reuses the buffers of an earlier call with the same
+        shapes; with `mats=None` the inputs already in packed["theta"] are used
+        (no copies: the form to capture in a graph)."""
+        import numpy as np
+        if packed is None:
+            ms = np.array([a.shape[0] for a in mats], dtype=np.int32)
+            ns = np.array([a.shape[1] for a in mats], dtype=np.int32)
+            rs = np.minimum(ms, ns).astype(np.int64)
+            oin = np.concatenate([[0], np.cumsum(ms.astype(np.int64) * ns)[:-1]]).astype(np.int64)
+            oU = np.concatenate([[0], np.cumsum(ms.astype(np.int64) * rs)[:-1]]).astype(np.int64)
+            os_ = np.concatenate([[0], np.cumsum(rs)[:-1]]).astype(np.int64)
+            oV = np.concatenate([[0], np.cumsum(rs * ns)[:-1]]).astype(np.int64)
+            dev = mats[0].device
+            packed = dict(
+                m=ms, n=ns, r=rs, oin=oin, oU=oU, os=os_, oV=oV,
+                theta=torch.empty(int((ms.astype(np.int64) * ns).sum()), dtype=torch.float64, device=dev),
+                U=torch.empty(int((ms * rs).sum()), dtype=torch.float64, device=dev),
+                s=torch.empty(int(rs.sum()), dtype=torch.float64, device=dev),
+                Vt=torch.empty(int((rs * ns).sum()), dtype=torch.float64, device=dev),
+                k=torch.empty(len(mats), dtype=torch.int32, device=dev),
+                S=torch.empty(len(mats), dtype=torch.float64, device=dev),
+                err=torch.empty(len(mats), dtype=torch.float64, device=dev))
+        p = packed
+        if mats is not None:
+            with torch.cuda.stream(self.stream):
+                for a, o in zip(mats, p["oin"]):
+                    p["theta"][int(o): int(o) + a.numel()].copy_(a.reshape(-1))
+        P = lambda arr: arr.ctypes.data_as(C.c_void_p)
+        _check(lib().svd_truncate_batched(self.h, prec, len(p["m"]), P(p["m"]), P(p["n"]), _ptr(p["theta"]),
+                                          P(p["oin"]), _ptr(p["U"]), P(p["oU"]), _ptr(p["s"]), P(p["os"]),
+                                          _ptr(p["Vt"]), P(p["oV"]), chi_max, eps, _ptr(p["k"]), _ptr(p["S"]),
+                                          _ptr(p["err"])), "svd_truncate_batched")
+        return packed
+
+    def graph_begin(self):
+        _check(lib().dmrg_graph_begin(self.h), "dmrg_graph_begin")
+
+    def graph_end(self):
+        g = C.c_void_p()
+        _check(lib().dmrg_graph_end(self.h, C.byref(g)), "dmrg_graph_end")
+        return g
+
+    def graph_launch(self, g):
+        _check(lib().dmrg_graph_launch(self.h, g), "dmrg_graph_launch")
 
     def entropy_pid_step(self, S_raw: torch.Tensor, states: torch.Tensor, params: Params, chi_out: torch.Tensor):
         n = S_raw.numel()

@@ -117,6 +117,9 @@ struct dmrg_ctx {
     int bjac_pairs = 152;        // blocked FP32 Jacobi: target block pairs per round
     int bjac_inner = 1;          // blocked FP32 Jacobi: max inner sweeps per block pair
     double mlp_eps_target = 1e-5;// truncation-error target of the learned scheduler's label
+    dmrg::DevBuf work4;          // batched SVD workspace
+    void *pinned_desc = nullptr; // batched SVD descriptors (pinned, read by the H2D copy / graph replays)
+    size_t pinned_desc_bytes = 0;
 };
 
 namespace dmrg {

@@ -566,6 +566,8 @@ void dmrg_destroy(dmrg_ctx *ctx)
     ctx->work2.release();
     ctx->work3.release();
     ctx->tcbuf.release();
+    ctx->work4.release();
+    if (ctx->pinned_desc) cudaFreeHost(ctx->pinned_desc);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_pinned_i) cudaFreeHost(ctx->h_pinned_i);
     if (ctx->h_pinned_d) cudaFreeHost(ctx->h_pinned_d);

@@ -55,3 +55,29 @@ def test_library_targets_sm103a(libpath):
     if out.returncode != 0:
         pytest.skip("cuobjdump unavailable")
     assert "sm_103a" in out.stdout
+
+
+def test_ctypes_structs_match_header(tmp_path):
+    """The binding's ctypes mirrors have the header's sizes and field offsets
+    (a mismatch would silently misread every record after the first)."""
+    import paper_2604_03960_gb300 as G
+    pairs = [("dmrg_params", G.Params), ("dmrg_model_params", G.ModelParams), ("dmrg_ctrl_state", G.CtrlState),
+             ("dmrg_sweep_record", G.SweepRecord), ("dmrg_visit_record", G.VisitRecord)]
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "dmrg.h"', 'int main(void){']
+    for cname, py in pairs:
+        src.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            src.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    src.append("return 0;}")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for cname, py in pairs:
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
