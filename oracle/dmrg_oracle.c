@@ -979,9 +979,9 @@ static void mlp_features(const ref_ctrl_state *st, int bond, int N, int sweep, i
 }
 
 /* Bond dimension chosen by the MLP, with the PID as fallback and judge:
- * the PID choice is used if the network output is not finite or outside
- * [chi_min, chi_max] before clamping, or if its truncation error exceeds
- * 10x the PID's plus 1e-10.                                                 */
+ * chi = clamp(round(2^y), chi_min, chi_max); the PID choice is used if the
+ * network output is not finite, or if the truncation error of the network's
+ * chi exceeds 10x the PID's plus 1e-10.                                     */
 static int mlp_choose(const double *P, const double *x, int chi_pid, const ref_params *p,
                       int r, const double *s, int *used_fallback)
 {
@@ -989,7 +989,9 @@ static int mlp_choose(const double *P, const double *x, int chi_pid, const ref_p
     ref_mlp_forward(P, 1, x, &y);
     double c = nearbyint(exp2(y));
     *used_fallback = 1;
-    if (!isfinite(y) || !(c >= p->chi_min && c <= p->chi_max)) return chi_pid;
+    if (!isfinite(y)) return chi_pid;
+    if (c < p->chi_min) c = p->chi_min;
+    if (c > p->chi_max) c = p->chi_max;
     int chi_m = (int)c;
     int k_m = ref_trunc_k(r, s, chi_m, p->eps_trunc, p->multiplet_guard);
     int k_p = ref_trunc_k(r, s, chi_pid, p->eps_trunc, p->multiplet_guard);

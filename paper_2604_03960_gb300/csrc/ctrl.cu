@@ -131,10 +131,11 @@ __global__ void __launch_bounds__(DB) k_decide(const double *__restrict__ s, int
     if (sh_mlp_ok) {
         float y = mlp_forward_block(mlp, xin, h1, h2, red);
         if (t == 0) {
+            // a finite output is clamped to [chi_min, chi_max]; a non-finite one falls back
             double c = rint(exp2((double)y));
+            c = c < (double)p.chi_min ? (double)p.chi_min : (c > (double)p.chi_max ? (double)p.chi_max : c);
             sh_fb = 1;
-            sh_chim = -1;
-            if (isfinite(y) && c >= p.chi_min && c <= p.chi_max) sh_chim = (int)c;
+            sh_chim = isfinite(y) ? (int)c : -1;
         }
         __syncthreads();
         if (sh_chim > 0) {

@@ -278,3 +278,29 @@ def test_mlp_forward_grad_adam(G, ctx):
     Pr = P.astype(np.float64).copy(); mr = np.zeros_like(Pr); vr = np.zeros_like(Pr)
     O.adam_step(Pr, g_ref.copy(), mr, vr, 1, lr=1e-3)
     assert np.allclose(Pd.cpu().numpy(), Pr, atol=1e-6)
+
+
+def test_dmrg_mlp_controller_matches_oracle(G, ctx):
+    """The learned-scheduler form against the oracle running the same network
+    in FP64: per-sweep energies to 1e-10 per site and the same schedule (the
+    FP32 inference can only move chi at a near-tie of round(2^y))."""
+    N = 16
+    u = synth.Xoshiro(synth.workload_seed(12, 0), lanes=64).uniform(G.MLP_NPARAM) * 2 - 1
+    P = (u * 0.5).astype(np.float32)
+    P[-1] = 4.0                                   # output bias: chi around 16 (y in about [2.5, 5.7])
+    kw = dict(ctrl=G.CTRL_MLP, chi_max=32, chi_init=4, max_sweeps=4)
+    p = G.make_params(**kw)
+    W = O.mpo(O.MODEL_XXZ, N, 1.0, 1.0)
+    m0 = synth.initial_mps_entries(synth.workload_seed(0, 3), N, p.chi_init)
+    ref = O.dmrg_run(W, m0, O.make_params(**kw), 4, mlp_params=P.astype(np.float64))
+    st = G.State(ctx, dev(W), dev(m0), p, 1.0, 1.0)
+    st.set_mlp(dev(P, torch.float32))
+    recs, vis = st.sweep(4)
+    st.close()
+    chi = np.array([v.chi_ctrl for v in vis])
+    # the network's chi differs from the fixed output bias somewhere (not a constant schedule)
+    assert len(set(chi.tolist())) > 2
+    assert np.array_equal(chi, ref["chi"])
+    assert np.array_equal(np.array([v.k for v in vis]), ref["k"])
+    E = np.array([r.E for r in recs])
+    assert np.all(np.abs(E - ref["E"]) / N <= 1e-10)
