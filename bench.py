@@ -50,11 +50,16 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--micro", choices=["gemm", "svd"], default=None,
+    ap.add_argument("--micro", choices=["gemm", "svd", "svd_batch"], default=None,
                     help="one kernel-level invocation (for profiling): gemm M,N,K or svd chi")
     ap.add_argument("--shape", default="5120,4096,1024", help="--micro gemm: M,N,K")
     ap.add_argument("--chi", type=int, default=512, help="--micro svd: matrix 2chi x 2chi")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--count", type=int, default=512, help="--micro svd_batch: number of matrices")
+    ap.add_argument("--chi-lo", type=int, default=32, help="--micro svd_batch: smallest chi")
+    ap.add_argument("--chi-hi", type=int, default=512, help="--micro svd_batch: largest chi")
+    ap.add_argument("--inner", type=int, default=4, help="--micro svd_batch: inner Jacobi sweeps per block pair")
+    ap.add_argument("--floor32", type=float, default=2.0 ** -23, help="--micro svd_batch: FP32 rotation floor")
     return ap.parse_args()
 
 
@@ -84,6 +89,8 @@ def run_micro(args):
         out = {"micro": "gemm", "shape": [M, N, K], "prec": args.prec, "ms_per_call": ev0.elapsed_time(ev1) / args.reps,
                "kernel_ms": pr["ms"] / max(1, pr["launches"]),
                "kernel_tflops": pr["flops"] / (pr["ms"] / 1e3) / 1e12 if pr["ms"] > 0 else None}
+    elif args.micro == "svd_batch":
+        out = svd_batch(args, G, synth, prec)
     else:
         chi = args.chi
         n = 2 * chi
@@ -101,6 +108,50 @@ def run_micro(args):
                "gflops_nominal": 21.0 * n ** 3 / (ms / 1e3) / 1e9}
     print(json.dumps(out))
     ctx.close()
+
+
+def svd_batch(args, G, synth, prec):
+    """The uneven isolated-SVD batch: `count` matrices 2chi x 2chi, chi uniform
+    in [chi_lo, chi_hi], exponential spectra s_k = exp(-k / (0.1 chi)), Haar
+    factors; one batched call captured in a CUDA graph and replayed."""
+    import numpy as np
+    import torch
+    chis = synth.uneven_sizes(synth.workload_seed(30, 0), args.count, args.chi_lo, args.chi_hi)
+    t0 = time.time()
+    mats = [torch.from_numpy(synth.svd_test_matrix(synth.workload_seed(31, b), 2 * int(c), 2 * int(c),
+                                                   synth.spectrum("exp", 2 * int(c), int(c))))
+            for b, c in enumerate(chis)]
+    gen_s = time.time() - t0
+    stream = torch.cuda.Stream()
+    ctx = G.Context(0, stream=stream)
+    ctx.set_option("batched_inner", args.inner)
+    ctx.set_option("batched_floor32", args.floor32)
+    dev = [a.cuda() for a in mats]
+    torch.cuda.synchronize()
+    p = ctx.svd_batched(dev, chi_max=int(args.chi_hi), eps=1e-10, prec=prec)
+    stream.synchronize()
+    ctx.graph_begin()
+    ctx.svd_batched(None, chi_max=int(args.chi_hi), eps=1e-10, prec=prec, packed=p)
+    g = ctx.graph_end()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.graph_launch(g)
+    stream.synchronize()
+    ev0.record(stream)
+    for _ in range(args.reps):
+        ctx.graph_launch(g)
+    ev1.record(stream)
+    stream.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.reps
+    G.lib().dmrg_graph_destroy(g)
+    n = 2 * chis.astype(np.float64)
+    nominal = float(np.sum(21.0 * n ** 3))
+    k = p["k"].cpu().numpy()
+    sw = p["sweeps"].cpu().numpy()
+    ctx.close()
+    return {"micro": "svd_batch", "sweeps": [int(np.abs(sw).min()), float(np.abs(sw).mean()), int(np.abs(sw).max())],
+            "not_converged": int((sw <= 0).sum()), "inner": int(args.inner), "floor32": args.floor32, "count": int(args.count), "chi": [int(args.chi_lo), int(args.chi_hi)],
+            "prec": args.prec, "ms_per_batch": ms, "gflops_nominal": nominal / (ms / 1e3) / 1e9,
+            "mean_k": float(np.mean(k)), "input_gen_s": gen_s}
 
 
 # ---------------------------------------------------------------------------

@@ -158,8 +158,10 @@ const char *dmrg_status_string(dmrg_status s);
  * projection for the other factor; values below 2^-22 s_0 are not resolved),
  * "bjac_pairs" / "bjac_inner" (blocked FP32 Jacobi: target block pairs per
  * round, inner sweeps per block pair), "jacobi_max_sweeps" (standalone
- * svd_truncate).  DMRG_EINVAL for an
- * unknown name or value. */
+ * svd_truncate and svd_truncate_batched), "batched_inner" (svd_truncate_batched:
+ * Jacobi sweeps on each 32 x 32 block-pair Gram matrix, 4), "batched_floor32"
+ * (FP32 svd_truncate_batched: vectors with norm below this x |A|_F take no
+ * rotation, 2^-23).  DMRG_EINVAL for an unknown name or value. */
 dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value);
 /* Bond dimension D of the MPO of `model` (5, 8, 3), or -1. */
 int dmrg_mpo_dim(int model);
@@ -245,12 +247,17 @@ dmrg_status svd_truncate_noalloc(dmrg_ctx *ctx, const double *theta_dev, int m, 
  * ~1e-5; values below 2^-22 s_0 unresolved).  One CTA per matrix.  No host
  * synchronisation; the descriptors are staged in the context's pinned
  * memory, so after a first call of the same shapes the call can be captured
- * with dmrg_graph_begin/end and replayed with dmrg_graph_launch. */
+ * with dmrg_graph_begin/end and replayed with dmrg_graph_launch (a batched
+ * call of other shapes on the same context between capture and replay
+ * changes what the graph replays).  sweeps_dev (device, batch ints, may be
+ * NULL) receives the Jacobi sweeps of each matrix, negative if it did not
+ * converge within "jacobi_max_sweeps" (the status word then holds
+ * DMRG_ENOCONV). */
 dmrg_status svd_truncate_batched(dmrg_ctx *ctx, int prec, int batch, const int *m, const int *n,
                                  const double *theta_dev, const long long *off_in, double *U_dev,
                                  const long long *off_U, double *s_dev, const long long *off_s, double *Vt_dev,
                                  const long long *off_Vt, int chi_max, double eps, int *k_dev, double *S_dev,
-                                 double *err_dev);
+                                 double *err_dev, int *sweeps_dev);
 /* CUDA-graph capture of a context's stream (which must not be the legacy
  * default stream): begin, end (instantiates into *graph_exec), launch, destroy. */
 dmrg_status dmrg_graph_begin(dmrg_ctx *ctx);

@@ -117,7 +117,7 @@ def _declare(L):
         "dmrg_launch_count": (C.c_longlong, []),
         "dmrg_profile": (S, [_VP, _I]),
         "svd_truncate_batched": (S, [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _D, _VP,
-                                     _VP, _VP]),
+                                     _VP, _VP, _VP]),
         "dmrg_graph_begin": (S, [_VP]),
         "dmrg_graph_end": (S, [_VP, C.POINTER(_VP)]),
         "dmrg_graph_launch": (S, [_VP, _VP]),
@@ -287,7 +287,8 @@ class Context:
                 Vt=torch.empty(int((rs * ns).sum()), dtype=torch.float64, device=dev),
                 k=torch.empty(len(mats), dtype=torch.int32, device=dev),
                 S=torch.empty(len(mats), dtype=torch.float64, device=dev),
-                err=torch.empty(len(mats), dtype=torch.float64, device=dev))
+                err=torch.empty(len(mats), dtype=torch.float64, device=dev),
+                sweeps=torch.empty(len(mats), dtype=torch.int32, device=dev))
         p = packed
         if mats is not None:
             with torch.cuda.stream(self.stream):
@@ -297,7 +298,7 @@ class Context:
         _check(lib().svd_truncate_batched(self.h, prec, len(p["m"]), P(p["m"]), P(p["n"]), _ptr(p["theta"]),
                                           P(p["oin"]), _ptr(p["U"]), P(p["oU"]), _ptr(p["s"]), P(p["os"]),
                                           _ptr(p["Vt"]), P(p["oV"]), chi_max, eps, _ptr(p["k"]), _ptr(p["S"]),
-                                          _ptr(p["err"])), "svd_truncate_batched")
+                                          _ptr(p["err"]), _ptr(p["sweeps"])), "svd_truncate_batched")
         return packed
 
     def graph_begin(self):

@@ -1,23 +1,62 @@
 // batched.cu -- many independent SVD + entropy + truncation problems in one
-// launch (the uneven isolated-SVD batch): one CTA per matrix, each running the
-// one-sided Jacobi iteration of jacobi.cu on its own matrix with only
-// __syncthreads between rounds, so the batch fills the GPU without grid
-// barriers.  FP64, or FP32 for the mixed form.  The call performs no host
-// synchronisation, so once a first call has sized the workspace the launch
-// sequence can be captured in a CUDA graph (dmrg_graph_*).
+// launch (the uneven isolated-SVD batch).  One CTA per matrix runs a one-sided
+// block Jacobi (Hestenes) iteration in Gram form:
+//
+//   the r vectors (columns or rows of A, whichever are fewer) are split into
+//   blocks of 16; in each round of a round-robin schedule over the blocks, a
+//   team of 4 warps takes a pair of blocks W = [X_I X_J] (32 vectors), forms
+//   the 32 x 32 Gram matrix G = W^T W over tiles of 32 positions staged in
+//   shared memory, diagonalises G with cyclic two-sided Jacobi (one warp,
+//   accumulating the rotation Q), and applies W <- W Q, V <- V Q as small
+//   matrix products.  A block pair whose G already has every cosine below the
+//   tolerance is left untouched; a sweep with no rotation anywhere ends the
+//   iteration.
+//
+// Compared with rotating one vector pair at a time this needs 2r/16 dependent
+// rounds per sweep instead of 2r, and the vector traffic of a round is three
+// passes over the 32 vectors (Gram, update of X, update of V) whatever the
+// number of rotations inside the pair.  FP64, or FP32 for the mixed form.
+// The call performs no host synchronisation, so once a first call has sized
+// the workspace the launch sequence can be captured in a CUDA graph
+// (dmrg_graph_*).
 #include "common.cuh"
 
 #include <algorithm>
+#include <numeric>
 
 namespace dmrg {
 namespace {
 
 struct BDesc {
-    int m, n, r, l, tr, pad;
-    long long off_in, off_U, off_s, off_Vt, off_X, off_V;
+    int m, n, r, l, tr, nb;            // nb: number of 16-vector blocks (even)
+    int ldx, ldv;                      // padded vector lengths (multiples of 32)
+    int idx, pad;                      // position of the matrix in the caller's arrays
+    long long off_in, off_U, off_s, off_Vt;
+    long long off_X, off_V, off_P;     // workspace: vectors, rotations, permutation + sorted values
 };
 
-constexpr int kBT = 512;   // threads per matrix
+constexpr int kBT = 512;                       // threads per matrix
+constexpr int kWarps = kBT / 32;
+constexpr int kTeamWarps = 4;                  // warps sharing one block pair
+constexpr int kTeams = kWarps / kTeamWarps;
+constexpr int kBlk = 16;                       // vectors per block; a pair is one warp wide
+
+template <typename T> struct TileStride;       // row stride of a [position][vector] tile
+template <> struct TileStride<float> { static constexpr int v = 36; };   // 144 B rows
+template <> struct TileStride<double> { static constexpr int v = 34; };  // 272 B rows
+
+template <typename T> struct GbjSmem {
+    T tile[kWarps][32][TileStride<T>::v];      // per-warp staging tile; also the Gram partials
+    T G[kTeams][32][33];
+    T Q[kTeams][32][33];
+    T rc[kTeams][2][16], rs[kTeams][2][16];   // rotations of a Jacobi step, double-buffered by step parity
+    int rp[kTeams][2][16], rq[kTeams][2][16];
+    unsigned rmask[kTeams][2];
+    int team_rot[kTeams];
+    unsigned rot_count;
+    double red[32];
+    BDesc d;
+};
 
 template <typename T> __device__ __forceinline__ T wsum(T v)
 {
@@ -25,79 +64,321 @@ template <typename T> __device__ __forceinline__ T wsum(T v)
     return v;
 }
 
+// 32 consecutive elements (16-byte aligned) of one vector into column `lane`
+// of a [position][vector] tile
+__device__ __forceinline__ void stage32(const float *__restrict__ p, float (*tile)[36], int lane)
+{
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 x = q[i];
+        tile[4 * i][lane] = x.x; tile[4 * i + 1][lane] = x.y;
+        tile[4 * i + 2][lane] = x.z; tile[4 * i + 3][lane] = x.w;
+    }
+}
+__device__ __forceinline__ void stage32(const double *__restrict__ p, double (*tile)[34], int lane)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const double2 x = q[i];
+        tile[2 * i][lane] = x.x; tile[2 * i + 1][lane] = x.y;
+    }
+}
+
+// acc[q] += sum_t tile[t][lane] * tile[t][q]   (row t broadcast to the warp)
+__device__ __forceinline__ void tile_gram(const float (*tile)[36], int lane, float (&acc)[32])
+{
+#pragma unroll 4
+    for (int t = 0; t < 32; ++t) {
+        const float o = tile[t][lane];
+#pragma unroll
+        for (int q = 0; q < 32; q += 4) {
+            const float4 x = *reinterpret_cast<const float4 *>(&tile[t][q]);
+            acc[q] = fmaf(o, x.x, acc[q]); acc[q + 1] = fmaf(o, x.y, acc[q + 1]);
+            acc[q + 2] = fmaf(o, x.z, acc[q + 2]); acc[q + 3] = fmaf(o, x.w, acc[q + 3]);
+        }
+    }
+}
+__device__ __forceinline__ void tile_gram(const double (*tile)[34], int lane, double (&acc)[32])
+{
+#pragma unroll 4
+    for (int t = 0; t < 32; ++t) {
+        const double o = tile[t][lane];
+#pragma unroll
+        for (int q = 0; q < 32; q += 2) {
+            const double2 x = *reinterpret_cast<const double2 *>(&tile[t][q]);
+            acc[q] = fma(o, x.x, acc[q]); acc[q + 1] = fma(o, x.y, acc[q + 1]);
+        }
+    }
+}
+// p[t] = sum_q qc[q] * tile[t][q] for the 32 positions, written in pieces of
+// 16 (FP32) or 8 (FP64) positions
+__device__ __forceinline__ void tile_apply(const float (*tile)[36], const float (&qc)[32], float *__restrict__ p)
+{
+#pragma unroll
+    for (int h = 0; h < 32; h += 16) {
+        float out[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+            for (int q = 0; q < 32; q += 4) {
+                const float4 x = *reinterpret_cast<const float4 *>(&tile[h + t][q]);
+                a0 = fmaf(qc[q], x.x, a0); a1 = fmaf(qc[q + 1], x.y, a1);
+                a0 = fmaf(qc[q + 2], x.z, a0); a1 = fmaf(qc[q + 3], x.w, a1);
+            }
+            out[t] = a0 + a1;
+        }
+        float4 *o4 = reinterpret_cast<float4 *>(p + h);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o4[i] = make_float4(out[4 * i], out[4 * i + 1], out[4 * i + 2], out[4 * i + 3]);
+    }
+}
+__device__ __forceinline__ void tile_apply(const double (*tile)[34], const double (&qc)[32], double *__restrict__ p)
+{
+#pragma unroll 1
+    for (int h = 0; h < 32; h += 8) {
+        double out[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+            for (int q = 0; q < 32; q += 2) {
+                const double2 x = *reinterpret_cast<const double2 *>(&tile[h + t][q]);
+                a0 = fma(qc[q], x.x, a0); a1 = fma(qc[q + 1], x.y, a1);
+            }
+            out[t] = a0 + a1;
+        }
+        double2 *o2 = reinterpret_cast<double2 *>(p + h);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o2[i] = make_double2(out[2 * i], out[2 * i + 1]);
+    }
+}
+
+__device__ __forceinline__ void team_bar(int team)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "r"(kTeamWarps * 32) : "memory");
+}
+
+// vector index of local vector j (0..31) of block pair (bi, bj)
+__device__ __forceinline__ int pair_vec(int bi, int bj, int j) { return j < kBlk ? bi * kBlk + j : bj * kBlk + j - kBlk; }
+
+// round-robin (circle) pairing of n (even) items: pair k of round t
+__device__ __forceinline__ void circle_pair(int n, int t, int k, int &p, int &q)
+{
+    if (k == 0) { p = n - 1; q = t; }
+    else { p = (t + k) % (n - 1); q = (t - k + n - 1) % (n - 1); }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ desc, const double *__restrict__ theta,
                                                     T *__restrict__ work, double *__restrict__ U,
                                                     double *__restrict__ s, double *__restrict__ Vt, int max_sweeps,
-                                                    double tol_unit, int tol_by_l, double small, int *info,
-                                                    int *status)
+                                                    int max_inner, int do_ns, double tol_unit, int tol_by_l,
+                                                    double small, int *info, int *status)
 {
-    __shared__ BDesc d;
-    __shared__ unsigned rot_count;
-    __shared__ double red[32];
-    if (threadIdx.x == 0) d = desc[blockIdx.x];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GbjSmem<T> &S = *reinterpret_cast<GbjSmem<T> *>(smem_raw);
+    if (threadIdx.x == 0) S.d = desc[blockIdx.x];
     __syncthreads();
-    const int m = d.m, n = d.n, r = d.r, l = d.l, tr = d.tr;
+    const BDesc &d = S.d;
+    const int m = d.m, n = d.n, r = d.r, l = d.l, tr = d.tr, nb = d.nb, ldx = d.ldx, ldv = d.ldv;
     T *X = work + d.off_X, *V = work + d.off_V;
     const double *A = theta + d.off_in;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kBT / 32;
-    // rotate while the cosine exceeds l eps (FP64) or 1e-5 (FP32)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int team = warp / kTeamWarps, tw = warp % kTeamWarps;
+    const int rpad = nb * kBlk;
+    // rotate while a cosine exceeds l eps (FP64) or 1e-5 (FP32)
     const double tol = tol_by_l ? tol_unit * (double)(l > 16 ? l : 16) : tol_unit;
-    // load: vectors are the columns (tr = 0) or the rows (tr = 1) of A
+
+    // load: X[i][t] = vector i (column i of A when tr = 0, row i when tr = 1),
+    // zero padded to rpad x ldx; V = identity on the first r vectors
     double f2 = 0.0;
-    for (long long e = threadIdx.x; e < (long long)r * l; e += kBT) {
-        const int i = (int)(e / l), t = (int)(e % l);
-        const double v = tr ? A[(long long)i * n + t] : A[(long long)t * n + i];
+    for (long long e = threadIdx.x; e < (long long)rpad * ldx; e += kBT) {
+        const int i = (int)(e / ldx), t = (int)(e % ldx);
+        double v = 0.0;
+        if (i < r && t < l) v = tr ? A[(long long)i * n + t] : A[(long long)t * n + i];
         X[e] = (T)v;
         f2 += v * v;
     }
-    for (long long e = threadIdx.x; e < (long long)r * r; e += kBT) V[e] = (e / r == e % r) ? (T)1 : (T)0;
-    f2 = block_sum(f2, red);
+    for (long long e = threadIdx.x; e < (long long)rpad * ldv; e += kBT) {
+        const int i = (int)(e / ldv), k = (int)(e % ldv);
+        V[e] = (i == k && i < r) ? (T)1 : (T)0;
+    }
+    f2 = block_sum(f2, S.red);
     const double floor2 = small * small * f2;
     __syncthreads();
-    const int rp = r + (r & 1), npairs = rp / 2;
+
     int sweep = 0;
     bool converged = false;
+    const int npairs = nb / 2, ntx = ldx / 32, ntv = ldv / 32;
     for (; sweep < max_sweeps; ++sweep) {
-        if (threadIdx.x == 0) rot_count = 0;
+        if (threadIdx.x == 0) S.rot_count = 0u;
         __syncthreads();
-        for (int t = 0; t < rp - 1; ++t) {
-            for (int p = warp; p < npairs; p += nw) {
-                int i, j;
-                if (p == 0) { i = rp - 1; j = t; } else { i = (t + p) % (rp - 1); j = (t - p + rp - 1) % (rp - 1); }
-                if (i >= r || j >= r) continue;
-                T *xi = X + (long long)i * l, *xj = X + (long long)j * l;
-                T a = 0, b = 0, g = 0;
-                for (int k = lane; k < l; k += 32) {
-                    const T u = xi[k], v = xj[k];
-                    a = fma(u, u, a); b = fma(v, v, b); g = fma(u, v, g);
+        for (int rnd = 0; rnd < nb - 1; ++rnd) {
+            for (int k = team; k < npairs; k += kTeams) {
+                int bi, bj;
+                circle_pair(nb, rnd, k, bi, bj);
+                const int vj = pair_vec(bi, bj, lane);
+                // 1. Gram partial over this warp's tiles of positions
+                T acc[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) acc[q] = (T)0;
+                for (int tt = tw; tt < ntx; tt += kTeamWarps) {
+                    stage32(X + (long long)vj * ldx + tt * 32, S.tile[warp], lane);
+                    __syncwarp();
+                    tile_gram(S.tile[warp], lane, acc);
+                    __syncwarp();
                 }
-                a = wsum(a); b = wsum(b); g = wsum(g);
-                if (!((double)a > floor2 && (double)b > floor2)) continue;
-                if (!(fabs((double)g) > tol * sqrt((double)a) * sqrt((double)b))) continue;
-                T c, sn;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) S.tile[warp][q][lane] = acc[q];
+                team_bar(team);
+                // 2. the team: reduce the partials, diagonalise G with cyclic
+                // Jacobi (16 disjoint rotations per step, rows then columns),
+                // accumulate Q
                 {
-                    const T zeta = (b - a) / (T(2) * g);
-                    const T tt = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-                    c = T(1) / sqrt(T(1) + tt * tt);
-                    sn = c * tt;
+                    T(*G)[33] = S.G[team];
+                    T(*Qm)[33] = S.Q[team];
+                    const int tt = tw * 32 + lane;            // 0..127 within the team
+                    const int w0 = team * kTeamWarps;
+                    for (int e = tt; e < 32 * 32; e += kTeamWarps * 32) {
+                        const int q = e >> 5, j = e & 31;
+                        T g = S.tile[w0][q][j];
+#pragma unroll
+                        for (int w = 1; w < kTeamWarps; ++w) g += S.tile[w0 + w][q][j];
+                        G[q][j] = g;
+                        Qm[q][j] = (q == j) ? (T)1 : (T)0;
+                    }
+                    team_bar(team);
+                    int first = 0, any = 0;
+                    int gstep = 0;   // running step count: consecutive steps use alternate buffers,
+                                     // including across inner sweeps (31 steps per sweep is odd)
+                    for (int isw = 0; isw < max_inner; ++isw) {
+                        int nrot = 0;
+                        for (int st = 0; st < 31; ++st, ++gstep) {
+                            const int buf = gstep & 1;
+                            if (tw == 0) {
+                                bool rot = false;
+                                if (lane < 16) {
+                                    int p, q;
+                                    circle_pair(32, st, lane, p, q);
+                                    const T a = G[p][p], b = G[q][q], g = G[p][q];
+                                    rot = (double)a > floor2 && (double)b > floor2 &&
+                                          fabs((double)g) > tol * sqrt((double)a) * sqrt((double)b);
+                                    T c = (T)1, sn = (T)0;
+                                    if (rot) {
+                                        const T zeta = (b - a) / (T(2) * g);
+                                        const T t = (zeta >= T(0) ? T(1) : T(-1)) /
+                                                    (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                                        c = T(1) / sqrt(T(1) + t * t);
+                                        sn = c * t;
+                                    }
+                                    S.rc[team][buf][lane] = c; S.rs[team][buf][lane] = sn;
+                                    S.rp[team][buf][lane] = p; S.rq[team][buf][lane] = q;
+                                }
+                                const unsigned msk = __ballot_sync(0xffffffffu, rot);
+                                if (lane == 0) S.rmask[team][buf] = msk;
+                            }
+                            team_bar(team);
+                            const unsigned msk = S.rmask[team][buf];
+                            if (msk == 0u) continue;                 // uniform over the team
+                            nrot += __popc(msk);
+                            // rows p, q of G: element (pair kk, column j)
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int e = tt + 128 * i, kk = e >> 5, j = e & 31;
+                                if ((msk >> kk) & 1u) {
+                                    const int p = S.rp[team][buf][kk], q = S.rq[team][buf][kk];
+                                    const T c = S.rc[team][buf][kk], sn = S.rs[team][buf][kk];
+                                    const T x = G[p][j], y = G[q][j];
+                                    G[p][j] = c * x - sn * y;
+                                    G[q][j] = sn * x + c * y;
+                                }
+                            }
+                            team_bar(team);
+                            // columns p, q of G and Q: element (pair kk, row j)
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int e = tt + 128 * i, kk = e >> 5, j = e & 31;
+                                if ((msk >> kk) & 1u) {
+                                    const int p = S.rp[team][buf][kk], q = S.rq[team][buf][kk];
+                                    const T c = S.rc[team][buf][kk], sn = S.rs[team][buf][kk];
+                                    const T x = G[j][p], y = G[j][q];
+                                    G[j][p] = c * x - sn * y;
+                                    G[j][q] = sn * x + c * y;
+                                    const T u = Qm[j][p], w = Qm[j][q];
+                                    Qm[j][p] = c * u - sn * w;
+                                    Qm[j][q] = sn * u + c * w;
+                                }
+                            }
+                            team_bar(team);
+                        }
+                        if (isw == 0) first = nrot;
+                        any += nrot;
+                        if (nrot == 0) break;
+                    }
+                    if (sizeof(T) == 4 && any && do_ns) {
+                        // Q holds up to max_inner x 31 FP32 rotations per column:
+                        // one Newton-Schulz step Q <- Q (3 I - Q^T Q) / 2 brings it
+                        // back to orthogonal at FP32 rounding before it is applied.
+                        // N = (3 I - Q^T Q) / 2 goes to G (no longer needed).
+                        T nv[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int e = tt + 128 * i, r0 = e >> 5, c0 = e & 31;
+                            T a = (T)0;
+#pragma unroll 8
+                            for (int k2 = 0; k2 < 32; ++k2) a = fma(Qm[k2][r0], Qm[k2][c0], a);
+                            nv[i] = (r0 == c0 ? T(1.5) : T(0)) - T(0.5) * a;
+                        }
+                        team_bar(team);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int e = tt + 128 * i;
+                            G[e >> 5][e & 31] = nv[i];
+                        }
+                        team_bar(team);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int e = tt + 128 * i, r0 = e >> 5, c0 = e & 31;
+                            T a = (T)0;
+#pragma unroll 8
+                            for (int k2 = 0; k2 < 32; ++k2) a = fma(Qm[r0][k2], G[k2][c0], a);
+                            nv[i] = a;
+                        }
+                        team_bar(team);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int e = tt + 128 * i;
+                            Qm[e >> 5][e & 31] = nv[i];
+                        }
+                    }
+                    if (tt == 0) {
+                        S.team_rot[team] = any;
+                        if (first) atomicAdd(&S.rot_count, (unsigned)first);
+                    }
                 }
-                for (int k = lane; k < l; k += 32) {
-                    const T u = xi[k], v = xj[k];
-                    xi[k] = c * u - sn * v;
-                    xj[k] = sn * u + c * v;
+                team_bar(team);
+                // 3. W <- W Q and V <- V Q (skipped when nothing rotated)
+                if (S.team_rot[team]) {
+                    T qc[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) qc[q] = S.Q[team][q][lane];
+                    for (int tt = tw; tt < ntx + ntv; tt += kTeamWarps) {
+                        T *base = tt < ntx ? X + (long long)vj * ldx + tt * 32 : V + (long long)vj * ldv + (tt - ntx) * 32;
+                        stage32(base, S.tile[warp], lane);
+                        __syncwarp();
+                        tile_apply(S.tile[warp], qc, base);
+                        __syncwarp();
+                    }
                 }
-                T *vi = V + (long long)i * r, *vj = V + (long long)j * r;
-                for (int k = lane; k < r; k += 32) {
-                    const T u = vi[k], v = vj[k];
-                    vi[k] = c * u - sn * v;
-                    vj[k] = sn * u + c * v;
-                }
-                if (lane == 0) atomicAdd(&rot_count, 1u);
+                // the next pair's Gram partials overwrite only this warp's
+                // tile; G and Q are rewritten after the next team barrier
             }
             __syncthreads();
         }
-        const unsigned tot = rot_count;
+        const unsigned tot = S.rot_count;
         __syncthreads();
         if (tot == 0u) {
             converged = true;
@@ -106,22 +387,22 @@ __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ d
         }
     }
     if (threadIdx.x == 0) {
-        info[blockIdx.x] = converged ? sweep : -sweep;
+        info[d.idx] = converged ? sweep : -sweep;
         if (!converged) atomicOr(status, ST_NOCONV);
     }
     // norms into the s slot (unsorted), then rank and write the factors
     double *sb = s + d.off_s;
-    for (int i = warp; i < r; i += nw) {
-        const T *x = X + (long long)i * l;
+    for (int i = warp; i < r; i += kWarps) {
+        const T *x = X + (long long)i * ldx;
         double a = 0.0;
         for (int k = lane; k < l; k += 32) a = fma((double)x[k], (double)x[k], a);
         a = wsum(a);
         if (lane == 0) sb[i] = sqrt(a);
     }
     __syncthreads();
-    // rank by counting (descending, ties by index), one thread per vector;
-    // the permutation is kept in the spare workspace after V
-    int *perm = reinterpret_cast<int *>(V + (long long)r * r) + 2;
+    // rank by counting (descending, ties by index), one thread per vector
+    int *perm = reinterpret_cast<int *>(work + d.off_P);
+    double *tmp = reinterpret_cast<double *>(perm + ((r + 1) & ~1));
     for (int i = threadIdx.x; i < r; i += kBT) {
         const double v = sb[i];
         int rank = 0;
@@ -134,11 +415,11 @@ __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ d
     __syncthreads();
     double *Ub = U + d.off_U, *Vb = Vt + d.off_Vt;
     // one warp per output index: sign convention "largest |U[:, c]| positive"
-    for (int c = warp; c < r; c += nw) {
+    for (int c = warp; c < r; c += kWarps) {
         const int i = perm[c];
         const double sig = sb[i];
         const double inv = sig > 0.0 ? 1.0 / sig : 0.0;
-        const T *usrc = tr ? (V + (long long)i * r) : (X + (long long)i * l);
+        const T *usrc = tr ? (V + (long long)i * ldv) : (X + (long long)i * ldx);
         const double usc = tr ? 1.0 : inv;
         double best = -1.0;
         int bi = 0;
@@ -153,13 +434,12 @@ __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ d
         }
         const double sign = ((double)usrc[bi] < 0.0) ? -1.0 : 1.0;
         for (int k = lane; k < m; k += 32) Ub[(long long)k * r + c] = sign * usc * (double)usrc[k];
-        const T *vsrc = tr ? (X + (long long)i * l) : (V + (long long)i * r);
+        const T *vsrc = tr ? (X + (long long)i * ldx) : (V + (long long)i * ldv);
         const double vsc = tr ? inv : 1.0;
         for (int k = lane; k < n; k += 32) Vb[(long long)c * n + k] = sign * vsc * (double)vsrc[k];
     }
     __syncthreads();
     // sorted singular values back into the s slot
-    double *tmp = reinterpret_cast<double *>(X);   // X no longer needed
     for (int c = threadIdx.x; c < r; c += kBT) tmp[c] = sb[perm[c]];
     __syncthreads();
     for (int c = threadIdx.x; c < r; c += kBT) sb[c] = tmp[c];
@@ -197,9 +477,9 @@ __global__ void k_decide_batched(const BDesc *__restrict__ desc, const double *_
         if (j >= k) t += Z > 0.0 ? sb[j] * sb[j] / Z : 0.0;
     const double T = block_sum(t, sh);
     if (threadIdx.x == 0) {
-        k_out[blockIdx.x] = k;
-        S_out[blockIdx.x] = S;
-        err_out[blockIdx.x] = sqrt(fmax(T, 0.0));
+        k_out[d.idx] = k;
+        S_out[d.idx] = S;
+        err_out[d.idx] = sqrt(fmax(T, 0.0));
     }
 }
 
@@ -214,7 +494,7 @@ extern "C" dmrg_status svd_truncate_batched(dmrg_ctx *ctx, int prec, int batch, 
                                             const double *theta_dev, const long long *off_in, double *U_dev,
                                             const long long *off_U, double *s_dev, const long long *off_s,
                                             double *Vt_dev, const long long *off_Vt, int chi_max, double eps,
-                                            int *k_dev, double *S_dev, double *err_dev)
+                                            int *k_dev, double *S_dev, double *err_dev, int *sweeps_dev)
 {
     if (!ctx || batch < 1 || !m || !n || !theta_dev || !off_in || !U_dev || !off_U || !s_dev || !off_s || !Vt_dev ||
         !off_Vt || chi_max < 1 || !(eps >= 0.0) || !k_dev || !S_dev || !err_dev)
@@ -222,7 +502,13 @@ extern "C" dmrg_status svd_truncate_batched(dmrg_ctx *ctx, int prec, int batch, 
     if (prec != DMRG_PREC_FP64 && prec != DMRG_PREC_3XTF32) return DMRG_EUNSUPPORTED;
     const size_t esz = prec == DMRG_PREC_FP64 ? sizeof(double) : sizeof(float);
     std::vector<BDesc> h(batch);
+    std::vector<double> cost(batch);
     long long wo = 0;
+    auto take = [&](size_t bytes) {   // element offset of a 256-byte aligned region
+        const long long o = wo;
+        wo += (long long)(al256(bytes) / esz);
+        return o;
+    };
     for (int b = 0; b < batch; ++b) {
         if (m[b] < 1 || n[b] < 1) return DMRG_EINVAL;
         BDesc &d = h[b];
@@ -231,17 +517,30 @@ extern "C" dmrg_status svd_truncate_batched(dmrg_ctx *ctx, int prec, int batch, 
         d.tr = m[b] < n[b];
         d.r = std::min(m[b], n[b]);
         d.l = std::max(m[b], n[b]);
+        d.nb = (d.r + kBlk - 1) / kBlk;
+        d.nb += d.nb & 1;
+        d.ldx = (d.l + 31) & ~31;
+        d.ldv = (d.r + 31) & ~31;
+        d.idx = b;
         d.pad = 0;
         d.off_in = off_in[b];
         d.off_U = off_U[b];
         d.off_s = off_s[b];
         d.off_Vt = off_Vt[b];
-        // X needs max(r*l, r) elements (it also holds the sorted values), V r*r plus the permutation
-        const long long xs = std::max<long long>((long long)d.r * d.l, 2LL * d.r);
-        d.off_X = wo;
-        wo += (long long)(al256(esz * xs) / esz);
-        d.off_V = wo;
-        wo += (long long)(al256(esz * ((long long)d.r * d.r) + sizeof(int) * (d.r + 8) + 16) / esz);
+        const long long rpad = (long long)d.nb * kBlk;
+        d.off_X = take(esz * rpad * d.ldx);
+        d.off_V = take(esz * rpad * d.ldv);
+        d.off_P = take(sizeof(int) * (d.r + 2) + sizeof(double) * d.r + 16);
+        cost[b] = (double)rpad * rpad * (double)(d.ldx + d.ldv);
+    }
+    // largest problems first, so that the CTAs that run longest start first
+    std::vector<int> order(batch);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    {
+        std::vector<BDesc> sorted(batch);
+        for (int b = 0; b < batch; ++b) sorted[b] = h[order[b]];
+        h.swap(sorted);
     }
     const size_t need_desc = al256(sizeof(BDesc) * batch), need_info = al256(sizeof(int) * batch);
     const size_t need = need_desc + need_info + esz * (size_t)wo;
@@ -256,22 +555,36 @@ extern "C" dmrg_status svd_truncate_batched(dmrg_ctx *ctx, int prec, int batch, 
     std::memcpy(ctx->pinned_desc, h.data(), sizeof(BDesc) * batch);
     char *base = ctx->work4.as<char>();
     BDesc *ddesc = reinterpret_cast<BDesc *>(base);
-    int *info = reinterpret_cast<int *>(base + need_desc);
+    int *info = sweeps_dev ? sweeps_dev : reinterpret_cast<int *>(base + need_desc);
     void *work = base + need_desc + need_info;
     DMRG_CUDA(cudaMemcpyAsync(ddesc, ctx->pinned_desc, sizeof(BDesc) * batch, cudaMemcpyHostToDevice, ctx->stream));
     const int sweeps = ctx->jacobi_max_sweeps;
+    const int inner = ctx->batched_inner;
+    // descriptors are in cost order; results go to each matrix's own index (BDesc::idx)
     if (prec == DMRG_PREC_FP64) {
-        k_svd_batched<double><<<batch, kBT, 0, ctx->stream>>>(ddesc, theta_dev, static_cast<double *>(work), U_dev,
-                                                              s_dev, Vt_dev, sweeps, 2.220446049250313e-16, 1,
-                                                              16.0 * 2.220446049250313e-16, info, ctx->d_status); DMRG_COUNT_LAUNCH();
-        k_decide_batched<<<batch, 256, 0, ctx->stream>>>(ddesc, s_dev, chi_max, eps, 2.220446049250313e-16, 1, k_dev,
-                                                  S_dev, err_dev); DMRG_COUNT_LAUNCH();
+        static bool attr = false;
+        if (!attr) {
+            DMRG_CUDA(cudaFuncSetAttribute(k_svd_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sizeof(GbjSmem<double>)));
+            attr = true;
+        }
+        k_svd_batched<double><<<batch, kBT, sizeof(GbjSmem<double>), ctx->stream>>>(
+            ddesc, theta_dev, static_cast<double *>(work), U_dev, s_dev, Vt_dev, sweeps, inner, 0,
+            2.220446049250313e-16, 1, 16.0 * 2.220446049250313e-16, info, ctx->d_status); DMRG_COUNT_LAUNCH();
+        k_decide_batched<<<batch, 256, 0, ctx->stream>>>(ddesc, s_dev, chi_max, eps, 2.220446049250313e-16, 1,
+                                                         k_dev, S_dev, err_dev); DMRG_COUNT_LAUNCH();
     } else {
-        k_svd_batched<float><<<batch, kBT, 0, ctx->stream>>>(ddesc, theta_dev, static_cast<float *>(work), U_dev, s_dev,
-                                                             Vt_dev, sweeps, 1e-5, 0, 1.1920928955078125e-07, info,
-                                                             ctx->d_status); DMRG_COUNT_LAUNCH();
-        k_decide_batched<<<batch, 256, 0, ctx->stream>>>(ddesc, s_dev, chi_max, eps, 2.384185791015625e-07, 0, k_dev,
-                                                         S_dev, err_dev); DMRG_COUNT_LAUNCH();
+        static bool attr = false;
+        if (!attr) {
+            DMRG_CUDA(cudaFuncSetAttribute(k_svd_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sizeof(GbjSmem<float>)));
+            attr = true;
+        }
+        k_svd_batched<float><<<batch, kBT, sizeof(GbjSmem<float>), ctx->stream>>>(
+            ddesc, theta_dev, static_cast<float *>(work), U_dev, s_dev, Vt_dev, sweeps, inner, ctx->batched_ns, 1e-5, 0,
+            ctx->batched_floor32, info, ctx->d_status); DMRG_COUNT_LAUNCH();
+        k_decide_batched<<<batch, 256, 0, ctx->stream>>>(ddesc, s_dev, chi_max, eps, 2.384185791015625e-07, 0,
+                                                         k_dev, S_dev, err_dev); DMRG_COUNT_LAUNCH();
     }
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;

@@ -118,6 +118,9 @@ struct dmrg_ctx {
     int bjac_inner = 1;          // blocked FP32 Jacobi: max inner sweeps per block pair
     double mlp_eps_target = 1e-5;// truncation-error target of the learned scheduler's label
     dmrg::DevBuf work4;          // batched SVD workspace
+    int batched_inner = 4;       // batched SVD: inner Jacobi sweeps per block pair
+    int batched_ns = 1;          // FP32 batched SVD: Newton-Schulz step on each block rotation
+    double batched_floor32 = 1.1920928955078125e-07;  // FP32 batched SVD: vectors below this x |A|_F do not rotate
     void *pinned_desc = nullptr; // batched SVD descriptors (pinned, read by the H2D copy / graph replays)
     size_t pinned_desc_bytes = 0;
 };

@@ -504,6 +504,17 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         ctx->bjac_pairs = (int)value;
         return DMRG_OK;
     }
+    if (!std::strcmp(name, "batched_inner")) {
+        if (!(value >= 1.0 && value <= 16.0)) return DMRG_EINVAL;
+        ctx->batched_inner = (int)value;
+        return DMRG_OK;
+    }
+    if (!std::strcmp(name, "batched_ns")) { ctx->batched_ns = value != 0.0; return DMRG_OK; }
+    if (!std::strcmp(name, "batched_floor32")) {
+        if (!(value >= 0.0 && value < 1e-2)) return DMRG_EINVAL;
+        ctx->batched_floor32 = value;
+        return DMRG_OK;
+    }
     if (!std::strcmp(name, "bjac_inner")) {
         if (!(value >= 1.0 && value <= 8.0)) return DMRG_EINVAL;
         ctx->bjac_inner = (int)value;

@@ -79,6 +79,7 @@ def test_batched_fp64_uneven(G, ctx):
     dev = [torch.from_numpy(A).cuda() for A in mats]
     p = ctx.svd_batched(dev, chi_max=40, eps=1e-8, prec=G.PREC_FP64)
     torch.cuda.synchronize()
+    assert (p["sweeps"].cpu().numpy() > 0).all()
     check_fp64(p, mats, 40, 1e-8)
 
 
@@ -104,6 +105,7 @@ def test_batched_fp32_form(G, ctx):
     mats = make_batch(44, shapes)
     dev = [torch.from_numpy(A).cuda() for A in mats]
     p = ctx.svd_batched(dev, chi_max=512, eps=1e-6, prec=G.PREC_3XTF32)
+    assert (p["sweeps"].cpu().numpy() > 0).all()
     U = p["U"].cpu().numpy(); s = p["s"].cpu().numpy(); Vt = p["Vt"].cpu().numpy()
     S = p["S"].cpu().numpy(); k = p["k"].cpu().numpy()
     for b, A in enumerate(mats):
@@ -168,5 +170,5 @@ def test_batched_rejects_bad_input(G, ctx):
     ki = torch.zeros(1, dtype=torch.int32, device="cuda")
     st = G.lib().svd_truncate_batched(ctx.h, G.PREC_FP64, 1, m, n, buf.data_ptr(), off, buf.data_ptr(), off,
                                       buf.data_ptr(), off, buf.data_ptr(), off, 4, 0.0, ki.data_ptr(),
-                                      buf.data_ptr(), buf.data_ptr())
+                                      buf.data_ptr(), buf.data_ptr(), None)
     assert st != 0
