@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--micro", choices=["gemm", "svd", "svd_batch"], default=None,
+    ap.add_argument("--micro", choices=["gemm", "svd", "svd_batch", "chains"], default=None,
                     help="one kernel-level invocation (for profiling): gemm M,N,K or svd chi")
     ap.add_argument("--shape", default="5120,4096,1024", help="--micro gemm: M,N,K")
     ap.add_argument("--chi", type=int, default=512, help="--micro svd: matrix 2chi x 2chi")
@@ -60,6 +60,11 @@ def parse():
     ap.add_argument("--chi-hi", type=int, default=512, help="--micro svd_batch: largest chi")
     ap.add_argument("--inner", type=int, default=4, help="--micro svd_batch: inner Jacobi sweeps per block pair")
     ap.add_argument("--floor32", type=float, default=2.0 ** -23, help="--micro svd_batch: FP32 rotation floor")
+    ap.add_argument("--n-lo", type=int, default=32, help="--micro chains: shortest chain")
+    ap.add_argument("--n-hi", type=int, default=128, help="--micro chains: longest chain")
+    ap.add_argument("--chi-max", type=int, default=256, help="--micro chains: bond dimension cap")
+    ap.add_argument("--seq", action="store_true", help="--micro chains: also time the chains one after another")
+    ap.add_argument("--warmup-sweeps", type=int, default=2, help="--micro chains: untimed sweeps first")
     return ap.parse_args()
 
 
@@ -91,6 +96,8 @@ def run_micro(args):
                "kernel_tflops": pr["flops"] / (pr["ms"] / 1e3) / 1e12 if pr["ms"] > 0 else None}
     elif args.micro == "svd_batch":
         out = svd_batch(args, G, synth, prec)
+    elif args.micro == "chains":
+        out = chains(args, G, synth, prec)
     else:
         chi = args.chi
         n = 2 * chi
@@ -152,6 +159,52 @@ def svd_batch(args, G, synth, prec):
             "not_converged": int((sw <= 0).sum()), "inner": int(args.inner), "floor32": args.floor32, "count": int(args.count), "chi": [int(args.chi_lo), int(args.chi_hi)],
             "prec": args.prec, "ms_per_batch": ms, "gflops_nominal": nominal / (ms / 1e3) / 1e9,
             "mean_k": float(np.mean(k)), "input_gen_s": gen_s}
+
+
+def chains(args, G, synth, prec):
+    """Independent XXZ chains advanced together: N uniform in [n_lo, n_hi],
+    Delta uniform in [0, 2], threshold truncation (eps 1e-10) under chi_max,
+    so each chain's spectrum sets its own uneven bond dimensions.  `reps`
+    sweeps of every chain after `warmup` sweeps; chains x sweeps / s."""
+    import numpy as np
+    import torch
+    Ns = synth.uneven_sizes(synth.workload_seed(40, 1), args.count, args.n_lo, args.n_hi)
+    Ds = synth.uniform_range(synth.workload_seed(40, 2), args.count, 0.0, 2.0)
+
+    def build():
+        out = []
+        for c in range(args.count):
+            N, D = int(Ns[c]), float(Ds[c])
+            ctx = G.Context(0, stream=torch.cuda.Stream())
+            p = G.make_params(prec=prec, ctrl=G.CTRL_THRESHOLD, chi_max=args.chi_max, chi_init=8)
+            W = ctx.build_mpo(G.XXZ, N, 1.0, D)
+            m0 = torch.from_numpy(synth.initial_mps_entries(synth.workload_seed(41, c), N, 8)).cuda()
+            torch.cuda.synchronize()
+            out.append((ctx, G.State(ctx, W, m0, p, 1.0, D)))
+        return out
+
+    pairs = build()
+    states = [st for _, st in pairs]
+    G.sweep_chains(states, args.warmup_sweeps)
+    recs, secs = G.sweep_chains(states, args.reps)
+    mean_chi = float(np.mean([r.mean_chi for rr in recs for r in rr]))
+    max_chi = int(max(r.max_chi for rr in recs for r in rr))
+    flops = float(sum(r.flops for rr in recs for r in rr))
+    res = {"micro": "chains", "count": int(args.count), "N": [int(args.n_lo), int(args.n_hi)],
+           "chi_max": int(args.chi_max), "prec": args.prec, "sweeps": int(args.reps), "seconds": secs,
+           "chain_sweeps_per_s": args.count * args.reps / secs, "mean_chi": mean_chi, "max_chi": max_chi,
+           "gflops": flops / secs / 1e9}
+    if args.seq:
+        t = 0.0
+        for st in states:
+            r, _ = st.sweep(args.reps, visits=False)
+            t += sum(x.seconds for x in r)
+        res["sequential_seconds"] = t
+        res["speedup_vs_sequential"] = t / secs
+    for ctx, st in pairs:
+        st.close()
+        ctx.close()
+    return res
 
 
 # ---------------------------------------------------------------------------

@@ -195,6 +195,21 @@ void dmrg_state_destroy(dmrg_state *st);
 dmrg_status dmrg_sweep(dmrg_ctx *ctx, dmrg_state *st, int n_sweeps, int stop_on_conv,
                        dmrg_sweep_record *rec_host, dmrg_visit_record *visits_host, int *sweeps_done);
 
+/* Advance n_chains independent chains (batched bond steps, Section 10's
+ * sweep on each) by n_sweeps sweeps each.  Chain c is states[c] on ctxs[c];
+ * every chain needs a context of its own, with a stream of its own (a
+ * context's workspace serves one chain at a time).  The bond steps are
+ * interleaved: the first phase of the current bond step of every live chain
+ * (two-site tensor, Lanczos, SVD, entropy, controller) is enqueued, then the
+ * second phase of each (truncation, split, environment update) after its
+ * retained k has reached the host, so the chains' kernels overlap on the
+ * device; chains of different lengths finish at different steps.  Results
+ * are those of dmrg_sweep on each chain alone.  rec_host (host, may be NULL)
+ * receives n_chains x n_sweeps records, chain-major; their `seconds` is 0
+ * (the chains share the device), and *seconds_out (may be NULL) gets the
+ * wall time of the whole call. */
+dmrg_status dmrg_sweep_chains(int n_chains, dmrg_ctx *const *ctxs, dmrg_state *const *states, int n_sweeps,
+                              dmrg_sweep_record *rec_host, double *seconds_out);
 /* One local update at `bond` (sites bond, bond+1) in `direction` (+1: the
  * orthogonality centre moves right, -1: left).  The state's centre must
  * be at that bond (as it is at every visit of dmrg_sweep).  *E_out (host)

@@ -119,6 +119,7 @@ def _declare(L):
         "svd_truncate_batched": (S, [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _D, _VP,
                                      _VP, _VP, _VP]),
         "dmrg_graph_begin": (S, [_VP]),
+        "dmrg_sweep_chains": (S, [_I, _VP, _VP, _I, _VP, _VP]),
         "dmrg_graph_end": (S, [_VP, C.POINTER(_VP)]),
         "dmrg_graph_launch": (S, [_VP, _VP]),
         "dmrg_graph_destroy": (S, [_VP]),
@@ -156,7 +157,7 @@ def exported_symbols():
         "dmrg_mlp_loss_grad", "dmrg_mlp_adam", "dmrg_gemm", "dmrg_set_option",
         "dmrg_state_mps_size", "dmrg_state_get_mps", "dmrg_state_put_mps", "dmrg_launch_count",
         "dmrg_profile", "dmrg_profile_read", "svd_truncate_noalloc", "dmrg_mlp_train",
-        "svd_truncate_batched", "dmrg_graph_begin", "dmrg_graph_end", "dmrg_graph_launch", "dmrg_graph_destroy",
+        "svd_truncate_batched", "dmrg_sweep_chains", "dmrg_graph_begin", "dmrg_graph_end", "dmrg_graph_launch", "dmrg_graph_destroy",
     ]
 
 
@@ -456,6 +457,20 @@ class State:
 
     def set_mlp(self, P: torch.Tensor | None):
         _check(lib().dmrg_state_set_mlp(self.h, _ptr(P) if P is not None else None), "dmrg_state_set_mlp")
+
+
+def sweep_chains(states, n_sweeps: int):
+    """Advance independent chains together (each State on a Context of its
+    own, with its own stream); returns per chain the list of sweep records and
+    the wall time of the call."""
+    n = len(states)
+    ctxs = (C.c_void_p * n)(*[st.ctx.h.value for st in states])
+    hs = (C.c_void_p * n)(*[st.h.value for st in states])
+    recs = (SweepRecord * max(1, n * n_sweeps))()
+    secs = C.c_double()
+    _check(lib().dmrg_sweep_chains(n, ctxs, hs, n_sweeps, recs, C.byref(secs)), "dmrg_sweep_chains")
+    out = [list(recs[c * n_sweeps:(c + 1) * n_sweeps]) for c in range(n)]
+    return out, secs.value
 
 
 def launch_count() -> int:

@@ -42,13 +42,14 @@ constexpr int kTeams = kWarps / kTeamWarps;
 constexpr int kBlk = 16;                       // vectors per block; a pair is one warp wide
 
 template <typename T> struct TileStride;       // row stride of a [position][vector] tile
-template <> struct TileStride<float> { static constexpr int v = 36; };   // 144 B rows
+template <> struct TileStride<float> { static constexpr int v = 44; };   // 176 B rows: conflict-free MMA fragments
 template <> struct TileStride<double> { static constexpr int v = 34; };  // 272 B rows
 
 template <typename T> struct GbjSmem {
     T tile[kWarps][32][TileStride<T>::v];      // per-warp staging tile; also the Gram partials
     T G[kTeams][32][33];
     T Q[kTeams][32][33];
+    T Qa[kTeams][32][sizeof(T) == 4 ? 44 : 1];   // FP32: the block rotation in the MMA-friendly stride
     T rc[kTeams][2][16], rs[kTeams][2][16];   // rotations of a Jacobi step, double-buffered by step parity
     int rp[kTeams][2][16], rq[kTeams][2][16];
     unsigned rmask[kTeams][2];
@@ -66,7 +67,7 @@ template <typename T> __device__ __forceinline__ T wsum(T v)
 
 // 32 consecutive elements (16-byte aligned) of one vector into column `lane`
 // of a [position][vector] tile
-__device__ __forceinline__ void stage32(const float *__restrict__ p, float (*tile)[36], int lane)
+__device__ __forceinline__ void stage32(const float *__restrict__ p, float (*tile)[44], int lane)
 {
     const float4 *q = reinterpret_cast<const float4 *>(p);
 #pragma unroll
@@ -86,20 +87,99 @@ __device__ __forceinline__ void stage32(const double *__restrict__ p, double (*t
     }
 }
 
-// acc[q] += sum_t tile[t][lane] * tile[t][q]   (row t broadcast to the warp)
-__device__ __forceinline__ void tile_gram(const float (*tile)[36], int lane, float (&acc)[32])
+// ---------------------------------------------------------------------------
+// FP32 form: the per-tile products on the tensor cores, 3xTF32 (x = hi + lo,
+// hi = tf32(x), lo = tf32(x - hi); a b ~ hi_a hi_b + hi_a lo_b + lo_a hi_b),
+// mma.m16n8k8 with FP32 accumulation.  Fragment layout of m16n8k8 (g = lane/4,
+// c = lane%4): A a0..a3 = (g, c), (g+8, c), (g, c+4), (g+8, c+4); B b0, b1 =
+// (k=c, n=g), (k=c+4, n=g); D d0..d3 = (g, 2c), (g, 2c+1), (g+8, 2c), (g+8, 2c+1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo)
 {
-#pragma unroll 4
-    for (int t = 0; t < 32; ++t) {
-        const float o = tile[t][lane];
-#pragma unroll
-        for (int q = 0; q < 32; q += 4) {
-            const float4 x = *reinterpret_cast<const float4 *>(&tile[t][q]);
-            acc[q] = fmaf(o, x.x, acc[q]); acc[q + 1] = fmaf(o, x.y, acc[q + 1]);
-            acc[q + 2] = fmaf(o, x.z, acc[q + 2]); acc[q + 3] = fmaf(o, x.w, acc[q + 3]);
-        }
-    }
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+    const float r = x - __uint_as_float(hi);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
 }
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// 3xTF32 product into d: A rows/columns from `arow(r, k)`, B from `bcol(k, n)`
+template <typename FA, typename FB>
+__device__ __forceinline__ void mma3(float (&d)[4], int g, int c, FA arow, FB bcol, int m0, int n0, int k0)
+{
+    uint32_t ah[4], al[4], bh0, bl0, bh1, bl1;
+    split_tf32(arow(m0 + g, k0 + c), ah[0], al[0]);
+    split_tf32(arow(m0 + g + 8, k0 + c), ah[1], al[1]);
+    split_tf32(arow(m0 + g, k0 + c + 4), ah[2], al[2]);
+    split_tf32(arow(m0 + g + 8, k0 + c + 4), ah[3], al[3]);
+    split_tf32(bcol(k0 + c, n0 + g), bh0, bl0);
+    split_tf32(bcol(k0 + c + 4, n0 + g), bh1, bl1);
+    mma_tf32(d, al, bh0, bh1);
+    mma_tf32(d, ah, bl0, bl1);
+    mma_tf32(d, ah, bh0, bh1);
+}
+
+// Gram partial of a tile: acc[mi][ni][.] += sum_t tile[t][m] tile[t][n],
+// m = 16 mi + ..., n = 8 ni + ... (mma D layout)
+__device__ __forceinline__ void tile_gram_tc(const float (*tile)[44], int lane, float (&acc)[2][4][4])
+{
+    const int g = lane >> 2, c = lane & 3;
+    auto a = [&](int m, int k) { return tile[k][m]; };
+    auto b = [&](int k, int n) { return tile[k][n]; };
+#pragma unroll
+    for (int ks = 0; ks < 32; ks += 8)
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni) mma3(acc[mi][ni], g, c, a, b, 16 * mi, 8 * ni, ks);
+}
+
+// p[j][t] = sum_q tile[t][q] Q[q][j] for the warp's 32 vectors j (lane = j writes
+// its own vector's 32 positions); the tile is overwritten by the result
+__device__ __forceinline__ void tile_apply_tc(float (*tile)[44], const float (*Qa)[44], int lane,
+                                              float *__restrict__ p)
+{
+    const int g = lane >> 2, c = lane & 3;
+    float d[2][4][4];
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) d[mi][ni][e] = 0.f;
+    auto a = [&](int m, int k) { return tile[m][k]; };   // A[position][old vector]
+    auto b = [&](int k, int n) { return Qa[k][n]; };     // B[old vector][new vector]
+#pragma unroll
+    for (int ks = 0; ks < 32; ks += 8)
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni) mma3(d[mi][ni], g, c, a, b, 16 * mi, 8 * ni, ks);
+    __syncwarp();
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) {
+            const int r0 = 16 * mi + g, c0 = 8 * ni + 2 * c;
+            tile[r0][c0] = d[mi][ni][0];
+            tile[r0][c0 + 1] = d[mi][ni][1];
+            tile[r0 + 8][c0] = d[mi][ni][2];
+            tile[r0 + 8][c0 + 1] = d[mi][ni][3];
+        }
+    __syncwarp();
+    float4 *o4 = reinterpret_cast<float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        o4[i] = make_float4(tile[4 * i][lane], tile[4 * i + 1][lane], tile[4 * i + 2][lane], tile[4 * i + 3][lane]);
+}
+
+// FP64: acc[q] += sum_t tile[t][lane] * tile[t][q]   (row t broadcast to the warp)
 __device__ __forceinline__ void tile_gram(const double (*tile)[34], int lane, double (&acc)[32])
 {
 #pragma unroll 4
@@ -112,29 +192,7 @@ __device__ __forceinline__ void tile_gram(const double (*tile)[34], int lane, do
         }
     }
 }
-// p[t] = sum_q qc[q] * tile[t][q] for the 32 positions, written in pieces of
-// 16 (FP32) or 8 (FP64) positions
-__device__ __forceinline__ void tile_apply(const float (*tile)[36], const float (&qc)[32], float *__restrict__ p)
-{
-#pragma unroll
-    for (int h = 0; h < 32; h += 16) {
-        float out[16];
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-            for (int q = 0; q < 32; q += 4) {
-                const float4 x = *reinterpret_cast<const float4 *>(&tile[h + t][q]);
-                a0 = fmaf(qc[q], x.x, a0); a1 = fmaf(qc[q + 1], x.y, a1);
-                a0 = fmaf(qc[q + 2], x.z, a0); a1 = fmaf(qc[q + 3], x.w, a1);
-            }
-            out[t] = a0 + a1;
-        }
-        float4 *o4 = reinterpret_cast<float4 *>(p + h);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) o4[i] = make_float4(out[4 * i], out[4 * i + 1], out[4 * i + 2], out[4 * i + 3]);
-    }
-}
+// FP64: p[t] = sum_q qc[q] * tile[t][q] for the 32 positions, written in pieces of 8
 __device__ __forceinline__ void tile_apply(const double (*tile)[34], const double (&qc)[32], double *__restrict__ p)
 {
 #pragma unroll 1
@@ -208,6 +266,7 @@ __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ d
     }
     f2 = block_sum(f2, S.red);
     const double floor2 = small * small * f2;
+    const T floor2T = (T)floor2, tolT = (T)tol;
     __syncthreads();
 
     int sweep = 0;
@@ -222,17 +281,44 @@ __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ d
                 circle_pair(nb, rnd, k, bi, bj);
                 const int vj = pair_vec(bi, bj, lane);
                 // 1. Gram partial over this warp's tiles of positions
-                T acc[32];
+                if constexpr (sizeof(T) == 4) {
+                    float acc[2][4][4];
 #pragma unroll
-                for (int q = 0; q < 32; ++q) acc[q] = (T)0;
-                for (int tt = tw; tt < ntx; tt += kTeamWarps) {
-                    stage32(X + (long long)vj * ldx + tt * 32, S.tile[warp], lane);
-                    __syncwarp();
-                    tile_gram(S.tile[warp], lane, acc);
-                    __syncwarp();
+                    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) acc[mi][ni][e] = 0.f;
+                    for (int tt = tw; tt < ntx; tt += kTeamWarps) {
+                        stage32(X + (long long)vj * ldx + tt * 32, S.tile[warp], lane);
+                        __syncwarp();
+                        tile_gram_tc(S.tile[warp], lane, acc);
+                        __syncwarp();
+                    }
+                    const int g = lane >> 2, c = lane & 3;
+#pragma unroll
+                    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                        for (int ni = 0; ni < 4; ++ni) {
+                            const int r0 = 16 * mi + g, c0 = 8 * ni + 2 * c;
+                            S.tile[warp][r0][c0] = acc[mi][ni][0];
+                            S.tile[warp][r0][c0 + 1] = acc[mi][ni][1];
+                            S.tile[warp][r0 + 8][c0] = acc[mi][ni][2];
+                            S.tile[warp][r0 + 8][c0 + 1] = acc[mi][ni][3];
+                        }
+                } else {
+                    T acc[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) acc[q] = (T)0;
+                    for (int tt = tw; tt < ntx; tt += kTeamWarps) {
+                        stage32(X + (long long)vj * ldx + tt * 32, S.tile[warp], lane);
+                        __syncwarp();
+                        tile_gram(S.tile[warp], lane, acc);
+                        __syncwarp();
+                    }
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) S.tile[warp][q][lane] = acc[q];
                 }
-#pragma unroll
-                for (int q = 0; q < 32; ++q) S.tile[warp][q][lane] = acc[q];
                 team_bar(team);
                 // 2. the team: reduce the partials, diagonalise G with cyclic
                 // Jacobi (16 disjoint rotations per step, rows then columns),
@@ -264,8 +350,9 @@ __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ d
                                     int p, q;
                                     circle_pair(32, st, lane, p, q);
                                     const T a = G[p][p], b = G[q][q], g = G[p][q];
-                                    rot = (double)a > floor2 && (double)b > floor2 &&
-                                          fabs((double)g) > tol * sqrt((double)a) * sqrt((double)b);
+                                    // |g| > tol sqrt(a b), both norms above the floor (in T:
+                                    // FP64 arithmetic is scarce on this part)
+                                    rot = a > floor2T && b > floor2T && fabs(g) > tolT * sqrt(a) * sqrt(b);
                                     T c = (T)1, sn = (T)0;
                                     if (rot) {
                                         const T zeta = (b - a) / (T(2) * g);
@@ -354,6 +441,12 @@ __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ d
                             Qm[e >> 5][e & 31] = nv[i];
                         }
                     }
+                    if constexpr (sizeof(T) == 4) {
+                        if (any) {
+                            team_bar(team);
+                            for (int e = tt; e < 32 * 32; e += kTeamWarps * 32) S.Qa[team][e >> 5][e & 31] = Qm[e >> 5][e & 31];
+                        }
+                    }
                     if (tt == 0) {
                         S.team_rot[team] = any;
                         if (first) atomicAdd(&S.rot_count, (unsigned)first);
@@ -362,15 +455,27 @@ __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ d
                 team_bar(team);
                 // 3. W <- W Q and V <- V Q (skipped when nothing rotated)
                 if (S.team_rot[team]) {
-                    T qc[32];
+                    if constexpr (sizeof(T) == 4) {
+                        for (int tt = tw; tt < ntx + ntv; tt += kTeamWarps) {
+                            T *base = tt < ntx ? X + (long long)vj * ldx + tt * 32
+                                               : V + (long long)vj * ldv + (tt - ntx) * 32;
+                            stage32(base, S.tile[warp], lane);
+                            __syncwarp();
+                            tile_apply_tc(S.tile[warp], S.Qa[team], lane, base);
+                            __syncwarp();
+                        }
+                    } else {
+                        T qc[32];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) qc[q] = S.Q[team][q][lane];
-                    for (int tt = tw; tt < ntx + ntv; tt += kTeamWarps) {
-                        T *base = tt < ntx ? X + (long long)vj * ldx + tt * 32 : V + (long long)vj * ldv + (tt - ntx) * 32;
-                        stage32(base, S.tile[warp], lane);
-                        __syncwarp();
-                        tile_apply(S.tile[warp], qc, base);
-                        __syncwarp();
+                        for (int q = 0; q < 32; ++q) qc[q] = S.Q[team][q][lane];
+                        for (int tt = tw; tt < ntx + ntv; tt += kTeamWarps) {
+                            T *base = tt < ntx ? X + (long long)vj * ldx + tt * 32
+                                               : V + (long long)vj * ldv + (tt - ntx) * 32;
+                            stage32(base, S.tile[warp], lane);
+                            __syncwarp();
+                            tile_apply(S.tile[warp], qc, base);
+                            __syncwarp();
+                        }
                     }
                 }
                 // the next pair's Gram partials overwrite only this warp's

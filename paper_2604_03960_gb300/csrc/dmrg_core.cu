@@ -20,6 +20,7 @@
 #include "lanczos.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <new>
 
@@ -459,6 +460,14 @@ struct dmrg_state {
     int sweep_index = 0;
     long long nmax = 0;
     int K = 20;
+    cudaEvent_t ev_res = nullptr;    // recorded after the bond result is copied to h_res
+    // a bond step between its two phases (bond_step_a / bond_step_b)
+    struct Pending {
+        int k = 0, go_right = 0, direction = 1, m = 0, n = 0, r = 0, cl = 0, cm = 0, cr = 0, K = 0;
+        float *X32 = nullptr;
+        double *nrm = nullptr;
+        int *perm = nullptr;
+    } pend;
 };
 
 extern "C" {
@@ -619,14 +628,24 @@ dmrg_status dmrg_build_mpo(dmrg_ctx *ctx, dmrg_model model, const dmrg_model_par
 // one local update (Section 10): theta, Lanczos, SVD, entropy + controller +
 // truncation, split, environment update
 // ---------------------------------------------------------------------------
-static dmrg_status bond_step(dmrg_state *st, int k, int go_right, int do_ctrl, dmrg_visit_record *visit,
-                             int direction, double *flops, int *k_out, double *E_out)
+// A bond step runs in two phases.  Phase A enqueues the two-site tensor, the
+// Lanczos solve, the SVD and the entropy/controller/truncation decision, and
+// starts the copy of the decision to pinned host memory (event ev_res).
+// Phase B waits for that copy (the one host synchronisation of a bond step:
+// the retained k sizes every later launch) and enqueues the split and the
+// environment update.  Several chains interleave their phases (A for all,
+// then B for all) so that their kernels overlap on the device.
+static dmrg_status bond_step_a(dmrg_state *st, int k, int go_right, int do_ctrl, dmrg_visit_record *visit,
+                               int direction)
 {
     dmrg_ctx *ctx = st->ctx;
     const int D = st->D, prec = st->p.prec;
     const int cl = st->chi[k], cm = st->chi[k + 1], cr = st->chi[k + 2];
     const int m = 2 * cl, n = 2 * cr, r = std::min(m, n);
     const long long nn = (long long)m * n;
+    auto &P = st->pend;
+    P.k = k; P.go_right = go_right; P.direction = direction;
+    P.m = m; P.n = n; P.r = r; P.cl = cl; P.cm = cm; P.cr = cr;
     // two-site tensor (Eq. 20's left-hand side)
     DMRG_TRY(gemm(ctx, prec, m, n, cm, 1.0, st->A[k], cm, 1, 0, st->A[k + 1], n, 1, 0, 0.0, st->theta, n, 1, 0, 1));
     // Lanczos on H_eff (Eq. 19)
@@ -636,6 +655,7 @@ static dmrg_status bond_step(dmrg_state *st, int k, int go_right, int do_ctrl, d
         return heff_apply_dev(ctx, prec, D, cl, cr, L, Rt, C, st->X, st->Y, x, y);
     };
     const int K = (int)std::min<long long>(st->K, nn);
+    P.K = K;
     DMRG_TRY(lanczos_run(ctx, st->lw, nn, K, st->theta, mv));
     if (prec != DMRG_PREC_FP64 && k == 0 && direction == -1) {
         // last visit of a sweep: the sweep energy is the FP64 Rayleigh
@@ -646,7 +666,6 @@ static dmrg_status bond_step(dmrg_state *st, int k, int go_right, int do_ctrl, d
         DMRG_CUDA(cudaGetLastError());
     }
     const float *mlp = st->has_mlp ? st->mlp : nullptr;
-    int kk;
     if (prec == DMRG_PREC_FP64) {
         // SVD (Eq. 20) in FP64, then entropy, controller and truncation
         DMRG_TRY(svd_jacobi(ctx, st->theta, m, n, st->U, st->s, st->Vt, st->svdw, st->p.jacobi_max_sweeps,
@@ -654,44 +673,49 @@ static dmrg_status bond_step(dmrg_state *st, int k, int go_right, int do_ctrl, d
         DMRG_TRY(launch_decide(ctx, st->s, r, st->ctrl + k, st->p, do_ctrl, 0, mlp, k, st->N, st->sweep_index,
                                st->lw.lz, st->d_res, visit, direction, (double)r * 2.220446049250313e-16,
                                st->d_info));
-        DMRG_CUDA(cudaMemcpyAsync(st->h_res, st->d_res, sizeof(BondResult), cudaMemcpyDeviceToHost, ctx->stream));
-        DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
-        kk = st->h_res->k;
-        if (kk < 1 || kk > r || kk > st->cap[k + 1]) return DMRG_ENAN;
+    } else {
+        // Mixed form: FP32 Jacobi on the vectors that become the isometry
+        // (columns of theta if the centre moves right, rows if it moves left)
+        const int dir = go_right ? 0 : 1;
+        DMRG_TRY(svd_jacobi32(ctx, st->theta, m, n, dir, st->svdw, st->p.jacobi_max_sweeps, st->d_info, st->s,
+                              &P.X32, &P.nrm, &P.perm));
+        DMRG_TRY(launch_decide(ctx, st->s, r, st->ctrl + k, st->p, do_ctrl, 0, mlp, k, st->N, st->sweep_index,
+                               st->lw.lz, st->d_res, visit, direction, kMixedRankFloor, st->d_info));
+    }
+    DMRG_CUDA(cudaMemcpyAsync(st->h_res, st->d_res, sizeof(BondResult), cudaMemcpyDeviceToHost, ctx->stream));
+    DMRG_CUDA(cudaEventRecord(st->ev_res, ctx->stream));
+    return DMRG_OK;
+}
+
+static dmrg_status bond_step_b(dmrg_state *st, double *flops, int *k_out, double *E_out)
+{
+    dmrg_ctx *ctx = st->ctx;
+    const int D = st->D, prec = st->p.prec;
+    const auto &P = st->pend;
+    const int k = P.k, go_right = P.go_right, m = P.m, n = P.n, r = P.r, cl = P.cl, cm = P.cm, cr = P.cr;
+    DMRG_CUDA(cudaEventSynchronize(st->ev_res));
+    const int kk = st->h_res->k;
+    if (kk < 1 || kk > r || kk > st->cap[k + 1]) return DMRG_ENAN;
+    if (prec == DMRG_PREC_FP64) {
         long long tot = std::max((long long)m * kk, (long long)kk * n);
         k_split<<<grid1d(tot, 256, ctx->num_sms), 256, 0, ctx->stream>>>(st->U, st->s, st->Vt, m, n, r, st->d_res,
                                                                          go_right, st->A[k], st->A[k + 1]); DMRG_COUNT_LAUNCH();
         DMRG_CUDA(cudaGetLastError());
     } else {
-        // Mixed form: FP32 Jacobi on the vectors that become the isometry
-        // (columns of theta if the centre moves right, rows if it moves left),
         // one FP64 Newton-Schulz step Q <- Q - (Q Q^T - I) Q / 2 on the k
         // retained unit vectors, and the centre tensor as the projection of
-        // theta on them (3xTF32), renormalised.
+        // theta on them (3xTF32), renormalised
         const int dir = go_right ? 0 : 1;
         const int len = dir == 0 ? m : n;
-        float *X32;
-        double *nrm;
-        int *perm;
-        DMRG_TRY(svd_jacobi32(ctx, st->theta, m, n, dir, st->svdw, st->p.jacobi_max_sweeps, st->d_info, st->s, &X32,
-                              &nrm, &perm));
-        DMRG_TRY(launch_decide(ctx, st->s, r, st->ctrl + k, st->p, do_ctrl, 0, mlp, k, st->N, st->sweep_index,
-                               st->lw.lz, st->d_res, visit, direction, kMixedRankFloor, st->d_info));
-        DMRG_CUDA(cudaMemcpyAsync(st->h_res, st->d_res, sizeof(BondResult), cudaMemcpyDeviceToHost, ctx->stream));
-        DMRG_CUDA(cudaStreamSynchronize(ctx->stream));
-        kk = st->h_res->k;
-        if (kk < 1 || kk > r || kk > st->cap[k + 1]) return DMRG_ENAN;
         double *Q = st->X, *T = st->Y, *E = st->Vt;
-        DMRG_TRY(gather_unit_vectors(ctx, X32, nrm, perm, &st->d_res->k, kk, len, Q));
+        DMRG_TRY(gather_unit_vectors(ctx, P.X32, P.nrm, P.perm, &st->d_res->k, kk, len, Q));
         DMRG_TRY(gemm_f64(ctx->stream, kk, kk, len, 1.0, Q, len, 1, 0, Q, 1, len, 0, 0.0, E, kk, 1, 0, 1));
         DMRG_CUDA(cudaMemcpyAsync(T, Q, sizeof(double) * (size_t)kk * len, cudaMemcpyDeviceToDevice, ctx->stream));
         DMRG_TRY(gemm_f64(ctx->stream, kk, len, kk, -0.5, E, kk, 1, 0, Q, len, 1, 0, 1.5, T, len, 1, 0, 1));
         if (dir == 0) {
-            dim3 g((kk + 31) / 32, (m + 31) / 32);
             // A_k = T^T (m x kk): k_transpose_rect(in = T (kk x m), out = A_k (m x kk))
             k_transpose_rect<<<dim3((m + 31) / 32, (kk + 31) / 32), dim3(32, 8), 0, ctx->stream>>>(T, st->A[k], kk, m); DMRG_COUNT_LAUNCH();
             DMRG_CUDA(cudaGetLastError());
-            (void)g;
             DMRG_TRY(gemm(ctx, prec, kk, n, m, 1.0, T, m, 1, 0, st->theta, n, 1, 0, 0.0, st->A[k + 1], n, 1, 0, 1));
             DMRG_TRY(normalise(ctx, st->A[k + 1], (long long)kk * n, st->s + r));
         } else {
@@ -702,7 +726,7 @@ static dmrg_status bond_step(dmrg_state *st, int k, int go_right, int do_ctrl, d
         }
     }
     st->chi[k + 1] = kk;
-    double f = 2.0 * m * n * cm + K * matvec_flops(D, cl, cr) + svd_nominal_flops(m, n);
+    double f = 2.0 * m * n * cm + P.K * matvec_flops(D, cl, cr) + svd_nominal_flops(m, n);
     // Environments carry the energy of whole blocks and each is built from the
     // previous one, so FP32-accumulated errors would add up along the chain:
     // the mixed form keeps them in FP64 unless the context asks otherwise.
@@ -720,6 +744,13 @@ static dmrg_status bond_step(dmrg_state *st, int k, int go_right, int do_ctrl, d
     if (k_out) *k_out = kk;
     if (E_out) *E_out = st->h_res->E;
     return DMRG_OK;
+}
+
+static dmrg_status bond_step(dmrg_state *st, int k, int go_right, int do_ctrl, dmrg_visit_record *visit,
+                             int direction, double *flops, int *k_out, double *E_out)
+{
+    DMRG_TRY(bond_step_a(st, k, go_right, do_ctrl, visit, direction));
+    return bond_step_b(st, flops, k_out, E_out);
 }
 
 dmrg_status dmrg_state_create(dmrg_ctx *ctx, int D, const dmrg_model_params *mp, const double *W_dev,
@@ -822,8 +853,14 @@ dmrg_status dmrg_state_create(dmrg_ctx *ctx, int D, const dmrg_model_params *mp,
     st->d_visits = reinterpret_cast<dmrg_visit_record *>(base + off_vis);
     st->mlp = reinterpret_cast<float *>(base + off_mlp);
     if (cudaMallocHost(&st->h_res, sizeof(BondResult)) != cudaSuccess) { st->arena.release(); delete st; return DMRG_ENOMEM; }
+    if (cudaEventCreateWithFlags(&st->ev_res, cudaEventDisableTiming) != cudaSuccess) {
+        cudaFreeHost(st->h_res); st->arena.release(); delete st; return DMRG_ECUDA;
+    }
     cudaStream_t cs = ctx->stream;
-    auto fail = [&](dmrg_status s) { cudaStreamSynchronize(cs); cudaFreeHost(st->h_res); st->arena.release(); delete st; return s; };
+    auto fail = [&](dmrg_status s) {
+        cudaStreamSynchronize(cs); cudaEventDestroy(st->ev_res); cudaFreeHost(st->h_res); st->arena.release();
+        delete st; return s;
+    };
     if (cudaMemcpyAsync(st->W, W_dev, sizeof(double) * (size_t)N * D * D * 4, cudaMemcpyDeviceToDevice, cs) != cudaSuccess)
         return fail(DMRG_ECUDA);
     // coefficient tables
@@ -881,62 +918,129 @@ void dmrg_state_destroy(dmrg_state *st)
 {
     if (!st) return;
     cudaStreamSynchronize(st->stream);
+    if (st->ev_res) cudaEventDestroy(st->ev_res);
     if (st->h_res) cudaFreeHost(st->h_res);
     st->arena.release();
     delete st;
+}
+
+// Visit v of a sweep of N sites: bond k, whether the centre moves right, the
+// direction and whether the controller steps (Section 10's sweep order).
+static void visit_of(const dmrg_state *st, int v, int &k, int &go_right, int &direction, int &do_ctrl)
+{
+    const int N = st->N;
+    const int half = v < N - 1 ? 0 : 1;
+    const int q = half == 0 ? v : v - (N - 1);
+    k = (half == 0) ? q : N - 3 - q;
+    go_right = (half == 0 && k < N - 2);
+    direction = half == 0 ? 1 : -1;
+    do_ctrl = (st->p.pid_steps_per_sweep >= 2) || (half == 0);
+}
+
+// End of a sweep: copy the visit records, fill the sweep record, advance the
+// sweep index and read the status word.
+static dmrg_status sweep_close(dmrg_state *st, double E_last, double flops, double seconds,
+                               dmrg_sweep_record *rec, dmrg_visit_record *visits_host)
+{
+    const int V = 2 * st->N - 3;
+    std::vector<dmrg_visit_record> vis(V);
+    DMRG_CUDA(cudaMemcpyAsync(vis.data(), st->d_visits, sizeof(dmrg_visit_record) * V, cudaMemcpyDeviceToHost,
+                              st->ctx->stream));
+    DMRG_CUDA(cudaStreamSynchronize(st->ctx->stream));
+    if (visits_host) std::memcpy(visits_host, vis.data(), sizeof(dmrg_visit_record) * V);
+    if (rec) {
+        dmrg_sweep_record r{};
+        r.E = E_last;
+        double mx = 0.0, sum = 0.0;
+        int mk = 0;
+        for (auto &x : vis) { mx = std::max(mx, x.trunc_err); sum += x.k; mk = std::max(mk, x.k); }
+        r.max_trunc_err = mx;
+        r.mean_chi = sum / V;
+        r.max_chi = mk;
+        r.n_visits = V;
+        r.seconds = seconds;
+        r.flops = flops;
+        *rec = r;
+    }
+    st->sweep_index++;
+    dmrg_status ds = dmrg_get_status(st->ctx);
+    if (ds != DMRG_OK && ds != DMRG_ENOCONV) return ds;
+    return DMRG_OK;
 }
 
 dmrg_status dmrg_sweep(dmrg_ctx *ctx, dmrg_state *st, int n_sweeps, int stop_on_conv, dmrg_sweep_record *rec_host,
                        dmrg_visit_record *visits_host, int *sweeps_done)
 {
     if (!ctx || !st || st->ctx != ctx || n_sweeps < 0) return DMRG_EINVAL;
-    const int N = st->N, V = 2 * N - 3;
+    const int V = 2 * st->N - 3;
     double E_prev = 0.0;
     int done = 0;
     for (int t = 0; t < n_sweeps; ++t) {
-        double flops = 0.0;
+        double flops = 0.0, E_last = 0.0;
         DMRG_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
-        int v = 0;
-        double E_last = 0.0;
-        for (int half = 0; half < 2; ++half) {
-            const int nb = (half == 0) ? N - 1 : N - 2;
-            for (int q = 0; q < nb; ++q, ++v) {
-                const int k = (half == 0) ? q : N - 3 - q;
-                const int go_right = (half == 0 && k < N - 2);
-                const int do_ctrl = (st->p.pid_steps_per_sweep >= 2) || (half == 0);
-                int kk;
-                DMRG_TRY(bond_step(st, k, go_right, do_ctrl, st->d_visits + v, half == 0 ? 1 : -1, &flops, &kk, &E_last));
-            }
+        for (int v = 0; v < V; ++v) {
+            int k, go_right, direction, do_ctrl, kk;
+            visit_of(st, v, k, go_right, direction, do_ctrl);
+            DMRG_TRY(bond_step(st, k, go_right, do_ctrl, st->d_visits + v, direction, &flops, &kk, &E_last));
         }
         DMRG_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
         DMRG_CUDA(cudaEventSynchronize(ctx->ev1));
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-        std::vector<dmrg_visit_record> vis(V);
-        DMRG_CUDA(cudaMemcpy(vis.data(), st->d_visits, sizeof(dmrg_visit_record) * V, cudaMemcpyDeviceToHost));
-        if (visits_host) std::memcpy(visits_host + (size_t)t * V, vis.data(), sizeof(dmrg_visit_record) * V);
-        if (rec_host) {
-            dmrg_sweep_record r{};
-            r.E = E_last;
-            double mx = 0.0, sum = 0.0;
-            int mk = 0;
-            for (auto &x : vis) { mx = std::max(mx, x.trunc_err); sum += x.k; mk = std::max(mk, x.k); }
-            r.max_trunc_err = mx;
-            r.mean_chi = sum / V;
-            r.max_chi = mk;
-            r.n_visits = V;
-            r.seconds = ms * 1e-3;
-            r.flops = flops;
-            rec_host[t] = r;
-        }
-        st->sweep_index++;
+        DMRG_TRY(sweep_close(st, E_last, flops, ms * 1e-3, rec_host ? rec_host + t : nullptr,
+                             visits_host ? visits_host + (size_t)t * V : nullptr));
         done = t + 1;
-        dmrg_status ds = dmrg_get_status(ctx);
-        if (ds != DMRG_OK && ds != DMRG_ENOCONV) return ds;
         if (stop_on_conv && t > 0 && std::fabs((E_last - E_prev) / E_last) < st->p.eps_conv) break;
         E_prev = E_last;
     }
     if (sweeps_done) *sweeps_done = done;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_sweep_chains(int n_chains, dmrg_ctx *const *ctxs, dmrg_state *const *states, int n_sweeps,
+                              dmrg_sweep_record *rec_host, double *seconds_out)
+{
+    if (n_chains < 1 || !ctxs || !states || n_sweeps < 0) return DMRG_EINVAL;
+    for (int c = 0; c < n_chains; ++c) {
+        if (!ctxs[c] || !states[c] || states[c]->ctx != ctxs[c]) return DMRG_EINVAL;
+        for (int d = 0; d < c; ++d)
+            if (ctxs[d] == ctxs[c] || states[d] == states[c]) return DMRG_EINVAL;   // one context per chain
+    }
+    struct Run {
+        int v = 0, sweep = 0;
+        double flops = 0.0, E_last = 0.0;
+    };
+    std::vector<Run> run(n_chains);
+    auto t0 = std::chrono::steady_clock::now();
+    int live = n_sweeps > 0 ? n_chains : 0;
+    std::vector<int> active;
+    while (live > 0) {
+        active.clear();
+        for (int c = 0; c < n_chains; ++c)
+            if (run[c].sweep < n_sweeps) active.push_back(c);
+        // phase A of every live chain, then phase B of every live chain
+        for (int c : active) {
+            dmrg_state *st = states[c];
+            int k, go_right, direction, do_ctrl;
+            visit_of(st, run[c].v, k, go_right, direction, do_ctrl);
+            DMRG_TRY(bond_step_a(st, k, go_right, do_ctrl, st->d_visits + run[c].v, direction));
+        }
+        for (int c : active) {
+            dmrg_state *st = states[c];
+            int kk;
+            DMRG_TRY(bond_step_b(st, &run[c].flops, &kk, &run[c].E_last));
+            if (++run[c].v == 2 * st->N - 3) {
+                dmrg_sweep_record *rec = rec_host ? rec_host + (size_t)c * n_sweeps + run[c].sweep : nullptr;
+                DMRG_TRY(sweep_close(st, run[c].E_last, run[c].flops, 0.0, rec, nullptr));
+                run[c].v = 0;
+                run[c].flops = 0.0;
+                if (++run[c].sweep == n_sweeps) --live;
+            }
+        }
+    }
+    for (int c = 0; c < n_chains; ++c) DMRG_CUDA(cudaStreamSynchronize(ctxs[c]->stream));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (seconds_out) *seconds_out = secs;
     return DMRG_OK;
 }
 
