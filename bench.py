@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--chi-max", type=int, default=256, help="--micro chains: bond dimension cap")
     ap.add_argument("--seq", action="store_true", help="--micro chains: also time the chains one after another")
     ap.add_argument("--warmup-sweeps", type=int, default=2, help="--micro chains: untimed sweeps first")
+    ap.add_argument("--tune-cache", default=os.path.join(ROOT, "autotune_cache.json"),
+                    help="autotuner table (loaded if present, else tuned and written); '' to tune without saving")
     return ap.parse_args()
 
 
@@ -347,6 +349,30 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+def autotune(args, ctx, chi_max):
+    """Launch choices for the workload's contraction and SVD buckets: loaded
+    from the cache file when it exists, else timed on this GPU and saved."""
+    path = args.tune_cache
+    if path and os.path.exists(path):
+        try:
+            ctx.autotune_load(path)
+            return f"loaded {os.path.basename(path)}"
+        except Exception:
+            pass
+    shapes, sizes = [], []
+    D = 5
+    chi = 128
+    while chi <= min(chi_max, 512):
+        shapes += [(D * chi, 4 * chi, chi), (4 * chi, chi, D * chi)]    # the two H_eff contractions
+        sizes.append(2 * chi)                                            # theta of the bond
+        chi *= 2
+    ctx.autotune_gemm(shapes, reps=2)
+    ctx.autotune_svd(sizes, reps=1)
+    if path:
+        ctx.autotune_save(path)
+    return f"tuned {len(shapes)} GEMM and {len(sizes)} SVD buckets"
+
+
 def run_ours(args):
     import torch
 
@@ -366,6 +392,7 @@ def run_ours(args):
     N, chi_max = wl["N"], wl["chi_max"]
     prec = G.PREC_3XTF32 if args.prec == "mixed" else G.PREC_FP64
     ctx = G.Context(local)
+    tuned = autotune(args, ctx, chi_max) if args.prec == "mixed" else "off (FP64 form)"
     p = G.make_params(chi_max=chi_max, chi_init=wl["chi_init"], ctrl=G.CTRL_THRESHOLD, prec=prec, eps_trunc=1e-10,
                       max_sweeps=args.warmup + args.steps)
     W = ctx.build_mpo(G.XXZ, N, 1.0, wl["Delta"])
@@ -472,7 +499,7 @@ def run_ours(args):
                    "chi_max": chi_max, "model": wl["model"], "d": 2, "D": 5, "lanczos_steps": 20,
                    "truncation": "per-bond threshold eps_trunc=1e-10 capped at chi_max",
                    "chi_init": wl["chi_init"], "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (MPS + environments of several GB)"},
+                   "l2": "inputs larger than L2 (MPS + environments of several GB)", "autotune": tuned},
         "svd_gflops": (svd["flops"] / (svd["ms"] / 1e3) / 1e9) if svd["ms"] > 0 else None,
         "svd_note": "nominal full-SVD count 4m^2n+8mn^2+9n^3 over the Jacobi sweep kernels' device time",
         "sweep_gflops": sweep_flops / per_sweep / 1e9,

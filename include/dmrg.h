@@ -273,6 +273,28 @@ dmrg_status svd_truncate_batched(dmrg_ctx *ctx, int prec, int batch, const int *
                                  const long long *off_U, double *s_dev, const long long *off_s, double *Vt_dev,
                                  const long long *off_Vt, int chi_max, double eps, int *k_dev, double *S_dev,
                                  double *err_dev, int *sweeps_dev);
+/* Autotuner (no counterpart in the paper): times, on this context's device
+ * and stream, the launch choices of the hot path and keeps the fastest in the
+ * context, where the launchers consult it before their heuristics.
+ * dmrg_autotune_gemm: for each M x N x K (host arrays of n_shapes), the
+ * 3xTF32 tensor-core GEMM with 128- and 256-column tiles; the choice applies
+ * to the shape's bucket (ceil log2 of each dimension).  The result bits do
+ * not depend on the tile width.  dmrg_autotune_svd: for each n (host array),
+ * the mixed-precision SVD of an n x n matrix with the blocked FP32 Jacobi's
+ * block-pair target in {24, 48, 96, 152} and 1 or 2 inner sweeps; applies to
+ * the (ceil log2 n, ceil log2 n) bucket.  Inputs are generated on the device;
+ * `reps` timed calls follow one warm-up call.  These calls allocate and free
+ * device memory and synchronise.  dmrg_autotune_save / _load write and read
+ * the tables as JSON (format "dmrg-autotune-1"); load replaces the tables and
+ * returns DMRG_EINVAL for a file that is missing or not in that format.
+ * dmrg_autotune_entries: number of GEMM (which = 0) or SVD (1) entries. */
+dmrg_status dmrg_autotune_gemm(dmrg_ctx *ctx, int n_shapes, const int *M, const int *N, const int *K, int reps);
+dmrg_status dmrg_autotune_svd(dmrg_ctx *ctx, int n_sizes, const int *n, int reps);
+dmrg_status dmrg_autotune_clear(dmrg_ctx *ctx);
+dmrg_status dmrg_autotune_save(const dmrg_ctx *ctx, const char *path);
+dmrg_status dmrg_autotune_load(dmrg_ctx *ctx, const char *path);
+int dmrg_autotune_entries(const dmrg_ctx *ctx, int which);
+
 /* CUDA-graph capture of a context's stream (which must not be the legacy
  * default stream): begin, end (instantiates into *graph_exec), launch, destroy. */
 dmrg_status dmrg_graph_begin(dmrg_ctx *ctx);

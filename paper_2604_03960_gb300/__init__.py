@@ -120,6 +120,12 @@ def _declare(L):
                                      _VP, _VP, _VP]),
         "dmrg_graph_begin": (S, [_VP]),
         "dmrg_sweep_chains": (S, [_I, _VP, _VP, _I, _VP, _VP]),
+        "dmrg_autotune_gemm": (S, [_VP, _I, _VP, _VP, _VP, _I]),
+        "dmrg_autotune_svd": (S, [_VP, _I, _VP, _I]),
+        "dmrg_autotune_clear": (S, [_VP]),
+        "dmrg_autotune_save": (S, [_VP, C.c_char_p]),
+        "dmrg_autotune_load": (S, [_VP, C.c_char_p]),
+        "dmrg_autotune_entries": (C.c_int, [_VP, _I]),
         "dmrg_graph_end": (S, [_VP, C.POINTER(_VP)]),
         "dmrg_graph_launch": (S, [_VP, _VP]),
         "dmrg_graph_destroy": (S, [_VP]),
@@ -157,7 +163,8 @@ def exported_symbols():
         "dmrg_mlp_loss_grad", "dmrg_mlp_adam", "dmrg_gemm", "dmrg_set_option",
         "dmrg_state_mps_size", "dmrg_state_get_mps", "dmrg_state_put_mps", "dmrg_launch_count",
         "dmrg_profile", "dmrg_profile_read", "svd_truncate_noalloc", "dmrg_mlp_train",
-        "svd_truncate_batched", "dmrg_sweep_chains", "dmrg_graph_begin", "dmrg_graph_end", "dmrg_graph_launch", "dmrg_graph_destroy",
+        "svd_truncate_batched", "dmrg_sweep_chains", "dmrg_autotune_gemm", "dmrg_autotune_svd",
+        "dmrg_autotune_clear", "dmrg_autotune_save", "dmrg_autotune_load", "dmrg_autotune_entries", "dmrg_graph_begin", "dmrg_graph_end", "dmrg_graph_launch", "dmrg_graph_destroy",
     ]
 
 
@@ -301,6 +308,31 @@ class Context:
                                           _ptr(p["Vt"]), P(p["oV"]), chi_max, eps, _ptr(p["k"]), _ptr(p["S"]),
                                           _ptr(p["err"]), _ptr(p["sweeps"])), "svd_truncate_batched")
         return packed
+
+    def autotune_gemm(self, shapes, reps: int = 3):
+        """Time 128- and 256-column tiles of the 3xTF32 GEMM for each (M, N, K)."""
+        n = len(shapes)
+        M = (C.c_int * n)(*[s[0] for s in shapes]); N = (C.c_int * n)(*[s[1] for s in shapes])
+        K = (C.c_int * n)(*[s[2] for s in shapes])
+        _check(lib().dmrg_autotune_gemm(self.h, n, M, N, K, reps), "dmrg_autotune_gemm")
+
+    def autotune_svd(self, sizes, reps: int = 2):
+        """Time the blocked FP32 Jacobi's grid choices for n x n SVDs."""
+        n = len(sizes)
+        arr = (C.c_int * n)(*sizes)
+        _check(lib().dmrg_autotune_svd(self.h, n, arr, reps), "dmrg_autotune_svd")
+
+    def autotune_save(self, path: str):
+        _check(lib().dmrg_autotune_save(self.h, path.encode()), "dmrg_autotune_save")
+
+    def autotune_load(self, path: str):
+        _check(lib().dmrg_autotune_load(self.h, path.encode()), "dmrg_autotune_load")
+
+    def autotune_clear(self):
+        _check(lib().dmrg_autotune_clear(self.h), "dmrg_autotune_clear")
+
+    def autotune_entries(self):
+        return int(lib().dmrg_autotune_entries(self.h, 0)), int(lib().dmrg_autotune_entries(self.h, 1))
 
     def graph_begin(self):
         _check(lib().dmrg_graph_begin(self.h), "dmrg_graph_begin")

@@ -117,6 +117,13 @@ struct dmrg_ctx {
     int bjac_pairs = 152;        // blocked FP32 Jacobi: target block pairs per round
     int bjac_inner = 1;          // blocked FP32 Jacobi: max inner sweeps per block pair
     double mlp_eps_target = 1e-5;// truncation-error target of the learned scheduler's label
+    // autotuner decisions (autotune.cu): tensor-core tile width per GEMM
+    // shape bucket, blocked-Jacobi grid target and inner sweeps per SVD
+    // size bucket; buckets are ceil(log2) of each dimension
+    struct TuneGemm { int lm, ln, lk, bn; float ms128, ms256; };
+    struct TuneSvd { int lr, ll, pairs, inner; float ms; };
+    std::vector<TuneGemm> tune_gemm;
+    std::vector<TuneSvd> tune_svd;
     dmrg::DevBuf work4;          // batched SVD workspace
     int batched_inner = 4;       // batched SVD: inner Jacobi sweeps per block pair
     int batched_ns = 1;          // FP32 batched SVD: Newton-Schulz step on each block rotation
@@ -214,6 +221,10 @@ __device__ __forceinline__ double block_sum(double v, double *sh /* >= 32 */)
 // ---------------------------------------------------------------------------
 // Host-side launchers implemented in the other translation units.
 // ---------------------------------------------------------------------------
+
+// Autotuner table lookups (autotune.cu): 0 / false when the bucket has no entry.
+int tune_lookup_bn(const dmrg_ctx *ctx, int M, int N, int K);
+bool tune_lookup_svd(const dmrg_ctx *ctx, int r, int l, int *pairs, int *inner);
 
 // FP64 strided batched GEMM:
 //   C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n)

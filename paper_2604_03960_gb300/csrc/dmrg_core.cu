@@ -292,25 +292,69 @@ __global__ void k_scale_partials(double *__restrict__ x, long long n, const doub
 
 __global__ void k_fill_int(int *p, int v) { *p = v; }
 
-// out[i][j] = in[i][j] / s[i]  (r x n), zero where s[i] == 0
-__global__ void k_scale_rows_inv(const double *__restrict__ in, double *__restrict__ out, int r, int n,
-                                 const double *__restrict__ s)
+// Norms of the rows of P (r x n) or of its columns (m x r), in FP64.
+__global__ void k_row_norms(const double *__restrict__ P, int r, int n, double *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= r) return;
+    double a = 0.0;
+    for (int j = lane; j < n; j += 32) a = fma(P[(long long)row * n + j], P[(long long)row * n + j], a);
+    a = warp_sum(a);
+    if (lane == 0) out[row] = sqrt(a);
+}
+__global__ void k_col_norms(const double *__restrict__ P, int m, int r, double *__restrict__ out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= r) return;
+    double a = 0.0;
+    for (int i = 0; i < m; ++i) a = fma(P[(long long)i * r + c], P[(long long)i * r + c], a);
+    out[c] = sqrt(a);
+}
+// perm[rank] = i with ranks by descending value, ties by index; s[c] = v[perm[c]]
+__global__ void k_rank_sorted(const double *__restrict__ v, int r, int *__restrict__ perm)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r) return;
+    const double x = v[i];
+    int rank = 0;
+    for (int j = 0; j < r; ++j) rank += (v[j] > x) || (v[j] == x && j < i);
+    perm[rank] = i;
+}
+__global__ void k_take_sorted(const double *__restrict__ v, const int *__restrict__ perm, int r, double *__restrict__ s)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < r) s[c] = v[perm[c]];
+}
+// out[c][j] = in[perm[c]][j] * (scale ? 1 / s[c] : 1)   (r x n rows)
+__global__ void k_gather_rows(const double *__restrict__ in, const int *__restrict__ perm, const double *__restrict__ s,
+                              int r, int n, double *__restrict__ out)
 {
     const long long total = (long long)r * n;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const double v = s[e / n];
-        out[e] = v > 0.0 ? in[e] / v : 0.0;
+        const int c = (int)(e / n), j = (int)(e % n);
+        const double f = s ? (s[c] > 0.0 ? 1.0 / s[c] : 0.0) : 1.0;
+        out[e] = in[(long long)perm[c] * n + j] * f;
     }
 }
-
-// out[i][j] = in[i][j] / s[j]  (m x r)
-__global__ void k_scale_cols_inv(const double *__restrict__ in, double *__restrict__ out, int m, int r,
-                                 const double *__restrict__ s)
+// out[i][c] = in[perm[c]][i]  (in r x m, out m x r)
+__global__ void k_gather_rows_t(const double *__restrict__ in, const int *__restrict__ perm, int r, int m,
+                                double *__restrict__ out)
 {
     const long long total = (long long)m * r;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const double v = s[e % r];
-        out[e] = v > 0.0 ? in[e] / v : 0.0;
+        const int i = (int)(e / r), c = (int)(e % r);
+        out[e] = in[(long long)perm[c] * m + i];
+    }
+}
+// out[i][c] = in[i][perm[c]] / s[c]  (m x r)
+__global__ void k_gather_cols_scaled(const double *__restrict__ in, const int *__restrict__ perm,
+                                     const double *__restrict__ s, int m, int r, double *__restrict__ out)
+{
+    const long long total = (long long)m * r;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / r), c = (int)(e % r);
+        out[e] = s[c] > 0.0 ? in[(long long)i * r + perm[c]] / s[c] : 0.0;
     }
 }
 
@@ -1164,8 +1208,12 @@ dmrg_status dmrg_state_set_mlp(dmrg_state *st, const float *params_dev)
 // ---------------------------------------------------------------------------
 // Mixed-precision SVD (context option svd_prec = 1): FP32 Jacobi on the
 // min(m,n) vectors of the longer side, one FP64 Newton-Schulz step on the
-// unit vectors, the other factor as diag(1/s) (isometry^T theta) on the
-// tensor cores.  Singular values below 2^-22 s_0 are not resolved.
+// unit vectors, and the FP64 projection of theta on them.  The singular
+// values are the norms of the projection: they depend on the isometry's
+// direction errors only to second order, while the FP32 Jacobi norms carry
+// the rounding of every rotation (about 1e-4 relative at n ~ 1000) and a
+// 3xTF32 projection its own (about 1e-5).  The other factor is the
+// projection scaled by 1/s.  Singular values below 2^-22 s_0 are not resolved.
 static dmrg_status svd_mixed_full(dmrg_ctx *ctx, const double *A, int m, int n, double *U, double *s, double *Vt,
                                   BondResult *res, int *info)
 {
@@ -1173,7 +1221,8 @@ static dmrg_status svd_mixed_full(dmrg_ctx *ctx, const double *A, int m, int n, 
     const int r = std::min(m, n), len = dir == 0 ? m : n;
     const size_t w1 = al256(jac32_work_bytes(dir == 0 ? n : m, len));
     const size_t need = w1 + 3 * al256(sizeof(double) * (size_t)r * len) + al256(sizeof(double) * (size_t)r * r) +
-                        al256(sizeof(double) * 512) + al256(sizeof(int) * 4);
+                        al256(sizeof(double) * 512) + al256(sizeof(int) * 4) + al256(sizeof(double) * r) +
+                        al256(sizeof(int) * r);
     DMRG_TRY(ctx->work3.ensure(need));
     char *b = ctx->work3.as<char>();
     void *jw = b; b += w1;
@@ -1181,7 +1230,9 @@ static dmrg_status svd_mixed_full(dmrg_ctx *ctx, const double *A, int m, int n, 
     double *T = reinterpret_cast<double *>(b); b += al256(sizeof(double) * (size_t)r * len);
     double *P = reinterpret_cast<double *>(b); b += al256(sizeof(double) * (size_t)r * len);
     double *E = reinterpret_cast<double *>(b); b += al256(sizeof(double) * (size_t)r * r);
-    int *rdev = reinterpret_cast<int *>(b);
+    int *rdev = reinterpret_cast<int *>(b); b += al256(sizeof(int) * 4);
+    double *pn = reinterpret_cast<double *>(b); b += al256(sizeof(double) * r);
+    int *pperm = reinterpret_cast<int *>(b);
     float *X32;
     double *nrm;
     int *perm;
@@ -1193,16 +1244,23 @@ static dmrg_status svd_mixed_full(dmrg_ctx *ctx, const double *A, int m, int n, 
     DMRG_TRY(gemm_f64(ctx->stream, r, r, len, 1.0, Q, len, 1, 0, Q, 1, len, 0, 0.0, E, r, 1, 0, 1));
     DMRG_CUDA(cudaMemcpyAsync(T, Q, sizeof(double) * (size_t)r * len, cudaMemcpyDeviceToDevice, ctx->stream));
     DMRG_TRY(gemm_f64(ctx->stream, r, len, r, -0.5, E, r, 1, 0, Q, len, 1, 0, 1.5, T, len, 1, 0, 1));
+    const int rb = (r + 255) / 256;
     if (dir == 0) {
-        // U = T^T (m x r); Vt = diag(1/s) T A  (r x n)
-        k_transpose_rect<<<dim3((m + 31) / 32, (r + 31) / 32), dim3(32, 8), 0, ctx->stream>>>(T, U, r, m); DMRG_COUNT_LAUNCH();
-        DMRG_TRY(gemm(ctx, DMRG_PREC_3XTF32, r, n, m, 1.0, T, m, 1, 0, A, n, 1, 0, 0.0, P, n, 1, 0, 1));
-        k_scale_rows_inv<<<grid1d((long long)r * n, 256, ctx->num_sms), 256, 0, ctx->stream>>>(P, Vt, r, n, s); DMRG_COUNT_LAUNCH();
+        // P = T A (r x n); s = |rows of P|, re-ranked; U = T^T, Vt = diag(1/s) P in that order
+        DMRG_TRY(gemm(ctx, DMRG_PREC_FP64, r, n, m, 1.0, T, m, 1, 0, A, n, 1, 0, 0.0, P, n, 1, 0, 1));
+        k_row_norms<<<(r * 32 + 255) / 256, 256, 0, ctx->stream>>>(P, r, n, pn); DMRG_COUNT_LAUNCH();
+        k_rank_sorted<<<rb, 256, 0, ctx->stream>>>(pn, r, pperm); DMRG_COUNT_LAUNCH();
+        k_take_sorted<<<rb, 256, 0, ctx->stream>>>(pn, pperm, r, s); DMRG_COUNT_LAUNCH();
+        k_gather_rows_t<<<grid1d((long long)m * r, 256, ctx->num_sms), 256, 0, ctx->stream>>>(T, pperm, r, m, U); DMRG_COUNT_LAUNCH();
+        k_gather_rows<<<grid1d((long long)r * n, 256, ctx->num_sms), 256, 0, ctx->stream>>>(P, pperm, s, r, n, Vt); DMRG_COUNT_LAUNCH();
     } else {
-        // Vt = T (r x n); U = A T^T diag(1/s)  (m x r)
-        DMRG_CUDA(cudaMemcpyAsync(Vt, T, sizeof(double) * (size_t)r * n, cudaMemcpyDeviceToDevice, ctx->stream));
-        DMRG_TRY(gemm(ctx, DMRG_PREC_3XTF32, m, r, n, 1.0, A, n, 1, 0, T, 1, n, 0, 0.0, P, r, 1, 0, 1));
-        k_scale_cols_inv<<<grid1d((long long)m * r, 256, ctx->num_sms), 256, 0, ctx->stream>>>(P, U, m, r, s); DMRG_COUNT_LAUNCH();
+        // P = A T^T (m x r); s = |columns of P|, re-ranked; Vt = T, U = P diag(1/s) in that order
+        DMRG_TRY(gemm(ctx, DMRG_PREC_FP64, m, r, n, 1.0, A, n, 1, 0, T, 1, n, 0, 0.0, P, r, 1, 0, 1));
+        k_col_norms<<<rb, 256, 0, ctx->stream>>>(P, m, r, pn); DMRG_COUNT_LAUNCH();
+        k_rank_sorted<<<rb, 256, 0, ctx->stream>>>(pn, r, pperm); DMRG_COUNT_LAUNCH();
+        k_take_sorted<<<rb, 256, 0, ctx->stream>>>(pn, pperm, r, s); DMRG_COUNT_LAUNCH();
+        k_gather_rows<<<grid1d((long long)r * n, 256, ctx->num_sms), 256, 0, ctx->stream>>>(T, pperm, nullptr, r, n, Vt); DMRG_COUNT_LAUNCH();
+        k_gather_cols_scaled<<<grid1d((long long)m * r, 256, ctx->num_sms), 256, 0, ctx->stream>>>(P, pperm, s, m, r, U); DMRG_COUNT_LAUNCH();
     }
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;

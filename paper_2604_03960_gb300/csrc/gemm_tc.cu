@@ -367,9 +367,13 @@ bool tc_available(dmrg_ctx *ctx)
 }
 
 // Tile width choice: 256-column tiles unless that leaves most SMs idle.
-int tc_pick_bn(dmrg_ctx *ctx, int M, int N, int batch)
+int tc_pick_bn(dmrg_ctx *ctx, int M, int N, int K, int batch)
 {
     if (ctx->tc_bn_override == 128 || ctx->tc_bn_override == 256) return ctx->tc_bn_override;
+    if (batch == 1) {
+        const int tuned = tune_lookup_bn(ctx, M, N, K);
+        if (tuned == 128 || tuned == 256) return tuned;
+    }
     long long t256 = (long long)((N + 255) / 256) * ((M + TBM - 1) / TBM) * batch;
     long long t128 = (long long)((N + 127) / 128) * ((M + TBM - 1) / TBM) * batch;
     if (N <= 128) return 128;
@@ -403,7 +407,7 @@ dmrg_status gemm_3xtf32(dmrg_ctx *ctx, int M, int N, int K, double alpha, const 
         k_split3<<<g2, dim3(32, 8), 0, ctx->stream>>>(B, sBn, sBk, sBb, N, K, Kp, Bh, 1); DMRG_COUNT_LAUNCH();
         DMRG_CUDA(cudaGetLastError());
     }
-    const int bn = tc_pick_bn(ctx, M, N, batch);
+    const int bn = tc_pick_bn(ctx, M, N, K, batch);
     if (bn == 128) return launch_tc<128>(ctx, Ah, Bh, M, N, K3, batch, alpha, beta, C, sCm, sCn, sCb);
     return launch_tc<256>(ctx, Ah, Bh, M, N, K3, batch, alpha, beta, C, sCm, sCn, sCb);
 }

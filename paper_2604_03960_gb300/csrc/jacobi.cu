@@ -622,9 +622,8 @@ __global__ void __launch_bounds__(kBjacThreads) k_bjac32(float *__restrict__ X, 
 
 template <int BW>
 dmrg_status launch_bjac32(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps, double tol, unsigned *sync,
-                          int *d_info, const double *F2, double small)
+                          int *d_info, const double *F2, double small, int max_inner)
 {
-    int max_inner = ctx->bjac_inner;
     const size_t smem = sizeof(float) * 2 * BW * (size_t)l;
     static size_t attr = 0;
     if (attr < smem) {
@@ -826,18 +825,20 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
         // each grid barrier costs a few microseconds with ~100 CTAs arriving,
         // so aim for ~48 block pairs per round: fewer, heavier rounds
         const long long cap = (200LL * 1024) / (8LL * l);      // max BW for shared memory
+        int pairs = ctx->bjac_pairs, inner = ctx->bjac_inner;
+        tune_lookup_svd(ctx, r, l, &pairs, &inner);            // autotuned bucket, if any
         int bw = 1;
-        while (bw < 16 && 2LL * bw <= cap && (r / (2 * bw)) > ctx->bjac_pairs) bw *= 2;
+        while (bw < 16 && 2LL * bw <= cap && (r / (2 * bw)) > pairs) bw *= 2;
         while (bw > 1 && (long long)bw > cap) bw /= 2;
         (void)args;
         (void)blocks;
         dmrg_status e;
         switch (bw) {
-        case 16: e = launch_bjac32<16>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small); break;
-        case 8: e = launch_bjac32<8>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small); break;
-        case 4: e = launch_bjac32<4>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small); break;
-        case 2: e = launch_bjac32<2>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small); break;
-        default: e = launch_bjac32<1>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small); break;
+        case 16: e = launch_bjac32<16>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner); break;
+        case 8: e = launch_bjac32<8>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner); break;
+        case 4: e = launch_bjac32<4>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner); break;
+        case 2: e = launch_bjac32<2>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner); break;
+        default: e = launch_bjac32<1>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner); break;
         }
         if (e != DMRG_OK) return e;
     }

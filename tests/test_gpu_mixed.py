@@ -83,3 +83,34 @@ def test_checkpoint_roundtrip(G, ctx):
     r2, _ = st.sweep(1)
     assert abs(r2[0].E - recs[-1].E) / 16 <= 1e-10
     st.close()
+
+
+@pytest.mark.parametrize("chi", [64, 256, 512])
+def test_mixed_svd_exact_spectrum(G, chi):
+    """Standalone mixed SVD (svd_prec = 1) on U diag(s) V^T with s known:
+    retained values within 1e-7 relative (FP64 norms of the FP64 projection
+    on the re-orthonormalised isometry: second order in its direction errors,
+    which the FP32 Jacobi leaves near its 1e-5 cosine tolerance) plus
+    8 sqrt(r) u |A|_F absolute, u = 2^-24: a vector near the FP32 rank floor
+    carries the rounding of its rotations against all r others, each up to
+    u times their norm, and its projection picks those components up (the
+    values there are overestimated); the isometry orthonormal to FP64
+    level after its
+    Newton-Schulz step, and the truncated reconstruction within the discarded
+    weight plus 1e-6 |A|."""
+    c = G.Context(0)
+    c.set_option("svd_prec", 1)
+    n = 2 * chi
+    s_ref = synth.spectrum("exp", n, chi)
+    A = synth.svd_test_matrix(synth.workload_seed(1, chi), n, n, s_ref)
+    U, s, Vt, k, S, err = c.svd_truncate(torch.from_numpy(A).cuda(), n, 1e-10)
+    U, s, Vt = (x.cpu().numpy() for x in (U, s, Vt))
+    fro = np.sqrt(np.sum(s_ref ** 2))
+    assert np.all(np.abs(s[:k] - s_ref[:k]) <= 1e-7 * s_ref[:k] + 8 * np.sqrt(len(s_ref)) * 2.0 ** -24 * fro)
+    assert np.abs(U[:, :k].T @ U[:, :k] - np.eye(k)).max() <= 1e-8
+    Ak = (U[:, :k] * s[:k]) @ Vt[:k]
+    tail = np.sqrt(np.sum(s_ref[k:] ** 2))
+    assert np.linalg.norm(Ak - A) <= tail + 1e-6 * np.linalg.norm(A)
+    S_ref, _ = O.entropy(s_ref)
+    assert abs(S - S_ref) <= 1e-6
+    c.close()
