@@ -58,12 +58,13 @@ def parse():
     ap.add_argument("--count", type=int, default=512, help="--micro svd_batch: number of matrices")
     ap.add_argument("--chi-lo", type=int, default=32, help="--micro svd_batch: smallest chi")
     ap.add_argument("--chi-hi", type=int, default=512, help="--micro svd_batch: largest chi")
-    ap.add_argument("--inner", type=int, default=4, help="--micro svd_batch: inner Jacobi sweeps per block pair")
+    ap.add_argument("--inner", type=int, default=1, help="--micro svd_batch: inner Jacobi sweeps per block pair")
     ap.add_argument("--floor32", type=float, default=2.0 ** -23, help="--micro svd_batch: FP32 rotation floor")
     ap.add_argument("--n-lo", type=int, default=32, help="--micro chains: shortest chain")
     ap.add_argument("--n-hi", type=int, default=128, help="--micro chains: longest chain")
     ap.add_argument("--chi-max", type=int, default=256, help="--micro chains: bond dimension cap")
     ap.add_argument("--seq", action="store_true", help="--micro chains: also time the chains one after another")
+    ap.add_argument("--no-qr", action="store_true", help="--micro svd / svd_batch: Jacobi without QR preconditioning")
     ap.add_argument("--warmup-sweeps", type=int, default=2, help="--micro chains: untimed sweeps first")
     ap.add_argument("--tune-cache", default=os.path.join(ROOT, "autotune_cache.json"),
                     help="autotuner table (loaded if present, else tuned and written); '' to tune without saving")
@@ -104,6 +105,8 @@ def run_micro(args):
         chi = args.chi
         n = 2 * chi
         ctx.set_option("svd_prec", 1 if prec == G.PREC_3XTF32 else 0)
+        if args.no_qr:
+            ctx.set_option("jacobi_qr", 0)
         A = torch.from_numpy(synth.svd_test_matrix(synth.workload_seed(1, chi), n, n,
                                                    synth.spectrum("exp", n, chi))).cuda()
         ctx.svd_truncate(A, chi, 1e-10)
@@ -113,7 +116,7 @@ def run_micro(args):
         ev1.record(ctx.stream)
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / args.reps
-        out = {"micro": "svd", "n": n, "prec": args.prec, "ms_per_call": ms,
+        out = {"micro": "svd", "n": n, "prec": args.prec, "qr_preconditioning": not args.no_qr, "ms_per_call": ms,
                "gflops_nominal": 21.0 * n ** 3 / (ms / 1e3) / 1e9}
     print(json.dumps(out))
     ctx.close()
@@ -135,6 +138,8 @@ def svd_batch(args, G, synth, prec):
     ctx = G.Context(0, stream=stream)
     ctx.set_option("batched_inner", args.inner)
     ctx.set_option("batched_floor32", args.floor32)
+    if args.no_qr:
+        ctx.set_option("jacobi_qr", 0)
     dev = [a.cuda() for a in mats]
     torch.cuda.synchronize()
     p = ctx.svd_batched(dev, chi_max=int(args.chi_hi), eps=1e-10, prec=prec)
@@ -158,7 +163,8 @@ def svd_batch(args, G, synth, prec):
     sw = p["sweeps"].cpu().numpy()
     ctx.close()
     return {"micro": "svd_batch", "sweeps": [int(np.abs(sw).min()), float(np.abs(sw).mean()), int(np.abs(sw).max())],
-            "not_converged": int((sw <= 0).sum()), "inner": int(args.inner), "floor32": args.floor32, "count": int(args.count), "chi": [int(args.chi_lo), int(args.chi_hi)],
+            "not_converged": int((sw <= 0).sum()), "inner": int(args.inner), "floor32": args.floor32,
+            "qr_preconditioning": not args.no_qr, "count": int(args.count), "chi": [int(args.chi_lo), int(args.chi_hi)],
             "prec": args.prec, "ms_per_batch": ms, "gflops_nominal": nominal / (ms / 1e3) / 1e9,
             "mean_k": float(np.mean(k)), "input_gen_s": gen_s}
 

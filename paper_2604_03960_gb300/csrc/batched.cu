@@ -33,6 +33,7 @@ struct BDesc {
     int idx, pad;                      // position of the matrix in the caller's arrays
     long long off_in, off_U, off_s, off_Vt;
     long long off_X, off_V, off_P;     // workspace: vectors, rotations, permutation + sorted values
+    long long off_R;                   // workspace: Householder reflectors of the QR preconditioning
 };
 
 constexpr int kBT = 512;                       // threads per matrix
@@ -229,12 +230,146 @@ __device__ __forceinline__ void circle_pair(int n, int t, int k, int &p, int &q)
     else { p = (t + k) % (n - 1); q = (t - k + n - 1) % (n - 1); }
 }
 
+// ---------------------------------------------------------------------------
+// QR preconditioning inside the CTA: [X | V] <- Q^T [X | V] with X = Q R
+// (Householder reflectors on the vector index, panels of 16 columns of X).
+// The Jacobi then rotates the rows of R, which converges in a third of the
+// sweeps on graded spectra, and V starts from Q^T instead of the identity so
+// that it still ends as the left factor.  The panel lives in the staging
+// tiles; the reflectors go to Vr (rows x 16, workspace); T and the panel's
+// small arrays go to the G/Q areas of team 0.
+// ---------------------------------------------------------------------------
+constexpr int kQB = 16;
+
+template <typename T>
+__device__ void cta_qr(GbjSmem<T> &S, T *__restrict__ X, T *__restrict__ V, T *__restrict__ Vr, int c, int l, int ldx,
+                       int ldv)
+{
+    T *P = &S.tile[0][0][0];                 // panel: rows x bw
+    T(*Tm)[33] = S.G[0];                     // compact-WY factor (16 x 16)
+    T(*Gv)[33] = S.Q[0];                     // V^T V of the panel
+    T *beta = &S.rc[0][0][0], *misc = &S.rs[0][0][0];
+    T *wv = &S.rc[0][1][0];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int kmax = c - 1 < l ? c - 1 : l;
+    for (int k = 0; k < kmax; k += kQB) {
+        const int bw = kmax - k < kQB ? kmax - k : kQB;
+        const int rows = c - k;
+        for (int e = tid; e < rows * bw; e += kBT) P[e] = X[(long long)(k + e / bw) * ldx + k + e % bw];
+        for (int e = tid; e < rows * kQB; e += kBT) Vr[e] = (T)0;
+        __syncthreads();
+        for (int j = 0; j < bw; ++j) {
+            double a = 0.0;
+            for (int i = j + tid; i < rows; i += kBT) {
+                const double x = (double)P[i * bw + j];
+                a = fma(x, x, a);
+            }
+            a = block_sum(a, S.red);
+            if (tid == 0) {
+                const T x0 = P[j * bw + j];
+                const double nrm = sqrt(a);
+                T b = (T)0, v0 = (T)1, alpha = x0;
+                if (rows - j > 1 && nrm > 0.0 && a > (double)x0 * (double)x0) {
+                    alpha = x0 >= (T)0 ? (T)-nrm : (T)nrm;
+                    v0 = x0 - alpha;
+                    b = (T)-1 / (alpha * v0);          // 2 / (v^T v)
+                }
+                beta[j] = b;
+                misc[0] = v0;
+                misc[1] = alpha;
+            }
+            __syncthreads();
+            const T b = beta[j], v0 = misc[0];
+            for (int i = j + tid; i < rows; i += kBT) Vr[(long long)i * kQB + j] = i == j ? v0 : P[i * bw + j];
+            if (b != (T)0) {
+                for (int q = j + 1 + warp; q < bw; q += kWarps) {
+                    T sacc = (T)0;
+                    for (int i = j + lane; i < rows; i += 32) sacc = fma(i == j ? v0 : P[i * bw + j], P[i * bw + q], sacc);
+                    sacc = wsum(sacc);
+                    if (lane == 0) wv[q] = sacc;
+                }
+                __syncthreads();
+                const int nq = bw - j - 1;
+                for (int e = tid; e < (rows - j) * nq; e += kBT) {
+                    const int i = j + e / nq, q = j + 1 + e % nq;
+                    const T vi = i == j ? v0 : P[i * bw + j];
+                    P[i * bw + q] -= b * vi * wv[q];
+                }
+            }
+            __syncthreads();
+            const T alpha = misc[1];
+            for (int i = j + tid; i < rows; i += kBT) P[i * bw + j] = (i == j) ? alpha : (T)0;
+            __syncthreads();
+        }
+        for (int e = tid; e < rows * bw; e += kBT) X[(long long)(k + e / bw) * ldx + k + e % bw] = P[e];
+        // Gram of the reflectors, then T (H_0 ... H_{bw-1} = I - V T V^T)
+        for (int pq = warp; pq < bw * bw; pq += kWarps) {
+            const int pp = pq / bw, qq = pq % bw;
+            if (pp >= qq) continue;
+            T sacc = (T)0;
+            for (int i = qq + lane; i < rows; i += 32) sacc = fma(Vr[(long long)i * kQB + pp], Vr[(long long)i * kQB + qq], sacc);
+            sacc = wsum(sacc);
+            if (lane == 0) Gv[pp][qq] = sacc;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int pp = 0; pp < kQB; ++pp)
+                for (int qq = 0; qq < kQB; ++qq) Tm[pp][qq] = (T)0;
+            for (int j = 0; j < bw; ++j) {
+                Tm[j][j] = beta[j];
+                for (int pp = 0; pp < j; ++pp) {
+                    T sacc = (T)0;
+                    for (int qq = pp; qq < j; ++qq) sacc = fma(Tm[pp][qq], Gv[qq][j], sacc);
+                    Tm[pp][j] = -beta[j] * sacc;
+                }
+            }
+        }
+        __syncthreads();
+        // trailing columns: X[k:, k+bw:ldx) and all of V[k:, 0:ldv), 32 per warp-group
+        const int nx = ldx - (k + bw), ntot = nx + ldv;
+        for (int g0 = warp * 32; g0 < ntot; g0 += kWarps * 32) {
+            const int u = g0 + lane;
+            T *col = nullptr;
+            long long ld = 0;
+            if (u < nx) { col = X + k + bw + u; ld = ldx; }
+            else if (u < ntot) { col = V + (u - nx); ld = ldv; }
+            T w[kQB];
+#pragma unroll
+            for (int j = 0; j < kQB; ++j) w[j] = (T)0;
+            if (col)
+                for (int i = 0; i < rows; ++i) {
+                    const T x = col[(long long)(k + i) * ld];
+                    const T *vi = Vr + (long long)i * kQB;
+#pragma unroll
+                    for (int j = 0; j < kQB; ++j) w[j] = fma(vi[j], x, w[j]);
+                }
+            T z[kQB];
+#pragma unroll
+            for (int j = 0; j < kQB; ++j) {
+                T sacc = (T)0;
+#pragma unroll
+                for (int t2 = 0; t2 <= j; ++t2) sacc = fma(Tm[t2][j], w[t2], sacc);
+                z[j] = sacc;
+            }
+            if (col)
+                for (int i = 0; i < rows; ++i) {
+                    const T *vi = Vr + (long long)i * kQB;
+                    T sacc = (T)0;
+#pragma unroll
+                    for (int j = 0; j < kQB; ++j) sacc = fma(vi[j], z[j], sacc);
+                    col[(long long)(k + i) * ld] -= sacc;
+                }
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ desc, const double *__restrict__ theta,
                                                     T *__restrict__ work, double *__restrict__ U,
                                                     double *__restrict__ s, double *__restrict__ Vt, int max_sweeps,
-                                                    int max_inner, int do_ns, double tol_unit, int tol_by_l,
-                                                    double small, int *info, int *status)
+                                                    int max_inner, int do_ns, int do_qr, double tol_unit,
+                                                    int tol_by_l, double small, int *info, int *status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GbjSmem<T> &S = *reinterpret_cast<GbjSmem<T> *>(smem_raw);
@@ -268,6 +403,8 @@ __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ d
     const double floor2 = small * small * f2;
     const T floor2T = (T)floor2, tolT = (T)tol;
     __syncthreads();
+    if (do_qr && r >= 32 && (long long)r * kQB <= (long long)kWarps * 32 * TileStride<T>::v)
+        cta_qr(S, X, V, work + d.off_R, r, l, ldx, ldv);
 
     int sweep = 0;
     bool converged = false;
@@ -636,6 +773,7 @@ extern "C" dmrg_status svd_truncate_batched(dmrg_ctx *ctx, int prec, int batch, 
         d.off_X = take(esz * rpad * d.ldx);
         d.off_V = take(esz * rpad * d.ldv);
         d.off_P = take(sizeof(int) * (d.r + 2) + sizeof(double) * d.r + 16);
+        d.off_R = take(esz * (size_t)d.r * kQB);
         cost[b] = (double)rpad * rpad * (double)(d.ldx + d.ldv);
     }
     // largest problems first, so that the CTAs that run longest start first
@@ -674,7 +812,7 @@ extern "C" dmrg_status svd_truncate_batched(dmrg_ctx *ctx, int prec, int batch, 
             attr = true;
         }
         k_svd_batched<double><<<batch, kBT, sizeof(GbjSmem<double>), ctx->stream>>>(
-            ddesc, theta_dev, static_cast<double *>(work), U_dev, s_dev, Vt_dev, sweeps, inner, 0,
+            ddesc, theta_dev, static_cast<double *>(work), U_dev, s_dev, Vt_dev, sweeps, inner, 0, ctx->jacobi_qr,
             2.220446049250313e-16, 1, 16.0 * 2.220446049250313e-16, info, ctx->d_status); DMRG_COUNT_LAUNCH();
         k_decide_batched<<<batch, 256, 0, ctx->stream>>>(ddesc, s_dev, chi_max, eps, 2.220446049250313e-16, 1,
                                                          k_dev, S_dev, err_dev); DMRG_COUNT_LAUNCH();
@@ -686,7 +824,7 @@ extern "C" dmrg_status svd_truncate_batched(dmrg_ctx *ctx, int prec, int batch, 
             attr = true;
         }
         k_svd_batched<float><<<batch, kBT, sizeof(GbjSmem<float>), ctx->stream>>>(
-            ddesc, theta_dev, static_cast<float *>(work), U_dev, s_dev, Vt_dev, sweeps, inner, ctx->batched_ns, 1e-5, 0,
+            ddesc, theta_dev, static_cast<float *>(work), U_dev, s_dev, Vt_dev, sweeps, inner, ctx->batched_ns, ctx->jacobi_qr, 1e-5, 0,
             ctx->batched_floor32, info, ctx->d_status); DMRG_COUNT_LAUNCH();
         k_decide_batched<<<batch, 256, 0, ctx->stream>>>(ddesc, s_dev, chi_max, eps, 2.384185791015625e-07, 0,
                                                          k_dev, S_dev, err_dev); DMRG_COUNT_LAUNCH();

@@ -127,6 +127,7 @@ struct dmrg_ctx {
     dmrg::DevBuf work4;          // batched SVD workspace
     int batched_inner = 4;       // batched SVD: inner Jacobi sweeps per block pair
     int batched_ns = 1;          // FP32 batched SVD: Newton-Schulz step on each block rotation
+    int jacobi_qr = 1;           // FP32 Jacobi on the R factor of the vectors (QR preconditioning)
     double batched_floor32 = 1.1920928955078125e-07;  // FP32 batched SVD: vectors below this x |A|_F do not rotate
     void *pinned_desc = nullptr; // batched SVD descriptors (pinned, read by the H2D copy / graph replays)
     size_t pinned_desc_bytes = 0;
@@ -221,6 +222,10 @@ __device__ __forceinline__ double block_sum(double v, double *sh /* >= 32 */)
 // ---------------------------------------------------------------------------
 // Host-side launchers implemented in the other translation units.
 // ---------------------------------------------------------------------------
+
+// QR preconditioning of the FP32 Jacobi (qr.cu): X (c x l) <- R of X = QR.
+size_t qr32_work_bytes(int c);
+dmrg_status qr_precondition32(dmrg_ctx *ctx, float *X, int c, int l, void *work);
 
 // Autotuner table lookups (autotune.cu): 0 / false when the bucket has no entry.
 int tune_lookup_bn(const dmrg_ctx *ctx, int M, int N, int K);

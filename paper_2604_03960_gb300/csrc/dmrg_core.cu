@@ -563,6 +563,7 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         return DMRG_OK;
     }
     if (!std::strcmp(name, "batched_ns")) { ctx->batched_ns = value != 0.0; return DMRG_OK; }
+    if (!std::strcmp(name, "jacobi_qr")) { ctx->jacobi_qr = value != 0.0; return DMRG_OK; }
     if (!std::strcmp(name, "batched_floor32")) {
         if (!(value >= 0.0 && value < 1e-2)) return DMRG_EINVAL;
         ctx->batched_floor32 = value;

@@ -762,7 +762,8 @@ namespace dmrg {
 size_t jac32_work_bytes(int r, int l)
 {
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    return al(sizeof(float) * (size_t)r * l) + al(sizeof(double) * r) + al(sizeof(int) * r) + al(sizeof(unsigned) * 8);
+    return al(sizeof(float) * (size_t)r * l) + al(sizeof(double) * r) + al(sizeof(int) * r) + al(sizeof(unsigned) * 8) +
+           qr32_work_bytes(r);
 }
 
 // FP32 one-sided Jacobi on the columns (dir 0) or rows (dir 1) of theta; on
@@ -778,12 +779,19 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
     float *X = reinterpret_cast<float *>(p); p += al(sizeof(float) * (size_t)r * l);
     double *nrm = reinterpret_cast<double *>(p); p += al(sizeof(double) * r);
     int *perm = reinterpret_cast<int *>(p); p += al(sizeof(int) * r);
-    unsigned *sync = reinterpret_cast<unsigned *>(p);
+    unsigned *sync = reinterpret_cast<unsigned *>(p); p += al(sizeof(unsigned) * 8);
+    void *qrw = p;
     cudaStream_t st = ctx->stream;
     {
         dim3 grid = dir == 0 ? dim3((n + 31) / 32, (m + 31) / 32) : dim3((n + 31) / 32, (m + 31) / 32);
         k_jac32_load<<<grid, dim3(32, 8), 0, st>>>(A, m, n, dir, r, l, X, sync); DMRG_COUNT_LAUNCH();
         DMRG_CUDA(cudaGetLastError());
+    }
+    // QR preconditioning: rotate the rows of R (X = Q R) instead of the rows
+    // of X -- same singular values and directions, a third of the sweeps
+    if (ctx->jacobi_qr && r >= 32) {
+        dmrg_status e = qr_precondition32(ctx, X, r, l, qrw);
+        if (e != DMRG_OK && e != DMRG_EUNSUPPORTED) return e;
     }
     // rotate while the cosine exceeds 1e-5: FP32 dot products over a few
     // thousand terms are good to ~1e-6, and the FP64 Newton-Schulz step that
