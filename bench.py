@@ -64,11 +64,19 @@ def parse():
     ap.add_argument("--n-hi", type=int, default=128, help="--micro chains: longest chain")
     ap.add_argument("--chi-max", type=int, default=256, help="--micro chains: bond dimension cap")
     ap.add_argument("--seq", action="store_true", help="--micro chains: also time the chains one after another")
+    ap.add_argument("--opt", action="append", default=[],
+                    help="context option name=value (repeatable), applied before the run")
     ap.add_argument("--no-qr", action="store_true", help="--micro svd / svd_batch: Jacobi without QR preconditioning")
     ap.add_argument("--warmup-sweeps", type=int, default=2, help="--micro chains: untimed sweeps first")
     ap.add_argument("--tune-cache", default=os.path.join(ROOT, "autotune_cache.json"),
                     help="autotuner table (loaded if present, else tuned and written); '' to tune without saving")
     return ap.parse_args()
+
+
+def apply_opts(ctx, args):
+    for kv in args.opt:
+        name, val = kv.split("=", 1)
+        ctx.set_option(name, float(val))
 
 
 def run_micro(args):
@@ -105,6 +113,7 @@ def run_micro(args):
         chi = args.chi
         n = 2 * chi
         ctx.set_option("svd_prec", 1 if prec == G.PREC_3XTF32 else 0)
+        apply_opts(ctx, args)
         if args.no_qr:
             ctx.set_option("jacobi_qr", 0)
         A = torch.from_numpy(synth.svd_test_matrix(synth.workload_seed(1, chi), n, n,
@@ -116,7 +125,8 @@ def run_micro(args):
         ev1.record(ctx.stream)
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / args.reps
-        out = {"micro": "svd", "n": n, "prec": args.prec, "qr_preconditioning": not args.no_qr, "ms_per_call": ms,
+        out = {"micro": "svd", "n": n, "prec": args.prec, "qr_preconditioning": not args.no_qr, "opts": args.opt,
+               "ms_per_call": ms,
                "gflops_nominal": 21.0 * n ** 3 / (ms / 1e3) / 1e9}
     print(json.dumps(out))
     ctx.close()
@@ -398,6 +408,7 @@ def run_ours(args):
     N, chi_max = wl["N"], wl["chi_max"]
     prec = G.PREC_3XTF32 if args.prec == "mixed" else G.PREC_FP64
     ctx = G.Context(local)
+    apply_opts(ctx, args)
     tuned = autotune(args, ctx, chi_max) if args.prec == "mixed" else "off (FP64 form)"
     p = G.make_params(chi_max=chi_max, chi_init=wl["chi_init"], ctrl=G.CTRL_THRESHOLD, prec=prec, eps_trunc=1e-10,
                       max_sweeps=args.warmup + args.steps)

@@ -364,58 +364,18 @@ __device__ void cta_qr(GbjSmem<T> &S, T *__restrict__ X, T *__restrict__ V, T *_
     }
 }
 
+// One block pair (bi, bj) of a round, processed by the calling team of four
+// warps: Gram partials over the team's tiles, team-parallel cyclic Jacobi on
+// the 32 x 32 Gram matrix, the rotation applied to the 32 vectors (and to V
+// when ntv > 0).  The number of first-inner-sweep rotations goes to
+// *rot_counter (shared or global memory).
 template <typename T>
-__global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ desc, const double *__restrict__ theta,
-                                                    T *__restrict__ work, double *__restrict__ U,
-                                                    double *__restrict__ s, double *__restrict__ Vt, int max_sweeps,
-                                                    int max_inner, int do_ns, int do_qr, double tol_unit,
-                                                    int tol_by_l, double small, int *info, int *status)
+__device__ __forceinline__ void gbj_pair(GbjSmem<T> &S, T *__restrict__ X, T *__restrict__ V, int ldx, int ldv,
+                                         int ntx, int ntv, int bi, int bj, T floor2T, T tolT, int max_inner,
+                                         int do_ns, unsigned *rot_counter)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    GbjSmem<T> &S = *reinterpret_cast<GbjSmem<T> *>(smem_raw);
-    if (threadIdx.x == 0) S.d = desc[blockIdx.x];
-    __syncthreads();
-    const BDesc &d = S.d;
-    const int m = d.m, n = d.n, r = d.r, l = d.l, tr = d.tr, nb = d.nb, ldx = d.ldx, ldv = d.ldv;
-    T *X = work + d.off_X, *V = work + d.off_V;
-    const double *A = theta + d.off_in;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int team = warp / kTeamWarps, tw = warp % kTeamWarps;
-    const int rpad = nb * kBlk;
-    // rotate while a cosine exceeds l eps (FP64) or 1e-5 (FP32)
-    const double tol = tol_by_l ? tol_unit * (double)(l > 16 ? l : 16) : tol_unit;
-
-    // load: X[i][t] = vector i (column i of A when tr = 0, row i when tr = 1),
-    // zero padded to rpad x ldx; V = identity on the first r vectors
-    double f2 = 0.0;
-    for (long long e = threadIdx.x; e < (long long)rpad * ldx; e += kBT) {
-        const int i = (int)(e / ldx), t = (int)(e % ldx);
-        double v = 0.0;
-        if (i < r && t < l) v = tr ? A[(long long)i * n + t] : A[(long long)t * n + i];
-        X[e] = (T)v;
-        f2 += v * v;
-    }
-    for (long long e = threadIdx.x; e < (long long)rpad * ldv; e += kBT) {
-        const int i = (int)(e / ldv), k = (int)(e % ldv);
-        V[e] = (i == k && i < r) ? (T)1 : (T)0;
-    }
-    f2 = block_sum(f2, S.red);
-    const double floor2 = small * small * f2;
-    const T floor2T = (T)floor2, tolT = (T)tol;
-    __syncthreads();
-    if (do_qr && r >= 32 && (long long)r * kQB <= (long long)kWarps * 32 * TileStride<T>::v)
-        cta_qr(S, X, V, work + d.off_R, r, l, ldx, ldv);
-
-    int sweep = 0;
-    bool converged = false;
-    const int npairs = nb / 2, ntx = ldx / 32, ntv = ldv / 32;
-    for (; sweep < max_sweeps; ++sweep) {
-        if (threadIdx.x == 0) S.rot_count = 0u;
-        __syncthreads();
-        for (int rnd = 0; rnd < nb - 1; ++rnd) {
-            for (int k = team; k < npairs; k += kTeams) {
-                int bi, bj;
-                circle_pair(nb, rnd, k, bi, bj);
                 const int vj = pair_vec(bi, bj, lane);
                 // 1. Gram partial over this warp's tiles of positions
                 if constexpr (sizeof(T) == 4) {
@@ -586,7 +546,7 @@ __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ d
                     }
                     if (tt == 0) {
                         S.team_rot[team] = any;
-                        if (first) atomicAdd(&S.rot_count, (unsigned)first);
+                        if (first) atomicAdd(rot_counter, (unsigned)first);
                     }
                 }
                 team_bar(team);
@@ -615,8 +575,61 @@ __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ d
                         }
                     }
                 }
-                // the next pair's Gram partials overwrite only this warp's
-                // tile; G and Q are rewritten after the next team barrier
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ desc, const double *__restrict__ theta,
+                                                    T *__restrict__ work, double *__restrict__ U,
+                                                    double *__restrict__ s, double *__restrict__ Vt, int max_sweeps,
+                                                    int max_inner, int do_ns, int do_qr, double tol_unit,
+                                                    int tol_by_l, double small, int *info, int *status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GbjSmem<T> &S = *reinterpret_cast<GbjSmem<T> *>(smem_raw);
+    if (threadIdx.x == 0) S.d = desc[blockIdx.x];
+    __syncthreads();
+    const BDesc &d = S.d;
+    const int m = d.m, n = d.n, r = d.r, l = d.l, tr = d.tr, nb = d.nb, ldx = d.ldx, ldv = d.ldv;
+    T *X = work + d.off_X, *V = work + d.off_V;
+    const double *A = theta + d.off_in;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int team = warp / kTeamWarps, tw = warp % kTeamWarps;
+    const int rpad = nb * kBlk;
+    // rotate while a cosine exceeds l eps (FP64) or 1e-5 (FP32)
+    const double tol = tol_by_l ? tol_unit * (double)(l > 16 ? l : 16) : tol_unit;
+
+    // load: X[i][t] = vector i (column i of A when tr = 0, row i when tr = 1),
+    // zero padded to rpad x ldx; V = identity on the first r vectors
+    double f2 = 0.0;
+    for (long long e = threadIdx.x; e < (long long)rpad * ldx; e += kBT) {
+        const int i = (int)(e / ldx), t = (int)(e % ldx);
+        double v = 0.0;
+        if (i < r && t < l) v = tr ? A[(long long)i * n + t] : A[(long long)t * n + i];
+        X[e] = (T)v;
+        f2 += v * v;
+    }
+    for (long long e = threadIdx.x; e < (long long)rpad * ldv; e += kBT) {
+        const int i = (int)(e / ldv), k = (int)(e % ldv);
+        V[e] = (i == k && i < r) ? (T)1 : (T)0;
+    }
+    f2 = block_sum(f2, S.red);
+    const double floor2 = small * small * f2;
+    const T floor2T = (T)floor2, tolT = (T)tol;
+    __syncthreads();
+    if (do_qr && r >= 32 && (long long)r * kQB <= (long long)kWarps * 32 * TileStride<T>::v)
+        cta_qr(S, X, V, work + d.off_R, r, l, ldx, ldv);
+
+    int sweep = 0;
+    bool converged = false;
+    const int npairs = nb / 2, ntx = ldx / 32, ntv = ldv / 32;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) S.rot_count = 0u;
+        __syncthreads();
+        for (int rnd = 0; rnd < nb - 1; ++rnd) {
+            for (int k = team; k < npairs; k += kTeams) {
+                int bi, bj;
+                circle_pair(nb, rnd, k, bi, bj);
+                gbj_pair(S, X, V, ldx, ldv, ntx, ntv, bi, bj, floor2T, tolT, max_inner, do_ns, &S.rot_count);
             }
             __syncthreads();
         }
@@ -687,6 +700,80 @@ __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ d
     for (int c = threadIdx.x; c < r; c += kBT) sb[c] = tmp[c];
 }
 
+// One matrix on many CTAs (cooperative launch): the block pairs of each
+// round are spread over all teams of the grid, with a grid barrier between
+// rounds.  FP32 vectors only (the mixed form's isometry; the other factor is
+// a projection, so no V).  X: rpad x ldx (zero padded), rotated in place.
+// sync: [0..1] barrier words, [2..3] rotation counters by sweep parity.
+__global__ void __launch_bounds__(kBT) k_gbj32_coop(float *__restrict__ X, int nb, int ldx, int l, int max_sweeps,
+                                                   double tol, const double *__restrict__ F2, double small,
+                                                   unsigned *sync, int *status, int *info, int max_inner)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GbjSmem<float> &S = *reinterpret_cast<GbjSmem<float> *>(smem_raw);
+    const int warp = threadIdx.x >> 5, team = warp / kTeamWarps;
+    unsigned *barrier = sync, *rotc = sync + 2;
+    const float floor2T = (float)(small * small * F2[0]);
+    const float tolT = (float)tol;
+    const int npairs = nb / 2, ntx = ldx / 32;
+    const int gteam = blockIdx.x * kTeams + team, nteams = gridDim.x * kTeams;
+    (void)l;
+    int sweep = 0;
+    bool converged = false;
+    for (; sweep < max_sweeps; ++sweep) {
+        for (int rnd = 0; rnd < nb - 1; ++rnd) {
+            for (int k = gteam; k < npairs; k += nteams) {
+                int bi, bj;
+                circle_pair(nb, rnd, k, bi, bj);
+                gbj_pair<float>(S, X, nullptr, ldx, 0, ntx, 0, bi, bj, floor2T, tolT, max_inner, 1,
+                                &rotc[sweep & 1]);
+            }
+            if (!grid_barrier(barrier, status)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
+                return;
+            }
+        }
+        const unsigned total = *(volatile unsigned *)&rotc[sweep & 1];
+        if (blockIdx.x == 0 && threadIdx.x == 0) rotc[(sweep + 1) & 1] = 0u;
+        if (total == 0u) {
+            converged = true;
+            ++sweep;
+            break;
+        }
+        if (!grid_barrier(barrier, status)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
+            return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        info[0] = converged ? sweep : -sweep;
+        if (!converged) atomicOr(status, ST_NOCONV);
+    }
+}
+
+// A: m x n row-major FP64; vectors = columns (dir 0, r = n, l = m) or rows
+// (dir 1, r = m, l = n) -> Xp (rpad x ldx FP32, zero padded); clears sync[0..3]
+__global__ void k_load_padded32(const double *__restrict__ A, int m, int n, int dir, int r, int l, int rpad, int ldx,
+                                float *__restrict__ Xp, unsigned *sync)
+{
+    const long long total = (long long)rpad * ldx;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ldx), t = (int)(e % ldx);
+        float v = 0.f;
+        if (i < r && t < l) v = (float)(dir == 0 ? A[(long long)t * n + i] : A[(long long)i * n + t]);
+        Xp[e] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 4) sync[threadIdx.x] = 0u;
+}
+
+// Xp (rpad x ldx) -> X (r x l), dropping the padding
+__global__ void k_unpad32(const float *__restrict__ Xp, int r, int l, int ldx, float *__restrict__ X)
+{
+    const long long total = (long long)r * l;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x)
+        X[e] = Xp[(long long)(e / l) * ldx + e % l];
+}
+
 // entropy, truncation error and k for every matrix (one CTA each)
 // (rank floor: floor_unit * r * s_0 when floor_by_r, else floor_unit * s_0)
 __global__ void k_decide_batched(const BDesc *__restrict__ desc, const double *__restrict__ s, int chi_max, double eps,
@@ -727,10 +814,75 @@ __global__ void k_decide_batched(const BDesc *__restrict__ desc, const double *_
 
 size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
+int grid1d_batched(long long n, int num_sms)
+{
+    long long b = (n + 255) / 256;
+    if (b > (long long)num_sms * 8) b = (long long)num_sms * 8;
+    return (int)(b < 1 ? 1 : b);
+}
+
 }  // namespace
 }  // namespace dmrg
 
 using namespace dmrg;
+
+namespace dmrg {
+
+size_t gbj32_padded_bytes(int r, int l)
+{
+    int nb = (r + kBlk - 1) / kBlk;
+    nb += nb & 1;
+    const size_t ldx = (size_t)((l + 31) & ~31);
+    return (((size_t)nb * kBlk * ldx * sizeof(float)) + 255) & ~size_t(255);
+}
+
+// FP32 one-sided Jacobi of the r vectors of A (columns for dir 0, rows for
+// dir 1) in Gram-block form on a cooperative grid, QR-preconditioned when the
+// context asks; the rotated vectors end in X (r x l).  Xp is the padded
+// scratch (gbj32_padded_bytes), qrw the QR scratch, sync the barrier/counter
+// words with F2 = |A|_F^2 written at sync + 4.
+dmrg_status gbj32_sweeps(dmrg_ctx *ctx, const double *A, int m, int n, int dir, float *X, float *Xp, void *qrw,
+                         unsigned *sync, int max_sweeps, double tol, double small, int *d_info)
+{
+    const int r = dir == 0 ? n : m, l = dir == 0 ? m : n;
+    int nb = (r + kBlk - 1) / kBlk;
+    nb += nb & 1;
+    const int rpad = nb * kBlk, ldx = (l + 31) & ~31;
+    cudaStream_t st = ctx->stream;
+    k_load_padded32<<<grid1d_batched((long long)rpad * ldx, ctx->num_sms), 256, 0, st>>>(A, m, n, dir, r, l, rpad, ldx,
+                                                                                         Xp, sync); DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    if (ctx->jacobi_qr && r >= 32) {
+        dmrg_status e = qr_precondition32(ctx, Xp, r, ldx, qrw);
+        if (e != DMRG_OK && e != DMRG_EUNSUPPORTED) return e;
+    }
+    double *F2 = reinterpret_cast<double *>(sync + 4);
+    DMRG_TRY(frob2_f32(ctx, Xp, (long long)rpad * ldx, F2));
+    static bool attr = false;
+    if (!attr) {
+        DMRG_CUDA(cudaFuncSetAttribute(k_gbj32_coop, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(GbjSmem<float>)));
+        attr = true;
+    }
+    int per_sm = 0;
+    DMRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gbj32_coop, kBT, sizeof(GbjSmem<float>)));
+    if (per_sm < 1) return DMRG_EUNSUPPORTED;
+    const int npairs = nb / 2;
+    int blocks = (npairs + kTeams - 1) / kTeams;
+    blocks = std::max(1, std::min(blocks, per_sm * ctx->num_sms));
+    int *status = ctx->d_status;
+    int max_inner = ctx->batched_inner;
+    const double *F2c = F2;
+    void *args[] = {&Xp, (void *)&nb, (void *)&ldx, (void *)&l, &max_sweeps, (void *)&tol, (void *)&F2c,
+                    (void *)&small, &sync, &status, &d_info, &max_inner};
+    DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_gbj32_coop, dim3(blocks), dim3(kBT), args,
+                                          sizeof(GbjSmem<float>), st)); DMRG_COUNT_LAUNCH();
+    k_unpad32<<<grid1d_batched((long long)r * l, ctx->num_sms), 256, 0, st>>>(Xp, r, l, ldx, X); DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
+}  // namespace dmrg
 
 extern "C" dmrg_status svd_truncate_batched(dmrg_ctx *ctx, int prec, int batch, const int *m, const int *n,
                                             const double *theta_dev, const long long *off_in, double *U_dev,

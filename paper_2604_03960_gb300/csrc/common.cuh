@@ -128,6 +128,8 @@ struct dmrg_ctx {
     int batched_inner = 4;       // batched SVD: inner Jacobi sweeps per block pair
     int batched_ns = 1;          // FP32 batched SVD: Newton-Schulz step on each block rotation
     int jacobi_qr = 1;           // FP32 Jacobi on the R factor of the vectors (QR preconditioning)
+    double jacobi32_floor = 1.1920928955078125e-07;   // FP32 Jacobi: vectors below this x |A|_F take no rotation
+    int gbj_min_r = 0;           // FP32 Jacobi: Gram-block cooperative form from this many vectors on (0 = off)
     double batched_floor32 = 1.1920928955078125e-07;  // FP32 batched SVD: vectors below this x |A|_F do not rotate
     void *pinned_desc = nullptr; // batched SVD descriptors (pinned, read by the H2D copy / graph replays)
     size_t pinned_desc_bytes = 0;
@@ -222,6 +224,12 @@ __device__ __forceinline__ double block_sum(double v, double *sh /* >= 32 */)
 // ---------------------------------------------------------------------------
 // Host-side launchers implemented in the other translation units.
 // ---------------------------------------------------------------------------
+
+// Gram-block FP32 Jacobi of one matrix on a cooperative grid (batched.cu).
+size_t gbj32_padded_bytes(int r, int l);
+dmrg_status gbj32_sweeps(dmrg_ctx *ctx, const double *A, int m, int n, int dir, float *X, float *Xp, void *qrw,
+                         unsigned *sync, int max_sweeps, double tol, double small, int *d_info);
+dmrg_status frob2_f32(dmrg_ctx *ctx, const float *A, long long n, double *F2);
 
 // QR preconditioning of the FP32 Jacobi (qr.cu): X (c x l) <- R of X = QR.
 size_t qr32_work_bytes(int c);

@@ -763,7 +763,14 @@ size_t jac32_work_bytes(int r, int l)
 {
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     return al(sizeof(float) * (size_t)r * l) + al(sizeof(double) * r) + al(sizeof(int) * r) + al(sizeof(unsigned) * 8) +
-           qr32_work_bytes(r);
+           al(qr32_work_bytes(r)) + gbj32_padded_bytes(r, l);
+}
+
+dmrg_status frob2_f32(dmrg_ctx *ctx, const float *A, long long n, double *F2)
+{
+    k_frob2_f<<<1, 256, 0, ctx->stream>>>(A, n, F2); DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
 }
 
 // FP32 one-sided Jacobi on the columns (dir 0) or rows (dir 1) of theta; on
@@ -780,8 +787,32 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
     double *nrm = reinterpret_cast<double *>(p); p += al(sizeof(double) * r);
     int *perm = reinterpret_cast<int *>(p); p += al(sizeof(int) * r);
     unsigned *sync = reinterpret_cast<unsigned *>(p); p += al(sizeof(unsigned) * 8);
-    void *qrw = p;
+    void *qrw = p; p += al(qr32_work_bytes(r));
+    float *Xp = reinterpret_cast<float *>(p);
     cudaStream_t st = ctx->stream;
+    // rotate while the cosine exceeds 1e-5 (see below)
+    if (ctx->gbj_min_r > 0 && r >= ctx->gbj_min_r) {
+        // Gram-block Jacobi on a cooperative grid (tensor-core Gram and
+        // rotation tiles), QR-preconditioned
+        prof_mark(ctx, PROF_JACOBI32);
+        DMRG_TRY(gbj32_sweeps(ctx, A, m, n, dir, X, Xp, qrw, sync, max_sweeps, 1.0e-5, ctx->jacobi32_floor, d_info));
+        prof_mark(ctx, PROF_JACOBI32);
+        {
+            const double M_ = l > r ? l : r, N_ = l > r ? r : l;
+            prof_count(ctx, PROF_JACOBI32, 4.0 * M_ * M_ * N_ + 8.0 * M_ * N_ * N_ + 9.0 * N_ * N_ * N_,
+                       4.0 * (double)r * l * 2.0);
+        }
+        const double *F2g = reinterpret_cast<const double *>(sync + 4);
+        k_jac32_norms<<<(r * 32 + 255) / 256, 256, 0, st>>>(X, r, l, nrm, F2g); DMRG_COUNT_LAUNCH();
+        k_jac_rank<<<(r + 255) / 256, 256, 0, st>>>(nrm, r, perm); DMRG_COUNT_LAUNCH();
+        const int r_out = m < n ? m : n;
+        k_sorted_values<<<(r_out + 255) / 256, 256, 0, st>>>(nrm, perm, r_out, s_sorted); DMRG_COUNT_LAUNCH();
+        DMRG_CUDA(cudaGetLastError());
+        *X_out = X;
+        *nrm_out = nrm;
+        *perm_out = perm;
+        return DMRG_OK;
+    }
     {
         dim3 grid = dir == 0 ? dim3((n + 31) / 32, (m + 31) / 32) : dim3((n + 31) / 32, (m + 31) / 32);
         k_jac32_load<<<grid, dim3(32, 8), 0, st>>>(A, m, n, dir, r, l, X, sync); DMRG_COUNT_LAUNCH();
@@ -811,7 +842,7 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
     int *status = ctx->d_status;
     // F2 = |A|_F^2 from the FP32 copy; vectors below 2^-23 |A|_F are dropped anyway
     const double *F2 = reinterpret_cast<const double *>(sync + 4);
-    const double small = 1.1920928955078125e-07;
+    const double small = ctx->jacobi32_floor;
     k_frob2_f<<<1, 256, 0, st>>>(X, (long long)r * l, reinterpret_cast<double *>(sync + 4)); DMRG_COUNT_LAUNCH();
     void *args[] = {&X, (void *)&r, (void *)&l, &max_sweeps, (void *)&tol, &sync, &status, &d_info, &F2,
                     (void *)&small};

@@ -40,8 +40,9 @@ def run(G, ctx, N, sweeps, prec, model=O.MODEL_XXZ, Delta=1.0, J2=0.0, **kw):
     return st, recs, vis
 
 
-@pytest.mark.parametrize("N,chi_max", [(16, 64), (24, 48)])
-def test_mixed_energy_matches_fp64_and_ed(G, ctx, N, chi_max):
+@pytest.mark.parametrize("N,chi_max,gbj", [(16, 64, 0), (24, 48, 0), (16, 64, 16)])
+def test_mixed_energy_matches_fp64_and_ed(G, ctx, N, chi_max, gbj):
+    ctx.set_option("gbj_min_r", gbj)
     kw = dict(ctrl=G.CTRL_THRESHOLD, chi_max=chi_max, chi_init=8)
     st64, r64, _ = run(G, ctx, N, 4, G.PREC_FP64, **kw)
     stm, rm, vm = run(G, ctx, N, 4, G.PREC_3XTF32, **kw)
@@ -59,6 +60,7 @@ def test_mixed_energy_matches_fp64_and_ed(G, ctx, N, chi_max):
         B = stm.site(i).cpu().numpy().reshape(chi[i], 2 * chi[i + 1])
         assert np.abs(B @ B.T - np.eye(chi[i])).max() <= 2 * chi[i] * 1e-10
     st64.close(); stm.close()
+    ctx.set_option("gbj_min_r", 0)
 
 
 def test_mixed_pid_schedule_close_to_fp64(G, ctx):
@@ -85,8 +87,8 @@ def test_checkpoint_roundtrip(G, ctx):
     st.close()
 
 
-@pytest.mark.parametrize("chi", [64, 256, 512])
-def test_mixed_svd_exact_spectrum(G, chi):
+@pytest.mark.parametrize("chi,gbj", [(64, 0), (256, 0), (512, 0), (256, 32), (512, 32)])
+def test_mixed_svd_exact_spectrum(G, chi, gbj):
     """Standalone mixed SVD (svd_prec = 1) on U diag(s) V^T with s known:
     retained values within 1e-7 relative (FP64 norms of the FP64 projection
     on the re-orthonormalised isometry: second order in its direction errors,
@@ -100,6 +102,7 @@ def test_mixed_svd_exact_spectrum(G, chi):
     weight plus 1e-6 |A|."""
     c = G.Context(0)
     c.set_option("svd_prec", 1)
+    c.set_option("gbj_min_r", gbj)          # 32: the Gram-block cooperative Jacobi
     n = 2 * chi
     s_ref = synth.spectrum("exp", n, chi)
     A = synth.svd_test_matrix(synth.workload_seed(1, chi), n, n, s_ref)
