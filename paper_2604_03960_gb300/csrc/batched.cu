@@ -259,18 +259,24 @@ __device__ void cta_qr(GbjSmem<T> &S, T *__restrict__ X, T *__restrict__ V, T *_
         for (int e = tid; e < rows * kQB; e += kBT) Vr[e] = (T)0;
         __syncthreads();
         for (int j = 0; j < bw; ++j) {
-            double a = 0.0;
+            // column norm in the working precision (FP64 is scarce on this part)
+            T a = (T)0;
             for (int i = j + tid; i < rows; i += kBT) {
-                const double x = (double)P[i * bw + j];
+                const T x = P[i * bw + j];
                 a = fma(x, x, a);
             }
-            a = block_sum(a, S.red);
+            a = wsum(a);
+            if (lane == 0) S.red[warp] = (double)a;
+            __syncthreads();
             if (tid == 0) {
+                T sacc = (T)0;
+                for (int w = 0; w < kWarps; ++w) sacc += (T)S.red[w];
+                a = sacc;
                 const T x0 = P[j * bw + j];
-                const double nrm = sqrt(a);
+                const T nrm = sqrt(a);
                 T b = (T)0, v0 = (T)1, alpha = x0;
-                if (rows - j > 1 && nrm > 0.0 && a > (double)x0 * (double)x0) {
-                    alpha = x0 >= (T)0 ? (T)-nrm : (T)nrm;
+                if (rows - j > 1 && nrm > (T)0 && a > x0 * x0) {
+                    alpha = x0 >= (T)0 ? -nrm : nrm;
                     v0 = x0 - alpha;
                     b = (T)-1 / (alpha * v0);          // 2 / (v^T v)
                 }

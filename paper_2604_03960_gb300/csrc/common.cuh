@@ -83,7 +83,10 @@ SvdWork svd_work_carve(void *base, int r, int l);
 namespace dmrg {
 // Live per-kernel timing (CUDA events on the context stream), enabled by
 // dmrg_profile; used for the roofline of the dominant kernel.
-enum ProfKind { PROF_TC_GEMM = 0, PROF_JACOBI32 = 1, PROF_JACOBI64 = 2, PROF_F64_GEMM = 3, PROF_KINDS = 4 };
+enum ProfKind {
+    PROF_TC_GEMM = 0, PROF_JACOBI32 = 1, PROF_JACOBI64 = 2, PROF_F64_GEMM = 3, PROF_MIX = 4, PROF_F32_GEMM = 5,
+    PROF_QR = 6, PROF_KINDS = 7
+};
 struct ProfSlot {
     std::vector<cudaEvent_t> ev;
     size_t used = 0;
@@ -114,7 +117,7 @@ struct dmrg_ctx {
     dmrg::ProfSlot prof_slot[dmrg::PROF_KINDS];
     int mixed_env_tc = 0;        // 1: environment updates of the mixed form on the tensor cores too
     int svd_prec = 0;            // standalone svd_truncate: 0 FP64 Jacobi, 1 mixed
-    int bjac_pairs = 152;        // blocked FP32 Jacobi: target block pairs per round
+    int bjac_pairs = 48;        // blocked FP32 Jacobi: target block pairs per round
     int bjac_inner = 1;          // blocked FP32 Jacobi: max inner sweeps per block pair
     double mlp_eps_target = 1e-5;// truncation-error target of the learned scheduler's label
     // autotuner decisions (autotune.cu): tensor-core tile width per GEMM

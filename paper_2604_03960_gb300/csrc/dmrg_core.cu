@@ -377,7 +377,10 @@ size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 static dmrg_status mix(dmrg_ctx *ctx, const double *in, double *out, const double *C, const MixDesc &d)
 {
     long long total = (long long)d.An * d.Bn;
+    prof_mark(ctx, PROF_MIX);
     k_mix<<<grid1d(total, kMixThreads, ctx->num_sms), kMixThreads, 0, ctx->stream>>>(in, out, C, d); DMRG_COUNT_LAUNCH();
+    prof_mark(ctx, PROF_MIX);
+    prof_count(ctx, PROF_MIX, 0.0, 8.0 * (double)total * (d.nin + d.nout));   // each input and output channel once
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }
@@ -750,7 +753,11 @@ static dmrg_status bond_step_b(dmrg_state *st, double *flops, int *k_out, double
     const int k = P.k, go_right = P.go_right, m = P.m, n = P.n, r = P.r, cl = P.cl, cm = P.cm, cr = P.cr;
     DMRG_CUDA(cudaEventSynchronize(st->ev_res));
     const int kk = st->h_res->k;
-    if (kk < 1 || kk > r || kk > st->cap[k + 1]) return DMRG_ENAN;
+    if (kk < 1 || kk > r || kk > st->cap[k + 1]) {
+        std::fprintf(stderr, "dmrg: bond %d: retained k = %d outside [1, min(r = %d, cap = %d)] (S = %g)\n", k, kk, r,
+                     st->cap[k + 1], st->h_res->S);
+        return DMRG_ENAN;
+    }
     if (prec == DMRG_PREC_FP64) {
         long long tot = std::max((long long)m * kk, (long long)kk * n);
         k_split<<<grid1d(tot, 256, ctx->num_sms), 256, 0, ctx->stream>>>(st->U, st->s, st->Vt, m, n, r, st->d_res,

@@ -391,9 +391,14 @@ dmrg_status gemm_3xtf32(dmrg_ctx *ctx, int M, int N, int K, double alpha, const 
     if (!tc_available(ctx)) return DMRG_EUNSUPPORTED;
     // small products: FP32 arithmetic on the CUDA cores is faster than
     // splitting into TF32 parts, at the same precision class
-    if (K <= 0 || (!ctx->tc_force && (double)M * N * K * batch < (double)ctx->tc_min_work))
-        return gemm_f32c(ctx->stream, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb,
-                         batch);
+    if (K <= 0 || (!ctx->tc_force && (double)M * N * K * batch < (double)ctx->tc_min_work)) {
+        prof_mark(ctx, PROF_F32_GEMM);
+        dmrg_status e = gemm_f32c(ctx->stream, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn,
+                                  sCb, batch);
+        prof_mark(ctx, PROF_F32_GEMM);
+        prof_count(ctx, PROF_F32_GEMM, 2.0 * M * N * (double)(K > 0 ? K : 0) * batch, 0.0);
+        return e;
+    }
     if (batch > 65535 || (M + TBM - 1) / TBM > 65535) return DMRG_EINVAL;
     const int Kp = (K + 31) / 32 * 32, K3 = 3 * Kp;
     const size_t bytesA = sizeof(float) * (size_t)batch * M * K3, bytesB = sizeof(float) * (size_t)batch * N * K3;

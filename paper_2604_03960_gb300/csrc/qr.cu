@@ -32,70 +32,74 @@ __device__ __forceinline__ float wsumf(float v)
     return v;
 }
 
+// Row ownership: thread t owns panel rows t, t + 512, ...; it alone reads and
+// writes them, so a column step needs only two block reductions -- the norm
+// of the column (which also publishes its diagonal entry) and the products of
+// the reflector with the columns to its right -- and every thread derives the
+// reflector from the reduced norm itself.  Panel rows have stride kQrB + 1.
+constexpr int kPS = kQrB + 1;
+
 __global__ void __launch_bounds__(kQrPanelThreads) k_qr_panel(float *__restrict__ X, int c, int l, int k, int bw,
                                                               float *__restrict__ V, float *__restrict__ T)
 {
-    extern __shared__ float P[];                   // rows x bw, row-major
-    __shared__ double red[32];
-    __shared__ float wv[kQrB], sbeta[kQrB], G[kQrB][kQrB + 1];
-    __shared__ float sv0, salpha;
-    const int rows = c - k, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kQrPanelThreads / 32;
-    for (int e = tid; e < rows * bw; e += kQrPanelThreads) {
-        const int i = e / bw, j = e % bw;
-        P[e] = X[(long long)(k + i) * l + k + j];
+    extern __shared__ float P[];                   // rows x kPS
+    constexpr int nw = kQrPanelThreads / 32;
+    __shared__ float part[nw][kQrB];
+    __shared__ float npart[nw];
+    __shared__ float sbeta[kQrB], G[kQrB][kQrB + 1];
+    const int rows = c - k, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < rows; i += kQrPanelThreads) {
+        for (int j = 0; j < bw; ++j) P[i * kPS + j] = X[(long long)(k + i) * l + k + j];
+        for (int j = 0; j < kQrB; ++j) V[(long long)i * kQrB + j] = 0.f;
     }
-    // columns bw..kQrB-1 of V are unused by this panel: zero them (the
-    // trailing update multiplies them by zero entries of T)
-    for (int e = tid; e < rows * (kQrB - bw); e += kQrPanelThreads)
-        V[(long long)(e / (kQrB - bw)) * kQrB + bw + e % (kQrB - bw)] = 0.f;
-    __syncthreads();
     for (int j = 0; j < bw; ++j) {
-        // |column j below the diagonal|^2, FP64 accumulation
-        double a = 0.0;
-        for (int i = j + tid; i < rows; i += kQrPanelThreads) {
-            const double x = P[i * bw + j];
-            a = fma(x, x, a);
-        }
-        a = block_sum(a, red);
-        if (tid == 0) {
-            const float x0 = P[j * bw + j];
-            const double nrm = sqrt(a);
-            float beta = 0.f, v0 = 1.f, alpha = x0;
-            if (rows - j > 1 && nrm > 0.0 && a > (double)x0 * x0) {
-                alpha = x0 >= 0.f ? (float)-nrm : (float)nrm;
-                v0 = x0 - alpha;
-                beta = -1.f / (alpha * v0);           // 2 / (v^T v)
-            }
-            sbeta[j] = beta;
-            sv0 = v0;
-            salpha = alpha;
-        }
-        __syncthreads();
-        const float beta = sbeta[j], v0 = sv0;
-        // reflector j: v = (v0, P[j+1:, j]); stored in column j of V
+        // 1. |P[j:, j]|^2, which also publishes P[j][j] after the barrier.  FP32
+        // (FP64 is scarce on this part, and every thread repeats the final sum):
+        // with alpha = -+sqrt(a) rounded once, beta = -1/(alpha v0) = 2/(v^T v)
+        // to FP32 rounding, so each reflector is orthogonal at FP32 level
+        float a = 0.f;
         for (int i = tid; i < rows; i += kQrPanelThreads)
-            V[(long long)i * kQrB + j] = i < j ? 0.f : (i == j ? v0 : P[i * bw + j]);
+            if (i >= j) { const float x = P[i * kPS + j]; a = fmaf(x, x, a); }
+        a = wsumf(a);
+        if (lane == 0) npart[warp] = a;
+        __syncthreads();
+        a = 0.f;
+        for (int w = 0; w < nw; ++w) a += npart[w];
+        const float x0 = P[j * kPS + j];
+        const float nrm = sqrtf(a);
+        float beta = 0.f, v0 = 1.f, alpha = x0;
+        if (rows - j > 1 && nrm > 0.f && a > x0 * x0) {
+            alpha = x0 >= 0.f ? -nrm : nrm;
+            v0 = x0 - alpha;
+            beta = -1.f / (alpha * v0);               // 2 / (v^T v)
+        }
+        if (tid == 0) sbeta[j] = beta;
+        // 2. w_q = v^T P[j:, q] for q > j (one warp per column, all rows: no
+        // row is written between the two barriers), then P[j:, q] -= beta v w_q
+        // on the own rows
         if (beta != 0.f) {
-            // w_q = v^T P[j:, q] for the columns q > j of the panel (one warp per column)
             for (int q = j + 1 + warp; q < bw; q += nw) {
-                float s = 0.f;
-                for (int i = j + lane; i < rows; i += 32) s = fmaf(i == j ? v0 : P[i * bw + j], P[i * bw + q], s);
-                s = wsumf(s);
-                if (lane == 0) wv[q] = s;
-            }
-            __syncthreads();
-            const int nq = bw - j - 1;
-            for (int e = tid; e < (rows - j) * nq; e += kQrPanelThreads) {
-                const int i = j + e / nq, q = j + 1 + e % nq;
-                const float vi = i == j ? v0 : P[i * bw + j];
-                P[i * bw + q] -= beta * vi * wv[q];
+                float sacc = 0.f;
+                for (int i = j + lane; i < rows; i += 32)
+                    sacc = fmaf(i == j ? v0 : P[i * kPS + j], P[i * kPS + q], sacc);
+                sacc = wsumf(sacc);
+                if (lane == 0) part[0][q] = sacc;
             }
         }
         __syncthreads();
-        // column j of R: alpha on the diagonal, zeros below
-        for (int i = j + tid; i < rows; i += kQrPanelThreads) P[i * bw + j] = (i == j) ? salpha : 0.f;
-        __syncthreads();
+        for (int i = tid; i < rows; i += kQrPanelThreads) {
+            if (i < j) continue;
+            const float vi = i == j ? v0 : P[i * kPS + j];
+            V[(long long)i * kQrB + j] = vi;
+            if (beta != 0.f) {
+                for (int q = j + 1; q < bw; ++q) P[i * kPS + q] -= beta * vi * part[0][q];
+            }
+            P[i * kPS + j] = (i == j) ? alpha : 0.f;
+        }
+        // the next column's norm reads only own rows; its barrier publishes
+        // the diagonal entry written above
     }
+    __syncthreads();
     // compact WY: T upper triangular, T[j][j] = beta_j,
     // T[0:j, j] = -beta_j T[0:j, 0:j] (V[:, 0:j]^T v_j)
     for (int pq = warp; pq < bw * bw; pq += nw) {
@@ -122,10 +126,8 @@ __global__ void __launch_bounds__(kQrPanelThreads) k_qr_panel(float *__restrict_
         for (int p = 0; p < kQrB; ++p)
             for (int q = 0; q < kQrB; ++q) T[p * kQrB + q] = Tl[p][q];
     }
-    for (int e = tid; e < rows * bw; e += kQrPanelThreads) {
-        const int i = e / bw, j = e % bw;
-        X[(long long)(k + i) * l + k + j] = P[e];
-    }
+    for (int i = tid; i < rows; i += kQrPanelThreads)
+        for (int j = 0; j < bw; ++j) X[(long long)(k + i) * l + k + j] = P[i * kPS + j];
 }
 
 // X[k:, p] <- X[k:, p] - V (T^T (V^T X[k:, p])) for the 32 columns p of this CTA
@@ -188,11 +190,11 @@ size_t qr32_work_bytes(int c)
 
 // In-place QR of X (c x l, row-major FP32): X <- R.  `work` holds
 // qr32_work_bytes(c) bytes.  Serves c up to the panel's shared-memory limit
-// (c * 16 floats <= 200 KB, c <= 3200); returns DMRG_EUNSUPPORTED beyond.
+// (c * 17 floats <= 200 KB, c <= 3011); returns DMRG_EUNSUPPORTED beyond.
 dmrg_status qr_precondition32(dmrg_ctx *ctx, float *X, int c, int l, void *work)
 {
     if (c <= 1 || l <= 0) return DMRG_OK;
-    const size_t smem_max = (size_t)c * kQrB * sizeof(float);
+    const size_t smem_max = (size_t)c * kPS * sizeof(float);
     if (smem_max > 200 * 1024) return DMRG_EUNSUPPORTED;
     static size_t attr = 0;
     if (attr < smem_max) {
@@ -203,9 +205,10 @@ dmrg_status qr_precondition32(dmrg_ctx *ctx, float *X, int c, int l, void *work)
     float *V = static_cast<float *>(work);
     float *T = reinterpret_cast<float *>(static_cast<char *>(work) + al(sizeof(float) * (size_t)c * kQrB));
     const int kmax = std::min(c - 1, l);          // reflectors 0..kmax-1
+    prof_mark(ctx, PROF_QR);
     for (int k = 0; k < kmax; k += kQrB) {
         const int bw = std::min(kQrB, kmax - k);
-        const size_t smem = (size_t)(c - k) * bw * sizeof(float);
+        const size_t smem = (size_t)(c - k) * kPS * sizeof(float);
         k_qr_panel<<<1, kQrPanelThreads, smem, ctx->stream>>>(X, c, l, k, bw, V, T); DMRG_COUNT_LAUNCH();
         const int ncols = l - (k + bw);
         if (ncols > 0) {
@@ -213,6 +216,8 @@ dmrg_status qr_precondition32(dmrg_ctx *ctx, float *X, int c, int l, void *work)
             DMRG_COUNT_LAUNCH();
         }
     }
+    prof_mark(ctx, PROF_QR);
+    prof_count(ctx, PROF_QR, 2.0 * (double)kmax * kmax * ((double)c + l - 2.0 * kmax / 3.0), 0.0);
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }

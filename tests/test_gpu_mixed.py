@@ -96,10 +96,9 @@ def test_mixed_svd_exact_spectrum(G, chi, gbj):
     8 sqrt(r) u |A|_F absolute, u = 2^-24: a vector near the FP32 rank floor
     carries the rounding of its rotations against all r others, each up to
     u times their norm, and its projection picks those components up (the
-    values there are overestimated); the isometry orthonormal to FP64
-    level after its
-    Newton-Schulz step, and the truncated reconstruction within the discarded
-    weight plus 1e-6 |A|."""
+    values there are overestimated); the isometry orthonormal within
+    (3/4) k tol^2 after its Newton-Schulz step, and the truncated
+    reconstruction within the discarded weight plus 1e-6 |A|."""
     c = G.Context(0)
     c.set_option("svd_prec", 1)
     c.set_option("gbj_min_r", gbj)          # 32: the Gram-block cooperative Jacobi
@@ -110,7 +109,9 @@ def test_mixed_svd_exact_spectrum(G, chi, gbj):
     U, s, Vt = (x.cpu().numpy() for x in (U, s, Vt))
     fro = np.sqrt(np.sum(s_ref ** 2))
     assert np.all(np.abs(s[:k] - s_ref[:k]) <= 1e-7 * s_ref[:k] + 8 * np.sqrt(len(s_ref)) * 2.0 ** -24 * fro)
-    assert np.abs(U[:, :k].T @ U[:, :k] - np.eye(k)).max() <= 1e-8
+    # the Jacobi leaves pairwise cosines up to tol = 1e-5; one Newton-Schulz
+    # step maps the error E of Q Q^T - I to about (3/4) E^2, |(E^2)_ij| <= k tol^2
+    assert np.abs(U[:, :k].T @ U[:, :k] - np.eye(k)).max() <= 0.75 * k * 1e-10
     Ak = (U[:, :k] * s[:k]) @ Vt[:k]
     tail = np.sqrt(np.sum(s_ref[k:] ** 2))
     assert np.linalg.norm(Ak - A) <= tail + 1e-6 * np.linalg.norm(A)
