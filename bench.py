@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--n-hi", type=int, default=128, help="--micro chains: longest chain")
     ap.add_argument("--chi-max", type=int, default=256, help="--micro chains: bond dimension cap")
     ap.add_argument("--seq", action="store_true", help="--micro chains: also time the chains one after another")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="also run the FP64 form on the same chain and sweeps (slow: FP64 is ~1.25 TFLOP/s here)")
     ap.add_argument("--opt", action="append", default=[],
                     help="context option name=value (repeatable), applied before the run")
     ap.add_argument("--no-qr", action="store_true", help="--micro svd / svd_batch: Jacobi without QR preconditioning")
@@ -389,6 +391,32 @@ def autotune(args, ctx, chi_max):
     return f"tuned {len(shapes)} GEMM and {len(sizes)} SVD buckets"
 
 
+def fp64_path(args, G, synth, wl, E_mixed):
+    """The same chain, initial MPS and sweep count in the FP64 form: its sweep
+    time and the energy difference per site to the mixed form's last sweep."""
+    import torch
+    N = wl["N"]
+    ctx = G.Context(0)
+    p = G.make_params(chi_max=wl["chi_max"], chi_init=wl["chi_init"], ctrl=G.CTRL_THRESHOLD, prec=G.PREC_FP64,
+                      eps_trunc=1e-10, max_sweeps=args.warmup + args.steps)
+    W = ctx.build_mpo(G.XXZ, N, 1.0, wl["Delta"])
+    m0 = torch.from_numpy(synth.initial_mps_entries(synth.workload_seed(2, 0), N, wl["chi_init"])).cuda()
+    st = G.State(ctx, W, m0, p, 1.0, wl["Delta"])
+    for _ in range(args.warmup):
+        st.sweep(1, visits=False)
+    recs = []
+    for _ in range(args.steps):
+        r, _ = st.sweep(1, visits=False)
+        recs += r
+    out = {"s_per_sweep": sum(r.seconds for r in recs) / len(recs), "energy_per_site": recs[-1].E / N,
+           "dE_per_site_vs_mixed": abs(recs[-1].E - E_mixed) / N, "mean_chi": sum(r.mean_chi for r in recs) / len(recs),
+           "sweeps": args.warmup + args.steps}
+    out["speedup_mixed_vs_fp64"] = None
+    st.close()
+    ctx.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -547,6 +575,9 @@ def run_ours(args):
         out["e2e"] = e2e
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(sweep_flops)
+    if args.compare_fp64:
+        out["fp64_path"] = fp64_path(args, G, synth, wl, recs[-1].E)
+        out["fp64_path"]["speedup_mixed_vs_fp64"] = out["fp64_path"]["s_per_sweep"] / per_sweep
     print(json.dumps(out))
     st.close()
     ctx.close()
