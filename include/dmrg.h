@@ -372,7 +372,8 @@ long long dmrg_launch_count(void);
  * profiling on, CUDA events on the context stream bracket every launch of
  * kind 0 (tensor-core GEMM), 1 (FP32 Jacobi sweeps), 2 (FP64 Jacobi sweeps),
  * 3 (FP64 GEMM), 4 (H_eff / environment mixing), 5 (FP32 SIMT GEMM of small
- * products), 6 (QR preconditioning).  dmrg_profile(ctx, on) resets the counters;
+ * products), 6 (QR preconditioning), 7 (Lanczos vector operations), 8 (the
+ * entropy/controller/truncation decision).  dmrg_profile(ctx, on) resets the counters;
  * dmrg_profile_read returns the summed device time (ms), the launches and
  * their algorithmic flops and bytes. */
 dmrg_status dmrg_profile(dmrg_ctx *ctx, int on);

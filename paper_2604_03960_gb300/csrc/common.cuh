@@ -85,7 +85,7 @@ namespace dmrg {
 // dmrg_profile; used for the roofline of the dominant kernel.
 enum ProfKind {
     PROF_TC_GEMM = 0, PROF_JACOBI32 = 1, PROF_JACOBI64 = 2, PROF_F64_GEMM = 3, PROF_MIX = 4, PROF_F32_GEMM = 5,
-    PROF_QR = 6, PROF_KINDS = 7
+    PROF_QR = 6, PROF_LZ_VEC = 7, PROF_DECIDE = 8, PROF_KINDS = 9
 };
 struct ProfSlot {
     std::vector<cudaEvent_t> ev;

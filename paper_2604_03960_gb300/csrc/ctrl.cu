@@ -262,9 +262,12 @@ dmrg_status launch_decide(dmrg_ctx *ctx, const double *s, int r, dmrg_ctrl_state
                           const void *lz_state, BondResult *res, dmrg_visit_record *visit, int direction,
                           double rank_floor, const int *jac_info)
 {
+    prof_mark(ctx, PROF_DECIDE);
     k_decide<<<1, DB, 0, ctx->stream>>>(s, r, st_bond, p, do_ctrl, chi_override, mlp, bond, N, sweep,
                                         static_cast<const LzState *>(lz_state), res, visit, direction, rank_floor,
                                         jac_info, ctx->mlp_eps_target, ctx->d_status); DMRG_COUNT_LAUNCH();
+    prof_mark(ctx, PROF_DECIDE);
+    prof_count(ctx, PROF_DECIDE, 0.0, 0.0);
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }

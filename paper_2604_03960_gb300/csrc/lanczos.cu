@@ -282,6 +282,7 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
     for (int j = 0; j < K; ++j) {
         double *vj = w.V + (size_t)n * j;
         DMRG_TRY(matvec(vj, w.w));
+        prof_mark(ctx, PROF_LZ_VEC);
         ReduceArgs a1{vj, n, 1, w.w, n, w.partials, w.counter};
         k_multidot<1><<<g, RB, 0, st>>>(a1, w.lz, j, nullptr); DMRG_COUNT_LAUNCH();
         k_three_term<<<g, RB, 0, st>>>(w.w, vj, j > 0 ? vj - n : vj, n, w.lz, j); DMRG_COUNT_LAUNCH();
@@ -293,6 +294,10 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
         ReduceArgs a3{nullptr, n, 0, w.w, n, w.partials, w.counter};
         k_multidot<2><<<g, RB, 0, st>>>(a3, w.lz, j, nullptr); DMRG_COUNT_LAUNCH();
         if (j + 1 < K) k_next_vec<<<g, RB, 0, st>>>(w.V + (size_t)n * (j + 1), w.w, n, w.lz, j); DMRG_COUNT_LAUNCH();
+        prof_mark(ctx, PROF_LZ_VEC);
+        // CGS2 and the three-term step: (j + 1) basis vectors read twice in each
+        // of two passes, the work vector about eight times, 8 B each
+        prof_count(ctx, PROF_LZ_VEC, 0.0, 8.0 * (double)n * (4.0 * (j + 1) + 8.0));
         DMRG_CUDA(cudaGetLastError());
     }
     k_tridiag_lowest<<<1, 32, 0, st>>>(w.lz, ctx->d_status); DMRG_COUNT_LAUNCH();
