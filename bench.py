@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--micro", choices=["gemm", "svd", "svd_batch", "chains"], default=None,
+    ap.add_argument("--micro", choices=["gemm", "svd", "svd_batch", "chains", "bond"], default=None,
                     help="one kernel-level invocation (for profiling): gemm M,N,K or svd chi")
     ap.add_argument("--shape", default="5120,4096,1024", help="--micro gemm: M,N,K")
     ap.add_argument("--chi", type=int, default=512, help="--micro svd: matrix 2chi x 2chi")
@@ -117,6 +117,8 @@ def run_micro(args):
         out = svd_batch(args, G, synth, prec)
     elif args.micro == "chains":
         out = chains(args, G, synth, prec)
+    elif args.micro == "bond":
+        out = bond_micro(args, G, synth, prec)
     else:
         chi = args.chi
         n = 2 * chi
@@ -185,6 +187,33 @@ def svd_batch(args, G, synth, prec):
             "qr_preconditioning": not args.no_qr, "count": int(args.count), "chi": [int(args.chi_lo), int(args.chi_hi)],
             "prec": args.prec, "ms_per_batch": ms, "gflops_nominal": nominal / (ms / 1e3) / 1e9,
             "mean_k": float(np.mean(k)), "input_gen_s": gen_s}
+
+
+def bond_micro(args, G, synth, prec):
+    """One full local update (20-step Lanczos, SVD, decision, split,
+    environment) at chi_l = chi_r = chi: the centre bond of an N = 20 XXZ
+    chain built at bond dimension chi, updated `reps` times after one warm-up."""
+    import torch
+    N, chi = 20, args.chi
+    ctx = G.Context(0)
+    apply_opts(ctx, args)
+    p = G.make_params(prec=prec, ctrl=G.CTRL_FIXED, chi_fixed=chi, chi_max=chi, chi_init=chi, eps_trunc=0.0)
+    W = ctx.build_mpo(G.XXZ, N, 1.0, 1.0)
+    m0 = torch.from_numpy(synth.initial_mps_entries(synth.workload_seed(3, chi), N, chi)).cuda()
+    torch.cuda.synchronize()
+    st = G.State(ctx, W, m0, p, 1.0, 1.0)
+    k = N // 2 - 1
+    st.bond_update(k, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.reps):
+        st.bond_update(k, 1)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) / args.reps * 1e3
+    c = st.chi()
+    st.close()
+    ctx.close()
+    return {"micro": "bond", "prec": args.prec, "chi": [c[k], c[k + 1], c[k + 2]], "ms_per_bond": ms}
 
 
 def chains(args, G, synth, prec):

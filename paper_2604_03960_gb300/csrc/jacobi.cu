@@ -406,12 +406,15 @@ __global__ void __launch_bounds__(256) k_jac32_sweeps(float *__restrict__ X, int
 // floats <= kSmemJacFloats): the rounds synchronise with __syncthreads only.
 constexpr int kSmemJacFloats = 50 * 1024;
 
-__global__ void __launch_bounds__(1024) k_jac32_smem(float *__restrict__ Xg, int r, int l, int max_sweeps, double tol,
-                                                     int *status, int *info, const double *F2, double small)
+__global__ void __launch_bounds__(1024) k_jac32_smem(float *__restrict__ Xg, int r_all, int l, int max_sweeps,
+                                                     double tol, int *status, int *info, const double *F2, double small,
+                                                     const int *r_eff)
 {
     extern __shared__ float xs[];
     __shared__ unsigned rot_count;
-    const long long n = (long long)r * l;
+    const long long n = (long long)r_all * l;
+    // rows beyond r_eff (negligible after QR preconditioning) are carried, not rotated
+    const int r = r_eff ? min(r_all, max(1, *r_eff)) : r_all;
     for (long long e = threadIdx.x; e < n; e += blockDim.x) xs[e] = Xg[e];
     const float floor2f = (float)(small * small * F2[0]), tolf = (float)tol;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -481,10 +484,13 @@ __global__ void __launch_bounds__(1024) k_jac32_smem(float *__restrict__ Xg, int
 constexpr int kBjacThreads = 512;
 
 template <int BW>
-__global__ void __launch_bounds__(kBjacThreads) k_bjac32(float *__restrict__ X, int r, int l, int max_sweeps,
+__global__ void __launch_bounds__(kBjacThreads) k_bjac32(float *__restrict__ X, int r_all, int l, int max_sweeps,
                                                          double tol, unsigned *sync, int *status, int *info,
-                                                         const double *F2, double small, int max_inner)
+                                                         const double *F2, double small, int max_inner,
+                                                         const int *r_eff)
 {
+    // rows beyond r_eff (negligible after QR preconditioning) are carried, not rotated
+    const int r = r_eff ? min(r_all, max(1, *r_eff)) : r_all;
     constexpr int NW = kBjacThreads / 32;
     constexpr int WPP = (NW / BW) > 0 ? (NW / BW) : 1;    // warps per pair
     constexpr int PPR = NW / WPP;                         // pairs in flight per inner round
@@ -622,7 +628,7 @@ __global__ void __launch_bounds__(kBjacThreads) k_bjac32(float *__restrict__ X, 
 
 template <int BW>
 dmrg_status launch_bjac32(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps, double tol, unsigned *sync,
-                          int *d_info, const double *F2, double small, int max_inner)
+                          int *d_info, const double *F2, double small, int max_inner, const int *r_eff)
 {
     const size_t smem = sizeof(float) * 2 * BW * (size_t)l;
     static size_t attr = 0;
@@ -639,7 +645,7 @@ dmrg_status launch_bjac32(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps,
     if (blocks < 1) blocks = 1;
     int *status = ctx->d_status;
     void *args[] = {&X, (void *)&r, (void *)&l, &max_sweeps, (void *)&tol, &sync, &status, &d_info, (void *)&F2,
-                    (void *)&small, &max_inner};
+                    (void *)&small, &max_inner, (void *)&r_eff};
     DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_bjac32<BW>, dim3(blocks), dim3(kBjacThreads), args, smem,
                                           ctx->stream)); DMRG_COUNT_LAUNCH();
     return DMRG_OK;
@@ -773,6 +779,33 @@ dmrg_status frob2_f32(dmrg_ctx *ctx, const float *A, long long n, double *F2)
     return DMRG_OK;
 }
 
+// Numerical row rank of R after the QR preconditioning: the smallest r_eff
+// such that the rows r_eff.. together have Frobenius norm <= 2^-23 |X|_F.
+// Dropping them moves no singular value by more than that (Weyl), the size of
+// the FP32 rounding X already carries; the Jacobi then rotates r_eff rows.
+__global__ void k_row_rank32(const float *__restrict__ X, int r, int l, double *__restrict__ rn, int *r_eff)
+{
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < r; i += nw) {
+        float a = 0.f;
+        for (int k = lane; k < l; k += 32) a = fmaf(X[(long long)i * l + k], X[(long long)i * l + k], a);
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) rn[i] = (double)a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int i = 0; i < r; ++i) tot += rn[i];
+        const double thr = tot * 1.4210854715202004e-14;   // (2^-23)^2 |X|_F^2
+        double suffix = 0.0;
+        int j = r;
+        while (j > 1 && suffix + rn[j - 1] <= thr) suffix += rn[--j];
+        *r_eff = j;
+    }
+    (void)sh;
+}
+
 // FP32 one-sided Jacobi on the columns (dir 0) or rows (dir 1) of theta; on
 // return s_sorted[0..min(m,n)) holds the vector norms in descending order and
 // perm the vector of each.  Scratch layout: X32 | nrm | perm | sync.
@@ -820,9 +853,15 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
     }
     // QR preconditioning: rotate the rows of R (X = Q R) instead of the rows
     // of X -- same singular values and directions, a third of the sweeps
+    const int *reff = nullptr;
     if (ctx->jacobi_qr && r >= 32) {
         dmrg_status e = qr_precondition32(ctx, X, r, l, qrw);
         if (e != DMRG_OK && e != DMRG_EUNSUPPORTED) return e;
+        if (e == DMRG_OK && ctx->jacobi_rank_drop) {
+            // row norms go to the norm slot (rewritten after the sweeps); r_eff to sync[6]
+            k_row_rank32<<<1, 512, 0, st>>>(X, r, l, nrm, reinterpret_cast<int *>(sync + 6)); DMRG_COUNT_LAUNCH();
+            reff = reinterpret_cast<const int *>(sync + 6);
+        }
     }
     // rotate while the cosine exceeds 1e-5: FP32 dot products over a few
     // thousand terms are good to ~1e-6, and the FP64 Newton-Schulz step that
@@ -856,7 +895,7 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
             attr = true;
         }
         int thr = r >= 64 ? 1024 : (r >= 16 ? 256 : 64);
-        k_jac32_smem<<<1, thr, smem, st>>>(X, r, l, max_sweeps, tol, status, d_info, F2, small);
+        k_jac32_smem<<<1, thr, smem, st>>>(X, r, l, max_sweeps, tol, status, d_info, F2, small, reff);
         DMRG_COUNT_LAUNCH();
     } else {
         // blocked form: block width so that about one block pair per SM is
@@ -873,11 +912,11 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
         (void)blocks;
         dmrg_status e;
         switch (bw) {
-        case 16: e = launch_bjac32<16>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner); break;
-        case 8: e = launch_bjac32<8>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner); break;
-        case 4: e = launch_bjac32<4>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner); break;
-        case 2: e = launch_bjac32<2>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner); break;
-        default: e = launch_bjac32<1>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner); break;
+        case 16: e = launch_bjac32<16>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner, reff); break;
+        case 8: e = launch_bjac32<8>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner, reff); break;
+        case 4: e = launch_bjac32<4>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner, reff); break;
+        case 2: e = launch_bjac32<2>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner, reff); break;
+        default: e = launch_bjac32<1>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner, reff); break;
         }
         if (e != DMRG_OK) return e;
     }
