@@ -53,12 +53,27 @@ __global__ void __launch_bounds__(RB) k_multidot(ReduceArgs a, LzState *lz, int 
             if (q < nq) acc[q] = fma(a.V[(long long)q * a.ldv + i], wi, acc[q]);
         acc[MAXQ] = fma(wi, wi, acc[MAXQ]);
     }
-    for (int q = 0; q <= MAXQ; ++q) {
-        if (q < nq || q == MAXQ) {
-            double s = block_sum(acc[q], sh);
-            if (threadIdx.x == 0) a.partials[(long long)blockIdx.x * (MAXQ + 1) + q] = s;
+    // block reduction of all nq + 1 sums at once: the partial sums go to
+    // shared memory column by column and one warp adds up each column (FP64
+    // adds are scarce on this part: 255 of them per column is the minimum,
+    // where a shuffle tree per column would spend 5 x 32 per warp)
+    extern __shared__ double red[];            // (MAXQ + 1) x RB
+#pragma unroll
+    for (int q = 0; q <= MAXQ; ++q)
+        if (q < nq || q == MAXQ) red[q * RB + threadIdx.x] = acc[q];
+    __syncthreads();
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int q = warp; q <= MAXQ; q += RB / 32) {
+            if (!(q < nq || q == MAXQ)) continue;
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < RB / 32; ++k) s += red[q * RB + lane + 32 * k];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) a.partials[(long long)blockIdx.x * (MAXQ + 1) + q] = s;
         }
     }
+    (void)sh;
     __threadfence();
     if (threadIdx.x == 0) {
         unsigned done = atomicAdd(a.counter, 1u);
@@ -231,6 +246,16 @@ __global__ void k_tridiag_lowest(LzState *lz, int *status)
     if (!isfinite(lam) || lz->nan) atomicOr(status, ST_NAN);
 }
 
+// multi-dot grid: one block per SM, so each thread accumulates several
+// elements before the (FP64-add bound) block reduction
+int grid_dot(long long n, int num_sms)
+{
+    long long b = (n + RB - 1) / RB;
+    if (b > num_sms) b = num_sms;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
 int grid_for(long long n, int num_sms)
 {
     long long b = (n + RB - 1) / RB;
@@ -272,11 +297,20 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
     if (K > LZ_MAXK) K = LZ_MAXK;
     if ((long long)K > n) K = (int)n;
     cudaStream_t st = ctx->stream;
-    const int g = grid_for(n, ctx->num_sms);
+    const int g = grid_for(n, ctx->num_sms), gd = grid_dot(n, ctx->num_sms);
+    const size_t dsm = sizeof(double) * (MAXQ + 1) * RB;
+    static bool dsm_attr = false;
+    if (!dsm_attr) {
+        DMRG_CUDA(cudaFuncSetAttribute(k_multidot<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+        DMRG_CUDA(cudaFuncSetAttribute(k_multidot<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+        DMRG_CUDA(cudaFuncSetAttribute(k_multidot<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+        DMRG_CUDA(cudaFuncSetAttribute(k_multidot<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+        dsm_attr = true;
+    }
     DMRG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned), st));
     k_lz_init<<<1, 1, 0, st>>>(w.lz, K); DMRG_COUNT_LAUNCH();
     ReduceArgs ra{nullptr, n, 0, theta, n, w.partials, w.counter};
-    k_multidot<3><<<g, RB, 0, st>>>(ra, w.lz, 0, nullptr); DMRG_COUNT_LAUNCH();          // |theta|
+    k_multidot<3><<<gd, RB, dsm, st>>>(ra, w.lz, 0, nullptr); DMRG_COUNT_LAUNCH();          // |theta|
     k_scale_by<<<g, RB, 0, st>>>(w.V, theta, n, w.lz); DMRG_COUNT_LAUNCH();                // v0
     DMRG_CUDA(cudaGetLastError());
     for (int j = 0; j < K; ++j) {
@@ -284,15 +318,15 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
         DMRG_TRY(matvec(vj, w.w));
         prof_mark(ctx, PROF_LZ_VEC);
         ReduceArgs a1{vj, n, 1, w.w, n, w.partials, w.counter};
-        k_multidot<1><<<g, RB, 0, st>>>(a1, w.lz, j, nullptr); DMRG_COUNT_LAUNCH();
+        k_multidot<1><<<gd, RB, dsm, st>>>(a1, w.lz, j, nullptr); DMRG_COUNT_LAUNCH();
         k_three_term<<<g, RB, 0, st>>>(w.w, vj, j > 0 ? vj - n : vj, n, w.lz, j); DMRG_COUNT_LAUNCH();
         for (int pass = 0; pass < 2; ++pass) {
             ReduceArgs a2{w.V, n, j + 1, w.w, n, w.partials, w.counter};
-            k_multidot<0><<<g, RB, 0, st>>>(a2, w.lz, j, w.c); DMRG_COUNT_LAUNCH();
+            k_multidot<0><<<gd, RB, dsm, st>>>(a2, w.lz, j, w.c); DMRG_COUNT_LAUNCH();
             k_multiaxpy<<<g, RB, 0, st>>>(w.w, w.V, n, j + 1, w.c, n, w.lz, 1, 0); DMRG_COUNT_LAUNCH();
         }
         ReduceArgs a3{nullptr, n, 0, w.w, n, w.partials, w.counter};
-        k_multidot<2><<<g, RB, 0, st>>>(a3, w.lz, j, nullptr); DMRG_COUNT_LAUNCH();
+        k_multidot<2><<<gd, RB, dsm, st>>>(a3, w.lz, j, nullptr); DMRG_COUNT_LAUNCH();
         if (j + 1 < K) k_next_vec<<<g, RB, 0, st>>>(w.V + (size_t)n * (j + 1), w.w, n, w.lz, j); DMRG_COUNT_LAUNCH();
         prof_mark(ctx, PROF_LZ_VEC);
         // CGS2 and the three-term step: (j + 1) basis vectors read twice in each
@@ -307,7 +341,7 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
         DMRG_CUDA(cudaMemcpyAsync(w.c, w.lz->y, sizeof(double) * K, cudaMemcpyDeviceToDevice, st));
         k_multiaxpy<<<g, RB, 0, st>>>(theta, w.V, n, -1, w.c, n, w.lz, 0, 1); DMRG_COUNT_LAUNCH();
         ReduceArgs a4{nullptr, n, 0, theta, n, w.partials, w.counter};
-        k_multidot<3><<<g, RB, 0, st>>>(a4, w.lz, 0, nullptr); DMRG_COUNT_LAUNCH();
+        k_multidot<3><<<gd, RB, dsm, st>>>(a4, w.lz, 0, nullptr); DMRG_COUNT_LAUNCH();
         k_scale_by<<<g, RB, 0, st>>>(theta, theta, n, w.lz); DMRG_COUNT_LAUNCH();
     }
     DMRG_CUDA(cudaGetLastError());
