@@ -3,8 +3,10 @@
 // The paper leaves the local eigensolver unnamed; this is the K-step Lanczos
 // recurrence with full reorthogonalisation by two classical Gram-Schmidt
 // passes, all in FP64 and all on the device:
-//   v0 = theta/|theta|;  w = H v_j;  alpha_j = v_j.w;  w -= alpha_j v_j + beta_j v_{j-1};
-//   w -= V (V^T w) (twice);  beta_{j+1} = |w|;  v_{j+1} = w / beta_{j+1}
+//   v0 = theta/|theta|;  w = H v_j;  w -= V (V^T w) (twice, against v_0..v_j);
+//   alpha_j = v_j . H v_j (the first pass's coefficient on v_j; that pass also
+//   removes alpha_j v_j + beta_j v_{j-1}, the three-term step);
+//   beta_{j+1} = |w|;  v_{j+1} = w / beta_{j+1}
 // stopping early (device flag, no host round trip) when beta < 1e-14 max|alpha|.
 // The K x K tridiagonal T is solved on the device by Sturm-sequence
 // bisection for its lowest eigenvalue and inverse iteration for the vector;
@@ -87,8 +89,12 @@ __global__ void __launch_bounds__(RB) k_multidot(ReduceArgs a, LzState *lz, int 
         if (!(q < nq || q == MAXQ)) continue;
         double s = 0.0;
         for (int b = 0; b < (int)gridDim.x; ++b) s += *(volatile double *)&a.partials[(long long)b * (MAXQ + 1) + q];
-        if (MODE == 0) {
+        if (MODE == 0 || MODE == 4) {
             out[q] = s;
+            if (MODE == 4 && q == j) {  // first Gram-Schmidt pass on w = H v_j: alpha_j = v_j . w
+                lz->alpha[j] = s;
+                if (fabs(s) > lz->amax) lz->amax = fabs(s);
+            }
         } else if (MODE == 1) {        // alpha_j = v_j . w
             if (q == 0) {
                 lz->alpha[j] = s;
@@ -109,21 +115,6 @@ __global__ void __launch_bounds__(RB) k_multidot(ReduceArgs a, LzState *lz, int 
     if (threadIdx.x == 0) *a.counter = 0u;
 }
 
-// w -= alpha_j v_j + beta_j v_{j-1}
-__global__ void k_three_term(double *__restrict__ w, const double *__restrict__ vj, const double *__restrict__ vjm1,
-                             long long n, const LzState *lz, int j)
-{
-    if (!lz->active) return;
-    const double a = lz->alpha[j];
-    const double b = (j > 0) ? lz->beta[j] : 0.0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        double v = w[i] - a * vj[i];
-        if (j > 0) v -= b * vjm1[i];
-        w[i] = v;
-    }
-}
-
 // w -= sum_q c[q] V[q]   (or w = sum_q c[q] V[q] when overwrite)
 __global__ void k_multiaxpy(double *__restrict__ w, const double *__restrict__ V, long long ldv, int nq,
                             const double *__restrict__ c, long long n, const LzState *lz, int check_active,
@@ -140,6 +131,52 @@ __global__ void k_multiaxpy(double *__restrict__ w, const double *__restrict__ V
         for (int q = 0; q < nq; ++q) acc = fma(cs[q], V[(long long)q * ldv + i], acc);
         w[i] = overwrite ? acc : w[i] - acc;
     }
+}
+
+// Second Gram-Schmidt pass fused with the norm: w -= sum_q c[q] V[q], then
+// beta_{j+1} = |w| (per-block partial sums of squares, summed in block order
+// by the last block, which also decides whether the recurrence continues).
+__global__ void __launch_bounds__(RB) k_multiaxpy_norm(double *__restrict__ w, const double *__restrict__ V,
+                                                       long long ldv, int nq, const double *__restrict__ c,
+                                                       long long n, LzState *lz, int j, double *partials,
+                                                       unsigned *counter)
+{
+    if (!lz->active) return;
+    __shared__ double cs[MAXQ];
+    __shared__ double red[RB / 32];
+    __shared__ bool last;
+    if (threadIdx.x < nq) cs[threadIdx.x] = c[threadIdx.x];
+    __syncthreads();
+    double ss = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        double acc = 0.0;
+        for (int q = 0; q < nq; ++q) acc = fma(cs[q], V[(long long)q * ldv + i], acc);
+        const double v = w[i] - acc;
+        w[i] = v;
+        ss = fma(v, v, ss);
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < RB / 32; ++k) t += red[k];
+        partials[blockIdx.x] = t;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double t = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) t += *(volatile double *)&partials[b];
+    const double bta = sqrt(t);
+    lz->beta[j + 1] = bta;
+    lz->m = j + 1;
+    if (j + 1 >= lz->K || !(bta > 1e-14 * lz->amax) || !isfinite(bta)) lz->active = 0;
+    if (!isfinite(bta)) lz->nan = 1;
+    *counter = 0u;
 }
 
 // dst = src * lz->scale  (start vector / Ritz vector normalisation)
@@ -302,9 +339,8 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
     static bool dsm_attr = false;
     if (!dsm_attr) {
         DMRG_CUDA(cudaFuncSetAttribute(k_multidot<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
-        DMRG_CUDA(cudaFuncSetAttribute(k_multidot<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
-        DMRG_CUDA(cudaFuncSetAttribute(k_multidot<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
         DMRG_CUDA(cudaFuncSetAttribute(k_multidot<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+        DMRG_CUDA(cudaFuncSetAttribute(k_multidot<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
         dsm_attr = true;
     }
     DMRG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned), st));
@@ -317,21 +353,22 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
         double *vj = w.V + (size_t)n * j;
         DMRG_TRY(matvec(vj, w.w));
         prof_mark(ctx, PROF_LZ_VEC);
-        ReduceArgs a1{vj, n, 1, w.w, n, w.partials, w.counter};
-        k_multidot<1><<<gd, RB, dsm, st>>>(a1, w.lz, j, nullptr); DMRG_COUNT_LAUNCH();
-        k_three_term<<<g, RB, 0, st>>>(w.w, vj, j > 0 ? vj - n : vj, n, w.lz, j); DMRG_COUNT_LAUNCH();
-        for (int pass = 0; pass < 2; ++pass) {
-            ReduceArgs a2{w.V, n, j + 1, w.w, n, w.partials, w.counter};
-            k_multidot<0><<<gd, RB, dsm, st>>>(a2, w.lz, j, w.c); DMRG_COUNT_LAUNCH();
-            k_multiaxpy<<<g, RB, 0, st>>>(w.w, w.V, n, j + 1, w.c, n, w.lz, 1, 0); DMRG_COUNT_LAUNCH();
-        }
-        ReduceArgs a3{nullptr, n, 0, w.w, n, w.partials, w.counter};
-        k_multidot<2><<<gd, RB, dsm, st>>>(a3, w.lz, j, nullptr); DMRG_COUNT_LAUNCH();
+        // Full reorthogonalisation by two classical Gram-Schmidt passes on
+        // w = H v_j against v_0..v_j.  The first pass subtracts alpha_j v_j and
+        // beta_j v_{j-1} with the rest (the three-term step is contained in
+        // it), and its coefficient on v_j is alpha_j = v_j . H v_j; the second
+        // pass also yields beta_{j+1} = |w|.
+        ReduceArgs a2{w.V, n, j + 1, w.w, n, w.partials, w.counter};
+        k_multidot<4><<<gd, RB, dsm, st>>>(a2, w.lz, j, w.c); DMRG_COUNT_LAUNCH();
+        k_multiaxpy<<<g, RB, 0, st>>>(w.w, w.V, n, j + 1, w.c, n, w.lz, 1, 0); DMRG_COUNT_LAUNCH();
+        k_multidot<0><<<gd, RB, dsm, st>>>(a2, w.lz, j, w.c); DMRG_COUNT_LAUNCH();
+        k_multiaxpy_norm<<<gd, RB, 0, st>>>(w.w, w.V, n, j + 1, w.c, n, w.lz, j, w.partials, w.counter);
+        DMRG_COUNT_LAUNCH();
         if (j + 1 < K) k_next_vec<<<g, RB, 0, st>>>(w.V + (size_t)n * (j + 1), w.w, n, w.lz, j); DMRG_COUNT_LAUNCH();
         prof_mark(ctx, PROF_LZ_VEC);
-        // CGS2 and the three-term step: (j + 1) basis vectors read twice in each
-        // of two passes, the work vector about eight times, 8 B each
-        prof_count(ctx, PROF_LZ_VEC, 0.0, 8.0 * (double)n * (4.0 * (j + 1) + 8.0));
+        // two Gram-Schmidt passes: (j + 1) basis vectors read twice in each,
+        // the work vector about six times, 8 B each
+        prof_count(ctx, PROF_LZ_VEC, 0.0, 8.0 * (double)n * (4.0 * (j + 1) + 6.0));
         DMRG_CUDA(cudaGetLastError());
     }
     k_tridiag_lowest<<<1, 32, 0, st>>>(w.lz, ctx->d_status); DMRG_COUNT_LAUNCH();
