@@ -560,7 +560,7 @@ def run_ours(args):
     # dominant kernel: the one with the largest live device time
     names = {0: "tcgen05 3xTF32 GEMM", 1: "FP32 Jacobi sweeps", 2: "FP64 Jacobi sweeps", 3: "FP64 GEMM",
              4: "H_eff/environment mix", 5: "FP32 SIMT GEMM (small products)", 6: "QR preconditioning",
-             7: "Lanczos vector ops (CGS2, three-term)", 8: "entropy/controller/truncation decision"}
+             7: "Lanczos vector ops (two Gram-Schmidt passes)", 8: "entropy/controller/truncation decision"}
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     total_ms = ms

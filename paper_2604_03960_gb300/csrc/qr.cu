@@ -36,11 +36,11 @@ __device__ __forceinline__ float wsumf(float v)
 // writes them, so a column step needs only two block reductions -- the norm
 // of the column (which also publishes its diagonal entry) and the products of
 // the reflector with the columns to its right -- and every thread derives the
-// reflector from the reduced norm itself.  Panel rows have stride kQrB + 1.
-constexpr int kPS = kQrB + 1;
+// reflector from the reduced norm itself.  Panel rows have stride ps = the
+// panel width + 1 (odd: no bank conflicts between consecutive rows).
 
 __global__ void __launch_bounds__(kQrPanelThreads) k_qr_panel(float *__restrict__ X, int c, int l, int k, int bw,
-                                                              float *__restrict__ V, float *__restrict__ T)
+                                                              int kPS, float *__restrict__ V, float *__restrict__ T)
 {
     extern __shared__ float P[];                   // rows x kPS
     constexpr int nw = kQrPanelThreads / 32;
@@ -189,11 +189,17 @@ size_t qr32_work_bytes(int c)
 }
 
 // In-place QR of X (c x l, row-major FP32): X <- R.  `work` holds
-// qr32_work_bytes(c) bytes.  Serves c up to the panel's shared-memory limit
-// (c * 17 floats <= 200 KB, c <= 3011); returns DMRG_EUNSUPPORTED beyond.
+// qr32_work_bytes(c) bytes.  The panel narrows from 16 to 8 or 4 columns for
+// tall matrices (c * (width + 1) floats <= 200 KB, so c up to ~17,000);
+// returns DMRG_EUNSUPPORTED beyond.
 dmrg_status qr_precondition32(dmrg_ctx *ctx, float *X, int c, int l, void *work)
 {
     if (c <= 1 || l <= 0) return DMRG_OK;
+    // panel width: 16 columns, narrower for tall panels so that a panel of c
+    // rows (stride width + 1) fits the 200 KB of shared memory
+    int bmax = kQrB;
+    while (bmax > 2 && (size_t)c * (bmax + 1) * sizeof(float) > 200 * 1024) bmax /= 2;
+    const int kPS = bmax + 1;
     const size_t smem_max = (size_t)c * kPS * sizeof(float);
     if (smem_max > 200 * 1024) return DMRG_EUNSUPPORTED;
     static size_t attr = 0;
@@ -206,10 +212,10 @@ dmrg_status qr_precondition32(dmrg_ctx *ctx, float *X, int c, int l, void *work)
     float *T = reinterpret_cast<float *>(static_cast<char *>(work) + al(sizeof(float) * (size_t)c * kQrB));
     const int kmax = std::min(c - 1, l);          // reflectors 0..kmax-1
     prof_mark(ctx, PROF_QR);
-    for (int k = 0; k < kmax; k += kQrB) {
-        const int bw = std::min(kQrB, kmax - k);
+    for (int k = 0; k < kmax; k += bmax) {
+        const int bw = std::min(bmax, kmax - k);
         const size_t smem = (size_t)(c - k) * kPS * sizeof(float);
-        k_qr_panel<<<1, kQrPanelThreads, smem, ctx->stream>>>(X, c, l, k, bw, V, T); DMRG_COUNT_LAUNCH();
+        k_qr_panel<<<1, kQrPanelThreads, smem, ctx->stream>>>(X, c, l, k, bw, kPS, V, T); DMRG_COUNT_LAUNCH();
         const int ncols = l - (k + bw);
         if (ncols > 0) {
             k_qr_trail<<<(ncols + 31) / 32, kQrTrailThreads, 0, ctx->stream>>>(X, c, l, k, bw, V, T);
