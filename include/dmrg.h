@@ -67,7 +67,11 @@ typedef enum {
     DMRG_CTRL_DIRECT = 1,    /* chi = clamp(ceil(gamma exp(Sbar))) (Algorithm 1)         */
     DMRG_CTRL_FIXED = 2,     /* chi = chi_fixed                                          */
     DMRG_CTRL_THRESHOLD = 3, /* chi = chi_max; the eps_trunc threshold decides (Sec. 10) */
-    DMRG_CTRL_MLP = 4        /* learned scheduler with the PID as fallback               */
+    DMRG_CTRL_MLP = 4,       /* learned scheduler with the PID as fallback               */
+    DMRG_CTRL_GLOBAL = 5     /* global adaptive chi (Section 6): one PID on the mean of the
+                                per-bond filtered entropies, stepped once per sweep (with
+                                alpha = 1: the inputs are already filtered); every bond is
+                                truncated to the same chi, which starts at chi_min        */
 } dmrg_ctrl_mode;
 
 /* Parameters of the local update and of the controller. */

@@ -24,7 +24,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-CTRL_PID, CTRL_DIRECT, CTRL_FIXED, CTRL_THRESHOLD, CTRL_MLP = range(5)
+CTRL_PID, CTRL_DIRECT, CTRL_FIXED, CTRL_THRESHOLD, CTRL_MLP, CTRL_GLOBAL = range(6)
 MODEL_XXZ, MODEL_J1J2, MODEL_TFIM = 0, 1, 2
 
 

@@ -62,7 +62,7 @@ typedef struct {
     int second_order;   /* 1: add the curvature term of the second-order predictor */
 } ref_params;
 
-enum { CTRL_PID = 0, CTRL_DIRECT = 1, CTRL_FIXED = 2, CTRL_THRESHOLD = 3, CTRL_MLP = 4 };
+enum { CTRL_PID = 0, CTRL_DIRECT = 1, CTRL_FIXED = 2, CTRL_THRESHOLD = 3, CTRL_MLP = 4, CTRL_GLOBAL = 5 };
 
 /* Per-bond controller state (Algorithm 2 requirements plus the predictor's
  * previous EMA value and the MLP's window of EMA values).                   */
@@ -1093,6 +1093,11 @@ int ref_dmrg_run(int N, int d, int D, const double *W, const double *mps_init,
         for (int b = 0; b < N - 1; ++b) own[b].chi = p->chi_min;
         cs = own;
     }
+    /* global adaptive chi (Section 6): one controller on the mean of the
+     * per-bond filtered entropies, stepped once per sweep, chi uniform */
+    ref_ctrl_state gcs;
+    memset(&gcs, 0, sizeof gcs);
+    gcs.chi = p->chi_min;
     int visits_per_sweep = 2 * N - 3;
     double E_prev = 0.0;
     int sweeps_done = 0;
@@ -1122,7 +1127,11 @@ int ref_dmrg_run(int N, int d, int D, const double *W, const double *mps_init,
                 double S = ref_entropy(r, s, eps);
                 int chi_c;
                 int do_ctrl = (p->pid_steps_per_sweep >= 2) || (half == 0);
-                if (do_ctrl) {
+                if (p->ctrl == CTRL_GLOBAL) {
+                    int unused;
+                    if (do_ctrl) ref_ctrl_step(&cs[k], S, p, &unused);   /* the bond's filter only */
+                    chi_c = gcs.chi;
+                } else if (do_ctrl) {
                     ref_ctrl_step(&cs[k], S, p, &chi_c);
                     if (p->ctrl == CTRL_MLP && mlp_params) {
                         double x[MLP_IN];
@@ -1168,6 +1177,17 @@ int ref_dmrg_run(int N, int d, int D, const double *W, const double *mps_init,
                 E_last = E;
                 free(theta); free(U); free(s); free(Vt); free(eps);
             }
+        }
+        if (p->ctrl == CTRL_GLOBAL) {
+            /* S-bar(t) = (N-1)^-1 sum_i S-bar_i(t); the per-bond values are
+             * already filtered, so the global controller takes it with alpha = 1 */
+            double sum = 0.0;
+            for (int b = 0; b < N - 1; ++b) sum += cs[b].Sbar;
+            double mean = sum / (double)(N - 1);
+            ref_params gp = *p;
+            gp.alpha_ema = 1.0;
+            int chi_g;
+            ref_ctrl_step(&gcs, mean, &gp, &chi_g);
         }
         E_sweep[t] = E_last;
         sweeps_done = t + 1;

@@ -17,12 +17,12 @@ from .build import LIB as _LIB_PATH, build as _build
 
 __all__ = [
     "lib", "Params", "ModelParams", "CtrlState", "SweepRecord", "VisitRecord", "Context", "State",
-    "PREC_FP64", "PREC_3XTF32", "CTRL_PID", "CTRL_DIRECT", "CTRL_FIXED", "CTRL_THRESHOLD", "CTRL_MLP",
+    "PREC_FP64", "PREC_3XTF32", "CTRL_PID", "CTRL_DIRECT", "CTRL_FIXED", "CTRL_THRESHOLD", "CTRL_MLP", "CTRL_GLOBAL",
     "XXZ", "J1J2", "TFIM", "DMRGError", "make_params", "MLP_NPARAM",
 ]
 
 PREC_FP64, PREC_3XTF32, PREC_BF16X3 = 0, 1, 2
-CTRL_PID, CTRL_DIRECT, CTRL_FIXED, CTRL_THRESHOLD, CTRL_MLP = range(5)
+CTRL_PID, CTRL_DIRECT, CTRL_FIXED, CTRL_THRESHOLD, CTRL_MLP, CTRL_GLOBAL = range(6)
 XXZ, J1J2, TFIM = 0, 1, 2
 MLP_NPARAM = 4929
 

@@ -109,7 +109,12 @@ __global__ void __launch_bounds__(DB) k_decide(const double *__restrict__ s, int
     // 4. controller
     if (t == 0) {
         int c;
-        if (chi_override > 0) c = chi_override;
+        if (p.ctrl == DMRG_CTRL_GLOBAL && st) {
+            // global adaptive chi: the bond's filter advances, the uniform chi
+            // of this sweep (chi_override) truncates
+            if (do_ctrl) (void)ctrl_step_dev(st, S, p);
+            c = chi_override > 0 ? chi_override : st->chi;
+        } else if (chi_override > 0) c = chi_override;
         else if (do_ctrl) c = ctrl_step_dev(st, S, p);
         else c = st->chi;
         sh_chi = c;
@@ -256,6 +261,27 @@ __global__ void k_entropy(int n, const double *__restrict__ s, double *S_out, do
 }
 
 }  // namespace
+
+// Global adaptive chi: S-bar(t) = (N-1)^-1 sum_i S-bar_i(t) over the bonds'
+// filtered entropies (summed in bond order), then one controller step with
+// alpha = 1 (the inputs are already filtered).  Same arithmetic as the oracle.
+__global__ void k_global_step(const dmrg_ctrl_state *__restrict__ bonds, int n_bonds, dmrg_ctrl_state *g,
+                              dmrg_params p)
+{
+    double sum = 0.0;
+    for (int b = 0; b < n_bonds; ++b) sum = __dadd_rn(sum, bonds[b].Sbar);
+    const double mean = __ddiv_rn(sum, (double)n_bonds);
+    p.alpha_ema = 1.0;
+    (void)ctrl_step_dev(g, mean, p);
+}
+
+dmrg_status launch_global_step(dmrg_ctx *ctx, const dmrg_ctrl_state *bonds, int n_bonds, dmrg_ctrl_state *g,
+                               const dmrg_params &p)
+{
+    k_global_step<<<1, 1, 0, ctx->stream>>>(bonds, n_bonds, g, p); DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
 
 dmrg_status launch_decide(dmrg_ctx *ctx, const double *s, int r, dmrg_ctrl_state *st_bond, const dmrg_params &p,
                           int do_ctrl, int chi_override, const float *mlp, int bond, int N, int sweep,

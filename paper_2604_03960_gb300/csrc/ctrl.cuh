@@ -83,6 +83,8 @@ __device__ __forceinline__ int ctrl_step_dev(dmrg_ctrl_state *st, double S, cons
 // Launchers (ctrl.cu)
 // rank_floor: singular values <= rank_floor * s_0 count as zero (r eps for the
 // FP64 SVD; the FP32 Jacobi of the mixed form resolves about 2^-22).
+dmrg_status launch_global_step(dmrg_ctx *ctx, const dmrg_ctrl_state *bonds, int n_bonds, dmrg_ctrl_state *g,
+                               const dmrg_params &p);
 dmrg_status launch_decide(dmrg_ctx *ctx, const double *s, int r, dmrg_ctrl_state *st_bond, const dmrg_params &p,
                           int do_ctrl, int chi_override, const float *mlp, int bond, int N, int sweep,
                           const void *lz_state, BondResult *res, dmrg_visit_record *visit, int direction,

@@ -508,6 +508,8 @@ struct dmrg_state {
     long long nmax = 0;
     int K = 20;
     cudaEvent_t ev_res = nullptr;    // recorded after the bond result is copied to h_res
+    dmrg_ctrl_state *gctrl = nullptr;  // global adaptive chi: the one controller (device)
+    int global_chi = 0;                // ... and its current chi (host copy, set at sweep ends)
     // a bond step between its two phases (bond_step_a / bond_step_b)
     struct Pending {
         int k = 0, go_right = 0, direction = 1, m = 0, n = 0, r = 0, cl = 0, cm = 0, cr = 0, K = 0;
@@ -725,21 +727,22 @@ static dmrg_status bond_step_a(dmrg_state *st, int k, int go_right, int do_ctrl,
         DMRG_CUDA(cudaGetLastError());
     }
     const float *mlp = st->has_mlp ? st->mlp : nullptr;
+    const int chi_global = st->p.ctrl == DMRG_CTRL_GLOBAL ? st->global_chi : 0;
     if (prec == DMRG_PREC_FP64) {
         // SVD (Eq. 20) in FP64, then entropy, controller and truncation
         DMRG_TRY(svd_jacobi(ctx, st->theta, m, n, st->U, st->s, st->Vt, st->svdw, st->p.jacobi_max_sweeps,
                             st->d_info));
-        DMRG_TRY(launch_decide(ctx, st->s, r, st->ctrl + k, st->p, do_ctrl, 0, mlp, k, st->N, st->sweep_index,
-                               st->lw.lz, st->d_res, visit, direction, (double)r * 2.220446049250313e-16,
-                               st->d_info));
+        DMRG_TRY(launch_decide(ctx, st->s, r, st->ctrl + k, st->p, do_ctrl, chi_global, mlp, k, st->N,
+                               st->sweep_index, st->lw.lz, st->d_res, visit, direction,
+                               (double)r * 2.220446049250313e-16, st->d_info));
     } else {
         // Mixed form: FP32 Jacobi on the vectors that become the isometry
         // (columns of theta if the centre moves right, rows if it moves left)
         const int dir = go_right ? 0 : 1;
         DMRG_TRY(svd_jacobi32(ctx, st->theta, m, n, dir, st->svdw, st->p.jacobi_max_sweeps, st->d_info, st->s,
                               &P.X32, &P.nrm, &P.perm));
-        DMRG_TRY(launch_decide(ctx, st->s, r, st->ctrl + k, st->p, do_ctrl, 0, mlp, k, st->N, st->sweep_index,
-                               st->lw.lz, st->d_res, visit, direction, kMixedRankFloor, st->d_info));
+        DMRG_TRY(launch_decide(ctx, st->s, r, st->ctrl + k, st->p, do_ctrl, chi_global, mlp, k, st->N,
+                               st->sweep_index, st->lw.lz, st->d_res, visit, direction, kMixedRankFloor, st->d_info));
     }
     DMRG_CUDA(cudaMemcpyAsync(st->h_res, st->d_res, sizeof(BondResult), cudaMemcpyDeviceToHost, ctx->stream));
     DMRG_CUDA(cudaEventRecord(st->ev_res, ctx->stream));
@@ -879,6 +882,7 @@ dmrg_status dmrg_state_create(dmrg_ctx *ctx, int D, const dmrg_model_params *mp,
     for (int i = 0; i < N; ++i) { site_off[i] = total; total += al256(sizeof(double) * (size_t)st->cap[i] * 2 * st->cap[i + 1]); }
     for (int i = 0; i <= N; ++i) { env_off[i] = total; total += al256(sizeof(double) * (size_t)D * st->cap[i] * st->cap[i]); }
     size_t off_ctrl = total; total += al256(sizeof(dmrg_ctrl_state) * (N - 1));
+    size_t off_gctrl = total; total += al256(sizeof(dmrg_ctrl_state));
     size_t off_theta = total; total += al256(sizeof(double) * nmax);
     size_t off_X = total; total += al256(sizeof(double) * nmax * D);
     size_t off_Y = total; total += al256(sizeof(double) * nmax * D);
@@ -903,6 +907,8 @@ dmrg_status dmrg_state_create(dmrg_ctx *ctx, int D, const dmrg_model_params *mp,
     for (int i = 0; i < N; ++i) st->A[i] = reinterpret_cast<double *>(base + site_off[i]);
     for (int i = 0; i <= N; ++i) st->env[i] = reinterpret_cast<double *>(base + env_off[i]);
     st->ctrl = reinterpret_cast<dmrg_ctrl_state *>(base + off_ctrl);
+    st->gctrl = reinterpret_cast<dmrg_ctrl_state *>(base + off_gctrl);
+    st->global_chi = p->chi_min;
     st->theta = reinterpret_cast<double *>(base + off_theta);
     st->X = reinterpret_cast<double *>(base + off_X);
     st->Y = reinterpret_cast<double *>(base + off_Y);
@@ -971,6 +977,7 @@ dmrg_status dmrg_state_create(dmrg_ctx *ctx, int D, const dmrg_model_params *mp,
         if (s0 != DMRG_OK) return fail(s0);
     }
     k_init_ctrl<<<(N - 1 + 127) / 128, 128, 0, cs>>>(st->ctrl, N - 1, p->chi_min); DMRG_COUNT_LAUNCH();
+    k_init_ctrl<<<1, 128, 0, cs>>>(st->gctrl, 1, p->chi_min); DMRG_COUNT_LAUNCH();
     if (cudaGetLastError() != cudaSuccess) return fail(DMRG_ECUDA);
     if (cudaStreamSynchronize(cs) != cudaSuccess) return fail(DMRG_ECUDA);
     *out = st;
@@ -1024,6 +1031,15 @@ static dmrg_status sweep_close(dmrg_state *st, double E_last, double flops, doub
         r.seconds = seconds;
         r.flops = flops;
         *rec = r;
+    }
+    if (st->p.ctrl == DMRG_CTRL_GLOBAL) {
+        // global adaptive chi: one controller step per sweep, on the mean of
+        // the bonds' filtered entropies; its chi truncates every bond next sweep
+        DMRG_TRY(launch_global_step(st->ctx, st->ctrl, st->N - 1, st->gctrl, st->p));
+        DMRG_CUDA(cudaMemcpyAsync(st->ctx->h_pinned_i + 48, &st->gctrl->chi, sizeof(int), cudaMemcpyDeviceToHost,
+                                  st->ctx->stream));
+        DMRG_CUDA(cudaStreamSynchronize(st->ctx->stream));
+        st->global_chi = st->ctx->h_pinned_i[48];
     }
     st->sweep_index++;
     dmrg_status ds = dmrg_get_status(st->ctx);

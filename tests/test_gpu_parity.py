@@ -232,7 +232,7 @@ def near_tie_mask(ref, vis_k):
     return np.zeros(len(vis_k), dtype=bool)
 
 
-@pytest.mark.parametrize("ctrl,chi_max", [(3, 256), (0, 32), (2, 32)])
+@pytest.mark.parametrize("ctrl,chi_max", [(3, 256), (0, 32), (2, 32), (5, 32)])
 def test_dmrg_sweeps_match_oracle_N16(G, ctx, ctrl, chi_max):
     N = 16
     ref, recs, vis = run_pair(G, ctx, N, 4, ctrl=ctrl, chi_max=chi_max)

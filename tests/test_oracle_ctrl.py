@@ -9,6 +9,7 @@ import pytest
 from scipy.stats import norm
 
 import oracle as O
+import synth
 
 
 def P(**kw):
@@ -204,3 +205,29 @@ def test_adam_training_reduces_loss():
         L, g = O.mlp_loss_grad(Pv, X, t)
         O.adam_step(Pv, g, m, v, step, lr=3e-3)
     assert O.mlp_loss_grad(Pv, X, t)[0] < 0.1 * L_first
+
+
+def test_global_adaptive_chi_closed_form():
+    """Global adaptive chi (Section 6): one controller on the mean of the
+    per-bond filtered entropies, stepped once per sweep, chi uniform over the
+    bonds.  With alpha = 1 (S-bar_i = the bond's latest entropy), beta = 0,
+    K_p = 1, K_i = K_d = 0 the law is chi(t+1) = clamp(chi(t) +
+    round_half_even(mean_i S_last(i, t) - S_target)), written out here from
+    the recorded per-visit entropies."""
+    N, chi_min, chi_max, sweeps = 10, 2, 24, 4
+    kw = dict(ctrl=O.CTRL_GLOBAL, alpha_ema=1.0, beta=0.0, Kp=1.0, Ki=0.0, Kd=0.0, S_target=-3.0,
+              chi_min=chi_min, chi_max=chi_max, chi_init=chi_min, eps_trunc=1e-10)
+    p = O.make_params(**kw)
+    m0 = synth.initial_mps_entries(synth.workload_seed(0, 7), N, chi_min)
+    ref = O.dmrg_run(O.mpo(O.MODEL_XXZ, N, 1.0, 1.0), m0, p, sweeps)
+    V = ref["visits_per_sweep"]
+    g = chi_min
+    for t in range(sweeps):
+        chi_t = ref["chi"][t * V:(t + 1) * V]
+        assert np.all(chi_t == g), (t, chi_t, g)          # uniform over the bonds, set before the sweep
+        last = {}
+        for b, S in zip(ref["bond"][t * V:(t + 1) * V], ref["S"][t * V:(t + 1) * V]):
+            last[int(b)] = S                              # the bond's latest visit in this sweep
+        mean = sum(last[b] for b in range(N - 1)) / (N - 1)
+        g = int(min(max(g + round(mean - kw["S_target"]), chi_min), chi_max))
+    assert g > chi_min                                    # the law did move chi
