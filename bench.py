@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--micro", choices=["gemm", "svd", "svd_batch", "chains", "bond"], default=None,
+    ap.add_argument("--micro", choices=["gemm", "svd", "svd_batch", "chains", "bond", "ablation"], default=None,
                     help="one kernel-level invocation (for profiling): gemm M,N,K or svd chi")
     ap.add_argument("--shape", default="5120,4096,1024", help="--micro gemm: M,N,K")
     ap.add_argument("--chi", type=int, default=512, help="--micro svd: matrix 2chi x 2chi")
@@ -120,6 +120,8 @@ def run_micro(args):
         out = chains(args, G, synth, prec)
     elif args.micro == "bond":
         out = bond_micro(args, G, synth, prec)
+    elif args.micro == "ablation":
+        out = ablation(args, G, synth, prec)
     else:
         chi = args.chi
         n = 2 * chi
@@ -215,6 +217,36 @@ def bond_micro(args, G, synth, prec):
     st.close()
     ctx.close()
     return {"micro": "bond", "prec": args.prec, "chi": [c[k], c[k + 1], c[k + 2]], "ms_per_bond": ms}
+
+
+def ablation(args, G, synth, prec):
+    """The controller ablation on the 20-site Heisenberg chain, chi_max = 64,
+    5 sweeps: fixed chi = 64, the PID of Algorithm 2, threshold truncation
+    (eps_trunc = 1e-10), Algorithm 1's direct rule and the global adaptive
+    chi.  E/N is also given in the paper's Pauli-matrix units (x 4)."""
+    import torch
+    N, cm, sweeps = 20, 64, 5
+    modes = [("fixed", G.CTRL_FIXED), ("pid", G.CTRL_PID), ("threshold", G.CTRL_THRESHOLD),
+             ("direct", G.CTRL_DIRECT), ("global", G.CTRL_GLOBAL)]
+    out = {"micro": "ablation", "N": N, "chi_max": cm, "sweeps": sweeps, "prec": args.prec, "runs": {}}
+    for name, mode in modes:
+        ctx = G.Context(0)
+        apply_opts(ctx, args)
+        p = G.make_params(prec=prec, ctrl=mode, chi_max=cm, chi_fixed=cm, chi_init=4, max_sweeps=sweeps)
+        W = ctx.build_mpo(G.XXZ, N, 1.0, 1.0)
+        m0 = torch.from_numpy(synth.initial_mps_entries(synth.workload_seed(1, 20), N, p.chi_init)).cuda()
+        torch.cuda.synchronize()
+        st = G.State(ctx, W, m0, p, 1.0, 1.0)
+        recs, vis = st.sweep(sweeps)
+        V = 2 * N - 3
+        last = vis[-V:]
+        out["runs"][name] = {"E_per_site": recs[-1].E / N, "E_per_site_pauli": 4 * recs[-1].E / N,
+                             "seconds": sum(r.seconds for r in recs),
+                             "mean_chi_last_sweep": sum(v.k for v in last) / V,
+                             "max_chi": max(v.k for v in vis)}
+        st.close()
+        ctx.close()
+    return out
 
 
 def chains(args, G, synth, prec):

@@ -304,3 +304,22 @@ def test_dmrg_mlp_controller_matches_oracle(G, ctx):
     assert np.array_equal(np.array([v.k for v in vis]), ref["k"])
     E = np.array([r.E for r in recs])
     assert np.all(np.abs(E - ref["E"]) / N <= 1e-10)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_table4_fixed_chi_energy(G, ctx, prec):
+    """Table 4's fixed-chi row: the 20-site Heisenberg chain at chi = 64 after
+    5 sweeps gives E/N = -1.73649 in the table's Pauli-matrix units (x 4), to
+    the 5 printed decimals."""
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    ref = gold["heisenberg_N20_pauli_E_per_site"]
+    N = 20
+    p = G.make_params(prec=G.PREC_FP64 if prec == "fp64" else G.PREC_3XTF32, ctrl=G.CTRL_FIXED, chi_max=64,
+                      chi_fixed=64, chi_init=4)
+    W = ctx.build_mpo(G.XXZ, N, 1.0, 1.0)
+    m0 = synth.initial_mps_entries(synth.workload_seed(1, 20), N, p.chi_init)
+    st = G.State(ctx, W, dev(m0), p, 1.0, 1.0)
+    recs, _ = st.sweep(5)
+    st.close()
+    assert abs(4 * recs[-1].E / N - ref["value"]) <= 0.5 * 10.0 ** -ref["decimals"]
