@@ -370,6 +370,14 @@ dmrg_status dmrg_state_ctrl(dmrg_state *st, dmrg_ctrl_state **ctrl_dev /* N-1 */
 long long dmrg_state_mps_size(dmrg_state *st);
 dmrg_status dmrg_state_get_mps(dmrg_state *st, double *out);
 dmrg_status dmrg_state_put_mps(dmrg_state *st, const double *in);
+/* Failure detection without a fault (no counterpart in the paper): runs the
+ * bounded grid barrier of the cooperative kernels with two co-resident
+ * blocks.  With absent = 1 one block never arrives; the other polls the
+ * barrier spin_limit times, records DMRG_ETIMEOUT in the context's status
+ * word and returns (no trap).  Returns the status read back (DMRG_ETIMEOUT
+ * when absent = 1, DMRG_OK when both blocks arrive); the context stays
+ * usable.  Allocates and frees 64 bytes and synchronises. */
+dmrg_status dmrg_wait_selftest(dmrg_ctx *ctx, long long spin_limit, int absent);
 /* Kernels launched by this library since it was loaded (all contexts). */
 long long dmrg_launch_count(void);
 /* Live timing of the heavy kernels (no counterpart in the paper): with

@@ -120,6 +120,7 @@ def _declare(L):
                                      _VP, _VP, _VP]),
         "dmrg_graph_begin": (S, [_VP]),
         "dmrg_sweep_chains": (S, [_I, _VP, _VP, _I, _VP, _VP]),
+        "dmrg_wait_selftest": (S, [_VP, C.c_longlong, _I]),
         "dmrg_autotune_gemm": (S, [_VP, _I, _VP, _VP, _VP, _I]),
         "dmrg_autotune_svd": (S, [_VP, _I, _VP, _I]),
         "dmrg_autotune_clear": (S, [_VP]),
@@ -163,7 +164,7 @@ def exported_symbols():
         "dmrg_mlp_loss_grad", "dmrg_mlp_adam", "dmrg_gemm", "dmrg_set_option",
         "dmrg_state_mps_size", "dmrg_state_get_mps", "dmrg_state_put_mps", "dmrg_launch_count",
         "dmrg_profile", "dmrg_profile_read", "svd_truncate_noalloc", "dmrg_mlp_train",
-        "svd_truncate_batched", "dmrg_sweep_chains", "dmrg_autotune_gemm", "dmrg_autotune_svd",
+        "svd_truncate_batched", "dmrg_sweep_chains", "dmrg_wait_selftest", "dmrg_autotune_gemm", "dmrg_autotune_svd",
         "dmrg_autotune_clear", "dmrg_autotune_save", "dmrg_autotune_load", "dmrg_autotune_entries", "dmrg_graph_begin", "dmrg_graph_end", "dmrg_graph_launch", "dmrg_graph_destroy",
     ]
 
@@ -333,6 +334,10 @@ class Context:
 
     def autotune_entries(self):
         return int(lib().dmrg_autotune_entries(self.h, 0)), int(lib().dmrg_autotune_entries(self.h, 1))
+
+    def wait_selftest(self, spin_limit: int, absent: bool) -> int:
+        """Status code of the bounded-barrier self-test (0 = ok)."""
+        return int(lib().dmrg_wait_selftest(self.h, int(spin_limit), int(absent)))
 
     def graph_begin(self):
         _check(lib().dmrg_graph_begin(self.h), "dmrg_graph_begin")

@@ -168,7 +168,7 @@ namespace dmrg {
 // co-resident).  words[0] = arrival count, words[1] = generation.
 // Returns false (and sets ST_TIMEOUT) if the wait gave up.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool grid_barrier(unsigned *words, int *status)
+__device__ __forceinline__ bool grid_barrier(unsigned *words, int *status, long long spin_limit = kSpinLimit)
 {
     __shared__ int ok_s;
     __syncthreads();
@@ -186,7 +186,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *words, int *status)
             long long spins = 0;
             while (*gen == g) {
                 if (spins > 4096) __nanosleep(64);
-                if (++spins > kSpinLimit) {
+                if (++spins > spin_limit) {
                     atomicOr(status, ST_TIMEOUT);
                     ok = 0;
                     break;

@@ -1203,6 +1203,41 @@ dmrg_status dmrg_state_put_mps(dmrg_state *st, const double *in)
 
 long long dmrg_launch_count(void) { return g_launch_count.load(); }
 
+}  // extern "C"
+
+namespace dmrg {
+namespace {
+// Two co-resident blocks meet at the bounded grid barrier; with `absent` set,
+// block 0 never arrives, so block 1 polls until spin_limit, records
+// ST_TIMEOUT in the status word and returns.  Nothing traps or faults.
+__global__ void k_wait_selftest(unsigned *words, int *status, long long spin_limit, int absent, int *result)
+{
+    if (absent && blockIdx.x == 0) return;
+    const bool ok = grid_barrier(words, status, spin_limit);
+    if (threadIdx.x == 0) result[blockIdx.x] = ok ? 1 : -1;
+}
+}  // namespace
+}  // namespace dmrg
+
+extern "C" {
+
+dmrg_status dmrg_wait_selftest(dmrg_ctx *ctx, long long spin_limit, int absent)
+{
+    if (!ctx || spin_limit < 1) return DMRG_EINVAL;
+    void *buf = nullptr;
+    DMRG_CUDA(cudaMalloc(&buf, 64));
+    DMRG_CUDA(cudaMemsetAsync(buf, 0, 64, ctx->stream));
+    unsigned *words = static_cast<unsigned *>(buf);
+    int *result = reinterpret_cast<int *>(static_cast<char *>(buf) + 32);
+    int *status = ctx->d_status;
+    void *args[] = {&words, &status, &spin_limit, &absent, &result};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_wait_selftest, dim3(2), dim3(32), args, 0, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(buf);
+    if (e != cudaSuccess) return DMRG_ECUDA;
+    return dmrg_get_status(ctx);
+}
+
 dmrg_status dmrg_profile(dmrg_ctx *ctx, int on)
 {
     if (!ctx) return DMRG_EINVAL;
