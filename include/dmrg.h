@@ -161,7 +161,10 @@ const char *dmrg_status_string(dmrg_status s);
  * 1 mixed: FP32 Jacobi, FP64-re-orthonormalised isometry, tensor-core
  * projection for the other factor; values below 2^-22 s_0 are not resolved),
  * "bjac_pairs" / "bjac_inner" (blocked FP32 Jacobi: target block pairs per
- * round, inner sweeps per block pair), "jacobi_max_sweeps" (standalone
+ * round, inner sweeps per block pair), "bjac_gram" (1: the blocked FP32
+ * Jacobi takes its inner sweep on the block pair's Gram matrix and applies
+ * the accumulated rotation once; 0: rotations of the vectors themselves),
+ * "jacobi_max_sweeps" (standalone
  * svd_truncate and svd_truncate_batched), "batched_inner" (svd_truncate_batched:
  * Jacobi sweeps on each 32 x 32 block-pair Gram matrix, 4), "batched_floor32"
  * (FP32 svd_truncate_batched: vectors with norm below this x |A|_F take no

@@ -132,6 +132,7 @@ struct dmrg_ctx {
     int batched_ns = 1;          // FP32 batched SVD: Newton-Schulz step on each block rotation
     int jacobi_qr = 1;           // FP32 Jacobi on the R factor of the vectors (QR preconditioning)
     int jacobi_rank_drop = 1;    // ... and only on its rows above the FP32 noise (numerical row rank)
+    int bjac_gram = 1;           // blocked FP32 Jacobi: inner sweep in Gram form (k_bjac32g)
     double jacobi32_floor = 1.1920928955078125e-07;   // FP32 Jacobi: vectors below this x |A|_F take no rotation
     int gbj_min_r = 0;           // FP32 Jacobi: Gram-block cooperative form from this many vectors on (0 = off)
     double batched_floor32 = 1.1920928955078125e-07;  // FP32 batched SVD: vectors below this x |A|_F do not rotate

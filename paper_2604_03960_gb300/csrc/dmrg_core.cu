@@ -570,6 +570,7 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
     if (!std::strcmp(name, "batched_ns")) { ctx->batched_ns = value != 0.0; return DMRG_OK; }
     if (!std::strcmp(name, "jacobi_qr")) { ctx->jacobi_qr = value != 0.0; return DMRG_OK; }
     if (!std::strcmp(name, "jacobi_rank_drop")) { ctx->jacobi_rank_drop = value != 0.0; return DMRG_OK; }
+    if (!std::strcmp(name, "bjac_gram")) { ctx->bjac_gram = value != 0.0; return DMRG_OK; }
     if (!std::strcmp(name, "gbj_min_r")) {
         if (!(value >= 0.0 && value <= 1e6)) return DMRG_EINVAL;
         ctx->gbj_min_r = (int)value;

@@ -15,6 +15,7 @@
 // without rotations.  On exit s_i = |x_i|, u_i = x_i / s_i and the
 // accumulated rotations give V.
 #include "common.cuh"
+#include "mma_tf32.cuh"
 
 #include <cooperative_groups.h>
 #include <algorithm>
@@ -626,6 +627,263 @@ __global__ void __launch_bounds__(kBjacThreads) k_bjac32(float *__restrict__ X, 
     }
 }
 
+// Blocked FP32 Jacobi with the inner sweep in Gram form.  The CTA that owns a
+// block pair stages its NV = 2 BW vectors in shared memory and
+//   1. forms their Gram matrix G = X X^T on the tensor cores (3xTF32);
+//   2. runs one cyclic Jacobi sweep on G -- the rotations an inner sweep over
+//      the vector pairs would apply, in exact arithmetic -- accumulating the
+//      product Q of the rotations, then one FP32 Newton-Schulz step on Q;
+//   3. writes x_j <- sum_i Q[i][j] x_i with FP32 FMAs (3xTF32 products carry
+//      ~2^-22 relative error, which would accumulate in the vectors over the
+//      rounds; in G it only perturbs the rotations, which stay orthogonal).
+// A round is a few dozen dependent steps on a small matrix, where the vector
+// form takes 2 BW - 1 steps of reductions over length-l vectors.  Outer
+// rounds, grid barrier and convergence test as k_bjac32.
+//
+// Rotation of pair (p, q): x_p <- c x_p - s x_q, x_q <- s x_p + c x_q, i.e.
+// X <- X J with J[x][x] = c, J[partner][x] = -s for x = p and +s for x = q.
+// Then G <- J^T G J and Q <- Q J entrywise from the previous step's buffer
+// (double-buffered: one barrier per step).  The rotation of step u + 1 is
+// taken in step u by the thread that owns its pair, from the same
+// expressions that produce the new entries.  Entry (i, j) is evaluated in
+// the order of (min, max), so G stays bitwise symmetric.
+template <int BW>
+__global__ void __launch_bounds__(kBjacThreads) k_bjac32g(float *__restrict__ X, int r_all, int l, int ls,
+                                                          int max_sweeps, double tol, unsigned *sync, int *status,
+                                                          int *info, const double *F2, double small,
+                                                          const int *r_eff)
+{
+    constexpr int NW = kBjacThreads / 32;
+    constexpr int NV = 2 * BW;
+    constexpr int MT = (NV + 15) / 16, NT = NV / 8;     // Gram tiles of 16 x 8
+    constexpr int WPT = NW / (MT * NT);                  // warps per Gram tile (k split)
+    static_assert(NV >= 8 && WPT >= 1, "block width");
+    extern __shared__ float xs[];                        // [NV][ls]: vector q at xs + q ls
+    __shared__ int vid[NV];
+    __shared__ float Gb[2][NV][NV + 1], Qb[2][NV][NV + 1];
+    __shared__ float part[NW][16][8];
+    __shared__ float pc[2][NV], psn[2][NV];              // step parameters per index: c, J[partner][x]
+    __shared__ int ppt[2][NV];                           // partner (the index itself when not rotated)
+    __shared__ unsigned block_rot, pair_rot;
+    const int r = r_eff ? min(r_all, max(1, *r_eff)) : r_all;
+    const float floor2f = (float)(small * small * F2[0]), tolf = (float)tol;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, c4 = lane & 3;
+    const int nb = (r + BW - 1) / BW;
+    const int nbp = nb + (nb & 1);
+    const int npairs = nbp / 2;
+    const int nchunk = (l + 7) / 8;                      // positions in chunks of 8 (zero tail up to ls)
+    unsigned *barrier = sync;
+    unsigned *rotc = sync + 2;
+    int sweep = 0;
+    bool converged = false;
+
+    // new G entry (i <= j) of step parameters `pb` from buffer `gb`
+    auto gnew = [&](int pb, int gb, int i, int j) {
+        const float ci = pc[pb][i], si = psn[pb][i], cj = pc[pb][j], sj = psn[pb][j];
+        const int pi = ppt[pb][i], pj = ppt[pb][j];
+        float v = ci * cj * Gb[gb][i][j];
+        v = fmaf(ci * sj, Gb[gb][i][pj], v);
+        v = fmaf(si * cj, Gb[gb][pi][j], v);
+        return fmaf(si * sj, Gb[gb][pi][pj], v);
+    };
+    // parameters of pair (a, b) from its three Gram entries; true if it rotates
+    auto setpar = [&](int pb, int a, int b, float gaa, float gbb, float gab) {
+        float c = 1.f, sn = 0.f;
+        const bool rot = vid[a] >= 0 && vid[b] >= 0 && rot32(gaa, gbb, gab, floor2f, tolf, c, sn);
+        pc[pb][a] = c; psn[pb][a] = rot ? -sn : 0.f; ppt[pb][a] = rot ? b : a;
+        pc[pb][b] = c; psn[pb][b] = rot ? sn : 0.f; ppt[pb][b] = rot ? a : b;
+        return rot;
+    };
+
+    for (; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) block_rot = 0;
+        __syncthreads();
+        for (int t = 0; t < nbp - 1; ++t) {
+            for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
+                int I, J;
+                rr_pair(nbp, t, p, I, J);
+                if (threadIdx.x < NV) {
+                    const int blk = threadIdx.x < BW ? I : J;
+                    const int v = blk * BW + (threadIdx.x % BW);
+                    vid[threadIdx.x] = (blk < nb && v < r) ? v : -1;
+                }
+                if (threadIdx.x == 0) pair_rot = 0;
+                __syncthreads();
+                for (int q = warp; q < NV; q += NW) {
+                    const int v = vid[q];
+                    float *dst = xs + (long long)q * ls;
+                    const float *src = X + (long long)(v < 0 ? 0 : v) * l;
+                    for (int e = lane; e < ls; e += 32) dst[e] = (v >= 0 && e < l) ? src[e] : 0.f;
+                }
+                __syncthreads();
+                // 1. Gram matrix: warp w adds chunks w % WPT, + WPT, ... of tile w / WPT
+                {
+                    const int tile = warp / WPT, kp = warp % WPT;
+                    const int mi = tile / NT, ni = tile % NT;
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                    auto fa = [&](int m, int k) { return m < NV ? xs[m * ls + k] : 0.f; };
+                    auto fb = [&](int k, int n) { return xs[n * ls + k]; };
+                    for (int ck = kp; ck < nchunk; ck += WPT) mma3(acc, g, c4, fa, fb, 16 * mi, 8 * ni, 8 * ck);
+                    part[warp][g][2 * c4] = acc[0];
+                    part[warp][g][2 * c4 + 1] = acc[1];
+                    part[warp][g + 8][2 * c4] = acc[2];
+                    part[warp][g + 8][2 * c4 + 1] = acc[3];
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < NV * NV; e += kBjacThreads) {
+                    const int i = e / NV, j = e % NV;
+                    Qb[0][i][j] = (i == j) ? 1.f : 0.f;
+                    if (i > j) continue;
+                    const int tile = (i / 16) * NT + j / 8;
+                    float a = 0.f;
+                    for (int kp = 0; kp < WPT; ++kp) a += part[tile * WPT + kp][i % 16][j % 8];
+                    Gb[0][i][j] = a;
+                    Gb[0][j][i] = a;
+                }
+                __syncthreads();
+                unsigned myrot = 0;
+                if (threadIdx.x < BW) {
+                    int a_, b_;
+                    rr_pair(NV, 0, threadIdx.x, a_, b_);
+                    myrot += setpar(0, a_, b_, Gb[0][a_][a_], Gb[0][b_][b_], Gb[0][min(a_, b_)][max(a_, b_)]);
+                }
+                __syncthreads();
+                // 2. the sweep on G; step u reads buffer u & 1 and its parameters u & 1
+                for (int u = 0; u < NV - 1; ++u) {
+                    const int cb = u & 1, nbf = cb ^ 1;
+                    for (int e = threadIdx.x; e < 2 * NV * NV; e += kBjacThreads) {
+                        if (e < NV * NV) {
+                            const int i = e / NV, j = e % NV;
+                            if (i > j) continue;
+                            const float v = gnew(cb, cb, i, j);
+                            Gb[nbf][i][j] = v;
+                            Gb[nbf][j][i] = v;
+                        } else {
+                            const int e2 = e - NV * NV, i = e2 / NV, j = e2 % NV;
+                            Qb[nbf][i][j] = fmaf(psn[cb][j], Qb[cb][i][ppt[cb][j]], pc[cb][j] * Qb[cb][i][j]);
+                        }
+                    }
+                    if (u + 1 < NV - 1 && threadIdx.x < BW) {
+                        int a_, b_;
+                        rr_pair(NV, u + 1, threadIdx.x, a_, b_);
+                        const float gaa = gnew(cb, cb, a_, a_), gbb = gnew(cb, cb, b_, b_);
+                        const float gab = gnew(cb, cb, min(a_, b_), max(a_, b_));
+                        myrot += setpar(nbf, a_, b_, gaa, gbb, gab);
+                    }
+                    __syncthreads();
+                }
+                if (myrot) atomicAdd(&pair_rot, myrot);
+                __syncthreads();
+                constexpr int qf = (NV - 1) & 1;                 // buffer holding the final Q
+                const float(*Qf)[NV + 1] = Qb[qf];
+                const unsigned prot = pair_rot;
+                if (prot) {
+                    // Q <- Q (3 I - Q^T Q) / 2: orthogonal again at FP32 rounding
+                    for (int e = threadIdx.x; e < NV * NV; e += kBjacThreads) {
+                        const int i = e / NV, j = e % NV;
+                        float a = 0.f;
+                        for (int k2 = 0; k2 < NV; ++k2) a = fmaf(Qb[qf][k2][i], Qb[qf][k2][j], a);
+                        Gb[qf ^ 1][i][j] = (i == j ? 1.5f : 0.f) - 0.5f * a;
+                    }
+                    __syncthreads();
+                    for (int e = threadIdx.x; e < NV * NV; e += kBjacThreads) {
+                        const int i = e / NV, j = e % NV;
+                        float a = 0.f;
+                        for (int k2 = 0; k2 < NV; ++k2) a = fmaf(Qb[qf][i][k2], Gb[qf ^ 1][k2][j], a);
+                        Qb[qf ^ 1][i][j] = a;
+                    }
+                    __syncthreads();
+                    Qf = Qb[qf ^ 1];
+                    if (threadIdx.x == 0) block_rot += prot;
+                    // 3. x_j <- sum_i Q[i][j] x_i in FP32 (the vectors carry FP32
+                    // rounding only), straight to X: a thread keeps OPT columns
+                    // of Q in registers and walks positions with its group
+                    constexpr int OPT = NV >= 32 ? 2 : 4, NG = NV / OPT, TPG = kBjacThreads / NG;
+                    const int gi = threadIdx.x / TPG, t0 = threadIdx.x % TPG;
+                    float qr[OPT][NV];
+                    int vo[OPT];
+#pragma unroll
+                    for (int o = 0; o < OPT; ++o) {
+                        vo[o] = vid[gi * OPT + o];
+#pragma unroll
+                        for (int i = 0; i < NV; ++i) qr[o][i] = Qf[i][gi * OPT + o];
+                    }
+                    for (int e = t0; e < l; e += TPG) {
+                        float acc[OPT];
+#pragma unroll
+                        for (int o = 0; o < OPT; ++o) acc[o] = 0.f;
+#pragma unroll
+                        for (int i = 0; i < NV; ++i) {
+                            const float x = xs[i * ls + e];
+#pragma unroll
+                            for (int o = 0; o < OPT; ++o) acc[o] = fmaf(qr[o][i], x, acc[o]);
+                        }
+#pragma unroll
+                        for (int o = 0; o < OPT; ++o)
+                            if (vo[o] >= 0) X[(long long)vo[o] * l + e] = acc[o];
+                    }
+                }
+                __syncthreads();
+            }
+            if (!block_barrier(barrier, status)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
+                return;
+            }
+        }
+        if (threadIdx.x == 0 && block_rot) atomicAdd(&rotc[sweep & 1], block_rot);
+        if (!block_barrier(barrier, status)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
+            return;
+        }
+        const unsigned total = *(volatile unsigned *)&rotc[sweep & 1];
+        if (blockIdx.x == 0 && threadIdx.x == 0) rotc[(sweep + 1) & 1] = 0u;
+        if (total == 0u) {
+            converged = true;
+            ++sweep;
+            break;
+        }
+        if (!block_barrier(barrier, status)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
+            return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        info[0] = converged ? sweep : -sweep;
+        if (!converged) atomicOr(status, ST_NOCONV);
+    }
+}
+
+// shared-memory row stride of the Gram form: l rounded up to whole 8-position
+// chunks, + 4 (odd multiple of 4 floats: the mma fragment reads of 8 rows x 4
+// columns fall in 32 distinct banks)
+inline int bjac32g_stride(int l) { return ((l + 7) / 8) * 8 + 4; }
+
+template <int BW>
+dmrg_status launch_bjac32g(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps, double tol, unsigned *sync,
+                           int *d_info, const double *F2, double small, const int *r_eff)
+{
+    int ls = bjac32g_stride(l);
+    const size_t smem = sizeof(float) * 2 * BW * (size_t)ls;
+    static size_t attr = 0;
+    if (attr < smem) {
+        DMRG_CUDA(cudaFuncSetAttribute(k_bjac32g<BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = smem;
+    }
+    int per_sm = 0;
+    DMRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bjac32g<BW>, kBjacThreads, smem));
+    if (per_sm < 1) return DMRG_EUNSUPPORTED;
+    const int nb = (r + BW - 1) / BW;
+    const int npairs = (nb + (nb & 1)) / 2;
+    int blocks = std::min(npairs, per_sm * ctx->num_sms);
+    if (blocks < 1) blocks = 1;
+    int *status = ctx->d_status;
+    void *args[] = {&X, (void *)&r, (void *)&l, &ls, &max_sweeps, (void *)&tol, &sync, &status, &d_info,
+                    (void *)&F2, (void *)&small, (void *)&r_eff};
+    DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_bjac32g<BW>, dim3(blocks), dim3(kBjacThreads), args, smem,
+                                          ctx->stream)); DMRG_COUNT_LAUNCH();
+    return DMRG_OK;
+}
+
 template <int BW>
 dmrg_status launch_bjac32(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps, double tol, unsigned *sync,
                           int *d_info, const double *F2, double small, int max_inner, const int *r_eff)
@@ -910,8 +1168,17 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
         while (bw > 1 && (long long)bw > cap) bw /= 2;
         (void)args;
         (void)blocks;
-        dmrg_status e;
-        switch (bw) {
+        dmrg_status e = DMRG_EUNSUPPORTED;
+        // Gram-form inner sweep (one inner sweep per block pair, BW >= 4)
+        const bool gram = ctx->bjac_gram && inner == 1 && bw >= 4 &&
+                          8LL * bw * bjac32g_stride(l) <= 192LL * 1024;
+        if (gram) {
+            switch (bw) {
+            case 16: e = launch_bjac32g<16>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, reff); break;
+            case 8: e = launch_bjac32g<8>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, reff); break;
+            default: e = launch_bjac32g<4>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, reff); break;
+            }
+        } else switch (bw) {
         case 16: e = launch_bjac32<16>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner, reff); break;
         case 8: e = launch_bjac32<8>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner, reff); break;
         case 4: e = launch_bjac32<4>(ctx, X, r, l, max_sweeps, tol, sync, d_info, F2, small, inner, reff); break;

@@ -87,8 +87,9 @@ def test_checkpoint_roundtrip(G, ctx):
     st.close()
 
 
-@pytest.mark.parametrize("chi,gbj", [(64, 0), (256, 0), (512, 0), (256, 32), (512, 32)])
-def test_mixed_svd_exact_spectrum(G, chi, gbj):
+@pytest.mark.parametrize("chi,opt", [(64, None), (256, None), (512, None), (1024, None), (256, ("gbj_min_r", 32)),
+                                     (512, ("gbj_min_r", 32)), (256, ("bjac_gram", 0)), (512, ("bjac_gram", 0))])
+def test_mixed_svd_exact_spectrum(G, chi, opt):
     """Standalone mixed SVD (svd_prec = 1) on U diag(s) V^T with s known:
     retained values within 1e-7 relative (FP64 norms of the FP64 projection
     on the re-orthonormalised isometry: second order in its direction errors,
@@ -101,7 +102,8 @@ def test_mixed_svd_exact_spectrum(G, chi, gbj):
     reconstruction within the discarded weight plus 1e-6 |A|."""
     c = G.Context(0)
     c.set_option("svd_prec", 1)
-    c.set_option("gbj_min_r", gbj)          # 32: the Gram-block cooperative Jacobi
+    if opt:                                 # gbj_min_r: the Gram-block cooperative Jacobi;
+        c.set_option(*opt)                  # bjac_gram = 0: blocked Jacobi, inner sweep over vectors
     n = 2 * chi
     s_ref = synth.spectrum("exp", n, chi)
     A = synth.svd_test_matrix(synth.workload_seed(1, chi), n, n, s_ref)
