@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(kBT) k_svd_batched(const BDesc *__restrict__ d
     T *X = work + d.off_X, *V = work + d.off_V;
     const double *A = theta + d.off_in;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int team = warp / kTeamWarps, tw = warp % kTeamWarps;
+    const int team = warp / kTeamWarps;
     const int rpad = nb * kBlk;
     // rotate while a cosine exceeds l eps (FP64) or 1e-5 (FP32)
     const double tol = tol_by_l ? tol_unit * (double)(l > 16 ? l : 16) : tol_unit;

@@ -326,83 +326,6 @@ __global__ void k_jac32_load(const double *__restrict__ A, int m, int n, int dir
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.y == 0 && threadIdx.x < 8) sync[threadIdx.x] = 0u;
 }
 
-__global__ void __launch_bounds__(256) k_jac32_sweeps(float *__restrict__ X, int r, int l, int max_sweeps, double tol,
-                                                      unsigned *sync, int *status, int *info, const double *F2,
-                                                      double small)
-{
-    const float floor2f = (float)(small * small * F2[0]), tolf = (float)tol;
-    const int lane = threadIdx.x & 31;
-    const int warps_per_block = blockDim.x >> 5;
-    const int gwarp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
-    const int nwarps = gridDim.x * warps_per_block;
-    const int rp = r + (r & 1);
-    const int npairs = rp / 2;
-    unsigned *barrier = sync;
-    unsigned *rotc = sync + 2;
-    __shared__ unsigned block_rot;
-    int sweep = 0;
-    bool converged = false;
-    for (; sweep < max_sweeps; ++sweep) {
-        if (threadIdx.x == 0) block_rot = 0;
-        __syncthreads();
-        unsigned my_rot = 0;
-        for (int t = 0; t < rp - 1; ++t) {
-            for (int p = gwarp; p < npairs; p += nwarps) {
-                int i, j;
-                rr_pair(rp, t, p, i, j);
-                if (i >= r || j >= r) continue;
-                float *xi = X + (long long)i * l, *xj = X + (long long)j * l;
-                float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f, g0 = 0.f, g1 = 0.f;
-                int k = lane;
-                for (; k + 32 < l; k += 64) {
-                    float u = xi[k], v = xj[k], u2 = xi[k + 32], v2 = xj[k + 32];
-                    a0 = fmaf(u, u, a0); b0 = fmaf(v, v, b0); g0 = fmaf(u, v, g0);
-                    a1 = fmaf(u2, u2, a1); b1 = fmaf(v2, v2, b1); g1 = fmaf(u2, v2, g1);
-                }
-                if (k < l) {
-                    float u = xi[k], v = xj[k];
-                    a0 = fmaf(u, u, a0); b0 = fmaf(v, v, b0); g0 = fmaf(u, v, g0);
-                }
-                const float a = warp_sum_f(a0 + a1), b = warp_sum_f(b0 + b1), g = warp_sum_f(g0 + g1);
-                float c, s;
-                if (!rot32(a, b, g, floor2f, tolf, c, s)) continue;
-                for (int q = lane; q < l; q += 32) {
-                    float u = xi[q], v = xj[q];
-                    xi[q] = fmaf(c, u, -s * v);
-                    xj[q] = fmaf(s, u, c * v);
-                }
-                if (lane == 0) my_rot++;
-            }
-            if (!block_barrier(barrier, status)) {
-                if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
-                return;
-            }
-        }
-        if (lane == 0 && my_rot) atomicAdd(&block_rot, my_rot);
-        __syncthreads();
-        if (threadIdx.x == 0 && block_rot) atomicAdd(&rotc[sweep & 1], block_rot);
-        if (!block_barrier(barrier, status)) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
-            return;
-        }
-        unsigned total = *(volatile unsigned *)&rotc[sweep & 1];
-        if (blockIdx.x == 0 && threadIdx.x == 0) rotc[(sweep + 1) & 1] = 0u;
-        if (total == 0u) {
-            converged = true;
-            ++sweep;
-            break;
-        }
-        if (!block_barrier(barrier, status)) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = -(sweep + 1);
-            return;
-        }
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        info[0] = converged ? sweep : -sweep;
-        if (!converged) atomicOr(status, ST_NOCONV);
-    }
-}
-
 // Single-CTA FP32 Jacobi with the vectors resident in shared memory (r*l
 // floats <= kSmemJacFloats): the rounds synchronise with __syncthreads only.
 constexpr int kSmemJacFloats = 50 * 1024;
@@ -1043,7 +966,6 @@ dmrg_status frob2_f32(dmrg_ctx *ctx, const float *A, long long n, double *F2)
 // the FP32 rounding X already carries; the Jacobi then rotates r_eff rows.
 __global__ void k_row_rank32(const float *__restrict__ X, int r, int l, double *__restrict__ rn, int *r_eff)
 {
-    __shared__ double sh[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = warp; i < r; i += nw) {
         float a = 0.f;
@@ -1061,7 +983,6 @@ __global__ void k_row_rank32(const float *__restrict__ X, int r, int l, double *
         while (j > 1 && suffix + rn[j - 1] <= thr) suffix += rn[--j];
         *r_eff = j;
     }
-    (void)sh;
 }
 
 // FP32 one-sided Jacobi on the columns (dir 0) or rows (dir 1) of theta; on
@@ -1125,24 +1046,11 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
     // thousand terms are good to ~1e-6, and the FP64 Newton-Schulz step that
     // follows takes the retained vectors from 1e-5 to ~1e-10
     const double tol = 1.0e-5;
-    const int rp = r + (r & 1);
-    const int npairs = rp / 2;
-    int threads = 256, blocks = 1;
-    if (r > 128) {
-        int per_sm = 0;
-        DMRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jac32_sweeps, threads, 0));
-        int maxb = per_sm * ctx->num_sms;
-        blocks = (npairs + 7) / 8;
-        if (blocks > maxb) blocks = maxb;
-        if (blocks < 1) blocks = 1;
-    }
     int *status = ctx->d_status;
     // F2 = |A|_F^2 from the FP32 copy; vectors below 2^-23 |A|_F are dropped anyway
     const double *F2 = reinterpret_cast<const double *>(sync + 4);
     const double small = ctx->jacobi32_floor;
     k_frob2_f<<<1, 256, 0, st>>>(X, (long long)r * l, reinterpret_cast<double *>(sync + 4)); DMRG_COUNT_LAUNCH();
-    void *args[] = {&X, (void *)&r, (void *)&l, &max_sweeps, (void *)&tol, &sync, &status, &d_info, &F2,
-                    (void *)&small};
     prof_mark(ctx, PROF_JACOBI32);
     if ((long long)r * l <= kSmemJacFloats) {
         const int smem = (int)(sizeof(float) * (size_t)r * l);
@@ -1166,8 +1074,6 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
         int bw = 1;
         while (bw < 16 && 2LL * bw <= cap && (r / (2 * bw)) > pairs) bw *= 2;
         while (bw > 1 && (long long)bw > cap) bw /= 2;
-        (void)args;
-        (void)blocks;
         dmrg_status e = DMRG_EUNSUPPORTED;
         // Gram-form inner sweep (one inner sweep per block pair, BW >= 4)
         const bool gram = ctx->bjac_gram && inner == 1 && bw >= 4 &&
