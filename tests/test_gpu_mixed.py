@@ -40,7 +40,9 @@ def run(G, ctx, N, sweeps, prec, model=O.MODEL_XXZ, Delta=1.0, J2=0.0, **kw):
     return st, recs, vis
 
 
-@pytest.mark.parametrize("N,chi_max,gbj", [(16, 64, 0), (24, 48, 0), (16, 64, 16)])
+# chi_max = 128: theta up to 256 x 256 takes the blocked FP32 Jacobi (block
+# width 4, Gram-form inner sweep); smaller bonds take the single-CTA kernel
+@pytest.mark.parametrize("N,chi_max,gbj", [(16, 64, 0), (24, 48, 0), (16, 64, 16), (16, 128, 0)])
 def test_mixed_energy_matches_fp64_and_ed(G, ctx, N, chi_max, gbj):
     ctx.set_option("gbj_min_r", gbj)
     kw = dict(ctrl=G.CTRL_THRESHOLD, chi_max=chi_max, chi_init=8)
@@ -87,7 +89,8 @@ def test_checkpoint_roundtrip(G, ctx):
     st.close()
 
 
-@pytest.mark.parametrize("chi,opt", [(64, None), (256, None), (512, None), (1024, None), (256, ("gbj_min_r", 32)),
+@pytest.mark.parametrize("chi,opt", [(64, None), (150, None), (256, None), (512, None), (1024, None),
+                                     (256, ("gbj_min_r", 32)),
                                      (512, ("gbj_min_r", 32)), (256, ("bjac_gram", 0)), (512, ("bjac_gram", 0))])
 def test_mixed_svd_exact_spectrum(G, chi, opt):
     """Standalone mixed SVD (svd_prec = 1) on U diag(s) V^T with s known:
