@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(kBjacThreads) k_bjac32g(float *__restrict__ X,
     constexpr int MT = (NV + 15) / 16, NT = NV / 8;     // Gram tiles of 16 x 8
     constexpr int WPT = NW / (MT * NT);                  // warps per Gram tile (k split)
     static_assert(NV >= 8 && WPT >= 1, "block width");
-    extern __shared__ float xs[];                        // [NV][ls]: vector q at xs + q ls
+    extern __shared__ __align__(16) float xs[];          // [NV][ls]: vector q at xs + q ls
     __shared__ int vid[NV];
     __shared__ float Gb[2][NV][NV + 1], Qb[2][NV][NV + 1];
     __shared__ float part[NW][16][8];
@@ -595,6 +595,7 @@ __global__ void __launch_bounds__(kBjacThreads) k_bjac32g(float *__restrict__ X,
     const int nbp = nb + (nb & 1);
     const int npairs = nbp / 2;
     const int nchunk = (l + 7) / 8;                      // positions in chunks of 8 (zero tail up to ls)
+    const bool vec4 = (l & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;   // rows 16-byte aligned
     unsigned *barrier = sync;
     unsigned *rotc = sync + 2;
     int sweep = 0;
@@ -632,11 +633,29 @@ __global__ void __launch_bounds__(kBjacThreads) k_bjac32g(float *__restrict__ X,
                 }
                 if (threadIdx.x == 0) pair_rot = 0;
                 __syncthreads();
-                for (int q = warp; q < NV; q += NW) {
-                    const int v = vid[q];
-                    float *dst = xs + (long long)q * ls;
-                    const float *src = X + (long long)(v < 0 ? 0 : v) * l;
-                    for (int e = lane; e < ls; e += 32) dst[e] = (v >= 0 && e < l) ? src[e] : 0.f;
+                if (vec4) {
+                    // every load of a thread issued before its stores: one L2
+                    // round trip per round instead of one per few elements
+                    const int l4 = l >> 2, ls4 = ls >> 2;
+                    float4 *xs4 = reinterpret_cast<float4 *>(xs);
+#pragma unroll 4
+                    for (int idx = threadIdx.x; idx < NV * l4; idx += kBjacThreads) {
+                        const int q = idx / l4, e4 = idx - q * l4;
+                        const int v = vid[q];
+                        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (v >= 0) val = reinterpret_cast<const float4 *>(X + (long long)v * l)[e4];
+                        xs4[q * ls4 + e4] = val;
+                    }
+                    const int tail = ls - l;
+                    for (int idx = threadIdx.x; idx < NV * tail; idx += kBjacThreads)
+                        xs[(idx / tail) * ls + l + idx % tail] = 0.f;
+                } else {
+                    for (int q = warp; q < NV; q += NW) {
+                        const int v = vid[q];
+                        float *dst = xs + (long long)q * ls;
+                        const float *src = X + (long long)(v < 0 ? 0 : v) * l;
+                        for (int e = lane; e < ls; e += 32) dst[e] = (v >= 0 && e < l) ? src[e] : 0.f;
+                    }
                 }
                 __syncthreads();
                 // 1. Gram matrix: warp w adds chunks w % WPT, + WPT, ... of tile w / WPT
