@@ -617,13 +617,13 @@ def run_ours(args):
         peak = 152 * 128 * 2 * mhz * 1e6 / 1e12 if dom != 2 else 1.25
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else 0.0
         # DRAM traffic: one ncu capture of the FP32 blocked Jacobi (Gram-form
-        # inner sweep, k_bjac32g<8>) on a 560 x 560 matrix read 1.155 MB and
-        # wrote 0.326 MB (the matrix once, plus the result; the sweeps run from
+        # inner sweep, k_bjac32g<8>) on a 560 x 560 matrix read 1.163 MB and
+        # wrote 0.332 MB (the matrix once, plus the result; the sweeps run from
         # shared memory and L2), scaled here to the mean matrix of the timed
         # launches by its algorithmic bytes
         traffic = None
         if dom == 1 and d["launches"] > 0:
-            traffic = 1.481e6 * (d["bytes"] / d["launches"]) / (8.0 * 560 * 560)
+            traffic = 1.495e6 * (d["bytes"] / d["launches"]) / (8.0 * 560 * 560)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_note": "ncu dram read+write of k_bjac32g<8> at n = 560, scaled by matrix size"
                 if traffic else None, "kernel": names[dom],
