@@ -46,7 +46,7 @@ WORKLOADS = {
 }
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--warmup-sweeps", type=int, default=2, help="--micro chains: untimed sweeps first")
     ap.add_argument("--tune-cache", default=os.path.join(ROOT, "autotune_cache.json"),
                     help="autotuner table (loaded if present, else tuned and written); '' to tune without saving")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def apply_opts(ctx, args):
@@ -406,6 +406,31 @@ def cpu_baseline(sweep_flops: float, budget_s: float = 12.0):
 
 
 # ---------------------------------------------------------------------------
+# Replicas across ranks (torchrun, one process per GPU): a single chain does
+# not shard, so every rank advances its own chain; the ranks meet only at the
+# barriers around the timed region and at the max-over-ranks of the times.
+def replica_seed(rank: int) -> int:
+    """Seed of the initial MPS of rank `rank`'s chain."""
+    import synth
+    return synth.workload_seed(2, rank)
+
+
+def sync_ranks(dist) -> None:
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -520,7 +545,7 @@ def run_ours(args):
                       max_sweeps=args.warmup + args.steps)
     W = ctx.build_mpo(G.XXZ, N, 1.0, wl["Delta"])
     # replicas only: each rank runs its own chain (seeded by rank)
-    m0 = torch.from_numpy(synth.initial_mps_entries(synth.workload_seed(2, rank), N, wl["chi_init"])).cuda()
+    m0 = torch.from_numpy(synth.initial_mps_entries(replica_seed(rank), N, wl["chi_init"])).cuda()
     st = G.State(ctx, W, m0, p, 1.0, wl["Delta"])
     for _ in range(args.warmup):
         st.sweep(1, visits=False)
@@ -528,8 +553,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    if dist:
-        dist.barrier()
+    sync_ranks(dist)
     torch.cuda.synchronize()
     l0 = G.launch_count()
     ctx.profile(True)
@@ -542,18 +566,13 @@ def run_ours(args):
         recs += r
     ev1.record(ctx.stream)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    sync_ranks(dist)
     l1 = G.launch_count()
     ms = ev0.elapsed_time(ev1)
     prof = {k: ctx.profile_read(k) for k in range(9)}
     ctx.profile(False)
     clk = clocks.stop()
-    per_sweep = ms / 1e3 / args.steps
-    if dist:
-        t = torch.tensor([per_sweep], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        per_sweep = float(t.item())
+    per_sweep = max_over_ranks(ms / 1e3 / args.steps, dist, "cuda")
     sweep_flops = sum(r.flops for r in recs) / len(recs)
     # end to end: MPS in pinned host memory -> device, sweep, MPS and records -> host
     e2e = None
@@ -561,8 +580,7 @@ def run_ours(args):
         host = torch.empty(st.mps_size(), dtype=torch.float64).pin_memory()
         st.get_mps(host)
         torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
+        sync_ranks(dist)
         t0 = time.perf_counter()
         h2d = d2h = 0
         e2e_steps = max(1, min(args.steps, 1))
@@ -577,11 +595,7 @@ def run_ours(args):
             st.get_mps(host[:n_out])
             d2h += 8 * n_out + (2 * N - 3) * 40
         torch.cuda.synchronize()
-        t_e2e = (time.perf_counter() - t0) / e2e_steps
-        if dist:
-            t = torch.tensor([t_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, "cuda")
         e2e = {"value": t_e2e, "unit": "s/sweep", "h2d_bytes_per_step": h2d // e2e_steps,
                "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
                "path": "MPS from pinned host memory -> dmrg_state_put_mps -> dmrg_sweep -> dmrg_state_get_mps + records"}
