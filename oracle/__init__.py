@@ -105,6 +105,8 @@ def lib():
             L.ref_ctrl_step.argtypes = [C.POINTER(CtrlState), C.c_double, C.POINTER(Params), C.POINTER(C.c_int)]
             L.ref_ctrl_replay.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(Params),
                                           C.POINTER(CtrlState), C.POINTER(C.c_int)]
+            L.ref_ctrl_step_real.argtypes = [C.POINTER(CtrlState), C.c_double, C.POINTER(Params),
+                                             C.POINTER(C.c_double)]
             L.ref_mlp_nparam.restype = C.c_int
             L.ref_mlp_forward.argtypes = [C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.ref_mlp_loss_grad.argtypes = [C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double),
@@ -202,6 +204,20 @@ def ctrl_replay(S_seq: np.ndarray, params: Params, chi0: int | None = None, stat
     out = np.zeros((T, B), dtype=np.int32)
     lib().ref_ctrl_replay(T, B, _dp(S_seq), C.byref(params), states, _ip(out))
     return out, states
+
+
+def ctrl_closed_loop_real(params: Params, g: float, S_star: float, chi_star: float, chi0: float,
+                          n_steps: int) -> np.ndarray:
+    """chi(0..n_steps) of one real-valued controller (rounding and clamp off)
+    driving the linear plant S(t) = S_star + g (chi(t) - chi_star)."""
+    st = CtrlState()
+    chi = C.c_double(chi0)
+    out = [chi0]
+    for _ in range(n_steps):
+        S = S_star + g * (chi.value - chi_star)
+        lib().ref_ctrl_step_real(C.byref(st), S, C.byref(params), C.byref(chi))
+        out.append(chi.value)
+    return np.array(out)
 
 
 def mlp_nparam() -> int:

@@ -530,7 +530,8 @@ static int clamp_int(double x, int lo, int hi)
     return (int)x;
 }
 
-int ref_ctrl_step(ref_ctrl_state *st, double S, const ref_params *p, int *chi_out)
+/* EMA (Eq. 8) and predictor (Eq. 16) of one visit; returns S-hat. */
+static double ctrl_filter(ref_ctrl_state *st, double S, const ref_params *p)
 {
     double a = p->alpha_ema;
     if (!st->initialized) {
@@ -553,6 +554,25 @@ int ref_ctrl_step(ref_ctrl_state *st, double S, const ref_params *p, int *chi_ou
     double Shat = st->Sbar + p->beta * (st->Sbar - st->Sbar_prev);
     if (p->second_order)
         Shat = Shat + p->beta * ((st->Sbar - 2.0 * st->Sbar_prev) + st->Sbar_prev2);
+    return Shat;
+}
+
+/* PID control signal before rounding (Algorithm 2, Eq. 10): error e (Eq. 9),
+ * integral update, derivative on e - e_prev.  Returns u; e in *e_out. */
+static double ctrl_pid_u(ref_ctrl_state *st, double Shat, const ref_params *p, double *e_out)
+{
+    double e = Shat - p->S_target;
+    if (!st->initialized) st->e_prev = e;
+    double P = p->Kp * e;
+    st->I = st->I + p->Ki * e;
+    double Dt = p->Kd * (e - st->e_prev);
+    *e_out = e;
+    return (P + st->I) + Dt;
+}
+
+int ref_ctrl_step(ref_ctrl_state *st, double S, const ref_params *p, int *chi_out)
+{
+    double Shat = ctrl_filter(st, S, p);
     int chi_new;
     if (p->ctrl == CTRL_DIRECT) {
         double tgt = ceil(p->gamma * exp(st->Sbar));
@@ -562,12 +582,8 @@ int ref_ctrl_step(ref_ctrl_state *st, double S, const ref_params *p, int *chi_ou
     } else if (p->ctrl == CTRL_THRESHOLD) {
         chi_new = p->chi_max;
     } else {
-        double e = Shat - p->S_target;
-        if (!st->initialized) st->e_prev = e;
-        double P = p->Kp * e;
-        st->I = st->I + p->Ki * e;
-        double Dt = p->Kd * (e - st->e_prev);
-        double u = (P + st->I) + Dt;
+        double e;
+        double u = ctrl_pid_u(st, Shat, p, &e);
         double delta = nearbyint(u);               /* FE_TONEAREST: half to even */
         double raw = (double)st->chi + delta;
         chi_new = clamp_int(raw, p->chi_min, p->chi_max);
@@ -577,6 +593,22 @@ int ref_ctrl_step(ref_ctrl_state *st, double S, const ref_params *p, int *chi_ou
     st->chi = chi_new;
     st->initialized = 1;
     *chi_out = chi_new;
+    return REF_OK;
+}
+
+/* The same EMA -> predictor -> PID step with rounding and clamping switched
+ * off (so anti-windup never fires) and chi carried as a real number in
+ * *chi_real: chi <- chi + u.  This is the linear loop that the stability
+ * analysis of Section 5 reasons about; it exists only to pin the filter and
+ * PID arithmetic above against the closed-form solution of that loop. */
+int ref_ctrl_step_real(ref_ctrl_state *st, double S, const ref_params *p, double *chi_real)
+{
+    double Shat = ctrl_filter(st, S, p);
+    double e;
+    double u = ctrl_pid_u(st, Shat, p, &e);
+    *chi_real = *chi_real + u;
+    st->e_prev = e;
+    st->initialized = 1;
     return REF_OK;
 }
 

@@ -231,3 +231,77 @@ def test_global_adaptive_chi_closed_form():
         mean = sum(last[b] for b in range(N - 1)) / (N - 1)
         g = int(min(max(g + round(mean - kw["S_target"]), chi_min), chi_max))
     assert g > chi_min                                    # the law did move chi
+
+
+# ---------------------------------------------------------------------------
+# Closed loop with rounding and clamping off (the linear loop that Section 5's
+# stability analysis reasons about).  Plant S(t) = S* + g (chi(t) - chi*),
+# target S_target = S*, so with x = chi - chi*:
+#   EMA (Eq. 8)        s(t) = alpha g x(t) + (1 - alpha) s(t-1)
+#   predictor (Eq. 16) e(t) = s(t) + beta (s(t) - s(t-1))
+#   PID (Algorithm 2)  u(t) = Kp e(t) + I(t) + Kd (e(t) - e(t-1)),
+#                      I(t) = I(t-1) + Ki e(t)
+#   update             x(t+1) = x(t) + u(t).
+# In z: (z - 1) X = C(z) F(z) g X with C = Kp + Ki z/(z-1) + Kd (z-1)/z and
+# F = alpha ((1+beta) z - beta) / (z - (1-alpha)); cleared of denominators,
+#   z (z-1)^2 (z-(1-alpha)) - g alpha ((1+beta) z - beta)
+#       [Kp z (z-1) + Ki z^2 + Kd (z-1)^2] = 0.
+# (Eqs. 14-15 omit the integrating update of chi, so the paper's quadratic is
+# not this loop's polynomial.)  The first visit's initialisation (S-bar = S,
+# S-bar_prev = S-bar, e_prev = e, I = Ki e) is the linear state extended
+# backwards, so the whole trajectory from t = 0 obeys the recurrence.
+
+
+def _char_poly(alpha, beta, Kp, Ki, Kd, g):
+    """Coefficients (highest power first) of the closed loop's polynomial."""
+    P_ = np.polynomial.polynomial
+    z = [0.0, 1.0]
+    zm1 = [-1.0, 1.0]
+    lhs = P_.polymul(P_.polymul(z, P_.polymul(zm1, zm1)), [-(1.0 - alpha), 1.0])
+    ctrl = P_.polyadd(P_.polyadd(Kp * P_.polymul(z, zm1), Ki * P_.polymul(z, z)), Kd * P_.polymul(zm1, zm1))
+    rhs = g * alpha * P_.polymul([-beta, 1.0 + beta], ctrl)
+    return P_.polysub(lhs, rhs)[::-1]
+
+
+@pytest.mark.parametrize("alpha,beta,g", [(0.3, 0.4, -0.2), (0.5, 0.8, -0.05), (0.3, 0.0, 0.02), (0.9, 0.4, -0.6)])
+def test_closed_loop_real_valued_obeys_characteristic_recurrence(alpha, beta, g):
+    Kp, Ki, Kd = 2.0, 0.1, 0.5
+    p = P(alpha_ema=alpha, beta=beta, Kp=Kp, Ki=Ki, Kd=Kd, S_target=1.3)
+    chi = O.ctrl_closed_loop_real(p, g, S_star=1.3, chi_star=100.0, chi0=40.0, n_steps=40)
+    x = chi - 100.0
+    c = _char_poly(alpha, beta, Kp, Ki, Kd, g)
+    assert len(c) == 5
+    scale = np.max(np.abs(x)) * np.sum(np.abs(c))
+    for t in range(len(x) - 4):
+        r = sum(c[k] * x[t + 4 - k] for k in range(5))
+        assert abs(r) <= 1e-13 * scale, (t, r)
+    # a plausible slip changes the polynomial and breaks the recurrence
+    wrong = _char_poly(alpha, beta, Kp, Ki, -Kd, g)
+    res = max(abs(sum(wrong[k] * x[t + 4 - k] for k in range(5))) for t in range(len(x) - 4))
+    assert res > 1e-6 * scale
+
+
+def test_closed_loop_pure_pid_closed_form():
+    """alpha = 1, beta = 0: the state is (x(t), I(t-1), e(t-1)) and the loop's
+    polynomial is the cubic z (z-1)^2 - g [Kp z(z-1) + Ki z^2 + Kd (z-1)^2]
+    = z^3 - (2 + g(Kp+Ki+Kd)) z^2 + (1 + g(Kp+2Kd)) z - g Kd.  So x(t) =
+    sum_i c_i r_i^t, with c fixed by x(0), x(1), x(2) worked out by hand from
+    the first visit's rules."""
+    Kp, Ki, Kd, g, x0 = 2.0, 0.1, 0.5, -0.3, -60.0
+    p = P(alpha_ema=1.0, beta=0.0, Kp=Kp, Ki=Ki, Kd=Kd, S_target=0.7)
+    chi = O.ctrl_closed_loop_real(p, g, S_star=0.7, chi_star=100.0, chi0=100.0 + x0, n_steps=40)
+    x = chi - 100.0
+    e0 = g * x0
+    I0 = Ki * e0
+    x1 = x0 + Kp * e0 + I0                    # e_prev = e on the first visit: no D term
+    e1 = g * x1
+    I1 = I0 + Ki * e1
+    x2 = x1 + Kp * e1 + I1 + Kd * (e1 - e0)
+    r = np.roots([1.0, -(2.0 + g * (Kp + Ki + Kd)), 1.0 + g * (Kp + 2.0 * Kd), -g * Kd])
+    V = np.vander(r, 3, increasing=True).T    # V[k][i] = r_i^k
+    c = np.linalg.solve(V, np.array([x0, x1, x2], dtype=complex))
+    t = np.arange(len(x))
+    closed = np.real((c[None, :] * r[None, :] ** t[:, None]).sum(axis=1))
+    assert np.max(np.abs(closed - x)) <= 1e-12 * np.max(np.abs(x))
+    # the loop settles (|r| < 1 for these gains), towards chi* = 100
+    assert np.max(np.abs(r)) < 1.0 and abs(x[-1]) < abs(x0)
