@@ -228,3 +228,47 @@ def test_lanczos_against_dense_eigensolve():
     # with 20 steps on a larger space the Ritz value is an upper bound
     E20, *_ = O.lanczos(L, W[2], W[3], R, theta, K=3)
     assert E20 >= ev[0] - 1e-12
+
+
+def _sturm_count(a, b, x):
+    """Eigenvalues of the symmetric tridiagonal (a diagonal, b off-diagonal)
+    below x: negative pivots of the LDL^T factorisation of T - x I."""
+    cnt, q = 0, 1.0
+    for i in range(len(a)):
+        q = (a[i] - x) - (b[i - 1] ** 2 / q if i > 0 else 0.0)
+        if q == 0.0:
+            q = 1e-300
+        cnt += q < 0.0
+    return cnt
+
+
+def _bisect_eig(a, b, k):
+    """k-th smallest eigenvalue by bisection on Sturm counts (Gershgorin start)."""
+    r = np.abs(np.r_[b, 0.0]) + np.abs(np.r_[0.0, b])
+    lo, hi = float(np.min(a - r)), float(np.max(a + r))
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if mid in (lo, hi):
+            break
+        if _sturm_count(a, b, mid) > k:
+            hi = mid
+        else:
+            lo = mid
+    return 0.5 * (lo + hi)
+
+
+def test_sym_eig_tridiagonal_against_sturm_bisection():
+    """The eigensolver that also solves the Lanczos tridiagonal matrix, on
+    T of the Lanczos sizes (K <= 20), against bisection on Sturm sequence
+    counts written out here (Golub-Van Loan 8.4.1): every eigenvalue to 1e-13
+    relative to |T|, including a glued pair of nearly equal ones."""
+    rng = np.random.default_rng(11)
+    for n in (1, 2, 7, 20):
+        a = rng.standard_normal(n)
+        b = rng.uniform(0.05, 1.0, n - 1)
+        if n == 20:
+            b[9] = 1e-9                                   # two nearly decoupled halves
+        T = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+        w, _ = O.sym_eig(T)
+        ref = np.array([_bisect_eig(a, b, k) for k in range(n)])
+        assert np.max(np.abs(np.sort(w) - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))

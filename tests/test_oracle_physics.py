@@ -1,5 +1,6 @@
 """Pins of the oracle's MPOs, exact diagonalisation and DMRG driver against
 values the paper prints, closed forms and independently built Hamiltonians."""
+import functools
 import json
 import os
 
@@ -14,6 +15,12 @@ GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_v
 SX = np.array([[0, 0.5], [0.5, 0]]); SZ = np.diag([0.5, -0.5]); SY2 = None
 SP = np.array([[0, 1.0], [0, 0]]); SM = SP.T.copy(); I2 = np.eye(2)
 PX = 2 * SX; PZ = 2 * SZ
+
+
+@functools.lru_cache(maxsize=None)
+def ed_heisenberg(N):
+    """Oracle ED ground energy of the open Heisenberg chain (J = Delta = 1), cached."""
+    return O.ed_ground(O.MODEL_XXZ, N, 1.0, 1.0)
 
 
 def kron_op(ops):
@@ -86,7 +93,7 @@ def test_majumdar_ghosh_dimer_energy():
 def test_paper_table4_heisenberg_N20():
     """Table 4: E/N = -1.73649 for the 20-site Heisenberg chain in the Pauli convention (= 4 E0/N)."""
     g = GOLD["heisenberg_N20_pauli_E_per_site"]
-    E0 = O.ed_ground(O.MODEL_XXZ, 20, 1.0, 1.0)
+    E0 = ed_heisenberg(20)
     assert round(4 * E0 / 20, g["decimals"]) == g["value"]
 
 
@@ -141,3 +148,19 @@ def test_dmrg_pid_is_variational_and_records_schedule():
     assert np.all(r["k"] <= r["chi"])
     # the first visit of every bond starts from chi_min plus the proportional/integral kick
     assert np.all(r["k"] >= 1)
+
+
+def test_bulk_energy_approaches_bethe_ansatz():
+    """Section 10: the spin-1/2 Heisenberg chain's energy per site tends to
+    1/4 - ln 2.  Differences of open-chain ground energies cancel the two
+    ends, e(N1, N2) = (E0(N2) - E0(N1)) / (N2 - N1); from the oracle's
+    exact diagonalisation at N = 12, 16, 20 they approach the Bethe value
+    from above, within 1e-3 at (16, 20) and closer than at (12, 16)."""
+    e_inf = GOLD["bethe_ansatz_E_per_site"]["value"]
+    assert abs(e_inf - (0.25 - np.log(2.0))) < 1e-15
+    E = {N: ed_heisenberg(N) for N in (12, 16, 20)}
+    e1 = (E[16] - E[12]) / 4.0
+    e2 = (E[20] - E[16]) / 4.0
+    assert e2 > e_inf and e1 > e_inf
+    assert abs(e2 - e_inf) < abs(e1 - e_inf)
+    assert abs(e2 - e_inf) < 1e-3
