@@ -325,7 +325,7 @@ def dmrg_run(W, mps_init, params: Params, n_sweeps: int, stop_on_conv: bool = Fa
     n = ret
     sl = slice(0, n * V)
     return dict(sweeps=n, E=E_sweep[:n], bond=rb[sl], E_visit=rE[sl], S=rS[sl], eps=reps[sl], k=rk[sl],
-                chi=rchi[sl], chi_final=chi_f, visits_per_sweep=V)
+                chi=rchi[sl], chi_final=chi_f, visits_per_sweep=V, norm=float(nrm[0]))
 
 
 def ed_ground(model: int, N: int, J=1.0, Delta=1.0, J2=0.0, n_up=None, max_iter=400) -> float:

@@ -120,6 +120,9 @@ def test_dmrg_reaches_ed_energy_N12():
     E0 = O.ed_ground(O.MODEL_XXZ, 12)
     assert abs(r["E"][-1] - E0) / 12 < 1e-10
     assert np.all(np.diff(r["E"]) <= 1e-12)          # variational, monotone at fixed cap
+    # after the closing right-to-left half-sweep site 0 is the orthogonality
+    # centre, so |A_0| = <psi|psi>^(1/2) = 1 (renormalised retained spectrum)
+    assert abs(r["norm"] - 1.0) < 1e-13
 
 
 def test_dmrg_xxz_and_j1j2_against_ed():
