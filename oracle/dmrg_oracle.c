@@ -1010,7 +1010,7 @@ static void mlp_features(const ref_ctrl_state *st, int bond, int N, int sweep, i
     x[9] = (double)sweep / (double)(max_sweeps > 0 ? max_sweeps : 1);
 }
 
-/* Bond dimension chosen by the MLP, with the PID as fallback and judge:
+/* Bond dimension chosen by the MLP, with the PID as fallback and arbiter:
  * chi = clamp(round(2^y), chi_min, chi_max); the PID choice is used if the
  * network output is not finite, or if the truncation error of the network's
  * chi exceeds 10x the PID's plus 1e-10.                                     */
