@@ -42,6 +42,38 @@ def test_svd_2x2_closed_form():
         assert np.allclose(s, ref, rtol=1e-14, atol=1e-15)
 
 
+def _sym3_eigvals(B):
+    """Eigenvalues of a symmetric 3 x 3 matrix in closed form (Smith, CACM
+    1961): with q = tr(B)/3, p^2 = |B - qI|_F^2 / 6 and r = det((B - qI)/p)/2,
+    they are q + 2p cos(phi + 2 pi j/3), phi = acos(r)/3."""
+    q = np.trace(B) / 3.0
+    p1 = B[0, 1] ** 2 + B[0, 2] ** 2 + B[1, 2] ** 2
+    p2 = (B[0, 0] - q) ** 2 + (B[1, 1] - q) ** 2 + (B[2, 2] - q) ** 2 + 2.0 * p1
+    p = np.sqrt(p2 / 6.0)
+    C = (B - q * np.eye(3)) / p
+    detC = (C[0, 0] * (C[1, 1] * C[2, 2] - C[1, 2] * C[2, 1]) - C[0, 1] * (C[1, 0] * C[2, 2] - C[1, 2] * C[2, 0])
+            + C[0, 2] * (C[1, 0] * C[2, 1] - C[1, 1] * C[2, 0]))
+    phi = np.arccos(np.clip(detC / 2.0, -1.0, 1.0)) / 3.0
+    e1 = q + 2.0 * p * np.cos(phi)
+    e3 = q + 2.0 * p * np.cos(phi + 2.0 * np.pi / 3.0)
+    return np.array([e1, 3.0 * q - e1 - e3, e3])
+
+
+def test_svd_3x3_closed_form():
+    """Squared singular values of a 3 x 3 matrix against the closed-form
+    eigenvalues of A^T A, descending.  Forming A^T A and the formula carry an
+    absolute error of a few eps |A|_F^2 per eigenvalue, so the comparison is
+    on s^2 with that bar (the square root would amplify it for small s)."""
+    eps = np.finfo(float).eps
+    for _ in range(20):
+        A = RNG.standard_normal((3, 3))
+        ref = _sym3_eigvals(A.T @ A)
+        U, s, Vt = O.svd(A)
+        assert np.all(np.abs(s ** 2 - ref) <= 50 * eps * np.sum(A * A))
+        assert np.all(np.diff(s) <= 0)
+        assert np.allclose((U * s) @ Vt, A, atol=1e-14)
+
+
 @pytest.mark.parametrize("kind", ["exp", "pow"])
 @pytest.mark.parametrize("chi", [8, 32])
 def test_svd_exact_spectrum(kind, chi):
