@@ -306,6 +306,27 @@ def peaks():
     return 6800.0, 1900.0, 1700.0, "fallback"
 
 
+def kernel_rates(prof: dict, names: dict, steps: int, hbm_gbs: float) -> dict:
+    """Per kernel kind of the live profile: device ms per step and the rates
+    of the work each kind counts (algorithmic flops and bytes per launch, see
+    dmrg_profile), with the HBM fraction of measured copy bandwidth for the
+    kinds that count bytes."""
+    out = {}
+    for k, d in sorted(prof.items()):
+        ms = d.get("ms", 0.0)
+        if ms <= 0.0:
+            continue
+        sec = ms / 1e3
+        e = {"ms_per_step": ms / max(1, steps), "launches_per_step": d.get("launches", 0) / max(1, steps)}
+        if d.get("flops", 0.0) > 0.0:
+            e["gflops"] = d["flops"] / sec / 1e9
+        if d.get("bytes", 0.0) > 0.0:
+            e["gbs"] = d["bytes"] / sec / 1e9
+            e["frac_hbm"] = e["gbs"] / hbm_gbs
+        out[names.get(k, str(k))] = e
+    return out
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -673,6 +694,7 @@ def run_ours(args):
                                     **{"other (splits, copies, small kernels, device idle)":
                                        per_sweep * 1e3 - sum(prof[k]["ms"] for k in prof) / args.steps}),
         "roofline": roof, "gpu_launches": l1 - l0, "clocks": clk,
+        "kernel_rates": kernel_rates(prof, names, args.steps, hbm),
     }
     if e2e:
         out["e2e"] = e2e
