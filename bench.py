@@ -34,15 +34,27 @@ sys.path.insert(0, ROOT)
 METRIC = "DMRG sweep s & SVD GFLOP/s, N=200 chi<=1024: mixed vs FP64 path at dE/N<=1e-8"
 
 WORKLOADS = {
-    # sweep_flops: algorithmic flops of one sweep at the bond dimensions the
-    # threshold rule (eps_trunc = 1e-10) reaches on this chain (mean chi ~200,
-    # max 281: the sweep record's own count after three warm-up sweeps); the
-    # CPU reference arm scales its measured oracle rate by it, as the GPU arm's
-    # cpu_baseline does with its own count
-    "xxz_n200_chi1024": dict(N=200, chi_max=1024, Delta=1.0, chi_init=16, model="XXZ (Delta=1, Heisenberg)",
-                             sweep_flops=8.12e12),
-    "xxz_n100_chi256": dict(N=100, chi_max=256, Delta=1.0, chi_init=16, model="XXZ (Delta=1, Heisenberg)"),
-    "xxz_n40_chi64": dict(N=40, chi_max=64, Delta=1.0, chi_init=8, model="XXZ (Delta=1, Heisenberg)"),
+    # The headline: Section 10's adaptive DMRG on the N = 200 Heisenberg chain
+    # with the per-bond PID controller under chi_max = 1024, from a random MPS
+    # at chi_init = chi_min = 4.  sweep_flops: algorithmic flops of one timed
+    # sweep on the realised bond dimensions (the sweep records' own count
+    # from a GPU run of the default command); the CPU reference arm scales its
+    # measured oracle rate by it, as the GPU arm's cpu_baseline does with its
+    # own count.  ref_chi: the bond dimension the oracle sample runs at (about
+    # the timed sweeps' mean retained chi).
+    "xxz_n200_chi1024": dict(N=200, chi_max=1024, Delta=1.0, chi_init=4, model="XXZ (Delta=1, Heisenberg)",
+                             ctrl="CTRL_PID", sweep_flops=2.0e11, ref_chi=32),
+    # the same chain under threshold truncation alone (labelled comparison)
+    "xxz_n200_chi1024_threshold": dict(N=200, chi_max=1024, Delta=1.0, chi_init=16,
+                                       model="XXZ (Delta=1, Heisenberg)", ctrl="CTRL_THRESHOLD"),
+    "xxz_n200_chi1024_d05": dict(N=200, chi_max=1024, Delta=0.5, chi_init=4, model="XXZ (Delta=0.5)",
+                                 ctrl="CTRL_PID"),
+    "xxz_n200_chi1024_d15": dict(N=200, chi_max=1024, Delta=1.5, chi_init=4, model="XXZ (Delta=1.5)",
+                                 ctrl="CTRL_PID"),
+    "xxz_n100_chi256": dict(N=100, chi_max=256, Delta=1.0, chi_init=4, model="XXZ (Delta=1, Heisenberg)",
+                            ctrl="CTRL_PID"),
+    "xxz_n40_chi64": dict(N=40, chi_max=64, Delta=1.0, chi_init=4, model="XXZ (Delta=1, Heisenberg)",
+                          ctrl="CTRL_PID"),
 }
 
 
@@ -71,8 +83,10 @@ def parse(argv=None):
     ap.add_argument("--chi-max", type=int, default=256, help="--micro chains: bond dimension cap")
     ap.add_argument("--seq", action="store_true", help="--micro chains: also time the chains one after another")
     ap.add_argument("--tune-svd", action="store_true", help="also autotune the Jacobi's grid per SVD size bucket")
-    ap.add_argument("--compare-fp64", action="store_true",
-                    help="also run the FP64 form on the same chain and sweeps (slow: FP64 is ~1.25 TFLOP/s here)")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the FP64 arm (same chain, controller and sweeps in the plain FP64 form)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the threshold-truncation comparison and the isolated SVDs")
     ap.add_argument("--opt", action="append", default=[],
                     help="context option name=value (repeatable), applied before the run")
     ap.add_argument("--no-qr", action="store_true", help="--micro svd / svd_batch: Jacobi without QR preconditioning")
@@ -418,12 +432,46 @@ def oracle_sample(budget_s: float = 12.0, chi: int = 48):
     return dict(seconds=dt, bonds=n, flops=fl, rate=fl / dt, chi=chi)
 
 
-def cpu_baseline(sweep_flops: float, budget_s: float = 12.0):
-    smp = oracle_sample(budget_s)
-    return {"value": sweep_flops / smp["rate"], "unit": "s/sweep", "cores": 1, "kind": "oracle",
-            "sample": (f"{smp['bonds']} oracle bond updates (20-step Lanczos, two-sided Jacobi SVD, entropy, "
-                       f"environment) at chi_l=chi_r={smp['chi']}, D=5 in {smp['seconds']:.1f} s single-threaded "
-                       f"({smp['rate'] / 1e9:.2f} GFLOP/s), scaled to the timed sweeps' algorithmic flops")}
+def _oracle_worker(args):
+    budget, chi = args
+    sys.path.insert(0, ROOT)
+    return oracle_sample(budget, chi)
+
+
+def oracle_all_cores(budget_s: float, chi: int):
+    """The oracle (single-threaded C) on every host core at once, one
+    independent sample per core in processes started with spawn: the host's
+    aggregate oracle rate (flops/s)."""
+    import multiprocessing as mp
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(budget_s, chi)] * cores)
+    return sum(r["rate"] for r in res), cores, sum(r["bonds"] for r in res)
+
+
+def oracle_chi(recs) -> int:
+    """Bond dimension of the oracle sample: the timed sweeps' mean retained chi."""
+    m = sum(r.mean_chi for r in recs) / max(1, len(recs))
+    return max(8, int(round(m)))
+
+
+def cpu_baseline(sweep_flops: float, chi: int = 48, budget_s: float = 12.0, all_cores: bool = True):
+    smp = oracle_sample(budget_s, chi)
+    out = {"value": sweep_flops / smp["rate"], "unit": "s/sweep", "cores": 1, "kind": "oracle",
+           "sample": (f"{smp['bonds']} oracle bond updates (20-step Lanczos, two-sided Jacobi SVD, entropy, "
+                      f"environment) at chi_l=chi_r={smp['chi']}, D=5 in {smp['seconds']:.1f} s single-threaded "
+                      f"({smp['rate'] / 1e9:.2f} GFLOP/s), scaled to the timed sweeps' algorithmic flops "
+                      f"({sweep_flops / 1e9:.1f} GFLOP per sweep)")}
+    if all_cores:
+        rate, cores, bonds = oracle_all_cores(budget_s / 2, chi)
+        out["all_cores"] = {"value": sweep_flops / rate, "unit": "s/sweep", "cores": cores,
+                            "sample": f"{bonds} oracle bond updates at chi={chi}, one independent sample per core "
+                                      f"for {budget_s / 2:.0f} s ({rate / 1e9:.2f} GFLOP/s aggregate): the rate "
+                                      f"of independent chains on all host cores (one chain's sweep is sequential)"}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -453,33 +501,47 @@ def max_over_ranks(x: float, dist, device) -> float:
 
 # ---------------------------------------------------------------------------
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands (no code exists
+    upstream).  Each step times oracle bond updates at the timed sweeps'
+    mean bond dimension for a bounded time and converts the measured rate to
+    seconds per sweep with the realised sweep's algorithmic flops."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
     N, cm = wl["N"], wl["chi_max"]
-    if "sweep_flops" in wl:
-        # the realised sweep's algorithmic flops (see WORKLOADS)
-        fl = wl["sweep_flops"]
-    else:
-        # no realised count recorded: the grown profile chi_i = min(chi_max, 2^i, 2^(N-i))
-        chi = [min(cm, 2 ** min(i, 60), 2 ** min(N - i, 60)) for i in range(N + 1)]
+    fl = wl.get("sweep_flops")
+    chi = wl.get("ref_chi", 32)
+    if fl is None:
+        # no realised count recorded: chi_i = min(ref_chi, 2^i, 2^(N-i)) on every bond
+        c = [min(chi, 2 ** min(i, 60), 2 ** min(N - i, 60)) for i in range(N + 1)]
         visits = list(range(N - 1)) + list(range(N - 3, -1, -1))
-        fl = sum(bond_flops(5, chi[k], chi[k + 1], chi[k + 2]) for k in visits)
-    times = []
-    per_step_budget = max(3.0, 60.0 / max(1, args.steps + args.warmup))
+        fl = sum(bond_flops(5, c[k], c[k + 1], c[k + 2]) for k in visits)
+    per_step_budget = max(2.0, 90.0 / max(1, args.steps + args.warmup))
+    walls, rates, bonds = [], [], 0
+    t_all = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        smp = oracle_sample(per_step_budget)
+        t0 = time.perf_counter()
+        smp = oracle_sample(per_step_budget, chi)
         if i >= args.warmup:
-            times.append(fl / smp["rate"])
-    v = sum(times) / len(times)
+            walls.append(time.perf_counter() - t0)
+            rates.append(smp["rate"])
+            bonds += smp["bonds"]
+    rate = sum(rates) / len(rates)
+    v = fl / rate
+    step_ms = 1e3 * sum(walls) / len(walls)
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/sweep", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "N": N, "chi_max": cm},
+           "measured": {"s_per_bond_update": 1.0 / (rate / bond_flops(5, chi, chi, chi)), "chi": chi,
+                        "bond_updates": bonds, "gflops": rate / 1e9, "wall_s": time.perf_counter() - t_all},
+           "value_note": (f"value = the realised sweep's {fl / 1e9:.1f} GFLOP at the measured oracle rate; "
+                          f"ms_per_step = the wall time of each step's bounded sample "
+                          f"({per_step_budget:.1f} s of oracle bond updates)"),
            "cpu_baseline": {"value": v, "unit": "s/sweep", "cores": 1, "kind": "oracle",
-                            "sample": f"per step: oracle bond updates at chi=48 for {per_step_budget:.0f} s, "
-                                      f"scaled by algorithmic flops to the full sweep ({fl / 1e12:.2f} TFLOP)"},
+                            "sample": f"per step: oracle bond updates at chi={chi} for {per_step_budget:.1f} s, "
+                                      f"single-threaded, scaled by algorithmic flops to the realised sweep"},
            "e2e": {"value": v, "unit": "s/sweep", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -515,30 +577,181 @@ def autotune(args, ctx, chi_max):
     return f"tuned {len(shapes)} GEMM" + (f" and {len(sizes)} SVD" if args.tune_svd else "") + " buckets"
 
 
-def fp64_path(args, G, synth, wl, E_mixed):
-    """The same chain, initial MPS and sweep count in the FP64 form: its sweep
-    time and the energy difference per site to the mixed form's last sweep."""
+PROF_NAMES = {0: "tcgen05 3xTF32 GEMM", 1: "FP32 Jacobi sweeps", 2: "FP64 Jacobi sweeps", 3: "FP64 GEMM",
+              4: "H_eff/environment mix", 5: "FP32 SIMT GEMM (small products)", 6: "QR preconditioning",
+              7: "Lanczos vector ops (two Gram-Schmidt passes)", 8: "entropy/controller/truncation decision"}
+
+
+def chain_params(G, wl, prec, total_sweeps, ctrl=None):
+    """Parameters of the workload's chain: the PID of Algorithm 2 (Eqs. 8,
+    10-11, 16) with the library defaults (K_p=2, K_i=0.1, K_d=0.5, beta=0.4,
+    S_target=0.36, alpha=0.3, chi_min=4), the eps_trunc=1e-10 threshold,
+    chi <= chi_max."""
+    ctrl = wl["ctrl"] if ctrl is None else ctrl
+    return G.make_params(chi_max=wl["chi_max"], chi_init=wl["chi_init"], ctrl=getattr(G, ctrl), prec=prec,
+                         eps_trunc=1e-10, max_sweeps=total_sweeps)
+
+
+def new_chain(G, synth, ctx, wl, p, seed):
     import torch
+    W = ctx.build_mpo(G.XXZ, wl["N"], 1.0, wl["Delta"])
+    m0 = torch.from_numpy(synth.initial_mps_entries(seed, wl["N"], wl["chi_init"])).cuda()
+    return G.State(ctx, W, m0, p, 1.0, wl["Delta"])
+
+
+def timed_sweeps(st, ctx, steps, dom=None):
+    """`steps` sweeps between CUDA events on the context stream.  With `dom`
+    set, the launches of that profiler kind (and only those) are bracketed by
+    events too, for the dominant kernel's live launch times."""
+    import torch
+    if dom is not None:
+        ctx.set_option("prof_mask", 1 << dom)
+        ctx.profile(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(ctx.stream)
+    recs, vis = [], []
+    for _ in range(steps):
+        r, v = st.sweep(1, visits=True)
+        recs += r
+        vis += v
+    ev1.record(ctx.stream)
+    torch.cuda.synchronize()
+    prof = None
+    if dom is not None:
+        prof = ctx.profile_read(dom)
+        ctx.profile(False)
+        ctx.set_option("prof_mask", (1 << len(PROF_NAMES)) - 1)
+    return ev0.elapsed_time(ev1), recs, vis, prof
+
+
+def profiled_sweep(st, ctx):
+    """One sweep with every profiler kind bracketed: the per-kind breakdown."""
+    import torch
+    ctx.set_option("prof_mask", (1 << len(PROF_NAMES)) - 1)
+    ctx.profile(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(ctx.stream)
+    r, _ = st.sweep(1, visits=False)
+    ev1.record(ctx.stream)
+    torch.cuda.synchronize()
+    prof = {k: ctx.profile_read(k) for k in PROF_NAMES}
+    ctx.profile(False)
+    return ev0.elapsed_time(ev1), r[0], prof
+
+
+def fp64_path(args, G, synth, wl, E_mixed, mixed_s_per_sweep, seed):
+    """The plain FP64 GPU path on the same chain, initial MPS, controller and
+    sweep count as the mixed headline: its sweep time over the same timed
+    sweeps, its energy, and |E_mixed - E_fp64| / N after the last sweep."""
     N = wl["N"]
     ctx = G.Context(0)
-    p = G.make_params(chi_max=wl["chi_max"], chi_init=wl["chi_init"], ctrl=G.CTRL_THRESHOLD, prec=G.PREC_FP64,
-                      eps_trunc=1e-10, max_sweeps=args.warmup + args.steps)
-    W = ctx.build_mpo(G.XXZ, N, 1.0, wl["Delta"])
-    m0 = torch.from_numpy(synth.initial_mps_entries(synth.workload_seed(2, 0), N, wl["chi_init"])).cuda()
-    st = G.State(ctx, W, m0, p, 1.0, wl["Delta"])
-    for _ in range(args.warmup):
+    total = args.warmup + 1 + args.steps
+    p = chain_params(G, wl, G.PREC_FP64, total)
+    st = new_chain(G, synth, ctx, wl, p, seed)
+    t0 = time.perf_counter()
+    for _ in range(args.warmup + 1):
         st.sweep(1, visits=False)
-    recs = []
-    for _ in range(args.steps):
-        r, _ = st.sweep(1, visits=False)
-        recs += r
-    out = {"s_per_sweep": sum(r.seconds for r in recs) / len(recs), "energy_per_site": recs[-1].E / N,
-           "dE_per_site_vs_mixed": abs(recs[-1].E - E_mixed) / N, "mean_chi": sum(r.mean_chi for r in recs) / len(recs),
-           "sweeps": args.warmup + args.steps}
-    out["speedup_mixed_vs_fp64"] = None
+    ms, recs, vis, _ = timed_sweeps(st, ctx, args.steps)
+    s64 = ms / 1e3 / args.steps
+    out = {"s_per_sweep": s64, "energy_per_site": recs[-1].E / N, "dE_per_site_vs_mixed": abs(recs[-1].E - E_mixed) / N,
+           "mean_chi": sum(r.mean_chi for r in recs) / len(recs), "max_chi": max(r.max_chi for r in recs),
+           "sweeps": total, "speedup_mixed_vs_fp64": s64 / mixed_s_per_sweep,
+           "wall_s": time.perf_counter() - t0,
+           "note": "same chain, initial MPS, PID controller and sweep count as the mixed run; timed over the same "
+                   "sweeps (the last --steps); FP64 everywhere (DFMA contractions, FP64 Jacobi)"}
+    st.close()
+    ctx.close()
+    return out, [v.chi_ctrl for v in vis]
+
+
+def threshold_comparison(args, G, synth):
+    """Labelled comparison: the same N = 200 chain under threshold truncation
+    alone (eps_trunc = 1e-10 under chi_max, the standard rule that Section 10's
+    controller replaces), mixed form, grown from chi_init = 16 over 3 sweeps,
+    then one sweep timed with every profiler kind bracketed."""
+    wl = WORKLOADS["xxz_n200_chi1024_threshold"]
+    ctx = G.Context(0)
+    p = chain_params(G, wl, G.PREC_3XTF32, 4)
+    st = new_chain(G, synth, ctx, wl, p, synth.workload_seed(2, 0))
+    for _ in range(3):
+        st.sweep(1, visits=False)
+    ms, rec, prof = profiled_sweep(st, ctx)
+    out = {"s_per_sweep": ms / 1e3, "energy_per_site": rec.E / wl["N"], "mean_chi": rec.mean_chi,
+           "max_chi": rec.max_chi, "sweep_gflops": rec.flops / (ms / 1e3) / 1e9,
+           "kernel_ms_per_sweep": {PROF_NAMES[k]: prof[k]["ms"] for k in prof},
+           "note": "threshold truncation only (no controller), chi_init 16, sweep 4 with per-launch events on"}
     st.close()
     ctx.close()
     return out
+
+
+def isolated_svd(G, synth, chis=(256, 1024), fp64_chis=(256,), reps=3):
+    """Config-2 isolated SVDs (2chi x 2chi, Haar factors, s_k = exp(-k/(0.1 chi))):
+    ms per call and nominal GFLOP/s (21 n^3) for the mixed and FP64 forms."""
+    import torch
+    out = {}
+    for form, cs in (("mixed", chis), ("fp64", fp64_chis)):
+        for chi in cs:
+            ctx = G.Context(0)
+            ctx.set_option("svd_prec", 1 if form == "mixed" else 0)
+            n = 2 * chi
+            A = torch.from_numpy(synth.svd_test_matrix(synth.workload_seed(1, chi), n, n,
+                                                       synth.spectrum("exp", n, chi))).cuda()
+            ctx.svd_truncate(A, chi, 1e-10)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(ctx.stream)
+            for _ in range(reps):
+                ctx.svd_truncate(A, chi, 1e-10)
+            ev1.record(ctx.stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / reps
+            out[f"{form}_chi{chi}"] = {"ms": ms, "gflops_nominal": 21.0 * n ** 3 / (ms / 1e3) / 1e9}
+            ctx.close()
+    return out
+
+
+def roofline(prof_dom, dom, clk, num_sms):
+    hbm, bf16, bf16_sus, src = peaks()
+    d = prof_dom
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    if d["ms"] <= 0 or d["launches"] <= 0:
+        return None
+    sec = d["ms"] / 1e3
+    if dom == 0:
+        tf32_peak = bf16_sus * (1.1 / 2.25)   # tf32 dense nominal / bf16 dense nominal, sustained (long step)
+        achieved = d["flops"] / sec / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                "frac": achieved / tf32_peak, "traffic": None,
+                "peak_note": "sustained bf16 of measured x 1.1/2.25 (nominal dense tf32/bf16 ratio)"}
+    elif dom in (4, 7):
+        achieved = d["bytes"] / sec / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "peak_note": "measured copy bandwidth",
+                "work_note": "8 B per input and output channel element" if dom == 4 else "8 B per vector element pass"}
+    elif dom in (1, 5, 6, 8):
+        # FP32 SIMT/latency-class kernels: nominal work against the FP32 ALU
+        # peak from unit counts (SMs of this device x 128 lanes x 2 flops x
+        # the median SM clock sampled during the timed region)
+        peak = num_sms * 128 * 2 * mhz * 1e6 / 1e12
+        achieved = d["flops"] / sec / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "peak_note": "FP32: %d SMs x 128 lanes x 2 flops x median SM clock %.0f MHz" % (num_sms, mhz),
+                "hbm_view_gbs": d["bytes"] / sec / 1e9}
+    else:
+        # FP64 kernels: the nominal FP64 rate scaled to the sampled clock
+        peak = 1.25 * mhz / 2070.0 * num_sms / 152.0
+        achieved = d["flops"] / sec / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_note": "FP64 nominal 1.25 TFLOP/s at 2070 MHz on 152 SMs, scaled to the "
+                                              "sampled clock and this device's SM count"}
+    roof["kernel"] = PROF_NAMES[dom]
+    roof["launches"] = d["launches"]
+    roof["avg_launch_us"] = d["ms"] * 1e3 / d["launches"]
+    roof["peak_source"] = src
+    return roof
 
 
 def run_ours(args):
@@ -562,14 +775,17 @@ def run_ours(args):
     ctx = G.Context(local)
     apply_opts(ctx, args)
     tuned = autotune(args, ctx, chi_max) if args.prec == "mixed" else "off (FP64 form)"
-    p = G.make_params(chi_max=chi_max, chi_init=wl["chi_init"], ctrl=G.CTRL_THRESHOLD, prec=prec, eps_trunc=1e-10,
-                      max_sweeps=args.warmup + args.steps)
-    W = ctx.build_mpo(G.XXZ, N, 1.0, wl["Delta"])
+    total = args.warmup + 1 + args.steps
+    p = chain_params(G, wl, prec, total)
     # replicas only: each rank runs its own chain (seeded by rank)
-    m0 = torch.from_numpy(synth.initial_mps_entries(replica_seed(rank), N, wl["chi_init"])).cuda()
-    st = G.State(ctx, W, m0, p, 1.0, wl["Delta"])
+    seed = replica_seed(rank)
+    st = new_chain(G, synth, ctx, wl, p, seed)
     for _ in range(args.warmup):
         st.sweep(1, visits=False)
+    # one sweep with every kernel kind bracketed: the breakdown, and the
+    # dominant kind, whose launches alone are bracketed in the timed region
+    prof_ms, prof_rec, prof = profiled_sweep(st, ctx)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
@@ -577,24 +793,13 @@ def run_ours(args):
     sync_ranks(dist)
     torch.cuda.synchronize()
     l0 = G.launch_count()
-    ctx.profile(True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(ctx.stream)
-    recs = []
-    for _ in range(args.steps):
-        r, vis = st.sweep(1, visits=True)
-        recs += r
-    ev1.record(ctx.stream)
-    torch.cuda.synchronize()
+    ms, recs, vis, prof_dom = timed_sweeps(st, ctx, args.steps, dom)
     sync_ranks(dist)
     l1 = G.launch_count()
-    ms = ev0.elapsed_time(ev1)
-    prof = {k: ctx.profile_read(k) for k in range(9)}
-    ctx.profile(False)
     clk = clocks.stop()
     per_sweep = max_over_ranks(ms / 1e3 / args.steps, dist, "cuda")
     sweep_flops = sum(r.flops for r in recs) / len(recs)
+    E_mixed = recs[-1].E
     # end to end: MPS in pinned host memory -> device, sweep, MPS and records -> host
     e2e = None
     if not args.no_e2e:
@@ -604,7 +809,7 @@ def run_ours(args):
         sync_ranks(dist)
         t0 = time.perf_counter()
         h2d = d2h = 0
-        e2e_steps = max(1, min(args.steps, 1))
+        e2e_steps = 1
         for _ in range(e2e_steps):
             n_in = st.mps_size()
             st.put_mps(host[:n_in])
@@ -620,92 +825,51 @@ def run_ours(args):
         e2e = {"value": t_e2e, "unit": "s/sweep", "h2d_bytes_per_step": h2d // e2e_steps,
                "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
                "path": "MPS from pinned host memory -> dmrg_state_put_mps -> dmrg_sweep -> dmrg_state_get_mps + records"}
+    st.close()
+    ctx.close()
     if rank != 0:
-        st.close(); ctx.close()
         return
-    hbm, bf16, bf16_sus, src = peaks()
-    # dominant kernel: the one with the largest live device time
-    names = {0: "tcgen05 3xTF32 GEMM", 1: "FP32 Jacobi sweeps", 2: "FP64 Jacobi sweeps", 3: "FP64 GEMM",
-             4: "H_eff/environment mix", 5: "FP32 SIMT GEMM (small products)", 6: "QR preconditioning",
-             7: "Lanczos vector ops (two Gram-Schmidt passes)", 8: "entropy/controller/truncation decision"}
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    d = prof[dom]
-    total_ms = ms
-    if dom == 0:
-        tf32_peak = bf16_sus * (1.1 / 2.25)   # tf32 dense nominal / bf16 dense nominal, sustained (long step)
-        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else 0.0
-        roof = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                "frac": achieved / tf32_peak, "traffic": None, "kernel": names[dom],
-                "peak_note": "sustained bf16 of measured x 1.1/2.25 (nominal tf32/bf16 dense ratio)"}
-    elif dom in (4, 7):
-        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": names[dom],
-                "work_note": "8 B per input and output channel element" if dom == 4 else "8 B per vector element pass"}
-    elif dom in (1, 2, 5, 6, 8):
-        # The Jacobi sweeps are ALU/latency-class: rotations of vectors held in
-        # shared memory or L2, with a barrier per round; their DRAM traffic is
-        # the input and the result only.  Peak from unit counts and clocks:
-        # FP32 152 SMs x 128 lanes x 2 flops x SM clock (median under load),
-        # FP64 the nominal 1.25 TFLOP/s.  Work: the nominal full-SVD count.
-        mhz = (clk or {}).get("sm_mhz") or 2070.0
-        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12 if dom != 2 else 1.25
-        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else 0.0
-        # DRAM traffic: one ncu capture of the FP32 blocked Jacobi (Gram-form
-        # inner sweep, k_bjac32g<8>) on a 560 x 560 matrix read 1.163 MB and
-        # wrote 0.332 MB (the matrix once, plus the result; the sweeps run from
-        # shared memory and L2), scaled here to the mean matrix of the timed
-        # launches by its algorithmic bytes
-        traffic = None
-        if dom == 1 and d["launches"] > 0:
-            traffic = 1.495e6 * (d["bytes"] / d["launches"]) / (8.0 * 560 * 560)
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_note": "ncu dram read+write of k_bjac32g<8> at n = 560, scaled by matrix size"
-                if traffic else None, "kernel": names[dom],
-                "peak_note": ("FP32: 152 SMs x 128 lanes x 2 flops x median SM clock %.0f MHz" % mhz) if dom != 2
-                else "FP64 nominal 1.25 TFLOP/s",
-                "work_note": "nominal SVD count 4m^2n + 8mn^2 + 9n^3 per call",
-                "hbm_view_gbs": d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0}
-    else:
-        fp64_peak = 1.25
-        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else 0.0
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None, "kernel": names[dom]}
-    roof["share_of_step"] = d["ms"] / total_ms if total_ms > 0 else None
-    roof["launches"] = d["launches"]
-    roof["peak_source"] = src
-    svd_kind = 1 if prec == G.PREC_3XTF32 else 2
-    svd = prof[svd_kind]
+    num_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    roof = roofline(prof_dom, dom, clk, num_sms)
+    if roof is not None:
+        roof["share_of_step"] = prof_dom["ms"] / ms if ms > 0 else None
     out = {
         "metric": METRIC, "value": per_sweep, "unit": "s/sweep", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_sweep * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "tf32x3+f32+f64" if prec == G.PREC_3XTF32 else "f64", "data": "synthetic",
         "config": {"workload": args.workload + ("_mixed" if prec == G.PREC_3XTF32 else "_fp64"), "N": N,
                    "chi_max": chi_max, "model": wl["model"], "d": 2, "D": 5, "lanczos_steps": 20,
-                   "truncation": "per-bond threshold eps_trunc=1e-10 capped at chi_max",
-                   "chi_init": wl["chi_init"], "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (MPS + environments of several GB)", "autotune": tuned},
-        "svd_gflops": (svd["flops"] / (svd["ms"] / 1e3) / 1e9) if svd["ms"] > 0 else None,
-        "svd_note": "nominal full-SVD count 4m^2n+8mn^2+9n^3 over the Jacobi sweep kernels' device time",
-        "sweep_gflops": sweep_flops / per_sweep / 1e9,
-        "energy_per_site": recs[-1].E / N, "mean_chi": sum(r.mean_chi for r in recs) / len(recs),
+                   "truncation": "per-bond PID (Algorithm 2 with the EMA of Eq. 8 and the predictor of Eq. 16; "
+                                 "Kp=2, Ki=0.1, Kd=0.5, beta=0.4, alpha=0.3, S_target=0.36, chi_min=4) "
+                                 "with the eps_trunc=1e-10 threshold, chi <= chi_max",
+                   "chi_init": wl["chi_init"], "sweeps_before_timed": args.warmup + 1,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (MPS + environments + workspace sized for chi_max, several GB)",
+                   "autotune": tuned},
+        "energy_per_site": E_mixed / N, "mean_chi": sum(r.mean_chi for r in recs) / len(recs),
         "max_chi": max(r.max_chi for r in recs),
-        "kernel_ms_per_sweep": dict({names[k]: prof[k]["ms"] / args.steps for k in prof},
+        "sweep_gflops": sweep_flops / per_sweep / 1e9,
+        "kernel_ms_per_sweep": dict({PROF_NAMES[k]: prof[k]["ms"] for k in prof},
                                     **{"other (splits, copies, small kernels, device idle)":
-                                       per_sweep * 1e3 - sum(prof[k]["ms"] for k in prof) / args.steps}),
+                                       prof_ms - sum(prof[k]["ms"] for k in prof)}),
+        "kernel_profile_note": "from one sweep with every kind bracketed by events, run right before the timed "
+                               "sweeps; the timed sweeps bracket only the dominant kind",
         "roofline": roof, "gpu_launches": l1 - l0, "clocks": clk,
-        "kernel_rates": kernel_rates(prof, names, args.steps, hbm),
+        "kernel_rates": kernel_rates(prof, PROF_NAMES, 1, peaks()[0]),
     }
     if e2e:
         out["e2e"] = e2e
     if not args.no_cpu:
-        out["cpu_baseline"] = cpu_baseline(sweep_flops)
-    if args.compare_fp64:
-        out["fp64_path"] = fp64_path(args, G, synth, wl, recs[-1].E)
-        out["fp64_path"]["speedup_mixed_vs_fp64"] = out["fp64_path"]["s_per_sweep"] / per_sweep
+        out["cpu_baseline"] = cpu_baseline(sweep_flops, chi=oracle_chi(recs))
+    if prec == G.PREC_3XTF32 and not args.no_fp64:
+        f64, chi64 = fp64_path(args, G, synth, wl, E_mixed, per_sweep, seed)
+        f64["chi_schedule_agreement"] = float(sum(a == b for a, b in zip(chi64, [v.chi_ctrl for v in vis]))
+                                              / max(1, len(chi64)))
+        out["fp64_path"] = f64
+    if prec == G.PREC_3XTF32 and not args.no_compare:
+        out["threshold_comparison"] = threshold_comparison(args, G, synth)
+        out["isolated_svd"] = isolated_svd(G, synth)
     print(json.dumps(out))
-    st.close()
-    ctx.close()
 
 
 def main():

@@ -57,8 +57,11 @@ typedef enum { DMRG_XXZ = 0, DMRG_J1J2 = 1, DMRG_TFIM = 2 } dmrg_model;
 
 typedef enum {
     DMRG_PREC_FP64 = 0,    /* every contraction in FP64                                  */
-    DMRG_PREC_3XTF32 = 1,  /* H_eff / environment / theta contractions as 3xTF32 tcgen05
-                              GEMMs with FP32 accumulation; Lanczos, SVD, entropy in FP64 */
+    DMRG_PREC_3XTF32 = 1,  /* theta and H_eff contractions as 3xTF32 tcgen05 GEMMs with
+                              FP32 accumulation; environment updates in FP64 (option
+                              "mixed_env_tc" moves them to the tensor cores); SVD as an
+                              FP32 Jacobi whose retained isometry is re-orthonormalised
+                              in FP64; Lanczos vectors, tridiagonal solve and entropy FP64 */
     DMRG_PREC_BF16X3 = 2   /* reserved: split-BF16 contractions                           */
 } dmrg_precision;
 
@@ -154,7 +157,9 @@ const char *dmrg_status_string(dmrg_status s);
 /* Tuning knobs of a context (no counterpart in the paper): "tc_force" (1: use
  * the tensor cores even for tiny products), "tc_min_work" (multiply-adds
  * below which 3xTF32 requests run on the FP64 kernel), "tc_bn" (0, 128 or
- * 256: tile width of the tensor-core GEMM, 0 = heuristic),
+ * 256: tile width of the tensor-core GEMM, 0 = heuristic), "prof_mask"
+ * (bit k set: dmrg_profile brackets the launches of kind k; default all 9
+ * kinds; bracketing one kind keeps the events off every other launch),
  * "mlp_eps_target" (truncation-error target of the k_star label, 1e-5),
  * "mixed_env_tc" (1: environment updates of the 3xTF32 form on the tensor
  * cores instead of FP64), "svd_prec" (standalone svd_truncate: 0 FP64 Jacobi,
@@ -248,11 +253,18 @@ dmrg_status svd_truncate(dmrg_ctx *ctx, const double *theta_dev, int m, int n, i
  * device array of about 1.06 MiB (1088 KiB reserved) that every GPU which
  * loads the library holds until the process exits.
  *  - The first call on a device looks up that array's device address with
- *    that device current; make this first call before any stream capture.
+ *    that device current (with CUDA's lazy module loading this lookup also
+ *    loads the library's device code, which creates the array), so only the
+ *    calls after the first are free of any device-memory growth; make this
+ *    first call before any stream capture.
  *  - Every call on a device shares the one array, and it keeps the last
  *    call's contents (the call clears what must start at zero).  Calls that
  *    overlap on the GPU (other streams, other threads, other contexts on the
  *    same device) race on it: serialise them.
+ *  - The SVD is always the FP64 Jacobi of svd_truncate's default form,
+ *    whatever the context's "svd_prec" option says.
+ *  - The call synchronises the context's stream before it returns (it reads
+ *    k, S and the truncation error back to the host).
  *  - Sizes above 256 return DMRG_EINVAL with a message on stderr. */
 dmrg_status svd_truncate_noalloc(dmrg_ctx *ctx, const double *theta_dev, int m, int n, int chi_max, double eps,
                                  double *U_dev, double *s_dev, double *Vt_dev, int *k_out, double *S_out,

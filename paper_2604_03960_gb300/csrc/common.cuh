@@ -114,6 +114,7 @@ struct dmrg_ctx {
     int tc_force = 0;            // use the tensor cores even for tiny products
     double tc_min_work = 4194304.0;   // M*N*K below which the FP64 kernel is used
     int prof = 0;
+    int prof_mask = 0x1ff;       // kinds bracketed by events while profiling (bit k = kind k)
     dmrg::ProfSlot prof_slot[dmrg::PROF_KINDS];
     int mixed_env_tc = 0;        // 1: environment updates of the mixed form on the tensor cores too
     int svd_prec = 0;            // standalone svd_truncate: 0 FP64 Jacobi, 1 mixed
@@ -143,7 +144,7 @@ struct dmrg_ctx {
 namespace dmrg {
 inline void prof_mark(dmrg_ctx *ctx, int kind)
 {
-    if (!ctx || !ctx->prof) return;
+    if (!ctx || !ctx->prof || !((ctx->prof_mask >> kind) & 1)) return;
     ProfSlot &p = ctx->prof_slot[kind];
     if (p.used == p.ev.size()) {
         cudaEvent_t e;
@@ -154,7 +155,7 @@ inline void prof_mark(dmrg_ctx *ctx, int kind)
 }
 inline void prof_count(dmrg_ctx *ctx, int kind, double flops, double bytes)
 {
-    if (!ctx || !ctx->prof) return;
+    if (!ctx || !ctx->prof || !((ctx->prof_mask >> kind) & 1)) return;
     ProfSlot &p = ctx->prof_slot[kind];
     p.n++;
     p.flops += flops;

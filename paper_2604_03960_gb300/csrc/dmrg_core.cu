@@ -596,6 +596,12 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         ctx->svd_prec = (int)value;
         return DMRG_OK;
     }
+    if (!std::strcmp(name, "prof_mask")) {
+        if (!(value >= 1.0 && value <= (double)((1 << PROF_KINDS) - 1)) || value != (double)(int)value)
+            return DMRG_EINVAL;
+        ctx->prof_mask = (int)value;
+        return DMRG_OK;
+    }
     if (!std::strcmp(name, "jacobi_max_sweeps")) {
         if (!(value >= 1.0 && value <= 1000.0)) return DMRG_EINVAL;
         ctx->jacobi_max_sweeps = (int)value;

@@ -65,16 +65,23 @@ def test_mixed_energy_matches_fp64_and_ed(G, ctx, N, chi_max, gbj):
     ctx.set_option("gbj_min_r", 0)
 
 
-def test_mixed_pid_schedule_close_to_fp64(G, ctx):
-    """Same controller on both forms: the integer schedules agree except at
-    near-ties of the rounded PID output."""
+def test_mixed_pid_schedule_matches_fp64(G, ctx):
+    """The paper's controller (Algorithm 2 with Eqs. 8, 16) live on both forms,
+    20-site chain, 4 sweeps: the mixed form takes the same integer chi at
+    every visit as the FP64 form (its entropies differ by far less than the
+    distance of the PID output from a rounding tie) and the same energy to
+    the mixed forms' bar of 1e-8 per site."""
     kw = dict(ctrl=G.CTRL_PID, chi_max=32, chi_init=4)
     st64, r64, v64 = run(G, ctx, 20, 4, G.PREC_FP64, **kw)
     stm, rm, vm = run(G, ctx, 20, 4, G.PREC_3XTF32, **kw)
     chi64 = np.array([v.chi_ctrl for v in v64])
     chim = np.array([v.chi_ctrl for v in vm])
-    assert np.mean(chi64 == chim) >= 0.95
-    assert abs(rm[-1].E - r64[-1].E) / 20 <= 1e-6
+    assert len(set(chi64.tolist())) > 2          # the controller moves
+    assert np.array_equal(chi64, chim)
+    assert np.array_equal(np.array([v.k for v in v64]), np.array([v.k for v in vm]))
+    assert np.max(np.abs(np.array([v.S for v in v64]) - np.array([v.S for v in vm]))) <= 1e-5
+    for a, b in zip(r64, rm):
+        assert abs(a.E - b.E) / 20 <= 1e-8
     st64.close(); stm.close()
 
 

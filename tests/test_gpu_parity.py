@@ -323,3 +323,57 @@ def test_table4_fixed_chi_energy(G, ctx, prec):
     recs, _ = st.sweep(5)
     st.close()
     assert abs(4 * recs[-1].E / N - ref["value"]) <= 0.5 * 10.0 ** -ref["decimals"]
+
+
+def test_table4_pid_row(G, ctx):
+    """Table 4's PID row in its setting (20-site Heisenberg chain, chi_max = 64,
+    5 sweeps) with the library's default target S_target = 0.36: the GPU run
+    equals the oracle's (same integer schedule, energies to 1e-10 per site)
+    and ends at the table's mean bond dimension 7.6 (within 0.25)."""
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    N = 20
+    kw = dict(ctrl=G.CTRL_PID, chi_max=64, chi_init=4, max_sweeps=5)
+    W = O.mpo(O.MODEL_XXZ, N, 1.0, 1.0)
+    m0 = synth.initial_mps_entries(synth.workload_seed(1, 20), N, 4)
+    ref = O.dmrg_run(W, m0, O.make_params(**kw), 5)
+    st = G.State(ctx, dev(W), dev(m0), G.make_params(**kw), 1.0, 1.0)
+    recs, vis = st.sweep(5)
+    st.close()
+    assert np.array_equal(np.array([v.chi_ctrl for v in vis]), ref["chi"])
+    assert np.array_equal(np.array([v.k for v in vis]), ref["k"])
+    assert np.all(np.abs(np.array([r.E for r in recs]) - ref["E"]) / N <= 1e-10)
+    V = 2 * N - 3
+    assert abs(np.mean([v.k for v in vis[-V:]]) - gold["table4_pid_mean_chi"]["value"]) <= 0.25
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("h", [1.0, 0.2])
+def test_tfim_sweep_against_free_fermions(G, ctx, prec, h):
+    """Transverse-field Ising chain (Table 5's 'Ising critical' h = J = 1 and
+    'Ising ordered' h = 0.2), N = 20 open chain, threshold truncation under
+    chi_max = 64: the sweep energy equals the free-fermion ground energy
+    E0 = -sum_k Lambda_k, Lambda_k the singular values of the (N x N)
+    bidiagonal matrix with J on the off-diagonal and h on the diagonal
+    (Lieb-Schultz-Mattis / Pfeuty), to 1e-10 per site (FP64) or 1e-8 (mixed);
+    at h = J it is the closed form 1 - 1/sin(pi / (2 (2N + 1))) whose value
+    per site Table 5 / Section 13.2 print as -1.25539.  The FP64 run also
+    equals the oracle's sweep energies."""
+    N = 20
+    M = np.diag(np.full(N, h)) + np.diag(np.full(N - 1, 1.0), 1)
+    E0 = -np.sum(np.linalg.svd(M, compute_uv=False))
+    if h == 1.0:
+        assert abs(E0 - (1.0 - 1.0 / np.sin(np.pi / (2 * (2 * N + 1))))) < 1e-10
+    kw = dict(ctrl=G.CTRL_THRESHOLD, chi_max=64, chi_init=8,
+              prec=G.PREC_FP64 if prec == "fp64" else G.PREC_3XTF32)
+    W = O.mpo(O.MODEL_TFIM, N, 1.0, h)
+    m0 = synth.initial_mps_entries(synth.workload_seed(6, int(10 * h)), N, 8)
+    st = G.State(ctx, dev(W), dev(m0), G.make_params(**kw), 1.0, h)
+    recs, _ = st.sweep(4)
+    st.close()
+    tol = 1e-10 if prec == "fp64" else 1e-8
+    assert abs(recs[-1].E - E0) / N <= tol
+    if prec == "fp64":
+        kw.pop("prec")
+        ref = O.dmrg_run(W, m0, O.make_params(**kw), 4)
+        assert np.all(np.abs(np.array([r.E for r in recs]) - ref["E"]) / N <= 1e-10)

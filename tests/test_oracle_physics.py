@@ -167,3 +167,27 @@ def test_bulk_energy_approaches_bethe_ansatz():
     assert e2 > e_inf and e1 > e_inf
     assert abs(e2 - e_inf) < abs(e1 - e_inf)
     assert abs(e2 - e_inf) < 1e-3
+
+
+def test_pid_target_reading_reproduces_table4_mean_chi():
+    """The paper gives no S_target.  The reading S_target = 0.36 nats (the
+    default of make_params) is the value at which Algorithm 2 with the
+    paper's gains, run in Table 4's ablation setting (20-site Heisenberg
+    chain, chi_max = 64, 5 sweeps, chi = chi_min = 4 at the start), ends with
+    the table's mean bond dimension 7.6.  The PID run stays variational and
+    below the fixed-chi accuracy: its energy lies between the exact ground
+    energy and Table 4's PID value plus 3e-4 (Pauli units per site)."""
+    g_chi = GOLD["table4_pid_mean_chi"]["value"]
+    g_E = GOLD["table4_pid_E_per_site_pauli"]["value"]
+    N = 20
+    p = O.make_params(chi_max=64, chi_init=4, max_sweeps=5, ctrl=O.CTRL_PID)
+    assert p.S_target == 0.36
+    W = O.mpo(O.MODEL_XXZ, N, 1.0, 1.0)
+    m0 = synth.initial_mps_entries(synth.workload_seed(1, 20), N, 4)
+    r = O.dmrg_run(W, m0, p, 5)
+    V = r["visits_per_sweep"]
+    mean_chi = float(np.mean(r["k"][-V:]))
+    assert abs(mean_chi - g_chi) <= 0.25
+    E_pauli = 4 * r["E"][-1] / N
+    E0_pauli = GOLD["heisenberg_N20_pauli_E_per_site"]["value"]
+    assert E0_pauli - 1e-5 <= E_pauli <= g_E + 3e-4
