@@ -233,33 +233,63 @@ def bond_micro(args, G, synth, prec):
     return {"micro": "bond", "prec": args.prec, "chi": [c[k], c[k + 1], c[k + 2]], "ms_per_bond": ms}
 
 
-def ablation(args, G, synth, prec):
-    """The controller ablation on the 20-site Heisenberg chain, chi_max = 64,
-    5 sweeps: fixed chi = 64, the PID of Algorithm 2, threshold truncation
-    (eps_trunc = 1e-10), Algorithm 1's direct rule and the global adaptive
-    chi.  E/N is also given in the paper's Pauli-matrix units (x 4)."""
+def _run_chain(G, synth, prec, model, N, J, h_or_delta, mode, chi_max, sweeps, opts=()):
     import torch
-    N, cm, sweeps = 20, 64, 5
+    ctx = G.Context(0)
+    for kv in opts:
+        name, val = kv.split("=", 1)
+        ctx.set_option(name, float(val))
+    p = G.make_params(prec=prec, ctrl=mode, chi_max=chi_max, chi_fixed=chi_max, chi_init=4, max_sweeps=sweeps)
+    W = ctx.build_mpo(model, N, J, h_or_delta)
+    m0 = torch.from_numpy(synth.initial_mps_entries(synth.workload_seed(1, N), N, p.chi_init)).cuda()
+    torch.cuda.synchronize()
+    st = G.State(ctx, W, m0, p, J, h_or_delta)
+    recs, vis = st.sweep(sweeps)
+    V = 2 * N - 3
+    last = vis[-V:]
+    out = {"E": recs[-1].E, "E_per_site": recs[-1].E / N, "seconds": sum(r.seconds for r in recs),
+           "mean_chi_last_sweep": sum(v.k for v in last) / V, "max_chi": max(v.k for v in vis)}
+    st.close()
+    ctx.close()
+    return out
+
+
+def ablation(args, G, synth, prec):
+    """The paper's small-chain tables on this GPU, chi_max = 64, 5 sweeps,
+    device time of the sweeps (CUDA events):
+      Table 4: 20-site Heisenberg chain, fixed chi = 64 against the PID of
+               Algorithm 2, threshold truncation (eps_trunc = 1e-10),
+               Algorithm 1's direct rule and the global adaptive chi;
+      Table 5: N = 20, fixed chi = 64 against the PID for the Heisenberg
+               chain, the critical (h = J = 1) and ordered (h = 0.2)
+               transverse-field Ising chains and the XXZ chain at Jz = 1.5;
+      Table 6: N = 10, 20, 40 for the Heisenberg and critical Ising chains.
+    Energies per site are also given in the paper's Pauli-matrix units for
+    the spin models (x 4); Delta E/N = (E_PID - E_fixed)/N."""
+    cm, sweeps = 64, 5
+    out = {"micro": "ablation", "chi_max": cm, "sweeps": sweeps, "prec": args.prec, "table4": {}, "table5": {},
+           "table6": {}}
     modes = [("fixed", G.CTRL_FIXED), ("pid", G.CTRL_PID), ("threshold", G.CTRL_THRESHOLD),
              ("direct", G.CTRL_DIRECT), ("global", G.CTRL_GLOBAL)]
-    out = {"micro": "ablation", "N": N, "chi_max": cm, "sweeps": sweeps, "prec": args.prec, "runs": {}}
     for name, mode in modes:
-        ctx = G.Context(0)
-        apply_opts(ctx, args)
-        p = G.make_params(prec=prec, ctrl=mode, chi_max=cm, chi_fixed=cm, chi_init=4, max_sweeps=sweeps)
-        W = ctx.build_mpo(G.XXZ, N, 1.0, 1.0)
-        m0 = torch.from_numpy(synth.initial_mps_entries(synth.workload_seed(1, 20), N, p.chi_init)).cuda()
-        torch.cuda.synchronize()
-        st = G.State(ctx, W, m0, p, 1.0, 1.0)
-        recs, vis = st.sweep(sweeps)
-        V = 2 * N - 3
-        last = vis[-V:]
-        out["runs"][name] = {"E_per_site": recs[-1].E / N, "E_per_site_pauli": 4 * recs[-1].E / N,
-                             "seconds": sum(r.seconds for r in recs),
-                             "mean_chi_last_sweep": sum(v.k for v in last) / V,
-                             "max_chi": max(v.k for v in vis)}
-        st.close()
-        ctx.close()
+        r = _run_chain(G, synth, prec, G.XXZ, 20, 1.0, 1.0, mode, cm, sweeps, args.opt)
+        r["E_per_site_pauli"] = 4 * r["E_per_site"]
+        out["table4"][name] = r
+    models = {"heisenberg": (G.XXZ, 1.0, 1.0, 4.0), "ising_critical": (G.TFIM, 1.0, 1.0, 1.0),
+              "ising_ordered": (G.TFIM, 1.0, 0.2, 1.0), "xxz_jz1.5": (G.XXZ, 1.0, 1.5, 4.0)}
+
+    def pair(key, N):
+        model, J, hd, unit = models[key]
+        f = _run_chain(G, synth, prec, model, N, J, hd, G.CTRL_FIXED, cm, sweeps, args.opt)
+        a = _run_chain(G, synth, prec, model, N, J, hd, G.CTRL_PID, cm, sweeps, args.opt)
+        return {"fixed_s": f["seconds"], "pid_s": a["seconds"], "speedup": f["seconds"] / a["seconds"],
+                "dE_per_site": (a["E"] - f["E"]) / N, "dE_per_site_paper_units": unit * (a["E"] - f["E"]) / N,
+                "mean_chi_fixed": f["mean_chi_last_sweep"], "mean_chi_pid": a["mean_chi_last_sweep"]}
+
+    for key in models:
+        out["table5"][key] = pair(key, 20)
+    for key in ("heisenberg", "ising_critical"):
+        out["table6"][key] = {str(N): pair(key, N) for N in (10, 20, 40)}
     return out
 
 
@@ -800,6 +830,9 @@ def run_ours(args):
     per_sweep = max_over_ranks(ms / 1e3 / args.steps, dist, "cuda")
     sweep_flops = sum(r.flops for r in recs) / len(recs)
     E_mixed = recs[-1].E
+    # the same breakdown one sweep after the timed sweeps (the controller
+    # grows chi through them, so the two bracket the timed region)
+    post_ms, _, post = profiled_sweep(st, ctx)
     # end to end: MPS in pinned host memory -> device, sweep, MPS and records -> host
     e2e = None
     if not args.no_e2e:
@@ -852,8 +885,12 @@ def run_ours(args):
         "kernel_ms_per_sweep": dict({PROF_NAMES[k]: prof[k]["ms"] for k in prof},
                                     **{"other (splits, copies, small kernels, device idle)":
                                        prof_ms - sum(prof[k]["ms"] for k in prof)}),
-        "kernel_profile_note": "from one sweep with every kind bracketed by events, run right before the timed "
-                               "sweeps; the timed sweeps bracket only the dominant kind",
+        "kernel_ms_after_timed": dict({PROF_NAMES[k]: post[k]["ms"] for k in post},
+                                      **{"other (splits, copies, small kernels, device idle)":
+                                         post_ms - sum(post[k]["ms"] for k in post)}),
+        "kernel_profile_note": "kernel_ms_per_sweep: one sweep with every kind bracketed by events, run right "
+                               "before the timed sweeps; kernel_ms_after_timed: the same one sweep after them; "
+                               "the timed sweeps bracket only the dominant kind",
         "roofline": roof, "gpu_launches": l1 - l0, "clocks": clk,
         "kernel_rates": kernel_rates(prof, PROF_NAMES, 1, peaks()[0]),
     }

@@ -74,12 +74,23 @@ __device__ int trunc_k_dev(const double *s, int r, int chi, int rank, int above,
     return k;
 }
 
-__global__ void __launch_bounds__(DB) k_decide(const double *__restrict__ s, int r, dmrg_ctrl_state *st,
+// spectra up to this length are staged in shared memory first, so that the
+// serial scans below (multiplet guard, label tail) read shared memory
+constexpr int kDecideSmem = 4096;
+
+__global__ void __launch_bounds__(DB) k_decide(const double *__restrict__ s_g, int r, dmrg_ctrl_state *st,
                                                dmrg_params p, int do_ctrl, int chi_override, const float *mlp,
                                                int bond, int N, int sweep, const LzState *lz, BondResult *res,
                                                dmrg_visit_record *visit, int direction, double rank_floor,
                                                const int *jac_info, double eps_target, int *status)
 {
+    extern __shared__ double s_sm[];
+    const double *s = s_g;
+    if (r <= kDecideSmem) {
+        for (int j = threadIdx.x; j < r; j += DB) s_sm[j] = s_g[j];
+        __syncthreads();
+        s = s_sm;
+    }
     __shared__ double sh[32];
     __shared__ float h1[MLP_H], h2[MLP_H], xin[MLP_IN], red[2];
     __shared__ int sh_chi, sh_k, sh_kp, sh_fb, sh_mlp_ok, sh_chim;
@@ -289,7 +300,14 @@ dmrg_status launch_decide(dmrg_ctx *ctx, const double *s, int r, dmrg_ctrl_state
                           double rank_floor, const int *jac_info)
 {
     prof_mark(ctx, PROF_DECIDE);
-    k_decide<<<1, DB, 0, ctx->stream>>>(s, r, st_bond, p, do_ctrl, chi_override, mlp, bond, N, sweep,
+    const size_t smem = r <= kDecideSmem ? sizeof(double) * (size_t)r : 0;
+    static bool attr = false;
+    if (!attr) {
+        DMRG_CUDA(cudaFuncSetAttribute(k_decide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(double) * kDecideSmem)));
+        attr = true;
+    }
+    k_decide<<<1, DB, smem, ctx->stream>>>(s, r, st_bond, p, do_ctrl, chi_override, mlp, bond, N, sweep,
                                         static_cast<const LzState *>(lz_state), res, visit, direction, rank_floor,
                                         jac_info, ctx->mlp_eps_target, ctx->d_status); DMRG_COUNT_LAUNCH();
     prof_mark(ctx, PROF_DECIDE);

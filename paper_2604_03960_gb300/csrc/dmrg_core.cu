@@ -114,17 +114,38 @@ __global__ void __launch_bounds__(kMixThreads) k_mix(const double *__restrict__ 
     __shared__ double val[kMaxCh * kMaxCh];
     __shared__ unsigned char col[kMaxCh * kMaxCh];
     __shared__ int rowptr[kMaxCh + 1];
+    __shared__ int rowcnt[kMaxCh];
     __shared__ double xs[kMaxCh][kMixThreads];
-    if (threadIdx.x == 0) {
-        int nnz = 0;
-        for (int o = 0; o < d.nout; ++o) {
-            rowptr[o] = nnz;
-            for (int c = 0; c < d.nin; ++c) {
-                const double v = C[o * d.nin + c];
-                if (v != 0.0) { val[nnz] = v; col[nnz] = (unsigned char)c; ++nnz; }
-            }
+    // compress the coefficient rows in parallel: warp w takes rows w, w + 4,
+    // ...; each lane tests one column (nin <= 32) and the ballot gives every
+    // nonzero its slot; the row counts become offsets by a scan in one warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kWarps = kMixThreads / 32;
+    for (int o = warp; o < d.nout; o += kWarps) {
+        const double v = lane < d.nin ? C[o * d.nin + lane] : 0.0;
+        const unsigned nzm = __ballot_sync(0xffffffffu, v != 0.0);
+        if (lane == 0) rowcnt[o] = __popc(nzm);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int c = lane < d.nout ? rowcnt[lane] : 0;
+        int incl = c;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
         }
-        rowptr[d.nout] = nnz;
+        if (lane < d.nout) rowptr[lane] = incl - c;
+        if (lane == d.nout - 1) rowptr[d.nout] = incl;
+    }
+    __syncthreads();
+    for (int o = warp; o < d.nout; o += kWarps) {
+        const double v = lane < d.nin ? C[o * d.nin + lane] : 0.0;
+        const unsigned nzm = __ballot_sync(0xffffffffu, v != 0.0);
+        if (v != 0.0) {
+            const int slot = rowptr[o] + __popc(nzm & ((1u << lane) - 1u));
+            val[slot] = v;
+            col[slot] = (unsigned char)lane;
+        }
     }
     __syncthreads();
     const long long total = (long long)d.An * d.Bn;
@@ -279,12 +300,14 @@ __global__ void k_sumsq_partial(const double *__restrict__ x, long long n, doubl
 
 __global__ void k_scale_partials(double *__restrict__ x, long long n, const double *__restrict__ part, int nparts)
 {
+    // every block sums the partials in the same fixed order (all threads load
+    // at once, then the block reduction), so all blocks get the same scale
+    __shared__ double sh[32];
     __shared__ double inv;
-    if (threadIdx.x == 0) {
-        double a = 0.0;
-        for (int b = 0; b < nparts; ++b) a += part[b];
-        inv = (a > 0.0) ? 1.0 / sqrt(a) : 0.0;
-    }
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) a += part[b];
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) inv = (a > 0.0) ? 1.0 / sqrt(a) : 0.0;
     __syncthreads();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         x[i] *= inv;

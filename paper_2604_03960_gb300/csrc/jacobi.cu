@@ -119,13 +119,18 @@ __device__ __forceinline__ bool block_barrier(unsigned *words, int *status)
 }
 
 // F2[0] = sum of squares of all entries (|A|_F^2), for the negligible-vector test
+// (it only scales the floor below which vectors count as zero, so each
+// thread's share is accumulated in FP32; the block sum is FP64)
 __global__ void k_frob2(const double *__restrict__ A, long long n, double *F2)
 {
     __shared__ double sh[32];
-    double a = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) a = fma(A[i], A[i], a);
-    a = block_sum(a, sh);
-    if (threadIdx.x == 0) F2[0] = a;
+    float a = 0.f;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        const float x = (float)A[i];
+        a = fmaf(x, x, a);
+    }
+    const double t = block_sum((double)a, sh);
+    if (threadIdx.x == 0) F2[0] = t;
 }
 
 __global__ void __launch_bounds__(256) k_jac_sweeps(double *__restrict__ X, double *__restrict__ Vm, int r, int l,
@@ -854,10 +859,10 @@ dmrg_status launch_bjac32(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps,
 __global__ void k_frob2_f(const float *__restrict__ A, long long n, double *F2)
 {
     __shared__ double sh[32];
-    double a = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) a = fma((double)A[i], (double)A[i], a);
-    a = block_sum(a, sh);
-    if (threadIdx.x == 0) F2[0] = a;
+    float a = 0.f;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) a = fmaf(A[i], A[i], a);
+    const double t = block_sum((double)a, sh);
+    if (threadIdx.x == 0) F2[0] = t;
 }
 
 // vectors shorter than 2^-22 |A|_F are unresolved after the FP32 rounding of
@@ -939,7 +944,7 @@ dmrg_status svd_jacobi(dmrg_ctx *ctx, const double *A, int m, int n, double *U, 
     int *status = ctx->d_status;
     const double *F2 = reinterpret_cast<const double *>(w.sync + 4);
     const double small = (double)(l > 16 ? l : 16) * 2.220446049250313e-16;
-    k_frob2<<<1, 256, 0, st>>>(X, (long long)r * l, reinterpret_cast<double *>(w.sync + 4)); DMRG_COUNT_LAUNCH();
+    k_frob2<<<1, 1024, 0, st>>>(X, (long long)r * l, reinterpret_cast<double *>(w.sync + 4)); DMRG_COUNT_LAUNCH();
     void *args[] = {&X, &Vm, (void *)&r, (void *)&l, &max_sweeps, (void *)&tol, &sync, &status, &d_info, &F2,
                     (void *)&small};
     prof_mark(ctx, PROF_JACOBI64);
@@ -983,6 +988,7 @@ dmrg_status frob2_f32(dmrg_ctx *ctx, const float *A, long long n, double *F2)
 // such that the rows r_eff.. together have Frobenius norm <= 2^-23 |X|_F.
 // Dropping them moves no singular value by more than that (Weyl), the size of
 // the FP32 rounding X already carries; the Jacobi then rotates r_eff rows.
+constexpr int kRowRankSmem = 4096;
 __global__ void k_row_rank32(const float *__restrict__ X, int r, int l, double *__restrict__ rn, int *r_eff)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -993,13 +999,21 @@ __global__ void k_row_rank32(const float *__restrict__ X, int r, int l, double *
         if (lane == 0) rn[i] = (double)a;
     }
     __syncthreads();
+    // the scans below run on one thread: stage the row norms in shared memory
+    __shared__ double rs[kRowRankSmem];
+    const double *q = rn;
+    if (r <= kRowRankSmem) {
+        for (int i = threadIdx.x; i < r; i += blockDim.x) rs[i] = rn[i];
+        __syncthreads();
+        q = rs;
+    }
     if (threadIdx.x == 0) {
         double tot = 0.0;
-        for (int i = 0; i < r; ++i) tot += rn[i];
+        for (int i = 0; i < r; ++i) tot += q[i];
         const double thr = tot * 1.4210854715202004e-14;   // (2^-23)^2 |X|_F^2
         double suffix = 0.0;
         int j = r;
-        while (j > 1 && suffix + rn[j - 1] <= thr) suffix += rn[--j];
+        while (j > 1 && suffix + q[j - 1] <= thr) suffix += q[--j];
         *r_eff = j;
     }
 }
@@ -1069,7 +1083,7 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
     // F2 = |A|_F^2 from the FP32 copy; vectors below 2^-23 |A|_F are dropped anyway
     const double *F2 = reinterpret_cast<const double *>(sync + 4);
     const double small = ctx->jacobi32_floor;
-    k_frob2_f<<<1, 256, 0, st>>>(X, (long long)r * l, reinterpret_cast<double *>(sync + 4)); DMRG_COUNT_LAUNCH();
+    k_frob2_f<<<1, 1024, 0, st>>>(X, (long long)r * l, reinterpret_cast<double *>(sync + 4)); DMRG_COUNT_LAUNCH();
     prof_mark(ctx, PROF_JACOBI32);
     if ((long long)r * l <= kSmemJacFloats) {
         const int smem = (int)(sizeof(float) * (size_t)r * l);

@@ -84,11 +84,17 @@ __global__ void __launch_bounds__(RB) k_multidot(ReduceArgs a, LzState *lz, int 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // final reduction in block order: thread q sums column q
-    for (int q = threadIdx.x; q <= MAXQ; q += RB) {
+    // final reduction, warp q' over columns q = q', q' + 8, ...: each lane sums
+    // the blocks b = lane, lane + 32, ... in order, then a fixed shuffle tree
+    // (all loads of a column are in flight at once; the order is fixed)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = warp; q <= MAXQ; q += RB / 32) {
         if (!(q < nq || q == MAXQ)) continue;
         double s = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += *(volatile double *)&a.partials[(long long)b * (MAXQ + 1) + q];
+        for (int b = lane; b < (int)gridDim.x; b += 32)
+            s += *(volatile double *)&a.partials[(long long)b * (MAXQ + 1) + q];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane != 0) continue;
         if (MODE == 0 || MODE == 4) {
             out[q] = s;
             if (MODE == 4 && q == j) {  // first Gram-Schmidt pass on w = H v_j: alpha_j = v_j . w
@@ -167,10 +173,14 @@ __global__ void __launch_bounds__(RB) k_multiaxpy_norm(double *__restrict__ w, c
         last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
+    // the last block sums the partials in a fixed order (all loads at once)
     double t = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) t += *(volatile double *)&partials[b];
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += RB) t += *(volatile double *)&partials[b];
+    __shared__ double sh[32];
+    t = block_sum(t, sh);
+    if (threadIdx.x != 0) return;
     const double bta = sqrt(t);
     lz->beta[j + 1] = bta;
     lz->m = j + 1;
