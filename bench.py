@@ -663,37 +663,71 @@ def profiled_sweep(st, ctx):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(ctx.stream)
-    r, _ = st.sweep(1, visits=False)
+    r, v = st.sweep(1, visits=True)
     ev1.record(ctx.stream)
     torch.cuda.synchronize()
     prof = {k: ctx.profile_read(k) for k in PROF_NAMES}
     ctx.profile(False)
-    return ev0.elapsed_time(ev1), r[0], prof
+    return ev0.elapsed_time(ev1), r[0], prof, v
 
 
-def fp64_path(args, G, synth, wl, E_mixed, mixed_s_per_sweep, seed):
-    """The plain FP64 GPU path on the same chain, initial MPS, controller and
-    sweep count as the mixed headline: its sweep time over the same timed
-    sweeps, its energy, and |E_mixed - E_fp64| / N after the last sweep."""
+HOLD_SWEEPS = 6
+
+
+def hold_sweeps(G, st, wl, prec, total):
+    """Freeze every bond at the chi its controller reached (DMRG_CTRL_HOLD)
+    and run HOLD_SWEEPS sweeps there: the run settles at that schedule, free
+    of the controller's transient."""
+    p = chain_params(G, wl, prec, total, ctrl="CTRL_HOLD")
+    st.set_params(p)
+    recs, vis = st.sweep(HOLD_SWEEPS, visits=True)
+    return recs, vis
+
+
+def per_sweep_k(vis, V):
+    return [[v.k for v in vis[i:i + V]] for i in range(0, len(vis), V)]
+
+
+def fp64_path(args, G, synth, wl, seed, schedule, timed_idx, E_mixed_timed, E_mixed_end, mixed_s_per_sweep):
+    """The plain FP64 GPU path on the mixed run's retained bond dimensions:
+    the same chain and initial MPS, every sweep replaying the k the mixed run
+    retained at each visit (DMRG_CTRL_REPLAY), so the two differ only in
+    precision.  Its sweep time over the sweeps the mixed run timed, and
+    |E_mixed - E_fp64| / N after the last timed sweep and after the last
+    sweep (the end of the held phase)."""
     N = wl["N"]
     ctx = G.Context(0)
-    total = args.warmup + 1 + args.steps
-    p = chain_params(G, wl, G.PREC_FP64, total)
+    p = chain_params(G, wl, G.PREC_FP64, len(schedule), ctrl="CTRL_REPLAY")
     st = new_chain(G, synth, ctx, wl, p, seed)
     t0 = time.perf_counter()
-    for _ in range(args.warmup + 1):
-        st.sweep(1, visits=False)
-    ms, recs, vis, _ = timed_sweeps(st, ctx, args.steps)
-    s64 = ms / 1e3 / args.steps
-    out = {"s_per_sweep": s64, "energy_per_site": recs[-1].E / N, "dE_per_site_vs_mixed": abs(recs[-1].E - E_mixed) / N,
-           "mean_chi": sum(r.mean_chi for r in recs) / len(recs), "max_chi": max(r.max_chi for r in recs),
-           "sweeps": total, "speedup_mixed_vs_fp64": s64 / mixed_s_per_sweep,
-           "wall_s": time.perf_counter() - t0,
-           "note": "same chain, initial MPS, PID controller and sweep count as the mixed run; timed over the same "
-                   "sweeps (the last --steps); FP64 everywhere (DFMA contractions, FP64 Jacobi)"}
+    t_timed, E_timed, E_all, ks = 0.0, None, [], []
+    import torch
+    for i, sched in enumerate(schedule):
+        st.set_schedule(sched)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(ctx.stream)
+        r, v = st.sweep(1, visits=True)
+        ev1.record(ctx.stream)
+        torch.cuda.synchronize()
+        E_all.append(r[0].E)
+        ks.append([x.k for x in v])
+        if i in timed_idx:
+            t_timed += ev0.elapsed_time(ev1) / 1e3
+            if i == max(timed_idx):
+                E_timed = r[0].E
+    s64 = t_timed / len(timed_idx)
+    same_k = sum(a == b for x, y in zip(ks, schedule) for a, b in zip(x, y)) / max(1, sum(len(x) for x in ks))
+    out = {"s_per_sweep": s64, "speedup_mixed_vs_fp64": s64 / mixed_s_per_sweep,
+           "energy_per_site_after_timed": E_timed / N, "dE_per_site_after_timed": abs(E_timed - E_mixed_timed) / N,
+           "energy_per_site_end": E_all[-1] / N, "dE_per_site_end": abs(E_all[-1] - E_mixed_end) / N,
+           "sweeps": len(schedule), "k_agreement": same_k, "wall_s": time.perf_counter() - t0,
+           "note": ("same chain and initial MPS; every sweep replays the retained k of the mixed run at each visit "
+                    "(DMRG_CTRL_REPLAY), so the forms differ only in precision; timed over the mixed run's timed "
+                    "sweeps; 'end' is after the %d held sweeps (every bond at the chi its PID reached)" % HOLD_SWEEPS)}
     st.close()
     ctx.close()
-    return out, [v.chi_ctrl for v in vis]
+    return out
 
 
 def threshold_comparison(args, G, synth):
@@ -707,7 +741,7 @@ def threshold_comparison(args, G, synth):
     st = new_chain(G, synth, ctx, wl, p, synth.workload_seed(2, 0))
     for _ in range(3):
         st.sweep(1, visits=False)
-    ms, rec, prof = profiled_sweep(st, ctx)
+    ms, rec, prof, _ = profiled_sweep(st, ctx)
     out = {"s_per_sweep": ms / 1e3, "energy_per_site": rec.E / wl["N"], "mean_chi": rec.mean_chi,
            "max_chi": rec.max_chi, "sweep_gflops": rec.flops / (ms / 1e3) / 1e9,
            "kernel_ms_per_sweep": {PROF_NAMES[k]: prof[k]["ms"] for k in prof},
@@ -810,11 +844,16 @@ def run_ours(args):
     # replicas only: each rank runs its own chain (seeded by rank)
     seed = replica_seed(rank)
     st = new_chain(G, synth, ctx, wl, p, seed)
+    V = 2 * N - 3
+    schedule = []                 # retained k of every visit of every sweep (the FP64 arm replays it)
     for _ in range(args.warmup):
-        st.sweep(1, visits=False)
+        _, v = st.sweep(1, visits=True)
+        schedule += per_sweep_k(v, V)
     # one sweep with every kernel kind bracketed: the breakdown, and the
     # dominant kind, whose launches alone are bracketed in the timed region
-    prof_ms, prof_rec, prof = profiled_sweep(st, ctx)
+    prof_ms, prof_rec, prof, v = profiled_sweep(st, ctx)
+    schedule += per_sweep_k(v, V)
+    timed_idx = set(range(len(schedule), len(schedule) + args.steps))
     dom = max(prof, key=lambda k: prof[k]["ms"])
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
@@ -830,9 +869,11 @@ def run_ours(args):
     per_sweep = max_over_ranks(ms / 1e3 / args.steps, dist, "cuda")
     sweep_flops = sum(r.flops for r in recs) / len(recs)
     E_mixed = recs[-1].E
+    schedule += per_sweep_k(vis, V)
     # the same breakdown one sweep after the timed sweeps (the controller
     # grows chi through them, so the two bracket the timed region)
-    post_ms, _, post = profiled_sweep(st, ctx)
+    post_ms, _, post, v = profiled_sweep(st, ctx)
+    schedule += per_sweep_k(v, V)
     # end to end: MPS in pinned host memory -> device, sweep, MPS and records -> host
     e2e = None
     if not args.no_e2e:
@@ -847,7 +888,8 @@ def run_ours(args):
             n_in = st.mps_size()
             st.put_mps(host[:n_in])
             h2d += 8 * n_in
-            st.sweep(1, visits=True)
+            _, v = st.sweep(1, visits=True)
+            schedule += per_sweep_k(v, V)
             n_out = st.mps_size()
             if n_out > host.numel():
                 host = torch.empty(n_out, dtype=torch.float64).pin_memory()
@@ -858,6 +900,11 @@ def run_ours(args):
         e2e = {"value": t_e2e, "unit": "s/sweep", "h2d_bytes_per_step": h2d // e2e_steps,
                "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
                "path": "MPS from pinned host memory -> dmrg_state_put_mps -> dmrg_sweep -> dmrg_state_get_mps + records"}
+    E_end = None
+    if prec == G.PREC_3XTF32 and not args.no_fp64 and rank == 0:
+        hr, hv = hold_sweeps(G, st, wl, prec, total)
+        schedule += per_sweep_k(hv, V)
+        E_end = hr[-1].E
     st.close()
     ctx.close()
     if rank != 0:
@@ -899,9 +946,8 @@ def run_ours(args):
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(sweep_flops, chi=oracle_chi(recs))
     if prec == G.PREC_3XTF32 and not args.no_fp64:
-        f64, chi64 = fp64_path(args, G, synth, wl, E_mixed, per_sweep, seed)
-        f64["chi_schedule_agreement"] = float(sum(a == b for a, b in zip(chi64, [v.chi_ctrl for v in vis]))
-                                              / max(1, len(chi64)))
+        f64 = fp64_path(args, G, synth, wl, seed, schedule, timed_idx, E_mixed, E_end, per_sweep)
+        f64["mixed_energy_per_site_end"] = E_end / N
         out["fp64_path"] = f64
     if prec == G.PREC_3XTF32 and not args.no_compare:
         out["threshold_comparison"] = threshold_comparison(args, G, synth)

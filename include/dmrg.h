@@ -71,10 +71,17 @@ typedef enum {
     DMRG_CTRL_FIXED = 2,     /* chi = chi_fixed                                          */
     DMRG_CTRL_THRESHOLD = 3, /* chi = chi_max; the eps_trunc threshold decides (Sec. 10) */
     DMRG_CTRL_MLP = 4,       /* learned scheduler with the PID as fallback               */
-    DMRG_CTRL_GLOBAL = 5     /* global adaptive chi (Section 6): one PID on the mean of the
+    DMRG_CTRL_GLOBAL = 5,    /* global adaptive chi (Section 6): one PID on the mean of the
                                 per-bond filtered entropies, stepped once per sweep (with
                                 alpha = 1: the inputs are already filtered); every bond is
                                 truncated to the same chi, which starts at chi_min        */
+    DMRG_CTRL_HOLD = 6,      /* no controller step: every bond keeps the chi its controller
+                                holds (no counterpart in the paper; with
+                                dmrg_state_set_params it converges a run at the schedule
+                                the controller reached)                                   */
+    DMRG_CTRL_REPLAY = 7     /* the chi of every visit of dmrg_sweep comes from the schedule
+                                set by dmrg_state_set_schedule (no counterpart in the
+                                paper: runs another precision on a recorded schedule)     */
 } dmrg_ctrl_mode;
 
 /* Parameters of the local update and of the controller. */
@@ -405,6 +412,18 @@ long long dmrg_launch_count(void);
  * their algorithmic flops and bytes. */
 dmrg_status dmrg_profile(dmrg_ctx *ctx, int on);
 dmrg_status dmrg_profile_read(dmrg_ctx *ctx, int kind, double *ms, long long *launches, double *flops, double *bytes);
+/* Replace the state's controller and truncation parameters between sweeps
+ * (no counterpart in the paper), e.g. DMRG_CTRL_HOLD to finish a run at the
+ * chi the per-bond controllers reached.  chi_max, prec and lanczos_steps
+ * must equal the state's (its memory is sized for them): DMRG_EINVAL
+ * otherwise.  The controllers' device state is kept. */
+dmrg_status dmrg_state_set_params(dmrg_state *st, const dmrg_params *p);
+/* Schedule of DMRG_CTRL_REPLAY: chi_host[v] (host, n = 2N - 3 entries in
+ * [1, chi_max]) bounds the retained dimension at visit v of every following
+ * dmrg_sweep (k = min(chi, rank, threshold count)), until replaced.  The
+ * schedule is copied.  bond_update is not available in that mode
+ * (DMRG_EINVAL); a sweep without a schedule returns DMRG_EINVAL. */
+dmrg_status dmrg_state_set_schedule(dmrg_state *st, const int *chi_host, int n);
 /* Set the learned scheduler's parameters (4929 FP32 values, layout of
  * dmrg_mlp_forward) used when ctrl == DMRG_CTRL_MLP. */
 dmrg_status dmrg_state_set_mlp(dmrg_state *st, const float *params_dev);

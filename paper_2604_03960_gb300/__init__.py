@@ -18,11 +18,12 @@ from .build import LIB as _LIB_PATH, build as _build
 __all__ = [
     "lib", "Params", "ModelParams", "CtrlState", "SweepRecord", "VisitRecord", "Context", "State",
     "PREC_FP64", "PREC_3XTF32", "CTRL_PID", "CTRL_DIRECT", "CTRL_FIXED", "CTRL_THRESHOLD", "CTRL_MLP", "CTRL_GLOBAL",
+    "CTRL_HOLD", "CTRL_REPLAY",
     "XXZ", "J1J2", "TFIM", "DMRGError", "make_params", "MLP_NPARAM",
 ]
 
 PREC_FP64, PREC_3XTF32, PREC_BF16X3 = 0, 1, 2
-CTRL_PID, CTRL_DIRECT, CTRL_FIXED, CTRL_THRESHOLD, CTRL_MLP, CTRL_GLOBAL = range(6)
+CTRL_PID, CTRL_DIRECT, CTRL_FIXED, CTRL_THRESHOLD, CTRL_MLP, CTRL_GLOBAL, CTRL_HOLD, CTRL_REPLAY = range(8)
 XXZ, J1J2, TFIM = 0, 1, 2
 MLP_NPARAM = 4929
 
@@ -106,6 +107,8 @@ def _declare(L):
         "dmrg_state_env": (S, [_VP, _I, _I, _VP]),
         "dmrg_state_ctrl": (S, [_VP, C.POINTER(_VP)]),
         "dmrg_state_set_mlp": (S, [_VP, _VP]),
+        "dmrg_state_set_params": (S, [_VP, C.POINTER(Params)]),
+        "dmrg_state_set_schedule": (S, [_VP, C.POINTER(_I), _I]),
         "dmrg_mlp_forward": (S, [_VP, _VP, _I, _VP, _VP]),
         "dmrg_mlp_loss_grad": (S, [_VP, _VP, _I, _VP, _VP, _VP, _VP]),
         "dmrg_mlp_adam": (S, [_VP, _I, _VP, _VP, _VP, _VP, _I, C.c_float, C.c_float, C.c_float, C.c_float]),
@@ -160,7 +163,8 @@ def exported_symbols():
         "dmrg_create", "dmrg_destroy", "dmrg_get_status", "dmrg_status_string", "dmrg_mpo_dim", "dmrg_build_mpo",
         "dmrg_state_create", "dmrg_state_destroy", "dmrg_sweep", "bond_update", "svd_truncate", "entropy_pid_step",
         "dmrg_entropy", "dmrg_heff_apply", "dmrg_env_left", "dmrg_env_right", "dmrg_lanczos", "dmrg_state_chi",
-        "dmrg_state_site", "dmrg_state_env", "dmrg_state_ctrl", "dmrg_state_set_mlp", "dmrg_mlp_forward",
+        "dmrg_state_site", "dmrg_state_env", "dmrg_state_ctrl", "dmrg_state_set_mlp", "dmrg_state_set_params",
+        "dmrg_state_set_schedule", "dmrg_mlp_forward",
         "dmrg_mlp_loss_grad", "dmrg_mlp_adam", "dmrg_gemm", "dmrg_set_option",
         "dmrg_state_mps_size", "dmrg_state_get_mps", "dmrg_state_put_mps", "dmrg_launch_count",
         "dmrg_profile", "dmrg_profile_read", "svd_truncate_noalloc", "dmrg_mlp_train",
@@ -492,6 +496,17 @@ class State:
 
     def put_mps(self, src: torch.Tensor):
         _check(lib().dmrg_state_put_mps(self.h, C.c_void_p(src.data_ptr())), "dmrg_state_put_mps")
+
+    def set_params(self, params: Params):
+        """Replace the controller/truncation parameters between sweeps (chi_max,
+        prec and lanczos_steps must stay)."""
+        _check(lib().dmrg_state_set_params(self.h, C.byref(params)), "dmrg_state_set_params")
+        self.params = params
+
+    def set_schedule(self, chi):
+        """Per-visit chi (2N - 3 ints) of the following sweeps in DMRG_CTRL_REPLAY mode."""
+        arr = (C.c_int * len(chi))(*[int(x) for x in chi])
+        _check(lib().dmrg_state_set_schedule(self.h, arr, len(chi)), "dmrg_state_set_schedule")
 
     def set_mlp(self, P: torch.Tensor | None):
         _check(lib().dmrg_state_set_mlp(self.h, _ptr(P) if P is not None else None), "dmrg_state_set_mlp")

@@ -533,6 +533,8 @@ struct dmrg_state {
     cudaEvent_t ev_res = nullptr;    // recorded after the bond result is copied to h_res
     dmrg_ctrl_state *gctrl = nullptr;  // global adaptive chi: the one controller (device)
     int global_chi = 0;                // ... and its current chi (host copy, set at sweep ends)
+    std::vector<int> sched;            // DMRG_CTRL_REPLAY: chi of each visit of the next sweeps
+    int cur_visit = -1;                // visit index within the running sweep (-1 outside dmrg_sweep)
     // a bond step between its two phases (bond_step_a / bond_step_b)
     struct Pending {
         int k = 0, go_right = 0, direction = 1, m = 0, n = 0, r = 0, cl = 0, cm = 0, cr = 0, K = 0;
@@ -757,7 +759,14 @@ static dmrg_status bond_step_a(dmrg_state *st, int k, int go_right, int do_ctrl,
         DMRG_CUDA(cudaGetLastError());
     }
     const float *mlp = st->has_mlp ? st->mlp : nullptr;
-    const int chi_global = st->p.ctrl == DMRG_CTRL_GLOBAL ? st->global_chi : 0;
+    int chi_global = st->p.ctrl == DMRG_CTRL_GLOBAL ? st->global_chi : 0;
+    if (st->p.ctrl == DMRG_CTRL_REPLAY) {
+        // the recorded schedule decides (the controllers do not step)
+        const int V = 2 * st->N - 3;
+        const int v = st->cur_visit;
+        if (v < 0 || (int)st->sched.size() < V) return DMRG_EINVAL;
+        chi_global = st->sched[v];
+    }
     if (prec == DMRG_PREC_FP64) {
         // SVD (Eq. 20) in FP64, then entropy, controller and truncation
         DMRG_TRY(svd_jacobi(ctx, st->theta, m, n, st->U, st->s, st->Vt, st->svdw, st->p.jacobi_max_sweeps,
@@ -1034,7 +1043,8 @@ static void visit_of(const dmrg_state *st, int v, int &k, int &go_right, int &di
     k = (half == 0) ? q : N - 3 - q;
     go_right = (half == 0 && k < N - 2);
     direction = half == 0 ? 1 : -1;
-    do_ctrl = (st->p.pid_steps_per_sweep >= 2) || (half == 0);
+    do_ctrl = ((st->p.pid_steps_per_sweep >= 2) || (half == 0)) && st->p.ctrl != DMRG_CTRL_HOLD &&
+              st->p.ctrl != DMRG_CTRL_REPLAY;
 }
 
 // End of a sweep: copy the visit records, fill the sweep record, advance the
@@ -1090,7 +1100,10 @@ dmrg_status dmrg_sweep(dmrg_ctx *ctx, dmrg_state *st, int n_sweeps, int stop_on_
         for (int v = 0; v < V; ++v) {
             int k, go_right, direction, do_ctrl, kk;
             visit_of(st, v, k, go_right, direction, do_ctrl);
-            DMRG_TRY(bond_step(st, k, go_right, do_ctrl, st->d_visits + v, direction, &flops, &kk, &E_last));
+            st->cur_visit = v;
+            dmrg_status bs = bond_step(st, k, go_right, do_ctrl, st->d_visits + v, direction, &flops, &kk, &E_last);
+            st->cur_visit = -1;
+            if (bs != DMRG_OK) return bs;
         }
         DMRG_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
         DMRG_CUDA(cudaEventSynchronize(ctx->ev1));
@@ -1132,6 +1145,7 @@ dmrg_status dmrg_sweep_chains(int n_chains, dmrg_ctx *const *ctxs, dmrg_state *c
             dmrg_state *st = states[c];
             int k, go_right, direction, do_ctrl;
             visit_of(st, run[c].v, k, go_right, direction, do_ctrl);
+            st->cur_visit = run[c].v;
             DMRG_TRY(bond_step_a(st, k, go_right, do_ctrl, st->d_visits + run[c].v, direction));
         }
         for (int c : active) {
@@ -1157,8 +1171,10 @@ dmrg_status bond_update(dmrg_ctx *ctx, dmrg_state *st, int bond, int direction, 
 {
     if (!ctx || !st || st->ctx != ctx || bond < 0 || bond > st->N - 2 || (direction != 1 && direction != -1))
         return DMRG_EINVAL;
+    if (st->p.ctrl == DMRG_CTRL_REPLAY) return DMRG_EINVAL;   // a schedule is per sweep visit
     int go_right = (direction == 1) && (bond < st->N - 2);
-    DMRG_TRY(bond_step(st, bond, go_right, 1, st->d_visits, direction, nullptr, k_out, E_out));
+    const int do_ctrl = st->p.ctrl != DMRG_CTRL_HOLD;
+    DMRG_TRY(bond_step(st, bond, go_right, do_ctrl, st->d_visits, direction, nullptr, k_out, E_out));
     return DMRG_OK;
 }
 
@@ -1291,6 +1307,29 @@ dmrg_status dmrg_profile_read(dmrg_ctx *ctx, int kind, double *ms, long long *la
     if (launches) *launches = p.n;
     if (flops) *flops = p.flops;
     if (bytes) *bytes = p.bytes;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_state_set_params(dmrg_state *st, const dmrg_params *p)
+{
+    if (!st || !p) return DMRG_EINVAL;
+    const dmrg_params &o = st->p;
+    // the state's memory and precision were sized for these: they stay
+    if (p->chi_max != o.chi_max || p->prec != o.prec || p->lanczos_steps != o.lanczos_steps ||
+        p->chi_min < 1 || p->chi_min > p->chi_max || p->ctrl < DMRG_CTRL_PID || p->ctrl > DMRG_CTRL_REPLAY)
+        return DMRG_EINVAL;
+    const int jms = o.jacobi_max_sweeps;
+    st->p = *p;
+    if (st->p.jacobi_max_sweeps <= 0) st->p.jacobi_max_sweeps = jms;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_state_set_schedule(dmrg_state *st, const int *chi_host, int n)
+{
+    if (!st || !chi_host || n != 2 * st->N - 3) return DMRG_EINVAL;
+    for (int v = 0; v < n; ++v)
+        if (chi_host[v] < 1 || chi_host[v] > st->p.chi_max) return DMRG_EINVAL;
+    st->sched.assign(chi_host, chi_host + n);
     return DMRG_OK;
 }
 

@@ -130,3 +130,50 @@ def test_mixed_svd_exact_spectrum(G, chi, opt):
     S_ref, _ = O.entropy(s_ref)
     assert abs(S - S_ref) <= 1e-6
     c.close()
+
+
+def test_hold_mode_freezes_the_schedule(G, ctx):
+    """DMRG_CTRL_HOLD set between sweeps keeps every bond at the chi its PID
+    reached: the controller chi of the held sweeps equals the last PID sweep's
+    chi at the same visit, and at a fixed schedule the energy does not rise."""
+    N = 20
+    st, recs, vis = run(G, ctx, N, 3, G.PREC_FP64, ctrl=G.CTRL_PID, chi_max=32, chi_init=4)
+    held = {}
+    for v in vis:                      # each bond's chi after its last PID step
+        held[v.bond] = v.chi_ctrl
+    assert len(set(held.values())) > 1
+    p = G.make_params(prec=G.PREC_FP64, ctrl=G.CTRL_HOLD, chi_max=32, chi_init=4)
+    st.set_params(p)
+    r2, v2 = st.sweep(3)
+    assert all(v.chi_ctrl == held[v.bond] for v in v2)
+    E = [r.E for r in r2]
+    assert all(b <= a + 1e-12 for a, b in zip(E, E[1:]))
+    with pytest.raises(G.DMRGError):
+        st.set_params(G.make_params(prec=G.PREC_FP64, ctrl=G.CTRL_HOLD, chi_max=64, chi_init=4))
+    st.close()
+
+
+def test_replay_reproduces_a_run_and_compares_precisions(G, ctx):
+    """DMRG_CTRL_REPLAY: an FP64 run that replays, sweep by sweep, the retained
+    k of an FP64 PID run reproduces it bit for bit (same kernels, same k), and
+    the mixed form replaying the same k ends within the mixed forms' 1e-8 per
+    site of it."""
+    N, sweeps = 20, 4
+    kw = dict(ctrl=G.CTRL_PID, chi_max=32, chi_init=4)
+    st, recs, vis = run(G, ctx, N, sweeps, G.PREC_FP64, **kw)
+    st.close()
+    V = 2 * N - 3
+    sched = [[v.k for v in vis[i * V:(i + 1) * V]] for i in range(sweeps)]
+    for prec in (G.PREC_FP64, G.PREC_3XTF32):
+        st2, _, _ = run(G, ctx, N, 0, prec, ctrl=G.CTRL_REPLAY, chi_max=32, chi_init=4)
+        E = []
+        for t in range(sweeps):
+            st2.set_schedule(sched[t])
+            r, v = st2.sweep(1)
+            assert [x.k for x in v] == sched[t]
+            E.append(r[0].E)
+        st2.close()
+        if prec == G.PREC_FP64:
+            assert E == [r.E for r in recs]
+        else:
+            assert all(abs(a - b.E) / N <= 1e-8 for a, b in zip(E, recs))
