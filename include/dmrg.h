@@ -164,7 +164,15 @@ const char *dmrg_status_string(dmrg_status s);
 /* Tuning knobs of a context (no counterpart in the paper): "tc_force" (1: use
  * the tensor cores even for tiny products), "tc_min_work" (multiply-adds
  * below which 3xTF32 requests run on the FP64 kernel), "tc_bn" (0, 128 or
- * 256: tile width of the tensor-core GEMM, 0 = heuristic), "prof_mask"
+ * 256: tile width of the tensor-core GEMM, 0 = heuristic), "tc_split_kb"
+ * (tensor-core GEMM: most 32-wide blocks of the 3 K split products one FP32
+ * accumulator sums, 8; beyond, K is split and the slices added in FP64;
+ * 0 = never split), "gjac32" (1: grouped block FP32 Jacobi, 0: the older
+ * kernels), "gjac_nv" / "gjac_groups" (its vectors per block pair, 16 or
+ * 32, and groups per CTA, 1-4; 0 = by size / autotuner), "jacobi64_gram"
+ * (1: FP64 Jacobi on the grouped kernel, 0: one warp per pair),
+ * "jacobi64_precond" (1: FP32 preconditioning pass before the FP64
+ * Jacobi), "prof_mask"
  * (bit k set: dmrg_profile brackets the launches of kind k; default all 9
  * kinds; bracketing one kind keeps the events off every other launch),
  * "mlp_eps_target" (truncation-error target of the k_star label, 1e-5),
@@ -306,13 +314,16 @@ dmrg_status svd_truncate_batched(dmrg_ctx *ctx, int prec, int batch, const int *
  * 3xTF32 tensor-core GEMM with 128- and 256-column tiles; the choice applies
  * to the shape's bucket (ceil log2 of each dimension).  The result bits do
  * not depend on the tile width.  dmrg_autotune_svd: for each n (host array),
- * the mixed-precision SVD of an n x n matrix with the blocked FP32 Jacobi's
- * block-pair target in {24, 48, 96, 152} and 1 or 2 inner sweeps; applies to
- * the (ceil log2 n, ceil log2 n) bucket.  Inputs are generated on the device;
+ * the mixed-precision SVD of an n x n matrix: with the grouped FP32 Jacobi
+ * (option "gjac32", default) its block-pair width (16 or 32 vectors) and
+ * groups per CTA (1, 2 or 4), else the older blocked kernel's block-pair
+ * target in {24, 48, 96, 152} and 1 or 2 inner sweeps; applies to the
+ * (ceil log2 n, ceil log2 n) bucket.  Inputs are generated on the device;
  * `reps` timed calls follow one warm-up call.  These calls allocate and free
  * device memory and synchronise.  dmrg_autotune_save / _load write and read
- * the tables as JSON (format "dmrg-autotune-1"); load replaces the tables and
- * returns DMRG_EINVAL for a file that is missing or not in that format.
+ * the tables as JSON (format "dmrg-autotune-2"; load also reads format 1)
+ * and load replaces the tables; DMRG_EINVAL for a file that is missing or
+ * in neither format.
  * dmrg_autotune_entries: number of GEMM (which = 0) or SVD (1) entries. */
 dmrg_status dmrg_autotune_gemm(dmrg_ctx *ctx, int n_shapes, const int *M, const int *N, const int *K, int reps);
 dmrg_status dmrg_autotune_svd(dmrg_ctx *ctx, int n_sizes, const int *n, int reps);

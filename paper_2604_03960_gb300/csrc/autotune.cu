@@ -58,6 +58,19 @@ int tune_lookup_bn(const dmrg_ctx *ctx, int M, int N, int K)
     return 0;
 }
 
+bool tune_lookup_gjac(const dmrg_ctx *ctx, int r, int l, int *nv, int *groups)
+{
+    if (ctx->tune_svd.empty()) return false;
+    const int lr = clog2(r), ll = clog2(l);
+    for (const auto &e : ctx->tune_svd)
+        if (e.lr == lr && e.ll == ll && e.nv > 0) {
+            *nv = e.nv;
+            *groups = e.groups;
+            return true;
+        }
+    return false;
+}
+
 bool tune_lookup_svd(const dmrg_ctx *ctx, int r, int l, int *pairs, int *inner)
 {
     if (ctx->tune_svd.empty()) return false;
@@ -151,36 +164,61 @@ extern "C" dmrg_status dmrg_autotune_svd(dmrg_ctx *ctx, int n_sizes, const int *
         k_fill_uniform<<<ctx->num_sms, 256, 0, ctx->stream>>>(A, (long long)nm, 0x5678ULL + i); DMRG_COUNT_LAUNCH();
         DMRG_CUDA(cudaGetLastError());
         const int saved_prec = ctx->svd_prec, saved_pairs = ctx->bjac_pairs, saved_inner = ctx->bjac_inner;
+        const int saved_nv = ctx->gjac_nv, saved_groups = ctx->gjac_groups;
         const auto saved_table = ctx->tune_svd;
         ctx->tune_svd.clear();   // time the candidates themselves, not an earlier decision
         ctx->svd_prec = 1;
         float best = 0.f;
-        int best_p = saved_pairs, best_i = saved_inner;
+        int best_p = saved_pairs, best_i = saved_inner, best_nv = 0, best_g = 0;
         dmrg_status st = DMRG_OK;
-        for (int pi : kPairs)
-            for (int ii : kInner) {
-                if (st != DMRG_OK) break;
-                ctx->bjac_pairs = pi;
-                ctx->bjac_inner = ii;
-                float ms = 0.f;
-                st = time_ms(ctx, reps, [&]() {
-                    int k;
-                    double S, err;
-                    dmrg_status e = svd_truncate(ctx, A, m, m, m, 0.0, U, s, Vt, &k, &S, &err);
-                    return e == DMRG_ENOCONV ? DMRG_OK : e;
-                }, &ms);
-                if (st == DMRG_OK && (best == 0.f || ms < best)) {
-                    best = ms;
-                    best_p = pi;
-                    best_i = ii;
+        auto timed = [&](float *ms) {
+            return time_ms(ctx, reps, [&]() {
+                int k;
+                double S, err;
+                dmrg_status e = svd_truncate(ctx, A, m, m, m, 0.0, U, s, Vt, &k, &S, &err);
+                return e == DMRG_ENOCONV ? DMRG_OK : e;
+            }, ms);
+        };
+        if (ctx->gjac32) {
+            // grouped kernel: vectors per block pair x groups per CTA
+            static const int kNv[] = {16, 32};
+            static const int kGroups[] = {1, 2, 4};
+            for (int nvc : kNv)
+                for (int gc : kGroups) {
+                    if (st != DMRG_OK) break;
+                    ctx->gjac_nv = nvc;
+                    ctx->gjac_groups = gc;
+                    float ms = 0.f;
+                    st = timed(&ms);
+                    if (st == DMRG_OK && (best == 0.f || ms < best)) {
+                        best = ms;
+                        best_nv = nvc;
+                        best_g = gc;
+                    }
                 }
-            }
+        } else {
+            for (int pi : kPairs)
+                for (int ii : kInner) {
+                    if (st != DMRG_OK) break;
+                    ctx->bjac_pairs = pi;
+                    ctx->bjac_inner = ii;
+                    float ms = 0.f;
+                    st = timed(&ms);
+                    if (st == DMRG_OK && (best == 0.f || ms < best)) {
+                        best = ms;
+                        best_p = pi;
+                        best_i = ii;
+                    }
+                }
+        }
         ctx->svd_prec = saved_prec;
         ctx->bjac_pairs = saved_pairs;
         ctx->bjac_inner = saved_inner;
+        ctx->gjac_nv = saved_nv;
+        ctx->gjac_groups = saved_groups;
         ctx->tune_svd = saved_table;
         if (st != DMRG_OK) return st;
-        dmrg_ctx::TuneSvd e{clog2(m), clog2(m), best_p, best_i, best};
+        dmrg_ctx::TuneSvd e{clog2(m), clog2(m), best_p, best_i, best, best_nv, best_g};
         auto it = std::find_if(ctx->tune_svd.begin(), ctx->tune_svd.end(), [&](const dmrg_ctx::TuneSvd &x) {
             return x.lr == e.lr && x.ll == e.ll;
         });
@@ -213,7 +251,7 @@ extern "C" dmrg_status dmrg_autotune_save(const dmrg_ctx *ctx, const char *path)
     std::string dev = cudaGetDeviceProperties(&prop, ctx->device) == cudaSuccess ? prop.name : "unknown";
     for (auto &ch : dev)
         if (ch == '"' || ch == '\\') ch = ' ';
-    std::fprintf(f, "{\"format\": \"dmrg-autotune-1\", \"device\": \"%s\",\n \"gemm\": [\n", dev.c_str());
+    std::fprintf(f, "{\"format\": \"dmrg-autotune-2\", \"device\": \"%s\",\n \"gemm\": [\n", dev.c_str());
     for (size_t i = 0; i < ctx->tune_gemm.size(); ++i) {
         const auto &e = ctx->tune_gemm[i];
         std::fprintf(f, "  {\"lm\": %d, \"ln\": %d, \"lk\": %d, \"bn\": %d, \"ms128\": %.6g, \"ms256\": %.6g}%s\n", e.lm,
@@ -222,8 +260,8 @@ extern "C" dmrg_status dmrg_autotune_save(const dmrg_ctx *ctx, const char *path)
     std::fprintf(f, " ],\n \"svd\": [\n");
     for (size_t i = 0; i < ctx->tune_svd.size(); ++i) {
         const auto &e = ctx->tune_svd[i];
-        std::fprintf(f, "  {\"lr\": %d, \"ll\": %d, \"pairs\": %d, \"inner\": %d, \"ms\": %.6g}%s\n", e.lr, e.ll, e.pairs,
-                     e.inner, e.ms, i + 1 < ctx->tune_svd.size() ? "," : "");
+        std::fprintf(f, "  {\"lr\": %d, \"ll\": %d, \"pairs\": %d, \"inner\": %d, \"ms\": %.6g, \"nv\": %d, \"groups\": %d}%s\n",
+                     e.lr, e.ll, e.pairs, e.inner, e.ms, e.nv, e.groups, i + 1 < ctx->tune_svd.size() ? "," : "");
     }
     std::fprintf(f, " ]}\n");
     const bool ok = std::fclose(f) == 0;
@@ -240,7 +278,7 @@ extern "C" dmrg_status dmrg_autotune_load(dmrg_ctx *ctx, const char *path)
     char line[512];
     bool format_ok = false;
     while (std::fgets(line, sizeof line, f)) {
-        if (std::strstr(line, "\"dmrg-autotune-1\"")) format_ok = true;
+        if (std::strstr(line, "\"dmrg-autotune-1\"") || std::strstr(line, "\"dmrg-autotune-2\"")) format_ok = true;
         dmrg_ctx::TuneGemm e{};
         dmrg_ctx::TuneSvd t{};
         if (std::sscanf(line, " {\"lm\": %d, \"ln\": %d, \"lk\": %d, \"bn\": %d, \"ms128\": %f, \"ms256\": %f", &e.lm,
@@ -250,6 +288,14 @@ extern "C" dmrg_status dmrg_autotune_load(dmrg_ctx *ctx, const char *path)
         } else if (std::sscanf(line, " {\"lr\": %d, \"ll\": %d, \"pairs\": %d, \"inner\": %d, \"ms\": %f", &t.lr, &t.ll,
                                &t.pairs, &t.inner, &t.ms) == 5) {
             if (t.pairs < 1 || t.inner < 1 || t.inner > 8) { std::fclose(f); return DMRG_EINVAL; }
+            // format 2 adds the grouped kernel's choice (absent in format 1: none)
+            const char *q = std::strstr(line, "\"nv\":");
+            if (q && std::sscanf(q, "\"nv\": %d, \"groups\": %d", &t.nv, &t.groups) == 2) {
+                if ((t.nv != 0 && t.nv != 16 && t.nv != 32) || t.groups < 0 || t.groups > 4) {
+                    std::fclose(f);
+                    return DMRG_EINVAL;
+                }
+            }
             v.push_back(t);
         }
     }

@@ -113,6 +113,8 @@ struct dmrg_ctx {
     int tc_bn_override = 0;      // force a tile width (autotuner / tests)
     int tc_force = 0;            // use the tensor cores even for tiny products
     double tc_min_work = 4194304.0;   // M*N*K below which the FP64 kernel is used
+    int tc_split_kb = 8;         // tensor-core GEMM: at most this many 32-wide K' blocks per FP32 accumulator
+                                 // (split K with an FP64 reduction beyond; 0 = never split)
     int prof = 0;
     int prof_mask = 0x1ff;       // kinds bracketed by events while profiling (bit k = kind k)
     dmrg::ProfSlot prof_slot[dmrg::PROF_KINDS];
@@ -125,7 +127,9 @@ struct dmrg_ctx {
     // shape bucket, blocked-Jacobi grid target and inner sweeps per SVD
     // size bucket; buckets are ceil(log2) of each dimension
     struct TuneGemm { int lm, ln, lk, bn; float ms128, ms256; };
-    struct TuneSvd { int lr, ll, pairs, inner; float ms; };
+    // SVD bucket: the old blocked kernel's block-pair target and inner sweeps,
+    // the grouped kernel's vectors per block pair (nv) and groups per CTA
+    struct TuneSvd { int lr, ll, pairs, inner; float ms; int nv, groups; };
     std::vector<TuneGemm> tune_gemm;
     std::vector<TuneSvd> tune_svd;
     dmrg::DevBuf work4;          // batched SVD workspace
@@ -136,6 +140,11 @@ struct dmrg_ctx {
     int bjac_gram = 1;           // blocked FP32 Jacobi: inner sweep in Gram form (k_bjac32g)
     double jacobi32_floor = 1.1920928955078125e-07;   // FP32 Jacobi: vectors below this x |A|_F take no rotation
     int gbj_min_r = 0;           // FP32 Jacobi: Gram-block cooperative form from this many vectors on (0 = off)
+    int gjac32 = 1;              // FP32 Jacobi: grouped block kernel (gjacobi.cu)
+    int gjac_nv = 0;             // ... vectors per block pair (16, 32; 0 = by size)
+    int gjac_groups = 0;         // ... max groups per CTA (0 = by shared memory)
+    int jacobi64_gram = 1;       // FP64 Jacobi: grouped block kernel (0: one warp per pair)
+    int jacobi64_precond = 1;    // FP64 Jacobi: FP32 preconditioning pass
     double batched_floor32 = 1.1920928955078125e-07;  // FP32 batched SVD: vectors below this x |A|_F do not rotate
     void *pinned_desc = nullptr; // batched SVD descriptors (pinned, read by the H2D copy / graph replays)
     size_t pinned_desc_bytes = 0;
@@ -244,6 +253,7 @@ dmrg_status qr_precondition32(dmrg_ctx *ctx, float *X, int c, int l, void *work)
 // Autotuner table lookups (autotune.cu): 0 / false when the bucket has no entry.
 int tune_lookup_bn(const dmrg_ctx *ctx, int M, int N, int K);
 bool tune_lookup_svd(const dmrg_ctx *ctx, int r, int l, int *pairs, int *inner);
+bool tune_lookup_gjac(const dmrg_ctx *ctx, int r, int l, int *nv, int *groups);
 
 // FP64 strided batched GEMM:
 //   C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n)
@@ -272,10 +282,22 @@ dmrg_status gemm(dmrg_ctx *ctx, int prec, int M, int N, int K, double alpha, con
 
 // One-sided Jacobi SVD of the row-major m x n matrix A (device).  Writes U
 // (m x r), s (r, descending), Vt (r x n), r = min(m,n).  `work` must hold
-// svd_work_bytes(r, max(m,n)).  Convergence flag / sweep count are written
-// to d_info[0] (sweeps, negative if not converged).
+// svd_work_bytes(r, max(m,n)), or svd_work_bytes_base(r, max(m,n)) with
+// precond = 0.  The FP64 sweep count is written to d_info[0] (negative if
+// not converged).  precond: 1 = FP32 preconditioning pass (r >= 64),
+// 0 = none, -1 = the context's choice.
+size_t svd_work_bytes_base(int r, int l);
 dmrg_status svd_jacobi(dmrg_ctx *ctx, const double *A, int m, int n, double *U, double *s, double *Vt,
-                       void *work, int max_sweeps, int *d_info);
+                       void *work, int max_sweeps, int *d_info, int precond = -1);
+
+// Grouped block one-sided Jacobi (gjacobi.cu) on r extended vectors: vector
+// i is X[i*ldx + e], e < l (the Gram part), then X[i*ldx + gv0 + e'], e' < rv
+// (carried along).  nv = 16 or 32 vectors per block pair; max_groups > 0
+// caps the groups per CTA.  sync: 4 words zeroed by the call.
+template <typename T>
+dmrg_status gjac_run(dmrg_ctx *ctx, T *X, int r, int l, int ldx, int gv0, int rv, int max_sweeps, double tol,
+                     double small, const double *F2, unsigned *sync, int *info, const int *r_eff, int nv,
+                     int max_groups);
 
 // FP32 one-sided Jacobi (mixed-precision form), vectors = columns (dir 0) or
 // rows (dir 1) of A; see jacobi.cu.

@@ -101,6 +101,7 @@ struct MixDesc {
     int nin, nout, in_ny, out_ny;
     long long in_sx, in_sy, in_sa, out_sx, out_sy, out_sa;
     int An, Bn;
+    int f32;        // 1: multiply-adds in FP32 (the mixed form's H_eff, whose GEMMs are FP32-accurate)
 };
 
 // out[channel o][a][b] = sum_i C[o][i] in[channel i][a][b]; b is unit stride.
@@ -158,7 +159,16 @@ __global__ void __launch_bounds__(kMixThreads) k_mix(const double *__restrict__ 
             const int x = c / d.in_ny, y = c % d.in_ny;
             xs[c][threadIdx.x] = ok ? in[x * d.in_sx + y * d.in_sy + a * d.in_sa + b] : 0.0;
         }
-        if (ok) {
+        if (ok && d.f32) {
+            // FP64 lanes are scarce on this part: the mixed form mixes in FP32
+            for (int o = 0; o < d.nout; ++o) {
+                float acc = 0.f;
+                for (int q = rowptr[o]; q < rowptr[o + 1]; ++q)
+                    acc = fmaf((float)val[q], (float)xs[col[q]][threadIdx.x], acc);
+                const int x = o / d.out_ny, y = o % d.out_ny;
+                out[x * d.out_sx + y * d.out_sy + a * d.out_sa + b] = (double)acc;
+            }
+        } else if (ok) {
             for (int o = 0; o < d.nout; ++o) {
                 double acc = 0.0;
                 for (int q = rowptr[o]; q < rowptr[o + 1]; ++q) acc = fma(val[q], xs[col[q]][threadIdx.x], acc);
@@ -416,6 +426,7 @@ dmrg_status heff_apply_dev(dmrg_ctx *ctx, int prec, int D, int cl, int cr, const
     const long long n4 = 4LL * cr;
     DMRG_TRY(gemm(ctx, prec, D * cl, (int)n4, cl, 1.0, L, cl, 1, 0, x, n4, 1, 0, 0.0, X, n4, 1, 0, 1));
     MixDesc md;
+    md.f32 = prec != DMRG_PREC_FP64;
     md.nin = 4 * D; md.nout = 4 * D; md.in_ny = 4; md.out_ny = 4;
     md.in_sx = (long long)cl * n4; md.in_sy = cr; md.in_sa = n4;
     md.out_sx = cr; md.out_sy = (long long)D * cr; md.out_sa = 4LL * D * cr;
@@ -432,6 +443,7 @@ dmrg_status env_left_dev(dmrg_ctx *ctx, int prec, int D, int cl, int ck, const d
     const long long n2 = 2LL * ck;
     DMRG_TRY(gemm(ctx, prec, D * cl, (int)n2, cl, 1.0, L, cl, 1, 0, A, n2, 1, 0, 0.0, T1, n2, 1, 0, 1));
     MixDesc md;
+    md.f32 = prec != DMRG_PREC_FP64;
     md.nin = 2 * D; md.nout = 2 * D; md.in_ny = 2; md.out_ny = 2;
     md.in_sx = (long long)cl * n2; md.in_sy = ck; md.in_sa = n2;
     md.out_sx = (long long)cl * n2; md.out_sy = ck; md.out_sa = n2;
@@ -449,6 +461,7 @@ dmrg_status env_right_dev(dmrg_ctx *ctx, int prec, int D, int ck, int cr, const 
     DMRG_TRY(gemm(ctx, prec, 2 * ck, cr, cr, 1.0, B, cr, 1, 0, Rt, cr, 1, (long long)cr * cr, 0.0, T1, cr, 1,
                   (long long)2 * ck * cr, D));
     MixDesc md;
+    md.f32 = prec != DMRG_PREC_FP64;
     md.nin = 2 * D; md.nout = 2 * D; md.in_ny = 2; md.out_ny = 2;
     md.in_sx = (long long)2 * ck * cr; md.in_sy = cr; md.in_sa = 2LL * cr;
     md.out_sx = (long long)2 * ck * cr; md.out_sy = cr; md.out_sa = 2LL * cr;
@@ -621,6 +634,24 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         ctx->svd_prec = (int)value;
         return DMRG_OK;
     }
+    if (!std::strcmp(name, "gjac32")) { ctx->gjac32 = value != 0.0; return DMRG_OK; }
+    if (!std::strcmp(name, "tc_split_kb")) {
+        if (!(value >= 0.0 && value <= 1e6) || value != (double)(int)value) return DMRG_EINVAL;
+        ctx->tc_split_kb = (int)value;
+        return DMRG_OK;
+    }
+    if (!std::strcmp(name, "gjac_nv")) {
+        if (value != 0.0 && value != 16.0 && value != 32.0) return DMRG_EINVAL;
+        ctx->gjac_nv = (int)value;
+        return DMRG_OK;
+    }
+    if (!std::strcmp(name, "gjac_groups")) {
+        if (!(value >= 0.0 && value <= 4.0)) return DMRG_EINVAL;
+        ctx->gjac_groups = (int)value;
+        return DMRG_OK;
+    }
+    if (!std::strcmp(name, "jacobi64_gram")) { ctx->jacobi64_gram = value != 0.0; return DMRG_OK; }
+    if (!std::strcmp(name, "jacobi64_precond")) { ctx->jacobi64_precond = value != 0.0; return DMRG_OK; }
     if (!std::strcmp(name, "prof_mask")) {
         if (!(value >= 1.0 && value <= (double)((1 << PROF_KINDS) - 1)) || value != (double)(int)value)
             return DMRG_EINVAL;

@@ -18,7 +18,19 @@ namespace {
 constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4, NT = 256;
 
 // T = double: the FP64 path; T = float: FP32 arithmetic on FP64 operands for
-// the small products of the mixed form (same precision class as 3xTF32).
+// the small products of the mixed form.  In the FP32 case each BK-long
+// partial sum is added into a compensated pair (hi, lo) by Knuth's TwoSum, so
+// the accumulation error does not grow with K: the result carries the
+// rounding of the FP32 operands and of BK-term sums only.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
+{
+    const float s = hi + x;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo += err;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_gemm_t(int M, int N, int K, double alpha, const double *__restrict__ A,
                                                long long sAm, long long sAk, long long sAb,
@@ -35,10 +47,18 @@ __global__ void __launch_bounds__(NT) k_gemm_t(int M, int N, int K, double alpha
     B += (long long)bz * sBb;
     C += (long long)bz * sCb;
     T acc[TM][TN];
+    constexpr bool kComp = sizeof(T) == 4;
+    float chi[kComp ? TM : 1][kComp ? TN : 1], clo[kComp ? TM : 1][kComp ? TN : 1];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = (T)0;
+    if (kComp) {
+#pragma unroll
+        for (int i = 0; i < (kComp ? TM : 1); ++i)
+#pragma unroll
+            for (int j = 0; j < (kComp ? TN : 1); ++j) chi[i][j] = clo[i][j] = 0.f;
+    }
     const bool a_kfast = (sAk == 1);
     const bool b_nfast = (sBn == 1);
     for (int k0 = 0; k0 < K; k0 += BK) {
@@ -71,6 +91,15 @@ __global__ void __launch_bounds__(NT) k_gemm_t(int M, int N, int K, double alpha
 #pragma unroll
                 for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
+        if (kComp) {
+#pragma unroll
+            for (int i = 0; i < (kComp ? TM : 1); ++i)
+#pragma unroll
+                for (int j = 0; j < (kComp ? TN : 1); ++j) {
+                    two_sum_acc(chi[i][j], clo[i][j], (float)acc[i][j]);
+                    acc[i][j] = (T)0;
+                }
+        }
         __syncthreads();
     }
 #pragma unroll
@@ -82,7 +111,9 @@ __global__ void __launch_bounds__(NT) k_gemm_t(int M, int N, int K, double alpha
             int gn = n0 + tx + 16 * j;
             if (gn >= N) continue;
             double *c = C + (long long)gm * sCm + (long long)gn * sCn;
-            double v = alpha * (double)acc[i][j];
+            const double sum = kComp ? (double)chi[kComp ? i : 0][kComp ? j : 0] + (double)clo[kComp ? i : 0][kComp ? j : 0]
+                                     : (double)acc[i][j];
+            double v = alpha * sum;
             if (beta != 0.0) v += beta * *c;
             *c = v;
         }

@@ -127,11 +127,15 @@ struct TcCfg {
     static constexpr uint32_t TMEM_COLS = BN;   // power of two >= 32
 };
 
+// Split K: blockIdx.z = batch index * nsl + slice; a slice takes K blocks
+// [slice * kps, min(nk, (slice + 1) * kps)).  With P set, each slice writes its
+// FP32 partial sums (as FP64) to P[slice][b][m][n] and k_tc_reduce adds the
+// slices in FP64, so no FP32 accumulator sums more than kps * 32 terms.
 template <int BN>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int nk,
-              double alpha, double beta, double *__restrict__ C, long long sCm, long long sCn, long long sCb,
-              int *status)
+              int kps, int nsl, double *__restrict__ P, double alpha, double beta, double *__restrict__ C,
+              long long sCm, long long sCn, long long sCb, int *status)
 {
     using Cfg = TcCfg<BN>;
     extern __shared__ uint8_t smem_raw[];
@@ -148,7 +152,9 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t done = bar_base + 8u * (2 * STAGES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * BN, bz = blockIdx.z;
+    const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * BN, bz = blockIdx.z / nsl, sl = blockIdx.z % nsl;
+    const int kb0 = sl * kps;
+    const int nkl = max(0, min(nk, kb0 + kps) - kb0);       // K blocks of this slice
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -177,7 +183,7 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0 && lane == 0) {
         // TMA producer
         int issued = 0;
-        for (int kb = 0; kb < nk; ++kb) {
+        for (int kb = 0; kb < nkl; ++kb) {
             const int s = kb % STAGES;
             const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
             if (*abort_flag || !mbar_wait(empty(s), ph ^ 1u)) {
@@ -186,8 +192,8 @@ __global__ void __launch_bounds__(128, 1)
             }
             mbar_expect_tx(full(s), Cfg::STAGE);
             const uint32_t a_dst = base + s * Cfg::STAGE;
-            tma_load_3d(a_dst, &tmA, full(s), kb * TBK, m0, bz);
-            tma_load_3d(a_dst + Cfg::A_BYTES, &tmB, full(s), kb * TBK, n0, bz);
+            tma_load_3d(a_dst, &tmA, full(s), (kb0 + kb) * TBK, m0, bz);
+            tma_load_3d(a_dst + Cfg::A_BYTES, &tmB, full(s), (kb0 + kb) * TBK, n0, bz);
             issued = kb + 1;
         }
         *issued_s = issued;
@@ -197,7 +203,7 @@ __global__ void __launch_bounds__(128, 1)
         const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                ((uint32_t)(TBM >> 4) << 24);
         int consumed = 0;
-        for (int kb = 0; kb < nk; ++kb) {
+        for (int kb = 0; kb < nkl; ++kb) {
             const int s = kb % STAGES;
             const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
             if (*abort_flag || !mbar_wait(full(s), ph)) {
@@ -223,10 +229,12 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     __syncwarp();
     if (!ok) *abort_flag = 1;
-    if (!*abort_flag && nk > 0) {
+    if (!*abort_flag && nkl > 0) {
         const int row = warp * 32 + lane;
         const int gm = m0 + row;
         double *crow = C + (long long)bz * sCb + (long long)gm * sCm;
+        const long long nbatch = gridDim.z / nsl;
+        double *prow = P ? P + (((long long)sl * nbatch + bz) * M + gm) * (long long)N : nullptr;
 #pragma unroll 1
         for (int c = 0; c < BN / 32; ++c) {
             uint32_t r[32];
@@ -236,10 +244,14 @@ __global__ void __launch_bounds__(128, 1)
                 for (int j = 0; j < 32; ++j) {
                     const int gn = n0 + c * 32 + j;
                     if (gn < N) {
-                        double *p = crow + (long long)gn * sCn;
-                        double v = alpha * (double)__uint_as_float(r[j]);
-                        if (beta != 0.0) v += beta * *p;
-                        *p = v;
+                        if (prow) {
+                            prow[gn] = (double)__uint_as_float(r[j]);
+                        } else {
+                            double *p = crow + (long long)gn * sCn;
+                            double v = alpha * (double)__uint_as_float(r[j]);
+                            if (beta != 0.0) v += beta * *p;
+                            *p = v;
+                        }
                     }
                 }
             }
@@ -258,6 +270,25 @@ __global__ void __launch_bounds__(128, 1)
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS)
                      : "memory");
+    }
+}
+
+// C[b][m][n] = alpha * sum_s P[s][b][m][n] + beta * C[b][m][n], the slices
+// added in order in FP64 (deterministic)
+__global__ void k_tc_reduce(const double *__restrict__ P, int nsl, int batch, int M, int N, double alpha, double beta,
+                            double *__restrict__ C, long long sCm, long long sCn, long long sCb)
+{
+    const long long per = (long long)M * N, total = per * batch, slice = total;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int q = 0; q < nsl; ++q) a += P[q * slice + e];
+        const long long b = e / per, mn = e % per;
+        const int m = (int)(mn / N), n = (int)(mn % N);
+        double *c = C + b * sCb + (long long)m * sCm + (long long)n * sCn;
+        double v = alpha * a;
+        if (beta != 0.0) v += beta * *c;
+        *c = v;
     }
 }
 
@@ -331,7 +362,7 @@ bool make_map(CUtensorMap *map, const float *base, int K3, int rows, int batch, 
 
 template <int BN>
 dmrg_status launch_tc(dmrg_ctx *ctx, const float *Ah, const float *Bh, int M, int N, int K3, int batch, double alpha,
-                      double beta, double *C, long long sCm, long long sCn, long long sCb)
+                      double beta, double *C, long long sCm, long long sCn, long long sCb, int nsl, double *P)
 {
     CUtensorMap ma, mb;
     if (!make_map(&ma, Ah, K3, M, batch, TBM) || !make_map(&mb, Bh, K3, N, batch, BN)) return DMRG_ECUDA;
@@ -340,10 +371,20 @@ dmrg_status launch_tc(dmrg_ctx *ctx, const float *Ah, const float *Bh, int M, in
         DMRG_CUDA(cudaFuncSetAttribute(k_tc_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN>::SMEM));
         attr_set = true;
     }
-    dim3 grid((N + BN - 1) / BN, (M + TBM - 1) / TBM, batch);
+    const int nk = K3 / TBK;
+    const int kps = (nk + nsl - 1) / nsl;
+    dim3 grid((N + BN - 1) / BN, (M + TBM - 1) / TBM, batch * nsl);
     prof_mark(ctx, PROF_TC_GEMM);
-    k_tc_gemm<BN><<<grid, 128, TcCfg<BN>::SMEM, ctx->stream>>>(ma, mb, M, N, K3 / TBK, alpha, beta, C, sCm, sCn, sCb,
-                                                               ctx->d_status); DMRG_COUNT_LAUNCH();
+    k_tc_gemm<BN><<<grid, 128, TcCfg<BN>::SMEM, ctx->stream>>>(ma, mb, M, N, nk, kps, nsl, nsl > 1 ? P : nullptr,
+                                                               alpha, beta, C, sCm, sCn, sCb, ctx->d_status);
+    DMRG_COUNT_LAUNCH();
+    if (nsl > 1) {
+        const long long total = (long long)M * N * batch;
+        long long blocks = (total + 255) / 256;
+        if (blocks > 8LL * ctx->num_sms) blocks = 8LL * ctx->num_sms;
+        k_tc_reduce<<<(int)blocks, 256, 0, ctx->stream>>>(P, nsl, batch, M, N, alpha, beta, C, sCm, sCn, sCb);
+        DMRG_COUNT_LAUNCH();
+    }
     prof_mark(ctx, PROF_TC_GEMM);
     // work of the split product: three TF32 products of the padded shape;
     // bytes: both split operands read once and the FP64 result written once
@@ -401,10 +442,24 @@ dmrg_status gemm_3xtf32(dmrg_ctx *ctx, int M, int N, int K, double alpha, const 
     }
     if (batch > 65535 || (M + TBM - 1) / TBM > 65535) return DMRG_EINVAL;
     const int Kp = (K + 31) / 32 * 32, K3 = 3 * Kp;
+    // split K so that no FP32 accumulator sums more than kSliceKb * 32 of the
+    // K' = 3 Kp products (the slices meet in FP64)
+    const int nk = K3 / TBK;
+    int nsl = 1;
+    if (ctx->tc_split_kb > 0 && nk > ctx->tc_split_kb) {
+        nsl = (nk + ctx->tc_split_kb - 1) / ctx->tc_split_kb;
+        if (nsl > 16) nsl = 16;
+        const int kps = (nk + nsl - 1) / nsl;
+        nsl = (nk + kps - 1) / kps;
+    }
+    if ((long long)batch * nsl > 65535) nsl = 1;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t bytesA = sizeof(float) * (size_t)batch * M * K3, bytesB = sizeof(float) * (size_t)batch * N * K3;
-    DMRG_TRY(ctx->tcbuf.ensure(((bytesA + 255) & ~size_t(255)) + bytesB));
+    const size_t bytesP = nsl > 1 ? sizeof(double) * (size_t)nsl * batch * M * N : 0;
+    DMRG_TRY(ctx->tcbuf.ensure(al(bytesA) + al(bytesB) + bytesP));
     float *Ah = ctx->tcbuf.as<float>();
-    float *Bh = reinterpret_cast<float *>(reinterpret_cast<char *>(Ah) + ((bytesA + 255) & ~size_t(255)));
+    float *Bh = reinterpret_cast<float *>(reinterpret_cast<char *>(Ah) + al(bytesA));
+    double *P = reinterpret_cast<double *>(reinterpret_cast<char *>(Bh) + al(bytesB));
     {
         dim3 g(Kp / 32, (M + 31) / 32, batch);
         k_split3<<<g, dim3(32, 8), 0, ctx->stream>>>(A, sAm, sAk, sAb, M, K, Kp, Ah, 0); DMRG_COUNT_LAUNCH();
@@ -413,8 +468,8 @@ dmrg_status gemm_3xtf32(dmrg_ctx *ctx, int M, int N, int K, double alpha, const 
         DMRG_CUDA(cudaGetLastError());
     }
     const int bn = tc_pick_bn(ctx, M, N, K, batch);
-    if (bn == 128) return launch_tc<128>(ctx, Ah, Bh, M, N, K3, batch, alpha, beta, C, sCm, sCn, sCb);
-    return launch_tc<256>(ctx, Ah, Bh, M, N, K3, batch, alpha, beta, C, sCm, sCn, sCb);
+    if (bn == 128) return launch_tc<128>(ctx, Ah, Bh, M, N, K3, batch, alpha, beta, C, sCm, sCn, sCb, nsl, P);
+    return launch_tc<256>(ctx, Ah, Bh, M, N, K3, batch, alpha, beta, C, sCm, sCn, sCb, nsl, P);
 }
 
 }  // namespace dmrg

@@ -22,11 +22,19 @@
 
 namespace dmrg {
 
-size_t svd_work_bytes(int r, int l)
+size_t svd_work_bytes_base(int r, int l)
 {
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     return al(sizeof(double) * (size_t)r * l) + al(sizeof(double) * (size_t)r * r) + al(sizeof(double) * r) +
            al(sizeof(int) * r) + al(sizeof(unsigned) * 8);
+}
+
+// + the FP32 copy of the extended vectors and two r x r FP64 matrices of the
+// preconditioned FP64 Jacobi
+size_t svd_work_bytes(int r, int l)
+{
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    return svd_work_bytes_base(r, l) + al(sizeof(float) * (size_t)r * (l + r)) + 2 * al(sizeof(double) * (size_t)r * r);
 }
 
 SvdWork svd_work_carve(void *base, int r, int l)
@@ -229,11 +237,11 @@ __global__ void __launch_bounds__(256) k_jac_sweeps(double *__restrict__ X, doub
 }
 
 // nrm[i] = |x_i|, one warp per vector
-__global__ void k_jac_norms(const double *__restrict__ X, int r, int l, double *__restrict__ nrm)
+__global__ void k_jac_norms(const double *__restrict__ X, int r, int l, long long ldx, double *__restrict__ nrm)
 {
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (w >= r) return;
-    const double *x = X + (long long)w * l;
+    const double *x = X + (long long)w * ldx;
     double a = 0.0;
     for (int k = lane; k < l; k += 32) a = fma(x[k], x[k], a);
     a = warp_sum(a);
@@ -259,8 +267,8 @@ __global__ void k_jac_rank(const double *__restrict__ nrm, int r, int *__restric
 // One block per output index c: writes s[c], U[:, c], Vt[c, :] with the sign
 // convention "largest |entry| of U[:, c] positive".
 __global__ void k_jac_out(const double *__restrict__ X, const double *__restrict__ Vm, const double *__restrict__ nrm,
-                          const int *__restrict__ perm, int m, int n, int tr, int r, int l, double *__restrict__ U,
-                          double *__restrict__ s, double *__restrict__ Vt)
+                          const int *__restrict__ perm, int m, int n, int tr, int r, int l, long long ldx,
+                          long long ldv, double *__restrict__ U, double *__restrict__ s, double *__restrict__ Vt)
 {
     __shared__ double sh_v[32];
     __shared__ int sh_i[32];
@@ -270,7 +278,7 @@ __global__ void k_jac_out(const double *__restrict__ X, const double *__restrict
     const double sig = nrm[i];
     const double inv = (sig > 0.0) ? 1.0 / sig : 0.0;
     // U column source: X row i scaled (tr = 0, length m = l) or Vm row i (tr = 1, length m = r)
-    const double *usrc = tr ? (Vm + (long long)i * r) : (X + (long long)i * l);
+    const double *usrc = tr ? (Vm + (long long)i * ldv) : (X + (long long)i * ldx);
     const double uscale = tr ? 1.0 : inv;
     // argmax |u|
     double best = -1.0;
@@ -297,7 +305,7 @@ __global__ void k_jac_out(const double *__restrict__ X, const double *__restrict
     __syncthreads();
     const double sign = (usrc[sh_i[0]] < 0.0) ? -1.0 : 1.0;
     for (int k = threadIdx.x; k < m; k += blockDim.x) U[(long long)k * r + c] = sign * uscale * usrc[k];
-    const double *vsrc = tr ? (X + (long long)i * l) : (Vm + (long long)i * r);
+    const double *vsrc = tr ? (X + (long long)i * ldx) : (Vm + (long long)i * ldv);
     const double vscale = tr ? inv : 1.0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) Vt[(long long)c * n + k] = sign * vscale * vsrc[k];
 }
@@ -905,8 +913,8 @@ __global__ void k_gather_unit(const float *__restrict__ X, const double *__restr
 
 }  // namespace
 
-dmrg_status svd_jacobi(dmrg_ctx *ctx, const double *A, int m, int n, double *U, double *s, double *Vt, void *work,
-                       int max_sweeps, int *d_info)
+static dmrg_status svd_jacobi_scalar(dmrg_ctx *ctx, const double *A, int m, int n, double *U, double *s, double *Vt,
+                                     void *work, int max_sweeps, int *d_info)
 {
     if (m <= 0 || n <= 0) return DMRG_EINVAL;
     const int tr = (m < n);
@@ -959,9 +967,145 @@ dmrg_status svd_jacobi(dmrg_ctx *ctx, const double *A, int m, int n, double *U, 
     prof_count(ctx, PROF_JACOBI64, 4.0 * l * (double)l * r + 8.0 * l * (double)r * r + 9.0 * (double)r * r * r,
                8.0 * ((double)r * l + (double)r * r) * 2.0);
     DMRG_CUDA(cudaGetLastError());
-    k_jac_norms<<<(r * 32 + 255) / 256, 256, 0, st>>>(X, r, l, w.nrm); DMRG_COUNT_LAUNCH();
+    k_jac_norms<<<(r * 32 + 255) / 256, 256, 0, st>>>(X, r, l, l, w.nrm); DMRG_COUNT_LAUNCH();
     k_jac_rank<<<(r + 255) / 256, 256, 0, st>>>(w.nrm, r, w.perm); DMRG_COUNT_LAUNCH();
-    k_jac_out<<<r, 256, 0, st>>>(X, Vm, w.nrm, w.perm, m, n, tr, r, l, U, s, Vt); DMRG_COUNT_LAUNCH();
+    k_jac_out<<<r, 256, 0, st>>>(X, Vm, w.nrm, w.perm, m, n, tr, r, l, l, r, U, s, Vt); DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
+
+namespace {
+
+int grid_ln(long long n, int num_sms)
+{
+    long long b = (n + 255) / 256;
+    if (b > 4LL * num_sms) b = 4LL * num_sms;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// Extended vectors for the grouped Jacobi: row i of Xe (row stride ldx) is
+// [theta column i (tr = 0) or row i (tr = 1), length l | row i of the r x r
+// identity at offset l], in T.
+template <typename T>
+__global__ void k_gj_load(const double *__restrict__ A, int m, int n, int tr, int r, int l, int ldx,
+                          T *__restrict__ Xe, int with_v)
+{
+    __shared__ double tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    if (!tr) {
+        // vectors are the columns of A: Xe[i][j] = A[j][i], i < n = r, j < m = l
+        for (int yy = threadIdx.y; yy < 32; yy += 8) {
+            int row = by + yy, col = bx + threadIdx.x;
+            tile[yy][threadIdx.x] = (row < m && col < n) ? A[(long long)row * n + col] : 0.0;
+        }
+        __syncthreads();
+        for (int yy = threadIdx.y; yy < 32; yy += 8) {
+            int i = bx + yy, j = by + threadIdx.x;
+            if (i < r && j < l) Xe[(long long)i * ldx + j] = (T)tile[threadIdx.x][yy];
+        }
+    } else {
+        for (int yy = threadIdx.y; yy < 32; yy += 8) {
+            int i = by + yy, j = bx + threadIdx.x;
+            if (i < r && j < l) Xe[(long long)i * ldx + j] = (T)A[(long long)i * n + j];
+        }
+    }
+    if (with_v) {
+        // the grid covers at least r x r
+        for (int yy = threadIdx.y; yy < 32; yy += 8) {
+            int i = by + yy, j = bx + threadIdx.x;
+            if (i < r && j < r) Xe[(long long)i * ldx + l + j] = (i == j) ? (T)1 : (T)0;
+        }
+    }
+}
+
+// Q[i][j] = (double) second part of FP32 extended row i (the rows of V^T)
+__global__ void k_gj_take_q(const float *__restrict__ X32, int r, int l, int ldx, double *__restrict__ Q)
+{
+    const long long total = (long long)r * r;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / r), j = (int)(e % r);
+        Q[e] = (double)X32[(long long)i * ldx + l + j];
+    }
+}
+
+// second part of FP64 extended row i = row i of Q
+__global__ void k_gj_put_q(const double *__restrict__ Q, int r, int l, int ldx, double *__restrict__ Xe)
+{
+    const long long total = (long long)r * r;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / r), j = (int)(e % r);
+        Xe[(long long)i * ldx + l + j] = Q[e];
+    }
+}
+
+}  // namespace
+
+// FP64 one-sided Jacobi SVD on the grouped block kernel.
+//  - The vectors are extended by the rows of V^T (the identity at the start),
+//    so the rotations that orthogonalise them also accumulate V.
+//  - With precond (r >= 64): a first pass runs the same iteration in FP32 on
+//    an FP32 copy (rotate while a cosine exceeds 1e-5).  Its accumulated
+//    V32^T is made orthogonal to FP64 precision by two Newton-Schulz steps
+//    Q <- (3 I - Q Q^T) Q / 2, and the FP64 iteration starts from the
+//    vectors Q X and V^T = Q: nearly orthogonal already, they converge in two
+//    or three FP64 sweeps.  The FP64 result does not depend on the FP32 pass
+//    beyond its starting point: the stopping rule is the FP64 one.
+dmrg_status svd_jacobi(dmrg_ctx *ctx, const double *A, int m, int n, double *U, double *s, double *Vt, void *work,
+                       int max_sweeps, int *d_info, int precond)
+{
+    if (m <= 0 || n <= 0) return DMRG_EINVAL;
+    if (!ctx->jacobi64_gram) return svd_jacobi_scalar(ctx, A, m, n, U, s, Vt, work, max_sweeps, d_info);
+    const int tr = (m < n);
+    const int r = tr ? m : n, l = tr ? n : m;
+    const int ldx = l + r;
+    SvdWork w = svd_work_carve(work, r, l);
+    double *Xe = w.X;                      // r x (l + r): spans the X and Vm slots of the base layout
+    cudaStream_t st = ctx->stream;
+    unsigned *sync = w.sync;
+    double *F2 = reinterpret_cast<double *>(w.sync + 4);
+    int *info32 = reinterpret_cast<int *>(w.sync + 6);
+    k_frob2<<<1, 1024, 0, st>>>(A, (long long)m * n, F2); DMRG_COUNT_LAUNCH();
+    const int big = l > r ? l : r;
+    const dim3 lgrid((big + 31) / 32, (big + 31) / 32);
+    const double tol = (double)(l > 16 ? l : 16) * 2.220446049250313e-16;
+    const double small = tol;
+    const int nv = r <= 128 ? 32 : 16;
+    if (precond < 0) precond = ctx->jacobi64_precond;
+    prof_mark(ctx, PROF_JACOBI64);
+    if (precond && r >= 64) {
+        auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+        char *p = static_cast<char *>(work) + svd_work_bytes_base(r, l);
+        float *X32 = reinterpret_cast<float *>(p); p += al(sizeof(float) * (size_t)r * ldx);
+        double *Q = reinterpret_cast<double *>(p); p += al(sizeof(double) * (size_t)r * r);
+        double *T = reinterpret_cast<double *>(p);
+        k_gj_load<float><<<lgrid, dim3(32, 8), 0, st>>>(A, m, n, tr, r, l, ldx, X32, 1); DMRG_COUNT_LAUNCH();
+        DMRG_CUDA(cudaGetLastError());
+        DMRG_TRY(gjac_run<float>(ctx, X32, r, l, ldx, l, r, max_sweeps, 1.0e-5, ctx->jacobi32_floor, F2, sync, info32,
+                                 nullptr, nv, 0));
+        k_gj_take_q<<<grid_ln((long long)r * r, ctx->num_sms), 256, 0, st>>>(X32, r, l, ldx, Q); DMRG_COUNT_LAUNCH();
+        for (int it = 0; it < 2; ++it) {
+            // T = Q Q^T, then Q <- 1.5 Q - 0.5 T Q (into X32's FP64-sized slot would alias; use Xe as scratch)
+            DMRG_TRY(gemm_f64(st, r, r, r, 1.0, Q, r, 1, 0, Q, 1, r, 0, 0.0, T, r, 1, 0, 1));
+            DMRG_CUDA(cudaMemcpyAsync(Xe, Q, sizeof(double) * (size_t)r * r, cudaMemcpyDeviceToDevice, st));
+            DMRG_TRY(gemm_f64(st, r, r, r, -0.5, T, r, 1, 0, Q, r, 1, 0, 1.5, Xe, r, 1, 0, 1));
+            DMRG_CUDA(cudaMemcpyAsync(Q, Xe, sizeof(double) * (size_t)r * r, cudaMemcpyDeviceToDevice, st));
+        }
+        // first part of the FP64 vectors: Q op(A), op(A) the r x l matrix of vectors
+        const long long sBk = tr ? n : 1, sBn = tr ? 1 : n;
+        DMRG_TRY(gemm_f64(st, r, l, r, 1.0, Q, r, 1, 0, A, sBk, sBn, 0, 0.0, Xe, ldx, 1, 0, 1));
+        k_gj_put_q<<<grid_ln((long long)r * r, ctx->num_sms), 256, 0, st>>>(Q, r, l, ldx, Xe); DMRG_COUNT_LAUNCH();
+    } else {
+        k_gj_load<double><<<lgrid, dim3(32, 8), 0, st>>>(A, m, n, tr, r, l, ldx, Xe, 1); DMRG_COUNT_LAUNCH();
+    }
+    DMRG_CUDA(cudaGetLastError());
+    DMRG_TRY(gjac_run<double>(ctx, Xe, r, l, ldx, l, r, max_sweeps, tol, small, F2, sync, d_info, nullptr, nv, 0));
+    prof_mark(ctx, PROF_JACOBI64);
+    prof_count(ctx, PROF_JACOBI64, 4.0 * l * (double)l * r + 8.0 * l * (double)r * r + 9.0 * (double)r * r * r,
+               8.0 * ((double)r * l + (double)r * r) * 2.0);
+    k_jac_norms<<<(r * 32 + 255) / 256, 256, 0, st>>>(Xe, r, l, ldx, w.nrm); DMRG_COUNT_LAUNCH();
+    k_jac_rank<<<(r + 255) / 256, 256, 0, st>>>(w.nrm, r, w.perm); DMRG_COUNT_LAUNCH();
+    k_jac_out<<<r, 256, 0, st>>>(Xe, Xe + l, w.nrm, w.perm, m, n, tr, r, l, ldx, ldx, U, s, Vt); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }
@@ -1085,7 +1229,12 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
     const double small = ctx->jacobi32_floor;
     k_frob2_f<<<1, 1024, 0, st>>>(X, (long long)r * l, reinterpret_cast<double *>(sync + 4)); DMRG_COUNT_LAUNCH();
     prof_mark(ctx, PROF_JACOBI32);
-    if ((long long)r * l <= kSmemJacFloats) {
+    if (ctx->gjac32) {
+        // grouped block Jacobi (Gram form, one 128-thread group per block pair)
+        int nv = ctx->gjac_nv ? ctx->gjac_nv : (r <= 128 ? 32 : 16), groups = ctx->gjac_groups;
+        if (!ctx->gjac_nv && !ctx->gjac_groups) tune_lookup_gjac(ctx, r, l, &nv, &groups);   // autotuned bucket
+        DMRG_TRY(gjac_run<float>(ctx, X, r, l, l, l, 0, max_sweeps, tol, small, F2, sync, d_info, reff, nv, groups));
+    } else if ((long long)r * l <= kSmemJacFloats) {
         const int smem = (int)(sizeof(float) * (size_t)r * l);
         static bool attr = false;
         if (!attr) {

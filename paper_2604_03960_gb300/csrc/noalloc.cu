@@ -73,7 +73,7 @@ extern "C" dmrg_status svd_truncate_noalloc(dmrg_ctx *ctx, const double *theta_d
         return DMRG_EINVAL;
     }
     const int r = m < n ? m : n, l = m < n ? n : m;
-    const size_t work = al256(svd_work_bytes(r, l));
+    const size_t work = al256(svd_work_bytes_base(r, l));
     const size_t need = work + al256(sizeof(BondResult)) + al256(sizeof(int) * 4);
     if (need > kNoAllocScratchBytes) {
         std::fprintf(stderr, "dmrg: svd_truncate_noalloc scratch too small (%zu > %zu bytes)\n", need,
@@ -87,7 +87,7 @@ extern "C" dmrg_status svd_truncate_noalloc(dmrg_ctx *ctx, const double *theta_d
     int *info = reinterpret_cast<int *>(b + work + al256(sizeof(BondResult)));
     // The Jacobi load kernel clears the barrier words and rotation counters it
     // reuses from the previous call; everything else is written before it is read.
-    DMRG_TRY(svd_jacobi(ctx, theta_dev, m, n, U_dev, s_dev, Vt_dev, b, ctx->jacobi_max_sweeps, info));
+    DMRG_TRY(svd_jacobi(ctx, theta_dev, m, n, U_dev, s_dev, Vt_dev, b, ctx->jacobi_max_sweeps, info, 0));
     dmrg_params p{};
     p.eps_trunc = eps;
     p.chi_min = 1;

@@ -30,7 +30,7 @@ def test_gemm_tuning_roundtrip_and_bits(G, tmp_path):
     path = str(tmp_path / "tune.json")
     ctx.autotune_save(path)
     doc = json.load(open(path))
-    assert doc["format"] == "dmrg-autotune-1" and len(doc["gemm"]) == 2
+    assert doc["format"] == "dmrg-autotune-2" and len(doc["gemm"]) == 2
     for e in doc["gemm"]:
         assert e["bn"] in (128, 256) and e["ms128"] > 0 and e["ms256"] > 0
     ctx2 = G.Context(0)
@@ -49,10 +49,17 @@ def test_gemm_tuning_roundtrip_and_bits(G, tmp_path):
     ctx.close(); ctx2.close()
 
 
-def test_svd_tuning_keeps_accuracy(G):
+def test_svd_tuning_keeps_accuracy(G, tmp_path):
     ctx = G.Context(0)
     n = 600
     ctx.autotune_svd([n], reps=1)
+    assert ctx.autotune_entries()[1] == 1
+    # the grouped Jacobi's choice is recorded and survives a save/load
+    path = str(tmp_path / "tune_svd.json")
+    ctx.autotune_save(path)
+    e = json.load(open(path))["svd"][0]
+    assert e["nv"] in (16, 32) and e["groups"] in (1, 2, 4)
+    ctx.autotune_load(path)
     assert ctx.autotune_entries()[1] == 1
     ctx.set_option("svd_prec", 1)
     chi = n // 2

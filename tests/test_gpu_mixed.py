@@ -146,8 +146,11 @@ def test_hold_mode_freezes_the_schedule(G, ctx):
     st.set_params(p)
     r2, v2 = st.sweep(3)
     assert all(v.chi_ctrl == held[v.bond] for v in v2)
+    # at a frozen schedule the run settles: the held sweeps' energies agree to
+    # well within the truncation's effect (two-site sweep energies are Ritz
+    # values before truncation, so they need not fall monotonically)
     E = [r.E for r in r2]
-    assert all(b <= a + 1e-12 for a, b in zip(E, E[1:]))
+    assert max(E) - min(E) <= 1e-6 * N
     with pytest.raises(G.DMRGError):
         st.set_params(G.make_params(prec=G.PREC_FP64, ctrl=G.CTRL_HOLD, chi_max=64, chi_init=4))
     st.close()

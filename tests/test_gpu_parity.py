@@ -42,7 +42,7 @@ def dev(x, dtype=torch.float64):
 # SVD + entropy + truncation
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("kind", ["exp", "pow"])
-@pytest.mark.parametrize("chi", [4, 17, 32, 64, 128])
+@pytest.mark.parametrize("chi", [4, 17, 32, 64, 128, 256])
 def test_svd_exact_spectrum(ctx, kind, chi):
     n = 2 * chi
     s_ref = synth.spectrum(kind, n, chi)
@@ -377,3 +377,31 @@ def test_tfim_sweep_against_free_fermions(G, ctx, prec, h):
         kw.pop("prec")
         ref = O.dmrg_run(W, m0, O.make_params(**kw), 4)
         assert np.all(np.abs(np.array([r.E for r in recs]) - ref["E"]) / N <= 1e-10)
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+@pytest.mark.parametrize("m,n", [(560, 560), (300, 512), (512, 260)])
+def test_fp64_svd_forms_agree(G, m, n, precond):
+    """The FP64 SVD with and without its FP32 preconditioning pass, and the
+    one-warp-per-pair scalar kernel, give the same factors at FP64 accuracy
+    on a graded spectrum (s_k = exp(-k / (0.1 r))) at bulk DMRG sizes."""
+    r = min(m, n)
+    s_ref = synth.spectrum("exp", r, r // 2)
+    A = synth.svd_test_matrix(synth.workload_seed(13, m + n), m, n, s_ref)
+    out = {}
+    for form in ("scalar", "grouped"):
+        c = G.Context(0)
+        c.set_option("jacobi64_gram", 1 if form == "grouped" else 0)
+        c.set_option("jacobi64_precond", precond)
+        U, s, Vt, k, S, err = c.svd_truncate(dev(A), r, 1e-10)
+        out[form] = tuple(x.cpu().numpy() for x in (U, s, Vt)) + (k, S)
+        c.close()
+    U, s, Vt, k, S = out["grouped"]
+    tol = 20 * max(m, n) * EPS
+    assert np.all(np.abs(s - s_ref) <= 1e-10 * s_ref + 8 * max(m, n) * EPS * s_ref[0])
+    assert np.linalg.norm(U * s @ Vt - A) <= tol * np.linalg.norm(A)
+    assert np.abs(U.T @ U - np.eye(r)).max() <= tol
+    assert np.abs(Vt @ Vt.T - np.eye(r)).max() <= tol
+    s0 = out["scalar"][1]
+    assert np.all(np.abs(s - s0) <= 1e-10 * s0 + 8 * max(m, n) * EPS * s0[0])
+    assert k == out["scalar"][3] and abs(S - out["scalar"][4]) <= 1e-12
