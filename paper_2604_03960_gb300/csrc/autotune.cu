@@ -179,7 +179,7 @@ extern "C" dmrg_status dmrg_autotune_svd(dmrg_ctx *ctx, int n_sizes, const int *
                 return e == DMRG_ENOCONV ? DMRG_OK : e;
             }, ms);
         };
-        if (ctx->gjac32) {
+        if (ctx->gjac32 == 2 || (ctx->gjac32 == 1 && (long long)m * m <= kSmemJacFloats)) {
             // grouped kernel: vectors per block pair x groups per CTA
             static const int kNv[] = {16, 32};
             static const int kGroups[] = {1, 2, 4};

@@ -74,6 +74,10 @@ struct SvdWork {
     unsigned *sync = nullptr;  // grid barrier words (2) + rotation counters (2)
 };
 
+// FP32 Jacobi problems of at most this many floats (r vectors x length l)
+// fit one CTA's shared memory: the single-CTA kernels take them.
+constexpr int kSmemJacFloats = 50 * 1024;
+
 // Bytes needed by the Jacobi scratch for r vectors of length l.
 size_t svd_work_bytes(int r, int l);
 SvdWork svd_work_carve(void *base, int r, int l);
@@ -140,7 +144,7 @@ struct dmrg_ctx {
     int bjac_gram = 1;           // blocked FP32 Jacobi: inner sweep in Gram form (k_bjac32g)
     double jacobi32_floor = 1.1920928955078125e-07;   // FP32 Jacobi: vectors below this x |A|_F take no rotation
     int gbj_min_r = 0;           // FP32 Jacobi: Gram-block cooperative form from this many vectors on (0 = off)
-    int gjac32 = 1;              // FP32 Jacobi: grouped block kernel (gjacobi.cu)
+    int gjac32 = 1;              // FP32 Jacobi: grouped block kernel (gjacobi.cu): 0 never, 1 small problems, 2 always
     int gjac_nv = 0;             // ... vectors per block pair (16, 32; 0 = by size)
     int gjac_groups = 0;         // ... max groups per CTA (0 = by shared memory)
     int jacobi64_gram = 1;       // FP64 Jacobi: grouped block kernel (0: one warp per pair)

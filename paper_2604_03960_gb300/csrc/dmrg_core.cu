@@ -634,7 +634,11 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         ctx->svd_prec = (int)value;
         return DMRG_OK;
     }
-    if (!std::strcmp(name, "gjac32")) { ctx->gjac32 = value != 0.0; return DMRG_OK; }
+    if (!std::strcmp(name, "gjac32")) {
+        if (value != 0.0 && value != 1.0 && value != 2.0) return DMRG_EINVAL;
+        ctx->gjac32 = (int)value;
+        return DMRG_OK;
+    }
     if (!std::strcmp(name, "tc_split_kb")) {
         if (!(value >= 0.0 && value <= 1e6) || value != (double)(int)value) return DMRG_EINVAL;
         ctx->tc_split_kb = (int)value;

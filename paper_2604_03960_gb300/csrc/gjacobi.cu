@@ -85,6 +85,21 @@ __device__ __forceinline__ bool rot_params(double a, double b, double g, double 
 
 __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// one element from global to shared memory without a register round trip;
+// zero-filled when !valid (no global read then)
+__device__ __forceinline__ void cp_async_elem(float *dst, const float *src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double *dst, const double *src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+
 // per-group shared memory (after the vectors): Gram and rotation buffers,
 // Gram partial sums, step parameters, vector ids, a rotation counter
 template <typename T, int NV>
@@ -231,17 +246,20 @@ __global__ void __launch_bounds__(GT *kMaxGroups)
                 }
                 if (tg == 0) S.rot = 0;
                 group_sync(grp);
-                // 1. stage the vectors (positions l..lpad zero)
-                for (int idx = tg; idx < NV * lv; idx += GT) {
-                    const int q = idx / lv, e = idx - q * lv;
+                // 1. stage the vectors (positions l..lpad zero) with asynchronous
+                //    copies: every copy of a thread is in flight at once, one
+                //    L2 round trip per round instead of one per element
+                for (int q = 0; q < NV; ++q) {
                     const int v = S.vid[q];
-                    T val = (T)0;
-                    if (v >= 0) {
-                        if (e < l) val = X[(long long)v * ldx + e];
-                        else if (e >= lpad) val = X[(long long)v * ldx + gv0 + (e - lpad)];
+                    const T *src = X + (long long)(v < 0 ? 0 : v) * ldx;
+                    T *dst = xs + q * ls;
+                    for (int e = tg; e < lv; e += GT) {
+                        const bool valid = v >= 0 && (e < l || e >= lpad);
+                        const T *g = valid ? (e < l ? src + e : src + gv0 + (e - lpad)) : X;
+                        cp_async_elem(dst + e, g, valid);
                     }
-                    xs[q * ls + e] = val;
                 }
+                asm volatile("cp.async.wait_all;" ::: "memory");
                 group_sync(grp);
                 // 2. Gram matrix, made bitwise symmetric (upper triangle mirrored)
                 gram<NV>(xs, ls, lpad, S, tg);
@@ -387,13 +405,19 @@ dmrg_status launch_gjac(dmrg_ctx *ctx, T *X, int r, int l, int ldx, int gv0, int
     const int ls = sizeof(T) == 4 ? round_up(lpad + rv, 8) + 4 : round_up(lpad + rv, 2) + 1;
     const size_t gb = group_bytes<T, NV>(ls);
     const size_t smem_cap = 220 * 1024;
-    int G = (int)std::min<size_t>(kMaxGroups, smem_cap / gb);
-    if (max_groups > 0) G = std::min(G, max_groups);
-    if (G < 1) return DMRG_EUNSUPPORTED;
+    const int Gfit = (int)std::min<size_t>(kMaxGroups, smem_cap / gb);
+    if (Gfit < 1) return DMRG_EUNSUPPORTED;
     const int BW = NV / 2;
     const int nb = (r + BW - 1) / BW;
     const int npairs = (nb + (nb & 1)) / 2;
+    // groups per CTA: all block pairs in one CTA when they fit (no grid
+    // barrier), else one pair per SM as long as there are SMs for them
+    int G;
+    if (max_groups > 0) G = std::min(Gfit, max_groups);
+    else if (npairs <= Gfit) G = npairs;
+    else G = std::min(Gfit, (npairs + ctx->num_sms - 1) / ctx->num_sms);
     if (G > npairs) G = npairs;
+    if (G < 1) G = 1;
     const int threads = G * GT;
     const size_t smem = gb * G;
     static size_t attr[2] = {0, 0};

@@ -341,7 +341,6 @@ __global__ void k_jac32_load(const double *__restrict__ A, int m, int n, int dir
 
 // Single-CTA FP32 Jacobi with the vectors resident in shared memory (r*l
 // floats <= kSmemJacFloats): the rounds synchronise with __syncthreads only.
-constexpr int kSmemJacFloats = 50 * 1024;
 
 __global__ void __launch_bounds__(1024) k_jac32_smem(float *__restrict__ Xg, int r_all, int l, int max_sweeps,
                                                      double tol, int *status, int *info, const double *F2, double small,
@@ -1229,8 +1228,11 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
     const double small = ctx->jacobi32_floor;
     k_frob2_f<<<1, 1024, 0, st>>>(X, (long long)r * l, reinterpret_cast<double *>(sync + 4)); DMRG_COUNT_LAUNCH();
     prof_mark(ctx, PROF_JACOBI32);
-    if (ctx->gjac32) {
-        // grouped block Jacobi (Gram form, one 128-thread group per block pair)
+    // grouped block Jacobi (Gram form, one 128-thread group per block pair):
+    // option gjac32 = 1 (default) for the small problems the single-CTA
+    // kernel would take, where it measured faster inside the sweeps; 2 for
+    // every size (at bulk sizes the blocked kernel below measured faster)
+    if (ctx->gjac32 == 2 || (ctx->gjac32 == 1 && (long long)r * l <= kSmemJacFloats)) {
         int nv = ctx->gjac_nv ? ctx->gjac_nv : (r <= 128 ? 32 : 16), groups = ctx->gjac_groups;
         if (!ctx->gjac_nv && !ctx->gjac_groups) tune_lookup_gjac(ctx, r, l, &nv, &groups);   // autotuned bucket
         DMRG_TRY(gjac_run<float>(ctx, X, r, l, l, l, 0, max_sweeps, tol, small, F2, sync, d_info, reff, nv, groups));

@@ -52,15 +52,16 @@ def test_gemm_tuning_roundtrip_and_bits(G, tmp_path):
 def test_svd_tuning_keeps_accuracy(G, tmp_path):
     ctx = G.Context(0)
     n = 600
-    ctx.autotune_svd([n], reps=1)
-    assert ctx.autotune_entries()[1] == 1
-    # the grouped Jacobi's choice is recorded and survives a save/load
+    # n = 200 takes the grouped Jacobi (one CTA's shared memory), n = 600 the blocked kernel
+    ctx.autotune_svd([200, n], reps=1)
+    assert ctx.autotune_entries()[1] == 2
     path = str(tmp_path / "tune_svd.json")
     ctx.autotune_save(path)
-    e = json.load(open(path))["svd"][0]
-    assert e["nv"] in (16, 32) and e["groups"] in (1, 2, 4)
+    small, big = json.load(open(path))["svd"]
+    assert small["nv"] in (16, 32) and small["groups"] in (1, 2, 4)
+    assert big["nv"] == 0 and big["pairs"] in (24, 48, 96, 152) and big["inner"] in (1, 2)
     ctx.autotune_load(path)
-    assert ctx.autotune_entries()[1] == 1
+    assert ctx.autotune_entries()[1] == 2
     ctx.set_option("svd_prec", 1)
     chi = n // 2
     A = synth.svd_test_matrix(synth.workload_seed(2, 5), n, n, synth.spectrum("exp", n, chi))
