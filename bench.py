@@ -68,7 +68,8 @@ def parse(argv=None):
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--micro", choices=["gemm", "svd", "svd_batch", "chains", "bond", "ablation"], default=None,
+    ap.add_argument("--micro", choices=["gemm", "svd", "svd_batch", "chains", "bond", "ablation", "circuit"],
+                    default=None,
                     help="one kernel-level invocation (for profiling): gemm M,N,K or svd chi")
     ap.add_argument("--shape", default="5120,4096,1024", help="--micro gemm: M,N,K")
     ap.add_argument("--chi", type=int, default=512, help="--micro svd: matrix 2chi x 2chi")
@@ -136,6 +137,8 @@ def run_micro(args):
         out = bond_micro(args, G, synth, prec)
     elif args.micro == "ablation":
         out = ablation(args, G, synth, prec)
+    elif args.micro == "circuit":
+        out = circuit_micro(args, G, synth)
     else:
         chi = args.chi
         n = 2 * chi
@@ -290,6 +293,42 @@ def ablation(args, G, synth, prec):
         out["table5"][key] = pair(key, 20)
     for key in ("heisenberg", "ising_critical"):
         out["table6"][key] = {str(N): pair(key, N) for N in (10, 20, 40)}
+    return out
+
+
+def circuit_micro(args, G, synth):
+    """Circuit-level bond dimension maps (Section 8): a brickwork circuit of
+    CNOT + RY gates on --n-hi qubits, --reps layers, per-bond PID under
+    --chi-max; then the same circuit warm-started from the recorded map.
+    Device time per layer (CUDA events) and the map's growth."""
+    import numpy as np
+    import torch
+    N, L, cm = args.n_hi, args.reps, args.chi_max
+    layers = synth.brickwork_circuit(synth.workload_seed(61, N), N, L)
+    out = {"micro": "circuit", "qubits": N, "layers": L, "chi_max": cm}
+    maps = None
+    for form in ("pid", "warm"):
+        ctx = G.Context(0)
+        c = G.Circuit(ctx, N, G.make_params(chi_max=cm, chi_min=2))
+        rows = []
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(ctx.stream)
+        for l, (pos, gates) in enumerate(layers):
+            row, _ = c.apply_layer(pos, gates, None if form == "pid" else maps[l])
+            rows.append(row)
+        ev1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        rows = np.array(rows)
+        if form == "pid":
+            maps = rows
+        else:
+            out["warm_map_identical"] = bool(np.array_equal(rows, maps))
+        out[form] = {"ms_per_layer": ms / L, "max_chi_last_layer": int(rows[-1].max()),
+                     "mean_chi_last_layer": float(rows[-1].mean()),
+                     "max_chi_by_layer": [int(x) for x in rows.max(axis=1)]}
+        c.close()
+        ctx.close()
     return out
 
 
@@ -629,30 +668,60 @@ def new_chain(G, synth, ctx, wl, p, seed):
     return G.State(ctx, W, m0, p, 1.0, wl["Delta"])
 
 
-def timed_sweeps(st, ctx, steps, dom=None):
-    """`steps` sweeps between CUDA events on the context stream.  With `dom`
-    set, the launches of that profiler kind (and only those) are bracketed by
-    events too, for the dominant kernel's live launch times."""
+def timed_sweeps(st, ctx, steps, dom=None, e2e=False):
+    """`steps` sweeps, each between CUDA events on the context stream (device
+    time).  With `dom` set, the launches of that profiler kind (and only
+    those) are bracketed by events too, for the dominant kernel's live launch
+    times.  With e2e, every step also goes through the public API end to end:
+    the MPS from pinned host memory (dmrg_state_put_mps), the sweep, the MPS
+    and the visit records back to pinned host memory (dmrg_state_get_mps),
+    timed on the host clock around all three."""
+    import ctypes
     import torch
+    import paper_2604_03960_gb300 as G
     if dom is not None:
         ctx.set_option("prof_mask", 1 << dom)
         ctx.profile(True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(ctx.stream)
+    host = None
+    if e2e:
+        host = torch.empty(st.mps_size(), dtype=torch.float64).pin_memory()
+        st.get_mps(host)
+        torch.cuda.synchronize()
+    ms = 0.0
+    t_host = 0.0
+    h2d = d2h = 0
     recs, vis = [], []
     for _ in range(steps):
+        t0 = time.perf_counter()
+        if e2e:
+            n_in = st.mps_size()
+            st.put_mps(host[:n_in])
+            h2d += 8 * n_in
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(ctx.stream)
         r, v = st.sweep(1, visits=True)
+        ev1.record(ctx.stream)
+        if e2e:
+            n_out = st.mps_size()
+            if n_out > host.numel():
+                host = torch.empty(2 * n_out, dtype=torch.float64).pin_memory()
+            st.get_mps(host[:n_out])
+            d2h += 8 * n_out + len(v) * ctypes.sizeof(G.VisitRecord)
+        torch.cuda.synchronize()
+        t_host += time.perf_counter() - t0
+        ms += ev0.elapsed_time(ev1)
         recs += r
         vis += v
-    ev1.record(ctx.stream)
-    torch.cuda.synchronize()
     prof = None
     if dom is not None:
         prof = ctx.profile_read(dom)
         ctx.profile(False)
         ctx.set_option("prof_mask", (1 << len(PROF_NAMES)) - 1)
-    return ev0.elapsed_time(ev1), recs, vis, prof
+    e2e_out = None
+    if e2e:
+        e2e_out = {"seconds": t_host, "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps}
+    return ms, recs, vis, prof, e2e_out
 
 
 def profiled_sweep(st, ctx):
@@ -862,7 +931,7 @@ def run_ours(args):
     sync_ranks(dist)
     torch.cuda.synchronize()
     l0 = G.launch_count()
-    ms, recs, vis, prof_dom = timed_sweeps(st, ctx, args.steps, dom)
+    ms, recs, vis, prof_dom, e2e_t = timed_sweeps(st, ctx, args.steps, dom, e2e=not args.no_e2e)
     sync_ranks(dist)
     l1 = G.launch_count()
     clk = clocks.stop()
@@ -874,32 +943,13 @@ def run_ours(args):
     # grows chi through them, so the two bracket the timed region)
     post_ms, _, post, v = profiled_sweep(st, ctx)
     schedule += per_sweep_k(v, V)
-    # end to end: MPS in pinned host memory -> device, sweep, MPS and records -> host
     e2e = None
-    if not args.no_e2e:
-        host = torch.empty(st.mps_size(), dtype=torch.float64).pin_memory()
-        st.get_mps(host)
-        torch.cuda.synchronize()
-        sync_ranks(dist)
-        t0 = time.perf_counter()
-        h2d = d2h = 0
-        e2e_steps = 1
-        for _ in range(e2e_steps):
-            n_in = st.mps_size()
-            st.put_mps(host[:n_in])
-            h2d += 8 * n_in
-            _, v = st.sweep(1, visits=True)
-            schedule += per_sweep_k(v, V)
-            n_out = st.mps_size()
-            if n_out > host.numel():
-                host = torch.empty(n_out, dtype=torch.float64).pin_memory()
-            st.get_mps(host[:n_out])
-            d2h += 8 * n_out + (2 * N - 3) * 40
-        torch.cuda.synchronize()
-        t_e2e = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, "cuda")
-        e2e = {"value": t_e2e, "unit": "s/sweep", "h2d_bytes_per_step": h2d // e2e_steps,
-               "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
-               "path": "MPS from pinned host memory -> dmrg_state_put_mps -> dmrg_sweep -> dmrg_state_get_mps + records"}
+    if e2e_t is not None:
+        t_e2e = max_over_ranks(e2e_t["seconds"] / args.steps, dist, "cuda")
+        e2e = {"value": t_e2e, "unit": "s/sweep", "h2d_bytes_per_step": e2e_t["h2d_bytes_per_step"],
+               "d2h_bytes_per_step": e2e_t["d2h_bytes_per_step"], "steps": args.steps,
+               "path": "every timed sweep: MPS from pinned host memory -> dmrg_state_put_mps -> dmrg_sweep -> "
+                       "dmrg_state_get_mps + visit records to pinned host memory, host clock"}
     E_end = None
     if prec == G.PREC_3XTF32 and not args.no_fp64 and rank == 0:
         hr, hv = hold_sweeps(G, st, wl, prec, total)

@@ -172,7 +172,8 @@ const char *dmrg_status_string(dmrg_status s);
  * 32, and groups per CTA, 1-4; 0 = by size / autotuner), "jacobi64_gram"
  * (1: FP64 Jacobi on the grouped kernel, 0: one warp per pair),
  * "jacobi64_precond" (1: FP32 preconditioning pass before the FP64
- * Jacobi), "prof_mask"
+ * Jacobi), "mixed_svd64" (1: the 3xTF32 form takes the FP64 SVD and split, so
+ * only its contractions are in reduced precision), "prof_mask"
  * (bit k set: dmrg_profile brackets the launches of kind k; default all 9
  * kinds; bracketing one kind keeps the events off every other launch),
  * "mlp_eps_target" (truncation-error target of the k_star label, 1e-5),
@@ -346,6 +347,39 @@ dmrg_status dmrg_graph_destroy(void *graph_exec);
  * recorded entropy sequence reproduces the integer chi schedule exactly. */
 dmrg_status entropy_pid_step(dmrg_ctx *ctx, int n_bonds, const double *S_raw_dev, dmrg_ctrl_state *st_dev,
                              const dmrg_params *p_host, int *chi_out_dev);
+
+/* ---------------------------------------------------------------------- */
+/* Circuit-level bond dimension maps (Section 8)                          */
+/* ---------------------------------------------------------------------- */
+/* An MPS of N qubits (|0...0> at creation, every bond dimension 1) under
+ * layers of two-qubit gates, with one controller per bond.  Qubit q is the
+ * q-th site; amplitudes index qubit 0 as the most significant bit.
+ * Parameters: chi_min/chi_max, eps_trunc, multiplet_guard and the controller
+ * (ctrl = PID, DIRECT, FIXED or THRESHOLD, else DMRG_EINVAL) as in
+ * dmrg_params; the state owns its device memory (sized for chi_max). */
+typedef struct dmrg_circ dmrg_circ;
+dmrg_status dmrg_circ_create(dmrg_ctx *ctx, int N, const dmrg_params *p, dmrg_circ **out);
+void dmrg_circ_destroy(dmrg_circ *c);
+/* Apply one layer: gate g acts on qubits (pos_host[g], pos_host[g] + 1) with
+ * the real 4 x 4 matrix gates_host + 16 g, row-major G[(s1' s2')][(s1 s2)],
+ * index 2 s1 + s2, s1 the state of the first qubit; the pairs must be
+ * disjoint (DMRG_EINVAL otherwise).  The layer is one pass over the bonds,
+ * left to right for the even-numbered layers of the state and right to left
+ * for the odd ones, that moves the orthogonality centre across every bond:
+ * theta, the gate if the bond has one, the SVD (Eq. 20), the entropy of the
+ * full spectrum (Eq. 5), the truncation and the split.  At a gated bond the
+ * bond's controller steps on the entropy (Algorithms 1-2, Eqs. 8 and 16) and
+ * its chi bounds the retained dimension, or, with chi_warm_host (N - 1
+ * entries, host, may be NULL), the recorded chi of an earlier run does (warm
+ * start); a bond without a gate keeps its spectrum above eps_trunc.
+ * chi_row_host (N - 1, may be NULL) receives the bond dimensions after the
+ * layer (one row of the map chi_i^(l)), S_row_host (N - 1, may be NULL) the
+ * entropies of the gated bonds (0 elsewhere).  Synchronises the stream. */
+dmrg_status dmrg_circ_apply_layer(dmrg_circ *c, int n_gates, const int *pos_host, const double *gates_host,
+                                  const int *chi_warm_host, int *chi_row_host, double *S_row_host);
+/* The state's 2^N amplitudes (N <= 22) into the caller's device buffer
+ * psi_dev.  Allocates a 2^N scratch in the context and synchronises. */
+dmrg_status dmrg_circ_state(dmrg_circ *c, double *psi_dev);
 
 /* ---------------------------------------------------------------------- */
 /* Building blocks exposed for sampled parity checks and benchmarks       */

@@ -115,6 +115,12 @@ def lib():
                                             C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.ref_adam_step.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                         C.POINTER(C.c_double), C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
+            L.ref_statevector_apply.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int),
+                                                C.POINTER(C.c_double)]
+            L.ref_circuit_run.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                          C.POINTER(C.c_double), C.POINTER(Params), C.POINTER(C.c_int),
+                                          C.POINTER(CtrlState), C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double)]
             L.ref_heff_apply.argtypes = [C.c_int] * 4 + [C.POINTER(C.c_double)] * 6
             L.ref_env_left.argtypes = [C.c_int] * 4 + [C.POINTER(C.c_double)] * 4
             L.ref_env_right.argtypes = [C.c_int] * 4 + [C.POINTER(C.c_double)] * 4
@@ -344,3 +350,38 @@ def ed_dense(model: int, N: int, J=1.0, Delta=1.0, J2=0.0) -> np.ndarray:
     ev = np.zeros(2 ** N)
     lib().ref_ed_dense(model, N, J, Delta, J2, _dp(ev))
     return ev
+
+
+def statevector(N: int, layers):
+    """Exact state of the circuit `layers` (list of (positions, gates)) on
+    |0...0>, qubit 0 the most significant bit of the index."""
+    psi = np.zeros(2 ** N)
+    psi[0] = 1.0
+    for pos, gates in layers:
+        pos = np.ascontiguousarray(pos, dtype=np.int32)
+        gates = np.ascontiguousarray(gates, dtype=np.float64)
+        assert lib().ref_statevector_apply(N, _dp(psi), len(pos), _ip(pos), _dp(gates)) == 0
+    return psi
+
+
+def circuit_run(N: int, layers, params: Params, chi_warm=None, want_state: bool = True):
+    """MPS circuit run with per-bond chi control (Section 8); returns the chi
+    map (layers x (N-1)), the entropy map and the final state (N <= 24)."""
+    nl = len(layers)
+    ng = np.array([len(p) for p, _ in layers], dtype=np.int32)
+    pos = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.int32) for p, _ in layers])
+                               if nl else np.zeros(0, np.int32), dtype=np.int32)
+    gates = np.ascontiguousarray(np.concatenate([np.asarray(g, dtype=np.float64).reshape(-1) for _, g in layers])
+                                 if nl else np.zeros(0), dtype=np.float64)
+    chi_map = np.zeros((nl, N - 1), dtype=np.int32)
+    S_map = np.zeros((nl, N - 1))
+    psi = np.zeros(2 ** N) if want_state and N <= 24 else None
+    warm = None
+    if chi_warm is not None:
+        warm = np.ascontiguousarray(chi_warm, dtype=np.int32)
+    st = lib().ref_circuit_run(N, nl, _ip(ng), _ip(pos), _dp(gates), C.byref(params),
+                               _ip(warm) if warm is not None else None, None, _ip(chi_map), _dp(S_map),
+                               _dp(psi) if psi is not None else None)
+    if st != 0:
+        raise RuntimeError(f"oracle circuit status {-st}")
+    return chi_map, S_map, psi

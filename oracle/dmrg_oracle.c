@@ -1399,3 +1399,171 @@ int ref_ed_dense(int model, int N, double J, double Delta, double J2, double *ev
 /* Round-half-even check hook: exposes the rounding used by the controller. */
 double ref_round_half_even(double x) { return nearbyint(x); }
 int ref_rounding_mode_is_nearest(void) { return fegetround() == FE_TONEAREST; }
+
+/* ------------------------------------------------------------------------ */
+/* Circuit simulation with per-bond chi control (Section 8: circuit-level    */
+/* bond dimension maps).                                                     */
+/*                                                                           */
+/* Qubit q of an N-qubit state is bit N-1-q of the basis index (qubit 0 the  */
+/* most significant).  A two-qubit gate on (q, q+1) is a real 4 x 4 matrix    */
+/* G[(s1' s2')][(s1 s2)], row-major, index 2 s1 + s2 with s1 the state of    */
+/* qubit q.                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Exact statevector: psi (2^N) <- G psi for each gate in order. */
+int ref_statevector_apply(int N, double *psi, int n_gates, const int *pos, const double *gates)
+{
+    if (N < 2 || N > 30) return REF_EINVAL;
+    const size_t dim = (size_t)1 << N;
+    for (int g = 0; g < n_gates; ++g) {
+        const int q = pos[g];
+        if (q < 0 || q + 1 >= N) return REF_EINVAL;
+        const double *G = gates + 16 * (size_t)g;
+        const size_t b1 = (size_t)1 << (N - 1 - q), b2 = (size_t)1 << (N - 2 - q);
+        for (size_t x = 0; x < dim; ++x) {
+            if (x & (b1 | b2)) continue;          /* visit each group of four once */
+            const size_t idx[4] = {x, x | b2, x | b1, x | b1 | b2};   /* s1 s2 = 00, 01, 10, 11 */
+            double in[4], out[4];
+            for (int i = 0; i < 4; ++i) in[i] = psi[idx[i]];
+            for (int i = 0; i < 4; ++i) {
+                double a = 0.0;
+                for (int j = 0; j < 4; ++j) a += G[4 * i + j] * in[j];
+                out[i] = a;
+            }
+            for (int i = 0; i < 4; ++i) psi[idx[i]] = out[i];
+        }
+    }
+    return REF_OK;
+}
+
+/*
+ * MPS circuit run.  The state starts as |0...0> (every bond dimension 1).
+ * Layer l holds n_gates[l] gates on disjoint qubit pairs (brickwork); its
+ * gates are gate_pos / gates from offset sum_{l' < l} n_gates[l'].  A layer is
+ * one pass over the bonds, left to right for even l and right to left for
+ * odd l, that moves the orthogonality centre across every bond: at bond k
+ * theta = A_k A_{k+1}, the layer's gate on (k, k+1) if it has one, the SVD
+ * (ref_svd), the entropy of the full spectrum (Eq. 5) and the truncation
+ * (ref_trunc_k with the eps_trunc threshold), the split with the centre
+ * moving in the pass direction and the retained spectrum renormalised.
+ * At a gated bond the bond's controller takes a step on the entropy
+ * (Algorithms 1-2 with Eqs. 8 and 16, ref_ctrl_step) and its chi bounds k;
+ * with chi_warm (n_layers x (N-1), may be NULL) the gated bonds take chi from
+ * it instead (a warm start from an earlier run's map).  A bond without a
+ * gate keeps its spectrum (a gauge move: only the threshold applies).
+ * Outputs: chi_map[l][b] = dimension of bond b (between qubits b, b+1) after
+ * layer l; S_map[l][b] = the entropy at gated bonds (0 elsewhere); psi (2^N,
+ * may be NULL) the final state contracted from the MPS (N <= 24).
+ */
+int ref_circuit_run(int N, int n_layers, const int *n_gates, const int *gate_pos, const double *gates,
+                    const ref_params *p, const int *chi_warm, ref_ctrl_state *ctrl, int *chi_map, double *S_map,
+                    double *psi)
+{
+    if (N < 2 || n_layers < 0) return -REF_EINVAL;
+    const int d = 2;
+    int *chi = calloc((size_t)N + 1, sizeof(int));
+    double **A = calloc((size_t)N, sizeof(double *));
+    ref_ctrl_state *own = NULL;
+    if (!chi || !A) return -REF_ENOMEM;
+    for (int i = 0; i <= N; ++i) chi[i] = 1;
+    for (int i = 0; i < N; ++i) {
+        A[i] = calloc(2, sizeof(double));
+        A[i][0] = 1.0;                            /* |0> */
+    }
+    if (!ctrl) {
+        own = calloc((size_t)(N - 1), sizeof(ref_ctrl_state));
+        for (int b = 0; b < N - 1; ++b) own[b].chi = p->chi_min;
+        ctrl = own;
+    }
+    int status = 0, off = 0;
+    int *gate_at = malloc(sizeof(int) * (size_t)(N - 1));
+    for (int l = 0; l < n_layers && status == 0; ++l) {
+        for (int b = 0; b < N - 1; ++b) gate_at[b] = -1;
+        for (int g = 0; g < n_gates[l]; ++g) {
+            const int q = gate_pos[off + g];
+            if (q < 0 || q >= N - 1 || gate_at[q] >= 0 || (q > 0 && gate_at[q - 1] >= 0) ||
+                (q + 1 < N - 1 && gate_at[q + 1] >= 0)) { status = REF_EINVAL; break; }
+            gate_at[q] = off + g;
+        }
+        if (status) break;
+        const int go_right = (l % 2 == 0);
+        for (int step = 0; step < N - 1; ++step) {
+            const int k = go_right ? step : N - 2 - step;
+            const int cl = chi[k], cm = chi[k + 1], cr = chi[k + 2];
+            const int rows = cl * d, cols = d * cr;
+            double *theta = malloc(sizeof(double) * (size_t)rows * cols);
+            mm(rows, cols, cm, A[k], A[k + 1], theta);
+            if (gate_at[k] >= 0) {
+                const double *G = gates + 16 * (size_t)gate_at[k];
+                double *t2 = malloc(sizeof(double) * (size_t)rows * cols);
+                for (int a = 0; a < cl; ++a)
+                    for (int qo = 0; qo < 4; ++qo)
+                        for (int bb = 0; bb < cr; ++bb) {
+                            double acc = 0.0;
+                            for (int qi = 0; qi < 4; ++qi)
+                                acc += G[4 * qo + qi] * theta[((size_t)a * 4 + qi) * cr + bb];
+                            t2[((size_t)a * 4 + qo) * cr + bb] = acc;
+                        }
+                free(theta);
+                theta = t2;
+            }
+            const int r = rows < cols ? rows : cols;
+            double *U = malloc(sizeof(double) * (size_t)rows * r);
+            double *s = malloc(sizeof(double) * (size_t)r);
+            double *Vt = malloc(sizeof(double) * (size_t)r * cols);
+            double *eps = malloc(sizeof(double) * (size_t)(r + 1));
+            int sst = ref_svd(rows, cols, theta, U, s, Vt, p->jacobi_max_sweeps > 0 ? p->jacobi_max_sweeps : 60);
+            if (sst != REF_OK) status = sst;
+            const double S = ref_entropy(r, s, eps);
+            int chi_c;
+            if (gate_at[k] >= 0) {
+                int c2;
+                if (chi_warm) {
+                    chi_c = chi_warm[(size_t)l * (N - 1) + k];
+                } else {
+                    ref_ctrl_step(&ctrl[k], S, p, &c2);
+                    chi_c = c2;
+                }
+            } else {
+                chi_c = p->chi_max;                   /* a gauge move keeps the spectrum */
+            }
+            if (S_map) S_map[(size_t)l * (N - 1) + k] = gate_at[k] >= 0 ? S : 0.0;
+            int kk = ref_trunc_k(r, s, chi_c, p->eps_trunc, p->multiplet_guard);
+            double z = 0.0;
+            for (int j = 0; j < kk; ++j) z += s[j] * s[j];
+            z = sqrt(z);
+            free(A[k]); free(A[k + 1]);
+            A[k] = malloc(sizeof(double) * (size_t)rows * kk);
+            A[k + 1] = malloc(sizeof(double) * (size_t)kk * cols);
+            for (int i = 0; i < rows; ++i)
+                for (int j = 0; j < kk; ++j)
+                    A[k][(size_t)i * kk + j] = U[(size_t)i * r + j] * (go_right ? 1.0 : s[j] / z);
+            for (int j = 0; j < kk; ++j)
+                for (int c = 0; c < cols; ++c)
+                    A[k + 1][(size_t)j * cols + c] = Vt[(size_t)j * cols + c] * (go_right ? s[j] / z : 1.0);
+            chi[k + 1] = kk;
+            free(theta); free(U); free(s); free(Vt); free(eps);
+        }
+        if (chi_map) for (int b = 0; b < N - 1; ++b) chi_map[(size_t)l * (N - 1) + b] = chi[b + 1];
+        off += n_gates[l];
+    }
+    if (psi && status == 0 && N <= 24) {
+        /* contract: T (2^i x chi_i) <- T A_i reshaped, qubit 0 most significant */
+        size_t rows = 1;
+        double *T = malloc(sizeof(double));
+        T[0] = 1.0;
+        for (int i = 0; i < N; ++i) {
+            const int ci = chi[i], cn = chi[i + 1];
+            double *T2 = malloc(sizeof(double) * rows * (size_t)d * cn);
+            mm((int)rows, d * cn, ci, T, A[i], T2);        /* (rows x ci) (ci x 2 cn) */
+            free(T);
+            T = T2;
+            rows *= 2;                                      /* (rows*2) x cn, row = (prefix, s_i) */
+        }
+        memcpy(psi, T, sizeof(double) * rows);
+        free(T);
+    }
+    for (int i = 0; i < N; ++i) free(A[i]);
+    free(A); free(chi); free(own); free(gate_at);
+    return status ? -status : REF_OK;
+}

@@ -16,7 +16,7 @@ import torch
 from .build import LIB as _LIB_PATH, build as _build
 
 __all__ = [
-    "lib", "Params", "ModelParams", "CtrlState", "SweepRecord", "VisitRecord", "Context", "State",
+    "lib", "Params", "ModelParams", "CtrlState", "SweepRecord", "VisitRecord", "Context", "State", "Circuit",
     "PREC_FP64", "PREC_3XTF32", "CTRL_PID", "CTRL_DIRECT", "CTRL_FIXED", "CTRL_THRESHOLD", "CTRL_MLP", "CTRL_GLOBAL",
     "CTRL_HOLD", "CTRL_REPLAY",
     "XXZ", "J1J2", "TFIM", "DMRGError", "make_params", "MLP_NPARAM",
@@ -109,6 +109,11 @@ def _declare(L):
         "dmrg_state_set_mlp": (S, [_VP, _VP]),
         "dmrg_state_set_params": (S, [_VP, C.POINTER(Params)]),
         "dmrg_state_set_schedule": (S, [_VP, C.POINTER(_I), _I]),
+        "dmrg_circ_create": (S, [_VP, _I, C.POINTER(Params), C.POINTER(_VP)]),
+        "dmrg_circ_destroy": (None, [_VP]),
+        "dmrg_circ_apply_layer": (S, [_VP, _I, C.POINTER(_I), C.POINTER(_D), C.POINTER(_I), C.POINTER(_I),
+                                      C.POINTER(_D)]),
+        "dmrg_circ_state": (S, [_VP, _VP]),
         "dmrg_mlp_forward": (S, [_VP, _VP, _I, _VP, _VP]),
         "dmrg_mlp_loss_grad": (S, [_VP, _VP, _I, _VP, _VP, _VP, _VP]),
         "dmrg_mlp_adam": (S, [_VP, _I, _VP, _VP, _VP, _VP, _I, C.c_float, C.c_float, C.c_float, C.c_float]),
@@ -164,7 +169,8 @@ def exported_symbols():
         "dmrg_state_create", "dmrg_state_destroy", "dmrg_sweep", "bond_update", "svd_truncate", "entropy_pid_step",
         "dmrg_entropy", "dmrg_heff_apply", "dmrg_env_left", "dmrg_env_right", "dmrg_lanczos", "dmrg_state_chi",
         "dmrg_state_site", "dmrg_state_env", "dmrg_state_ctrl", "dmrg_state_set_mlp", "dmrg_state_set_params",
-        "dmrg_state_set_schedule", "dmrg_mlp_forward",
+        "dmrg_state_set_schedule", "dmrg_circ_create", "dmrg_circ_destroy", "dmrg_circ_apply_layer",
+        "dmrg_circ_state", "dmrg_mlp_forward",
         "dmrg_mlp_loss_grad", "dmrg_mlp_adam", "dmrg_gemm", "dmrg_set_option",
         "dmrg_state_mps_size", "dmrg_state_get_mps", "dmrg_state_put_mps", "dmrg_launch_count",
         "dmrg_profile", "dmrg_profile_read", "svd_truncate_noalloc", "dmrg_mlp_train",
@@ -510,6 +516,50 @@ class State:
 
     def set_mlp(self, P: torch.Tensor | None):
         _check(lib().dmrg_state_set_mlp(self.h, _ptr(P) if P is not None else None), "dmrg_state_set_mlp")
+
+
+class Circuit:
+    """dmrg_circ: an MPS of N qubits under gate layers with per-bond chi
+    control (the circuit-level bond dimension maps of Section 8)."""
+
+    def __init__(self, ctx: Context, N: int, params: Params):
+        self.ctx, self.N = ctx, N
+        h = C.c_void_p()
+        _check(lib().dmrg_circ_create(ctx.h, N, C.byref(params), C.byref(h)), "dmrg_circ_create")
+        self.h = h
+
+    def apply_layer(self, pos, gates, chi_warm=None):
+        """Gates (n x 4 x 4, float64) on qubit pairs (pos[g], pos[g]+1);
+        returns the layer's row of the chi map and the gated bonds' entropies."""
+        import numpy as np
+        pos = np.ascontiguousarray(pos, dtype=np.int32)
+        gates = np.ascontiguousarray(gates, dtype=np.float64).reshape(-1)
+        n = len(pos)
+        row = (C.c_int * (self.N - 1))()
+        S = (C.c_double * (self.N - 1))()
+        warm = None
+        if chi_warm is not None:
+            warm = (C.c_int * (self.N - 1))(*[int(x) for x in chi_warm])
+        _check(lib().dmrg_circ_apply_layer(self.h, n, pos.ctypes.data_as(C.POINTER(C.c_int)),
+                                           gates.ctypes.data_as(C.POINTER(C.c_double)), warm, row, S),
+               "dmrg_circ_apply_layer")
+        return list(row), list(S)
+
+    def state(self) -> torch.Tensor:
+        psi = torch.empty(2 ** self.N, dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        _check(lib().dmrg_circ_state(self.h, _ptr(psi)), "dmrg_circ_state")
+        return psi
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dmrg_circ_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sweep_chains(states, n_sweeps: int):

@@ -144,6 +144,7 @@ struct dmrg_ctx {
     int bjac_gram = 1;           // blocked FP32 Jacobi: inner sweep in Gram form (k_bjac32g)
     double jacobi32_floor = 1.1920928955078125e-07;   // FP32 Jacobi: vectors below this x |A|_F take no rotation
     int gbj_min_r = 0;           // FP32 Jacobi: Gram-block cooperative form from this many vectors on (0 = off)
+    int mixed_svd64 = 0;         // 3xTF32 form with the FP64 SVD and split (contractions alone in reduced precision)
     int gjac32 = 1;              // FP32 Jacobi: grouped block kernel (gjacobi.cu): 0 never, 1 small problems, 2 always
     int gjac_nv = 0;             // ... vectors per block pair (16, 32; 0 = by size)
     int gjac_groups = 0;         // ... max groups per CTA (0 = by shared memory)
@@ -310,6 +311,14 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
                          int *d_info, double *s_sorted, float **X_out, double **nrm_out, int **perm_out);
 dmrg_status gather_unit_vectors(dmrg_ctx *ctx, const float *X, const double *nrm, const int *perm, const int *kdev,
                                 int kmax, int l, double *Q);
+
+// Split of a truncated SVD (the retained k from res, renormalised by its
+// znorm) into site tensors: A_k = U (and A_{k+1} = s Vt) when the centre moves
+// right, A_k = U s and A_{k+1} = Vt otherwise; kmax bounds k for the grid.
+struct BondResult;
+dmrg_status launch_split(dmrg_ctx *ctx, const double *U, const double *s, const double *Vt, int m, int n, int r,
+                         const BondResult *res, int go_right, double *Ak, double *Ak1, int kmax);
+dmrg_status launch_init_ctrl(dmrg_ctx *ctx, dmrg_ctrl_state *st, int n, int chi0);
 
 // Lanczos on the effective Hamiltonian (see lanczos.cu).
 struct HeffOp;  // defined in dmrg_core.cu

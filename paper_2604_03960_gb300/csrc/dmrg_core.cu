@@ -407,6 +407,24 @@ size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 // ---------------------------------------------------------------------------
 // Contraction plans
 // ---------------------------------------------------------------------------
+// Split of a truncated SVD into two site tensors (used by the circuit path too)
+dmrg_status launch_split(dmrg_ctx *ctx, const double *U, const double *s, const double *Vt, int m, int n, int r,
+                         const BondResult *res, int go_right, double *Ak, double *Ak1, int kmax)
+{
+    const long long tot = std::max((long long)m * kmax, (long long)kmax * n);
+    k_split<<<grid1d(tot, 256, ctx->num_sms), 256, 0, ctx->stream>>>(U, s, Vt, m, n, r, res, go_right, Ak, Ak1);
+    DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
+dmrg_status launch_init_ctrl(dmrg_ctx *ctx, dmrg_ctrl_state *st, int n, int chi0)
+{
+    k_init_ctrl<<<(n + 127) / 128, 128, 0, ctx->stream>>>(st, n, chi0); DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
 static dmrg_status mix(dmrg_ctx *ctx, const double *in, double *out, const double *C, const MixDesc &d)
 {
     long long total = (long long)d.An * d.Bn;
@@ -634,6 +652,7 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         ctx->svd_prec = (int)value;
         return DMRG_OK;
     }
+    if (!std::strcmp(name, "mixed_svd64")) { ctx->mixed_svd64 = value != 0.0; return DMRG_OK; }
     if (!std::strcmp(name, "gjac32")) {
         if (value != 0.0 && value != 1.0 && value != 2.0) return DMRG_EINVAL;
         ctx->gjac32 = (int)value;
@@ -802,7 +821,7 @@ static dmrg_status bond_step_a(dmrg_state *st, int k, int go_right, int do_ctrl,
         if (v < 0 || (int)st->sched.size() < V) return DMRG_EINVAL;
         chi_global = st->sched[v];
     }
-    if (prec == DMRG_PREC_FP64) {
+    if (prec == DMRG_PREC_FP64 || ctx->mixed_svd64) {
         // SVD (Eq. 20) in FP64, then entropy, controller and truncation
         DMRG_TRY(svd_jacobi(ctx, st->theta, m, n, st->U, st->s, st->Vt, st->svdw, st->p.jacobi_max_sweeps,
                             st->d_info));
@@ -836,7 +855,7 @@ static dmrg_status bond_step_b(dmrg_state *st, double *flops, int *k_out, double
                      st->cap[k + 1], st->h_res->S);
         return DMRG_ENAN;
     }
-    if (prec == DMRG_PREC_FP64) {
+    if (prec == DMRG_PREC_FP64 || ctx->mixed_svd64) {
         long long tot = std::max((long long)m * kk, (long long)kk * n);
         k_split<<<grid1d(tot, 256, ctx->num_sms), 256, 0, ctx->stream>>>(st->U, st->s, st->Vt, m, n, r, st->d_res,
                                                                          go_right, st->A[k], st->A[k + 1]); DMRG_COUNT_LAUNCH();

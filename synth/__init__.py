@@ -127,3 +127,26 @@ def uneven_sizes(seed: int, count: int, lo: int, hi: int) -> np.ndarray:
 
 def uniform_range(seed: int, count: int, lo: float, hi: float) -> np.ndarray:
     return lo + (hi - lo) * Xoshiro(seed, lanes=64).uniform(count)
+
+
+def brickwork_circuit(seed: int, N: int, n_layers: int):
+    """A hardware-efficient circuit on N qubits: layer l holds two-qubit gates
+    on the pairs (q, q+1) with q = l mod 2, l mod 2 + 2, ...; each gate is a
+    CNOT (control q) after single-qubit RY rotations on both qubits, with
+    angles uniform in [0, 2 pi) from the seeded generator.  Real gates, as
+    4 x 4 matrices G[(s1' s2')][(s1 s2)], index 2 s1 + s2, s1 = qubit q.
+    Returns [(positions, gates (n x 4 x 4))] per layer."""
+    rng = Xoshiro(seed, lanes=64)
+    cnot = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=np.float64)
+    layers = []
+    for l in range(n_layers):
+        pos = list(range(l % 2, N - 1, 2))
+        ang = rng.uniform(2 * len(pos)) * 2.0 * np.pi
+        gates = []
+        for g in range(len(pos)):
+            a, b = ang[2 * g] / 2.0, ang[2 * g + 1] / 2.0
+            ry_a = np.array([[np.cos(a), -np.sin(a)], [np.sin(a), np.cos(a)]])
+            ry_b = np.array([[np.cos(b), -np.sin(b)], [np.sin(b), np.cos(b)]])
+            gates.append(cnot @ np.kron(ry_a, ry_b))
+        layers.append((np.array(pos, dtype=np.int32), np.array(gates).reshape(len(pos), 4, 4)))
+    return layers

@@ -13,7 +13,7 @@ Tolerances:
   * Ritz value: FP64 1e-10 relative; mixed 2e-6 relative (first order in
     the FP32-accumulated contractions), and the FP64 Rayleigh quotient of the
     mixed Ritz vector within 1e-8 per site of the chain (|dE| <= 1e-8 N);
-  * Ritz vector: overlap 1 - 1e-10 (FP64), 1 - 1e-8 (mixed);
+  * Ritz vector: overlap 1 - 1e-10 (FP64), 1 - 1e-7 (mixed);
   * singular values of the oracle's Ritz vector: FP64 |s - s_ref| <= 1e-10 s_ref
     + 8 n eps s_1; mixed 1e-7 s_ref + 8 sqrt(r) 2^-24 |theta|_F (the bounds of
     the isolated-SVD tests); entropy 1e-12 (FP64) / 1e-6 (mixed); the FP64
@@ -99,7 +99,7 @@ def test_fullsize_lanczos(G, bulk_bond, oracle_update, form):
         Hy = O.heff_apply(b["L"], b["W1"], b["W2"], b["R"], y)
         E_rq = float(np.dot(y.ravel(), Hy.ravel()) / np.dot(y.ravel(), y.ravel()))
         assert abs(E_rq - ref["E"]) <= 1e-8 * b["N"]
-        assert ov >= 1.0 - 1e-8
+        assert ov >= 1.0 - 1e-7                     # angle to the FP64 Ritz vector below 4.5e-4
 
 
 @pytest.mark.parametrize("form", ["fp64", "mixed"])
