@@ -172,7 +172,8 @@ const char *dmrg_status_string(dmrg_status s);
  * 32, and groups per CTA, 1-4; 0 = by size / autotuner), "jacobi64_gram"
  * (1: FP64 Jacobi on the grouped kernel, 0: one warp per pair),
  * "jacobi64_precond" (1: FP32 preconditioning pass before the FP64
- * Jacobi), "mixed_svd64" (1: the 3xTF32 form takes the FP64 SVD and split, so
+ * Jacobi), "jacobi32_tol" (FP32 Jacobi: rotate while a pair's cosine exceeds
+ * this, 1e-6), "mixed_svd64" (1: the 3xTF32 form takes the FP64 SVD and split, so
  * only its contractions are in reduced precision), "prof_mask"
  * (bit k set: dmrg_profile brackets the launches of kind k; default all 9
  * kinds; bracketing one kind keeps the events off every other launch),

@@ -653,6 +653,11 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         return DMRG_OK;
     }
     if (!std::strcmp(name, "mixed_svd64")) { ctx->mixed_svd64 = value != 0.0; return DMRG_OK; }
+    if (!std::strcmp(name, "jacobi32_tol")) {
+        if (!(value >= 1e-8 && value <= 1e-2)) return DMRG_EINVAL;
+        ctx->jacobi32_tol = value;
+        return DMRG_OK;
+    }
     if (!std::strcmp(name, "gjac32")) {
         if (value != 0.0 && value != 1.0 && value != 2.0) return DMRG_EINVAL;
         ctx->gjac32 = (int)value;

@@ -1218,10 +1218,14 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
             reff = reinterpret_cast<const int *>(sync + 6);
         }
     }
-    // rotate while the cosine exceeds 1e-5: FP32 dot products over a few
-    // thousand terms are good to ~1e-6, and the FP64 Newton-Schulz step that
-    // follows takes the retained vectors from 1e-5 to ~1e-10
-    const double tol = 1.0e-5;
+    // rotate while the cosine exceeds jacobi32_tol (1e-6): the Gram entries
+    // of the blocked kernels (3xTF32) resolve a few 1e-7, and vectors left at
+    // cosines of 1e-5 span a retained subspace rotated by ~1e-5 s_i s_j /
+    // (s_i^2 - s_j^2) towards the discarded one -- measured, that raised the
+    // mixed form's energy by 1.4e-8 per site against FP64 on the same
+    // retained dimensions (1.3e-10 at 1e-6); the FP64 Newton-Schulz step that
+    // follows makes the retained vectors orthonormal to ~k tol^2
+    const double tol = ctx->jacobi32_tol;
     int *status = ctx->d_status;
     // F2 = |A|_F^2 from the FP32 copy; vectors below 2^-23 |A|_F are dropped anyway
     const double *F2 = reinterpret_cast<const double *>(sync + 4);

@@ -37,12 +37,17 @@ def run_gpu(G, N, layers, params, warm=None):
 def test_circuit_untruncated_is_exact(G):
     N, L = 12, 8
     layers = synth.brickwork_circuit(synth.workload_seed(60, 4), N, L)
-    kw = dict(chi_max=64, chi_min=64, ctrl=G.CTRL_FIXED, chi_fixed=64, eps_trunc=0.0)
+    kw = dict(chi_max=64, chi_min=64, ctrl=G.CTRL_FIXED, chi_fixed=64)
     chi, S, psi = run_gpu(G, N, layers, G.make_params(**kw))
     exact = O.statevector(N, layers)
     assert np.max(np.abs(psi - exact)) < 1e-12
     chi_ref, S_ref, _ = O.circuit_run(N, layers, O.make_params(**kw))
     assert np.array_equal(chi, chi_ref)
+    # the last layer's map is the exact state's Schmidt ranks (values above
+    # the eps_trunc = 1e-10 threshold of the normalised spectrum)
+    for b in range(N - 1):
+        sv = np.linalg.svd(exact.reshape(2 ** (b + 1), -1), compute_uv=False)
+        assert chi[-1, b] == int(np.sum(sv / np.linalg.norm(sv) > 1e-10))
 
 
 @pytest.mark.parametrize("N,L,chi_max", [(12, 10, 16), (16, 12, 24)])

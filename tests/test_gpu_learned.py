@@ -9,9 +9,11 @@ position and the sweep index.
 
 Gain: on an unseen chain (N=40, between the training lengths 24, 32, 48),
 the network with the PID fallback reaches the energy of the threshold-
-truncated run (chi_max everywhere, the accuracy reference) to within 1e-4 per
-site at less than half its cost sum_visits k^3, and a lower energy than the
-PID-only run of the same controller parameters.
+truncated run (chi_max everywhere, the accuracy reference) to within 1e-6 per
+site at less than half its cost sum_visits k^3, and an energy lower, by more
+than 1e-5 per site, than the PID-only run of the same controller parameters
+(the PID of Algorithm 2 at S_target = 0.36, which grows chi only a few units
+per visit and ends far from the converged energy after 5 sweeps).
 """
 import math
 
@@ -105,8 +107,10 @@ def test_learned_scheduler_trains_and_gains(G, ctx):
     for name, ctrl, PP in [("pid", G.CTRL_PID, None), ("mlp", G.CTRL_MLP, P), ("thr", G.CTRL_THRESHOLD, None)]:
         recs, vis = run(G, ctx, N, Delta, ctrl, 5, P=PP, seed=99)
         out[name] = dict(E=recs[-1].E / N, cost=sum(vv.k ** 3 for vv in vis),
-                         used=int(sum(vv.mlp_used for vv in vis)))
+                         used=int(sum(vv.mlp_used for vv in vis)), maxk=max(vv.k for vv in vis))
     assert out["mlp"]["used"] > 0                       # the network, not only its fallback, chose chi
-    assert abs(out["mlp"]["E"] - out["thr"]["E"]) <= 1e-4
+    assert abs(out["mlp"]["E"] - out["thr"]["E"]) <= 1e-6
     assert out["mlp"]["cost"] < 0.5 * out["thr"]["cost"]
-    assert out["mlp"]["E"] < out["pid"]["E"]
+    assert out["mlp"]["E"] < out["pid"]["E"] - 1e-5
+    # the PID moved: its chi is not stuck at chi_min
+    assert out["pid"]["maxk"] > 8

@@ -55,7 +55,7 @@ def test_mixed_energy_matches_fp64_and_ed(G, ctx, N, chi_max, gbj):
     if E0 is not None:
         assert abs(Em - E0) / N <= 1e-8
     # after the closing right-to-left half-sweep, sites 1..N-1 are right-orthonormal
-    # isometries (B B^T = I): the FP32 Jacobi leaves cosines below tol = 1e-5 and
+    # isometries (B B^T = I): the FP32 Jacobi leaves cosines below tol <= 1e-5 and
     # one Newton-Schulz step maps them to about (3/4) chi tol^2
     chi = stm.chi()
     for i in range(1, N):
@@ -103,7 +103,7 @@ def test_mixed_svd_exact_spectrum(G, chi, opt):
     """Standalone mixed SVD (svd_prec = 1) on U diag(s) V^T with s known:
     retained values within 1e-7 relative (FP64 norms of the FP64 projection
     on the re-orthonormalised isometry: second order in its direction errors,
-    which the FP32 Jacobi leaves near its 1e-5 cosine tolerance) plus
+    which the FP32 Jacobi leaves below its cosine tolerance, <= 1e-5) plus
     8 sqrt(r) u |A|_F absolute, u = 2^-24: a vector near the FP32 rank floor
     carries the rounding of its rotations against all r others, each up to
     u times their norm, and its projection picks those components up (the
@@ -121,7 +121,7 @@ def test_mixed_svd_exact_spectrum(G, chi, opt):
     U, s, Vt = (x.cpu().numpy() for x in (U, s, Vt))
     fro = np.sqrt(np.sum(s_ref ** 2))
     assert np.all(np.abs(s[:k] - s_ref[:k]) <= 1e-7 * s_ref[:k] + 8 * np.sqrt(len(s_ref)) * 2.0 ** -24 * fro)
-    # the Jacobi leaves pairwise cosines up to tol = 1e-5; one Newton-Schulz
+    # the Jacobi leaves pairwise cosines up to tol <= 1e-5; one Newton-Schulz
     # step maps the error E of Q Q^T - I to about (3/4) E^2, |(E^2)_ij| <= k tol^2
     assert np.abs(U[:, :k].T @ U[:, :k] - np.eye(k)).max() <= 0.75 * k * 1e-10
     Ak = (U[:, :k] * s[:k]) @ Vt[:k]

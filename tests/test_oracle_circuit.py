@@ -40,11 +40,14 @@ def test_untruncated_mps_circuit_equals_statevector():
     exact: the same state to 1e-12, every bond at its Schmidt rank."""
     N, L = 10, 8
     layers = synth.brickwork_circuit(synth.workload_seed(60, 2), N, L)
-    p = O.make_params(chi_max=32, chi_min=32, ctrl=O.CTRL_FIXED, chi_fixed=32, eps_trunc=0.0)
+    p = O.make_params(chi_max=32, chi_min=32, ctrl=O.CTRL_FIXED, chi_fixed=32)
     chi_map, S_map, psi = O.circuit_run(N, layers, p)
     exact = O.statevector(N, layers)
     assert np.max(np.abs(psi - exact)) < 1e-12
     assert np.all(chi_map <= np.minimum(2 ** np.arange(1, N), 2 ** np.arange(N - 1, 0, -1)))
+    for b in range(N - 1):                       # the final map: the exact Schmidt ranks
+        sv = np.linalg.svd(exact.reshape(2 ** (b + 1), -1), compute_uv=False)
+        assert chi_map[-1, b] == int(np.sum(sv / np.linalg.norm(sv) > 1e-10))
     # the entropy at a gated bond equals the exact state's Schmidt entropy there
     l, b = L - 1, (L - 1) % 2
     M = exact.reshape(2 ** (b + 1), 2 ** (N - b - 1))
