@@ -68,7 +68,8 @@ def parse(argv=None):
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--micro", choices=["gemm", "svd", "svd_batch", "chains", "bond", "ablation", "circuit"],
+    ap.add_argument("--micro", choices=["gemm", "svd", "svd_batch", "chains", "bond", "ablation", "circuit",
+                                        "learned"],
                     default=None,
                     help="one kernel-level invocation (for profiling): gemm M,N,K or svd chi")
     ap.add_argument("--shape", default="5120,4096,1024", help="--micro gemm: M,N,K")
@@ -139,6 +140,8 @@ def run_micro(args):
         out = ablation(args, G, synth, prec)
     elif args.micro == "circuit":
         out = circuit_micro(args, G, synth)
+    elif args.micro == "learned":
+        out = learned_micro(args, G, synth)
     else:
         chi = args.chi
         n = 2 * chi
@@ -329,6 +332,79 @@ def circuit_micro(args, G, synth):
                      "max_chi_by_layer": [int(x) for x in rows.max(axis=1)]}
         c.close()
         ctx.close()
+    return out
+
+
+def learned_micro(args, G, synth):
+    """The learned scheduler's workload: an MLP (10 -> 64 -> 64 -> 1, GELU)
+    trained on the GPU with the library's kernels on entropy traces of the
+    Heisenberg/XXZ chains (N = 100 at chi <= 256 and N = 200 at chi <= 1024,
+    Delta in {0.5, 1, 1.5}, threshold truncation, 3 sweeps each; label log2 of
+    the next visit's k* at truncation error 1e-5), then run on the J1-J2 chain
+    (N = --n-hi, J2/J1 = 0.24, D = 8, chi_max = --chi-max, --reps sweeps,
+    mixed form) against the PID-only run of the same parameters: s/sweep,
+    energy, sum_visits k^3 and how often the network chose chi."""
+    import math
+    import numpy as np
+    import torch
+    ctx = G.Context(0)
+    X, y = [], []
+    t0 = time.time()
+    for N, cm in ((100, 256), (200, 1024)):
+        for D_ in (0.5, 1.0, 1.5):
+            p = G.make_params(prec=G.PREC_3XTF32, ctrl=G.CTRL_THRESHOLD, chi_max=cm, chi_init=16, max_sweeps=3)
+            W = ctx.build_mpo(G.XXZ, N, 1.0, D_)
+            m0 = torch.from_numpy(synth.initial_mps_entries(synth.workload_seed(50, N), N, 16)).cuda()
+            st = G.State(ctx, W, m0, p, 1.0, D_)
+            _, vis = st.sweep(3)
+            st.close()
+            by = {}
+            for v in vis:
+                by.setdefault(v.bond, []).append(v)
+            for vs in by.values():
+                for a, c in zip(vs[:-1], vs[1:]):
+                    X.append(list(a.feat))
+                    y.append(math.log2(max(1, c.k_star)))
+    trace_s = time.time() - t0
+    Xt = torch.tensor(X, dtype=torch.float32, device="cuda")
+    yt = torch.tensor(y, dtype=torch.float32, device="cuda")
+    u = synth.Xoshiro(synth.workload_seed(51, 0), lanes=64).uniform(G.MLP_NPARAM) * 2 - 1
+    P = np.zeros(G.MLP_NPARAM, dtype=np.float32)
+    H = 64
+    n1, n2, n3 = 10 * H, H * H, H
+    o2 = n1 + H
+    o3 = o2 + n2 + H
+    P[:n1] = u[:n1] * math.sqrt(6 / (10 + H))
+    P[o2:o2 + n2] = u[o2:o2 + n2] * math.sqrt(6 / (2 * H))
+    P[o3:o3 + n3] = u[o3:o3 + n3] * math.sqrt(6 / (H + 1))
+    P[o3 + n3] = float(np.mean(y))
+    Pd = torch.from_numpy(P).cuda()
+    m = torch.zeros_like(Pd); v = torch.zeros_like(Pd)
+    t1 = time.time()
+    l0 = ctx.mlp_loss_grad(Pd, Xt, yt)[0].item()
+    ctx.mlp_train(Pd, Xt, yt, m, v, 1, 4000, lr=3e-3)
+    l1 = ctx.mlp_loss_grad(Pd, Xt, yt)[0].item()
+    train_s = time.time() - t1
+    N, cm, sweeps = args.n_hi, args.chi_max, args.reps
+    out = {"micro": "learned", "train": {"samples": len(X), "loss_before": l0, "loss_after": l1,
+                                         "label_variance": float(np.var(y)), "trace_s": trace_s, "train_s": train_s},
+           "run": {"model": "J1-J2", "N": N, "J2": 0.24, "chi_max": cm, "sweeps": sweeps, "prec": "mixed"}}
+    for name, ctrl in (("pid", G.CTRL_PID), ("mlp", G.CTRL_MLP)):
+        c2 = G.Context(0)
+        p = G.make_params(prec=G.PREC_3XTF32, ctrl=ctrl, chi_max=cm, chi_init=4, max_sweeps=sweeps)
+        W = c2.build_mpo(G.J1J2, N, 1.0, 1.0, 0.24)
+        m0 = torch.from_numpy(synth.initial_mps_entries(synth.workload_seed(52, N), N, 4)).cuda()
+        st = G.State(c2, W, m0, p, 1.0, 1.0, 0.24)
+        if ctrl == G.CTRL_MLP:
+            st.set_mlp(Pd)
+        recs, vis = st.sweep(sweeps)
+        out[name] = {"energy_per_site": recs[-1].E / N, "s_per_sweep": sum(r.seconds for r in recs) / sweeps,
+                     "cost_k3": float(sum(float(x.k) ** 3 for x in vis)), "max_k": max(x.k for x in vis),
+                     "mean_k_last_sweep": float(np.mean([x.k for x in vis[-(2 * N - 3):]])),
+                     "network_chose": int(sum(x.mlp_used for x in vis)), "visits": len(vis)}
+        st.close()
+        c2.close()
+    ctx.close()
     return out
 
 
@@ -840,7 +916,20 @@ def isolated_svd(G, synth, chis=(256, 1024), fp64_chis=(256,), reps=3):
             ev1.record(ctx.stream)
             torch.cuda.synchronize()
             ms = ev0.elapsed_time(ev1) / reps
-            out[f"{form}_chi{chi}"] = {"ms": ms, "gflops_nominal": 21.0 * n ** 3 / (ms / 1e3) / 1e9}
+            e = {"ms": ms, "gflops_nominal": 21.0 * n ** 3 / (ms / 1e3) / 1e9}
+            # measured accuracy of the factors against the known spectrum
+            import numpy as np
+            U, sv, Vt, k, S, err = ctx.svd_truncate(A, n, 0.0)
+            An, Un, sn, Vn = (x.cpu().numpy() for x in (A, U, sv, Vt))
+            s_ref = synth.spectrum("exp", n, chi)
+            e["max_rel_err_s_top_half"] = float(np.max(np.abs(sn[:n // 2] - s_ref[:n // 2]) / s_ref[:n // 2]))
+            if form == "fp64":
+                eps = float(np.finfo(float).eps)
+                e["reconstruction_over_n_eps"] = float(np.linalg.norm((Un * sn) @ Vn - An) / np.linalg.norm(An)
+                                                       / (n * eps))
+                e["orthogonality_U_over_n_eps"] = float(np.abs(Un.T @ Un - np.eye(n)).max() / (n * eps))
+                e["orthogonality_V_over_n_eps"] = float(np.abs(Vn @ Vn.T - np.eye(n)).max() / (n * eps))
+            out[f"{form}_chi{chi}"] = e
             ctx.close()
     return out
 

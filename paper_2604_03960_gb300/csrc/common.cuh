@@ -146,7 +146,7 @@ struct dmrg_ctx {
     int gbj_min_r = 0;           // FP32 Jacobi: Gram-block cooperative form from this many vectors on (0 = off)
     double jacobi32_tol = 1e-6;  // FP32 Jacobi: rotate while a pair's cosine exceeds this
     int mixed_svd64 = 0;         // 3xTF32 form with the FP64 SVD and split (contractions alone in reduced precision)
-    int gjac32 = 1;              // FP32 Jacobi: grouped block kernel (gjacobi.cu): 0 never, 1 small problems, 2 always
+    int gjac32 = 0;              // FP32 Jacobi: grouped block kernel (gjacobi.cu): 0 never, 1 small problems, 2 always
     int gjac_nv = 0;             // ... vectors per block pair (16, 32; 0 = by size)
     int gjac_groups = 0;         // ... max groups per CTA (0 = by shared memory)
     int jacobi64_gram = 1;       // FP64 Jacobi: grouped block kernel (0: one warp per pair)

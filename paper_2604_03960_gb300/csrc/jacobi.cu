@@ -1233,9 +1233,10 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
     k_frob2_f<<<1, 1024, 0, st>>>(X, (long long)r * l, reinterpret_cast<double *>(sync + 4)); DMRG_COUNT_LAUNCH();
     prof_mark(ctx, PROF_JACOBI32);
     // grouped block Jacobi (Gram form, one 128-thread group per block pair):
-    // option gjac32 = 1 (default) for the small problems the single-CTA
-    // kernel would take, where it measured faster inside the sweeps; 2 for
-    // every size (at bulk sizes the blocked kernel below measured faster)
+    // option gjac32 = 1 for the problems that fit one CTA, 2 for every size.
+    // Off by default: measured, the single-CTA kernel below takes 2.45 ms on
+    // a 128 x 128 two-site tensor where the grouped one takes 3.85 ms, and
+    // the blocked kernel is 1.2-2x faster at the bulk sizes
     if (ctx->gjac32 == 2 || (ctx->gjac32 == 1 && (long long)r * l <= kSmemJacFloats)) {
         int nv = ctx->gjac_nv ? ctx->gjac_nv : (r <= 128 ? 32 : 16), groups = ctx->gjac_groups;
         if (!ctx->gjac_nv && !ctx->gjac_groups) tune_lookup_gjac(ctx, r, l, &nv, &groups);   // autotuned bucket

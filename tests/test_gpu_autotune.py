@@ -51,6 +51,7 @@ def test_gemm_tuning_roundtrip_and_bits(G, tmp_path):
 
 def test_svd_tuning_keeps_accuracy(G, tmp_path):
     ctx = G.Context(0)
+    ctx.set_option("gjac32", 1)
     n = 600
     # n = 200 takes the grouped Jacobi (one CTA's shared memory), n = 600 the blocked kernel
     ctx.autotune_svd([200, n], reps=1)
