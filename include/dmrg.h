@@ -167,7 +167,12 @@ const char *dmrg_status_string(dmrg_status s);
  * 256: tile width of the tensor-core GEMM, 0 = heuristic), "tc_split_kb"
  * (tensor-core GEMM: most 32-wide blocks of the 3 K split products one FP32
  * accumulator sums, 8; beyond, K is split and the slices added in FP64;
- * 0 = never split), "gjac32" (grouped block FP32 Jacobi: 0 never (default),
+ * 0 = never split), "cjac32" (1, default: the FP32 Jacobi of the mixed form
+ * runs on one 8-CTA thread-block cluster, vectors in blocks in the CTAs'
+ * shared memory and moved between them through distributed shared memory,
+ * for problems of at least "cjac_min_r" (32) vectors with at most 32 vectors
+ * a block and length <= 512; 0: the kernels below), "gjac32" (grouped block
+ * FP32 Jacobi: 0 never (default),
  * 1 for problems that fit one CTA's shared memory, 2 always), "gjac_nv" / "gjac_groups" (its vectors per block pair, 16 or
  * 32, and groups per CTA, 1-4; 0 = by size / autotuner), "jacobi64_gram"
  * (1: FP64 Jacobi on the grouped kernel, 0: one warp per pair),

@@ -1,0 +1,298 @@
+// cjacobi.cu -- FP32 one-sided Jacobi (Eq. 20) on one thread-block cluster.
+//
+// The mixed form's SVD of the two-site tensor orthogonalises r vectors (the
+// rows of X, length l) by plane rotations.  On one CTA every round of a sweep
+// moves all r x l values through one SM's shared-memory pipe; on a grid the
+// rounds pay a global barrier.  Here the work is spread over the C = 8 CTAs
+// of one cluster and only block moves cross SMs:
+//   * the vectors form 2C blocks of b = ceil(r / 2C); CTA c holds two of them
+//     (its "top" and "bottom" block) in shared memory;
+//   * a sweep first rotates the pairs inside every block (circle method on
+//     the b vectors of a block, both blocks of all CTAs at once), then runs
+//     2C - 1 block rounds: the b^2 pairs between the CTA's two blocks in b
+//     inner rounds of b disjoint pairs (top i with bottom (i + s) mod b),
+//     after which the blocks advance one place along the circle-method cycle
+//         bottom_0 -> top_1 -> ... -> top_{C-1} -> bottom_{C-1} -> ... -> bottom_0
+//     (top_0 stays), pushed into the receiving CTA's shared memory through
+//     distributed shared memory, and one cluster barrier;
+//   * so every pair of vectors meets exactly once a sweep (a cyclic
+//     ordering), and a sweep costs 2C cluster barriers;
+//   * one warp handles a pair: x_i . x_j from registers (two FP32 chains and
+//     a butterfly, so every lane holds the same sum), the 2 x 2 symmetric
+//     Schur rotation, and the squared norms carried along as
+//     |x_i'|^2 = |x_i|^2 - t g, |x_j'|^2 = |x_j|^2 + t g (recomputed at the
+//     start of every sweep).
+// The iteration stops after a sweep without rotations (cosine above the
+// tolerance), counted across the cluster in CTA 0's shared memory.  Vectors
+// keep their identity (an index travels with each), so the result is written
+// back to the rows it came from.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cooperative_groups.h>
+
+namespace dmrg {
+namespace {
+
+namespace cg = cooperative_groups;
+
+constexpr int kCjC = 8;             // CTAs per cluster (portable size)
+constexpr int kCjMaxB = 32;         // vectors per block: one warp per pair, <= 1024 threads
+
+__device__ __forceinline__ void cj_circle(int np, int t, int p, int &i, int &j)
+{
+    const int q = np - 1;
+    if (p == 0) {
+        i = q;
+        j = t;
+    } else {
+        i = (t + p) % q;
+        j = (t - p + q) % q;
+    }
+}
+
+// One pair on one warp.  xi, xj: the two vectors (length l, shared memory);
+// na, nb: their squared norms.  Returns true if a rotation was applied.
+template <int TM>
+__device__ __forceinline__ bool cj_pair(float *__restrict__ xi, float *__restrict__ xj, float *na, float *nb, int l,
+                                        float floor2, float tol, int lane)
+{
+    const float a = *na, b = *nb;
+    if (!(a > floor2 && b > floor2)) return false;
+    float u[TM], v[TM];
+    float g0 = 0.f, g1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < TM; ++q) {
+        const int k = lane + 32 * q;
+        u[q] = k < l ? xi[k] : 0.f;
+        v[q] = k < l ? xj[k] : 0.f;
+        if (q & 1)
+            g1 = fmaf(u[q], v[q], g1);
+        else
+            g0 = fmaf(u[q], v[q], g0);
+    }
+    float g = g0 + g1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+    if (!(fabsf(g) > tol * sqrtf(a) * sqrtf(b))) return false;
+    const float zeta = (b - a) / (2.0f * g);
+    const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+    const float c = rsqrtf(fmaf(t, t, 1.0f)), s = c * t;
+#pragma unroll
+    for (int q = 0; q < TM; ++q) {
+        const int k = lane + 32 * q;
+        if (k < l) {
+            xi[k] = fmaf(c, u[q], -s * v[q]);
+            xj[k] = fmaf(s, u[q], c * v[q]);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        *na = a - t * g;
+        *nb = b + t * g;
+    }
+    return true;
+}
+
+// Shared memory (dynamic, 16-byte aligned):
+//   blocks  [2 parities][2: top, bottom][b][ldl] floats
+//   norms   [2][2][b] floats
+//   ids     [2][2][b] ints
+//   counts  [3] unsigned: [0], [1] the cluster's rotations of even / odd
+//           sweeps (used on rank 0), [2] this CTA's rotations of the sweep
+template <int TM>
+__global__ void __cluster_dims__(kCjC, 1, 1) __launch_bounds__(1024)
+    k_cjac32(float *__restrict__ X, int r_all, int l, int ldl, int b, int max_sweeps, float tol,
+             const double *__restrict__ F2, double small, const int *__restrict__ r_eff_p, int *status, int *info)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) float cj_sm[];
+    const int C = kCjC;
+    const int crank = (int)cluster.block_rank();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long blk = (long long)b * ldl;
+    float *const nrm = cj_sm + 4 * blk;
+    int *const ids = reinterpret_cast<int *>(nrm + 4 * b);
+    unsigned *const cnt = reinterpret_cast<unsigned *>(ids + 4 * b);
+    auto slot = [&](int par, int tb) { return cj_sm + (long long)(par * 2 + tb) * blk; };
+    auto nslot = [&](int par, int tb) { return nrm + (par * 2 + tb) * b; };
+    auto islot = [&](int par, int tb) { return ids + (par * 2 + tb) * b; };
+
+    const int r_eff = r_eff_p ? min(r_all, max(1, *r_eff_p)) : r_all;
+    // initial placement: CTA c holds blocks c (top) and C + c (bottom)
+    for (int v = warp; v < 2 * b; v += nw) {
+        const int tb = v / b, i = v - tb * b;
+        const int beta = tb ? C + crank : crank;
+        const int id = beta * b + i;
+        float *x = slot(0, tb) + (long long)i * ldl;
+        for (int k = lane; k < ldl; k += 32) x[k] = (id < r_eff && k < l) ? X[(long long)id * l + k] : 0.f;
+        if (lane == 0) islot(0, tb)[i] = id;
+    }
+    if (threadIdx.x < 3) cnt[threadIdx.x] = 0u;
+    const float floor2 = (float)(small * small * F2[0]);
+    // every CTA of the cluster is running and initialised before any remote access
+    cluster.sync();
+
+    // destinations of the two blocks along the cycle (rank, slot)
+    const int dt_rank = crank == 0 ? 0 : (crank < C - 1 ? crank + 1 : crank);
+    const int dt_tb = crank == C - 1 ? 1 : 0;
+    const int db_rank = crank == 0 ? 1 : crank - 1;
+    const int db_tb = crank == 0 ? 0 : 1;
+    unsigned *const cnt_r0 = cluster.map_shared_rank(cnt, 0);
+
+    const int rp = b + (b & 1), half = rp / 2;
+    int par = 0, sweep = 0;
+    bool converged = false;
+    for (; sweep < max_sweeps; ++sweep) {
+        // squared norms of the CTA's two blocks
+        for (int v = warp; v < 2 * b; v += nw) {
+            const int tb = v / b, i = v - tb * b;
+            const float *x = slot(par, tb) + (long long)i * ldl;
+            float a0 = 0.f, a1 = 0.f;
+            int k = lane;
+            for (; k + 32 < l; k += 64) {
+                a0 = fmaf(x[k], x[k], a0);
+                a1 = fmaf(x[k + 32], x[k + 32], a1);
+            }
+            if (k < l) a0 = fmaf(x[k], x[k], a0);
+            float a = a0 + a1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) nslot(par, tb)[i] = a;
+        }
+        __syncthreads();
+        // 1. the pairs inside each block
+        for (int t = 0; t < rp - 1; ++t) {
+            if (warp < 2 * half) {
+                const int tb = warp / half, p = warp - tb * half;
+                int i, j;
+                cj_circle(rp, t, p, i, j);
+                if (i < b && j < b) {
+                    float *x = slot(par, tb);
+                    float *n = nslot(par, tb);
+                    if (cj_pair<TM>(x + (long long)i * ldl, x + (long long)j * ldl, n + i, n + j, l, floor2, tol,
+                                    lane) &&
+                        lane == 0)
+                        atomicAdd(&cnt[2], 1u);
+                }
+            }
+            __syncthreads();
+        }
+        // 2. block rounds
+        for (int br = 0; br < 2 * C - 1; ++br) {
+            for (int s = 0; s < b; ++s) {
+                if (warp < b) {
+                    const int i = warp, j = (warp + s) % b;
+                    if (cj_pair<TM>(slot(par, 0) + (long long)i * ldl, slot(par, 1) + (long long)j * ldl,
+                                    nslot(par, 0) + i, nslot(par, 1) + j, l, floor2, tol, lane) &&
+                        lane == 0)
+                        atomicAdd(&cnt[2], 1u);
+                }
+                __syncthreads();
+            }
+            // advance the blocks: push into the receivers' other parity
+            const int np = par ^ 1;
+            {
+                const float4 *st = reinterpret_cast<const float4 *>(slot(par, 0));
+                const float4 *sb = reinterpret_cast<const float4 *>(slot(par, 1));
+                float4 *dt = reinterpret_cast<float4 *>(cluster.map_shared_rank(slot(np, dt_tb), dt_rank));
+                float4 *db = reinterpret_cast<float4 *>(cluster.map_shared_rank(slot(np, db_tb), db_rank));
+                const int n4 = (int)(blk >> 2);
+                for (int e = threadIdx.x; e < n4; e += blockDim.x) {
+                    dt[e] = st[e];
+                    db[e] = sb[e];
+                }
+                if (threadIdx.x < b) {
+                    cluster.map_shared_rank(nslot(np, dt_tb), dt_rank)[threadIdx.x] = nslot(par, 0)[threadIdx.x];
+                    cluster.map_shared_rank(islot(np, dt_tb), dt_rank)[threadIdx.x] = islot(par, 0)[threadIdx.x];
+                } else if (threadIdx.x >= 32 && threadIdx.x < 32 + b) {
+                    const int i = threadIdx.x - 32;
+                    cluster.map_shared_rank(nslot(np, db_tb), db_rank)[i] = nslot(par, 1)[i];
+                    cluster.map_shared_rank(islot(np, db_tb), db_rank)[i] = islot(par, 1)[i];
+                }
+            }
+            cluster.sync();
+            par = np;
+        }
+        // convergence: rotations of this sweep over the cluster
+        if (threadIdx.x == 0) {
+            atomicAdd(&cnt_r0[sweep & 1], cnt[2]);
+            cnt[2] = 0u;
+        }
+        cluster.sync();
+        const unsigned total = *reinterpret_cast<volatile unsigned *>(&cnt_r0[sweep & 1]);
+        if (crank == 0 && threadIdx.x == 0) cnt[(sweep + 1) & 1] = 0u;
+        if (total == 0u) {
+            converged = true;
+            ++sweep;
+            break;
+        }
+    }
+    // write back to the rows the vectors came from
+    for (int v = warp; v < 2 * b; v += nw) {
+        const int tb = v / b, i = v - tb * b;
+        const int id = islot(par, tb)[i];
+        if (id >= r_eff) continue;
+        const float *x = slot(par, tb) + (long long)i * ldl;
+        for (int k = lane; k < l; k += 32) X[(long long)id * l + k] = x[k];
+    }
+    if (crank == 0 && threadIdx.x == 0) {
+        info[0] = converged ? sweep : -sweep;
+        if (!converged) atomicOr(status, ST_NOCONV);
+    }
+    // no CTA leaves while another may still read its shared memory
+    cluster.sync();
+}
+
+template <int TM>
+dmrg_status launch_cjac32(dmrg_ctx *ctx, float *X, int r, int l, int ldl, int b, int threads, size_t smem,
+                          int max_sweeps, float tol, const double *F2, double small, int *d_info, const int *r_eff)
+{
+    static bool attr = false;
+    if (!attr) {
+        DMRG_CUDA(cudaFuncSetAttribute(k_cjac32<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr = true;
+    }
+    k_cjac32<TM><<<kCjC, threads, smem, ctx->stream>>>(X, r, l, ldl, b, max_sweeps, tol, F2, small, r_eff,
+                                                       ctx->d_status, d_info);
+    DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
+}  // namespace
+
+size_t cjac32_smem_bytes(int r, int l)
+{
+    const int b = (r + 2 * kCjC - 1) / (2 * kCjC);
+    const int ldl = (l + 3) & ~3;
+    return sizeof(float) * (4ull * b * ldl + 4ull * b) + sizeof(int) * 4ull * b + 4 * sizeof(unsigned);
+}
+
+bool cjac32_fits(int r, int l)
+{
+    const int b = (r + 2 * kCjC - 1) / (2 * kCjC);
+    return r >= 1 && l >= 1 && b <= kCjMaxB && l <= 512 && cjac32_smem_bytes(r, l) <= 227 * 1024;
+}
+
+// X: r x l row-major FP32 (device), rotated in place; r_eff (device, may be
+// null): only the first *r_eff rows take part, the rest are left untouched.
+dmrg_status cjac32_run(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps, double tol, double small,
+                       const double *F2, int *d_info, const int *r_eff)
+{
+    if (!cjac32_fits(r, l)) return DMRG_EUNSUPPORTED;
+    const int b = (r + 2 * kCjC - 1) / (2 * kCjC);
+    const int ldl = (l + 3) & ~3;
+    const int rp = b + (b & 1);
+    const int threads = 32 * std::max(4, std::max(rp, b));
+    const size_t smem = cjac32_smem_bytes(r, l);
+    const int tm = (l + 31) / 32;
+    const float tf = (float)tol;
+    if (tm <= 4) return launch_cjac32<4>(ctx, X, r, l, ldl, b, threads, smem, max_sweeps, tf, F2, small, d_info, r_eff);
+    if (tm <= 8) return launch_cjac32<8>(ctx, X, r, l, ldl, b, threads, smem, max_sweeps, tf, F2, small, d_info, r_eff);
+    if (tm <= 12)
+        return launch_cjac32<12>(ctx, X, r, l, ldl, b, threads, smem, max_sweeps, tf, F2, small, d_info, r_eff);
+    return launch_cjac32<16>(ctx, X, r, l, ldl, b, threads, smem, max_sweeps, tf, F2, small, d_info, r_eff);
+}
+
+}  // namespace dmrg

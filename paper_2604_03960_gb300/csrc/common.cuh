@@ -146,6 +146,9 @@ struct dmrg_ctx {
     int gbj_min_r = 0;           // FP32 Jacobi: Gram-block cooperative form from this many vectors on (0 = off)
     double jacobi32_tol = 1e-6;  // FP32 Jacobi: rotate while a pair's cosine exceeds this
     int mixed_svd64 = 0;         // 3xTF32 form with the FP64 SVD and split (contractions alone in reduced precision)
+    int lz_fused = 1;            // Lanczos: one cooperative launch per step for the orthogonalisation
+    int cjac32 = 1;              // FP32 Jacobi: one-cluster kernel (cjacobi.cu) from cjac_min_r vectors on
+    int cjac_min_r = 32;
     int gjac32 = 0;              // FP32 Jacobi: grouped block kernel (gjacobi.cu): 0 never, 1 small problems, 2 always
     int gjac_nv = 0;             // ... vectors per block pair (16, 32; 0 = by size)
     int gjac_groups = 0;         // ... max groups per CTA (0 = by shared memory)
@@ -248,6 +251,10 @@ __device__ __forceinline__ double block_sum(double v, double *sh /* >= 32 */)
 
 // Gram-block FP32 Jacobi of one matrix on a cooperative grid (batched.cu).
 size_t gbj32_padded_bytes(int r, int l);
+size_t cjac32_smem_bytes(int r, int l);
+bool cjac32_fits(int r, int l);
+dmrg_status cjac32_run(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps, double tol, double small,
+                       const double *F2, int *d_info, const int *r_eff);
 dmrg_status gbj32_sweeps(dmrg_ctx *ctx, const double *A, int m, int n, int dir, float *X, float *Xp, void *qrw,
                          unsigned *sync, int max_sweeps, double tol, double small, int *d_info);
 dmrg_status frob2_f32(dmrg_ctx *ctx, const float *A, long long n, double *F2);

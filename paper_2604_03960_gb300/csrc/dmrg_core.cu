@@ -658,6 +658,21 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         ctx->jacobi32_tol = value;
         return DMRG_OK;
     }
+    if (!std::strcmp(name, "lz_fused")) {
+        if (!(value == 0.0 || value == 1.0)) return DMRG_EINVAL;
+        ctx->lz_fused = (int)value;
+        return DMRG_OK;
+    }
+    if (!std::strcmp(name, "cjac32")) {
+        if (!(value == 0.0 || value == 1.0)) return DMRG_EINVAL;
+        ctx->cjac32 = (int)value;
+        return DMRG_OK;
+    }
+    if (!std::strcmp(name, "cjac_min_r")) {
+        if (!(value >= 2.0 && value <= 1e6)) return DMRG_EINVAL;
+        ctx->cjac_min_r = (int)value;
+        return DMRG_OK;
+    }
     if (!std::strcmp(name, "gjac32")) {
         if (value != 0.0 && value != 1.0 && value != 2.0) return DMRG_EINVAL;
         ctx->gjac32 = (int)value;

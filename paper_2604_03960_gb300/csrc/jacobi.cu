@@ -1237,7 +1237,15 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
     // Off by default: measured, the single-CTA kernel below takes 2.45 ms on
     // a 128 x 128 two-site tensor where the grouped one takes 3.85 ms, and
     // the blocked kernel is 1.2-2x faster at the bulk sizes
-    if (ctx->gjac32 == 2 || (ctx->gjac32 == 1 && (long long)r * l <= kSmemJacFloats)) {
+    bool done = false;
+    if (ctx->cjac32 && r >= ctx->cjac_min_r && cjac32_fits(r, l)) {
+        // one thread-block cluster: blocks of vectors in the CTAs' shared
+        // memory, moved between them through distributed shared memory
+        DMRG_TRY(cjac32_run(ctx, X, r, l, max_sweeps, tol, small, F2, d_info, reff));
+        done = true;
+    }
+    if (done) {
+    } else if (ctx->gjac32 == 2 || (ctx->gjac32 == 1 && (long long)r * l <= kSmemJacFloats)) {
         int nv = ctx->gjac_nv ? ctx->gjac_nv : (r <= 128 ? 32 : 16), groups = ctx->gjac_groups;
         if (!ctx->gjac_nv && !ctx->gjac_groups) tune_lookup_gjac(ctx, r, l, &nv, &groups);   // autotuned bucket
         DMRG_TRY(gjac_run<float>(ctx, X, r, l, l, l, 0, max_sweeps, tol, small, F2, sync, d_info, reff, nv, groups));

@@ -189,6 +189,130 @@ __global__ void __launch_bounds__(RB) k_multiaxpy_norm(double *__restrict__ w, c
     *counter = 0u;
 }
 
+// Column sums of acc[0..nq) over the block (FP64, fixed order), written to
+// part[q]; red: (MAXQ + 1) x RB doubles of shared memory.
+__device__ __forceinline__ void block_cols_to(const double *acc, int nq, double *red, double *part)
+{
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q)
+        if (q < nq) red[q * RB + threadIdx.x] = acc[q];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = warp; q < nq; q += RB / 32) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < RB / 32; ++k) s += red[q * RB + lane + 32 * k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) part[q] = s;
+    }
+}
+
+// Sum of the blocks' partials part[b * stride + q] for q < nq, b < G, in
+// block order (every CTA gets the same bits); result to cs[q].
+__device__ __forceinline__ void sum_parts(const double *part, int stride, int nq, double *cs)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = warp; q < nq; q += RB / 32) {
+        double s = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(&part[(long long)b * stride + q]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) cs[q] = s;
+    }
+    __syncthreads();
+}
+
+// One Lanczos step's orthogonalisation in one cooperative launch (the five
+// launches above fused; three bounded grid barriers):
+//   c = V^T w (v_0..v_j), alpha_j = c_j;  w -= V c, and in the same pass
+//   c' = V^T w;  w -= V c', |w|^2;  beta_{j+1} = |w|, continuation as in
+//   k_multiaxpy_norm;  v_{j+1} = w / beta_{j+1} if the recurrence goes on.
+// Each thread keeps its elements' v_q in registers between the update and
+// the next dot product, so V is read three times instead of four.
+// part: 3 x gridDim.x x (MAXQ + 1) doubles; bar: two zeroed words.
+__global__ void __launch_bounds__(RB) k_lz_orth(double *__restrict__ V, double *__restrict__ w, long long n, int j,
+                                                LzState *lz, double *__restrict__ part, unsigned *bar, int *status)
+{
+    if (!lz->active) return;                 // written by an earlier launch: the same in every CTA
+    extern __shared__ double red[];          // (MAXQ + 1) x RB
+    __shared__ double cs[MAXQ + 1];
+    const int nq = j + 1;
+    const int K = lz->K;
+    const double amax0 = lz->amax;
+    const int S = MAXQ + 1;
+    double *p0 = part, *p1 = part + (long long)gridDim.x * S, *p2 = part + 2LL * gridDim.x * S;
+    const long long stride = (long long)gridDim.x * RB;
+    const long long i0 = (long long)blockIdx.x * RB + threadIdx.x;
+    double acc[MAXQ];
+    // phase A: c = V^T w
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) acc[q] = 0.0;
+    for (long long i = i0; i < n; i += stride) {
+        const double wi = w[i];
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q)
+            if (q < nq) acc[q] = fma(V[(long long)q * n + i], wi, acc[q]);
+    }
+    block_cols_to(acc, nq, red, p0 + (long long)blockIdx.x * S);
+    if (!grid_barrier(bar, status)) return;
+    sum_parts(p0, S, nq, cs);
+    const double alpha = cs[j];
+    const double amax = fmax(amax0, fabs(alpha));
+    // phase B: w -= V c, c' = V^T w
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) acc[q] = 0.0;
+    for (long long i = i0; i < n; i += stride) {
+        double v[MAXQ];
+        double a = 0.0;
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q)
+            if (q < nq) {
+                v[q] = V[(long long)q * n + i];
+                a = fma(cs[q], v[q], a);
+            }
+        const double wi = w[i] - a;
+        w[i] = wi;
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q)
+            if (q < nq) acc[q] = fma(v[q], wi, acc[q]);
+    }
+    __syncthreads();                         // cs is rewritten below
+    block_cols_to(acc, nq, red, p1 + (long long)blockIdx.x * S);
+    if (!grid_barrier(bar, status)) return;
+    sum_parts(p1, S, nq, cs);
+    // phase C: w -= V c', |w|^2
+    double ss = 0.0;
+    for (long long i = i0; i < n; i += stride) {
+        double a = 0.0;
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q)
+            if (q < nq) a = fma(cs[q], V[(long long)q * n + i], a);
+        const double wi = w[i] - a;
+        w[i] = wi;
+        ss = fma(wi, wi, ss);
+    }
+    __syncthreads();
+    acc[0] = ss;
+    block_cols_to(acc, 1, red, p2 + (long long)blockIdx.x * S);
+    if (!grid_barrier(bar, status)) return;
+    sum_parts(p2, S, 1, cs);
+    // phase D: beta_{j+1}, continuation, next vector
+    const double bta = sqrt(cs[0]);
+    const bool go = (j + 1 < K) && (bta > 1e-14 * amax) && isfinite(bta);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        lz->alpha[j] = alpha;
+        lz->amax = amax;
+        lz->beta[j + 1] = bta;
+        lz->m = j + 1;
+        if (!go) lz->active = 0;
+        if (!isfinite(bta)) lz->nan = 1;
+    }
+    if (go) {
+        const double inv = 1.0 / bta;
+        double *vn = V + (long long)(j + 1) * n;
+        for (long long i = i0; i < n; i += stride) vn[i] = w[i] * inv;
+    }
+}
+
 // dst = src * lz->scale  (start vector / Ritz vector normalisation)
 __global__ void k_scale_by(double *__restrict__ dst, const double *__restrict__ src, long long n, const LzState *lz)
 {
@@ -218,27 +342,48 @@ __global__ void k_lz_init(LzState *lz, int K)
     for (int i = 0; i < LZ_MAXK; ++i) { lz->alpha[i] = 0.0; lz->y[i] = 0.0; }
 }
 
-// number of eigenvalues of the m x m tridiagonal (a, b[1..m-1]) below x
+// Number of eigenvalues of the m x m tridiagonal (a, b[1..m-1]) below x:
+// the negative pivots q_i = p_i / p_{i-1} of T - x I (Sylvester's inertia),
+// read off as sign changes of the leading minors p_i = (a_i - x) p_{i-1} -
+// b_i^2 p_{i-2}.  No division (FP64 division is a long dependent sequence on
+// this part); the minors are rescaled by 2^-500 / 2^500 when they leave
+// [2^-500, 2^500], which keeps every ratio.  A zero minor takes the sign of
+// the previous one (its pivot counts as +0, as in the quotient form).
 __device__ int sturm_count(int m, const double *a, const double *b, double x)
 {
     int cnt = 0;
-    double q = a[0] - x;
-    if (q < 0.0) cnt++;
+    double pm = 1.0, p = a[0] - x;
+    if (p == 0.0) p = 1e-300;
+    if (p < 0.0) cnt++;
     for (int i = 1; i < m; ++i) {
-        double qq = (q != 0.0) ? q : 1e-300;
-        q = (a[i] - x) - b[i] * b[i] / qq;
-        if (q < 0.0) cnt++;
+        double pn = fma(a[i] - x, p, -(b[i] * b[i]) * pm);
+        if (pn == 0.0) pn = (p < 0.0) ? -1e-300 : 1e-300;
+        if ((pn < 0.0) != (p < 0.0)) cnt++;
+        pm = p;
+        p = pn;
+        const double ap = fabs(p);
+        if (ap > 3.273390607896142e150) {            // 2^500
+            p *= 3.054936363499605e-151;             // 2^-500
+            pm *= 3.054936363499605e-151;
+        } else if (ap < 3.054936363499605e-151) {
+            p *= 3.273390607896142e150;
+            pm *= 3.273390607896142e150;
+        }
     }
     return cnt;
 }
 
 // Lowest eigenpair of T by one warp: multisection with 32 Sturm counts per
-// step (the interval shrinks 33x per step), then inverse iteration on one lane.
+// step (the interval shrinks 33x per step) until it is a few units in the
+// last place wide, then inverse iteration on one lane.
 __global__ void k_tridiag_lowest(LzState *lz, int *status)
 {
     const int lane = threadIdx.x & 31;
     const int m = lz->m;
-    const double *a = lz->alpha, *b = lz->beta;   // b[i] couples i-1 and i
+    __shared__ double a[LZ_MAXK], b[LZ_MAXK + 1];  // b[i] couples i-1 and i
+    for (int i = lane; i < m; i += 32) a[i] = lz->alpha[i];
+    for (int i = lane; i <= m && i <= LZ_MAXK; i += 32) b[i] = lz->beta[i];
+    __syncwarp();
     double lo = 1e300, hi = -1e300;
     for (int i = 0; i < m; ++i) {
         double r = (i > 0 ? fabs(b[i]) : 0.0) + (i + 1 < m ? fabs(b[i + 1]) : 0.0);
@@ -248,17 +393,20 @@ __global__ void k_tridiag_lowest(LzState *lz, int *status)
     lo -= 1e-300;
     for (int it = 0; it < 40; ++it) {
         const double w = hi - lo;
-        if (!(w > 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)))) break;
+        if (!(w > 4.440892098500626e-16 * fmax(fabs(lo), fabs(hi)))) break;
         const double x = lo + w * (double)(lane + 1) / 33.0;
         const unsigned below = __ballot_sync(0xffffffffu, sturm_count(m, a, b, x) >= 1);
+        double nlo = lo, nhi = hi;
         if (below == 0u) {
-            lo = lo + w * 32.0 / 33.0;
+            nlo = lo + w * 32.0 / 33.0;
         } else {
             const int f = __ffs(below) - 1;            // first point at or above lambda_0
-            const double nhi = lo + w * (double)(f + 1) / 33.0;
-            lo = (f > 0) ? lo + w * (double)f / 33.0 : lo;
-            hi = nhi;
+            nhi = lo + w * (double)(f + 1) / 33.0;
+            nlo = (f > 0) ? lo + w * (double)f / 33.0 : lo;
         }
+        if (nlo == lo && nhi == hi) break;             // no representable progress
+        lo = nlo;
+        hi = nhi;
     }
     if (lane != 0) return;
     const double lam = 0.5 * (lo + hi);
@@ -298,6 +446,16 @@ __global__ void k_tridiag_lowest(LzState *lz, int *status)
 int grid_dot(long long n, int num_sms)
 {
     long long b = (n + RB - 1) / RB;
+    if (b > num_sms) b = num_sms;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// fused orthogonalisation grid: at least 4 elements a thread, at most one
+// block per SM (all co-resident: the launch is cooperative)
+int grid_orth(long long n, int num_sms)
+{
+    long long b = (n + 4 * RB - 1) / (4 * RB);
     if (b > num_sms) b = num_sms;
     if (b < 1) b = 1;
     return (int)b;
@@ -353,16 +511,38 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
         DMRG_CUDA(cudaFuncSetAttribute(k_multidot<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
         dsm_attr = true;
     }
-    DMRG_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned), st));
+    DMRG_CUDA(cudaMemsetAsync(w.counter, 0, 64, st));    // last-block counter and grid-barrier words
     k_lz_init<<<1, 1, 0, st>>>(w.lz, K); DMRG_COUNT_LAUNCH();
     ReduceArgs ra{nullptr, n, 0, theta, n, w.partials, w.counter};
     k_multidot<3><<<gd, RB, dsm, st>>>(ra, w.lz, 0, nullptr); DMRG_COUNT_LAUNCH();          // |theta|
     k_scale_by<<<g, RB, 0, st>>>(w.V, theta, n, w.lz); DMRG_COUNT_LAUNCH();                // v0
     DMRG_CUDA(cudaGetLastError());
+    const int gc = grid_orth(n, ctx->num_sms);
+    static bool orth_attr = false;
+    if (!orth_attr) {
+        DMRG_CUDA(cudaFuncSetAttribute(k_lz_orth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+        orth_attr = true;
+    }
     for (int j = 0; j < K; ++j) {
         double *vj = w.V + (size_t)n * j;
         DMRG_TRY(matvec(vj, w.w));
         prof_mark(ctx, PROF_LZ_VEC);
+        if (ctx->lz_fused) {
+            // both Gram-Schmidt passes, the norm and v_{j+1} in one cooperative launch
+            double *Vp = w.V, *wp = w.w, *pp = w.partials;
+            long long nn = n;
+            int jj = j;
+            LzState *lzp = w.lz;
+            unsigned *bar = w.counter + 4;
+            int *stp = ctx->d_status;
+            void *args[] = {&Vp, &wp, &nn, &jj, &lzp, &pp, &bar, &stp};
+            DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_lz_orth, dim3(gc), dim3(RB), args, dsm, st));
+            DMRG_COUNT_LAUNCH();
+            prof_mark(ctx, PROF_LZ_VEC);
+            prof_count(ctx, PROF_LZ_VEC, 0.0, 8.0 * (double)n * (3.0 * (j + 1) + 7.0));
+            DMRG_CUDA(cudaGetLastError());
+            continue;
+        }
         // Full reorthogonalisation by two classical Gram-Schmidt passes on
         // w = H v_j against v_0..v_j.  The first pass subtracts alpha_j v_j and
         // beta_j v_{j-1} with the rest (the three-term step is contained in

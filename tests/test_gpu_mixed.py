@@ -132,6 +132,39 @@ def test_mixed_svd_exact_spectrum(G, chi, opt):
     c.close()
 
 
+@pytest.mark.parametrize("m,n", [(64, 64), (66, 70), (94, 130), (130, 94), (201, 199), (256, 256), (300, 300),
+                                 (40, 500), (450, 450)])
+@pytest.mark.parametrize("cj", [1, 0])
+def test_mixed_svd_cluster_kernel(G, m, n, cj):
+    """The FP32 Jacobi on one thread-block cluster (option cjac32 = 1: blocks
+    of vectors in eight CTAs' shared memory, moved through distributed shared
+    memory) and the single-CTA / grid kernels it replaces (cjac32 = 0) on
+    ragged and rectangular shapes (blocks of 2..29 vectors, padded blocks,
+    lengths not a multiple of 32): both meet the exact-spectrum bar of the
+    mixed SVD, and both converge (status word clean)."""
+    c = G.Context(0)
+    c.set_option("svd_prec", 1)
+    c.set_option("cjac32", cj)
+    r = min(m, n)
+    s_ref = synth.spectrum("exp", r, max(2, r // 2))
+    A = synth.svd_test_matrix(synth.workload_seed(4, m * 1000 + n), m, n, s_ref)
+    U, s, Vt, k, S, err = c.svd_truncate(torch.from_numpy(A).cuda(), r, 1e-10)
+    U, s, Vt = (x.cpu().numpy() for x in (U, s, Vt))
+    fro = np.sqrt(np.sum(s_ref ** 2))
+    assert np.all(np.abs(s[:k] - s_ref[:k]) <= 1e-7 * s_ref[:k] + 8 * np.sqrt(r) * 2.0 ** -24 * fro)
+    # the Jacobi's vectors lie along the longer side and become the isometry
+    # (U if n <= m, else V); the other factor is the projection scaled by 1/s
+    iso = U[:, :k] if n <= m else Vt[:k].T
+    assert np.abs(iso.T @ iso - np.eye(k)).max() <= 0.75 * k * 1e-10
+    Ak = (U[:, :k] * s[:k]) @ Vt[:k]
+    tail = np.sqrt(np.sum(s_ref[k:] ** 2))
+    assert np.linalg.norm(Ak - A) <= tail + 1e-6 * np.linalg.norm(A)
+    S_ref, _ = O.entropy(s_ref)
+    assert abs(S - S_ref) <= 1e-6
+    c.status()
+    c.close()
+
+
 def test_hold_mode_freezes_the_schedule(G, ctx):
     """DMRG_CTRL_HOLD set between sweeps keeps every bond at the chi its PID
     reached: the controller chi of the held sweeps equals the last PID sweep's
