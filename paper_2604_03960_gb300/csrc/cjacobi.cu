@@ -74,9 +74,21 @@ __device__ __forceinline__ bool cj_pair(float *__restrict__ xi, float *__restric
     float g = g0 + g1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-    if (!(fabsf(g) > tol * sqrtf(a) * sqrtf(b))) return false;
-    const float zeta = (b - a) / (2.0f * g);
-    const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+    // the rotation from the special-function unit (reciprocal and reciprocal
+    // square root, a few ulp): any angle this close to the Jacobi angle
+    // orthogonalises the pair to well below the tolerance, and c, s come
+    // from one rsqrt so c^2 + s^2 = 1 to its accuracy
+    if (!(fabsf(g) * rsqrtf(a) * rsqrtf(b) > tol)) return false;
+    const float zeta = __fdividef(b - a, 2.0f * g);
+    const float az = fabsf(zeta);
+    float t;
+    if (az > 1e15f) {
+        t = __fdividef(0.5f, az);
+    } else {
+        const float q = fmaf(zeta, zeta, 1.0f);
+        t = __fdividef(1.0f, az + q * rsqrtf(q));
+    }
+    t = copysignf(t, zeta);
     const float c = rsqrtf(fmaf(t, t, 1.0f)), s = c * t;
 #pragma unroll
     for (int q = 0; q < TM; ++q) {
@@ -143,6 +155,7 @@ __global__ void __cluster_dims__(kCjC, 1, 1) __launch_bounds__(1024)
     const int rp = b + (b & 1), half = rp / 2;
     int par = 0, sweep = 0;
     bool converged = false;
+    unsigned my_rot = 0u;                    // this warp's rotations in the sweep
     for (; sweep < max_sweeps; ++sweep) {
         // squared norms of the CTA's two blocks
         for (int v = warp; v < 2 * b; v += nw) {
@@ -170,10 +183,8 @@ __global__ void __cluster_dims__(kCjC, 1, 1) __launch_bounds__(1024)
                 if (i < b && j < b) {
                     float *x = slot(par, tb);
                     float *n = nslot(par, tb);
-                    if (cj_pair<TM>(x + (long long)i * ldl, x + (long long)j * ldl, n + i, n + j, l, floor2, tol,
-                                    lane) &&
-                        lane == 0)
-                        atomicAdd(&cnt[2], 1u);
+                    my_rot += cj_pair<TM>(x + (long long)i * ldl, x + (long long)j * ldl, n + i, n + j, l, floor2,
+                                          tol, lane);
                 }
             }
             __syncthreads();
@@ -183,10 +194,8 @@ __global__ void __cluster_dims__(kCjC, 1, 1) __launch_bounds__(1024)
             for (int s = 0; s < b; ++s) {
                 if (warp < b) {
                     const int i = warp, j = (warp + s) % b;
-                    if (cj_pair<TM>(slot(par, 0) + (long long)i * ldl, slot(par, 1) + (long long)j * ldl,
-                                    nslot(par, 0) + i, nslot(par, 1) + j, l, floor2, tol, lane) &&
-                        lane == 0)
-                        atomicAdd(&cnt[2], 1u);
+                    my_rot += cj_pair<TM>(slot(par, 0) + (long long)i * ldl, slot(par, 1) + (long long)j * ldl,
+                                          nslot(par, 0) + i, nslot(par, 1) + j, l, floor2, tol, lane);
                 }
                 __syncthreads();
             }
@@ -215,6 +224,9 @@ __global__ void __cluster_dims__(kCjC, 1, 1) __launch_bounds__(1024)
             par = np;
         }
         // convergence: rotations of this sweep over the cluster
+        if (lane == 0 && my_rot) atomicAdd(&cnt[2], my_rot);
+        my_rot = 0u;
+        __syncthreads();
         if (threadIdx.x == 0) {
             atomicAdd(&cnt_r0[sweep & 1], cnt[2]);
             cnt[2] = 0u;

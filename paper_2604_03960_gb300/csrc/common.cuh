@@ -146,6 +146,7 @@ struct dmrg_ctx {
     int gbj_min_r = 0;           // FP32 Jacobi: Gram-block cooperative form from this many vectors on (0 = off)
     double jacobi32_tol = 1e-6;  // FP32 Jacobi: rotate while a pair's cosine exceeds this
     int mixed_svd64 = 0;         // 3xTF32 form with the FP64 SVD and split (contractions alone in reduced precision)
+    int tc_presplit = 1;         // matvec: L, R split once per update; x and the mix output split by their producers
     int lz_fused = 1;            // Lanczos: one cooperative launch per step for the orthogonalisation
     int cjac32 = 1;              // FP32 Jacobi: one-cluster kernel (cjacobi.cu) from cjac_min_r vectors on
     int cjac_min_r = 32;
@@ -287,6 +288,87 @@ dmrg_status gemm_3xtf32(dmrg_ctx *ctx, int M, int N, int K, double alpha, const 
                         long long sBb, double beta, double *C, long long sCm, long long sCn, long long sCb,
                         int batch);
 bool tc_available(dmrg_ctx *ctx);
+// Whether gemm_3xtf32 of this shape runs on the tensor cores (else on the
+// FP32 CUDA-core kernel): the split operands below are only read there.
+bool tc_path(dmrg_ctx *ctx, int M, int N, int K, int batch);
+// Padded K of the split layout: the three TF32 parts of a row of K values
+// lie at [0, Kp), [Kp, 2 Kp), [2 Kp, 3 Kp), zero beyond K, Kp = K rounded up to 32.
+inline int split_kp(int K) { return (K + 31) / 32 * 32; }
+// Split operand in the tensor-core layout: out[b][row][slice * Kp + col] for
+// the R x Kc operand element (row, col) at in[b s_b + row s_row + col s_col].
+// pattern 0 (left operand): (hi, hi, lo); pattern 1 (right operand): (hi, lo, hi).
+dmrg_status split3_dev(dmrg_ctx *ctx, const double *in, long long s_row, long long s_col, long long s_b, int R,
+                       int Kc, int batch, int pattern, float *out);
+// gemm_3xtf32 with either operand already split (nullptr: split here).
+dmrg_status gemm_3xtf32_pre(dmrg_ctx *ctx, int M, int N, int K, double alpha, const double *A, long long sAm,
+                            long long sAk, long long sAb, const double *B, long long sBk, long long sBn,
+                            long long sBb, double beta, double *C, long long sCm, long long sCn, long long sCb,
+                            int batch, const float *Ah_pre, const float *Bh_pre);
+
+// FP32 -> FP64 by integer operations (exact, like the converting
+// instruction, which runs on the narrow FP64 pipe of this part); zeros,
+// subnormals, infinities and NaNs take the instruction.
+__device__ __forceinline__ double f32_widen(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    if (e == 0u || e == 0xffu) return (double)f;
+    const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// FP64 -> FP32 rounded to nearest even by integer operations, bit-identical
+// to the converting instruction in the normal range; zeros, subnormal or
+// overflowing results, infinities and NaNs take the instruction.
+__device__ __forceinline__ float f64_narrow(double v)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+    const uint32_t e = (hi >> 20) & 0x7ffu;
+    if ((hi & 0x7fffffffu) == 0u && lo == 0u) return __uint_as_float(hi & 0x80000000u);
+    if (e < 897u || e > 1150u) return (float)v;             // outside the FP32 normal exponents
+    // 23 kept mantissa bits: 20 from hi, 3 from lo; 29 dropped bits in lo
+    uint32_t r = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t drop = lo & 0x1fffffffu;
+    if (drop > 0x10000000u || (drop == 0x10000000u && (r & 1u))) ++r;   // a carry may reach the exponent
+    if ((r >> 23) >= 0xffu) return (float)v;                 // rounded up to infinity
+    return __uint_as_float(r | (hi & 0x80000000u));
+}
+
+// hi = tf32(float(v)), lo = tf32(float(v - hi)): the two TF32 parts of an
+// FP64 value (the split of the 3xTF32 products)
+__device__ __forceinline__ float tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ void tf32_split(double v, float &hi, float &lo)
+{
+    // conversions by integer operations; the one subtraction is exact
+    hi = tf32_rna(f64_narrow(v));
+    lo = tf32_rna(f64_narrow(v - f32_widen(hi)));
+}
+
+// Where a producer kernel also writes the right-operand split of the vector
+// it produces, viewed as a K x n4 row-major matrix (element i = k n4 + c):
+// h[c 3Kp + k] = hi, h[c 3Kp + Kp + k] = lo, h[c 3Kp + 2Kp + k] = hi.
+struct SplitSink {
+    float *h = nullptr;
+    long long n4 = 0;
+    int Kp = 0;
+};
+__device__ __forceinline__ void sink_write(const SplitSink &s, long long i, double v)
+{
+    float hi, lo;
+    tf32_split(v, hi, lo);
+    const long long k = i / s.n4, c = i - k * s.n4;
+    float *o = s.h + c * 3LL * s.Kp + k;
+    o[0] = hi;
+    o[s.Kp] = lo;
+    o[2LL * s.Kp] = hi;
+}
 
 // Dispatch on precision.
 dmrg_status gemm(dmrg_ctx *ctx, int prec, int M, int N, int K, double alpha, const double *A, long long sAm,

@@ -102,6 +102,9 @@ struct MixDesc {
     long long in_sx, in_sy, in_sa, out_sx, out_sy, out_sa;
     int An, Bn;
     int f32;        // 1: multiply-adds in FP32 (the mixed form's H_eff, whose GEMMs are FP32-accurate)
+    float *yh = nullptr;   // also write the left-operand split of the output, viewed as rows of y_rs
+    long long y_rs = 0;
+    int ykp = 0;
 };
 
 // out[channel o][a][b] = sum_i C[o][i] in[channel i][a][b]; b is unit stride.
@@ -113,6 +116,7 @@ __global__ void __launch_bounds__(kMixThreads) k_mix(const double *__restrict__ 
                                                      const double *__restrict__ C, MixDesc d)
 {
     __shared__ double val[kMaxCh * kMaxCh];
+    __shared__ float valf[kMaxCh * kMaxCh];        // the same, rounded once (FP32 mixing)
     __shared__ unsigned char col[kMaxCh * kMaxCh];
     __shared__ int rowptr[kMaxCh + 1];
     __shared__ int rowcnt[kMaxCh];
@@ -122,9 +126,19 @@ __global__ void __launch_bounds__(kMixThreads) k_mix(const double *__restrict__ 
     // nonzero its slot; the row counts become offsets by a scan in one warp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kWarps = kMixThreads / 32;
-    for (int o = warp; o < d.nout; o += kWarps) {
-        const double v = lane < d.nin ? C[o * d.nin + lane] : 0.0;
-        const unsigned nzm = __ballot_sync(0xffffffffu, v != 0.0);
+    constexpr int kRowsPerWarp = (kMaxCh + kWarps - 1) / kWarps;
+    // all loads of the table at once (one memory latency, not one per row)
+    double cv[kRowsPerWarp];
+#pragma unroll
+    for (int t = 0; t < kRowsPerWarp; ++t) {
+        const int o = warp + t * kWarps;
+        cv[t] = (o < d.nout && lane < d.nin) ? C[o * d.nin + lane] : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < kRowsPerWarp; ++t) {
+        const int o = warp + t * kWarps;
+        if (o >= d.nout) break;
+        const unsigned nzm = __ballot_sync(0xffffffffu, cv[t] != 0.0);
         if (lane == 0) rowcnt[o] = __popc(nzm);
     }
     __syncthreads();
@@ -139,12 +153,16 @@ __global__ void __launch_bounds__(kMixThreads) k_mix(const double *__restrict__ 
         if (lane == d.nout - 1) rowptr[d.nout] = incl;
     }
     __syncthreads();
-    for (int o = warp; o < d.nout; o += kWarps) {
-        const double v = lane < d.nin ? C[o * d.nin + lane] : 0.0;
+#pragma unroll
+    for (int t = 0; t < kRowsPerWarp; ++t) {
+        const int o = warp + t * kWarps;
+        if (o >= d.nout) break;
+        const double v = cv[t];
         const unsigned nzm = __ballot_sync(0xffffffffu, v != 0.0);
         if (v != 0.0) {
             const int slot = rowptr[o] + __popc(nzm & ((1u << lane) - 1u));
             val[slot] = v;
+            valf[slot] = (float)v;
             col[slot] = (unsigned char)lane;
         }
     }
@@ -155,20 +173,42 @@ __global__ void __launch_bounds__(kMixThreads) k_mix(const double *__restrict__ 
         const long long e = e0 + threadIdx.x;
         const bool ok = e < total;
         const int a = ok ? (int)(e / d.Bn) : 0, b = ok ? (int)(e % d.Bn) : 0;
+        if (d.f32) {
+            // FP64 lanes are scarce on this part: the mixed form mixes in FP32,
+            // with the inputs narrowed and the outputs widened by integer
+            // operations (bit-identical to the converting instructions)
+            float *xf = reinterpret_cast<float *>(&xs[0][0]);     // [kMaxCh][kMixThreads]
+            for (int c = 0; c < d.nin; ++c) {
+                const int x = c / d.in_ny, y = c % d.in_ny;
+                xf[c * kMixThreads + threadIdx.x] = ok ? f64_narrow(in[x * d.in_sx + y * d.in_sy + a * d.in_sa + b]) : 0.f;
+            }
+            if (!ok) continue;
+            for (int o = 0; o < d.nout; ++o) {
+                float acc = 0.f;
+                for (int q = rowptr[o]; q < rowptr[o + 1]; ++q)
+                    acc = fmaf(valf[q], xf[col[q] * kMixThreads + threadIdx.x], acc);
+                const int x = o / d.out_ny, y = o % d.out_ny;
+                const long long f = x * d.out_sx + y * d.out_sy + a * d.out_sa + b;
+                if (d.yh) {
+                    // only the next GEMM's left-operand parts (hi, hi, lo), the
+                    // bits its split of (double)acc would give: acc - hi is exact in FP32
+                    const float hi = tf32_rna(acc), lo = tf32_rna(acc - hi);
+                    const long long mrow = f / d.y_rs, kk = f - mrow * d.y_rs;
+                    float *q = d.yh + mrow * 3LL * d.ykp + kk;
+                    q[0] = hi;
+                    q[d.ykp] = hi;
+                    q[2LL * d.ykp] = lo;
+                } else {
+                    out[f] = f32_widen(acc);
+                }
+            }
+            continue;
+        }
         for (int c = 0; c < d.nin; ++c) {
             const int x = c / d.in_ny, y = c % d.in_ny;
             xs[c][threadIdx.x] = ok ? in[x * d.in_sx + y * d.in_sy + a * d.in_sa + b] : 0.0;
         }
-        if (ok && d.f32) {
-            // FP64 lanes are scarce on this part: the mixed form mixes in FP32
-            for (int o = 0; o < d.nout; ++o) {
-                float acc = 0.f;
-                for (int q = rowptr[o]; q < rowptr[o + 1]; ++q)
-                    acc = fmaf((float)val[q], (float)xs[col[q]][threadIdx.x], acc);
-                const int x = o / d.out_ny, y = o % d.out_ny;
-                out[x * d.out_sx + y * d.out_sy + a * d.out_sa + b] = (double)acc;
-            }
-        } else if (ok) {
+        if (ok) {
             for (int o = 0; o < d.nout; ++o) {
                 double acc = 0.0;
                 for (int q = rowptr[o]; q < rowptr[o + 1]; ++q) acc = fma(val[q], xs[col[q]][threadIdx.x], acc);
@@ -438,19 +478,42 @@ static dmrg_status mix(dmrg_ctx *ctx, const double *in, double *out, const doubl
 
 // y = H_eff x. L: [w][a'][a] (D cl cl); Rt: [u][b][b'] (D cr cr); C: (4D)^2;
 // X, Y: D*cl*4*cr doubles each.
+// Pre-split tensor-core operands of the matvec's two GEMMs (any may be null).
+struct HeffPre {
+    const float *Lh = nullptr, *Rh = nullptr, *xh = nullptr;
+    float *Yh = nullptr;
+};
+
 dmrg_status heff_apply_dev(dmrg_ctx *ctx, int prec, int D, int cl, int cr, const double *L, const double *Rt,
-                           const double *C, double *X, double *Y, const double *x, double *y)
+                           const double *C, double *X, double *Y, const double *x, double *y,
+                           const HeffPre *pre = nullptr)
 {
     const long long n4 = 4LL * cr;
-    DMRG_TRY(gemm(ctx, prec, D * cl, (int)n4, cl, 1.0, L, cl, 1, 0, x, n4, 1, 0, 0.0, X, n4, 1, 0, 1));
+    const bool p1 = pre && prec == DMRG_PREC_3XTF32 && pre->Lh && pre->xh;
+    const bool p2 = pre && prec == DMRG_PREC_3XTF32 && pre->Yh && pre->Rh;
+    if (p1)
+        DMRG_TRY(gemm_3xtf32_pre(ctx, D * cl, (int)n4, cl, 1.0, L, cl, 1, 0, x, n4, 1, 0, 0.0, X, n4, 1, 0, 1, pre->Lh,
+                                 pre->xh));
+    else
+        DMRG_TRY(gemm(ctx, prec, D * cl, (int)n4, cl, 1.0, L, cl, 1, 0, x, n4, 1, 0, 0.0, X, n4, 1, 0, 1));
     MixDesc md;
     md.f32 = prec != DMRG_PREC_FP64;
     md.nin = 4 * D; md.nout = 4 * D; md.in_ny = 4; md.out_ny = 4;
     md.in_sx = (long long)cl * n4; md.in_sy = cr; md.in_sa = n4;
     md.out_sx = cr; md.out_sy = (long long)D * cr; md.out_sa = 4LL * D * cr;
     md.An = cl; md.Bn = cr;
+    if (p2) {
+        md.yh = pre->Yh;
+        md.y_rs = (long long)D * cr;
+        md.ykp = split_kp(D * cr);
+    }
     DMRG_TRY(mix(ctx, X, Y, C, md));
-    DMRG_TRY(gemm(ctx, prec, 4 * cl, cr, D * cr, 1.0, Y, (long long)D * cr, 1, 0, Rt, cr, 1, 0, 0.0, y, cr, 1, 0, 1));
+    if (p2)
+        DMRG_TRY(gemm_3xtf32_pre(ctx, 4 * cl, cr, D * cr, 1.0, Y, (long long)D * cr, 1, 0, Rt, cr, 1, 0, 0.0, y, cr,
+                                 1, 0, 1, pre->Yh, pre->Rh));
+    else
+        DMRG_TRY(gemm(ctx, prec, 4 * cl, cr, D * cr, 1.0, Y, (long long)D * cr, 1, 0, Rt, cr, 1, 0, 0.0, y, cr, 1, 0,
+                      1));
     return DMRG_OK;
 }
 
@@ -549,6 +612,9 @@ struct dmrg_state {
     std::vector<double *> A, env;
     dmrg_ctrl_state *ctrl = nullptr;
     double *theta = nullptr, *X = nullptr, *Y = nullptr;
+    // tensor-core split operands of the matvec, made once per local update
+    // (L, R) or by their producers (the Lanczos vector, the mix output)
+    float *Lh = nullptr, *Rh = nullptr, *xh = nullptr, *Yh = nullptr;
     double *U = nullptr, *s = nullptr, *Vt = nullptr;
     void *svdw = nullptr;
     LanczosWork lw;
@@ -656,6 +722,11 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
     if (!std::strcmp(name, "jacobi32_tol")) {
         if (!(value >= 1e-8 && value <= 1e-2)) return DMRG_EINVAL;
         ctx->jacobi32_tol = value;
+        return DMRG_OK;
+    }
+    if (!std::strcmp(name, "tc_presplit")) {
+        if (!(value == 0.0 || value == 1.0)) return DMRG_EINVAL;
+        ctx->tc_presplit = (int)value;
         return DMRG_OK;
     }
     if (!std::strcmp(name, "lz_fused")) {
@@ -818,12 +889,34 @@ static dmrg_status bond_step_a(dmrg_state *st, int k, int go_right, int do_ctrl,
     // Lanczos on H_eff (Eq. 19)
     const double *L = st->env[k], *Rt = st->env[k + 2];
     const double *C = st->coef_mv + (size_t)k * (4 * D) * (4 * D);
+    // tensor-core matvecs: L and R split once for the whole Lanczos run, the
+    // Lanczos vector and the mix output split by the kernels that make them
+    HeffPre pre;
+    SplitSink sink;
+    if (prec == DMRG_PREC_3XTF32 && ctx->tc_presplit) {
+        if (tc_path(ctx, D * cl, 4 * cr, cl, 1)) {
+            DMRG_TRY(split3_dev(ctx, L, cl, 1, 0, D * cl, cl, 1, 0, st->Lh));
+            pre.Lh = st->Lh;
+            pre.xh = st->xh;
+            sink.h = st->xh;
+            sink.n4 = 4LL * cr;
+            sink.Kp = split_kp(cl);
+            // the producers write columns k < K only: the padding must read as zero
+            DMRG_CUDA(cudaMemsetAsync(st->xh, 0, sizeof(float) * (size_t)4 * cr * 3 * split_kp(cl), ctx->stream));
+        }
+        if (tc_path(ctx, 4 * cl, cr, D * cr, 1)) {
+            DMRG_TRY(split3_dev(ctx, Rt, 1, cr, 0, cr, D * cr, 1, 1, st->Rh));
+            pre.Rh = st->Rh;
+            pre.Yh = st->Yh;
+            DMRG_CUDA(cudaMemsetAsync(st->Yh, 0, sizeof(float) * (size_t)4 * cl * 3 * split_kp(D * cr), ctx->stream));
+        }
+    }
     MatvecFn mv = [&](const double *x, double *y) {
-        return heff_apply_dev(ctx, prec, D, cl, cr, L, Rt, C, st->X, st->Y, x, y);
+        return heff_apply_dev(ctx, prec, D, cl, cr, L, Rt, C, st->X, st->Y, x, y, &pre);
     };
     const int K = (int)std::min<long long>(st->K, nn);
     P.K = K;
-    DMRG_TRY(lanczos_run(ctx, st->lw, nn, K, st->theta, mv));
+    DMRG_TRY(lanczos_run(ctx, st->lw, nn, K, st->theta, mv, sink.h ? &sink : nullptr));
     if (prec != DMRG_PREC_FP64 && k == 0 && direction == -1) {
         // last visit of a sweep: the sweep energy is the FP64 Rayleigh
         // quotient of the Ritz vector (second order in its error), so the
@@ -1008,6 +1101,13 @@ dmrg_status dmrg_state_create(dmrg_ctx *ctx, int D, const dmrg_model_params *mp,
     size_t off_info = total; total += al256(sizeof(int) * 4);
     size_t off_vis = total; total += al256(sizeof(dmrg_visit_record) * (2 * N));
     size_t off_mlp = total; total += al256(sizeof(float) * MLP_NPARAM);
+    long long cmax = 1;
+    for (int i = 0; i <= N; ++i) cmax = std::max<long long>(cmax, st->cap[i]);
+    const long long kp_c = split_kp((int)cmax), kp_dc = split_kp((int)(D * cmax));
+    size_t off_Lh = total; total += al256(sizeof(float) * (size_t)(D * cmax) * 3 * kp_c);
+    size_t off_Rh = total; total += al256(sizeof(float) * (size_t)cmax * 3 * kp_dc);
+    size_t off_xh = total; total += al256(sizeof(float) * (size_t)(4 * cmax) * 3 * kp_c);
+    size_t off_Yh = total; total += al256(sizeof(float) * (size_t)(4 * cmax) * 3 * kp_dc);
     if (st->arena.ensure(total) != DMRG_OK) { delete st; return DMRG_ENOMEM; }
     char *base = st->arena.as<char>();
     size_t o = 0;
@@ -1034,6 +1134,10 @@ dmrg_status dmrg_state_create(dmrg_ctx *ctx, int D, const dmrg_model_params *mp,
     st->d_info = reinterpret_cast<int *>(base + off_info);
     st->d_visits = reinterpret_cast<dmrg_visit_record *>(base + off_vis);
     st->mlp = reinterpret_cast<float *>(base + off_mlp);
+    st->Lh = reinterpret_cast<float *>(base + off_Lh);
+    st->Rh = reinterpret_cast<float *>(base + off_Rh);
+    st->xh = reinterpret_cast<float *>(base + off_xh);
+    st->Yh = reinterpret_cast<float *>(base + off_Yh);
     if (cudaMallocHost(&st->h_res, sizeof(BondResult)) != cudaSuccess) { st->arena.release(); delete st; return DMRG_ENOMEM; }
     if (cudaEventCreateWithFlags(&st->ev_res, cudaEventDisableTiming) != cudaSuccess) {
         cudaFreeHost(st->h_res); st->arena.release(); delete st; return DMRG_ECUDA;

@@ -230,31 +230,43 @@ __global__ void __launch_bounds__(128, 1)
     __syncwarp();
     if (!ok) *abort_flag = 1;
     if (!*abort_flag && nkl > 0) {
-        const int row = warp * 32 + lane;
-        const int gm = m0 + row;
-        double *crow = C + (long long)bz * sCb + (long long)gm * sCm;
+        // Each warp's 32 rows x 32 columns go through a shared-memory tile
+        // (the stage buffers are idle once every MMA has completed), so that
+        // a warp then stores 32 consecutive columns of one row at a time;
+        // FP32 -> FP64 is widened with integer operations (the FP64 pipe,
+        // which the converting instruction uses, is narrow on this part).
+        float *tile = reinterpret_cast<float *>(gbase) + warp * (32 * 33);
         const long long nbatch = gridDim.z / nsl;
-        double *prow = P ? P + (((long long)sl * nbatch + bz) * M + gm) * (long long)N : nullptr;
+        const bool plain = (alpha == 1.0) && (beta == 0.0);
 #pragma unroll 1
         for (int c = 0; c < BN / 32; ++c) {
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-            if (gm < M) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int gn = n0 + c * 32 + j;
-                    if (gn < N) {
-                        if (prow) {
-                            prow[gn] = (double)__uint_as_float(r[j]);
+            for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
+            __syncwarp();
+            const int gn = n0 + c * 32 + lane;
+            if (gn < N) {
+#pragma unroll 4
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int gm = m0 + warp * 32 + rr;
+                    if (gm >= M) break;
+                    const double x = f32_widen(tile[rr * 33 + lane]);
+                    if (P) {
+                        P[(((long long)sl * nbatch + bz) * M + gm) * (long long)N + gn] = x;
+                    } else {
+                        double *p = C + (long long)bz * sCb + (long long)gm * sCm + (long long)gn * sCn;
+                        if (plain) {
+                            *p = x;
                         } else {
-                            double *p = crow + (long long)gn * sCn;
-                            double v = alpha * (double)__uint_as_float(r[j]);
+                            double v = alpha * x;
                             if (beta != 0.0) v += beta * *p;
                             *p = v;
                         }
                     }
                 }
             }
+            __syncwarp();
         }
     }
     tc_fence_before();
@@ -279,25 +291,25 @@ __global__ void k_tc_reduce(const double *__restrict__ P, int nsl, int batch, in
                             double *__restrict__ C, long long sCm, long long sCn, long long sCb)
 {
     const long long per = (long long)M * N, total = per * batch, slice = total;
+    const bool plain = (alpha == 1.0) && (beta == 0.0);
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        double a = 0.0;
-        for (int q = 0; q < nsl; ++q) a += P[q * slice + e];
+        double a = P[e];
+        for (int q = 1; q < nsl; ++q) a += P[q * slice + e];
         const long long b = e / per, mn = e % per;
         const int m = (int)(mn / N), n = (int)(mn % N);
         double *c = C + b * sCb + (long long)m * sCm + (long long)n * sCn;
-        double v = alpha * a;
-        if (beta != 0.0) v += beta * *c;
-        *c = v;
+        if (plain) {
+            *c = a;
+        } else {
+            double v = alpha * a;
+            if (beta != 0.0) v += beta * *c;
+            *c = v;
+        }
     }
 }
 
-__device__ __forceinline__ float to_tf32(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
+__device__ __forceinline__ float to_tf32(float x) { return tf32_rna(x); }
 
 // out[b][row][slice * Kp + col] = slice of in(b, row, col), rows R, cols Kc,
 // zero for Kc <= col < Kp.  pattern 0: (hi, hi, lo); pattern 1: (hi, lo, hi).
@@ -313,8 +325,8 @@ __global__ void k_split3(const double *__restrict__ in, long long s_row, long lo
         if (colfast) { rr = threadIdx.y + 8 * i; cc = threadIdx.x; } else { rr = threadIdx.x; cc = threadIdx.y + 8 * i; }
         const int r = r0 + rr, c = c0 + cc;
         const double v = (r < R && c < Kc) ? src[(long long)r * s_row + (long long)c * s_col] : 0.0;
-        const float h = to_tf32((float)v);
-        const float l = to_tf32((float)(v - (double)h));
+        float h, l;
+        tf32_split(v, h, l);
         hi_t[rr][cc] = h;
         lo_t[rr][cc] = l;
     }
@@ -424,9 +436,35 @@ int tc_pick_bn(dmrg_ctx *ctx, int M, int N, int K, int batch)
     return (w128 < w256) ? 128 : 256;
 }
 
+bool tc_path(dmrg_ctx *ctx, int M, int N, int K, int batch)
+{
+    return M > 0 && N > 0 && batch > 0 && K > 0 && tc_available(ctx) &&
+           (ctx->tc_force || (double)M * N * K * batch >= (double)ctx->tc_min_work);
+}
+
+dmrg_status split3_dev(dmrg_ctx *ctx, const double *in, long long s_row, long long s_col, long long s_b, int R,
+                       int Kc, int batch, int pattern, float *out)
+{
+    if (R <= 0 || Kc <= 0 || batch <= 0) return DMRG_OK;
+    const int Kp = split_kp(Kc);
+    dim3 g(Kp / 32, (R + 31) / 32, batch);
+    k_split3<<<g, dim3(32, 8), 0, ctx->stream>>>(in, s_row, s_col, s_b, R, Kc, Kp, out, pattern); DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
 dmrg_status gemm_3xtf32(dmrg_ctx *ctx, int M, int N, int K, double alpha, const double *A, long long sAm,
                         long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
                         double beta, double *C, long long sCm, long long sCn, long long sCb, int batch)
+{
+    return gemm_3xtf32_pre(ctx, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb, batch,
+                           nullptr, nullptr);
+}
+
+dmrg_status gemm_3xtf32_pre(dmrg_ctx *ctx, int M, int N, int K, double alpha, const double *A, long long sAm,
+                            long long sAk, long long sAb, const double *B, long long sBk, long long sBn,
+                            long long sBb, double beta, double *C, long long sCm, long long sCn, long long sCb,
+                            int batch, const float *Ah_pre, const float *Bh_pre)
 {
     if (M <= 0 || N <= 0 || batch <= 0) return DMRG_OK;
     if (!tc_available(ctx)) return DMRG_EUNSUPPORTED;
@@ -460,13 +498,19 @@ dmrg_status gemm_3xtf32(dmrg_ctx *ctx, int M, int N, int K, double alpha, const 
     float *Ah = ctx->tcbuf.as<float>();
     float *Bh = reinterpret_cast<float *>(reinterpret_cast<char *>(Ah) + al(bytesA));
     double *P = reinterpret_cast<double *>(reinterpret_cast<char *>(Bh) + al(bytesB));
-    {
+    if (!Ah_pre) {
         dim3 g(Kp / 32, (M + 31) / 32, batch);
         k_split3<<<g, dim3(32, 8), 0, ctx->stream>>>(A, sAm, sAk, sAb, M, K, Kp, Ah, 0); DMRG_COUNT_LAUNCH();
+    } else {
+        Ah = const_cast<float *>(Ah_pre);
+    }
+    if (!Bh_pre) {
         dim3 g2(Kp / 32, (N + 31) / 32, batch);
         k_split3<<<g2, dim3(32, 8), 0, ctx->stream>>>(B, sBn, sBk, sBb, N, K, Kp, Bh, 1); DMRG_COUNT_LAUNCH();
-        DMRG_CUDA(cudaGetLastError());
+    } else {
+        Bh = const_cast<float *>(Bh_pre);
     }
+    DMRG_CUDA(cudaGetLastError());
     const int bn = tc_pick_bn(ctx, M, N, K, batch);
     if (bn == 128) return launch_tc<128>(ctx, Ah, Bh, M, N, K3, batch, alpha, beta, C, sCm, sCn, sCb, nsl, P);
     return launch_tc<256>(ctx, Ah, Bh, M, N, K3, batch, alpha, beta, C, sCm, sCn, sCb, nsl, P);

@@ -230,7 +230,8 @@ __device__ __forceinline__ void sum_parts(const double *part, int stride, int nq
 // the next dot product, so V is read three times instead of four.
 // part: 3 x gridDim.x x (MAXQ + 1) doubles; bar: two zeroed words.
 __global__ void __launch_bounds__(RB) k_lz_orth(double *__restrict__ V, double *__restrict__ w, long long n, int j,
-                                                LzState *lz, double *__restrict__ part, unsigned *bar, int *status)
+                                                LzState *lz, double *__restrict__ part, unsigned *bar, int *status,
+                                                SplitSink sink)
 {
     if (!lz->active) return;                 // written by an earlier launch: the same in every CTA
     extern __shared__ double red[];          // (MAXQ + 1) x RB
@@ -309,8 +310,20 @@ __global__ void __launch_bounds__(RB) k_lz_orth(double *__restrict__ V, double *
     if (go) {
         const double inv = 1.0 / bta;
         double *vn = V + (long long)(j + 1) * n;
-        for (long long i = i0; i < n; i += stride) vn[i] = w[i] * inv;
+        for (long long i = i0; i < n; i += stride) {
+            const double v = w[i] * inv;
+            vn[i] = v;
+            if (sink.h) sink_write(sink, i, v);   // the next matvec's split right operand
+        }
     }
+}
+
+// The split of a vector for the next matvec (start vector; the unfused path)
+__global__ void k_sink_vec(const double *__restrict__ v, long long n, SplitSink sink, const LzState *lz)
+{
+    if (lz && !lz->active) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) sink_write(sink, i, v[i]);
 }
 
 // dst = src * lz->scale  (start vector / Ritz vector normalisation)
@@ -373,6 +386,32 @@ __device__ int sturm_count(int m, const double *a, const double *b, double x)
     return cnt;
 }
 
+// The same count in FP32 on FP32 copies of T (64x the FP64 rate on this
+// part): only used to narrow the bracket that the FP64 counts then refine.
+__device__ int sturm_count_f(int m, const float *a, const float *b, float x)
+{
+    int cnt = 0;
+    float pm = 1.f, p = a[0] - x;
+    if (p == 0.f) p = 1e-30f;
+    if (p < 0.f) cnt++;
+    for (int i = 1; i < m; ++i) {
+        float pn = fmaf(a[i] - x, p, -(b[i] * b[i]) * pm);
+        if (pn == 0.f) pn = (p < 0.f) ? -1e-30f : 1e-30f;
+        if ((pn < 0.f) != (p < 0.f)) cnt++;
+        pm = p;
+        p = pn;
+        const float ap = fabsf(p);
+        if (ap > 1.8446744e19f) {                    // 2^64
+            p *= 5.421011e-20f;
+            pm *= 5.421011e-20f;
+        } else if (ap < 5.421011e-20f) {
+            p *= 1.8446744e19f;
+            pm *= 1.8446744e19f;
+        }
+    }
+    return cnt;
+}
+
 // Lowest eigenpair of T by one warp: multisection with 32 Sturm counts per
 // step (the interval shrinks 33x per step) until it is a few units in the
 // last place wide, then inverse iteration on one lane.
@@ -381,8 +420,15 @@ __global__ void k_tridiag_lowest(LzState *lz, int *status)
     const int lane = threadIdx.x & 31;
     const int m = lz->m;
     __shared__ double a[LZ_MAXK], b[LZ_MAXK + 1];  // b[i] couples i-1 and i
-    for (int i = lane; i < m; i += 32) a[i] = lz->alpha[i];
-    for (int i = lane; i <= m && i <= LZ_MAXK; i += 32) b[i] = lz->beta[i];
+    __shared__ float af[LZ_MAXK], bf[LZ_MAXK + 1];
+    for (int i = lane; i < m; i += 32) {
+        a[i] = lz->alpha[i];
+        af[i] = (float)a[i];
+    }
+    for (int i = lane; i <= m && i <= LZ_MAXK; i += 32) {
+        b[i] = lz->beta[i];
+        bf[i] = (float)b[i];
+    }
     __syncwarp();
     double lo = 1e300, hi = -1e300;
     for (int i = 0; i < m; ++i) {
@@ -391,18 +437,52 @@ __global__ void k_tridiag_lowest(LzState *lz, int *status)
         hi = fmax(hi, a[i] + r);
     }
     lo -= 1e-300;
+    {
+        // FP32 multisection down to about 1e-5 of the Gershgorin scale, then
+        // a bracket widened by that much and checked with two FP64 counts
+        // (none below lo, at least one below hi); if the check fails the
+        // FP64 multisection starts from the Gershgorin interval instead
+        const double scale = fmax(fabs(lo), fabs(hi));
+        float flo = (float)lo, fhi = (float)hi;
+        const float cf = (float)(lane + 1) * (1.f / 33.f);
+        for (int it = 0; it < 8; ++it) {
+            const float w = fhi - flo;
+            if (!(w > 1e-6f * (float)scale)) break;
+            const float x = fmaf(w, cf, flo);
+            const unsigned below = __ballot_sync(0xffffffffu, sturm_count_f(m, af, bf, x) >= 1);
+            const int f = below ? __ffs(below) - 1 : 31;
+            const float xf = __shfl_sync(0xffffffffu, x, f), xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
+            if (below == 0u) {
+                flo = xf;                                  // every probe lies below lambda_0
+            } else {
+                flo = (f > 0) ? xp : flo;
+                fhi = xf;
+            }
+        }
+        const double margin = 1e-5 * scale;
+        const double clo = fmax(lo, (double)flo - margin), chi = fmin(hi, (double)fhi + margin);
+        int c = 0;
+        if (lane < 2) c = sturm_count(m, a, b, lane == 0 ? clo : chi);
+        const int c_lo = __shfl_sync(0xffffffffu, c, 0), c_hi = __shfl_sync(0xffffffffu, c, 1);
+        if (c_lo == 0 && c_hi >= 1 && clo < chi) {
+            lo = clo;
+            hi = chi;
+        }
+    }
+    const double cd = (double)(lane + 1) * (1.0 / 33.0);
     for (int it = 0; it < 40; ++it) {
         const double w = hi - lo;
         if (!(w > 4.440892098500626e-16 * fmax(fabs(lo), fabs(hi)))) break;
-        const double x = lo + w * (double)(lane + 1) / 33.0;
+        const double x = fmin(fma(w, cd, lo), hi);
         const unsigned below = __ballot_sync(0xffffffffu, sturm_count(m, a, b, x) >= 1);
+        const int f = below ? __ffs(below) - 1 : 31;   // first point at or above lambda_0
+        const double xf = __shfl_sync(0xffffffffu, x, f), xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
         double nlo = lo, nhi = hi;
         if (below == 0u) {
-            nlo = lo + w * 32.0 / 33.0;
+            nlo = xf;
         } else {
-            const int f = __ffs(below) - 1;            // first point at or above lambda_0
-            nhi = lo + w * (double)(f + 1) / 33.0;
-            nlo = (f > 0) ? lo + w * (double)f / 33.0 : lo;
+            nhi = xf;
+            nlo = (f > 0) ? xp : lo;
         }
         if (nlo == lo && nhi == hi) break;             // no representable progress
         lo = nlo;
@@ -411,25 +491,25 @@ __global__ void k_tridiag_lowest(LzState *lz, int *status)
     if (lane != 0) return;
     const double lam = 0.5 * (lo + hi);
     lz->E = lam;
-    double y[LZ_MAXK], rhs[LZ_MAXK], dd[LZ_MAXK], ll[LZ_MAXK];
+    double y[LZ_MAXK], rhs[LZ_MAXK], rd[LZ_MAXK], ll[LZ_MAXK];
     const double shift = lam - 1e-13 * fmax(fabs(lam), 1e-300) - 1e-300;
     for (int i = 0; i < m; ++i) y[i] = 1.0 / sqrt((double)m) * (1.0 + 0.01 * i);
-    // factor T - shift I once (LU without pivoting), then two solves
-    dd[0] = a[0] - shift;
-    for (int i = 1; i < m; ++i) {
-        double piv = (dd[i - 1] != 0.0) ? dd[i - 1] : 1e-300;
-        ll[i] = b[i] / piv;
-        dd[i] = (a[i] - shift) - ll[i] * b[i];
+    // factor T - shift I once (LU without pivoting), keeping the reciprocal
+    // pivots, so the two solves multiply instead of divide
+    {
+        double d = a[0] - shift;
+        rd[0] = 1.0 / ((d != 0.0) ? d : 1e-300);
+        for (int i = 1; i < m; ++i) {
+            ll[i] = b[i] * rd[i - 1];
+            d = (a[i] - shift) - ll[i] * b[i];
+            rd[i] = 1.0 / ((d != 0.0) ? d : 1e-300);
+        }
     }
     for (int it = 0; it < 2; ++it) {
         for (int i = 0; i < m; ++i) rhs[i] = y[i];
         for (int i = 1; i < m; ++i) rhs[i] -= ll[i] * rhs[i - 1];
-        double piv = (dd[m - 1] != 0.0) ? dd[m - 1] : 1e-300;
-        y[m - 1] = rhs[m - 1] / piv;
-        for (int i = m - 2; i >= 0; --i) {
-            double p = (dd[i] != 0.0) ? dd[i] : 1e-300;
-            y[i] = (rhs[i] - b[i + 1] * y[i + 1]) / p;
-        }
+        y[m - 1] = rhs[m - 1] * rd[m - 1];
+        for (int i = m - 2; i >= 0; --i) y[i] = (rhs[i] - b[i + 1] * y[i + 1]) * rd[i];
         double nn = 0.0;
         for (int i = 0; i < m; ++i) nn += y[i] * y[i];
         nn = 1.0 / sqrt(nn);
@@ -451,11 +531,12 @@ int grid_dot(long long n, int num_sms)
     return (int)b;
 }
 
-// fused orthogonalisation grid: at least 4 elements a thread, at most one
-// block per SM (all co-resident: the launch is cooperative)
+// fused orthogonalisation grid: one element a thread up to one block per SM
+// (all co-resident: the launch is cooperative); the FP64 multiply-adds of
+// the passes, 2 per clock per SM on this part, want every SM at large n
 int grid_orth(long long n, int num_sms)
 {
-    long long b = (n + 4 * RB - 1) / (4 * RB);
+    long long b = (n + RB - 1) / RB;
     if (b > num_sms) b = num_sms;
     if (b < 1) b = 1;
     return (int)b;
@@ -496,8 +577,10 @@ LanczosWork lanczos_work_carve(void *base, long long n, int K, int num_sms)
 }
 
 dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K, double *theta,
-                        const MatvecFn &matvec)
+                        const MatvecFn &matvec, const SplitSink *sink_p)
 {
+    SplitSink sink;
+    if (sink_p) sink = *sink_p;
     if (K < 1) K = 1;
     if (K > LZ_MAXK) K = LZ_MAXK;
     if ((long long)K > n) K = (int)n;
@@ -516,6 +599,7 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
     ReduceArgs ra{nullptr, n, 0, theta, n, w.partials, w.counter};
     k_multidot<3><<<gd, RB, dsm, st>>>(ra, w.lz, 0, nullptr); DMRG_COUNT_LAUNCH();          // |theta|
     k_scale_by<<<g, RB, 0, st>>>(w.V, theta, n, w.lz); DMRG_COUNT_LAUNCH();                // v0
+    if (sink.h) { k_sink_vec<<<g, RB, 0, st>>>(w.V, n, sink, nullptr); DMRG_COUNT_LAUNCH(); }
     DMRG_CUDA(cudaGetLastError());
     const int gc = grid_orth(n, ctx->num_sms);
     static bool orth_attr = false;
@@ -535,7 +619,7 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
             LzState *lzp = w.lz;
             unsigned *bar = w.counter + 4;
             int *stp = ctx->d_status;
-            void *args[] = {&Vp, &wp, &nn, &jj, &lzp, &pp, &bar, &stp};
+            void *args[] = {&Vp, &wp, &nn, &jj, &lzp, &pp, &bar, &stp, &sink};
             DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_lz_orth, dim3(gc), dim3(RB), args, dsm, st));
             DMRG_COUNT_LAUNCH();
             prof_mark(ctx, PROF_LZ_VEC);
@@ -554,7 +638,12 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
         k_multidot<0><<<gd, RB, dsm, st>>>(a2, w.lz, j, w.c); DMRG_COUNT_LAUNCH();
         k_multiaxpy_norm<<<gd, RB, 0, st>>>(w.w, w.V, n, j + 1, w.c, n, w.lz, j, w.partials, w.counter);
         DMRG_COUNT_LAUNCH();
-        if (j + 1 < K) k_next_vec<<<g, RB, 0, st>>>(w.V + (size_t)n * (j + 1), w.w, n, w.lz, j); DMRG_COUNT_LAUNCH();
+        if (j + 1 < K) {
+            k_next_vec<<<g, RB, 0, st>>>(w.V + (size_t)n * (j + 1), w.w, n, w.lz, j); DMRG_COUNT_LAUNCH();
+            if (sink.h) {
+                k_sink_vec<<<g, RB, 0, st>>>(w.V + (size_t)n * (j + 1), n, sink, w.lz); DMRG_COUNT_LAUNCH();
+            }
+        }
         prof_mark(ctx, PROF_LZ_VEC);
         // two Gram-Schmidt passes: (j + 1) basis vectors read twice in each,
         // the work vector about six times, 8 B each

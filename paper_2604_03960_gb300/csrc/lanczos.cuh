@@ -32,7 +32,9 @@ size_t lanczos_work_bytes(long long n, int K, int num_sms);
 LanczosWork lanczos_work_carve(void *base, long long n, int K, int num_sms);
 // theta: start vector on entry, normalised Ritz vector on exit; the Ritz
 // value is left in work.lz->E (device).
+// sink (may be null): where each new Lanczos vector's right-operand split
+// for the next tensor-core matvec is written as well
 dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K, double *theta,
-                        const MatvecFn &matvec);
+                        const MatvecFn &matvec, const SplitSink *sink = nullptr);
 
 }  // namespace dmrg

@@ -165,6 +165,28 @@ def test_mixed_svd_cluster_kernel(G, m, n, cj):
     c.close()
 
 
+def test_presplit_matvec_is_bit_identical(G):
+    """Option tc_presplit: L and R split into TF32 parts once per local
+    update, the Lanczos vector and the mix output split by the kernels that
+    produce them.  Same parts, same products, same order: the sweep must give
+    the same bits as splitting every operand before every product."""
+    out = []
+    for ps in (1, 0):
+        c = G.Context(0)
+        c.set_option("tc_force", 1)
+        c.set_option("tc_presplit", ps)
+        st, recs, vis = run(G, c, 16, 3, G.PREC_3XTF32, ctrl=G.CTRL_THRESHOLD, chi_max=64, chi_init=8)
+        n = st.mps_size()
+        host = torch.empty(n, dtype=torch.float64)
+        st.get_mps(host)
+        out.append((np.array([r.E for r in recs]), np.array([v.k for v in vis]), host.numpy().copy()))
+        st.close()
+        c.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
+
+
 def test_hold_mode_freezes_the_schedule(G, ctx):
     """DMRG_CTRL_HOLD set between sweeps keeps every bond at the chi its PID
     reached: the controller chi of the held sweeps equals the last PID sweep's
