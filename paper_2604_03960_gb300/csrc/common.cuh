@@ -113,6 +113,7 @@ struct dmrg_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // tensor-core GEMM path
     dmrg::DevBuf tcbuf;          // split TF32 operands
+    dmrg::DevBuf f64buf;         // split-K partial sums of the FP64 GEMM
     int tc_ok = -1;              // -1 unknown, 0 no, 1 yes
     int tc_bn_override = 0;      // force a tile width (autotuner / tests)
     int tc_force = 0;            // use the tensor cores even for tiny products
@@ -146,6 +147,7 @@ struct dmrg_ctx {
     int gbj_min_r = 0;           // FP32 Jacobi: Gram-block cooperative form from this many vectors on (0 = off)
     double jacobi32_tol = 1e-6;  // FP32 Jacobi: rotate while a pair's cosine exceeds this
     int mixed_svd64 = 0;         // 3xTF32 form with the FP64 SVD and split (contractions alone in reduced precision)
+    int f64_fill = 1;            // FP64 GEMM: 32 x 32 tiles and split K when 64 x 64 tiles leave SMs idle
     int tc_presplit = 1;         // matvec: L, R split once per update; x and the mix output split by their producers
     int lz_fused = 1;            // Lanczos: one cooperative launch per step for the orthogonalisation
     int cjac32 = 1;              // FP32 Jacobi: one-cluster kernel (cjacobi.cu) from cjac_min_r vectors on
@@ -275,6 +277,12 @@ bool tune_lookup_gjac(const dmrg_ctx *ctx, int r, int l, int *nv, int *groups);
 dmrg_status gemm_f64(cudaStream_t st, int M, int N, int K, double alpha, const double *A, long long sAm,
                      long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
                      double beta, double *C, long long sCm, long long sCn, long long sCb, int batch);
+
+// Same contract, with the grid sized to the GPU (32 x 32 tiles, split K)
+// when 64 x 64 tiles would leave SMs idle; scratch from the context.
+dmrg_status gemm_f64x(dmrg_ctx *ctx, int M, int N, int K, double alpha, const double *A, long long sAm,
+                      long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
+                      double beta, double *C, long long sCm, long long sCn, long long sCb, int batch);
 
 // Same contract with FP32 arithmetic (small products of the mixed form).
 dmrg_status gemm_f32c(cudaStream_t st, int M, int N, int K, double alpha, const double *A, long long sAm,

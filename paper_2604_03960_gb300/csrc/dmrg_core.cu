@@ -724,6 +724,11 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         ctx->jacobi32_tol = value;
         return DMRG_OK;
     }
+    if (!std::strcmp(name, "f64_fill")) {
+        if (!(value == 0.0 || value == 1.0)) return DMRG_EINVAL;
+        ctx->f64_fill = (int)value;
+        return DMRG_OK;
+    }
     if (!std::strcmp(name, "tc_presplit")) {
         if (!(value == 0.0 || value == 1.0)) return DMRG_EINVAL;
         ctx->tc_presplit = (int)value;
@@ -824,6 +829,7 @@ void dmrg_destroy(dmrg_ctx *ctx)
     ctx->work2.release();
     ctx->work3.release();
     ctx->tcbuf.release();
+    ctx->f64buf.release();
     ctx->work4.release();
     if (ctx->pinned_desc) cudaFreeHost(ctx->pinned_desc);
     if (ctx->d_status) cudaFree(ctx->d_status);
@@ -981,9 +987,9 @@ static dmrg_status bond_step_b(dmrg_state *st, double *flops, int *k_out, double
         const int len = dir == 0 ? m : n;
         double *Q = st->X, *T = st->Y, *E = st->Vt;
         DMRG_TRY(gather_unit_vectors(ctx, P.X32, P.nrm, P.perm, &st->d_res->k, kk, len, Q));
-        DMRG_TRY(gemm_f64(ctx->stream, kk, kk, len, 1.0, Q, len, 1, 0, Q, 1, len, 0, 0.0, E, kk, 1, 0, 1));
+        DMRG_TRY(gemm_f64x(ctx, kk, kk, len, 1.0, Q, len, 1, 0, Q, 1, len, 0, 0.0, E, kk, 1, 0, 1));
         DMRG_CUDA(cudaMemcpyAsync(T, Q, sizeof(double) * (size_t)kk * len, cudaMemcpyDeviceToDevice, ctx->stream));
-        DMRG_TRY(gemm_f64(ctx->stream, kk, len, kk, -0.5, E, kk, 1, 0, Q, len, 1, 0, 1.5, T, len, 1, 0, 1));
+        DMRG_TRY(gemm_f64x(ctx, kk, len, kk, -0.5, E, kk, 1, 0, Q, len, 1, 0, 1.5, T, len, 1, 0, 1));
         if (dir == 0) {
             // A_k = T^T (m x kk): k_transpose_rect(in = T (kk x m), out = A_k (m x kk))
             k_transpose_rect<<<dim3((m + 31) / 32, (kk + 31) / 32), dim3(32, 8), 0, ctx->stream>>>(T, st->A[k], kk, m); DMRG_COUNT_LAUNCH();

@@ -9,13 +9,15 @@
 // operand stride is unit.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace dmrg {
 
 std::atomic<long long> g_launch_count{0};
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4, NT = 256;
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
 // T = double: the FP64 path; T = float: FP32 arithmetic on FP64 operands for
 // the small products of the mixed form.  In the FP32 case each BK-long
@@ -31,17 +33,25 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
     lo += err;
 }
 
-template <typename T>
+// Tile BT x BT (64 or 32), 16 x 16 threads with TT = BT / 16 outputs a side.
+// Split K: blockIdx.z = batch index * nsl + slice; a slice takes K range
+// [slice * kps, min(K, (slice + 1) * kps)) and, when P is set, writes its
+// partial sums to P[slice][b][m][n] for k_gemm_reduce (slices added in order).
+template <typename T, int BT = 64>
 __global__ void __launch_bounds__(NT) k_gemm_t(int M, int N, int K, double alpha, const double *__restrict__ A,
                                                long long sAm, long long sAk, long long sAb,
                                                const double *__restrict__ B, long long sBk, long long sBn,
                                                long long sBb, double beta, double *__restrict__ C, long long sCm,
-                                               long long sCn, long long sCb)
+                                               long long sCn, long long sCb, int nsl = 1, int kps = 0,
+                                               double *__restrict__ P = nullptr)
 {
+    constexpr int BM = BT, BN = BT, TM = BT / 16, TN = BT / 16;
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN + 1];
-    const int bz = blockIdx.z;
+    const int bz = blockIdx.z / nsl, sl = blockIdx.z % nsl;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kb = nsl > 1 ? sl * kps : 0;
+    const int ke = nsl > 1 ? min(K, kb + kps) : K;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     A += (long long)bz * sAb;
     B += (long long)bz * sBb;
@@ -61,14 +71,14 @@ __global__ void __launch_bounds__(NT) k_gemm_t(int M, int N, int K, double alpha
     }
     const bool a_kfast = (sAk == 1);
     const bool b_nfast = (sBn == 1);
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int k0 = kb; k0 < ke; k0 += BK) {
 #pragma unroll
         for (int it = 0; it < (BM * BK) / NT; ++it) {
             int idx = tid + it * NT;
             int mm, kk;
             if (a_kfast) { mm = idx / BK; kk = idx % BK; } else { kk = idx / BM; mm = idx % BM; }
             int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < M && gk < K) ? (T)A[(long long)gm * sAm + (long long)gk * sAk] : (T)0;
+            As[kk][mm] = (gm < M && gk < ke) ? (T)A[(long long)gm * sAm + (long long)gk * sAk] : (T)0;
         }
 #pragma unroll
         for (int it = 0; it < (BN * BK) / NT; ++it) {
@@ -76,7 +86,7 @@ __global__ void __launch_bounds__(NT) k_gemm_t(int M, int N, int K, double alpha
             int nn, kk;
             if (b_nfast) { kk = idx / BN; nn = idx % BN; } else { nn = idx / BK; kk = idx % BK; }
             int gn = n0 + nn, gk = k0 + kk;
-            Bs[kk][nn] = (gn < N && gk < K) ? (T)B[(long long)gk * sBk + (long long)gn * sBn] : (T)0;
+            Bs[kk][nn] = (gn < N && gk < ke) ? (T)B[(long long)gk * sBk + (long long)gn * sBn] : (T)0;
         }
         __syncthreads();
 #pragma unroll
@@ -110,9 +120,13 @@ __global__ void __launch_bounds__(NT) k_gemm_t(int M, int N, int K, double alpha
         for (int j = 0; j < TN; ++j) {
             int gn = n0 + tx + 16 * j;
             if (gn >= N) continue;
-            double *c = C + (long long)gm * sCm + (long long)gn * sCn;
             const double sum = kComp ? (double)chi[kComp ? i : 0][kComp ? j : 0] + (double)clo[kComp ? i : 0][kComp ? j : 0]
                                      : (double)acc[i][j];
+            if (P) {
+                P[(((long long)sl * (gridDim.z / nsl) + bz) * M + gm) * (long long)N + gn] = sum;
+                continue;
+            }
+            double *c = C + (long long)gm * sCm + (long long)gn * sCn;
             double v = alpha * sum;
             if (beta != 0.0) v += beta * *c;
             *c = v;
@@ -120,7 +134,68 @@ __global__ void __launch_bounds__(NT) k_gemm_t(int M, int N, int K, double alpha
     }
 }
 
+// C[b][m][n] = alpha * sum_s P[s][b][m][n] + beta * C[b][m][n], slices in order
+__global__ void k_gemm_reduce(const double *__restrict__ P, int nsl, int batch, int M, int N, double alpha,
+                              double beta, double *__restrict__ C, long long sCm, long long sCn, long long sCb)
+{
+    const long long per = (long long)M * N, total = per * batch;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        double a = P[e];
+        for (int q = 1; q < nsl; ++q) a += P[q * total + e];
+        const long long b = e / per, mn = e % per;
+        const int m = (int)(mn / N), n = (int)(mn % N);
+        double *c = C + b * sCb + (long long)m * sCm + (long long)n * sCn;
+        double v = alpha * a;
+        if (beta != 0.0) v += beta * *c;
+        *c = v;
+    }
+}
+
 }  // namespace
+
+// FP64 GEMM sized to the GPU: the FP64 pipe gives each SM ~2 multiply-adds
+// a clock on this part, so a product that makes a handful of 64 x 64 tiles
+// runs at a few percent of the chip.  Such products take 32 x 32 tiles and,
+// if that is still under one CTA per SM, split K (>= 64 terms a slice) with
+// the slices added in order in FP64 (deterministic).
+dmrg_status gemm_f64x(dmrg_ctx *ctx, int M, int N, int K, double alpha, const double *A, long long sAm,
+                      long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
+                      double beta, double *C, long long sCm, long long sCn, long long sCb, int batch)
+{
+    if (M <= 0 || N <= 0 || batch <= 0) return DMRG_OK;
+    if (batch > 65535) return DMRG_EINVAL;
+    cudaStream_t st = ctx->stream;
+    const long long t64 = (long long)((N + 63) / 64) * ((M + 63) / 64) * batch;
+    if (!ctx->f64_fill || t64 >= ctx->num_sms || K < 64)
+        return gemm_f64(st, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb, batch);
+    dim3 grid((N + 31) / 32, (M + 31) / 32, batch);
+    if (grid.y > 65535) return DMRG_EINVAL;
+    const long long t32 = (long long)grid.x * grid.y * batch;
+    int nsl = (int)std::min<long long>((ctx->num_sms + t32 - 1) / t32, K / 64);
+    if (nsl < 1) nsl = 1;
+    if ((long long)batch * nsl > 65535) nsl = 1;
+    if (nsl == 1) {
+        k_gemm_t<double, 32><<<grid, NT, 0, st>>>(M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm,
+                                                   sCn, sCb); DMRG_COUNT_LAUNCH();
+        DMRG_CUDA(cudaGetLastError());
+        return DMRG_OK;
+    }
+    int kps = (K + nsl - 1) / nsl;
+    kps = (kps + BK - 1) / BK * BK;
+    nsl = (K + kps - 1) / kps;
+    const long long total = (long long)M * N * batch;
+    DMRG_TRY(ctx->f64buf.ensure(sizeof(double) * (size_t)total * nsl));
+    double *P = ctx->f64buf.as<double>();
+    grid.z = batch * nsl;
+    k_gemm_t<double, 32><<<grid, NT, 0, st>>>(M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn,
+                                               sCb, nsl, kps, P); DMRG_COUNT_LAUNCH();
+    long long blocks = (total + 255) / 256;
+    if (blocks > 4LL * ctx->num_sms) blocks = 4LL * ctx->num_sms;
+    k_gemm_reduce<<<(int)blocks, 256, 0, st>>>(P, nsl, batch, M, N, alpha, beta, C, sCm, sCn, sCb); DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
 
 dmrg_status gemm_f64(cudaStream_t st, int M, int N, int K, double alpha, const double *A, long long sAm,
                      long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
@@ -159,8 +234,8 @@ dmrg_status gemm(dmrg_ctx *ctx, int prec, int M, int N, int K, double alpha, con
 {
     if (prec == DMRG_PREC_FP64) {
         prof_mark(ctx, PROF_F64_GEMM);
-        dmrg_status s = gemm_f64(ctx->stream, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn,
-                                 sCb, batch);
+        dmrg_status s = gemm_f64x(ctx, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb,
+                                  batch);
         prof_mark(ctx, PROF_F64_GEMM);
         prof_count(ctx, PROF_F64_GEMM, 2.0 * M * (double)N * K * batch,
                    8.0 * ((double)M * K + (double)K * N + (double)M * N) * batch);
