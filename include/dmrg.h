@@ -168,10 +168,17 @@ const char *dmrg_status_string(dmrg_status s);
  * (tensor-core GEMM: most 32-wide blocks of the 3 K split products one FP32
  * accumulator sums, 8; beyond, K is split and the slices added in FP64;
  * 0 = never split), "cjac32" (1, default: the FP32 Jacobi of the mixed form
- * runs on one 8-CTA thread-block cluster, vectors in blocks in the CTAs'
- * shared memory and moved between them through distributed shared memory,
- * for problems of at least "cjac_min_r" (32) vectors with at most 32 vectors
- * a block and length <= 512; 0: the kernels below), "gjac32" (grouped block
+ * runs on one thread-block cluster of 8 CTAs, or 16 where 8 CTAs' shared
+ * memory cannot hold the blocks, vectors in blocks in the CTAs' shared
+ * memory and moved between them through distributed shared memory, for
+ * problems of at least "cjac_min_r" (32) vectors with at most 32 vectors a
+ * block and length <= 512; 0: the kernels below), "tc_presplit" (1, default:
+ * the matvec's L and R are split into TF32 parts once per local update and
+ * the Lanczos vector and mix output by the kernels that make them; 0: every
+ * product splits its operands), "lz_fused" (1, default: one cooperative
+ * launch per Lanczos step for both Gram-Schmidt passes; 0: five launches),
+ * "f64_fill" (1, default: FP64 GEMMs that would leave SMs idle take 32 x 32
+ * tiles and split K), "gjac32" (grouped block
  * FP32 Jacobi: 0 never (default),
  * 1 for problems that fit one CTA's shared memory, 2 always), "gjac_nv" / "gjac_groups" (its vectors per block pair, 16 or
  * 32, and groups per CTA, 1-4; 0 = by size / autotuner), "jacobi64_gram"

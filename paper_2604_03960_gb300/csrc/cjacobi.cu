@@ -3,8 +3,9 @@
 // The mixed form's SVD of the two-site tensor orthogonalises r vectors (the
 // rows of X, length l) by plane rotations.  On one CTA every round of a sweep
 // moves all r x l values through one SM's shared-memory pipe; on a grid the
-// rounds pay a global barrier.  Here the work is spread over the C = 8 CTAs
-// of one cluster and only block moves cross SMs:
+// rounds pay a global barrier.  Here the work is spread over the C CTAs of
+// one cluster (8; 16, the opt-in size, when 8 CTAs' shared memory cannot
+// hold the blocks) and only block moves cross SMs:
 //   * the vectors form 2C blocks of b = ceil(r / 2C); CTA c holds two of them
 //     (its "top" and "bottom" block) in shared memory;
 //   * a sweep first rotates the pairs inside every block (circle method on
@@ -30,13 +31,13 @@
 
 #include <algorithm>
 #include <cooperative_groups.h>
+#include <unordered_map>
 
 namespace dmrg {
 namespace {
 
 namespace cg = cooperative_groups;
 
-constexpr int kCjC = 8;             // CTAs per cluster (portable size)
 constexpr int kCjMaxB = 32;         // vectors per block: one warp per pair, <= 1024 threads
 
 __device__ __forceinline__ void cj_circle(int np, int t, int p, int &i, int &j)
@@ -112,14 +113,13 @@ __device__ __forceinline__ bool cj_pair(float *__restrict__ xi, float *__restric
 //   ids     [2][2][b] ints
 //   counts  [3] unsigned: [0], [1] the cluster's rotations of even / odd
 //           sweeps (used on rank 0), [2] this CTA's rotations of the sweep
-template <int TM>
-__global__ void __cluster_dims__(kCjC, 1, 1) __launch_bounds__(1024)
+template <int TM, int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(1024)
     k_cjac32(float *__restrict__ X, int r_all, int l, int ldl, int b, int max_sweeps, float tol,
              const double *__restrict__ F2, double small, const int *__restrict__ r_eff_p, int *status, int *info)
 {
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) float cj_sm[];
-    const int C = kCjC;
     const int crank = (int)cluster.block_rank();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const long long blk = (long long)b * ldl;
@@ -256,35 +256,121 @@ __global__ void __cluster_dims__(kCjC, 1, 1) __launch_bounds__(1024)
     cluster.sync();
 }
 
-template <int TM>
+template <int TM, int C>
 dmrg_status launch_cjac32(dmrg_ctx *ctx, float *X, int r, int l, int ldl, int b, int threads, size_t smem,
                           int max_sweeps, float tol, const double *F2, double small, int *d_info, const int *r_eff)
 {
     static bool attr = false;
     if (!attr) {
-        DMRG_CUDA(cudaFuncSetAttribute(k_cjac32<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        DMRG_CUDA(cudaFuncSetAttribute(k_cjac32<TM, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        if (C > 8) DMRG_CUDA(cudaFuncSetAttribute(k_cjac32<TM, C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         attr = true;
     }
-    k_cjac32<TM><<<kCjC, threads, smem, ctx->stream>>>(X, r, l, ldl, b, max_sweeps, tol, F2, small, r_eff,
+    k_cjac32<TM, C><<<C, threads, smem, ctx->stream>>>(X, r, l, ldl, b, max_sweeps, tol, F2, small, r_eff,
                                                        ctx->d_status, d_info);
     DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }
 
+// Whether a cluster of C CTAs of `threads` threads and `smem` bytes can be
+// resident (occupancy query, cached per size class); a launch that cannot is
+// not attempted.
+template <int TM, int C>
+bool cjac_cluster_fits(int threads, size_t smem)
+{
+    static std::unordered_map<unsigned long long, bool> seen;
+    const unsigned long long key = ((unsigned long long)threads << 32) | (unsigned long long)smem;
+    auto it = seen.find(key);
+    if (it != seen.end()) return it->second;
+    if (cudaFuncSetAttribute(k_cjac32<TM, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
+        return false;
+    if (C > 8 && cudaFuncSetAttribute(k_cjac32<TM, C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = C;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const bool ok = cudaOccupancyMaxActiveClusters(&n, (const void *)k_cjac32<TM, C>, &cfg) == cudaSuccess && n >= 1;
+    cudaGetLastError();
+    seen[key] = ok;
+    return ok;
+}
+
+struct CjPlan {
+    int C = 0, b = 0, ldl = 0, threads = 0, tm = 0;
+    size_t smem = 0;
+};
+
+CjPlan cj_plan(int r, int l, int C)
+{
+    CjPlan p;
+    p.C = C;
+    p.b = (r + 2 * C - 1) / (2 * C);
+    p.ldl = (l + 3) & ~3;
+    const int rp = p.b + (p.b & 1);
+    p.threads = 32 * std::max(4, std::max(rp, p.b));
+    p.smem = sizeof(float) * (4ull * p.b * p.ldl + 4ull * p.b) + sizeof(int) * 4ull * p.b + 4 * sizeof(unsigned);
+    const int tm = (l + 31) / 32;
+    p.tm = tm <= 4 ? 4 : tm <= 8 ? 8 : tm <= 12 ? 12 : 16;
+    return p;
+}
+
+bool cj_plan_ok(const CjPlan &p, int r, int l)
+{
+    return r >= 1 && l >= 1 && l <= 512 && p.b <= kCjMaxB && p.smem <= 227 * 1024;
+}
+
+template <int C>
+bool cj_fits_dispatch(const CjPlan &p)
+{
+    switch (p.tm) {
+    case 4: return cjac_cluster_fits<4, C>(p.threads, p.smem);
+    case 8: return cjac_cluster_fits<8, C>(p.threads, p.smem);
+    case 12: return cjac_cluster_fits<12, C>(p.threads, p.smem);
+    default: return cjac_cluster_fits<16, C>(p.threads, p.smem);
+    }
+}
+
+// 8 CTAs where the blocks fit them, else 16 (opt-in cluster size) if the GPU
+// can hold such a cluster; 0 if neither.
+int cj_choose(int r, int l, CjPlan *out)
+{
+    CjPlan p8 = cj_plan(r, l, 8);
+    if (cj_plan_ok(p8, r, l)) {
+        *out = p8;
+        return 8;
+    }
+    CjPlan p16 = cj_plan(r, l, 16);
+    if (cj_plan_ok(p16, r, l) && cj_fits_dispatch<16>(p16)) {
+        *out = p16;
+        return 16;
+    }
+    return 0;
+}
+
 }  // namespace
 
 size_t cjac32_smem_bytes(int r, int l)
 {
-    const int b = (r + 2 * kCjC - 1) / (2 * kCjC);
-    const int ldl = (l + 3) & ~3;
-    return sizeof(float) * (4ull * b * ldl + 4ull * b) + sizeof(int) * 4ull * b + 4 * sizeof(unsigned);
+    CjPlan p;
+    return cj_choose(r, l, &p) ? p.smem : 0;
 }
 
 bool cjac32_fits(int r, int l)
 {
-    const int b = (r + 2 * kCjC - 1) / (2 * kCjC);
-    return r >= 1 && l >= 1 && b <= kCjMaxB && l <= 512 && cjac32_smem_bytes(r, l) <= 227 * 1024;
+    CjPlan p;
+    return cj_choose(r, l, &p) != 0;
 }
 
 // X: r x l row-major FP32 (device), rotated in place; r_eff (device, may be
@@ -292,19 +378,27 @@ bool cjac32_fits(int r, int l)
 dmrg_status cjac32_run(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps, double tol, double small,
                        const double *F2, int *d_info, const int *r_eff)
 {
-    if (!cjac32_fits(r, l)) return DMRG_EUNSUPPORTED;
-    const int b = (r + 2 * kCjC - 1) / (2 * kCjC);
-    const int ldl = (l + 3) & ~3;
-    const int rp = b + (b & 1);
-    const int threads = 32 * std::max(4, std::max(rp, b));
-    const size_t smem = cjac32_smem_bytes(r, l);
-    const int tm = (l + 31) / 32;
+    CjPlan p;
+    const int C = cj_choose(r, l, &p);
+    if (!C) return DMRG_EUNSUPPORTED;
     const float tf = (float)tol;
-    if (tm <= 4) return launch_cjac32<4>(ctx, X, r, l, ldl, b, threads, smem, max_sweeps, tf, F2, small, d_info, r_eff);
-    if (tm <= 8) return launch_cjac32<8>(ctx, X, r, l, ldl, b, threads, smem, max_sweeps, tf, F2, small, d_info, r_eff);
-    if (tm <= 12)
-        return launch_cjac32<12>(ctx, X, r, l, ldl, b, threads, smem, max_sweeps, tf, F2, small, d_info, r_eff);
-    return launch_cjac32<16>(ctx, X, r, l, ldl, b, threads, smem, max_sweeps, tf, F2, small, d_info, r_eff);
+#define CJ_LAUNCH(TMV, CV)                                                                                           \
+    return launch_cjac32<TMV, CV>(ctx, X, r, l, p.ldl, p.b, p.threads, p.smem, max_sweeps, tf, F2, small, d_info, r_eff)
+    if (C == 8) {
+        switch (p.tm) {
+        case 4: CJ_LAUNCH(4, 8);
+        case 8: CJ_LAUNCH(8, 8);
+        case 12: CJ_LAUNCH(12, 8);
+        default: CJ_LAUNCH(16, 8);
+        }
+    }
+    switch (p.tm) {
+    case 4: CJ_LAUNCH(4, 16);
+    case 8: CJ_LAUNCH(8, 16);
+    case 12: CJ_LAUNCH(12, 16);
+    default: CJ_LAUNCH(16, 16);
+    }
+#undef CJ_LAUNCH
 }
 
 }  // namespace dmrg

@@ -108,113 +108,64 @@ struct MixDesc {
 };
 
 // out[channel o][a][b] = sum_i C[o][i] in[channel i][a][b]; b is unit stride.
-// The coefficient table (an MPO product, mostly zeros) is compressed by rows
-// into shared memory and the inputs of each element are staged there too, so
-// each element costs one multiply-add per nonzero coefficient.
-constexpr int kMixThreads = 128;
+// A block takes 32 consecutive elements (one per lane) and stages their
+// inputs in shared memory; warp w then forms the output channels w, w + 8,
+// ...  The coefficient table (an MPO product, mostly zeros) is the same for
+// every lane, so a zero coefficient is skipped by a warp-uniform branch and
+// each output costs one multiply-add per nonzero coefficient, in channel
+// order.  The mixed form (f32) mixes in FP32, with its inputs narrowed and
+// its outputs widened by integer operations (bit-identical to the
+// converting instructions, which would use the narrow FP64 pipe).
+constexpr int kMixThreads = 256;
+constexpr int kMixW = kMixThreads / 32;
+template <typename T>
 __global__ void __launch_bounds__(kMixThreads) k_mix(const double *__restrict__ in, double *__restrict__ out,
                                                      const double *__restrict__ C, MixDesc d)
 {
-    __shared__ double val[kMaxCh * kMaxCh];
-    __shared__ float valf[kMaxCh * kMaxCh];        // the same, rounded once (FP32 mixing)
-    __shared__ unsigned char col[kMaxCh * kMaxCh];
-    __shared__ int rowptr[kMaxCh + 1];
-    __shared__ int rowcnt[kMaxCh];
-    __shared__ double xs[kMaxCh][kMixThreads];
-    // compress the coefficient rows in parallel: warp w takes rows w, w + 4,
-    // ...; each lane tests one column (nin <= 32) and the ballot gives every
-    // nonzero its slot; the row counts become offsets by a scan in one warp
+    __shared__ T cs[kMaxCh * kMaxCh];
+    __shared__ T xs[kMaxCh][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int kWarps = kMixThreads / 32;
-    constexpr int kRowsPerWarp = (kMaxCh + kWarps - 1) / kWarps;
-    // all loads of the table at once (one memory latency, not one per row)
-    double cv[kRowsPerWarp];
-#pragma unroll
-    for (int t = 0; t < kRowsPerWarp; ++t) {
-        const int o = warp + t * kWarps;
-        cv[t] = (o < d.nout && lane < d.nin) ? C[o * d.nin + lane] : 0.0;
-    }
-#pragma unroll
-    for (int t = 0; t < kRowsPerWarp; ++t) {
-        const int o = warp + t * kWarps;
-        if (o >= d.nout) break;
-        const unsigned nzm = __ballot_sync(0xffffffffu, cv[t] != 0.0);
-        if (lane == 0) rowcnt[o] = __popc(nzm);
-    }
-    __syncthreads();
-    if (warp == 0) {
-        int c = lane < d.nout ? rowcnt[lane] : 0;
-        int incl = c;
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += y;
-        }
-        if (lane < d.nout) rowptr[lane] = incl - c;
-        if (lane == d.nout - 1) rowptr[d.nout] = incl;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < kRowsPerWarp; ++t) {
-        const int o = warp + t * kWarps;
-        if (o >= d.nout) break;
-        const double v = cv[t];
-        const unsigned nzm = __ballot_sync(0xffffffffu, v != 0.0);
-        if (v != 0.0) {
-            const int slot = rowptr[o] + __popc(nzm & ((1u << lane) - 1u));
-            val[slot] = v;
-            valf[slot] = (float)v;
-            col[slot] = (unsigned char)lane;
-        }
-    }
-    __syncthreads();
     const long long total = (long long)d.An * d.Bn;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long e0 = (long long)blockIdx.x * blockDim.x; e0 < total; e0 += stride) {
-        const long long e = e0 + threadIdx.x;
-        const bool ok = e < total;
-        const int a = ok ? (int)(e / d.Bn) : 0, b = ok ? (int)(e % d.Bn) : 0;
-        if (d.f32) {
-            // FP64 lanes are scarce on this part: the mixed form mixes in FP32,
-            // with the inputs narrowed and the outputs widened by integer
-            // operations (bit-identical to the converting instructions)
-            float *xf = reinterpret_cast<float *>(&xs[0][0]);     // [kMaxCh][kMixThreads]
-            for (int c = 0; c < d.nin; ++c) {
-                const int x = c / d.in_ny, y = c % d.in_ny;
-                xf[c * kMixThreads + threadIdx.x] = ok ? f64_narrow(in[x * d.in_sx + y * d.in_sy + a * d.in_sa + b]) : 0.f;
-            }
-            if (!ok) continue;
-            for (int o = 0; o < d.nout; ++o) {
-                float acc = 0.f;
-                for (int q = rowptr[o]; q < rowptr[o + 1]; ++q)
-                    acc = fmaf(valf[q], xf[col[q] * kMixThreads + threadIdx.x], acc);
-                const int x = o / d.out_ny, y = o % d.out_ny;
-                const long long f = x * d.out_sx + y * d.out_sy + a * d.out_sa + b;
-                if (d.yh) {
-                    // only the next GEMM's left-operand parts (hi, hi, lo), the
-                    // bits its split of (double)acc would give: acc - hi is exact in FP32
-                    const float hi = tf32_rna(acc), lo = tf32_rna(acc - hi);
-                    const long long mrow = f / d.y_rs, kk = f - mrow * d.y_rs;
-                    float *q = d.yh + mrow * 3LL * d.ykp + kk;
-                    q[0] = hi;
-                    q[d.ykp] = hi;
-                    q[2LL * d.ykp] = lo;
-                } else {
-                    out[f] = f32_widen(acc);
-                }
-            }
-            continue;
-        }
+    const long long e = (long long)blockIdx.x * 32 + lane;
+    const bool ok = e < total;
+    const int a = ok ? (int)(e / d.Bn) : 0, b = ok ? (int)(e % d.Bn) : 0;
+    for (int q = threadIdx.x; q < d.nout * d.nin; q += kMixThreads) {
+        const double v = C[q];
+        if constexpr (sizeof(T) == 4) cs[q] = f64_narrow(v); else cs[q] = v;
+    }
+    for (int c = warp; c < d.nin; c += kMixW) {
+        const int x = c / d.in_ny, y = c % d.in_ny;
+        const double v = ok ? in[x * d.in_sx + y * d.in_sy + a * d.in_sa + b] : 0.0;
+        if constexpr (sizeof(T) == 4) xs[c][lane] = f64_narrow(v); else xs[c][lane] = v;
+    }
+    __syncthreads();
+    if (!ok) return;
+    for (int o = warp; o < d.nout; o += kMixW) {
+        T acc = (T)0;
+        const T *crow = cs + o * d.nin;
         for (int c = 0; c < d.nin; ++c) {
-            const int x = c / d.in_ny, y = c % d.in_ny;
-            xs[c][threadIdx.x] = ok ? in[x * d.in_sx + y * d.in_sy + a * d.in_sa + b] : 0.0;
-        }
-        if (ok) {
-            for (int o = 0; o < d.nout; ++o) {
-                double acc = 0.0;
-                for (int q = rowptr[o]; q < rowptr[o + 1]; ++q) acc = fma(val[q], xs[col[q]][threadIdx.x], acc);
-                const int x = o / d.out_ny, y = o % d.out_ny;
-                out[x * d.out_sx + y * d.out_sy + a * d.out_sa + b] = acc;
+            const T cv = crow[c];
+            if (cv != (T)0) {
+                if constexpr (sizeof(T) == 4) acc = fmaf(cv, xs[c][lane], acc); else acc = fma(cv, xs[c][lane], acc);
             }
+        }
+        const int x = o / d.out_ny, y = o % d.out_ny;
+        const long long f = x * d.out_sx + y * d.out_sy + a * d.out_sa + b;
+        if constexpr (sizeof(T) == 4) {
+            if (d.yh) {
+                // only the next GEMM's left-operand parts (hi, hi, lo), the
+                // bits its split of (double)acc would give: acc - hi is exact in FP32
+                const float hi = tf32_rna(acc), lo = tf32_rna(acc - hi);
+                const long long mrow = f / d.y_rs, kk = f - mrow * d.y_rs;
+                float *q = d.yh + mrow * 3LL * d.ykp + kk;
+                q[0] = hi;
+                q[d.ykp] = hi;
+                q[2LL * d.ykp] = lo;
+            } else {
+                out[f] = f32_widen(acc);
+            }
+        } else {
+            out[f] = acc;
         }
     }
 }
@@ -469,7 +420,14 @@ static dmrg_status mix(dmrg_ctx *ctx, const double *in, double *out, const doubl
 {
     long long total = (long long)d.An * d.Bn;
     prof_mark(ctx, PROF_MIX);
-    k_mix<<<grid1d(total, kMixThreads, ctx->num_sms), kMixThreads, 0, ctx->stream>>>(in, out, C, d); DMRG_COUNT_LAUNCH();
+    if (total <= 0) return DMRG_OK;
+    const long long blocks = (total + 31) / 32;
+    if (blocks > 0x7fffffffLL) return DMRG_EINVAL;
+    if (d.f32)
+        k_mix<float><<<(unsigned)blocks, kMixThreads, 0, ctx->stream>>>(in, out, C, d);
+    else
+        k_mix<double><<<(unsigned)blocks, kMixThreads, 0, ctx->stream>>>(in, out, C, d);
+    DMRG_COUNT_LAUNCH();
     prof_mark(ctx, PROF_MIX);
     prof_count(ctx, PROF_MIX, 0.0, 8.0 * (double)total * (d.nin + d.nout));   // each input and output channel once
     DMRG_CUDA(cudaGetLastError());

@@ -111,20 +111,24 @@ __global__ void __launch_bounds__(kQrPanelThreads) k_qr_panel(float *__restrict_
         if (lane == 0) G[p][q] = s;
     }
     __syncthreads();
-    if (tid == 0) {
-        float Tl[kQrB][kQrB];
-        for (int p = 0; p < kQrB; ++p)
-            for (int q = 0; q < kQrB; ++q) Tl[p][q] = 0.f;
+    if (warp == 0) {
+        // column j of T from columns < j: lane p < j forms row p (the
+        // columns are sequential, the rows of one column are not)
+        __shared__ float Ts[kQrB][kQrB + 1];
+        for (int q = 0; q < kQrB; ++q)
+            if (lane < kQrB) Ts[lane][q] = 0.f;
+        __syncwarp();
         for (int j = 0; j < bw; ++j) {
-            Tl[j][j] = sbeta[j];
-            for (int p = 0; p < j; ++p) {
+            if (lane < j) {
                 float s = 0.f;
-                for (int q = p; q < j; ++q) s = fmaf(Tl[p][q], G[q][j], s);
-                Tl[p][j] = -sbeta[j] * s;
+                for (int q = lane; q < j; ++q) s = fmaf(Ts[lane][q], G[q][j], s);
+                Ts[lane][j] = -sbeta[j] * s;
+            } else if (lane == j) {
+                Ts[j][j] = sbeta[j];
             }
+            __syncwarp();
         }
-        for (int p = 0; p < kQrB; ++p)
-            for (int q = 0; q < kQrB; ++q) T[p * kQrB + q] = Tl[p][q];
+        for (int e = lane; e < kQrB * kQrB; e += 32) T[e] = Ts[e / kQrB][e % kQrB];
     }
     for (int i = tid; i < rows; i += kQrPanelThreads)
         for (int j = 0; j < bw; ++j) X[(long long)(k + i) * l + k + j] = P[i * kPS + j];

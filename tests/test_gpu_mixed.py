@@ -133,15 +133,16 @@ def test_mixed_svd_exact_spectrum(G, chi, opt):
 
 
 @pytest.mark.parametrize("m,n", [(64, 64), (66, 70), (94, 130), (130, 94), (201, 199), (256, 256), (300, 300),
-                                 (40, 500), (450, 450)])
+                                 (40, 500), (450, 450), (500, 500), (512, 512)])
 @pytest.mark.parametrize("cj", [1, 0])
 def test_mixed_svd_cluster_kernel(G, m, n, cj):
     """The FP32 Jacobi on one thread-block cluster (option cjac32 = 1: blocks
-    of vectors in eight CTAs' shared memory, moved through distributed shared
-    memory) and the single-CTA / grid kernels it replaces (cjac32 = 0) on
-    ragged and rectangular shapes (blocks of 2..29 vectors, padded blocks,
-    lengths not a multiple of 32): both meet the exact-spectrum bar of the
-    mixed SVD, and both converge (status word clean)."""
+    of vectors in the shared memory of 8 CTAs, or 16 for 500 and 512 vectors,
+    moved through distributed shared memory) and the single-CTA / grid
+    kernels it replaces (cjac32 = 0) on ragged and rectangular shapes (blocks
+    of 2..32 vectors, padded blocks, lengths not a multiple of 32): both meet
+    the exact-spectrum bar of the mixed SVD, and both converge (status word
+    clean)."""
     c = G.Context(0)
     c.set_option("svd_prec", 1)
     c.set_option("cjac32", cj)
