@@ -429,6 +429,7 @@ int tc_pick_bn(dmrg_ctx *ctx, int M, int N, int K, int batch)
     }
     long long t256 = (long long)((N + 255) / 256) * ((M + TBM - 1) / TBM) * batch;
     long long t128 = (long long)((N + 127) / 128) * ((M + TBM - 1) / TBM) * batch;
+    if (N <= 64) return 64;      // half the accumulator columns and epilogue of a 128 tile
     if (N <= 128) return 128;
     // compare wave-quantised work: tiles rounded up to whole waves, weighted by tile width
     long long w256 = ((t256 + ctx->num_sms - 1) / ctx->num_sms) * 2;
@@ -512,6 +513,7 @@ dmrg_status gemm_3xtf32_pre(dmrg_ctx *ctx, int M, int N, int K, double alpha, co
     }
     DMRG_CUDA(cudaGetLastError());
     const int bn = tc_pick_bn(ctx, M, N, K, batch);
+    if (bn == 64) return launch_tc<64>(ctx, Ah, Bh, M, N, K3, batch, alpha, beta, C, sCm, sCn, sCb, nsl, P);
     if (bn == 128) return launch_tc<128>(ctx, Ah, Bh, M, N, K3, batch, alpha, beta, C, sCm, sCn, sCb, nsl, P);
     return launch_tc<256>(ctx, Ah, Bh, M, N, K3, batch, alpha, beta, C, sCm, sCn, sCb, nsl, P);
 }

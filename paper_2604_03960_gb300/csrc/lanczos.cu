@@ -190,18 +190,19 @@ __global__ void __launch_bounds__(RB) k_multiaxpy_norm(double *__restrict__ w, c
 }
 
 // Column sums of acc[0..nq) over the block (FP64, fixed order), written to
-// part[q]; red: (MAXQ + 1) x RB doubles of shared memory.
+// part[q]; red: (MAXQ + 1) x OB doubles of shared memory (OB: block size).
+template <int OB>
 __device__ __forceinline__ void block_cols_to(const double *acc, int nq, double *red, double *part)
 {
 #pragma unroll
     for (int q = 0; q < MAXQ; ++q)
-        if (q < nq) red[q * RB + threadIdx.x] = acc[q];
+        if (q < nq) red[q * OB + threadIdx.x] = acc[q];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = warp; q < nq; q += RB / 32) {
+    for (int q = warp; q < nq; q += OB / 32) {
         double s = 0.0;
 #pragma unroll
-        for (int k = 0; k < RB / 32; ++k) s += red[q * RB + lane + 32 * k];
+        for (int k = 0; k < OB / 32; ++k) s += red[q * OB + lane + 32 * k];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) part[q] = s;
     }
@@ -209,10 +210,11 @@ __device__ __forceinline__ void block_cols_to(const double *acc, int nq, double 
 
 // Sum of the blocks' partials part[b * stride + q] for q < nq, b < G, in
 // block order (every CTA gets the same bits); result to cs[q].
+template <int OB>
 __device__ __forceinline__ void sum_parts(const double *part, int stride, int nq, double *cs)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = warp; q < nq; q += RB / 32) {
+    for (int q = warp; q < nq; q += OB / 32) {
         double s = 0.0;
         for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(&part[(long long)b * stride + q]);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -229,20 +231,21 @@ __device__ __forceinline__ void sum_parts(const double *part, int stride, int nq
 // Each thread keeps its elements' v_q in registers between the update and
 // the next dot product, so V is read three times instead of four.
 // part: 3 x gridDim.x x (MAXQ + 1) doubles; bar: two zeroed words.
-__global__ void __launch_bounds__(RB) k_lz_orth(double *__restrict__ V, double *__restrict__ w, long long n, int j,
+template <int OB>
+__global__ void __launch_bounds__(OB) k_lz_orth(double *__restrict__ V, double *__restrict__ w, long long n, int j,
                                                 LzState *lz, double *__restrict__ part, unsigned *bar, int *status,
                                                 SplitSink sink)
 {
     if (!lz->active) return;                 // written by an earlier launch: the same in every CTA
-    extern __shared__ double red[];          // (MAXQ + 1) x RB
+    extern __shared__ double red[];          // (MAXQ + 1) x OB
     __shared__ double cs[MAXQ + 1];
     const int nq = j + 1;
     const int K = lz->K;
     const double amax0 = lz->amax;
     const int S = MAXQ + 1;
     double *p0 = part, *p1 = part + (long long)gridDim.x * S, *p2 = part + 2LL * gridDim.x * S;
-    const long long stride = (long long)gridDim.x * RB;
-    const long long i0 = (long long)blockIdx.x * RB + threadIdx.x;
+    const long long stride = (long long)gridDim.x * OB;
+    const long long i0 = (long long)blockIdx.x * OB + threadIdx.x;
     double acc[MAXQ];
     // phase A: c = V^T w
 #pragma unroll
@@ -253,9 +256,9 @@ __global__ void __launch_bounds__(RB) k_lz_orth(double *__restrict__ V, double *
         for (int q = 0; q < MAXQ; ++q)
             if (q < nq) acc[q] = fma(V[(long long)q * n + i], wi, acc[q]);
     }
-    block_cols_to(acc, nq, red, p0 + (long long)blockIdx.x * S);
+    block_cols_to<OB>(acc, nq, red, p0 + (long long)blockIdx.x * S);
     if (!grid_barrier(bar, status)) return;
-    sum_parts(p0, S, nq, cs);
+    sum_parts<OB>(p0, S, nq, cs);
     const double alpha = cs[j];
     const double amax = fmax(amax0, fabs(alpha));
     // phase B: w -= V c, c' = V^T w
@@ -277,9 +280,9 @@ __global__ void __launch_bounds__(RB) k_lz_orth(double *__restrict__ V, double *
             if (q < nq) acc[q] = fma(v[q], wi, acc[q]);
     }
     __syncthreads();                         // cs is rewritten below
-    block_cols_to(acc, nq, red, p1 + (long long)blockIdx.x * S);
+    block_cols_to<OB>(acc, nq, red, p1 + (long long)blockIdx.x * S);
     if (!grid_barrier(bar, status)) return;
-    sum_parts(p1, S, nq, cs);
+    sum_parts<OB>(p1, S, nq, cs);
     // phase C: w -= V c', |w|^2
     double ss = 0.0;
     for (long long i = i0; i < n; i += stride) {
@@ -293,9 +296,9 @@ __global__ void __launch_bounds__(RB) k_lz_orth(double *__restrict__ V, double *
     }
     __syncthreads();
     acc[0] = ss;
-    block_cols_to(acc, 1, red, p2 + (long long)blockIdx.x * S);
+    block_cols_to<OB>(acc, 1, red, p2 + (long long)blockIdx.x * S);
     if (!grid_barrier(bar, status)) return;
-    sum_parts(p2, S, 1, cs);
+    sum_parts<OB>(p2, S, 1, cs);
     // phase D: beta_{j+1}, continuation, next vector
     const double bta = sqrt(cs[0]);
     const bool go = (j + 1 < K) && (bta > 1e-14 * amax) && isfinite(bta);
@@ -531,12 +534,14 @@ int grid_dot(long long n, int num_sms)
     return (int)b;
 }
 
-// fused orthogonalisation grid: one element a thread up to one block per SM
-// (all co-resident: the launch is cooperative); the FP64 multiply-adds of
-// the passes, 2 per clock per SM on this part, want every SM at large n
+// fused orthogonalisation: 128-thread blocks, one element a thread up to one
+// block per SM (all co-resident: the launch is cooperative).  The FP64
+// multiply-adds of the passes and of the block sums (2 a clock per SM on
+// this part) grow with elements + threads per SM, so small blocks on every SM.
+constexpr int kOB = 128;
 int grid_orth(long long n, int num_sms)
 {
-    long long b = (n + RB - 1) / RB;
+    long long b = (n + kOB - 1) / kOB;
     if (b > num_sms) b = num_sms;
     if (b < 1) b = 1;
     return (int)b;
@@ -604,7 +609,8 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
     const int gc = grid_orth(n, ctx->num_sms);
     static bool orth_attr = false;
     if (!orth_attr) {
-        DMRG_CUDA(cudaFuncSetAttribute(k_lz_orth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+        DMRG_CUDA(cudaFuncSetAttribute(k_lz_orth<kOB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(double) * (MAXQ + 1) * kOB)));
         orth_attr = true;
     }
     for (int j = 0; j < K; ++j) {
@@ -620,7 +626,8 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
             unsigned *bar = w.counter + 4;
             int *stp = ctx->d_status;
             void *args[] = {&Vp, &wp, &nn, &jj, &lzp, &pp, &bar, &stp, &sink};
-            DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_lz_orth, dim3(gc), dim3(RB), args, dsm, st));
+            DMRG_CUDA(cudaLaunchCooperativeKernel((const void *)k_lz_orth<kOB>, dim3(gc), dim3(kOB), args,
+                                                  sizeof(double) * (MAXQ + 1) * kOB, st));
             DMRG_COUNT_LAUNCH();
             prof_mark(ctx, PROF_LZ_VEC);
             prof_count(ctx, PROF_LZ_VEC, 0.0, 8.0 * (double)n * (3.0 * (j + 1) + 7.0));

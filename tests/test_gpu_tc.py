@@ -38,7 +38,8 @@ def tol_for(K):
 
 
 @pytest.mark.parametrize("M,N,K", [(1, 1, 1), (5, 7, 3), (128, 256, 32), (129, 257, 33), (300, 100, 1000),
-                                   (640, 96, 77), (257, 513, 515), (1024, 1024, 1024), (70, 50, 2000)])
+                                   (640, 96, 77), (257, 513, 515), (1024, 1024, 1024), (70, 50, 2000),
+                                   (300, 64, 500), (129, 33, 257)])
 def test_tc_gemm_vs_fp64(G, ctx, M, N, K):
     rng = np.random.default_rng(M + 3 * N + 7 * K)
     A = rng.standard_normal((M, K))
