@@ -52,25 +52,34 @@ __device__ __forceinline__ void cj_circle(int np, int t, int p, int &i, int &j)
     }
 }
 
-// One pair on one warp.  xi, xj: the two vectors (length l, shared memory);
-// na, nb: their squared norms.  Returns true if a rotation was applied.
+// One pair on one warp.  xi, xj: the two vectors (shared memory, rows of
+// ldl floats, zero beyond l); na, nb: their squared norms.  Lane i holds the
+// float4 chunks i, i + 32, ... of each (one 512-byte span per load or store
+// instruction, no bank conflicts; 32 TM >= ldl).  Returns true if a
+// rotation was applied.
 template <int TM>
-__device__ __forceinline__ bool cj_pair(float *__restrict__ xi, float *__restrict__ xj, float *na, float *nb, int l,
+__device__ __forceinline__ bool cj_pair(float *__restrict__ xi, float *__restrict__ xj, float *na, float *nb, int ldl,
                                         float floor2, float tol, int lane)
 {
     const float a = *na, b = *nb;
     if (!(a > floor2 && b > floor2)) return false;
-    float u[TM], v[TM];
+    constexpr int V4 = TM / 4;
+    float4 u[V4], v[V4];
     float g0 = 0.f, g1 = 0.f;
 #pragma unroll
-    for (int q = 0; q < TM; ++q) {
-        const int k = lane + 32 * q;
-        u[q] = k < l ? xi[k] : 0.f;
-        v[q] = k < l ? xj[k] : 0.f;
-        if (q & 1)
-            g1 = fmaf(u[q], v[q], g1);
-        else
-            g0 = fmaf(u[q], v[q], g0);
+    for (int q = 0; q < V4; ++q) {
+        const int k = 4 * (lane + 32 * q);
+        if (k < ldl) {
+            u[q] = *reinterpret_cast<const float4 *>(xi + k);
+            v[q] = *reinterpret_cast<const float4 *>(xj + k);
+        } else {
+            u[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            v[q] = u[q];
+        }
+        g0 = fmaf(u[q].x, v[q].x, g0);
+        g1 = fmaf(u[q].y, v[q].y, g1);
+        g0 = fmaf(u[q].z, v[q].z, g0);
+        g1 = fmaf(u[q].w, v[q].w, g1);
     }
     float g = g0 + g1;
 #pragma unroll
@@ -92,14 +101,22 @@ __device__ __forceinline__ bool cj_pair(float *__restrict__ xi, float *__restric
     t = copysignf(t, zeta);
     const float c = rsqrtf(fmaf(t, t, 1.0f)), s = c * t;
 #pragma unroll
-    for (int q = 0; q < TM; ++q) {
-        const int k = lane + 32 * q;
-        if (k < l) {
-            xi[k] = fmaf(c, u[q], -s * v[q]);
-            xj[k] = fmaf(s, u[q], c * v[q]);
+    for (int q = 0; q < V4; ++q) {
+        const int k = 4 * (lane + 32 * q);
+        if (k < ldl) {
+            float4 x, y;
+            x.x = fmaf(c, u[q].x, -s * v[q].x);
+            x.y = fmaf(c, u[q].y, -s * v[q].y);
+            x.z = fmaf(c, u[q].z, -s * v[q].z);
+            x.w = fmaf(c, u[q].w, -s * v[q].w);
+            y.x = fmaf(s, u[q].x, c * v[q].x);
+            y.y = fmaf(s, u[q].y, c * v[q].y);
+            y.z = fmaf(s, u[q].z, c * v[q].z);
+            y.w = fmaf(s, u[q].w, c * v[q].w);
+            *reinterpret_cast<float4 *>(xi + k) = x;
+            *reinterpret_cast<float4 *>(xj + k) = y;
         }
     }
-    __syncwarp();
     if (lane == 0) {
         *na = a - t * g;
         *nb = b + t * g;
@@ -183,7 +200,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(1024)
                 if (i < b && j < b) {
                     float *x = slot(par, tb);
                     float *n = nslot(par, tb);
-                    my_rot += cj_pair<TM>(x + (long long)i * ldl, x + (long long)j * ldl, n + i, n + j, l, floor2,
+                    my_rot += cj_pair<TM>(x + (long long)i * ldl, x + (long long)j * ldl, n + i, n + j, ldl, floor2,
                                           tol, lane);
                 }
             }
@@ -195,7 +212,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(1024)
                 if (warp < b) {
                     const int i = warp, j = (warp + s) % b;
                     my_rot += cj_pair<TM>(slot(par, 0) + (long long)i * ldl, slot(par, 1) + (long long)j * ldl,
-                                          nslot(par, 0) + i, nslot(par, 1) + j, l, floor2, tol, lane);
+                                          nslot(par, 0) + i, nslot(par, 1) + j, ldl, floor2, tol, lane);
                 }
                 __syncthreads();
             }

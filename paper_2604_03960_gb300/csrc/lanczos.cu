@@ -361,28 +361,31 @@ __global__ void k_lz_init(LzState *lz, int K)
 // Number of eigenvalues of the m x m tridiagonal (a, b[1..m-1]) below x:
 // the negative pivots q_i = p_i / p_{i-1} of T - x I (Sylvester's inertia),
 // read off as sign changes of the leading minors p_i = (a_i - x) p_{i-1} -
-// b_i^2 p_{i-2}.  No division (FP64 division is a long dependent sequence on
-// this part); the minors are rescaled by 2^-500 / 2^500 when they leave
-// [2^-500, 2^500], which keeps every ratio.  A zero minor takes the sign of
-// the previous one (its pivot counts as +0, as in the quotient form).
-__device__ int sturm_count(int m, const double *a, const double *b, double x)
+// b_i^2 p_{i-2} (b2[i] = b_i^2).  No division, and only the three FP64
+// operations of the recurrence per step: signs, zero tests and the range
+// test run on the integer bits (the FP64 pipe is narrow on this part).  The
+// minors are rescaled by 2^-500 / 2^500 when their exponent leaves
+// [-500, 500], which keeps every ratio.  A zero minor takes the sign of the
+// previous one (its pivot counts as +0, as in the quotient form).
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+__device__ int sturm_count(int m, const double *a, const double *b2, double x)
 {
     int cnt = 0;
     double pm = 1.0, p = a[0] - x;
-    if (p == 0.0) p = 1e-300;
-    if (p < 0.0) cnt++;
+    if ((dbits(p) << 1) == 0) p = 1e-300;
+    cnt += dbits(p) < 0;
     for (int i = 1; i < m; ++i) {
-        double pn = fma(a[i] - x, p, -(b[i] * b[i]) * pm);
-        if (pn == 0.0) pn = (p < 0.0) ? -1e-300 : 1e-300;
-        if ((pn < 0.0) != (p < 0.0)) cnt++;
+        double pn = fma(a[i] - x, p, -b2[i] * pm);
+        if ((dbits(pn) << 1) == 0) pn = dbits(p) < 0 ? -1e-300 : 1e-300;
+        cnt += (dbits(pn) ^ dbits(p)) < 0;
         pm = p;
         p = pn;
-        const double ap = fabs(p);
-        if (ap > 3.273390607896142e150) {            // 2^500
+        const int e = (int)((unsigned long long)dbits(p) >> 52) & 0x7ff;
+        if (e > 1523) {                              // |p| >= 2^501
             p *= 3.054936363499605e-151;             // 2^-500
             pm *= 3.054936363499605e-151;
-        } else if (ap < 3.054936363499605e-151) {
-            p *= 3.273390607896142e150;
+        } else if (e < 523) {                        // |p| < 2^-500
+            p *= 3.273390607896142e150;              // 2^500
             pm *= 3.273390607896142e150;
         }
     }
@@ -422,7 +425,7 @@ __global__ void k_tridiag_lowest(LzState *lz, int *status)
 {
     const int lane = threadIdx.x & 31;
     const int m = lz->m;
-    __shared__ double a[LZ_MAXK], b[LZ_MAXK + 1];  // b[i] couples i-1 and i
+    __shared__ double a[LZ_MAXK], b[LZ_MAXK + 1], b2[LZ_MAXK + 1];  // b[i] couples i-1 and i
     __shared__ float af[LZ_MAXK], bf[LZ_MAXK + 1];
     for (int i = lane; i < m; i += 32) {
         a[i] = lz->alpha[i];
@@ -430,6 +433,7 @@ __global__ void k_tridiag_lowest(LzState *lz, int *status)
     }
     for (int i = lane; i <= m && i <= LZ_MAXK; i += 32) {
         b[i] = lz->beta[i];
+        b2[i] = b[i] * b[i];
         bf[i] = (float)b[i];
     }
     __syncwarp();
@@ -465,7 +469,7 @@ __global__ void k_tridiag_lowest(LzState *lz, int *status)
         const double margin = 1e-5 * scale;
         const double clo = fmax(lo, (double)flo - margin), chi = fmin(hi, (double)fhi + margin);
         int c = 0;
-        if (lane < 2) c = sturm_count(m, a, b, lane == 0 ? clo : chi);
+        if (lane < 2) c = sturm_count(m, a, b2, lane == 0 ? clo : chi);
         const int c_lo = __shfl_sync(0xffffffffu, c, 0), c_hi = __shfl_sync(0xffffffffu, c, 1);
         if (c_lo == 0 && c_hi >= 1 && clo < chi) {
             lo = clo;
@@ -477,7 +481,7 @@ __global__ void k_tridiag_lowest(LzState *lz, int *status)
         const double w = hi - lo;
         if (!(w > 4.440892098500626e-16 * fmax(fabs(lo), fabs(hi)))) break;
         const double x = fmin(fma(w, cd, lo), hi);
-        const unsigned below = __ballot_sync(0xffffffffu, sturm_count(m, a, b, x) >= 1);
+        const unsigned below = __ballot_sync(0xffffffffu, sturm_count(m, a, b2, x) >= 1);
         const int f = below ? __ffs(below) - 1 : 31;   // first point at or above lambda_0
         const double xf = __shfl_sync(0xffffffffu, x, f), xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
         double nlo = lo, nhi = hi;
