@@ -249,16 +249,30 @@ __global__ void k_jac_norms(const double *__restrict__ X, int r, int l, long lon
 }
 
 // perm[rank] = i, descending by norm, ties by index
+// Order-preserving integer key of a norm: for v >= 0 (also -0.0) the bits
+// of |v| plus one, monotone in v; NaN and negatives map to 0 and sort last.
+// Ranking on the keys uses integer compares only (FP64 compares run on the
+// narrow FP64 pipe of this part, r of them per element).
+__device__ __forceinline__ unsigned long long norm_key(double v)
+{
+    return (v >= 0.0) ? ((unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL) + 1ULL : 0ULL;
+}
+
+constexpr int kRankSmemKeys = 6144;
 __global__ void k_jac_rank(const double *__restrict__ nrm, int r, int *__restrict__ perm)
 {
+    __shared__ unsigned long long keys[kRankSmemKeys];
+    const bool staged = r <= kRankSmemKeys;
+    if (staged) {
+        for (int j = threadIdx.x; j < r; j += blockDim.x) keys[j] = norm_key(nrm[j]);
+        __syncthreads();
+    }
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= r) return;
-    double v = nrm[i];
-    if (!(v >= 0.0)) v = -1.0;     // NaN sorts last and keeps the ranks a permutation
+    const unsigned long long v = staged ? keys[i] : norm_key(nrm[i]);
     int rank = 0;
     for (int j = 0; j < r; ++j) {
-        double w = nrm[j];
-        if (!(w >= 0.0)) w = -1.0;
+        const unsigned long long w = staged ? keys[j] : norm_key(nrm[j]);
         rank += (w > v) || (w == v && j < i);
     }
     perm[rank] = i;
