@@ -1142,6 +1142,10 @@ dmrg_status dmrg_state_create(dmrg_ctx *ctx, int D, const dmrg_model_params *mp,
         if (s0 != DMRG_OK) return fail(s0);
         if (r != rows) return fail(DMRG_EINVAL);
         k_copy_scale<<<grid1d((long long)r * cols, 256, ctx->num_sms), 256, 0, cs>>>(st->Vt, st->A[i], r, cols, nullptr); DMRG_COUNT_LAUNCH();
+        // the state is normalised at the end; renormalising S at every step
+        // keeps the carried norm (a product over the sites, about 2^N for a
+        // random MPS) from overflowing on long chains
+        k_normalise<<<1, 256, 0, cs>>>(st->s, r); DMRG_COUNT_LAUNCH();
         k_copy_scale<<<grid1d((long long)rows * r, 256, ctx->num_sms), 256, 0, cs>>>(st->U, st->theta, rows, r, st->s); DMRG_COUNT_LAUNCH();
         int pr = 2 * st->chi[i - 1];
         s0 = gemm_f64(cs, pr, r, rows, 1.0, st->A[i - 1], rows, 1, 0, st->theta, r, 1, 0, 0.0, st->X, r, 1, 0, 1);

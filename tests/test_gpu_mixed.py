@@ -188,6 +188,26 @@ def test_presplit_matvec_is_bit_identical(G):
     assert np.array_equal(out[0][2], out[1][2])
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_long_chain_state_stays_finite(G, prec):
+    """A random initial MPS on N = 400 sites carries a norm of about 2^N
+    through its right-canonicalisation; the state must come out normalised
+    and finite, and one sweep must give a Heisenberg energy per site in the
+    physical range (bound -ln 2 + 1/4 = -0.4431 below, and well below 0)."""
+    c = G.Context(0)
+    N = 400
+    p = G.make_params(prec=G.PREC_3XTF32 if prec == "mixed" else G.PREC_FP64, ctrl=G.CTRL_PID, chi_max=16,
+                      chi_init=4)
+    W = c.build_mpo(G.XXZ, N, 1.0, 1.0)
+    m0 = torch.from_numpy(synth.initial_mps_entries(synth.workload_seed(52, N), N, 4)).cuda()
+    st = G.State(c, W, m0, p, 1.0, 1.0)
+    recs, _ = st.sweep(1)
+    E = recs[0].E / N
+    assert np.isfinite(E) and -0.4432 < E < -0.3
+    st.close()
+    c.close()
+
+
 def test_hold_mode_freezes_the_schedule(G, ctx):
     """DMRG_CTRL_HOLD set between sweeps keeps every bond at the chi its PID
     reached: the controller chi of the held sweeps equals the last PID sweep's
