@@ -325,19 +325,23 @@ dmrg_status svd_truncate_batched(dmrg_ctx *ctx, int prec, int batch, const int *
  * and stream, the launch choices of the hot path and keeps the fastest in the
  * context, where the launchers consult it before their heuristics.
  * dmrg_autotune_gemm: for each M x N x K (host arrays of n_shapes), the
- * 3xTF32 tensor-core GEMM with 128- and 256-column tiles; the choice applies
- * to the shape's bucket (ceil log2 of each dimension).  The result bits do
- * not depend on the tile width.  dmrg_autotune_svd: for each n (host array),
- * the mixed-precision SVD of an n x n matrix: with the grouped FP32 Jacobi
- * (option "gjac32", default) its block-pair width (16 or 32 vectors) and
- * groups per CTA (1, 2 or 4), else the older blocked kernel's block-pair
- * target in {24, 48, 96, 152} and 1 or 2 inner sweeps; applies to the
- * (ceil log2 n, ceil log2 n) bucket.  Inputs are generated on the device;
- * `reps` timed calls follow one warm-up call.  These calls allocate and free
- * device memory and synchronise.  dmrg_autotune_save / _load write and read
- * the tables as JSON (format "dmrg-autotune-2"; load also reads format 1)
- * and load replaces the tables; DMRG_EINVAL for a file that is missing or
- * in neither format.
+ * 3xTF32 tensor-core GEMM with 64-, 128- and 256-column tiles at split
+ * depths 4 and 8 (K blocks of 32 per FP32 accumulator; depth 8 is the
+ * default, 4 accumulates less); the choice applies to the shape's bucket
+ * (ceil log2 of each dimension).  At a given depth the result bits do not
+ * depend on the tile width.  dmrg_autotune_svd: for each n (host array), the
+ * mixed-precision SVD of an n x n matrix: the cluster FP32 Jacobi on 8 and on
+ * 16 CTAs (where the vectors fit; this sets its block width ceil(n / 2C)),
+ * and the other kernels (with the grouped FP32 Jacobi, option "gjac32", its
+ * block-pair width, 16 or 32 vectors, and groups per CTA, 1, 2 or 4; else
+ * the blocked kernel's block-pair target in {24, 48, 96, 152} and 1 or 2
+ * inner sweeps); the fastest applies to the (ceil log2 n, ceil log2 n)
+ * bucket.  Inputs are generated on the device; `reps` timed calls follow one
+ * warm-up call.  These calls allocate and free device memory and
+ * synchronise.  dmrg_autotune_save / _load write and read the tables as JSON
+ * (format "dmrg-autotune-3"; load also reads formats 1 and 2) and load
+ * replaces the tables; DMRG_EINVAL for a file that is missing or in none of
+ * these formats.
  * dmrg_autotune_entries: number of GEMM (which = 0) or SVD (1) entries. */
 dmrg_status dmrg_autotune_gemm(dmrg_ctx *ctx, int n_shapes, const int *M, const int *N, const int *K, int reps);
 dmrg_status dmrg_autotune_svd(dmrg_ctx *ctx, int n_sizes, const int *n, int reps);

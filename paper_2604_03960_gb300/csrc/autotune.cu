@@ -1,19 +1,24 @@
 // autotune.cu -- on-device autotuner for the launch choices that the hot
 // path otherwise takes from fixed heuristics:
 //
-//   * the tile width (128 or 256 columns) of the 3xTF32 tensor-core GEMM, per
-//     shape bucket (ceil log2 of M, N and K);
-//   * the blocked FP32 Jacobi's target number of block pairs per round (which
-//     sets the block width and the grid) and its inner sweeps per block
-//     pair, per SVD size bucket (ceil log2 of the vector count and length).
+//   * the tile width (64, 128 or 256 columns) of the 3xTF32 tensor-core GEMM
+//     and its split depth (4 or 8 K blocks of 32 per FP32 accumulator, the
+//     K extent of a slice), per shape bucket (ceil log2 of M, N and K);
+//   * the FP32 Jacobi of the mixed SVD, per size bucket (ceil log2 of the
+//     vector count and length): the cluster kernel on 8 or 16 CTAs (which
+//     sets its block width b = ceil(r / 2C)), or else the other kernels with
+//     their own choices (the grouped kernel's vectors per block pair and
+//     groups per CTA; the blocked kernel's block pairs per round, which set
+//     its block width, and inner sweeps).
 //
 // Each candidate is timed with CUDA events on the context's stream after a
 // warm-up call; the fastest is kept in the context's table, which the GEMM
 // and Jacobi launchers consult before their heuristics.  Tables are saved to
 // and loaded from a small JSON file (one entry per line).  Only the launch
-// configuration changes: a GEMM gives the same bits with either tile width
-// (each output element accumulates its K terms in the same order), and the
-// Jacobi converges to the same tolerance.
+// configuration changes: at a given split depth a GEMM gives the same bits
+// with any tile width (each output element accumulates its K terms in the
+// same order); the split depths on offer bound the FP32 accumulation at or
+// below the default's; and the Jacobi converges to the same tolerance.
 #include "common.cuh"
 
 #include <algorithm>
@@ -49,13 +54,25 @@ struct DevScratch {
 
 }  // namespace
 
-int tune_lookup_bn(const dmrg_ctx *ctx, int M, int N, int K)
+int tune_lookup_bn(const dmrg_ctx *ctx, int M, int N, int K, int *kb)
 {
     if (ctx->tune_gemm.empty()) return 0;
     const int lm = clog2(M), ln = clog2(N), lk = clog2(K);
     for (const auto &e : ctx->tune_gemm)
-        if (e.lm == lm && e.ln == ln && e.lk == lk) return e.bn;
+        if (e.lm == lm && e.ln == ln && e.lk == lk) {
+            if (kb) *kb = e.kb;
+            return e.bn;
+        }
     return 0;
+}
+
+int tune_lookup_cj(const dmrg_ctx *ctx, int r, int l)
+{
+    if (ctx->tune_svd.empty()) return -1;
+    const int lr = clog2(r), ll = clog2(l);
+    for (const auto &e : ctx->tune_svd)
+        if (e.lr == lr && e.ll == ll) return e.cj;
+    return -1;
 }
 
 bool tune_lookup_gjac(const dmrg_ctx *ctx, int r, int l, int *nv, int *groups)
@@ -124,22 +141,32 @@ extern "C" dmrg_status dmrg_autotune_gemm(dmrg_ctx *ctx, int n_shapes, const int
         double *A = static_cast<double *>(buf.p), *B = A + na, *Cm = B + nb;
         k_fill_uniform<<<ctx->num_sms, 256, 0, ctx->stream>>>(A, (long long)(na + nb), 0x1234ULL + i); DMRG_COUNT_LAUNCH();
         DMRG_CUDA(cudaGetLastError());
-        const int saved_bn = ctx->tc_bn_override, saved_force = ctx->tc_force;
+        const int saved_bn = ctx->tc_bn_override, saved_force = ctx->tc_force, saved_kb = ctx->tc_split_kb;
         ctx->tc_force = 1;
-        float ms[2] = {0.f, 0.f};
-        const int cand[2] = {128, 256};
+        const int bns[3] = {64, 128, 256}, kbs[2] = {4, 8};
+        float ms[2][3] = {};
         dmrg_status st = DMRG_OK;
-        for (int c = 0; c < 2 && st == DMRG_OK; ++c) {
-            ctx->tc_bn_override = cand[c];
-            st = time_ms(ctx, reps, [&]() {
-                return gemm(ctx, DMRG_PREC_3XTF32, M[i], N[i], K[i], 1.0, A, K[i], 1, 0, B, N[i], 1, 0, 0.0, Cm, N[i], 1,
-                            0, 1);
-            }, &ms[c]);
-        }
+        for (int b = 0; b < 2 && st == DMRG_OK; ++b)
+            for (int c = 0; c < 3 && st == DMRG_OK; ++c) {
+                ctx->tc_split_kb = kbs[b];
+                ctx->tc_bn_override = bns[c];
+                st = time_ms(ctx, reps, [&]() {
+                    return gemm(ctx, DMRG_PREC_3XTF32, M[i], N[i], K[i], 1.0, A, K[i], 1, 0, B, N[i], 1, 0, 0.0, Cm,
+                                N[i], 1, 0, 1);
+                }, &ms[b][c]);
+            }
         ctx->tc_bn_override = saved_bn;
         ctx->tc_force = saved_force;
+        ctx->tc_split_kb = saved_kb;
         if (st != DMRG_OK) return st;
-        dmrg_ctx::TuneGemm e{clog2(M[i]), clog2(N[i]), clog2(K[i]), ms[0] <= ms[1] ? 128 : 256, ms[0], ms[1]};
+        int bb = 1, bc = 1;                  // default: 128 columns at depth 8
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 3; ++c)
+                if (ms[b][c] < ms[bb][bc]) {
+                    bb = b;
+                    bc = c;
+                }
+        dmrg_ctx::TuneGemm e{clog2(M[i]), clog2(N[i]), clog2(K[i]), bns[bc], ms[bb][1], ms[bb][2], kbs[bb], ms[bb][0]};
         auto it = std::find_if(ctx->tune_gemm.begin(), ctx->tune_gemm.end(), [&](const dmrg_ctx::TuneGemm &x) {
             return x.lm == e.lm && x.ln == e.ln && x.lk == e.lk;
         });
@@ -165,11 +192,12 @@ extern "C" dmrg_status dmrg_autotune_svd(dmrg_ctx *ctx, int n_sizes, const int *
         DMRG_CUDA(cudaGetLastError());
         const int saved_prec = ctx->svd_prec, saved_pairs = ctx->bjac_pairs, saved_inner = ctx->bjac_inner;
         const int saved_nv = ctx->gjac_nv, saved_groups = ctx->gjac_groups;
+        const int saved_cj = ctx->cjac32, saved_fc = ctx->cjac_force_c;
         const auto saved_table = ctx->tune_svd;
         ctx->tune_svd.clear();   // time the candidates themselves, not an earlier decision
         ctx->svd_prec = 1;
         float best = 0.f;
-        int best_p = saved_pairs, best_i = saved_inner, best_nv = 0, best_g = 0;
+        int best_p = saved_pairs, best_i = saved_inner, best_nv = 0, best_g = 0, best_cj = 0;
         dmrg_status st = DMRG_OK;
         auto timed = [&](float *ms) {
             return time_ms(ctx, reps, [&]() {
@@ -179,6 +207,23 @@ extern "C" dmrg_status dmrg_autotune_svd(dmrg_ctx *ctx, int n_sizes, const int *
                 return e == DMRG_ENOCONV ? DMRG_OK : e;
             }, ms);
         };
+        // the cluster kernel on 8 and on 16 CTAs, where the vectors fit
+        // (QR preconditioning leaves r = l = m here)
+        if (saved_cj && m >= ctx->cjac_min_r) {
+            for (int c : {8, 16}) {
+                if (st != DMRG_OK || !cjac32_fits_c(m, m, c)) continue;
+                ctx->cjac32 = 1;
+                ctx->cjac_force_c = c;
+                float ms = 0.f;
+                st = timed(&ms);
+                if (st == DMRG_OK && (best == 0.f || ms < best)) {
+                    best = ms;
+                    best_cj = c;
+                }
+            }
+        }
+        ctx->cjac32 = 0;          // the other kernels
+        ctx->cjac_force_c = 0;
         if (ctx->gjac32 == 2 || (ctx->gjac32 == 1 && (long long)m * m <= kSmemJacFloats)) {
             // grouped kernel: vectors per block pair x groups per CTA
             static const int kNv[] = {16, 32};
@@ -194,6 +239,7 @@ extern "C" dmrg_status dmrg_autotune_svd(dmrg_ctx *ctx, int n_sizes, const int *
                         best = ms;
                         best_nv = nvc;
                         best_g = gc;
+                        best_cj = 0;
                     }
                 }
         } else {
@@ -208,6 +254,9 @@ extern "C" dmrg_status dmrg_autotune_svd(dmrg_ctx *ctx, int n_sizes, const int *
                         best = ms;
                         best_p = pi;
                         best_i = ii;
+                        best_nv = 0;
+                        best_g = 0;
+                        best_cj = 0;
                     }
                 }
         }
@@ -216,9 +265,11 @@ extern "C" dmrg_status dmrg_autotune_svd(dmrg_ctx *ctx, int n_sizes, const int *
         ctx->bjac_inner = saved_inner;
         ctx->gjac_nv = saved_nv;
         ctx->gjac_groups = saved_groups;
+        ctx->cjac32 = saved_cj;
+        ctx->cjac_force_c = saved_fc;
         ctx->tune_svd = saved_table;
         if (st != DMRG_OK) return st;
-        dmrg_ctx::TuneSvd e{clog2(m), clog2(m), best_p, best_i, best, best_nv, best_g};
+        dmrg_ctx::TuneSvd e{clog2(m), clog2(m), best_p, best_i, best, best_nv, best_g, best_cj};
         auto it = std::find_if(ctx->tune_svd.begin(), ctx->tune_svd.end(), [&](const dmrg_ctx::TuneSvd &x) {
             return x.lr == e.lr && x.ll == e.ll;
         });
@@ -251,17 +302,19 @@ extern "C" dmrg_status dmrg_autotune_save(const dmrg_ctx *ctx, const char *path)
     std::string dev = cudaGetDeviceProperties(&prop, ctx->device) == cudaSuccess ? prop.name : "unknown";
     for (auto &ch : dev)
         if (ch == '"' || ch == '\\') ch = ' ';
-    std::fprintf(f, "{\"format\": \"dmrg-autotune-2\", \"device\": \"%s\",\n \"gemm\": [\n", dev.c_str());
+    std::fprintf(f, "{\"format\": \"dmrg-autotune-3\", \"device\": \"%s\",\n \"gemm\": [\n", dev.c_str());
     for (size_t i = 0; i < ctx->tune_gemm.size(); ++i) {
         const auto &e = ctx->tune_gemm[i];
-        std::fprintf(f, "  {\"lm\": %d, \"ln\": %d, \"lk\": %d, \"bn\": %d, \"ms128\": %.6g, \"ms256\": %.6g}%s\n", e.lm,
-                     e.ln, e.lk, e.bn, e.ms128, e.ms256, i + 1 < ctx->tune_gemm.size() ? "," : "");
+        std::fprintf(f, "  {\"lm\": %d, \"ln\": %d, \"lk\": %d, \"bn\": %d, \"ms128\": %.6g, \"ms256\": %.6g, "
+                        "\"kb\": %d, \"ms64\": %.6g}%s\n",
+                     e.lm, e.ln, e.lk, e.bn, e.ms128, e.ms256, e.kb, e.ms64, i + 1 < ctx->tune_gemm.size() ? "," : "");
     }
     std::fprintf(f, " ],\n \"svd\": [\n");
     for (size_t i = 0; i < ctx->tune_svd.size(); ++i) {
         const auto &e = ctx->tune_svd[i];
-        std::fprintf(f, "  {\"lr\": %d, \"ll\": %d, \"pairs\": %d, \"inner\": %d, \"ms\": %.6g, \"nv\": %d, \"groups\": %d}%s\n",
-                     e.lr, e.ll, e.pairs, e.inner, e.ms, e.nv, e.groups, i + 1 < ctx->tune_svd.size() ? "," : "");
+        std::fprintf(f, "  {\"lr\": %d, \"ll\": %d, \"pairs\": %d, \"inner\": %d, \"ms\": %.6g, \"nv\": %d, \"groups\": %d, "
+                        "\"cj\": %d}%s\n",
+                     e.lr, e.ll, e.pairs, e.inner, e.ms, e.nv, e.groups, e.cj, i + 1 < ctx->tune_svd.size() ? "," : "");
     }
     std::fprintf(f, " ]}\n");
     const bool ok = std::fclose(f) == 0;
@@ -278,12 +331,20 @@ extern "C" dmrg_status dmrg_autotune_load(dmrg_ctx *ctx, const char *path)
     char line[512];
     bool format_ok = false;
     while (std::fgets(line, sizeof line, f)) {
-        if (std::strstr(line, "\"dmrg-autotune-1\"") || std::strstr(line, "\"dmrg-autotune-2\"")) format_ok = true;
+        if (std::strstr(line, "\"dmrg-autotune-1\"") || std::strstr(line, "\"dmrg-autotune-2\"") ||
+            std::strstr(line, "\"dmrg-autotune-3\""))
+            format_ok = true;
         dmrg_ctx::TuneGemm e{};
         dmrg_ctx::TuneSvd t{};
         if (std::sscanf(line, " {\"lm\": %d, \"ln\": %d, \"lk\": %d, \"bn\": %d, \"ms128\": %f, \"ms256\": %f", &e.lm,
                         &e.ln, &e.lk, &e.bn, &e.ms128, &e.ms256) == 6) {
-            if (e.bn != 128 && e.bn != 256) { std::fclose(f); return DMRG_EINVAL; }
+            // format 3 adds the split depth and the 64-column time (absent: the defaults)
+            const char *q = std::strstr(line, "\"kb\":");
+            if (q && std::sscanf(q, "\"kb\": %d, \"ms64\": %f", &e.kb, &e.ms64) != 2) { std::fclose(f); return DMRG_EINVAL; }
+            if ((e.bn != 64 && e.bn != 128 && e.bn != 256) || (e.kb != 0 && e.kb != 4 && e.kb != 8)) {
+                std::fclose(f);
+                return DMRG_EINVAL;
+            }
             g.push_back(e);
         } else if (std::sscanf(line, " {\"lr\": %d, \"ll\": %d, \"pairs\": %d, \"inner\": %d, \"ms\": %f", &t.lr, &t.ll,
                                &t.pairs, &t.inner, &t.ms) == 5) {
@@ -295,6 +356,11 @@ extern "C" dmrg_status dmrg_autotune_load(dmrg_ctx *ctx, const char *path)
                     std::fclose(f);
                     return DMRG_EINVAL;
                 }
+            }
+            const char *c = std::strstr(line, "\"cj\":");
+            if (c && (std::sscanf(c, "\"cj\": %d", &t.cj) != 1 || (t.cj != -1 && t.cj != 0 && t.cj != 8 && t.cj != 16))) {
+                std::fclose(f);
+                return DMRG_EINVAL;
             }
             v.push_back(t);
         }

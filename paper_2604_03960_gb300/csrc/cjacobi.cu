@@ -360,9 +360,17 @@ bool cj_fits_dispatch(const CjPlan &p)
 }
 
 // 8 CTAs where the blocks fit them, else 16 (opt-in cluster size) if the GPU
-// can hold such a cluster; 0 if neither.
-int cj_choose(int r, int l, CjPlan *out)
+// can hold such a cluster; 0 if neither.  force_c = 8 or 16 takes that size
+// if it fits (the autotuner's choice), else 0.
+int cj_choose(int r, int l, CjPlan *out, int force_c = 0)
 {
+    if (force_c == 8 || force_c == 16) {
+        CjPlan p = cj_plan(r, l, force_c);
+        if (!cj_plan_ok(p, r, l)) return 0;
+        if (force_c == 16 && !cj_fits_dispatch<16>(p)) return 0;
+        *out = p;
+        return force_c;
+    }
     CjPlan p8 = cj_plan(r, l, 8);
     if (cj_plan_ok(p8, r, l)) {
         *out = p8;
@@ -390,13 +398,19 @@ bool cjac32_fits(int r, int l)
     return cj_choose(r, l, &p) != 0;
 }
 
+bool cjac32_fits_c(int r, int l, int C)
+{
+    CjPlan p;
+    return cj_choose(r, l, &p, C) == C;
+}
+
 // X: r x l row-major FP32 (device), rotated in place; r_eff (device, may be
 // null): only the first *r_eff rows take part, the rest are left untouched.
 dmrg_status cjac32_run(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps, double tol, double small,
-                       const double *F2, int *d_info, const int *r_eff)
+                       const double *F2, int *d_info, const int *r_eff, int force_c)
 {
     CjPlan p;
-    const int C = cj_choose(r, l, &p);
+    const int C = cj_choose(r, l, &p, force_c);
     if (!C) return DMRG_EUNSUPPORTED;
     const float tf = (float)tol;
 #define CJ_LAUNCH(TMV, CV)                                                                                           \

@@ -131,10 +131,14 @@ struct dmrg_ctx {
     // autotuner decisions (autotune.cu): tensor-core tile width per GEMM
     // shape bucket, blocked-Jacobi grid target and inner sweeps per SVD
     // size bucket; buckets are ceil(log2) of each dimension
-    struct TuneGemm { int lm, ln, lk, bn; float ms128, ms256; };
+    // GEMM bucket: tile width (64, 128, 256) and split depth (K blocks per
+    // FP32 accumulator, 4 or 8), with the time of each width at that depth
+    struct TuneGemm { int lm, ln, lk, bn; float ms128, ms256; int kb = 0; float ms64 = 0.f; };
     // SVD bucket: the old blocked kernel's block-pair target and inner sweeps,
-    // the grouped kernel's vectors per block pair (nv) and groups per CTA
-    struct TuneSvd { int lr, ll, pairs, inner; float ms; int nv, groups; };
+    // the grouped kernel's vectors per block pair (nv) and groups per CTA, and
+    // the cluster kernel's size (cj: 8 or 16 CTAs, 0 = not the cluster kernel,
+    // -1 = no choice recorded)
+    struct TuneSvd { int lr, ll, pairs, inner; float ms; int nv, groups; int cj = -1; };
     std::vector<TuneGemm> tune_gemm;
     std::vector<TuneSvd> tune_svd;
     dmrg::DevBuf work4;          // batched SVD workspace
@@ -152,6 +156,7 @@ struct dmrg_ctx {
     int lz_fused = 1;            // Lanczos: one cooperative launch per step for the orthogonalisation
     int cjac32 = 1;              // FP32 Jacobi: one-cluster kernel (cjacobi.cu) from cjac_min_r vectors on
     int cjac_min_r = 32;
+    int cjac_force_c = 0;        // cluster Jacobi: 8 or 16 CTAs forced (autotuner, option), 0 = by size
     int gjac32 = 0;              // FP32 Jacobi: grouped block kernel (gjacobi.cu): 0 never, 1 small problems, 2 always
     int gjac_nv = 0;             // ... vectors per block pair (16, 32; 0 = by size)
     int gjac_groups = 0;         // ... max groups per CTA (0 = by shared memory)
@@ -257,7 +262,8 @@ size_t gbj32_padded_bytes(int r, int l);
 size_t cjac32_smem_bytes(int r, int l);
 bool cjac32_fits(int r, int l);
 dmrg_status cjac32_run(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps, double tol, double small,
-                       const double *F2, int *d_info, const int *r_eff);
+                       const double *F2, int *d_info, const int *r_eff, int force_c = 0);
+bool cjac32_fits_c(int r, int l, int C);
 dmrg_status gbj32_sweeps(dmrg_ctx *ctx, const double *A, int m, int n, int dir, float *X, float *Xp, void *qrw,
                          unsigned *sync, int max_sweeps, double tol, double small, int *d_info);
 dmrg_status frob2_f32(dmrg_ctx *ctx, const float *A, long long n, double *F2);
@@ -267,7 +273,8 @@ size_t qr32_work_bytes(int c);
 dmrg_status qr_precondition32(dmrg_ctx *ctx, float *X, int c, int l, void *work);
 
 // Autotuner table lookups (autotune.cu): 0 / false when the bucket has no entry.
-int tune_lookup_bn(const dmrg_ctx *ctx, int M, int N, int K);
+int tune_lookup_bn(const dmrg_ctx *ctx, int M, int N, int K, int *kb = nullptr);
+int tune_lookup_cj(const dmrg_ctx *ctx, int r, int l);
 bool tune_lookup_svd(const dmrg_ctx *ctx, int r, int l, int *pairs, int *inner);
 bool tune_lookup_gjac(const dmrg_ctx *ctx, int r, int l, int *nv, int *groups);
 

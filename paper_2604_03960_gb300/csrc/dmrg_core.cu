@@ -627,8 +627,13 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
     }
     if (!std::strcmp(name, "tc_bn")) {
         int v = (int)value;
-        if (v != 0 && v != 128 && v != 256) return DMRG_EINVAL;
+        if (v != 0 && v != 64 && v != 128 && v != 256) return DMRG_EINVAL;
         ctx->tc_bn_override = v;
+        return DMRG_OK;
+    }
+    if (!std::strcmp(name, "cjac_force_c")) {
+        if (value != 0.0 && value != 8.0 && value != 16.0) return DMRG_EINVAL;
+        ctx->cjac_force_c = (int)value;
         return DMRG_OK;
     }
     if (!std::strcmp(name, "mixed_env_tc")) { ctx->mixed_env_tc = value != 0.0; return DMRG_OK; }

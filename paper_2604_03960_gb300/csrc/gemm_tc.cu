@@ -422,10 +422,11 @@ bool tc_available(dmrg_ctx *ctx)
 // Tile width choice: 256-column tiles unless that leaves most SMs idle.
 int tc_pick_bn(dmrg_ctx *ctx, int M, int N, int K, int batch)
 {
-    if (ctx->tc_bn_override == 128 || ctx->tc_bn_override == 256) return ctx->tc_bn_override;
+    if (ctx->tc_bn_override == 64 || ctx->tc_bn_override == 128 || ctx->tc_bn_override == 256)
+        return ctx->tc_bn_override;
     if (batch == 1) {
         const int tuned = tune_lookup_bn(ctx, M, N, K);
-        if (tuned == 128 || tuned == 256) return tuned;
+        if (tuned == 64 || tuned == 128 || tuned == 256) return tuned;
     }
     long long t256 = (long long)((N + 255) / 256) * ((M + TBM - 1) / TBM) * batch;
     long long t128 = (long long)((N + 127) / 128) * ((M + TBM - 1) / TBM) * batch;
@@ -485,8 +486,13 @@ dmrg_status gemm_3xtf32_pre(dmrg_ctx *ctx, int M, int N, int K, double alpha, co
     // K' = 3 Kp products (the slices meet in FP64)
     const int nk = K3 / TBK;
     int nsl = 1;
-    if (ctx->tc_split_kb > 0 && nk > ctx->tc_split_kb) {
-        nsl = (nk + ctx->tc_split_kb - 1) / ctx->tc_split_kb;
+    int kb = ctx->tc_split_kb;
+    if (batch == 1 && ctx->tc_bn_override == 0 && kb == 8) {
+        int tkb = 0;
+        if (tune_lookup_bn(ctx, M, N, K, &tkb) && (tkb == 4 || tkb == 8)) kb = tkb;   // autotuned depth
+    }
+    if (kb > 0 && nk > kb) {
+        nsl = (nk + kb - 1) / kb;
         if (nsl > 16) nsl = 16;
         const int kps = (nk + nsl - 1) / nsl;
         nsl = (nk + kps - 1) / kps;
