@@ -223,6 +223,16 @@ __device__ __forceinline__ void sum_parts(const double *part, int stride, int nq
     __syncthreads();
 }
 
+// grid barrier of the fused step; a one-block grid needs only the block's
+__device__ __forceinline__ bool lz_barrier(unsigned *bar, int *status)
+{
+    if (gridDim.x == 1) {
+        __syncthreads();
+        return true;
+    }
+    return grid_barrier(bar, status);
+}
+
 // One Lanczos step's orthogonalisation in one cooperative launch (the five
 // launches above fused; three bounded grid barriers):
 //   c = V^T w (v_0..v_j), alpha_j = c_j;  w -= V c, and in the same pass
@@ -257,7 +267,7 @@ __global__ void __launch_bounds__(OB) k_lz_orth(double *__restrict__ V, double *
             if (q < nq) acc[q] = fma(V[(long long)q * n + i], wi, acc[q]);
     }
     block_cols_to<OB>(acc, nq, red, p0 + (long long)blockIdx.x * S);
-    if (!grid_barrier(bar, status)) return;
+    if (!lz_barrier(bar, status)) return;
     sum_parts<OB>(p0, S, nq, cs);
     const double alpha = cs[j];
     const double amax = fmax(amax0, fabs(alpha));
@@ -281,7 +291,7 @@ __global__ void __launch_bounds__(OB) k_lz_orth(double *__restrict__ V, double *
     }
     __syncthreads();                         // cs is rewritten below
     block_cols_to<OB>(acc, nq, red, p1 + (long long)blockIdx.x * S);
-    if (!grid_barrier(bar, status)) return;
+    if (!lz_barrier(bar, status)) return;
     sum_parts<OB>(p1, S, nq, cs);
     // phase C: w -= V c', |w|^2
     double ss = 0.0;
@@ -297,7 +307,7 @@ __global__ void __launch_bounds__(OB) k_lz_orth(double *__restrict__ V, double *
     __syncthreads();
     acc[0] = ss;
     block_cols_to<OB>(acc, 1, red, p2 + (long long)blockIdx.x * S);
-    if (!grid_barrier(bar, status)) return;
+    if (!lz_barrier(bar, status)) return;
     sum_parts<OB>(p2, S, 1, cs);
     // phase D: beta_{j+1}, continuation, next vector
     const double bta = sqrt(cs[0]);

@@ -23,7 +23,10 @@ namespace dmrg {
 namespace {
 
 constexpr int kQrB = 16;          // panel width
+// panel threads: one warp per trailing panel column in the reflector step
+// (measured at 128 rows: 35 us a panel with 512 threads, 120 us with 32)
 constexpr int kQrPanelThreads = 512;
+inline int qr_panel_threads(int) { return kQrPanelThreads; }
 constexpr int kQrTrailThreads = 256;
 
 __device__ __forceinline__ float wsumf(float v)
@@ -39,16 +42,17 @@ __device__ __forceinline__ float wsumf(float v)
 // reflector from the reduced norm itself.  Panel rows have stride ps = the
 // panel width + 1 (odd: no bank conflicts between consecutive rows).
 
-__global__ void __launch_bounds__(kQrPanelThreads) k_qr_panel(float *__restrict__ X, int c, int l, int k, int bw,
+template <int PT>
+__global__ void __launch_bounds__(PT) k_qr_panel(float *__restrict__ X, int c, int l, int k, int bw,
                                                               int kPS, float *__restrict__ V, float *__restrict__ T)
 {
     extern __shared__ float P[];                   // rows x kPS
-    constexpr int nw = kQrPanelThreads / 32;
+    constexpr int nw = PT / 32;
     __shared__ float part[nw][kQrB];
     __shared__ float npart[nw];
     __shared__ float sbeta[kQrB], G[kQrB][kQrB + 1];
     const int rows = c - k, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < rows; i += kQrPanelThreads) {
+    for (int i = tid; i < rows; i += PT) {
         for (int j = 0; j < bw; ++j) P[i * kPS + j] = X[(long long)(k + i) * l + k + j];
         for (int j = 0; j < kQrB; ++j) V[(long long)i * kQrB + j] = 0.f;
     }
@@ -58,7 +62,7 @@ __global__ void __launch_bounds__(kQrPanelThreads) k_qr_panel(float *__restrict_
         // with alpha = -+sqrt(a) rounded once, beta = -1/(alpha v0) = 2/(v^T v)
         // to FP32 rounding, so each reflector is orthogonal at FP32 level
         float a = 0.f;
-        for (int i = tid; i < rows; i += kQrPanelThreads)
+        for (int i = tid; i < rows; i += PT)
             if (i >= j) { const float x = P[i * kPS + j]; a = fmaf(x, x, a); }
         a = wsumf(a);
         if (lane == 0) npart[warp] = a;
@@ -87,7 +91,7 @@ __global__ void __launch_bounds__(kQrPanelThreads) k_qr_panel(float *__restrict_
             }
         }
         __syncthreads();
-        for (int i = tid; i < rows; i += kQrPanelThreads) {
+        for (int i = tid; i < rows; i += PT) {
             if (i < j) continue;
             const float vi = i == j ? v0 : P[i * kPS + j];
             V[(long long)i * kQrB + j] = vi;
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(kQrPanelThreads) k_qr_panel(float *__restrict_
         }
         for (int e = lane; e < kQrB * kQrB; e += 32) T[e] = Ts[e / kQrB][e % kQrB];
     }
-    for (int i = tid; i < rows; i += kQrPanelThreads)
+    for (int i = tid; i < rows; i += PT)
         for (int j = 0; j < bw; ++j) X[(long long)(k + i) * l + k + j] = P[i * kPS + j];
 }
 
@@ -206,10 +210,13 @@ dmrg_status qr_precondition32(dmrg_ctx *ctx, float *X, int c, int l, void *work)
     const int kPS = bmax + 1;
     const size_t smem_max = (size_t)c * kPS * sizeof(float);
     if (smem_max > 200 * 1024) return DMRG_EUNSUPPORTED;
-    static size_t attr = 0;
-    if (attr < smem_max) {
-        DMRG_CUDA(cudaFuncSetAttribute(k_qr_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = 200 * 1024;
+    static bool attr = false;
+    if (!attr) {
+        DMRG_CUDA(cudaFuncSetAttribute(k_qr_panel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        DMRG_CUDA(cudaFuncSetAttribute(k_qr_panel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        DMRG_CUDA(cudaFuncSetAttribute(k_qr_panel<kQrPanelThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
+        attr = true;
     }
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     float *V = static_cast<float *>(work);
@@ -219,7 +226,14 @@ dmrg_status qr_precondition32(dmrg_ctx *ctx, float *X, int c, int l, void *work)
     for (int k = 0; k < kmax; k += bmax) {
         const int bw = std::min(bmax, kmax - k);
         const size_t smem = (size_t)(c - k) * kPS * sizeof(float);
-        k_qr_panel<<<1, kQrPanelThreads, smem, ctx->stream>>>(X, c, l, k, bw, kPS, V, T); DMRG_COUNT_LAUNCH();
+        const int pt = qr_panel_threads(c - k);
+        if (pt == 32)
+            k_qr_panel<32><<<1, 32, smem, ctx->stream>>>(X, c, l, k, bw, kPS, V, T);
+        else if (pt == 128)
+            k_qr_panel<128><<<1, 128, smem, ctx->stream>>>(X, c, l, k, bw, kPS, V, T);
+        else
+            k_qr_panel<kQrPanelThreads><<<1, kQrPanelThreads, smem, ctx->stream>>>(X, c, l, k, bw, kPS, V, T);
+        DMRG_COUNT_LAUNCH();
         const int ncols = l - (k + bw);
         if (ncols > 0) {
             k_qr_trail<<<(ncols + 31) / 32, kQrTrailThreads, 0, ctx->stream>>>(X, c, l, k, bw, V, T);
