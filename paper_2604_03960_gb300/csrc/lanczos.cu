@@ -189,17 +189,19 @@ __global__ void __launch_bounds__(RB) k_multiaxpy_norm(double *__restrict__ w, c
     *counter = 0u;
 }
 
-// Column sums of acc[0..nq) over the block (FP64, fixed order), written to
-// part[q]; red: (MAXQ + 1) x OB doubles of shared memory (OB: block size).
+// Column sums of acc[q] over the block (FP64, fixed order) for q < nq and,
+// with `last`, q = MAXQ, written to part[q]; red: (MAXQ + 1) x OB doubles of
+// shared memory (OB: block size).
 template <int OB>
-__device__ __forceinline__ void block_cols_to(const double *acc, int nq, double *red, double *part)
+__device__ __forceinline__ void block_cols_to(const double *acc, int nq, bool last, double *red, double *part)
 {
 #pragma unroll
-    for (int q = 0; q < MAXQ; ++q)
-        if (q < nq) red[q * OB + threadIdx.x] = acc[q];
+    for (int q = 0; q <= MAXQ; ++q)
+        if (q < nq || (last && q == MAXQ)) red[q * OB + threadIdx.x] = acc[q];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = warp; q < nq; q += OB / 32) {
+    for (int q = warp; q <= MAXQ; q += OB / 32) {
+        if (!(q < nq || (last && q == MAXQ))) continue;
         double s = 0.0;
 #pragma unroll
         for (int k = 0; k < OB / 32; ++k) s += red[q * OB + lane + 32 * k];
@@ -208,13 +210,14 @@ __device__ __forceinline__ void block_cols_to(const double *acc, int nq, double 
     }
 }
 
-// Sum of the blocks' partials part[b * stride + q] for q < nq, b < G, in
+// Sum of the blocks' partials part[b * stride + q] (the same columns), in
 // block order (every CTA gets the same bits); result to cs[q].
 template <int OB>
-__device__ __forceinline__ void sum_parts(const double *part, int stride, int nq, double *cs)
+__device__ __forceinline__ void sum_parts(const double *part, int stride, int nq, bool last, double *cs)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = warp; q < nq; q += OB / 32) {
+    for (int q = warp; q <= MAXQ; q += OB / 32) {
+        if (!(q < nq || (last && q == MAXQ))) continue;
         double s = 0.0;
         for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(&part[(long long)b * stride + q]);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -234,10 +237,11 @@ __device__ __forceinline__ bool lz_barrier(unsigned *bar, int *status)
 }
 
 // One Lanczos step's orthogonalisation in one cooperative launch (the five
-// launches above fused; three bounded grid barriers):
-//   c = V^T w (v_0..v_j), alpha_j = c_j;  w -= V c, and in the same pass
-//   c' = V^T w;  w -= V c', |w|^2;  beta_{j+1} = |w|, continuation as in
-//   k_multiaxpy_norm;  v_{j+1} = w / beta_{j+1} if the recurrence goes on.
+// launches above fused; two bounded grid barriers):
+//   c = V^T w (v_0..v_j), alpha_j = c_j;  w1 = w - V c, and in the same pass
+//   c' = V^T w1 and |w1|^2;  beta_{j+1} = |w1 - V c'| from |w1|^2 - |c'|^2,
+//   continuation as in k_multiaxpy_norm;  v_{j+1} = (w1 - V c') / beta_{j+1}
+//   if the recurrence goes on.
 // Each thread keeps its elements' v_q in registers between the update and
 // the next dot product, so V is read three times instead of four.
 // part: 3 x gridDim.x x (MAXQ + 1) doubles; bar: two zeroed words.
@@ -256,24 +260,25 @@ __global__ void __launch_bounds__(OB) k_lz_orth(double *__restrict__ V, double *
     double *p0 = part, *p1 = part + (long long)gridDim.x * S, *p2 = part + 2LL * gridDim.x * S;
     const long long stride = (long long)gridDim.x * OB;
     const long long i0 = (long long)blockIdx.x * OB + threadIdx.x;
-    double acc[MAXQ];
+    double acc[MAXQ + 1];
     // phase A: c = V^T w
 #pragma unroll
-    for (int q = 0; q < MAXQ; ++q) acc[q] = 0.0;
+    for (int q = 0; q <= MAXQ; ++q) acc[q] = 0.0;
     for (long long i = i0; i < n; i += stride) {
         const double wi = w[i];
 #pragma unroll
         for (int q = 0; q < MAXQ; ++q)
             if (q < nq) acc[q] = fma(V[(long long)q * n + i], wi, acc[q]);
     }
-    block_cols_to<OB>(acc, nq, red, p0 + (long long)blockIdx.x * S);
+    block_cols_to<OB>(acc, nq, false, red, p0 + (long long)blockIdx.x * S);
     if (!lz_barrier(bar, status)) return;
-    sum_parts<OB>(p0, S, nq, cs);
+    sum_parts<OB>(p0, S, nq, false, cs);
     const double alpha = cs[j];
     const double amax = fmax(amax0, fabs(alpha));
-    // phase B: w -= V c, c' = V^T w
+    // phase B: w1 = w - V c; c' = V^T w1 and |w1|^2 in the same pass
+    double acc2[MAXQ + 1];
 #pragma unroll
-    for (int q = 0; q < MAXQ; ++q) acc[q] = 0.0;
+    for (int q = 0; q <= MAXQ; ++q) acc2[q] = 0.0;
     for (long long i = i0; i < n; i += stride) {
         double v[MAXQ];
         double a = 0.0;
@@ -287,35 +292,25 @@ __global__ void __launch_bounds__(OB) k_lz_orth(double *__restrict__ V, double *
         w[i] = wi;
 #pragma unroll
         for (int q = 0; q < MAXQ; ++q)
-            if (q < nq) acc[q] = fma(v[q], wi, acc[q]);
+            if (q < nq) acc2[q] = fma(v[q], wi, acc2[q]);
+        acc2[MAXQ] = fma(wi, wi, acc2[MAXQ]);
     }
     __syncthreads();                         // cs is rewritten below
-    block_cols_to<OB>(acc, nq, red, p1 + (long long)blockIdx.x * S);
+    block_cols_to<OB>(acc2, nq, true, red, p1 + (long long)blockIdx.x * S);   // |w1|^2 in column MAXQ
     if (!lz_barrier(bar, status)) return;
-    sum_parts<OB>(p1, S, nq, cs);
-    // phase C: w -= V c', |w|^2
-    double ss = 0.0;
-    for (long long i = i0; i < n; i += stride) {
-        double a = 0.0;
-#pragma unroll
-        for (int q = 0; q < MAXQ; ++q)
-            if (q < nq) a = fma(cs[q], V[(long long)q * n + i], a);
-        const double wi = w[i] - a;
-        w[i] = wi;
-        ss = fma(wi, wi, ss);
-    }
-    __syncthreads();
-    acc[0] = ss;
-    block_cols_to<OB>(acc, 1, red, p2 + (long long)blockIdx.x * S);
-    if (!lz_barrier(bar, status)) return;
-    sum_parts<OB>(p2, S, 1, cs);
-    // phase D: beta_{j+1}, continuation, next vector
-    const double bta = sqrt(cs[0]);
+    sum_parts<OB>(p1, S, nq, true, cs);
+    // phase C: beta_{j+1}^2 = |w1 - V c'|^2 = |w1|^2 - |c'|^2 (V has
+    // orthonormal columns and c' = V^T w1 is tiny after the first pass, so
+    // the difference loses nothing); continuation; v_{j+1} = (w1 - V c') / beta
+    double cc = 0.0;
+    for (int q = 0; q < nq; ++q) cc = fma(cs[q], cs[q], cc);
+    const double b2 = cs[MAXQ] - cc;
+    const double bta = b2 > 0.0 ? sqrt(b2) : (b2 == 0.0 ? 0.0 : b2);   // negative: not finite below
     const bool go = (j + 1 < K) && (bta > 1e-14 * amax) && isfinite(bta);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         lz->alpha[j] = alpha;
         lz->amax = amax;
-        lz->beta[j + 1] = bta;
+        lz->beta[j + 1] = bta > 0.0 ? bta : 0.0;
         lz->m = j + 1;
         if (!go) lz->active = 0;
         if (!isfinite(bta)) lz->nan = 1;
@@ -324,7 +319,11 @@ __global__ void __launch_bounds__(OB) k_lz_orth(double *__restrict__ V, double *
         const double inv = 1.0 / bta;
         double *vn = V + (long long)(j + 1) * n;
         for (long long i = i0; i < n; i += stride) {
-            const double v = w[i] * inv;
+            double a = 0.0;
+#pragma unroll
+            for (int q = 0; q < MAXQ; ++q)
+                if (q < nq) a = fma(cs[q], V[(long long)q * n + i], a);
+            const double v = (w[i] - a) * inv;
             vn[i] = v;
             if (sink.h) sink_write(sink, i, v);   // the next matvec's split right operand
         }
