@@ -704,7 +704,7 @@ def autotune(args, ctx, chi_max):
             pass
     shapes, sizes = [], []
     D = 5
-    chi = 128
+    chi = 32
     while chi <= min(chi_max, 512):
         shapes += [(D * chi, 4 * chi, chi), (4 * chi, chi, D * chi)]    # the two H_eff contractions
         sizes.append(2 * chi)                                            # theta of the bond

@@ -431,6 +431,10 @@ int tc_pick_bn(dmrg_ctx *ctx, int M, int N, int K, int batch)
     long long t256 = (long long)((N + 255) / 256) * ((M + TBM - 1) / TBM) * batch;
     long long t128 = (long long)((N + 127) / 128) * ((M + TBM - 1) / TBM) * batch;
     if (N <= 64) return 64;      // half the accumulator columns and epilogue of a 128 tile
+    // products that fill under one wave even with 64-column tiles are
+    // latency-bound: twice the CTAs, each with half the epilogue
+    const long long t64 = (long long)((N + 63) / 64) * ((M + TBM - 1) / TBM) * batch;
+    if (t64 <= ctx->num_sms) return 64;
     if (N <= 128) return 128;
     // compare wave-quantised work: tiles rounded up to whole waves, weighted by tile width
     long long w256 = ((t256 + ctx->num_sms - 1) / ctx->num_sms) * 2;

@@ -550,7 +550,9 @@ int grid_dot(long long n, int num_sms)
 // fused orthogonalisation: 128-thread blocks, one element a thread up to one
 // block per SM (all co-resident: the launch is cooperative).  The FP64
 // multiply-adds of the passes and of the block sums (2 a clock per SM on
-// this part) grow with elements + threads per SM, so small blocks on every SM.
+// this part) grow with elements + threads per SM, and the grid barrier and
+// the sum over blocks' partials with the block count; measured at 16,384
+// elements: 28.4 us a step with 256 threads, 25.8 with 128, 40.9 with 64.
 constexpr int kOB = 128;
 int grid_orth(long long n, int num_sms)
 {
