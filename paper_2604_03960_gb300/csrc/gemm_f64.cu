@@ -19,6 +19,12 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
+// operand conversion: FP64 stays, FP32 narrows by integer operations
+// (bit-identical to the converting instruction, which uses the narrow FP64 pipe)
+template <typename T> __device__ __forceinline__ T narrow_to(double v);
+template <> __device__ __forceinline__ double narrow_to<double>(double v) { return v; }
+template <> __device__ __forceinline__ float narrow_to<float>(double v) { return f64_narrow(v); }
+
 // T = double: the FP64 path; T = float: FP32 arithmetic on FP64 operands for
 // the small products of the mixed form.  In the FP32 case each BK-long
 // partial sum is added into a compensated pair (hi, lo) by Knuth's TwoSum, so
@@ -52,6 +58,7 @@ __global__ void __launch_bounds__(NT) k_gemm_t(int M, int N, int K, double alpha
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int kb = nsl > 1 ? sl * kps : 0;
     const int ke = nsl > 1 ? min(K, kb + kps) : K;
+    const bool plain = (alpha == 1.0) && (beta == 0.0);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     A += (long long)bz * sAb;
     B += (long long)bz * sBb;
@@ -78,7 +85,7 @@ __global__ void __launch_bounds__(NT) k_gemm_t(int M, int N, int K, double alpha
             int mm, kk;
             if (a_kfast) { mm = idx / BK; kk = idx % BK; } else { kk = idx / BM; mm = idx % BM; }
             int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < M && gk < ke) ? (T)A[(long long)gm * sAm + (long long)gk * sAk] : (T)0;
+            As[kk][mm] = (gm < M && gk < ke) ? narrow_to<T>(A[(long long)gm * sAm + (long long)gk * sAk]) : (T)0;
         }
 #pragma unroll
         for (int it = 0; it < (BN * BK) / NT; ++it) {
@@ -86,20 +93,41 @@ __global__ void __launch_bounds__(NT) k_gemm_t(int M, int N, int K, double alpha
             int nn, kk;
             if (b_nfast) { kk = idx / BN; nn = idx % BN; } else { nn = idx / BK; kk = idx % BK; }
             int gn = n0 + nn, gk = k0 + kk;
-            Bs[kk][nn] = (gn < N && gk < ke) ? (T)B[(long long)gk * sBk + (long long)gn * sBn] : (T)0;
+            Bs[kk][nn] = (gn < N && gk < ke) ? narrow_to<T>(B[(long long)gk * sBk + (long long)gn * sBn]) : (T)0;
         }
         __syncthreads();
+        // multiply-adds only where they can reach an output: a thread whose
+        // first row or column lies beyond the matrix has none, and a short
+        // last K step stops at K (the padding would be FP64 work on zeros,
+        // and the FP64 pipe of this part gives ~2 a clock per SM)
+        if (ty < M - m0 && tx < N - n0) {
+            const int kn = ke - k0 < BK ? ke - k0 : BK;
+            if (kn == BK) {
 #pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            T a[TM], b[TN];
+                for (int kk = 0; kk < BK; ++kk) {
+                    T a[TM], b[TN];
 #pragma unroll
-            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+                    for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
+                    for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
+                    for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                }
+            } else {
+                for (int kk = 0; kk < kn; ++kk) {
+                    T a[TM], b[TN];
+#pragma unroll
+                    for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+                    for (int i = 0; i < TM; ++i)
+#pragma unroll
+                        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                }
+            }
         }
         if (kComp) {
 #pragma unroll
@@ -120,13 +148,18 @@ __global__ void __launch_bounds__(NT) k_gemm_t(int M, int N, int K, double alpha
         for (int j = 0; j < TN; ++j) {
             int gn = n0 + tx + 16 * j;
             if (gn >= N) continue;
-            const double sum = kComp ? (double)chi[kComp ? i : 0][kComp ? j : 0] + (double)clo[kComp ? i : 0][kComp ? j : 0]
+            const double sum = kComp ? f32_widen(chi[kComp ? i : 0][kComp ? j : 0]) +
+                                           f32_widen(clo[kComp ? i : 0][kComp ? j : 0])
                                      : (double)acc[i][j];
             if (P) {
                 P[(((long long)sl * (gridDim.z / nsl) + bz) * M + gm) * (long long)N + gn] = sum;
                 continue;
             }
             double *c = C + (long long)gm * sCm + (long long)gn * sCn;
+            if (plain) {
+                *c = sum;
+                continue;
+            }
             double v = alpha * sum;
             if (beta != 0.0) v += beta * *c;
             *c = v;
