@@ -151,6 +151,7 @@ struct dmrg_ctx {
     int gbj_min_r = 0;           // FP32 Jacobi: Gram-block cooperative form from this many vectors on (0 = off)
     double jacobi32_tol = 1e-6;  // FP32 Jacobi: rotate while a pair's cosine exceeds this
     int mixed_svd64 = 0;         // 3xTF32 form with the FP64 SVD and split (contractions alone in reduced precision)
+    int qr_wpanel = 1;           // QR panels of <= 256 rows: one warp per column (k_qr_panel_w)
     int f64_fill = 1;            // FP64 GEMM: 32 x 32 tiles and split K when 64 x 64 tiles leave SMs idle
     int tc_presplit = 1;         // matvec: L, R split once per update; x and the mix output split by their producers
     int lz_fused = 1;            // Lanczos: one cooperative launch per step for the orthogonalisation

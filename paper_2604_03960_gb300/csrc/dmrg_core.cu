@@ -687,6 +687,11 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         ctx->jacobi32_tol = value;
         return DMRG_OK;
     }
+    if (!std::strcmp(name, "qr_wpanel")) {
+        if (!(value == 0.0 || value == 1.0)) return DMRG_EINVAL;
+        ctx->qr_wpanel = (int)value;
+        return DMRG_OK;
+    }
     if (!std::strcmp(name, "f64_fill")) {
         if (!(value == 0.0 || value == 1.0)) return DMRG_EINVAL;
         ctx->f64_fill = (int)value;

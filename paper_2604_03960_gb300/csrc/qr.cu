@@ -138,6 +138,113 @@ __global__ void __launch_bounds__(PT) k_qr_panel(float *__restrict__ X, int c, i
         for (int j = 0; j < bw; ++j) X[(long long)(k + i) * l + k + j] = P[i * kPS + j];
 }
 
+// Column ownership, for panels of at most 32 RPL rows: warp q holds panel
+// column q in registers (lane i: rows i, i + 32, ...).  At column step j
+// the owner warp alone forms the reflector from its column (norm by a warp
+// reduction), publishes it to shared memory (double-buffered) with beta, and
+// finishes its column as R's; after one block barrier each warp q > j takes
+// w_q = v . col_q by a warp reduction and updates its own column.  So a step
+// costs one barrier and two warp reductions on its critical path, where the
+// row-owning form above needs two block reductions.  Same reflectors, V and
+// T layout, so k_qr_trail applies them unchanged.
+template <int RPL>
+__global__ void __launch_bounds__(32 * kQrB) k_qr_panel_w(float *__restrict__ X, int c, int l, int k, int bw,
+                                                          float *__restrict__ V, float *__restrict__ T)
+{
+    constexpr int MR = 32 * RPL;
+    __shared__ float vbuf[2][MR];
+    __shared__ float Vs[MR][kQrB + 1];
+    __shared__ float sbeta[kQrB], G[kQrB][kQrB + 1];
+    const int rows = c - k, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float col[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+        const int i = lane + 32 * t;
+        col[t] = (i < rows && warp < bw) ? X[(long long)(k + i) * l + k + warp] : 0.f;
+    }
+    for (int e = threadIdx.x; e < MR * (kQrB + 1); e += blockDim.x) (&Vs[0][0])[e] = 0.f;
+    __syncthreads();
+    for (int j = 0; j < bw; ++j) {
+        float *vb = vbuf[j & 1];
+        if (warp == j) {
+            float a = 0.f;
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) {
+                const int i = lane + 32 * t;
+                if (i >= j && i < rows) a = fmaf(col[t], col[t], a);
+            }
+            a = wsumf(a);
+            const float x0 = __shfl_sync(0xffffffffu, col[0], j);   // row j < 16 sits in lane j, t = 0
+            const float nrm = sqrtf(a);
+            float beta = 0.f, v0 = 1.f, alpha = x0;
+            if (rows - j > 1 && nrm > 0.f && a > x0 * x0) {
+                alpha = x0 >= 0.f ? -nrm : nrm;
+                v0 = x0 - alpha;
+                beta = -1.f / (alpha * v0);               // 2 / (v^T v)
+            }
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) {
+                const int i = lane + 32 * t;
+                const float vi = (i < j || i >= rows) ? 0.f : (i == j ? v0 : col[t]);
+                vb[i] = vi;
+                Vs[i][j] = vi;
+                if (i == j) col[t] = alpha;
+                else if (i > j) col[t] = 0.f;
+            }
+            if (lane == 0) sbeta[j] = beta;
+        }
+        __syncthreads();
+        if (warp > j && warp < bw) {
+            const float beta = sbeta[j];
+            if (beta != 0.f) {
+                float w = 0.f;
+#pragma unroll
+                for (int t = 0; t < RPL; ++t) w = fmaf(vb[lane + 32 * t], col[t], w);
+                w = wsumf(w);
+#pragma unroll
+                for (int t = 0; t < RPL; ++t) col[t] -= beta * vb[lane + 32 * t] * w;
+            }
+        }
+    }
+    __syncthreads();
+    // compact WY: G = V^T V over the panel rows, then T column by column
+    for (int pq = warp; pq < bw * bw; pq += kQrB) {
+        const int p = pq / bw, q = pq % bw;
+        if (p >= q) continue;
+        float sacc = 0.f;
+        for (int i = q + lane; i < rows; i += 32) sacc = fmaf(Vs[i][p], Vs[i][q], sacc);
+        sacc = wsumf(sacc);
+        if (lane == 0) G[p][q] = sacc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        __shared__ float Ts[kQrB][kQrB + 1];
+        for (int q = 0; q < kQrB; ++q)
+            if (lane < kQrB) Ts[lane][q] = 0.f;
+        __syncwarp();
+        for (int j = 0; j < bw; ++j) {
+            if (lane < j) {
+                float sacc = 0.f;
+                for (int q = lane; q < j; ++q) sacc = fmaf(Ts[lane][q], G[q][j], sacc);
+                Ts[lane][j] = -sbeta[j] * sacc;
+            } else if (lane == j) {
+                Ts[j][j] = sbeta[j];
+            }
+            __syncwarp();
+        }
+        for (int e = lane; e < kQrB * kQrB; e += 32) T[e] = Ts[e / kQrB][e % kQrB];
+    }
+    // R's columns back to X, the reflectors to V (rows x kQrB, zero beyond bw)
+    if (warp < bw) {
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int i = lane + 32 * t;
+            if (i < rows) X[(long long)(k + i) * l + k + warp] = col[t];
+        }
+    }
+    for (int e = threadIdx.x; e < rows * kQrB; e += blockDim.x) V[e] = Vs[e / kQrB][e % kQrB];
+}
+
 // X[k:, p] <- X[k:, p] - V (T^T (V^T X[k:, p])) for the 32 columns p of this CTA
 __global__ void __launch_bounds__(kQrTrailThreads) k_qr_trail(float *__restrict__ X, int c, int l, int k, int bw,
                                                               const float *__restrict__ V, const float *__restrict__ T)
@@ -227,7 +334,11 @@ dmrg_status qr_precondition32(dmrg_ctx *ctx, float *X, int c, int l, void *work)
         const int bw = std::min(bmax, kmax - k);
         const size_t smem = (size_t)(c - k) * kPS * sizeof(float);
         const int pt = qr_panel_threads(c - k);
-        if (pt == 32)
+        if (ctx->qr_wpanel && c - k <= 128)
+            k_qr_panel_w<4><<<1, 32 * kQrB, 0, ctx->stream>>>(X, c, l, k, bw, V, T);
+        else if (ctx->qr_wpanel && c - k <= 256)
+            k_qr_panel_w<8><<<1, 32 * kQrB, 0, ctx->stream>>>(X, c, l, k, bw, V, T);
+        else if (pt == 32)
             k_qr_panel<32><<<1, 32, smem, ctx->stream>>>(X, c, l, k, bw, kPS, V, T);
         else if (pt == 128)
             k_qr_panel<128><<<1, 128, smem, ctx->stream>>>(X, c, l, k, bw, kPS, V, T);
