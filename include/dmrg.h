@@ -198,7 +198,13 @@ const char *dmrg_status_string(dmrg_status s);
  * round, inner sweeps per block pair), "bjac_gram" (1: the blocked FP32
  * Jacobi takes its inner sweep on the block pair's Gram matrix and applies
  * the accumulated rotation once; 0: rotations of the vectors themselves),
- * "jacobi_max_sweeps" (standalone
+ * "tjac" (FP32 Jacobi of the mixed form: 64 or 128 = blocked one-sided
+ * Jacobi with pairs of that many vectors, whose Gram blocks G = P P^T and
+ * block rotations P <- Q^T P are 3xTF32 tcgen05 GEMMs around one Jacobi sweep
+ * of each G in a CTA; 0 = off; default 128), "tjac_min_r" (from this many
+ * vectors on, ahead of the other FP32 kernels; default 2560; not taken
+ * while the stream is captured, since it reads a convergence counter on the
+ * host once per outer sweep), "jacobi_max_sweeps" (standalone
  * svd_truncate and svd_truncate_batched), "batched_inner" (svd_truncate_batched:
  * Jacobi sweeps on each 32 x 32 block-pair Gram matrix, 4), "batched_floor32"
  * (FP32 svd_truncate_batched: vectors with norm below this x |A|_F take no
@@ -335,11 +341,13 @@ dmrg_status svd_truncate_batched(dmrg_ctx *ctx, int prec, int batch, const int *
  * and the other kernels (with the grouped FP32 Jacobi, option "gjac32", its
  * block-pair width, 16 or 32 vectors, and groups per CTA, 1, 2 or 4; else
  * the blocked kernel's block-pair target in {24, 48, 96, 152} and 1 or 2
- * inner sweeps); the fastest applies to the (ceil log2 n, ceil log2 n)
+ * inner sweeps), and from n = 256 on the blocked Jacobi whose Gram blocks
+ * and block rotations are tcgen05 GEMMs with pairs of 64 and of 128 vectors;
+ * the fastest applies to the (ceil log2 n, ceil log2 n)
  * bucket.  Inputs are generated on the device; `reps` timed calls follow one
  * warm-up call.  These calls allocate and free device memory and
  * synchronise.  dmrg_autotune_save / _load write and read the tables as JSON
- * (format "dmrg-autotune-3"; load also reads formats 1 and 2) and load
+ * (format "dmrg-autotune-4"; load also reads formats 1 to 3) and load
  * replaces the tables; DMRG_EINVAL for a file that is missing or in none of
  * these formats.
  * dmrg_autotune_entries: number of GEMM (which = 0) or SVD (1) entries. */
@@ -464,6 +472,10 @@ dmrg_status dmrg_state_put_mps(dmrg_state *st, const double *in);
 dmrg_status dmrg_wait_selftest(dmrg_ctx *ctx, long long spin_limit, int absent);
 /* Kernels launched by this library since it was loaded (all contexts). */
 long long dmrg_launch_count(void);
+/* Outer Jacobi sweeps of the context's last standalone svd_truncate (Eq. 20):
+ * positive if the iteration converged, minus the count if it stopped at the
+ * sweep limit, 0 before the first call.  Host read only; no GPU work. */
+int dmrg_svd_last_sweeps(const dmrg_ctx *ctx);
 /* Live timing of the heavy kernels (no counterpart in the paper): with
  * profiling on, CUDA events on the context stream bracket every launch of
  * kind 0 (tensor-core GEMM), 1 (FP32 Jacobi sweeps), 2 (FP64 Jacobi sweeps),

@@ -123,6 +123,7 @@ def _declare(L):
         "dmrg_state_get_mps": (S, [_VP, _VP]),
         "dmrg_state_put_mps": (S, [_VP, _VP]),
         "dmrg_launch_count": (C.c_longlong, []),
+        "dmrg_svd_last_sweeps": (C.c_int, [_VP]),
         "dmrg_profile": (S, [_VP, _I]),
         "svd_truncate_batched": (S, [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _D, _VP,
                                      _VP, _VP, _VP]),
@@ -173,7 +174,7 @@ def exported_symbols():
         "dmrg_circ_state", "dmrg_mlp_forward",
         "dmrg_mlp_loss_grad", "dmrg_mlp_adam", "dmrg_gemm", "dmrg_set_option",
         "dmrg_state_mps_size", "dmrg_state_get_mps", "dmrg_state_put_mps", "dmrg_launch_count",
-        "dmrg_profile", "dmrg_profile_read", "svd_truncate_noalloc", "dmrg_mlp_train",
+        "dmrg_svd_last_sweeps", "dmrg_profile", "dmrg_profile_read", "svd_truncate_noalloc", "dmrg_mlp_train",
         "svd_truncate_batched", "dmrg_sweep_chains", "dmrg_wait_selftest", "dmrg_autotune_gemm", "dmrg_autotune_svd",
         "dmrg_autotune_clear", "dmrg_autotune_save", "dmrg_autotune_load", "dmrg_autotune_entries", "dmrg_graph_begin", "dmrg_graph_end", "dmrg_graph_launch", "dmrg_graph_destroy",
     ]
@@ -248,6 +249,11 @@ class Context:
         _check(lib().dmrg_profile_read(self.h, kind, C.byref(ms), C.byref(n), C.byref(fl), C.byref(by)),
                "dmrg_profile_read")
         return dict(ms=ms.value, launches=n.value, flops=fl.value, bytes=by.value)
+
+    def svd_last_sweeps(self) -> int:
+        """Outer Jacobi sweeps of this context's last svd_truncate (negative:
+        stopped at the sweep limit)."""
+        return int(lib().dmrg_svd_last_sweeps(self.h))
 
     def set_option(self, name: str, value: float):
         _check(lib().dmrg_set_option(self.h, name.encode(), float(value)), f"dmrg_set_option({name})")

@@ -75,6 +75,15 @@ int tune_lookup_cj(const dmrg_ctx *ctx, int r, int l)
     return -1;
 }
 
+int tune_lookup_tj(const dmrg_ctx *ctx, int r, int l)
+{
+    if (ctx->tune_svd.empty()) return -1;
+    const int lr = clog2(r), ll = clog2(l);
+    for (const auto &e : ctx->tune_svd)
+        if (e.lr == lr && e.ll == ll) return e.tj;
+    return -1;
+}
+
 bool tune_lookup_gjac(const dmrg_ctx *ctx, int r, int l, int *nv, int *groups)
 {
     if (ctx->tune_svd.empty()) return false;
@@ -193,11 +202,13 @@ extern "C" dmrg_status dmrg_autotune_svd(dmrg_ctx *ctx, int n_sizes, const int *
         const int saved_prec = ctx->svd_prec, saved_pairs = ctx->bjac_pairs, saved_inner = ctx->bjac_inner;
         const int saved_nv = ctx->gjac_nv, saved_groups = ctx->gjac_groups;
         const int saved_cj = ctx->cjac32, saved_fc = ctx->cjac_force_c;
+        const int saved_tj = ctx->tjac, saved_tjr = ctx->tjac_min_r;
         const auto saved_table = ctx->tune_svd;
         ctx->tune_svd.clear();   // time the candidates themselves, not an earlier decision
         ctx->svd_prec = 1;
         float best = 0.f;
-        int best_p = saved_pairs, best_i = saved_inner, best_nv = 0, best_g = 0, best_cj = 0;
+        int best_p = saved_pairs, best_i = saved_inner, best_nv = 0, best_g = 0, best_cj = 0, best_tj = 0;
+        ctx->tjac = 0;            // the candidates below without the tensor-core block form
         dmrg_status st = DMRG_OK;
         auto timed = [&](float *ms) {
             return time_ms(ctx, reps, [&]() {
@@ -260,6 +271,33 @@ extern "C" dmrg_status dmrg_autotune_svd(dmrg_ctx *ctx, int n_sizes, const int *
                     }
                 }
         }
+        // the tensor-core block form (Gram blocks and rotations on tcgen05),
+        // pairs of 64 and 128 vectors, from 256 vectors on
+        if (m >= 256 && tc_available(ctx)) {
+            ctx->cjac32 = saved_cj;
+            ctx->bjac_pairs = saved_pairs;
+            ctx->bjac_inner = saved_inner;
+            ctx->tjac_min_r = 2;
+            for (int tb : {64, 128}) {
+                if (st != DMRG_OK) break;
+                ctx->tjac = tb;
+                float ms = 0.f;
+                st = timed(&ms);
+                if (st == DMRG_OK && (best == 0.f || ms < best)) {
+                    best = ms;
+                    best_tj = tb;
+                }
+            }
+        }
+        ctx->tjac = saved_tj;
+        ctx->tjac_min_r = saved_tjr;
+        if (best_tj) {            // the other kernels' fields keep their defaults
+            best_p = saved_pairs;
+            best_i = saved_inner;
+            best_nv = 0;
+            best_g = 0;
+            best_cj = 0;
+        }
         ctx->svd_prec = saved_prec;
         ctx->bjac_pairs = saved_pairs;
         ctx->bjac_inner = saved_inner;
@@ -269,7 +307,7 @@ extern "C" dmrg_status dmrg_autotune_svd(dmrg_ctx *ctx, int n_sizes, const int *
         ctx->cjac_force_c = saved_fc;
         ctx->tune_svd = saved_table;
         if (st != DMRG_OK) return st;
-        dmrg_ctx::TuneSvd e{clog2(m), clog2(m), best_p, best_i, best, best_nv, best_g, best_cj};
+        dmrg_ctx::TuneSvd e{clog2(m), clog2(m), best_p, best_i, best, best_nv, best_g, best_cj, best_tj};
         auto it = std::find_if(ctx->tune_svd.begin(), ctx->tune_svd.end(), [&](const dmrg_ctx::TuneSvd &x) {
             return x.lr == e.lr && x.ll == e.ll;
         });
@@ -302,7 +340,7 @@ extern "C" dmrg_status dmrg_autotune_save(const dmrg_ctx *ctx, const char *path)
     std::string dev = cudaGetDeviceProperties(&prop, ctx->device) == cudaSuccess ? prop.name : "unknown";
     for (auto &ch : dev)
         if (ch == '"' || ch == '\\') ch = ' ';
-    std::fprintf(f, "{\"format\": \"dmrg-autotune-3\", \"device\": \"%s\",\n \"gemm\": [\n", dev.c_str());
+    std::fprintf(f, "{\"format\": \"dmrg-autotune-4\", \"device\": \"%s\",\n \"gemm\": [\n", dev.c_str());
     for (size_t i = 0; i < ctx->tune_gemm.size(); ++i) {
         const auto &e = ctx->tune_gemm[i];
         std::fprintf(f, "  {\"lm\": %d, \"ln\": %d, \"lk\": %d, \"bn\": %d, \"ms128\": %.6g, \"ms256\": %.6g, "
@@ -313,8 +351,9 @@ extern "C" dmrg_status dmrg_autotune_save(const dmrg_ctx *ctx, const char *path)
     for (size_t i = 0; i < ctx->tune_svd.size(); ++i) {
         const auto &e = ctx->tune_svd[i];
         std::fprintf(f, "  {\"lr\": %d, \"ll\": %d, \"pairs\": %d, \"inner\": %d, \"ms\": %.6g, \"nv\": %d, \"groups\": %d, "
-                        "\"cj\": %d}%s\n",
-                     e.lr, e.ll, e.pairs, e.inner, e.ms, e.nv, e.groups, e.cj, i + 1 < ctx->tune_svd.size() ? "," : "");
+                        "\"cj\": %d, \"tj\": %d}%s\n",
+                     e.lr, e.ll, e.pairs, e.inner, e.ms, e.nv, e.groups, e.cj, e.tj,
+                     i + 1 < ctx->tune_svd.size() ? "," : "");
     }
     std::fprintf(f, " ]}\n");
     const bool ok = std::fclose(f) == 0;
@@ -332,7 +371,7 @@ extern "C" dmrg_status dmrg_autotune_load(dmrg_ctx *ctx, const char *path)
     bool format_ok = false;
     while (std::fgets(line, sizeof line, f)) {
         if (std::strstr(line, "\"dmrg-autotune-1\"") || std::strstr(line, "\"dmrg-autotune-2\"") ||
-            std::strstr(line, "\"dmrg-autotune-3\""))
+            std::strstr(line, "\"dmrg-autotune-3\"") || std::strstr(line, "\"dmrg-autotune-4\""))
             format_ok = true;
         dmrg_ctx::TuneGemm e{};
         dmrg_ctx::TuneSvd t{};
@@ -359,6 +398,12 @@ extern "C" dmrg_status dmrg_autotune_load(dmrg_ctx *ctx, const char *path)
             }
             const char *c = std::strstr(line, "\"cj\":");
             if (c && (std::sscanf(c, "\"cj\": %d", &t.cj) != 1 || (t.cj != -1 && t.cj != 0 && t.cj != 8 && t.cj != 16))) {
+                std::fclose(f);
+                return DMRG_EINVAL;
+            }
+            // format 4 adds the tensor-core block form's pair width (absent: not chosen)
+            const char *tq = std::strstr(line, "\"tj\":");
+            if (tq && (std::sscanf(tq, "\"tj\": %d", &t.tj) != 1 || (t.tj != 0 && t.tj != 64 && t.tj != 128))) {
                 std::fclose(f);
                 return DMRG_EINVAL;
             }

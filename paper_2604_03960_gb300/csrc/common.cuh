@@ -138,10 +138,14 @@ struct dmrg_ctx {
     // the grouped kernel's vectors per block pair (nv) and groups per CTA, and
     // the cluster kernel's size (cj: 8 or 16 CTAs, 0 = not the cluster kernel,
     // -1 = no choice recorded)
-    struct TuneSvd { int lr, ll, pairs, inner; float ms; int nv, groups; int cj = -1; };
+    struct TuneSvd { int lr, ll, pairs, inner; float ms; int nv, groups; int cj = -1; int tj = 0; };
     std::vector<TuneGemm> tune_gemm;
     std::vector<TuneSvd> tune_svd;
     dmrg::DevBuf work4;          // batched SVD workspace
+    dmrg::DevBuf tjbuf;          // tensor-core block Jacobi workspace (tjacobi.cu)
+    int tjac = 128;              // FP32 Jacobi: tensor-core block form with pairs of tjac (64, 128) vectors; 0 = off
+    int tjac_min_r = 2560;       // ... from this many vectors on (ahead of the other kernels; measured faster
+                                 // than the blocked grid kernel at 4096 vectors, slower at 2048)
     int batched_inner = 4;       // batched SVD: inner Jacobi sweeps per block pair
     int batched_ns = 1;          // FP32 batched SVD: Newton-Schulz step on each block rotation
     int jacobi_qr = 1;           // FP32 Jacobi on the R factor of the vectors (QR preconditioning)
@@ -276,6 +280,9 @@ dmrg_status qr_precondition32(dmrg_ctx *ctx, float *X, int c, int l, void *work)
 // Autotuner table lookups (autotune.cu): 0 / false when the bucket has no entry.
 int tune_lookup_bn(const dmrg_ctx *ctx, int M, int N, int K, int *kb = nullptr);
 int tune_lookup_cj(const dmrg_ctx *ctx, int r, int l);
+// tensor-core block Jacobi chosen for this bucket: its pair width (64, 128);
+// 0 another kernel; -1 no entry
+int tune_lookup_tj(const dmrg_ctx *ctx, int r, int l);
 bool tune_lookup_svd(const dmrg_ctx *ctx, int r, int l, int *pairs, int *inner);
 bool tune_lookup_gjac(const dmrg_ctx *ctx, int r, int l, int *nv, int *groups);
 
@@ -320,6 +327,23 @@ dmrg_status gemm_3xtf32_pre(dmrg_ctx *ctx, int M, int N, int K, double alpha, co
                             long long sAk, long long sAb, const double *B, long long sBk, long long sBn,
                             long long sBb, double beta, double *C, long long sCm, long long sCn, long long sCb,
                             int batch, const float *Ah_pre, const float *Bh_pre);
+
+// tcgen05 product of operands the caller has split already: Ah [batch][M][K3],
+// Bh [batch][N][K3] (K-major, K3 a multiple of 32, e.g. the (hi, hi, lo) and
+// (hi, lo, hi) layouts above), tile width bn (64, 128, 256).  Exactly one of
+// C64 / C32 is given: C64[b sCb + m sCm + n sCn] = the product in FP64, the K'
+// blocks spread over nsl slices whose FP32 sums (FP64 scratch P, nsl * batch *
+// M * N doubles) are added in FP64; C32 = the FP32 accumulator itself (nsl 1).
+// seg_map != 0: the operands store fewer K segments than the product reads
+// (K3 = 3 segments of K3 / 3 each, e.g. (hi, lo) stored once per operand):
+// nibble q (q < 3) of seg_map is the stored segment A reads as K' segment q,
+// nibble 3 + q the one B reads; e.g. 0x010100 reads A as (hi, hi, lo) and B
+// as (hi, lo, hi) from (hi, lo) storage of 2 K3 / 3 floats a row.
+dmrg_status tc_gemm_split(dmrg_ctx *ctx, const float *Ah, const float *Bh, int M, int N, int K3, int batch, int bn,
+                          int nsl, double *P, double *C64, float *C32, long long sCm, long long sCn, long long sCb,
+                          unsigned seg_map = 0u);
+// Tile width (64, 128, 256) the tensor-core GEMM takes for this shape.
+int tc_pick_bn(dmrg_ctx *ctx, int M, int N, int K, int batch);
 
 // FP32 -> FP64 by integer operations (exact, like the converting
 // instruction, which runs on the narrow FP64 pipe of this part); zeros,
@@ -409,6 +433,14 @@ template <typename T>
 dmrg_status gjac_run(dmrg_ctx *ctx, T *X, int r, int l, int ldx, int gv0, int rv, int max_sweeps, double tol,
                      double small, const double *F2, unsigned *sync, int *info, const int *r_eff, int nv,
                      int max_groups);
+
+// Blocked one-sided Jacobi with tcgen05 Gram blocks and block rotations
+// (tjacobi.cu) on the r x l FP32 rows of X, in place; TB = 64 or 128 vectors
+// per block pair.  DMRG_EUNSUPPORTED without tensor cores or while the
+// stream is captured (it reads a convergence counter once per sweep).
+dmrg_status tjac_run(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps, double tol, double small,
+                     const double *F2, int *d_info, int TB);
+size_t tjac_work_bytes(dmrg_ctx *ctx, int r, int l, int TB);
 
 // FP32 one-sided Jacobi (mixed-precision form), vectors = columns (dir 0) or
 // rows (dir 1) of A; see jacobi.cu.

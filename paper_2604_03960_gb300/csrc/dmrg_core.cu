@@ -717,6 +717,16 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         ctx->cjac_min_r = (int)value;
         return DMRG_OK;
     }
+    if (!std::strcmp(name, "tjac")) {
+        if (value != 0.0 && value != 64.0 && value != 128.0) return DMRG_EINVAL;
+        ctx->tjac = (int)value;
+        return DMRG_OK;
+    }
+    if (!std::strcmp(name, "tjac_min_r")) {
+        if (!(value >= 2.0 && value <= 1e6)) return DMRG_EINVAL;
+        ctx->tjac_min_r = (int)value;
+        return DMRG_OK;
+    }
     if (!std::strcmp(name, "gjac32")) {
         if (value != 0.0 && value != 1.0 && value != 2.0) return DMRG_EINVAL;
         ctx->gjac32 = (int)value;
@@ -783,6 +793,8 @@ dmrg_status dmrg_create(dmrg_ctx **out, int device, void *cuda_stream)
         delete c;
         return DMRG_ENOMEM;
     }
+    std::memset(c->h_pinned_i, 0, 64 * sizeof(int));
+    std::memset(c->h_pinned_d, 0, 64 * sizeof(double));
     cudaEventCreate(&c->ev0);
     cudaEventCreate(&c->ev1);
     *out = c;
@@ -799,6 +811,7 @@ void dmrg_destroy(dmrg_ctx *ctx)
     ctx->tcbuf.release();
     ctx->f64buf.release();
     ctx->work4.release();
+    ctx->tjbuf.release();
     if (ctx->pinned_desc) cudaFreeHost(ctx->pinned_desc);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_pinned_i) cudaFreeHost(ctx->h_pinned_i);
@@ -1404,6 +1417,8 @@ dmrg_status dmrg_state_put_mps(dmrg_state *st, const double *in)
 }
 
 long long dmrg_launch_count(void) { return g_launch_count.load(); }
+
+int dmrg_svd_last_sweeps(const dmrg_ctx *ctx) { return ctx ? ctx->h_pinned_i[32] : 0; }
 
 }  // extern "C"
 

@@ -135,7 +135,8 @@ template <int BN>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int nk,
               int kps, int nsl, double *__restrict__ P, double alpha, double beta, double *__restrict__ C,
-              long long sCm, long long sCn, long long sCb, int *status)
+              long long sCm, long long sCn, long long sCb, int *status, float *__restrict__ C32, int kseg,
+              unsigned kmap)
 {
     using Cfg = TcCfg<BN>;
     extern __shared__ uint8_t smem_raw[];
@@ -192,8 +193,16 @@ __global__ void __launch_bounds__(128, 1)
             }
             mbar_expect_tx(full(s), Cfg::STAGE);
             const uint32_t a_dst = base + s * Cfg::STAGE;
-            tma_load_3d(a_dst, &tmA, full(s), (kb0 + kb) * TBK, m0, bz);
-            tma_load_3d(a_dst + Cfg::A_BYTES, &tmB, full(s), (kb0 + kb) * TBK, n0, bz);
+            int ka = kb0 + kb, kbb = ka;
+            if (kseg > 0) {
+                // K' segment q (kseg blocks) of A reads stored segment nibble q of
+                // kmap, that of B nibble q of kmap >> 16
+                const int q = ka / kseg, w = ka - q * kseg;
+                ka = (int)((kmap >> (4 * q)) & 15u) * kseg + w;
+                kbb = (int)((kmap >> (16 + 4 * q)) & 15u) * kseg + w;
+            }
+            tma_load_3d(a_dst, &tmA, full(s), ka * TBK, m0, bz);
+            tma_load_3d(a_dst + Cfg::A_BYTES, &tmB, full(s), kbb * TBK, n0, bz);
             issued = kb + 1;
         }
         *issued_s = issued;
@@ -251,6 +260,11 @@ __global__ void __launch_bounds__(128, 1)
                 for (int rr = 0; rr < 32; ++rr) {
                     const int gm = m0 + warp * 32 + rr;
                     if (gm >= M) break;
+                    if (C32) {
+                        // FP32 result as accumulated (alpha = 1, beta = 0)
+                        C32[(long long)bz * sCb + (long long)gm * sCm + (long long)gn * sCn] = tile[rr * 33 + lane];
+                        continue;
+                    }
                     const double x = f32_widen(tile[rr * 33 + lane]);
                     if (P) {
                         P[(((long long)sl * nbatch + bz) * M + gm) * (long long)N + gn] = x;
@@ -372,12 +386,22 @@ bool make_map(CUtensorMap *map, const float *base, int K3, int rows, int batch, 
     return r == CUDA_SUCCESS;
 }
 
+// largest stored segment index in a 3-entry nibble map
+inline unsigned kmap_max(unsigned m)
+{
+    unsigned a = m & 15u, b = (m >> 4) & 15u, c = (m >> 8) & 15u;
+    return a > b ? (a > c ? a : c) : (b > c ? b : c);
+}
+
 template <int BN>
 dmrg_status launch_tc(dmrg_ctx *ctx, const float *Ah, const float *Bh, int M, int N, int K3, int batch, double alpha,
-                      double beta, double *C, long long sCm, long long sCn, long long sCb, int nsl, double *P)
+                      double beta, double *C, long long sCm, long long sCn, long long sCb, int nsl, double *P,
+                      float *C32 = nullptr, int kseg = 0, unsigned kmap = 0u)
 {
     CUtensorMap ma, mb;
-    if (!make_map(&ma, Ah, K3, M, batch, TBM) || !make_map(&mb, Bh, K3, N, batch, BN)) return DMRG_ECUDA;
+    // stored K extent: the three K' segments, or the distinct stored ones
+    const int Ks = kseg > 0 ? kseg * TBK * (int)(1 + max(kmap_max(kmap & 0xffffu), kmap_max(kmap >> 16))) : K3;
+    if (!make_map(&ma, Ah, Ks, M, batch, TBM) || !make_map(&mb, Bh, Ks, N, batch, BN)) return DMRG_ECUDA;
     static bool attr_set = false;
     if (!attr_set) {
         DMRG_CUDA(cudaFuncSetAttribute(k_tc_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN>::SMEM));
@@ -388,7 +412,8 @@ dmrg_status launch_tc(dmrg_ctx *ctx, const float *Ah, const float *Bh, int M, in
     dim3 grid((N + BN - 1) / BN, (M + TBM - 1) / TBM, batch * nsl);
     prof_mark(ctx, PROF_TC_GEMM);
     k_tc_gemm<BN><<<grid, 128, TcCfg<BN>::SMEM, ctx->stream>>>(ma, mb, M, N, nk, kps, nsl, nsl > 1 ? P : nullptr,
-                                                               alpha, beta, C, sCm, sCn, sCb, ctx->d_status);
+                                                               alpha, beta, C, sCm, sCn, sCb, ctx->d_status,
+                                                               C32, kseg, kmap);
     DMRG_COUNT_LAUNCH();
     if (nsl > 1) {
         const long long total = (long long)M * N * batch;
@@ -401,12 +426,45 @@ dmrg_status launch_tc(dmrg_ctx *ctx, const float *Ah, const float *Bh, int M, in
     // work of the split product: three TF32 products of the padded shape;
     // bytes: both split operands read once and the FP64 result written once
     prof_count(ctx, PROF_TC_GEMM, 2.0 * M * N * (double)K3 * batch,
-               4.0 * (double)(M + N) * K3 * batch + 8.0 * (double)M * N * batch);
+               4.0 * (double)(M + N) * K3 * batch + (C32 ? 4.0 : 8.0) * (double)M * N * batch);
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }
 
 }  // namespace
+
+dmrg_status tc_gemm_split(dmrg_ctx *ctx, const float *Ah, const float *Bh, int M, int N, int K3, int batch, int bn,
+                          int nsl, double *P, double *C64, float *C32, long long sCm, long long sCn, long long sCb,
+                          unsigned seg_map)
+{
+    if (M <= 0 || N <= 0 || batch <= 0) return DMRG_OK;
+    if (!tc_available(ctx)) return DMRG_EUNSUPPORTED;
+    if (K3 <= 0 || K3 % (3 * TBK) || (!C64 == !C32) || (C32 && nsl != 1) || (nsl > 1 && !P) || nsl < 1 ||
+        (long long)batch * nsl > 65535 || (M + TBM - 1) / TBM > 65535)
+        return DMRG_EINVAL;
+    // segment map: nibble q (A) and 4 + q (B) name the stored segment of K' segment q
+    int kseg = 0;
+    unsigned kmap = 0u;
+    if (seg_map) {
+        for (int q = 0; q < 6; ++q)
+            if (((seg_map >> (4 * q)) & 15u) > 2u) return DMRG_EINVAL;
+        kseg = K3 / (3 * TBK);
+        kmap = (seg_map & 0xfffu) | ((seg_map >> 12) & 0xfffu) << 16;
+    }
+    {
+        // no empty slice (its partial sums would never be written)
+        const int nk = K3 / TBK;
+        if (nsl > nk) nsl = nk;
+        const int kps = (nk + nsl - 1) / nsl;
+        nsl = (nk + kps - 1) / kps;
+    }
+    switch (bn) {
+    case 64: return launch_tc<64>(ctx, Ah, Bh, M, N, K3, batch, 1.0, 0.0, C64, sCm, sCn, sCb, nsl, P, C32, kseg, kmap);
+    case 128: return launch_tc<128>(ctx, Ah, Bh, M, N, K3, batch, 1.0, 0.0, C64, sCm, sCn, sCb, nsl, P, C32, kseg, kmap);
+    case 256: return launch_tc<256>(ctx, Ah, Bh, M, N, K3, batch, 1.0, 0.0, C64, sCm, sCn, sCb, nsl, P, C32, kseg, kmap);
+    default: return DMRG_EINVAL;
+    }
+}
 
 bool tc_available(dmrg_ctx *ctx)
 {

@@ -1252,10 +1252,19 @@ dmrg_status svd_jacobi32(dmrg_ctx *ctx, const double *A, int m, int n, int dir, 
     // a 128 x 128 two-site tensor where the grouped one takes 3.85 ms, and
     // the blocked kernel is 1.2-2x faster at the bulk sizes
     bool done = false;
+    // blocked form with tcgen05 Gram blocks and block rotations (tjacobi.cu):
+    // an autotuned bucket's choice, else by size
+    const int tj = tune_lookup_tj(ctx, r, l);
+    const int tb = tj > 0 ? tj : (tj < 0 && ctx->tjac && r >= ctx->tjac_min_r ? ctx->tjac : 0);
+    if (tb) {
+        dmrg_status e = tjac_run(ctx, X, r, l, max_sweeps, tol, small, F2, d_info, tb);
+        if (e == DMRG_OK) done = true;
+        else if (e != DMRG_EUNSUPPORTED) return e;
+    }
     // an autotuned bucket may pick the cluster size (8, 16) or another kernel (0)
     const int cj = (ctx->cjac32 && ctx->cjac_force_c == 0) ? tune_lookup_cj(ctx, r, l) : -1;
     const int force_c = ctx->cjac_force_c ? ctx->cjac_force_c : (cj > 0 ? cj : 0);
-    if (ctx->cjac32 && cj != 0 && r >= ctx->cjac_min_r &&
+    if (!done && ctx->cjac32 && cj != 0 && r >= ctx->cjac_min_r &&
         (force_c ? cjac32_fits_c(r, l, force_c) : cjac32_fits(r, l))) {
         // one thread-block cluster: blocks of vectors in the CTAs' shared
         // memory, moved between them through distributed shared memory

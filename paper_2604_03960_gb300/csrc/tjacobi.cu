@@ -1,0 +1,458 @@
+// tjacobi.cu -- blocked one-sided Jacobi (Eq. 20) whose Gram blocks and block
+// rotations are tcgen05 GEMMs.
+//
+// The r vectors being orthogonalised (rows of X, length l, FP32) are grouped
+// in nb blocks of b = TB / 2 vectors.  One round of an outer sweep pairs
+// neighbouring block slots; for each pair p, with its 2b vectors stacked as
+// the rows of P_p (2b x l):
+//   1. the Gram block G_p = P_p P_p^T, a 3xTF32 tcgen05 product batched over
+//      the round's pairs (K = l, split over several FP32 accumulators whose
+//      partial sums meet in FP64);
+//   2. one cyclic Jacobi sweep on G_p in one CTA (FP32, shared memory): the
+//      Schur rotation of every pair (i, j) of the 2b vectors whose cosine
+//      g_ij / sqrt(g_ii g_jj) exceeds the tolerance, applied to G_p from
+//      both sides and accumulated in Q_p; then one Newton-Schulz step makes
+//      Q_p orthogonal to FP32 rounding;
+//   3. the block rotation P_p <- Q_p^T P_p, a second 3xTF32 tcgen05 product
+//      (M = 2b, N = l, K = 2b), written back in place in FP32.
+// Block slots are paired in odd-even order: even rounds pair slots (0, 1),
+// (2, 3), ..., odd rounds (1, 2), (3, 4), ..., and the two blocks of a pair
+// change slots after their rotation (folded into the row order of Q_p^T).
+// After nb rounds every pair of blocks has met exactly once and the block
+// order is reversed, so the final slot of every block follows from the
+// number of sweeps.  The iteration stops after an outer sweep without any
+// rotation (the host reads one counter per sweep).
+//
+// Work per round: two HBM passes over the vectors (the split operands of
+// both products are written by one kernel), the Gram product (4 b^2 l
+// multiply-adds per pair, times three for the split), the in-CTA sweep and
+// the rotation product (the same count).
+#include "common.cuh"
+
+namespace dmrg {
+namespace {
+
+constexpr int kTjMaxSweeps = 64;
+// Both products read (hi, lo) storage as A = (hi, hi, lo) and B = (hi, lo, hi).
+constexpr unsigned kSegAB = 0x010100u;
+
+// Circle-method pairing of np (even) indices: step t in [0, np - 1), pair p
+// in [0, np / 2).
+__device__ __forceinline__ void tj_circle(int np, int t, int p, int &i, int &j)
+{
+    const int q = np - 1;
+    if (p == 0) {
+        i = q;
+        j = t;
+    } else {
+        i = (t + p) % q;
+        j = (t - p + q) % q;
+    }
+}
+
+__device__ __forceinline__ void tf32_split_f(float v, float &hi, float &lo)
+{
+    hi = tf32_rna(v);
+    lo = tf32_rna(v - hi);   // exact subtraction
+}
+
+// Vectors of X (rows < r) into the padded slot array; the block of slot s is
+// block s at the start.
+__global__ void k_tj_load(const float *__restrict__ X, long long n_real, long long n_all, float *__restrict__ Xp)
+{
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_all;
+         e += (long long)gridDim.x * blockDim.x)
+        Xp[e] = e < n_real ? X[e] : 0.f;
+}
+
+// Back to the rows the vectors came from: block B sits in slot nb - 1 - B
+// after an odd number of sweeps, in slot B after an even number.
+__global__ void k_tj_store(const float *__restrict__ Xp, int r, int l, int b, int nb, int flipped,
+                           float *__restrict__ X)
+{
+    const long long n = (long long)r * l;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / l), c = (int)(e - (long long)i * l);
+        const int B = i / b, slot = flipped ? nb - 1 - B : B;
+        X[e] = Xp[((long long)slot * b + (i - B * b)) * l + c];
+    }
+}
+
+// Split operands of one round, each value stored once as (hi, lo) TF32
+// parts; the products read them as (hi, hi, lo) x (hi, lo, hi) through their
+// segment maps.  Xr: the rows of the round's pairs (pair p = rows [p TB,
+// (p + 1) TB)), l floats each.  Writes
+//   GA[p][m][2 Lp] = (hi, lo) of row m (zero for l <= c < Lp): both operands
+//     of the Gram product;
+//   XB[p][n][2 TB] = (hi, lo) of element n of row k, at k: the right operand
+//     of the rotation (K = the pair's rows), transposed through shared memory.
+// Grid (Lp / 32, npairs TB / 32), block (32, 8).
+__global__ void k_tj_split(const float *__restrict__ Xr, int l, int Lp, int TB, float *__restrict__ GA,
+                           float *__restrict__ XB)
+{
+    __shared__ float hs[32][33], ls[32][33];
+    const int c0 = blockIdx.x * 32, R0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const long long K2 = 2LL * Lp;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int rr = ty + 8 * i, c = c0 + tx;
+        const long long R = R0 + rr;
+        const float v = c < l ? Xr[R * l + c] : 0.f;
+        float h, lo;
+        tf32_split_f(v, h, lo);
+        hs[rr][tx] = h;
+        ls[rr][tx] = lo;
+        float *ga = GA + R * K2 + c;
+        ga[0] = h;
+        ga[Lp] = lo;
+    }
+    __syncthreads();
+    const int p = R0 / TB, k0 = R0 - p * TB;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int cc = ty + 8 * i, n = c0 + cc;
+        if (n >= l) continue;
+        float *o = XB + ((long long)p * l + n) * (2LL * TB) + k0 + tx;
+        o[0] = hs[tx][cc];
+        o[TB] = ls[tx][cc];
+    }
+}
+
+// Rotation of one pair of a step, packed for one 16-byte shared load:
+// x = index a, y = index b (as int bits), z = c, w = s (s = 0: no rotation).
+struct __align__(16) TjRot {
+    int a, b;
+    float c, s;
+};
+
+// One Jacobi sweep on the Gram block of pair blockIdx.x, the Newton-Schulz
+// step, and the split left operand of the rotation:
+//   QA[p][m][2 TB] = (hi, lo) of Q[k][(m + TB / 2) % TB] at k,
+// so that row m of the rotated pair is column (m + TB / 2) % TB of Q applied
+// to the pair's vectors (the two blocks change slots).
+// cross = 0: every pair of the 2b vectors (circle method, 2b - 1 steps);
+// cross = 1: the b^2 pairs between the two blocks only (b steps of pairs
+//   (i, b + (i + s) mod b)), the pairs inside a block having had their turn
+//   in the sweep's first round.
+// cnt: rotations of the outer sweep (atomic).  Shared memory: G, Q and a work
+// matrix of TB x (TB + 1) floats, and the step's rotations.  NT = TB^2 / 16
+// threads (4 x 4 outputs each in the Newton-Schulz products).
+template <int TB>
+__global__ void __launch_bounds__(TB *TB / 16) k_tj_eig(const double *__restrict__ G, float tol,
+                                                       const double *__restrict__ F2, double small,
+                                                       float *__restrict__ QA, unsigned *__restrict__ cnt, int cross)
+{
+    constexpr int H = TB / 2, LD = TB + 1, NT = TB * TB / 16, T4 = TB / 4;
+    constexpr int NG = H / 2 * (H + 1);   // upper 2 x 2 blocks (with the diagonal) of the step's pairs
+    extern __shared__ __align__(16) float tj_sm[];
+    float *const g = tj_sm;
+    float *const q = g + TB * LD;
+    float *const w = q + TB * LD;
+    TjRot *const rot = reinterpret_cast<TjRot *>(w + TB * LD + ((TB * LD * 3) & 3 ? 4 - ((TB * LD * 3) & 3) : 0));
+    float2 *const dg = reinterpret_cast<float2 *>(rot + H);
+    __shared__ unsigned nrot;
+    const int tid = threadIdx.x;
+    const double *Gp = G + (long long)blockIdx.x * TB * TB;
+    for (int e = tid; e < TB * TB; e += NT) {
+        const int i = e / TB, j = e - i * TB;
+        const int a = i < j ? i : j, bb = i < j ? j : i;
+        g[i * LD + j] = f64_narrow(Gp[a * TB + bb]);   // the upper triangle, mirrored
+        q[i * LD + j] = i == j ? 1.f : 0.f;
+    }
+    if (tid == 0) nrot = 0u;
+    const float floor2 = (float)(small * small * F2[0]);
+    __syncthreads();
+    unsigned my = 0u;
+    const int steps = cross ? H : TB - 1;
+    for (int t = 0; t < steps; ++t) {
+        if (tid < H) {
+            int i, j;
+            if (cross) {
+                i = tid;
+                j = H + (tid + t) % H;
+            } else {
+                tj_circle(TB, t, tid, i, j);
+            }
+            const int a = i < j ? i : j, bb = i < j ? j : i;
+            const float ga = g[a * LD + a], gb = g[bb * LD + bb], gab = g[a * LD + bb];
+            TjRot r{a, bb, 1.f, 0.f};
+            float na = ga, nb = gb;
+            if (ga > floor2 && gb > floor2 && fabsf(gab) * rsqrtf(ga) * rsqrtf(gb) > tol) {
+                // Schur rotation zeroing g_ab: x_a' = c x_a - s x_b, x_b' = s x_a + c x_b
+                const float zeta = __fdividef(gb - ga, 2.0f * gab);
+                const float az = fabsf(zeta);
+                float tt;
+                if (az > 1e15f) {
+                    tt = __fdividef(0.5f, az);
+                } else {
+                    const float qq = fmaf(zeta, zeta, 1.0f);
+                    tt = __fdividef(1.0f, az + qq * rsqrtf(qq));
+                }
+                tt = copysignf(tt, zeta);
+                r.c = rsqrtf(fmaf(tt, tt, 1.0f));
+                r.s = r.c * tt;
+                na = ga - tt * gab;
+                nb = gb + tt * gab;
+                ++my;
+            }
+            rot[tid] = r;
+            dg[tid] = make_float2(na, nb);
+        }
+        __syncthreads();
+        // G <- R^T G R on the 2 x 2 blocks of the step's disjoint pairs: the
+        // blocks partition G, so each is read and written by one thread.  The
+        // upper blocks (k1 <= k2) are enumerated as H / 2 double rows: row d
+        // (k2 = d .. H - 1) followed by row H - 1 - d (k2 = H - 1 - d .. H - 1)
+#pragma unroll 2
+        for (int e = tid; e < NG; e += NT) {
+            const int d = e / (H + 1), jj = e - d * (H + 1);
+            int k1, k2;
+            if (jj < H - d) {
+                k1 = d;
+                k2 = d + jj;
+            } else {
+                k1 = H - 1 - d;
+                k2 = k1 + (jj - (H - d));
+            }
+            const TjRot r1 = rot[k1], r2 = rot[k2];
+            if (r1.s == 0.f && r2.s == 0.f) continue;
+            if (k1 == k2) {
+                const float2 nd = dg[k1];
+                g[r1.a * LD + r1.a] = nd.x;
+                g[r1.b * LD + r1.b] = nd.y;
+                g[r1.a * LD + r1.b] = 0.f;
+                g[r1.b * LD + r1.a] = 0.f;
+                continue;
+            }
+            const float x00 = g[r1.a * LD + r2.a], x01 = g[r1.a * LD + r2.b];
+            const float x10 = g[r1.b * LD + r2.a], x11 = g[r1.b * LD + r2.b];
+            const float h00 = fmaf(r2.c, x00, -r2.s * x01), h01 = fmaf(r2.s, x00, r2.c * x01);
+            const float h10 = fmaf(r2.c, x10, -r2.s * x11), h11 = fmaf(r2.s, x10, r2.c * x11);
+            const float n00 = fmaf(r1.c, h00, -r1.s * h10), n01 = fmaf(r1.c, h01, -r1.s * h11);
+            const float n10 = fmaf(r1.s, h00, r1.c * h10), n11 = fmaf(r1.s, h01, r1.c * h11);
+            g[r1.a * LD + r2.a] = n00;
+            g[r1.a * LD + r2.b] = n01;
+            g[r1.b * LD + r2.a] = n10;
+            g[r1.b * LD + r2.b] = n11;
+            g[r2.a * LD + r1.a] = n00;
+            g[r2.b * LD + r1.a] = n01;
+            g[r2.a * LD + r1.b] = n10;
+            g[r2.b * LD + r1.b] = n11;
+        }
+        // Q <- Q R: thread (i, k) with i fastest, so a warp reads one rotation
+#pragma unroll 4
+        for (int e = tid; e < TB * H; e += NT) {
+            const int k = e / TB, i = e - k * TB;
+            const TjRot r = rot[k];
+            if (r.s == 0.f) continue;
+            const float qa = q[i * LD + r.a], qb = q[i * LD + r.b];
+            q[i * LD + r.a] = fmaf(r.c, qa, -r.s * qb);
+            q[i * LD + r.b] = fmaf(r.s, qa, r.c * qb);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my += __shfl_xor_sync(0xffffffffu, my, o);
+    if ((tid & 31) == 0 && my) atomicAdd(&nrot, my);
+    __syncthreads();
+    const unsigned tot = nrot;
+    if (tid == 0 && tot) atomicAdd(cnt, tot);
+    const float *Qf = q;
+    if (tot) {
+        // Newton-Schulz: W = Q^T Q, then Q' = 1.5 Q - 0.5 Q W (into g); thread
+        // (ty, tx) owns rows ty + T4 u and columns tx + T4 v, u, v < 4
+        const int tx = tid % T4, ty = tid / T4;
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+        for (int i = 0; i < TB; ++i) {
+            float x[4], y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = q[i * LD + ty + T4 * u];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) y[v] = q[i * LD + tx + T4 * v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) w[(ty + T4 * u) * LD + tx + T4 * v] = acc[u][v];
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+        for (int a = 0; a < TB; ++a) {
+            float x[4], y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = q[(ty + T4 * u) * LD + a];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) y[v] = w[a * LD + tx + T4 * v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int i = ty + T4 * u, j = tx + T4 * v;
+                g[i * LD + j] = fmaf(1.5f, q[i * LD + j], -0.5f * acc[u][v]);
+            }
+        __syncthreads();
+        Qf = g;
+    }
+    float *qa = QA + (long long)blockIdx.x * TB * (2 * TB);
+    for (int e = tid; e < TB * TB; e += NT) {
+        const int m = e / TB, k = e - m * TB;
+        float h, lo;
+        tf32_split_f(Qf[k * LD + ((m + H) % TB)], h, lo);
+        float *o = qa + (long long)m * (2 * TB) + k;
+        o[0] = h;
+        o[TB] = lo;
+    }
+}
+
+__global__ void k_tj_info(int *info, int val, int *status, int noconv)
+{
+    info[0] = val;
+    if (noconv) atomicOr(status, ST_NOCONV);
+}
+
+template <int TB>
+constexpr size_t tj_eig_smem()
+{
+    // G, Q, W; padding to 16 bytes; the rotations and the updated diagonals
+    return sizeof(float) * (3ull * TB * (TB + 1) + 4) + sizeof(TjRot) * (TB / 2) + sizeof(float2) * (TB / 2);
+}
+
+struct TjLayout {
+    int b, nb, rp, Lp, P0, nsl;
+    size_t off_ga, off_xb, off_gs, off_g, off_qa, off_cnt, total;
+};
+
+TjLayout tj_layout(dmrg_ctx *ctx, int r, int l, int TB)
+{
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    TjLayout L;
+    L.b = TB / 2;
+    L.nb = (r + L.b - 1) / L.b;
+    if (L.nb & 1) ++L.nb;
+    if (L.nb < 2) L.nb = 2;
+    L.rp = L.nb * L.b;
+    L.Lp = split_kp(l);
+    L.P0 = L.nb / 2;
+    const int nk = 3 * L.Lp / 32, kb = ctx->tc_split_kb > 0 ? ctx->tc_split_kb : nk;
+    L.nsl = (nk + kb - 1) / kb;
+    if (L.nsl > 16) L.nsl = 16;
+    if (L.nsl < 1) L.nsl = 1;
+    const size_t xp = al(sizeof(float) * (size_t)L.rp * l);
+    const size_t ga = al(sizeof(float) * (size_t)L.P0 * TB * 2 * L.Lp);
+    const size_t xb = al(sizeof(float) * (size_t)L.P0 * l * 2 * TB);
+    const size_t gs = L.nsl > 1 ? al(sizeof(double) * (size_t)L.nsl * L.P0 * TB * TB) : 0;
+    const size_t gg = al(sizeof(double) * (size_t)L.P0 * TB * TB);
+    const size_t qa = al(sizeof(float) * (size_t)L.P0 * TB * 2 * TB);
+    L.off_ga = xp;
+    L.off_xb = xp + ga;
+    L.off_gs = L.off_xb + xb;
+    L.off_g = L.off_gs + gs;
+    L.off_qa = L.off_g + gg;
+    L.off_cnt = L.off_qa + qa;
+    L.total = L.off_cnt + al(sizeof(unsigned) * kTjMaxSweeps);
+    return L;
+}
+
+template <int TB>
+dmrg_status tj_sweeps(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps, double tol, double small,
+                      const double *F2, int *d_info)
+{
+    const TjLayout L = tj_layout(ctx, r, l, TB);
+    DMRG_TRY(ctx->tjbuf.ensure(L.total));
+    char *base = ctx->tjbuf.as<char>();
+    float *Xp = reinterpret_cast<float *>(base);
+    float *GA = reinterpret_cast<float *>(base + L.off_ga);
+    float *XB = reinterpret_cast<float *>(base + L.off_xb);
+    double *Gs = L.nsl > 1 ? reinterpret_cast<double *>(base + L.off_gs) : nullptr;
+    double *Gm = reinterpret_cast<double *>(base + L.off_g);
+    float *QA = reinterpret_cast<float *>(base + L.off_qa);
+    unsigned *cnt = reinterpret_cast<unsigned *>(base + L.off_cnt);
+    cudaStream_t st = ctx->stream;
+    static bool attr = false;
+    if (!attr) {
+        DMRG_CUDA(cudaFuncSetAttribute(k_tj_eig<TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tj_eig_smem<TB>()));
+        attr = true;
+    }
+    const int blocks = ctx->num_sms * 4;
+    k_tj_load<<<blocks, 256, 0, st>>>(X, (long long)r * l, (long long)L.rp * l, Xp); DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * kTjMaxSweeps, st));
+    const int sweeps_max = max_sweeps < kTjMaxSweeps ? max_sweeps : kTjMaxSweeps;
+    const int bn_rot = tc_pick_bn(ctx, TB, l, TB, L.P0);
+    const float tf = (float)tol;
+    int sweeps = 0;
+    bool converged = false;
+    for (int s = 0; s < sweeps_max && !converged; ++s) {
+        for (int rnd = 0; rnd < L.nb; ++rnd) {
+            const int par = rnd & 1;
+            const int P = par ? L.P0 - 1 : L.P0;
+            if (P <= 0) continue;
+            float *Xr = Xp + (long long)par * L.b * l;
+            k_tj_split<<<dim3(L.Lp / 32, P * TB / 32), dim3(32, 8), 0, st>>>(Xr, l, L.Lp, TB, GA, XB);
+            DMRG_COUNT_LAUNCH();
+            DMRG_CUDA(cudaGetLastError());
+            DMRG_TRY(tc_gemm_split(ctx, GA, GA, TB, TB, 3 * L.Lp, P, TB, L.nsl, Gs, Gm, nullptr, TB, 1,
+                                   (long long)TB * TB, kSegAB));
+            k_tj_eig<TB><<<P, TB * TB / 16, tj_eig_smem<TB>(), st>>>(Gm, tf, F2, small, QA, cnt + s,
+                                                                       rnd > 0 ? 1 : 0);
+            DMRG_COUNT_LAUNCH();
+            DMRG_CUDA(cudaGetLastError());
+            DMRG_TRY(tc_gemm_split(ctx, QA, XB, TB, l, 3 * TB, P, bn_rot, 1, nullptr, nullptr, Xr, l, 1,
+                                   (long long)TB * l, kSegAB));
+        }
+        sweeps = s + 1;
+        unsigned h = 1u;
+        DMRG_CUDA(cudaMemcpyAsync(&h, cnt + s, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        DMRG_CUDA(cudaStreamSynchronize(st));
+        converged = h == 0u;
+    }
+    k_tj_store<<<blocks, 256, 0, st>>>(Xp, r, l, L.b, L.nb, sweeps & 1, X); DMRG_COUNT_LAUNCH();
+    k_tj_info<<<1, 1, 0, st>>>(d_info, converged ? sweeps : -sweeps, ctx->d_status, converged ? 0 : 1);
+    DMRG_COUNT_LAUNCH();
+    DMRG_CUDA(cudaGetLastError());
+    return DMRG_OK;
+}
+
+}  // namespace
+
+size_t tjac_work_bytes(dmrg_ctx *ctx, int r, int l, int TB) { return tj_layout(ctx, r, l, TB).total; }
+
+// X: r x l row-major FP32 (device), rotated in place.  TB = 64 or 128 (the
+// pair width 2b).  Synchronises the stream once per outer sweep, so it is
+// not taken while the stream is being captured (DMRG_EUNSUPPORTED).
+dmrg_status tjac_run(dmrg_ctx *ctx, float *X, int r, int l, int max_sweeps, double tol, double small,
+                     const double *F2, int *d_info, int TB)
+{
+    if (r < 2 || l < 1 || max_sweeps < 1) return DMRG_EINVAL;
+    if (!tc_available(ctx)) return DMRG_EUNSUPPORTED;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    DMRG_CUDA(cudaStreamIsCapturing(ctx->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return DMRG_EUNSUPPORTED;
+    // the products' launches are part of this kernel's time in the live profile
+    const int saved_mask = ctx->prof_mask;
+    ctx->prof_mask &= ~(1 << PROF_TC_GEMM);
+    dmrg_status e = DMRG_EINVAL;
+    if (TB == 128) e = tj_sweeps<128>(ctx, X, r, l, max_sweeps, tol, small, F2, d_info);
+    else if (TB == 64) e = tj_sweeps<64>(ctx, X, r, l, max_sweeps, tol, small, F2, d_info);
+    ctx->prof_mask = saved_mask;
+    return e;
+}
+
+}  // namespace dmrg

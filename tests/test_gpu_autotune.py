@@ -37,7 +37,7 @@ def test_gemm_tuning_roundtrip_and_bits(G, tmp_path):
     path = str(tmp_path / "tune.json")
     ctx.autotune_save(path)
     doc = json.load(open(path))
-    assert doc["format"] == "dmrg-autotune-3" and len(doc["gemm"]) == 2
+    assert doc["format"] == "dmrg-autotune-4" and len(doc["gemm"]) == 2
     for e in doc["gemm"]:
         assert e["bn"] in (64, 128, 256) and e["kb"] in (4, 8)
         assert e["ms64"] > 0 and e["ms128"] > 0 and e["ms256"] > 0
@@ -78,11 +78,13 @@ def test_svd_tuning_keeps_accuracy(G, tmp_path):
     ctx.autotune_save(path)
     small, big = json.load(open(path))["svd"]
     # n = 200: the cluster kernel (8 or 16 CTAs) or the grouped kernel;
-    # n = 600: beyond a cluster's length limit, the blocked kernel
-    assert small["cj"] in (0, 8, 16)
+    # n = 600: beyond a cluster's length limit, the blocked kernel or the
+    # tensor-core block form (pairs of 64 or 128 vectors)
+    assert small["cj"] in (0, 8, 16) and small["tj"] == 0
     if small["cj"] == 0:
         assert small["nv"] in (16, 32) and small["groups"] in (1, 2, 4)
     assert big["cj"] == 0 and big["nv"] == 0 and big["pairs"] in (24, 48, 96, 152) and big["inner"] in (1, 2)
+    assert big["tj"] in (0, 64, 128)
     ctx.autotune_load(path)
     assert ctx.autotune_entries()[1] == 2
     ctx.set_option("svd_prec", 1)
