@@ -178,7 +178,8 @@ const char *dmrg_status_string(dmrg_status s);
  * product splits its operands), "lz_fused" (1, default: one cooperative
  * launch per Lanczos step for both Gram-Schmidt passes; 0: five launches),
  * "f64_fill" (1, default: FP64 GEMMs that would leave SMs idle take 32 x 32
- * tiles and split K), "gjac32" (grouped block
+ * tiles and split K), "f32_fill" (1, default: the same for the FP32
+ * small products of the mixed form), "gjac32" (grouped block
  * FP32 Jacobi: 0 never (default),
  * 1 for problems that fit one CTA's shared memory, 2 always), "gjac_nv" / "gjac_groups" (its vectors per block pair, 16 or
  * 32, and groups per CTA, 1-4; 0 = by size / autotuner), "jacobi64_gram"

@@ -157,6 +157,7 @@ struct dmrg_ctx {
     int mixed_svd64 = 0;         // 3xTF32 form with the FP64 SVD and split (contractions alone in reduced precision)
     int qr_wpanel = 1;           // QR panels of <= 256 rows: one warp per column (k_qr_panel_w)
     int f64_fill = 1;            // FP64 GEMM: 32 x 32 tiles and split K when 64 x 64 tiles leave SMs idle
+    int f32_fill = 1;            // the same for the FP32 small products of the mixed form
     int tc_presplit = 1;         // matvec: L, R split once per update; x and the mix output split by their producers
     int lz_fused = 1;            // Lanczos: one cooperative launch per step for the orthogonalisation
     int cjac32 = 1;              // FP32 Jacobi: one-cluster kernel (cjacobi.cu) from cjac_min_r vectors on
@@ -300,7 +301,7 @@ dmrg_status gemm_f64x(dmrg_ctx *ctx, int M, int N, int K, double alpha, const do
                       double beta, double *C, long long sCm, long long sCn, long long sCb, int batch);
 
 // Same contract with FP32 arithmetic (small products of the mixed form).
-dmrg_status gemm_f32c(cudaStream_t st, int M, int N, int K, double alpha, const double *A, long long sAm,
+dmrg_status gemm_f32c(dmrg_ctx *ctx, int M, int N, int K, double alpha, const double *A, long long sAm,
                       long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
                       double beta, double *C, long long sCm, long long sCn, long long sCb, int batch);
 

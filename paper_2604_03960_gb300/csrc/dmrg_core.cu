@@ -697,6 +697,11 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         ctx->f64_fill = (int)value;
         return DMRG_OK;
     }
+    if (!std::strcmp(name, "f32_fill")) {
+        if (!(value == 0.0 || value == 1.0)) return DMRG_EINVAL;
+        ctx->f32_fill = (int)value;
+        return DMRG_OK;
+    }
     if (!std::strcmp(name, "tc_presplit")) {
         if (!(value == 0.0 || value == 1.0)) return DMRG_EINVAL;
         ctx->tc_presplit = (int)value;

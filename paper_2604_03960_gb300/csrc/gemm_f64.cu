@@ -247,16 +247,53 @@ dmrg_status gemm_f64(cudaStream_t st, int M, int N, int K, double alpha, const d
     return DMRG_OK;
 }
 
-dmrg_status gemm_f32c(cudaStream_t st, int M, int N, int K, double alpha, const double *A, long long sAm,
+// FP32 small products of the mixed form, sized to the GPU like the FP64
+// kernel: a product that makes fewer 64 x 64 tiles than SMs (H_eff stage 3
+// at chi = 50 is 4 of them, each walking K = 250 alone) takes 32 x 32 tiles
+// and, if that is still under one CTA per SM, split K (>= 32 terms a slice,
+// each slice with its compensated accumulation) with the slices added in
+// order in FP64 (deterministic).
+dmrg_status gemm_f32c(dmrg_ctx *ctx, int M, int N, int K, double alpha, const double *A, long long sAm,
                       long long sAk, long long sAb, const double *B, long long sBk, long long sBn, long long sBb,
                       double beta, double *C, long long sCm, long long sCn, long long sCb, int batch)
 {
     if (M <= 0 || N <= 0 || batch <= 0) return DMRG_OK;
     if (batch > 65535) return DMRG_EINVAL;
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
-    if (grid.y > 65535) return DMRG_EINVAL;
+    cudaStream_t st = ctx->stream;
     if (K < 0) K = 0;
-    k_gemm_t<float><<<grid, NT, 0, st>>>(M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn, sCb); DMRG_COUNT_LAUNCH();
+    const long long t64 = (long long)((N + 63) / 64) * ((M + 63) / 64) * batch;
+    if (!ctx->f32_fill || t64 >= ctx->num_sms) {
+        dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+        if (grid.y > 65535) return DMRG_EINVAL;
+        k_gemm_t<float><<<grid, NT, 0, st>>>(M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn,
+                                             sCb); DMRG_COUNT_LAUNCH();
+        DMRG_CUDA(cudaGetLastError());
+        return DMRG_OK;
+    }
+    dim3 grid((N + 31) / 32, (M + 31) / 32, batch);
+    if (grid.y > 65535) return DMRG_EINVAL;
+    const long long t32 = (long long)grid.x * grid.y * batch;
+    int nsl = (int)std::min<long long>((ctx->num_sms + t32 - 1) / t32, K / 32);
+    if (nsl < 1) nsl = 1;
+    if ((long long)batch * nsl > 65535) nsl = 1;
+    if (nsl == 1) {
+        k_gemm_t<float, 32><<<grid, NT, 0, st>>>(M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm,
+                                                  sCn, sCb); DMRG_COUNT_LAUNCH();
+        DMRG_CUDA(cudaGetLastError());
+        return DMRG_OK;
+    }
+    int kps = (K + nsl - 1) / nsl;
+    kps = (kps + BK - 1) / BK * BK;
+    nsl = (K + kps - 1) / kps;
+    const long long total = (long long)M * N * batch;
+    DMRG_TRY(ctx->f64buf.ensure(sizeof(double) * (size_t)total * nsl));
+    double *P = ctx->f64buf.as<double>();
+    grid.z = batch * nsl;
+    k_gemm_t<float, 32><<<grid, NT, 0, st>>>(M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn,
+                                              sCb, nsl, kps, P); DMRG_COUNT_LAUNCH();
+    long long blocks = (total + 255) / 256;
+    if (blocks > 4LL * ctx->num_sms) blocks = 4LL * ctx->num_sms;
+    k_gemm_reduce<<<(int)blocks, 256, 0, st>>>(P, nsl, batch, M, N, alpha, beta, C, sCm, sCn, sCb); DMRG_COUNT_LAUNCH();
     DMRG_CUDA(cudaGetLastError());
     return DMRG_OK;
 }

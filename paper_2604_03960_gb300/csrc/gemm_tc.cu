@@ -536,7 +536,7 @@ dmrg_status gemm_3xtf32_pre(dmrg_ctx *ctx, int M, int N, int K, double alpha, co
     // splitting into TF32 parts, at the same precision class
     if (K <= 0 || (!ctx->tc_force && (double)M * N * K * batch < (double)ctx->tc_min_work)) {
         prof_mark(ctx, PROF_F32_GEMM);
-        dmrg_status e = gemm_f32c(ctx->stream, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn,
+        dmrg_status e = gemm_f32c(ctx, M, N, K, alpha, A, sAm, sAk, sAb, B, sBk, sBn, sBb, beta, C, sCm, sCn,
                                   sCb, batch);
         prof_mark(ctx, PROF_F32_GEMM);
         prof_count(ctx, PROF_F32_GEMM, 2.0 * M * N * (double)(K > 0 ? K : 0) * batch, 0.0);
