@@ -177,6 +177,9 @@ const char *dmrg_status_string(dmrg_status s);
  * the Lanczos vector and mix output by the kernels that make them; 0: every
  * product splits its operands), "lz_fused" (1, default: one cooperative
  * launch per Lanczos step for both Gram-Schmidt passes; 0: five launches),
+ * "lz_cluster_n" (the fused step on one thread-block cluster, with cluster
+ * barriers instead of grid barriers, for vectors up to this length; 4096
+ * by default, 0 = never),
  * "f64_fill" (1, default: FP64 GEMMs that would leave SMs idle take 32 x 32
  * tiles and split K), "f32_fill" (1, default: the same for the FP32
  * small products of the mixed form), "gjac32" (grouped block

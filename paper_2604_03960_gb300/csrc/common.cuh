@@ -160,6 +160,8 @@ struct dmrg_ctx {
     int f32_fill = 1;            // the same for the FP32 small products of the mixed form
     int tc_presplit = 1;         // matvec: L, R split once per update; x and the mix output split by their producers
     int lz_fused = 1;            // Lanczos: one cooperative launch per step for the orthogonalisation
+    long long lz_cluster_n = 4096;    // ... on one thread-block cluster instead, for vectors up to this length (0 = never):
+                                      // measured faster at 4096 (chi 32), slower at 16384 (chi 64)
     int cjac32 = 1;              // FP32 Jacobi: one-cluster kernel (cjacobi.cu) from cjac_min_r vectors on
     int cjac_min_r = 32;
     int cjac_force_c = 0;        // cluster Jacobi: 8 or 16 CTAs forced (autotuner, option), 0 = by size

@@ -707,6 +707,11 @@ dmrg_status dmrg_set_option(dmrg_ctx *ctx, const char *name, double value)
         ctx->tc_presplit = (int)value;
         return DMRG_OK;
     }
+    if (!std::strcmp(name, "lz_cluster_n")) {
+        if (!(value >= 0.0 && value <= 1e9)) return DMRG_EINVAL;
+        ctx->lz_cluster_n = (long long)value;
+        return DMRG_OK;
+    }
     if (!std::strcmp(name, "lz_fused")) {
         if (!(value == 0.0 || value == 1.0)) return DMRG_EINVAL;
         ctx->lz_fused = (int)value;

@@ -16,6 +16,8 @@
 #include "common.cuh"
 #include "lanczos.cuh"
 
+#include <cooperative_groups.h>
+
 namespace dmrg {
 namespace {
 
@@ -330,6 +332,106 @@ __global__ void __launch_bounds__(OB) k_lz_orth(double *__restrict__ V, double *
     }
 }
 
+// The same step on one thread-block cluster of C CTAs (no grid barrier):
+// each CTA's partial sums stay in its shared memory, and after a cluster
+// barrier every CTA adds the C partials through distributed shared memory in
+// rank order (lane r reads rank r, then a butterfly), so all CTAs get the
+// same bits.  Three cluster barriers a step: after each pass's partials, and
+// before exit (no CTA leaves while another may read its partials).
+template <int OB, int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(OB)
+    k_lz_orth_cl(double *__restrict__ V, double *__restrict__ w, long long n, int j, LzState *lz, SplitSink sink)
+{
+    if (!lz->active) return;                 // the same in every CTA of the cluster
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ double red[];          // (MAXQ + 1) x OB
+    __shared__ double pa[MAXQ + 1], pb[MAXQ + 1], cs[MAXQ + 1];
+    const int rank = (int)cluster.block_rank();
+    const int nq = j + 1;
+    const int K = lz->K;
+    const double amax0 = lz->amax;
+    const long long stride = (long long)C * OB;
+    const long long i0 = (long long)rank * OB + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto cluster_sum = [&](double *part, bool last) {
+        for (int q = warp; q <= MAXQ; q += OB / 32) {
+            if (!(q < nq || (last && q == MAXQ))) continue;
+            double s = lane < C ? cluster.map_shared_rank(part, lane)[q] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) cs[q] = s;
+        }
+        __syncthreads();
+    };
+    // phase A: c = V^T w
+    double acc[MAXQ + 1];
+#pragma unroll
+    for (int q = 0; q <= MAXQ; ++q) acc[q] = 0.0;
+    for (long long i = i0; i < n; i += stride) {
+        const double wi = w[i];
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q)
+            if (q < nq) acc[q] = fma(V[(long long)q * n + i], wi, acc[q]);
+    }
+    block_cols_to<OB>(acc, nq, false, red, pa);
+    cluster.sync();
+    cluster_sum(pa, false);
+    const double alpha = cs[j];
+    const double amax = fmax(amax0, fabs(alpha));
+    // phase B: w1 = w - V c; c' = V^T w1 and |w1|^2 in the same pass
+    double acc2[MAXQ + 1];
+#pragma unroll
+    for (int q = 0; q <= MAXQ; ++q) acc2[q] = 0.0;
+    for (long long i = i0; i < n; i += stride) {
+        double v[MAXQ];
+        double a = 0.0;
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q)
+            if (q < nq) {
+                v[q] = V[(long long)q * n + i];
+                a = fma(cs[q], v[q], a);
+            }
+        const double wi = w[i] - a;
+        w[i] = wi;
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q)
+            if (q < nq) acc2[q] = fma(v[q], wi, acc2[q]);
+        acc2[MAXQ] = fma(wi, wi, acc2[MAXQ]);
+    }
+    __syncthreads();                         // cs is rewritten below
+    block_cols_to<OB>(acc2, nq, true, red, pb);
+    cluster.sync();
+    cluster_sum(pb, true);
+    // phase C, as in k_lz_orth
+    double cc = 0.0;
+    for (int q = 0; q < nq; ++q) cc = fma(cs[q], cs[q], cc);
+    const double b2 = cs[MAXQ] - cc;
+    const double bta = b2 > 0.0 ? sqrt(b2) : (b2 == 0.0 ? 0.0 : b2);
+    const bool go = (j + 1 < K) && (bta > 1e-14 * amax) && isfinite(bta);
+    if (rank == 0 && threadIdx.x == 0) {
+        lz->alpha[j] = alpha;
+        lz->amax = amax;
+        lz->beta[j + 1] = bta > 0.0 ? bta : 0.0;
+        lz->m = j + 1;
+        if (!go) lz->active = 0;
+        if (!isfinite(bta)) lz->nan = 1;
+    }
+    if (go) {
+        const double inv = 1.0 / bta;
+        double *vn = V + (long long)(j + 1) * n;
+        for (long long i = i0; i < n; i += stride) {
+            double a = 0.0;
+#pragma unroll
+            for (int q = 0; q < MAXQ; ++q)
+                if (q < nq) a = fma(cs[q], V[(long long)q * n + i], a);
+            const double v = (w[i] - a) * inv;
+            vn[i] = v;
+            if (sink.h) sink_write(sink, i, v);
+        }
+    }
+    cluster.sync();
+}
+
 // The split of a vector for the next matvec (start vector; the unfused path)
 __global__ void k_sink_vec(const double *__restrict__ v, long long n, SplitSink sink, const LzState *lz)
 {
@@ -562,6 +664,45 @@ int grid_orth(long long n, int num_sms)
     return (int)b;
 }
 
+constexpr int kOBC = 256;     // threads per CTA of the cluster form (199 registers a thread)
+
+// Whether a cluster of C CTAs of the cluster form can be resident (queried
+// once per size; a launch that cannot is not attempted).
+template <int C>
+bool lz_cluster_fits()
+{
+    static int ok = -1;
+    if (ok >= 0) return ok == 1;
+    ok = 0;
+    const int smem = (int)(sizeof(double) * (MAXQ + 1) * kOBC);
+    if (cudaFuncSetAttribute(k_lz_orth_cl<kOBC, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (C > 8 && cudaFuncSetAttribute(k_lz_orth_cl<kOBC, C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                     cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kOBC);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = C;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    ok = (cudaOccupancyMaxActiveClusters(&nc, (const void *)k_lz_orth_cl<kOBC, C>, &cfg) == cudaSuccess && nc >= 1)
+             ? 1
+             : 0;
+    cudaGetLastError();
+    return ok == 1;
+}
+
 int grid_for(long long n, int num_sms)
 {
     long long b = (n + RB - 1) / RB;
@@ -628,10 +769,26 @@ dmrg_status lanczos_run(dmrg_ctx *ctx, const LanczosWork &w, long long n, int K,
                                        (int)(sizeof(double) * (MAXQ + 1) * kOB)));
         orth_attr = true;
     }
+    // cluster size of the cluster form (0: not available)
+    const int lz_c = ctx->lz_cluster_n > 0 ? (lz_cluster_fits<16>() ? 16 : (lz_cluster_fits<8>() ? 8 : 0)) : 0;
     for (int j = 0; j < K; ++j) {
         double *vj = w.V + (size_t)n * j;
         DMRG_TRY(matvec(vj, w.w));
         prof_mark(ctx, PROF_LZ_VEC);
+        if (ctx->lz_fused && n <= ctx->lz_cluster_n && (lz_c == 16 || lz_c == 8)) {
+            // the same step on one thread-block cluster: hardware cluster
+            // barriers instead of grid barriers
+            const size_t sm = sizeof(double) * (MAXQ + 1) * kOBC;
+            if (lz_c == 16)
+                k_lz_orth_cl<kOBC, 16><<<16, kOBC, sm, st>>>(w.V, w.w, n, j, w.lz, sink);
+            else
+                k_lz_orth_cl<kOBC, 8><<<8, kOBC, sm, st>>>(w.V, w.w, n, j, w.lz, sink);
+            DMRG_COUNT_LAUNCH();
+            prof_mark(ctx, PROF_LZ_VEC);
+            prof_count(ctx, PROF_LZ_VEC, 0.0, 8.0 * (double)n * (3.0 * (j + 1) + 7.0));
+            DMRG_CUDA(cudaGetLastError());
+            continue;
+        }
         if (ctx->lz_fused) {
             // both Gram-Schmidt passes, the norm and v_{j+1} in one cooperative launch
             double *Vp = w.V, *wp = w.w, *pp = w.partials;

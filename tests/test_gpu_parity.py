@@ -197,12 +197,16 @@ def canonical_envs(rng, N, k, chi, model=O.MODEL_XXZ):
     return W, L, R
 
 
-# lz_fused = 1: both Gram-Schmidt passes, the norm and the next vector in one
-# cooperative launch per step; 0: five launches per step
-@pytest.mark.parametrize("fused", [1, 0])
+# Forms of a Lanczos step's orthogonalisation: "cluster" = both Gram-Schmidt
+# passes, the norm and the next vector in one launch on a thread-block
+# cluster (cluster barriers, partial sums through distributed shared memory);
+# "grid" = the same in one cooperative launch (grid barriers); "unfused" =
+# five launches per step
+@pytest.mark.parametrize("form", ["cluster", "grid", "unfused"])
 @pytest.mark.parametrize("N,k,chi", [(8, 3, 8), (12, 5, 24), (14, 6, 48), (18, 8, 160)])
-def test_lanczos_fp64(ctx, N, k, chi, fused):
-    ctx.set_option("lz_fused", fused)
+def test_lanczos_fp64(ctx, N, k, chi, form):
+    ctx.set_option("lz_fused", 0 if form == "unfused" else 1)
+    ctx.set_option("lz_cluster_n", 1e9 if form == "cluster" else 0)
     rng = np.random.default_rng(N * 100 + chi)
     W, L, R = canonical_envs(rng, N, k, chi)
     cl, cr = L.shape[1], R.shape[1]
@@ -210,6 +214,7 @@ def test_lanczos_fp64(ctx, N, k, chi, fused):
     E_ref, th_ref, steps_ref, _, _ = O.lanczos(L, W[k], W[k + 1], R, th, K=20)
     E, th_g, steps = ctx.lanczos(dev(L), dev(W[k]), dev(W[k + 1]), dev(R), dev(th), K=20)
     ctx.set_option("lz_fused", 1)
+    ctx.set_option("lz_cluster_n", 4096)
     assert steps == steps_ref
     assert abs(E - E_ref) <= 1e-11 * max(1.0, abs(E_ref))
     ov = abs(np.dot(th_g.cpu().numpy().ravel(), th_ref.ravel()))
