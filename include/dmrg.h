@@ -162,9 +162,10 @@ void dmrg_destroy(dmrg_ctx *ctx);
 dmrg_status dmrg_get_status(dmrg_ctx *ctx);
 const char *dmrg_status_string(dmrg_status s);
 /* Tuning knobs of a context (no counterpart in the paper): "tc_force" (1: use
- * the tensor cores even for tiny products), "tc_min_work" (multiply-adds
- * below which 3xTF32 requests run on the FP64 kernel), "tc_bn" (0, 128 or
- * 256: tile width of the tensor-core GEMM, 0 = heuristic), "tc_split_kb"
+ * the tensor cores even for tiny products), "tc_min_work" (M N K below
+ * which 3xTF32 requests run on the FP32 CUDA-core kernel with compensated
+ * sums; 2^24 by default), "tc_bn" (0, 64, 128 or 256: tile width of the
+ * tensor-core GEMM, 0 = heuristic), "tc_split_kb"
  * (tensor-core GEMM: most 32-wide blocks of the 3 K split products one FP32
  * accumulator sums, 8; beyond, K is split and the slices added in FP64;
  * 0 = never split), "cjac32" (1, default: the FP32 Jacobi of the mixed form

@@ -117,7 +117,8 @@ struct dmrg_ctx {
     int tc_ok = -1;              // -1 unknown, 0 no, 1 yes
     int tc_bn_override = 0;      // force a tile width (autotuner / tests)
     int tc_force = 0;            // use the tensor cores even for tiny products
-    double tc_min_work = 4194304.0;   // M*N*K below which the FP64 kernel is used
+    double tc_min_work = 16777216.0;  // M*N*K below which the FP32 CUDA-core kernel takes 3xTF32 requests
+                                      // (measured: chi 64 update 2.60 -> 2.41 ms against 2^22; neutral at 48, 96, 128)
     int tc_split_kb = 8;         // tensor-core GEMM: at most this many 32-wide K' blocks per FP32 accumulator
                                  // (split K with an FP64 reduction beyond; 0 = never split)
     int prof = 0;
