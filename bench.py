@@ -971,6 +971,14 @@ def roofline(prof_dom, dom, clk, num_sms):
                 "traffic": None,
                 "peak_note": "FP32: %d SMs x 128 lanes x 2 flops x median SM clock %.0f MHz" % (num_sms, mhz),
                 "hbm_view_gbs": d["bytes"] / sec / 1e9}
+        if dom == 1 and d["bytes"] > 0:
+            # ncu dram read + write of the cluster Jacobi (k_cjac32, unchanged
+            # since): 85 KB at r = l = 128 and 187 KB at 148 x 256, i.e. 0.65
+            # and 0.62 of its 8 r l algorithmic bytes (the vectors are read once
+            # and stay in shared memory); scaled by this run's algorithmic bytes
+            roof["traffic"] = 0.635 * d["bytes"] / d["launches"]
+            roof["traffic_note"] = ("bytes per launch: ncu dram read+write of k_cjac32 at theta 128 x 128 and "
+                                    "256 x 148 (0.65 and 0.62 of 8 r l), scaled by the launches' 8 r l")
     else:
         # FP64 kernels: the nominal FP64 rate scaled to the sampled clock
         peak = 1.25 * mhz / 2070.0 * num_sms / 152.0

@@ -23,3 +23,21 @@ def test_kernel_rates_units_and_skips():
     assert abs(r["gemm"]["gflops"] - 2.0e6) < 1e-6 and "gbs" not in r["gemm"]
     assert abs(r["mix"]["gbs"] - 5000.0) < 1e-9 and abs(r["mix"]["frac_hbm"] - 0.625) < 1e-12
     assert r["decide"] == {"ms_per_step": 25.0, "launches_per_step": 50.0}
+
+
+def test_roofline_alu_peak_and_jacobi_traffic():
+    """The FP32 Jacobi kind (1) is reported against the FP32 ALU peak of this
+    device's SM count at the sampled clock, with its per-launch DRAM traffic
+    scaled from the ncu capture by the launches' algorithmic bytes; the mix
+    (4) against the measured copy bandwidth, with no traffic figure."""
+    d = dict(ms=250.0, launches=400, flops=6.0e10, bytes=8.0e8)     # 2 MB of 8 r l a launch
+    r = bench.roofline(d, 1, {"sm_mhz": 1000.0}, 100)
+    peak = 100 * 128 * 2 * 1000.0e6 / 1e12
+    assert r["bound"] == "alu" and abs(r["peak"] - peak) < 1e-12
+    assert abs(r["achieved"] - 6.0e10 / 0.25 / 1e12) < 1e-12 and abs(r["frac"] - r["achieved"] / peak) < 1e-15
+    assert abs(r["traffic"] - 0.635 * 2.0e6) < 1e-6 and "100 SMs" in r["peak_note"]
+    assert r["launches"] == 400 and abs(r["avg_launch_us"] - 625.0) < 1e-9
+    m = bench.roofline(dict(ms=100.0, launches=10, flops=0.0, bytes=5.0e11), 4, {"sm_mhz": 2070.0}, 152)
+    hbm = bench.peaks()[0]
+    assert m["bound"] == "hbm" and m["traffic"] is None
+    assert abs(m["achieved"] - 5000.0) < 1e-9 and abs(m["frac"] - 5000.0 / hbm) < 1e-12
