@@ -8,11 +8,13 @@
 //   1. the Gram block G_p = P_p P_p^T, a 3xTF32 tcgen05 product batched over
 //      the round's pairs (K = l, split over several FP32 accumulators whose
 //      partial sums meet in FP64);
-//   2. one cyclic Jacobi sweep on G_p in one CTA (FP32, shared memory): the
-//      Schur rotation of every pair (i, j) of the 2b vectors whose cosine
-//      g_ij / sqrt(g_ii g_jj) exceeds the tolerance, applied to G_p from
-//      both sides and accumulated in Q_p; then one Newton-Schulz step makes
-//      Q_p orthogonal to FP32 rounding;
+//   2. one Jacobi sweep on G_p in one CTA (FP32, shared memory): the Schur
+//      rotation of every pair (i, j) whose cosine g_ij / sqrt(g_ii g_jj)
+//      exceeds the tolerance, applied to G_p from both sides and accumulated
+//      in Q_p -- all pairs of the 2b vectors in the first round of an outer
+//      sweep (every block takes part in it), only the b^2 pairs between the
+//      two blocks in the later rounds; then one Newton-Schulz step makes Q_p
+//      orthogonal to FP32 rounding;
 //   3. the block rotation P_p <- Q_p^T P_p, a second 3xTF32 tcgen05 product
 //      (M = 2b, N = l, K = 2b), written back in place in FP32.
 // Block slots are paired in odd-even order: even rounds pair slots (0, 1),
