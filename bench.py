@@ -904,7 +904,7 @@ def isolated_svd(G, synth, chis=(256, 1024, 2048), fp64_chis=(256,), reps=3):
     """Config-2 isolated SVDs (2chi x 2chi, Haar factors, s_k = exp(-k/(0.1 chi))):
     ms per call and nominal GFLOP/s (21 n^3) for the mixed and FP64 forms, the
     outer Jacobi sweeps, and which FP32 Jacobi ran (the tensor-core block form
-    from 2560 vectors on, at the library's defaults)."""
+    from 3072 vectors on, at the library's defaults)."""
     import torch
     out = {}
     for form, cs in (("mixed", chis), ("fp64", fp64_chis)):
@@ -925,7 +925,7 @@ def isolated_svd(G, synth, chis=(256, 1024, 2048), fp64_chis=(256,), reps=3):
             e = {"ms": ms, "gflops_nominal": 21.0 * n ** 3 / (ms / 1e3) / 1e9, "sweeps": ctx.svd_last_sweeps()}
             if form == "mixed":
                 e["jacobi"] = ("tcgen05 block Jacobi (Gram blocks and rotations as 3xTF32 GEMMs, pairs of 128)"
-                               if n >= 2560 else "FP32 cluster / blocked Jacobi")
+                               if n >= 3072 else "FP32 cluster / blocked Jacobi")
             # measured accuracy of the factors against the known spectrum
             import numpy as np
             U, sv, Vt, k, S, err = ctx.svd_truncate(A, n, 0.0)

@@ -207,7 +207,7 @@ const char *dmrg_status_string(dmrg_status s);
  * Jacobi with pairs of that many vectors, whose Gram blocks G = P P^T and
  * block rotations P <- Q^T P are 3xTF32 tcgen05 GEMMs around one Jacobi sweep
  * of each G in a CTA; 0 = off; default 128), "tjac_min_r" (from this many
- * vectors on, ahead of the other FP32 kernels; default 2560; not taken
+ * vectors on, ahead of the other FP32 kernels; default 3072; not taken
  * while the stream is captured, since it reads a convergence counter on the
  * host once per outer sweep), "jacobi_max_sweeps" (standalone
  * svd_truncate and svd_truncate_batched), "batched_inner" (svd_truncate_batched:

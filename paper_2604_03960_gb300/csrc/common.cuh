@@ -145,8 +145,8 @@ struct dmrg_ctx {
     dmrg::DevBuf work4;          // batched SVD workspace
     dmrg::DevBuf tjbuf;          // tensor-core block Jacobi workspace (tjacobi.cu)
     int tjac = 128;              // FP32 Jacobi: tensor-core block form with pairs of tjac (64, 128) vectors; 0 = off
-    int tjac_min_r = 2560;       // ... from this many vectors on (ahead of the other kernels; measured faster
-                                 // than the blocked grid kernel at 4096 vectors, slower at 2048)
+    int tjac_min_r = 3072;       // ... from this many vectors on (ahead of the other kernels; measured faster
+                                 // than the blocked grid kernel at 3072 and 4096 vectors, slower at 2048 and 2560)
     int batched_inner = 4;       // batched SVD: inner Jacobi sweeps per block pair
     int batched_ns = 1;          // FP32 batched SVD: Newton-Schulz step on each block rotation
     int jacobi_qr = 1;           // FP32 Jacobi on the R factor of the vectors (QR preconditioning)
