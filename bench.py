@@ -43,7 +43,7 @@ WORKLOADS = {
     # own count.  ref_chi: the bond dimension the oracle sample runs at (about
     # the timed sweeps' mean retained chi).
     "xxz_n200_chi1024": dict(N=200, chi_max=1024, Delta=1.0, chi_init=4, model="XXZ (Delta=1, Heisenberg)",
-                             ctrl="CTRL_PID", sweep_flops=2.05e11, ref_chi=50),
+                             ctrl="CTRL_PID", sweep_flops=2.271e11, ref_chi=51),
     # the same chain under threshold truncation alone (labelled comparison)
     "xxz_n200_chi1024_threshold": dict(N=200, chi_max=1024, Delta=1.0, chi_init=16,
                                        model="XXZ (Delta=1, Heisenberg)", ctrl="CTRL_THRESHOLD"),
